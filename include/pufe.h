@@ -1,0 +1,181 @@
+/*
+ * pufe.h -- C ABI of the GB300 PUFE hot path.
+ *
+ * The library assembles the partition-of-unity finite element (PUFE)
+ * Hamiltonian H and overlap S of a periodic cell at the Gamma point, and
+ * evaluates the electron density at the quadrature points, on one NVIDIA
+ * GB300 (sm_103a).  It follows Pask & Sukumar, "Partition of unity finite
+ * element method for quantum mechanical materials calculations":
+ *   - basis (Sec. 4, eqs. pufebasis/psih): tricubic Lagrange FE functions on
+ *     every node, plus trilinear-PU x enrichment products phi_j^PU Psi_alpha
+ *     on every PU vertex j within r_e of alpha's atom (Sec. 5.1);
+ *   - enrichments (Sec. 5.1, eqs. Psitilde/Psi): R_nl(r) Y_lm h(r, r_c),
+ *     summed over periodic images; R_nl is a normalised Slater-type orbital
+ *     N r^(n-1) e^(-zeta r), Y_lm real and unit-normalised;
+ *   - matrices (Sec. 4, eq. disceig3d, local potential):
+ *       H_ij = int 1/2 grad phi_i . grad phi_j + phi_i V phi_j,
+ *       S_ij = int phi_i phi_j,
+ *     with every integral taken on one shared element quadrature rule
+ *     (Sec. 5.2);
+ *   - density (Sec. 3, eq. rhoe): n(x_q) = sum_k f_k |psi_k(x_q)|^2 >= 0
+ *     (the paper's rho_e = -n).
+ *
+ * Conventions
+ *   Units: bohr and hartree.  Cubic or orthorhombic cells only.
+ *   Numbering: elements e = ex + nx (ey + ny ez).  FE DOFs are the nodes of
+ *   the (3nx)(3ny)(3nz) periodic grid, index gx + 3nx (gy + 3ny gz); they are
+ *   followed by the enrichment DOFs ordered by (atom, orbital, enriched
+ *   vertex index).  Quadrature points are stored element by element; within
+ *   an element a tensor rule runs x fastest, and subdivided cells are
+ *   visited depth first in the order a + 2b + 4c of their octant offsets.
+ *   Matrices: one CSR pattern (int64 row pointers, int32 sorted column
+ *   indices, both triangles stored) shared by H and S; values are float64.
+ *   Ownership: the caller owns every pointer it passes.  The context owns
+ *   the mesh, rules, tables and work arrays and frees them in
+ *   pufe_destroy.  Device pointers must be on the context's device.
+ *   Streams: `stream` is a cudaStream_t (NULL = legacy default stream).
+ *   Compute calls are asynchronous on that stream; they never synchronise.
+ *   Errors: every call returns a pufe_status; pufe_last_error() gives a
+ *   message for the calling thread.  No call aborts or throws.
+ */
+#ifndef PUFE_H
+#define PUFE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pufe_ctx pufe_ctx;
+
+typedef enum {
+  PUFE_OK = 0,
+  PUFE_EINVAL = 1,   /* bad argument (size, pointer, mode) */
+  PUFE_ENOMEM = 2,   /* host or device allocation failed */
+  PUFE_ECUDA = 3,    /* a CUDA runtime call failed */
+  PUFE_ENOTSPD = 4,  /* reserved: S not positive definite */
+  PUFE_ENOTCONV = 5, /* reserved: SCF did not converge */
+  PUFE_ETIMEOUT = 6, /* a bounded device wait gave up */
+  PUFE_EDEVICE = 7,  /* a kernel reported a device-side error flag */
+  PUFE_ESTATE = 8    /* call out of order (e.g. assemble before tabulate) */
+} pufe_status;
+
+/* Arithmetic of the element contractions. */
+typedef enum {
+  PUFE_FP64 = 0,   /* FP64 everywhere (plain CUDA cores) */
+  PUFE_TF32X3 = 1  /* tcgen05 kind::tf32 with a 3-term hi/lo split, FP32
+                      accumulation in TMEM; FP64 kept for the enrichment-
+                      enrichment block of S and for global accumulation */
+} pufe_prec;
+
+/* Quadrature modes (Sec. 5.2). */
+enum {
+  PUFE_QUAD_FIXED = 0,  /* p_near^3 Gauss on elements within r_c of an atom
+                           image, p_far^3 elsewhere */
+  PUFE_QUAD_PADAPT = 1, /* per element the smallest p in [p_min, p_max] with
+                           |I_p - I_(p+2)| < tol for Psi^2 and |grad Psi|^2 of
+                           every enrichment of the element; p_min^3 on
+                           elements without enrichment */
+  PUFE_QUAD_HADAPT = 2  /* the paper's recursive scheme: 5^3 against the 8^3
+                           reference, failing integrands passed to the 8
+                           children, 8^3 kept on accepted (or max_depth)
+                           cells; p_far^3 on elements without enrichment */
+};
+
+/* what to assemble */
+enum { PUFE_WANT_H = 1, PUFE_WANT_S = 2 };
+
+typedef struct {
+  double a[3];         /* cell edge lengths (bohr), orthorhombic */
+  int nel[3];          /* elements per axis, each >= 1 */
+  int natoms;          /* >= 0 */
+  const double *tau;   /* natoms x 3 Cartesian positions (host) */
+  const int *species;  /* natoms species indices (host) */
+} pufe_cell;
+
+typedef struct {
+  int norb;            /* enrichment orbitals of this species, >= 0 */
+  const int *n;        /* principal quantum numbers, 1 <= n <= 8 (host) */
+  const int *l;        /* 0 <= l <= 3, l < n (host) */
+  const int *m;        /* -l <= m <= l (host) */
+  const double *zeta;  /* Slater exponents > 0 (host) */
+  double r_c;          /* cutoff radius of h(r, r_c) (bohr), > 0 */
+  double r_e;          /* support radius: vertices within r_e are enriched */
+} pufe_species;
+
+typedef struct {
+  int mode;            /* PUFE_QUAD_* */
+  int p_far, p_near;   /* FIXED: Gauss orders; HADAPT: p_far for plain cells */
+  int p_min, p_max;    /* PADAPT range (1..16) */
+  double tol;          /* absolute tolerance of the adaptive tests */
+  int max_depth;       /* HADAPT subdivision depth limit (0..4) */
+} pufe_quad;
+
+/* Build the mesh, enrichment sets, quadrature rules, CSR pattern and scatter
+ * maps on the host (Secs. 4, 5.1, 5.2) and copy them to the current CUDA
+ * device.  Blocking.  *out receives a new context. */
+pufe_status pufe_build_mesh(const pufe_cell *cell, const pufe_species *species,
+                            int nspecies, const pufe_quad *quad, pufe_ctx **out);
+
+/* Sizes: number of DOFs N, CSR non-zeros, quadrature points, elements and
+ * the largest element basis size.  Any pointer may be NULL. */
+pufe_status pufe_get_sizes(const pufe_ctx *ctx, int64_t *n_dof, int64_t *nnz,
+                           int64_t *n_q, int64_t *n_elem, int64_t *max_basis);
+
+/* Copy the quadrature rule to host buffers: points x (n_q x 3), weights w
+ * (n_q, Jacobian folded in) and element offsets (n_elem + 1).  NULL skips. */
+pufe_status pufe_get_quadrature(const pufe_ctx *ctx, double *x, double *w,
+                                int64_t *elem_offsets);
+
+/* Copy the CSR pattern to host buffers rowptr (N + 1) and col (nnz). */
+pufe_status pufe_get_pattern(const pufe_ctx *ctx, int64_t *rowptr, int32_t *col);
+
+/* Per-element basis sizes n_e (n_elem int32, host) and, optionally, the
+ * global DOF of every element column (sum n_e int32, host; element-major,
+ * 64 FE columns first). */
+pufe_status pufe_get_element_basis(const pufe_ctx *ctx, int32_t *n_e, int32_t *dofs);
+
+/* K0 (Sec. 5.1, eqs. Psitilde/Psi): tabulate Psi_alpha and grad Psi_alpha at
+ * every quadrature point of every element for the enrichments that appear in
+ * that element's basis.  The table lives in the context and is read by the
+ * assembly, density and adjoint kernels.  Asynchronous on `stream`. */
+pufe_status pufe_tabulate(pufe_ctx *ctx, void *stream);
+
+/* K1-K3 (Sec. 4, eq. disceig3d): H and/or S values into caller-owned device
+ * arrays of nnz float64 each (pattern of pufe_get_pattern).  V (n_q float64,
+ * device) is the local potential at the quadrature points; it may be NULL
+ * when only S is wanted.  The arrays are overwritten (zeroed, then
+ * accumulated).  `what` is a mask of PUFE_WANT_H | PUFE_WANT_S.
+ * Requires a prior pufe_tabulate.  Asynchronous. */
+pufe_status pufe_assemble_HS(pufe_ctx *ctx, const double *V, int prec, int what,
+                             double *H, double *S, void *stream);
+
+/* K4 (Sec. 3, eq. rhoe): n_q = sum_k f_k (sum_j B_qj C_jk)^2 for every
+ * quadrature point.  C: device float64, N x nocc, row-major with leading
+ * dimension ldc >= nocc (C[j * ldc + k]); f: device float64 (nocc);
+ * rho: device float64 (n_q), overwritten.  1 <= nocc <= 64.  Asynchronous. */
+pufe_status pufe_density(pufe_ctx *ctx, const double *C, int64_t ldc,
+                         const double *f, int nocc, int prec, double *rho,
+                         void *stream);
+
+/* K5, adjoint of V -> H (Sec. 4): Vbar_q = w_q b_q^T Hbar_e b_q for a
+ * cotangent Hbar given as nnz float64 values on the CSR pattern (device).
+ * Vbar: device float64 (n_q), overwritten.  With Hbar = sum_k f_k c_k c_k^T
+ * this equals w_q n_q.  Asynchronous. */
+pufe_status pufe_assemble_HV_adjoint(pufe_ctx *ctx, const double *Hbar, double *Vbar,
+                                     void *stream);
+
+/* Wait for `stream`, then report (and clear) any device-side error flag. */
+pufe_status pufe_sync_status(pufe_ctx *ctx, void *stream);
+
+/* Release the context and everything it owns.  NULL is a no-op. */
+void pufe_destroy(pufe_ctx *ctx);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *pufe_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PUFE_H */

@@ -1,0 +1,100 @@
+// C ABI entry points of the compute calls: argument checks, device guard,
+// output zeroing and dispatch to the FP64 or tensor-core kernels.
+#include "pufe_internal.h"
+
+namespace pufe {
+namespace {
+
+pufe_status need_device(const pufe_ctx *ctx) {
+  if (!ctx) return fail(PUFE_EINVAL, "ctx is NULL");
+  if (!ctx->on_device) return fail(PUFE_ESTATE, "context was built without a CUDA device");
+  return PUFE_OK;
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+}  // namespace
+}  // namespace pufe
+
+using namespace pufe;
+
+extern "C" {
+
+pufe_status pufe_tabulate(pufe_ctx *ctx, void *stream) {
+  if (pufe_status e0 = need_device(ctx)) return e0;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return fail(PUFE_ECUDA, "cudaSetDevice failed");
+  pufe_status st = launch_tabulate(ctx, (cudaStream_t)stream);
+  if (st == PUFE_OK) ctx->tabulated = true;
+  return st;
+}
+
+pufe_status pufe_assemble_HS(pufe_ctx *ctx, const double *V, int prec, int what, double *H,
+                             double *S, void *stream) {
+  if (pufe_status e0 = need_device(ctx)) return e0;
+  if (!ctx->tabulated && ctx->psi_len > 0) return fail(PUFE_ESTATE, "call pufe_tabulate first");
+  if (what <= 0 || what > (PUFE_WANT_H | PUFE_WANT_S)) return fail(PUFE_EINVAL, "bad `what` mask");
+  if ((what & PUFE_WANT_H) && (!H || !V)) return fail(PUFE_EINVAL, "H wanted: need H and V");
+  if ((what & PUFE_WANT_S) && !S) return fail(PUFE_EINVAL, "S wanted: need S");
+  if (prec != PUFE_FP64 && prec != PUFE_TF32X3) return fail(PUFE_EINVAL, "unknown precision");
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return fail(PUFE_ECUDA, "cudaSetDevice failed");
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t bytes = (size_t)ctx->nnz * sizeof(double);
+  if (what & PUFE_WANT_H) PUFE_CUDA_TRY(cudaMemsetAsync(H, 0, bytes, st));
+  if (what & PUFE_WANT_S) PUFE_CUDA_TRY(cudaMemsetAsync(S, 0, bytes, st));
+  if (prec == PUFE_FP64) return launch_assemble_fp64(ctx, V, what, H, S, st);
+  return launch_assemble_tc(ctx, V, what, H, S, st);
+}
+
+pufe_status pufe_density(pufe_ctx *ctx, const double *C, int64_t ldc, const double *f, int nocc,
+                         int prec, double *rho, void *stream) {
+  if (pufe_status e0 = need_device(ctx)) return e0;
+  if (!ctx->tabulated && ctx->psi_len > 0) return fail(PUFE_ESTATE, "call pufe_tabulate first");
+  if (!C || !f || !rho) return fail(PUFE_EINVAL, "C, f and rho must not be NULL");
+  if (nocc < 1 || nocc > 64 || ldc < nocc) return fail(PUFE_EINVAL, "need 1 <= nocc <= 64 and ldc >= nocc");
+  if (prec != PUFE_FP64 && prec != PUFE_TF32X3) return fail(PUFE_EINVAL, "unknown precision");
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return fail(PUFE_ECUDA, "cudaSetDevice failed");
+  if (prec == PUFE_FP64) return launch_density_fp64(ctx, C, ldc, f, nocc, rho, (cudaStream_t)stream);
+  return launch_density_tc(ctx, C, ldc, f, nocc, rho, (cudaStream_t)stream);
+}
+
+pufe_status pufe_assemble_HV_adjoint(pufe_ctx *ctx, const double *Hbar, double *Vbar,
+                                     void *stream) {
+  if (pufe_status e0 = need_device(ctx)) return e0;
+  if (!ctx->tabulated && ctx->psi_len > 0) return fail(PUFE_ESTATE, "call pufe_tabulate first");
+  if (!Hbar || !Vbar) return fail(PUFE_EINVAL, "Hbar and Vbar must not be NULL");
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return fail(PUFE_ECUDA, "cudaSetDevice failed");
+  return launch_adjoint_fp64(ctx, Hbar, Vbar, (cudaStream_t)stream);
+}
+
+pufe_status pufe_sync_status(pufe_ctx *ctx, void *stream) {
+  if (pufe_status e0 = need_device(ctx)) return e0;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return fail(PUFE_ECUDA, "cudaSetDevice failed");
+  PUFE_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+  unsigned flag = 0;
+  PUFE_CUDA_TRY(cudaMemcpy(&flag, ctx->d.err, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  if (flag) {
+    PUFE_CUDA_TRY(cudaMemset(ctx->d.err, 0, sizeof(unsigned)));
+    if (flag & DEVERR_TIMEOUT) return fail(PUFE_ETIMEOUT, "a device wait gave up");
+    return fail(PUFE_EDEVICE, "kernel reported device error flag " + std::to_string(flag));
+  }
+  return PUFE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,465 @@
+// FP64 CUDA-core kernels of the PUFE hot path:
+//   K0  enrichment tabulation (Sec. 5.1, eqs. Psitilde/Psi)
+//   K1+K2+K3  element basis tile, contraction and scatter (Sec. 4, eq. disceig3d)
+//   K4  density at quadrature points (Sec. 3, eq. rhoe)
+//   K5  adjoint of V -> H (derivative of sum Hbar_ij H_ij with respect to V_q)
+//
+// The element basis (64 tricubic FE columns, then phi_v^PU Psi_alpha columns)
+// is rebuilt on chip from the reference coordinates of each quadrature point
+// and the tabulated Psi / grad Psi; it is never stored in HBM.
+#include <math.h>
+
+#include "pufe_internal.h"
+
+namespace pufe {
+
+namespace {
+
+constexpr int QC = 8;         // quadrature points per chunk
+constexpr int ASM_NT = 256;   // threads of the assembly kernel
+constexpr int DEN_NT = 128;   // threads of the density kernel
+constexpr int ADJ_NT = 256;   // threads of the adjoint kernel
+
+__device__ __forceinline__ void set_err(unsigned *err, unsigned bit) { atomicOr(err, bit); }
+
+// ---------------------------------------------------------------------------
+// K0: Psi and grad Psi for every (enrichment slot, quadrature point) of an element.
+// Layout per element: psi[4*toff[e] + (slot*4 + comp)*Q + q].
+// ---------------------------------------------------------------------------
+__global__ void k_tabulate(const int64_t *__restrict__ qoff, const double *__restrict__ x,
+                           const int32_t *__restrict__ aoff, const int32_t *__restrict__ alist,
+                           const int64_t *__restrict__ toff, const Orbital *__restrict__ orb,
+                           double a0, double a1, double a2, int i0, int i1, int i2,
+                           double *__restrict__ psi) {
+  const int64_t e = blockIdx.x;
+  const int64_t q0 = qoff[e];
+  const int Q = (int)(qoff[e + 1] - q0);
+  const int A = aoff[e + 1] - aoff[e];
+  const double av[3] = {a0, a1, a2};
+  const int img[3] = {i0, i1, i2};
+  double *out = psi + 4 * toff[e];
+  for (int idx = threadIdx.x; idx < Q * A; idx += blockDim.x) {
+    const int slot = idx / Q, q = idx - slot * Q;
+    const Orbital o = orb[alist[aoff[e] + slot]];
+    const double p[3] = {x[3 * (q0 + q)], x[3 * (q0 + q) + 1], x[3 * (q0 + q) + 2]};
+    double v, g[3];
+    enrichment_eval(o, p, av, img, v, g);
+    double *dst = out + (int64_t)slot * 4 * Q + q;
+    dst[0] = v;
+    dst[Q] = g[0];
+    dst[2 * Q] = g[1];
+    dst[3 * Q] = g[2];
+  }
+}
+
+// Basis values and physical gradients of column c at reference point xi.
+// FE column c: node (c&3, (c>>2)&3, c>>4) from the 1D tables L, dL.
+// Enrichment column: PU vertex lv times Psi (value/gradient g4).
+struct Tab1D {
+  double L[3][4], dL[3][4];
+};
+
+__device__ __forceinline__ void fe_column(const Tab1D &t, int c, const double s[3], double &b,
+                                          double &gx, double &gy, double &gz) {
+  const int ia = c & 3, ib = (c >> 2) & 3, ic = c >> 4;
+  const double lx = t.L[0][ia], ly = t.L[1][ib], lz = t.L[2][ic];
+  b = lx * ly * lz;
+  gx = t.dL[0][ia] * ly * lz * s[0];
+  gy = lx * t.dL[1][ib] * lz * s[1];
+  gz = lx * ly * t.dL[2][ic] * s[2];
+}
+
+__device__ __forceinline__ void pu_column(const double xi[3], int lv, const double s[3],
+                                          const double ps[4], double &b, double &gx, double &gy,
+                                          double &gz) {
+  double h[3], dh[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int bit = (lv >> d) & 1;
+    h[d] = bit ? 0.5 * (1.0 + xi[d]) : 0.5 * (1.0 - xi[d]);
+    dh[d] = (bit ? 0.5 : -0.5) * s[d];
+  }
+  const double phi = h[0] * h[1] * h[2];
+  b = phi * ps[0];
+  gx = dh[0] * h[1] * h[2] * ps[0] + phi * ps[1];
+  gy = h[0] * dh[1] * h[2] * ps[0] + phi * ps[2];
+  gz = h[0] * h[1] * dh[2] * ps[0] + phi * ps[3];
+}
+
+// ---------------------------------------------------------------------------
+// K1+K2+K3 (FP64): one CTA per element.  Per chunk of QC points the CTA
+// builds y_d = sqrt(w/2) G_d, z = sqrt(w) B and zv = V z in shared memory;
+// each thread owns 4x4 blocks of the lower triangle and accumulates
+//   H += sum_d y_d y_d^T + zv z^T,   S += z z^T,
+// then adds its entries into the CSR values through the scatter map.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(ASM_NT) k_assemble_fp64(
+    const int32_t *__restrict__ order, const int64_t *__restrict__ qoff,
+    const double *__restrict__ w, const double *__restrict__ xi_all,
+    const int64_t *__restrict__ doff, const int32_t *__restrict__ ecol,
+    const int64_t *__restrict__ toff, const double *__restrict__ psi,
+    const int64_t *__restrict__ soff, const int32_t *__restrict__ smap,
+    const double *__restrict__ V, double sx, double sy, double sz, int npad_max, int want,
+    double *__restrict__ H, double *__restrict__ S, unsigned *err) {
+  extern __shared__ __align__(16) double smem[];
+  const int e = order[blockIdx.x];
+  const int64_t q0 = qoff[e];
+  const int Q = (int)(qoff[e + 1] - q0);
+  const int n = (int)(doff[e + 1] - doff[e]);
+  const int npad = (n + 3) & ~3;
+  if (npad > npad_max) {
+    if (threadIdx.x == 0) set_err(err, DEVERR_SHAPE);
+    return;
+  }
+  const int32_t *ec = ecol + (doff[e] - 64ll * e);
+  const double *pe = psi + 4 * toff[e];
+  // shared layout: 5 arrays [QC][npad] then 1D tables
+  double *Y0 = smem, *Y1 = Y0 + QC * npad, *Y2 = Y1 + QC * npad, *Z = Y2 + QC * npad,
+         *ZV = Z + QC * npad;
+  Tab1D *tab = reinterpret_cast<Tab1D *>(ZV + QC * npad);
+  const double s[3] = {sx, sy, sz};
+
+  const int nb = npad / 4;
+  const int nblk = nb * (nb + 1) / 2;
+  for (int base = 0; base < nblk; base += ASM_NT) {
+    const int t = base + threadIdx.x;
+    const bool active = t < nblk;
+    int I = 0, J = 0;
+    if (active) {
+      I = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+      while ((I + 1) * (I + 2) / 2 <= t) ++I;
+      while (I * (I + 1) / 2 > t) --I;
+      J = t - I * (I + 1) / 2;
+    }
+    const int i0 = 4 * I, j0 = 4 * J;
+    double h[4][4], sv[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) h[a][b] = sv[a][b] = 0.0;
+
+    for (int qc = 0; qc < Q; qc += QC) {
+      __syncthreads();
+      // 1D Lagrange tables of the chunk's points
+      for (int k = threadIdx.x; k < QC * 3; k += ASM_NT) {
+        const int qq = k / 3, d = k - 3 * qq;
+        const int q = qc + qq;
+        const double xv = (q < Q) ? xi_all[3 * (q0 + q) + d] : 0.0;
+        double L[4], dL[4];
+        lagrange3(xv, L, dL);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          tab[qq].L[d][c] = L[c];
+          tab[qq].dL[d][c] = dL[c];
+        }
+      }
+      __syncthreads();
+      for (int k = threadIdx.x; k < QC * npad; k += ASM_NT) {
+        const int qq = k / npad, c = k - qq * npad;
+        const int q = qc + qq;
+        double b = 0, gx = 0, gy = 0, gz = 0, sw = 0, vv = 0;
+        if (q < Q && c < n) {
+          if (c < 64) {
+            fe_column(tab[qq], c, s, b, gx, gy, gz);
+          } else {
+            const int code = ec[c - 64];
+            const int slot = code >> 3, lv = code & 7;
+            const double *pp = pe + (int64_t)slot * 4 * Q + q;
+            const double ps[4] = {pp[0], pp[Q], pp[2 * Q], pp[3 * Q]};
+            const double xq[3] = {xi_all[3 * (q0 + q)], xi_all[3 * (q0 + q) + 1],
+                                  xi_all[3 * (q0 + q) + 2]};
+            pu_column(xq, lv, s, ps, b, gx, gy, gz);
+          }
+          sw = w[q0 + q];
+          vv = V ? V[q0 + q] : 0.0;
+        }
+        const double r2 = sqrt(0.5 * sw), r1 = sqrt(sw);
+        Y0[k] = r2 * gx;
+        Y1[k] = r2 * gy;
+        Y2[k] = r2 * gz;
+        Z[k] = r1 * b;
+        ZV[k] = vv * r1 * b;
+      }
+      __syncthreads();
+      if (active) {
+        const int qn = min(QC, Q - qc);
+        for (int qq = 0; qq < qn; ++qq) {
+          const int ro = qq * npad;
+          double ai[5][4], bj[4][4];
+#pragma unroll
+          for (int a = 0; a < 4; ++a) {
+            ai[0][a] = Y0[ro + i0 + a];
+            ai[1][a] = Y1[ro + i0 + a];
+            ai[2][a] = Y2[ro + i0 + a];
+            ai[3][a] = ZV[ro + i0 + a];
+            ai[4][a] = Z[ro + i0 + a];
+            bj[0][a] = Y0[ro + j0 + a];
+            bj[1][a] = Y1[ro + j0 + a];
+            bj[2][a] = Y2[ro + j0 + a];
+            bj[3][a] = Z[ro + j0 + a];
+          }
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+              double acc = h[a][b];
+              acc = fma(ai[0][a], bj[0][b], acc);
+              acc = fma(ai[1][a], bj[1][b], acc);
+              acc = fma(ai[2][a], bj[2][b], acc);
+              acc = fma(ai[3][a], bj[3][b], acc);
+              h[a][b] = acc;
+              sv[a][b] = fma(ai[4][a], bj[3][b], sv[a][b]);
+            }
+        }
+      }
+    }
+    // scatter the owned lower-triangle entries (both (i,j) and (j,i))
+    if (active) {
+      const int32_t *m = smap + soff[e];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const int i = i0 + a, j = j0 + b;
+          if (i >= n || j >= n || j > i) continue;
+          const int32_t sij = m[(int64_t)i * n + j];
+          const int32_t sji = m[(int64_t)j * n + i];
+          if (want & PUFE_WANT_H) {
+            atomicAdd(H + sij, h[a][b]);
+            if (i != j) atomicAdd(H + sji, h[a][b]);
+          }
+          if (want & PUFE_WANT_S) {
+            atomicAdd(S + sij, sv[a][b]);
+            if (i != j) atomicAdd(S + sji, sv[a][b]);
+          }
+        }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K4 (FP64): one CTA per element, one thread per quadrature point.  The
+// element's coefficient block C_e (n x nocc, gathered through the element DOF
+// list) sits in shared memory; each thread evaluates its basis row on the fly.
+// ---------------------------------------------------------------------------
+template <int KC>
+__device__ __forceinline__ double density_point(const double xi[3], int q, int Q, int nenr,
+                                                const int32_t *ec, const double *pe,
+                                                const double *Cs, const double *fs, int nocc,
+                                                int k0) {
+  double L[3][4], dL[3][4];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) lagrange3(xi[d], L[d], dL[d]);
+  double acc[KC];
+#pragma unroll
+  for (int k = 0; k < KC; ++k) acc[k] = 0.0;
+#pragma unroll
+  for (int c3 = 0; c3 < 4; ++c3)
+#pragma unroll
+    for (int c2 = 0; c2 < 4; ++c2) {
+      const double lyz = L[1][c2] * L[2][c3];
+#pragma unroll
+      for (int c1 = 0; c1 < 4; ++c1) {
+        const double b = L[0][c1] * lyz;
+        const double *cr = Cs + (c1 + 4 * c2 + 16 * c3) * nocc + k0;
+#pragma unroll
+        for (int k = 0; k < KC; ++k) acc[k] = fma(b, cr[k], acc[k]);
+      }
+    }
+  for (int j = 0; j < nenr; ++j) {
+    const int code = ec[j];
+    const int slot = code >> 3, lv = code & 7;
+    double phi = 1.0;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) phi *= ((lv >> d) & 1) ? 0.5 * (1.0 + xi[d]) : 0.5 * (1.0 - xi[d]);
+    const double b = phi * pe[(int64_t)slot * 4 * Q + q];
+    const double *cr = Cs + (64 + j) * nocc + k0;
+#pragma unroll
+    for (int k = 0; k < KC; ++k) acc[k] = fma(b, cr[k], acc[k]);
+  }
+  double r = 0.0;
+#pragma unroll
+  for (int k = 0; k < KC; ++k) r = fma(fs[k0 + k] * acc[k], acc[k], r);
+  return r;
+}
+
+__global__ void __launch_bounds__(DEN_NT) k_density_fp64(
+    const int32_t *__restrict__ order, const int64_t *__restrict__ qoff,
+    const double *__restrict__ xi_all, const int64_t *__restrict__ doff,
+    const int32_t *__restrict__ dofs, const int32_t *__restrict__ ecol,
+    const int64_t *__restrict__ toff, const double *__restrict__ psi,
+    const double *__restrict__ C, int64_t ldc, const double *__restrict__ f, int nocc,
+    int noccp, double *__restrict__ rho) {
+  extern __shared__ __align__(16) double smem[];
+  const int e = order[blockIdx.x];
+  const int64_t q0 = qoff[e];
+  const int Q = (int)(qoff[e + 1] - q0);
+  const int n = (int)(doff[e + 1] - doff[e]);
+  const int nenr = n - 64;
+  const int32_t *ec = ecol + (doff[e] - 64ll * e);
+  const int32_t *dl = dofs + doff[e];
+  const double *pe = psi + 4 * toff[e];
+  double *Cs = smem;             // n x noccp
+  double *fs = Cs + n * noccp;   // noccp
+  for (int k = threadIdx.x; k < n * noccp; k += DEN_NT) {
+    const int j = k / noccp, kk = k - j * noccp;
+    Cs[k] = (kk < nocc) ? C[(int64_t)dl[j] * ldc + kk] : 0.0;
+  }
+  for (int k = threadIdx.x; k < noccp; k += DEN_NT) fs[k] = (k < nocc) ? f[k] : 0.0;
+  __syncthreads();
+  for (int q = threadIdx.x; q < Q; q += DEN_NT) {
+    const double xq[3] = {xi_all[3 * (q0 + q)], xi_all[3 * (q0 + q) + 1], xi_all[3 * (q0 + q) + 2]};
+    double r = 0.0;
+    for (int k0 = 0; k0 < noccp; k0 += 8)
+      r += density_point<8>(xq, q, Q, nenr, ec, pe, Cs, fs, noccp, k0);
+    rho[q0 + q] = r;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K5 (FP64): Vbar_q = w_q b_q^T Hbar_e b_q.  One CTA per element: the element
+// block Hbar_e is gathered into shared memory (or read through the scatter
+// map when it does not fit); per chunk of QC points the basis rows are built
+// in shared memory and each thread reduces one (q, i) pair over j.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(ADJ_NT) k_adjoint_fp64(
+    const int32_t *__restrict__ order, const int64_t *__restrict__ qoff,
+    const double *__restrict__ w, const double *__restrict__ xi_all,
+    const int64_t *__restrict__ doff, const int32_t *__restrict__ ecol,
+    const int64_t *__restrict__ toff, const double *__restrict__ psi,
+    const int64_t *__restrict__ soff, const int32_t *__restrict__ smap,
+    const double *__restrict__ Hbar, int hs_in_smem, double *__restrict__ Vbar) {
+  extern __shared__ __align__(16) double smem[];
+  const int e = order[blockIdx.x];
+  const int64_t q0 = qoff[e];
+  const int Q = (int)(qoff[e + 1] - q0);
+  const int n = (int)(doff[e + 1] - doff[e]);
+  const int32_t *ec = ecol + (doff[e] - 64ll * e);
+  const double *pe = psi + 4 * toff[e];
+  const int32_t *m = smap + soff[e];
+  double *Bc = smem;                 // QC x n
+  double *acc = Bc + QC * n;         // QC
+  Tab1D *tab = reinterpret_cast<Tab1D *>(acc + QC);
+  double *Hs = reinterpret_cast<double *>(tab + QC);  // n x n when it fits
+  if (hs_in_smem)
+    for (int k = threadIdx.x; k < n * n; k += ADJ_NT) Hs[k] = Hbar[m[k]];
+  const double s[3] = {0, 0, 0};
+  for (int qc = 0; qc < Q; qc += QC) {
+    __syncthreads();
+    for (int k = threadIdx.x; k < QC * 3; k += ADJ_NT) {
+      const int qq = k / 3, d = k - 3 * qq;
+      const int q = qc + qq;
+      const double xv = (q < Q) ? xi_all[3 * (q0 + q) + d] : 0.0;
+      double L[4], dL[4];
+      lagrange3(xv, L, dL);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        tab[qq].L[d][c] = L[c];
+        tab[qq].dL[d][c] = dL[c];
+      }
+    }
+    if (threadIdx.x < QC) acc[threadIdx.x] = 0.0;
+    __syncthreads();
+    for (int k = threadIdx.x; k < QC * n; k += ADJ_NT) {
+      const int qq = k / n, c = k - qq * n;
+      const int q = qc + qq;
+      double b = 0, gx, gy, gz;
+      if (q < Q) {
+        if (c < 64) {
+          fe_column(tab[qq], c, s, b, gx, gy, gz);
+        } else {
+          const int code = ec[c - 64];
+          const int slot = code >> 3, lv = code & 7;
+          const double *pp = pe + (int64_t)slot * 4 * Q + q;
+          const double ps[4] = {pp[0], 0.0, 0.0, 0.0};
+          const double xq[3] = {xi_all[3 * (q0 + q)], xi_all[3 * (q0 + q) + 1],
+                                xi_all[3 * (q0 + q) + 2]};
+          pu_column(xq, lv, s, ps, b, gx, gy, gz);
+        }
+      }
+      Bc[k] = b;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < QC * n; k += ADJ_NT) {
+      const int qq = k / n, i = k - qq * n;
+      if (qc + qq >= Q) continue;
+      const double *brow = Bc + qq * n;
+      double t = 0.0;
+      if (hs_in_smem) {
+        const double *hr = Hs + (int64_t)i * n;
+        for (int j = 0; j < n; ++j) t = fma(hr[j], brow[j], t);
+      } else {
+        const int32_t *mr = m + (int64_t)i * n;
+        for (int j = 0; j < n; ++j) t = fma(Hbar[mr[j]], brow[j], t);
+      }
+      atomicAdd(acc + qq, brow[i] * t);
+    }
+    __syncthreads();
+    if (threadIdx.x < QC && qc + (int)threadIdx.x < Q)
+      Vbar[q0 + qc + threadIdx.x] = w[q0 + qc + threadIdx.x] * acc[threadIdx.x];
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+pufe_status launch_tabulate(pufe_ctx *ctx, cudaStream_t st) {
+  if (ctx->psi_len == 0) return PUFE_OK;
+  auto &D = ctx->d;
+  k_tabulate<<<(unsigned)ctx->nelem, 128, 0, st>>>(D.qoff, D.x, D.aoff, D.alist, D.toff, D.orb,
+                                                   ctx->a[0], ctx->a[1], ctx->a[2],
+                                                   ctx->images[0], ctx->images[1], ctx->images[2],
+                                                   D.psi);
+  PUFE_CUDA_TRY(cudaGetLastError());
+  return PUFE_OK;
+}
+
+pufe_status launch_assemble_fp64(pufe_ctx *ctx, const double *V, int what, double *H, double *S,
+                                 cudaStream_t st) {
+  auto &D = ctx->d;
+  const int npad = (ctx->max_basis + 3) & ~3;
+  const size_t sm = (size_t)5 * QC * npad * sizeof(double) + QC * sizeof(Tab1D);
+  if (sm > 227 * 1024) return fail(PUFE_EINVAL, "element basis too large for the FP64 kernel");
+  PUFE_CUDA_TRY(cudaFuncSetAttribute(k_assemble_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)sm));
+  k_assemble_fp64<<<(unsigned)ctx->nelem, ASM_NT, sm, st>>>(
+      D.order, D.qoff, D.w, D.xi, D.doff, D.ecol, D.toff, D.psi, D.soff, D.smap, V,
+      2.0 / ctx->h[0], 2.0 / ctx->h[1], 2.0 / ctx->h[2], npad, what, H, S, D.err);
+  PUFE_CUDA_TRY(cudaGetLastError());
+  return PUFE_OK;
+}
+
+pufe_status launch_density_fp64(pufe_ctx *ctx, const double *C, int64_t ldc, const double *f,
+                                int nocc, double *rho, cudaStream_t st) {
+  auto &D = ctx->d;
+  const int noccp = (nocc + 7) & ~7;
+  const size_t sm = ((size_t)ctx->max_basis * noccp + noccp) * sizeof(double);
+  if (sm > 227 * 1024) return fail(PUFE_EINVAL, "n_e * nocc too large for the density kernel");
+  PUFE_CUDA_TRY(cudaFuncSetAttribute(k_density_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)sm));
+  k_density_fp64<<<(unsigned)ctx->nelem, DEN_NT, sm, st>>>(D.order, D.qoff, D.xi, D.doff, D.dofs,
+                                                           D.ecol, D.toff, D.psi, C, ldc, f, nocc,
+                                                           noccp, rho);
+  PUFE_CUDA_TRY(cudaGetLastError());
+  return PUFE_OK;
+}
+
+pufe_status launch_adjoint_fp64(pufe_ctx *ctx, const double *Hbar, double *Vbar, cudaStream_t st) {
+  auto &D = ctx->d;
+  const int n = ctx->max_basis;
+  size_t sm = (size_t)QC * n * sizeof(double) + QC * sizeof(double) + QC * sizeof(Tab1D);
+  const size_t hs = (size_t)n * n * sizeof(double);
+  int in_smem = (sm + hs <= 200 * 1024) ? 1 : 0;
+  if (in_smem) sm += hs;
+  PUFE_CUDA_TRY(cudaFuncSetAttribute(k_adjoint_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)sm));
+  k_adjoint_fp64<<<(unsigned)ctx->nelem, ADJ_NT, sm, st>>>(D.order, D.qoff, D.w, D.xi, D.doff,
+                                                           D.ecol, D.toff, D.psi, D.soff, D.smap,
+                                                           Hbar, in_smem, Vbar);
+  PUFE_CUDA_TRY(cudaGetLastError());
+  return PUFE_OK;
+}
+
+}  // namespace pufe

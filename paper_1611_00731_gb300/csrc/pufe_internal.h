@@ -1,0 +1,227 @@
+// Internal declarations of the GB300 PUFE library: the context, error
+// helpers and the basis functions shared by the host setup and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/pufe.h"
+
+namespace pufe {
+
+// ---------------------------------------------------------------------------
+// error reporting
+// ---------------------------------------------------------------------------
+void set_error(const std::string &msg);
+pufe_status fail(pufe_status st, const std::string &msg);
+pufe_status cuda_fail(cudaError_t err, const char *what);
+
+#define PUFE_CUDA_TRY(call)                                   \
+  do {                                                        \
+    cudaError_t _e = (call);                                  \
+    if (_e != cudaSuccess) return ::pufe::cuda_fail(_e, #call); \
+  } while (0)
+
+// device-side error flag bits
+enum : unsigned {
+  DEVERR_BOUNDS = 1u,   // an index check failed inside a kernel
+  DEVERR_TIMEOUT = 2u,  // a bounded wait gave up
+  DEVERR_SHAPE = 4u     // a kernel met a shape it was not built for
+};
+
+// ---------------------------------------------------------------------------
+// one enrichment function alpha = (atom, orbital)
+// ---------------------------------------------------------------------------
+struct Orbital {
+  double tau[3];   // atom position
+  double zeta;     // Slater exponent
+  double norm;     // STO normalisation (2 zeta)^(n+1/2) / sqrt((2n)!)
+  double rc;       // cutoff radius
+  int n, l, m;
+  int pad;
+};
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+struct DeviceArrays {
+  // quadrature
+  int64_t *qoff = nullptr;    // nelem + 1
+  double *x = nullptr;        // nq * 3
+  double *w = nullptr;        // nq
+  double *xi = nullptr;       // nq * 3, reference coordinates in [-1, 1]
+  // element basis description
+  int64_t *doff = nullptr;    // nelem + 1: offsets into dofs (n_e each)
+  int32_t *dofs = nullptr;    // sum n_e: global DOF of each element column
+  int32_t *ecol = nullptr;    // sum (n_e - 64): (aslot << 3) | local vertex
+  int32_t *aoff = nullptr;    // nelem + 1: offsets into alist
+  int32_t *alist = nullptr;   // element enrichment list (global alpha ids)
+  int64_t *toff = nullptr;    // nelem + 1: offsets into psi (units of q*alpha)
+  double *psi = nullptr;      // 4 * sum Q_e A_e: [aslot][comp][q] per element
+  Orbital *orb = nullptr;     // n_alpha
+  // global sparse storage
+  int64_t *rowptr = nullptr;  // N + 1
+  int32_t *col = nullptr;     // nnz
+  int64_t *soff = nullptr;    // nelem + 1: offsets into smap (n_e^2 each)
+  int32_t *smap = nullptr;    // CSR slot of each local pair (i, j), row-major
+  // work list: elements sorted by (n_e, Q_e) class, largest first
+  int32_t *order = nullptr;   // nelem
+  unsigned *err = nullptr;    // device error flag
+};
+
+}  // namespace pufe
+
+struct pufe_ctx {
+  int device = 0;
+  double a[3] = {0, 0, 0};
+  double h[3] = {0, 0, 0};
+  int nel[3] = {0, 0, 0};
+  int images[3] = {1, 1, 1};   // image search half-width per axis
+  int64_t nelem = 0, nq = 0, n_dof = 0, n_fe = 0, nnz = 0;
+  int64_t n_alpha = 0, psi_len = 0, smap_len = 0, dof_len = 0;
+  int max_basis = 0, max_q = 0, max_alpha = 0;
+  bool tabulated = false;
+  bool on_device = false;   // device copies exist (a CUDA device was present)
+  // host copies kept for getters
+  std::vector<int64_t> qoff, rowptr, doff;
+  std::vector<int32_t> col, dofs, n_e, q_e, order;
+  std::vector<double> x, w;
+  pufe::DeviceArrays d;
+};
+
+namespace pufe {
+
+// ---------------------------------------------------------------------------
+// basis functions shared by host setup and device kernels
+// ---------------------------------------------------------------------------
+
+// Cubic Lagrange polynomials on nodes -1, -1/3, 1/3, 1 and their slopes.
+__host__ __device__ inline void lagrange3(double t, double L[4], double dL[4]) {
+  const double a = t + 1.0, b = t + 1.0 / 3.0, c = t - 1.0 / 3.0, d = t - 1.0;
+  L[0] = -0.5625 * b * c * d;
+  L[1] = 1.6875 * a * c * d;
+  L[2] = -1.6875 * a * b * d;
+  L[3] = 0.5625 * a * b * c;
+  dL[0] = -0.5625 * (c * d + b * d + b * c);
+  dL[1] = 1.6875 * (c * d + a * d + a * c);
+  dL[2] = -1.6875 * (b * d + a * d + a * b);
+  dL[3] = 0.5625 * (b * c + a * c + a * b);
+}
+
+// Real solid harmonic r^l Y_lm(r^) (unit-normalised Y, no Condon-Shortley
+// phase, m < 0 <-> sin) and its gradient, for l <= 3.
+__host__ __device__ inline double solid_harmonic(int l, int m, double x, double y, double z,
+                                                 double g[3]) {
+  const double PI = 3.14159265358979323846;
+  g[0] = g[1] = g[2] = 0.0;
+  if (l == 0) return 0.5 / sqrt(PI);
+  if (l == 1) {
+    const double c = sqrt(3.0 / (4.0 * PI));
+    if (m == -1) { g[1] = c; return c * y; }
+    if (m == 0) { g[2] = c; return c * z; }
+    g[0] = c; return c * x;
+  }
+  if (l == 2) {
+    const double A = 0.5 * sqrt(15.0 / PI), B = 0.25 * sqrt(5.0 / PI), C = 0.25 * sqrt(15.0 / PI);
+    switch (m) {
+      case -2: g[0] = A * y; g[1] = A * x; return A * x * y;
+      case -1: g[1] = A * z; g[2] = A * y; return A * y * z;
+      case 0: g[0] = -2 * B * x; g[1] = -2 * B * y; g[2] = 4 * B * z;
+        return B * (2 * z * z - x * x - y * y);
+      case 1: g[0] = A * z; g[2] = A * x; return A * x * z;
+      default: g[0] = 2 * C * x; g[1] = -2 * C * y; return C * (x * x - y * y);
+    }
+  }
+  const double D = 0.25 * sqrt(35.0 / (2.0 * PI)), E = 0.5 * sqrt(105.0 / PI);
+  const double F = 0.25 * sqrt(21.0 / (2.0 * PI)), G = 0.25 * sqrt(7.0 / PI);
+  const double H = 0.25 * sqrt(105.0 / PI);
+  switch (m) {
+    case -3: g[0] = 6 * D * x * y; g[1] = 3 * D * (x * x - y * y); return D * y * (3 * x * x - y * y);
+    case -2: g[0] = E * y * z; g[1] = E * x * z; g[2] = E * x * y; return E * x * y * z;
+    case -1: g[0] = -2 * F * x * y; g[1] = F * (4 * z * z - x * x - 3 * y * y); g[2] = 8 * F * y * z;
+      return F * y * (4 * z * z - x * x - y * y);
+    case 0: g[0] = -6 * G * x * z; g[1] = -6 * G * y * z; g[2] = G * (6 * z * z - 3 * x * x - 3 * y * y);
+      return G * z * (2 * z * z - 3 * x * x - 3 * y * y);
+    case 1: g[0] = F * (4 * z * z - 3 * x * x - y * y); g[1] = -2 * F * x * y; g[2] = 8 * F * x * z;
+      return F * x * (4 * z * z - x * x - y * y);
+    case 2: g[0] = 2 * H * x * z; g[1] = -2 * H * y * z; g[2] = H * (x * x - y * y);
+      return H * z * (x * x - y * y);
+    default: g[0] = 3 * D * (x * x - y * y); g[1] = -6 * D * x * y; return D * x * (x * x - 3 * y * y);
+  }
+}
+
+__host__ __device__ inline double ipow(double r, int k) {
+  double p = 1.0;
+  for (int i = 0; i < k; ++i) p *= r;
+  return p;
+}
+
+// Psi~(d) h(|d|, r_c) for one image displacement d, plus its gradient
+// (accumulated into psi and g).  Psi~ = N r^(n-1) e^(-zeta r) Y_lm, written
+// as f(r) S_lm(d) with f = N r^(n-1-l) e^(-zeta r) h(r) and S_lm = r^l Y_lm.
+__host__ __device__ inline void orbital_accumulate(const Orbital &o, double dx, double dy,
+                                                   double dz, double &psi, double g[3]) {
+  const double r2 = dx * dx + dy * dy + dz * dz;
+  if (r2 >= o.rc * o.rc) return;
+  const double r = sqrt(r2);
+  const double x = r / o.rc;
+  const double x3 = x * x * x;
+  const double hc = 1.0 + x3 * x * (-35.0 + x * (84.0 + x * (-70.0 + 20.0 * x)));
+  const double omx = 1.0 - x;
+  const double dh = -140.0 * x3 * omx * omx * omx / o.rc;
+  const int k = o.n - 1 - o.l;  // >= 0
+  const double ez = o.norm * exp(-o.zeta * r);
+  const double rk = ipow(r, k);
+  const double f = ez * rk * hc;
+  const double rkm1 = (k > 0) ? ipow(r, k - 1) : 0.0;
+  const double df = ez * ((double)k * rkm1 * hc - o.zeta * rk * hc + rk * dh);
+  double gs[3];
+  const double S = solid_harmonic(o.l, o.m, dx, dy, dz, gs);
+  psi += f * S;
+  if (r > 1e-14) {
+    const double s = df * S / r;
+    g[0] += s * dx + f * gs[0];
+    g[1] += s * dy + f * gs[1];
+    g[2] += s * dz + f * gs[2];
+  } else {
+    g[0] += f * gs[0];
+    g[1] += f * gs[1];
+    g[2] += f * gs[2];
+  }
+}
+
+// Periodic enrichment Psi_alpha(p) (eq. Psi with f(R) = 1): all images of the
+// atom within r_c of p.  `img` = image half-width per axis.
+__host__ __device__ inline void enrichment_eval(const Orbital &o, const double p[3],
+                                                const double a[3], const int img[3],
+                                                double &psi, double g[3]) {
+  psi = 0.0;
+  g[0] = g[1] = g[2] = 0.0;
+  double d0[3];
+  for (int k = 0; k < 3; ++k) {
+    double d = p[k] - o.tau[k];
+    d -= a[k] * floor(d / a[k] + 0.5);
+    d0[k] = d;
+  }
+  for (int i = -img[0]; i <= img[0]; ++i)
+    for (int j = -img[1]; j <= img[1]; ++j)
+      for (int k = -img[2]; k <= img[2]; ++k)
+        orbital_accumulate(o, d0[0] + i * a[0], d0[1] + j * a[1], d0[2] + k * a[2], psi, g);
+}
+
+// launchers implemented in the .cu files
+pufe_status launch_tabulate(pufe_ctx *ctx, cudaStream_t s);
+pufe_status launch_assemble_fp64(pufe_ctx *ctx, const double *V, int what, double *H, double *S,
+                                 cudaStream_t s);
+pufe_status launch_density_fp64(pufe_ctx *ctx, const double *C, int64_t ldc, const double *f,
+                                int nocc, double *rho, cudaStream_t s);
+pufe_status launch_adjoint_fp64(pufe_ctx *ctx, const double *Hbar, double *Vbar, cudaStream_t s);
+pufe_status launch_assemble_tc(pufe_ctx *ctx, const double *V, int what, double *H, double *S,
+                               cudaStream_t s);
+pufe_status launch_density_tc(pufe_ctx *ctx, const double *C, int64_t ldc, const double *f,
+                              int nocc, double *rho, cudaStream_t s);
+
+}  // namespace pufe

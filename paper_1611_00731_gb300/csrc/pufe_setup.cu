@@ -1,0 +1,687 @@
+// Host-side setup of the PUFE context: mesh, enrichment sets, per-element
+// basis lists, quadrature rules, CSR pattern and scatter maps (runs once per
+// geometry), plus the getters, error reporting and teardown of the C ABI.
+//
+// Paper map: basis of Sec. 4 (eqs. pufebasis, psih); enriched vertex sets
+// and periodic enrichments of Sec. 5.1 (eq. Psi); quadrature of Sec. 5.2.
+#include <algorithm>
+#include <array>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <functional>
+#include <numeric>
+#include <thread>
+
+#include "pufe_internal.h"
+
+namespace pufe {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+pufe_status fail(pufe_status st, const std::string &msg) {
+  g_last_error = msg;
+  return st;
+}
+
+pufe_status cuda_fail(cudaError_t err, const char *what) {
+  g_last_error = std::string(what) + ": " + cudaGetErrorString(err);
+  return err == cudaErrorMemoryAllocation ? PUFE_ENOMEM : PUFE_ECUDA;
+}
+
+// ---------------------------------------------------------------------------
+// Gauss-Legendre nodes/weights on [-1, 1] by Newton iteration on P_p.
+// ---------------------------------------------------------------------------
+static void gauss_legendre(int p, std::vector<double> &x, std::vector<double> &w) {
+  x.assign(p, 0.0);
+  w.assign(p, 0.0);
+  const double PI = 3.14159265358979323846;
+  for (int i = 0; i < p; ++i) {
+    double t = std::cos(PI * (i + 0.75) / (p + 0.5));
+    double dp = 0.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = t;
+      for (int k = 2; k <= p; ++k) {
+        double p2 = ((2.0 * k - 1.0) * t * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      if (p == 1) { p1 = t; p0 = 1.0; }
+      dp = p * (t * p1 - p0) / (t * t - 1.0);
+      double dt = p1 / dp;
+      t -= dt;
+      if (std::fabs(dt) < 1e-16) break;
+    }
+    // final derivative at the converged node
+    double p0 = 1.0, p1 = t;
+    for (int k = 2; k <= p; ++k) {
+      double p2 = ((2.0 * k - 1.0) * t * p1 - (k - 1.0) * p0) / k;
+      p0 = p1;
+      p1 = p2;
+    }
+    if (p == 1) { p1 = t; p0 = 1.0; }
+    dp = p * (t * p1 - p0) / (t * t - 1.0);
+    x[p - 1 - i] = t;  // ascending order
+    w[p - 1 - i] = 2.0 / ((1.0 - t * t) * dp * dp);
+  }
+}
+
+struct Box {
+  double lo[3], hi[3];
+};
+
+struct RulePart {  // one tensor rule on one (sub)cell
+  Box box;
+  int p;
+};
+
+struct Setup {
+  double a[3], h[3];
+  int nel[3];
+  int img[3];
+  std::vector<Orbital> orb;          // alpha list
+  std::vector<int> orb_atom;         // alpha -> atom
+  std::vector<std::array<double, 3>> tau;
+  std::vector<int> atom_species;
+  std::vector<double> rc_species, re_species;
+  std::vector<std::vector<double>> gx, gw;  // Gauss tables by order (index p)
+};
+
+static double box_point_dist(const Box &b, const double p[3]) {
+  double s = 0.0;
+  for (int k = 0; k < 3; ++k) {
+    double d = std::max(std::max(b.lo[k] - p[k], p[k] - b.hi[k]), 0.0);
+    s += d * d;
+  }
+  return std::sqrt(s);
+}
+
+// smallest distance from any periodic image of atom position t to box b
+static double atom_box_dist(const Setup &S, const double t[3], const Box &b) {
+  double best = 1e300;
+  const int R = 2;
+  for (int i = -R; i <= R; ++i)
+    for (int j = -R; j <= R; ++j)
+      for (int k = -R; k <= R; ++k) {
+        double p[3] = {t[0] + i * S.a[0], t[1] + j * S.a[1], t[2] + k * S.a[2]};
+        best = std::min(best, box_point_dist(b, p));
+      }
+  return best;
+}
+
+// integrals of Psi^2 and |grad Psi|^2 on a box with the p^3 Gauss rule,
+// for each alpha of `alphas`: out[2*i], out[2*i+1]
+static void box_integrals(Setup &S, const std::vector<int> &alphas, const Box &b, int p,
+                          std::vector<double> &out) {
+  out.assign(2 * alphas.size(), 0.0);
+  const std::vector<double> &gx = S.gx[p], &gw = S.gw[p];
+  double half[3], mid[3];
+  for (int k = 0; k < 3; ++k) {
+    half[k] = 0.5 * (b.hi[k] - b.lo[k]);
+    mid[k] = 0.5 * (b.hi[k] + b.lo[k]);
+  }
+  for (size_t ia = 0; ia < alphas.size(); ++ia) {
+    const Orbital &o = S.orb[alphas[ia]];
+    double s0 = 0.0, s1 = 0.0;
+    for (int kz = 0; kz < p; ++kz)
+      for (int ky = 0; ky < p; ++ky)
+        for (int kx = 0; kx < p; ++kx) {
+          double pt[3] = {mid[0] + half[0] * gx[kx], mid[1] + half[1] * gx[ky],
+                          mid[2] + half[2] * gx[kz]};
+          double wt = gw[kx] * gw[ky] * gw[kz] * half[0] * half[1] * half[2];
+          double psi, g[3];
+          enrichment_eval(o, pt, S.a, S.img, psi, g);
+          s0 += wt * psi * psi;
+          s1 += wt * (g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+        }
+    out[2 * ia] = s0;
+    out[2 * ia + 1] = s1;
+  }
+}
+
+static void hadapt(Setup &S, const std::vector<int> &alphas, const Box &b, int depth,
+                   const pufe_quad &q, std::vector<RulePart> &parts) {
+  std::vector<double> i5, i8;
+  box_integrals(S, alphas, b, 5, i5);
+  box_integrals(S, alphas, b, 8, i8);
+  std::vector<int> failing;
+  for (size_t ia = 0; ia < alphas.size(); ++ia)
+    if (std::fabs(i5[2 * ia] - i8[2 * ia]) >= q.tol ||
+        std::fabs(i5[2 * ia + 1] - i8[2 * ia + 1]) >= q.tol)
+      failing.push_back(alphas[ia]);
+  if (failing.empty() || depth >= q.max_depth) {
+    parts.push_back({b, 8});
+    return;
+  }
+  double mid[3];
+  for (int k = 0; k < 3; ++k) mid[k] = 0.5 * (b.lo[k] + b.hi[k]);
+  for (int c = 0; c < 2; ++c)
+    for (int bb = 0; bb < 2; ++bb)
+      for (int a = 0; a < 2; ++a) {
+        int off[3] = {a, bb, c};
+        Box ch;
+        for (int k = 0; k < 3; ++k) {
+          ch.lo[k] = off[k] == 0 ? b.lo[k] : mid[k];
+          ch.hi[k] = off[k] == 0 ? mid[k] : b.hi[k];
+        }
+        hadapt(S, failing, ch, depth + 1, q, parts);
+      }
+}
+
+static void parallel_for(int64_t n, const std::function<void(int64_t)> &fn) {
+  unsigned nt = std::max(1u, std::thread::hardware_concurrency());
+  nt = (unsigned)std::min<int64_t>(nt, std::max<int64_t>(1, n));
+  if (nt <= 1) {
+    for (int64_t i = 0; i < n; ++i) fn(i);
+    return;
+  }
+  std::vector<std::thread> th;
+  std::atomic<int64_t> next(0);
+  for (unsigned t = 0; t < nt; ++t)
+    th.emplace_back([&]() {
+      for (;;) {
+        int64_t i = next.fetch_add(1);
+        if (i >= n) break;
+        fn(i);
+      }
+    });
+  for (auto &t : th) t.join();
+}
+
+template <class T>
+static pufe_status upload(T **dst, const std::vector<T> &src) {
+  size_t bytes = std::max<size_t>(1, src.size()) * sizeof(T);
+  PUFE_CUDA_TRY(cudaMalloc((void **)dst, bytes));
+  if (!src.empty()) PUFE_CUDA_TRY(cudaMemcpy(*dst, src.data(), src.size() * sizeof(T),
+                                             cudaMemcpyHostToDevice));
+  return PUFE_OK;
+}
+
+static double factorial(int k) {
+  double f = 1.0;
+  for (int i = 2; i <= k; ++i) f *= i;
+  return f;
+}
+
+static pufe_status build(const pufe_cell *cell, const pufe_species *species, int nspecies,
+                         const pufe_quad *quad, pufe_ctx *ctx) {
+  // ---- validate ----------------------------------------------------------
+  if (!cell || !quad) return fail(PUFE_EINVAL, "cell and quad must not be NULL");
+  if (cell->natoms < 0 || (cell->natoms > 0 && (!cell->tau || !cell->species)))
+    return fail(PUFE_EINVAL, "bad atom arrays");
+  if (nspecies < 0 || (nspecies > 0 && !species)) return fail(PUFE_EINVAL, "bad species");
+  for (int k = 0; k < 3; ++k) {
+    if (!(cell->a[k] > 0.0) || cell->nel[k] < 1 || cell->nel[k] > 4096)
+      return fail(PUFE_EINVAL, "cell edges must be > 0 and nel in [1, 4096]");
+  }
+  if (quad->mode < PUFE_QUAD_FIXED || quad->mode > PUFE_QUAD_HADAPT)
+    return fail(PUFE_EINVAL, "unknown quadrature mode");
+  if (quad->mode == PUFE_QUAD_FIXED &&
+      (quad->p_far < 1 || quad->p_far > 16 || quad->p_near < 1 || quad->p_near > 16))
+    return fail(PUFE_EINVAL, "FIXED rule orders must lie in [1, 16]");
+  if (quad->mode == PUFE_QUAD_PADAPT &&
+      (quad->p_min < 1 || quad->p_max < quad->p_min || quad->p_max > 16))
+    return fail(PUFE_EINVAL, "PADAPT needs 1 <= p_min <= p_max <= 16");
+  if (quad->mode == PUFE_QUAD_HADAPT &&
+      (quad->max_depth < 0 || quad->max_depth > 4 || quad->p_far < 1 || quad->p_far > 16))
+    return fail(PUFE_EINVAL, "HADAPT needs 0 <= max_depth <= 4 and p_far in [1, 16]");
+  if (quad->mode != PUFE_QUAD_FIXED && !(quad->tol > 0.0))
+    return fail(PUFE_EINVAL, "adaptive tolerance must be > 0");
+
+  Setup S;
+  double rc_max = 0.0;
+  for (int k = 0; k < 3; ++k) {
+    S.a[k] = cell->a[k];
+    S.nel[k] = cell->nel[k];
+    S.h[k] = cell->a[k] / cell->nel[k];
+  }
+  for (int s = 0; s < nspecies; ++s) {
+    const pufe_species &sp = species[s];
+    if (sp.norb < 0 || (sp.norb > 0 && (!sp.n || !sp.l || !sp.m || !sp.zeta)))
+      return fail(PUFE_EINVAL, "bad orbital arrays");
+    if (!(sp.r_c > 0.0) || !(sp.r_e >= 0.0)) return fail(PUFE_EINVAL, "need r_c > 0, r_e >= 0");
+    for (int o = 0; o < sp.norb; ++o) {
+      if (sp.l[o] < 0 || sp.l[o] > 3 || sp.n[o] <= sp.l[o] || sp.n[o] > 8 ||
+          sp.m[o] < -sp.l[o] || sp.m[o] > sp.l[o] || !(sp.zeta[o] > 0.0))
+        return fail(PUFE_EINVAL, "orbital needs 0<=l<=3, l<n<=8, |m|<=l, zeta>0");
+    }
+    S.rc_species.push_back(sp.r_c);
+    S.re_species.push_back(sp.r_e);
+    rc_max = std::max(rc_max, sp.r_c);
+  }
+  for (int k = 0; k < 3; ++k) S.img[k] = (int)std::ceil(rc_max / S.a[k] + 0.5);
+  for (int ia = 0; ia < cell->natoms; ++ia) {
+    int s = cell->species[ia];
+    if (s < 0 || s >= nspecies) return fail(PUFE_EINVAL, "atom species out of range");
+    S.tau.push_back({cell->tau[3 * ia], cell->tau[3 * ia + 1], cell->tau[3 * ia + 2]});
+    S.atom_species.push_back(s);
+    const pufe_species &sp = species[s];
+    for (int o = 0; o < sp.norb; ++o) {
+      Orbital ob;
+      for (int k = 0; k < 3; ++k) ob.tau[k] = cell->tau[3 * ia + k];
+      ob.n = sp.n[o];
+      ob.l = sp.l[o];
+      ob.m = sp.m[o];
+      ob.zeta = sp.zeta[o];
+      ob.rc = sp.r_c;
+      ob.norm = std::pow(2.0 * ob.zeta, ob.n + 0.5) / std::sqrt(factorial(2 * ob.n));
+      ob.pad = 0;
+      S.orb.push_back(ob);
+      S.orb_atom.push_back(ia);
+    }
+  }
+  S.gx.resize(19);
+  S.gw.resize(19);
+  for (int p = 1; p <= 18; ++p) gauss_legendre(p, S.gx[p], S.gw[p]);  // PADAPT reads p_max + 2
+
+  const int nx = S.nel[0], ny = S.nel[1], nz = S.nel[2];
+  const int64_t nelem = (int64_t)nx * ny * nz;
+  const int64_t nv = nelem;
+  const int mx = 3 * nx, my = 3 * ny, mz = 3 * nz;
+  const int64_t n_fe = (int64_t)mx * my * mz;
+  const int natoms = cell->natoms;
+
+  auto elem_box = [&](int64_t e) {
+    int ex = (int)(e % nx), ey = (int)((e / nx) % ny), ez = (int)(e / ((int64_t)nx * ny));
+    Box b;
+    int idx[3] = {ex, ey, ez};
+    for (int k = 0; k < 3; ++k) {
+      b.lo[k] = idx[k] * S.h[k];
+      b.hi[k] = b.lo[k] + S.h[k];
+    }
+    return b;
+  };
+  auto elem_vertex = [&](int64_t e, int lv) -> int64_t {
+    int ex = (int)(e % nx), ey = (int)((e / nx) % ny), ez = (int)(e / ((int64_t)nx * ny));
+    int a = lv & 1, b = (lv >> 1) & 1, c = (lv >> 2) & 1;
+    return ((ex + a) % nx) + (int64_t)nx * (((ey + b) % ny) + (int64_t)ny * ((ez + c) % nz));
+  };
+
+  // ---- element / atom proximity ------------------------------------------
+  std::vector<uint8_t> near((size_t)nelem * std::max(1, natoms), 0);
+  parallel_for(nelem, [&](int64_t e) {
+    Box b = elem_box(e);
+    for (int ia = 0; ia < natoms; ++ia) {
+      double d = atom_box_dist(S, S.tau[ia].data(), b);
+      near[(size_t)e * natoms + ia] = d < S.rc_species[S.atom_species[ia]] ? 1 : 0;
+    }
+  });
+
+  // ---- enriched vertices per atom (minimum image distance <= r_e) --------
+  std::vector<std::vector<int64_t>> enr_verts(natoms);
+  for (int ia = 0; ia < natoms; ++ia) {
+    double re = S.re_species[S.atom_species[ia]];
+    for (int64_t v = 0; v < nv; ++v) {
+      int vx = (int)(v % nx), vy = (int)((v / nx) % ny), vz = (int)(v / ((int64_t)nx * ny));
+      int vi[3] = {vx, vy, vz};
+      double s = 0.0;
+      for (int k = 0; k < 3; ++k) {
+        double d = vi[k] * S.h[k] - S.tau[ia][k];
+        d -= S.a[k] * std::nearbyint(d / S.a[k]);
+        s += d * d;
+      }
+      if (std::sqrt(s) <= re + 1e-12) enr_verts[ia].push_back(v);
+    }
+  }
+
+  // ---- enrichment DOFs and element columns --------------------------------
+  std::vector<std::vector<std::pair<int64_t, int>>> vert_elems(nv);  // (e, lv)
+  for (int64_t e = 0; e < nelem; ++e)
+    for (int lv = 0; lv < 8; ++lv) vert_elems[elem_vertex(e, lv)].push_back({e, lv});
+  struct Col {
+    int64_t dof;
+    int lv;
+    int alpha;
+  };
+  std::vector<std::vector<Col>> cols(nelem);
+  int64_t dof = n_fe;
+  for (size_t k = 0; k < S.orb.size(); ++k) {
+    int ia = S.orb_atom[k];
+    for (int64_t v : enr_verts[ia]) {
+      bool any = false;
+      for (auto &el : vert_elems[v]) {
+        if (near[(size_t)el.first * natoms + ia]) {
+          cols[el.first].push_back({dof, el.second, (int)k});
+          any = true;
+        }
+      }
+      if (any) ++dof;
+    }
+  }
+  const int64_t n_dof = dof;
+  if (n_dof > INT32_MAX) return fail(PUFE_EINVAL, "too many DOFs for int32 column indices");
+  for (auto &c : cols)
+    std::sort(c.begin(), c.end(), [](const Col &x, const Col &y) {
+      return x.dof != y.dof ? x.dof < y.dof : x.lv < y.lv;
+    });
+
+  // per-element alpha lists
+  std::vector<std::vector<int>> ealpha(nelem);
+  for (int64_t e = 0; e < nelem; ++e) {
+    for (auto &c : cols[e]) ealpha[e].push_back(c.alpha);
+    std::sort(ealpha[e].begin(), ealpha[e].end());
+    ealpha[e].erase(std::unique(ealpha[e].begin(), ealpha[e].end()), ealpha[e].end());
+  }
+
+  // ---- quadrature rules ----------------------------------------------------
+  std::vector<std::vector<RulePart>> rule(nelem);
+  parallel_for(nelem, [&](int64_t e) {
+    Box b = elem_box(e);
+    std::vector<RulePart> &parts = rule[e];
+    if (quad->mode == PUFE_QUAD_FIXED) {
+      bool nr = false;
+      for (int ia = 0; ia < natoms; ++ia) nr = nr || near[(size_t)e * natoms + ia];
+      parts.push_back({b, nr ? quad->p_near : quad->p_far});
+    } else if (quad->mode == PUFE_QUAD_PADAPT) {
+      const std::vector<int> &al = ealpha[e];
+      if (al.empty()) {
+        parts.push_back({b, quad->p_min});
+        return;
+      }
+      std::vector<std::vector<double>> I(quad->p_max + 3);
+      auto get = [&](int p) -> const std::vector<double> & {
+        if (I[p].empty()) box_integrals(S, al, b, p, I[p]);
+        return I[p];
+      };
+      int chosen = quad->p_max;
+      for (int p = quad->p_min; p <= quad->p_max; ++p) {
+        const std::vector<double> &a1 = get(p), &a2 = get(p + 2);
+        bool ok = true;
+        for (size_t i = 0; i < a1.size(); ++i) ok = ok && (std::fabs(a1[i] - a2[i]) < quad->tol);
+        if (ok) {
+          chosen = p;
+          break;
+        }
+      }
+      parts.push_back({b, chosen});
+    } else {
+      if (ealpha[e].empty()) {
+        parts.push_back({b, quad->p_far});
+        return;
+      }
+      hadapt(S, ealpha[e], b, 0, *quad, parts);
+    }
+  });
+  std::vector<int64_t> qoff(nelem + 1, 0);
+  for (int64_t e = 0; e < nelem; ++e) {
+    int64_t q = 0;
+    for (auto &pt : rule[e]) q += (int64_t)pt.p * pt.p * pt.p;
+    qoff[e + 1] = qoff[e] + q;
+  }
+  const int64_t nq = qoff[nelem];
+  std::vector<double> X(3 * nq), Wt(nq), XI(3 * nq);
+  parallel_for(nelem, [&](int64_t e) {
+    Box eb = elem_box(e);
+    int64_t q = qoff[e];
+    for (auto &pt : rule[e]) {
+      const std::vector<double> &gx = S.gx[pt.p], &gw = S.gw[pt.p];
+      double half[3], mid[3];
+      for (int k = 0; k < 3; ++k) {
+        half[k] = 0.5 * (pt.box.hi[k] - pt.box.lo[k]);
+        mid[k] = 0.5 * (pt.box.hi[k] + pt.box.lo[k]);
+      }
+      for (int kz = 0; kz < pt.p; ++kz)
+        for (int ky = 0; ky < pt.p; ++ky)
+          for (int kx = 0; kx < pt.p; ++kx, ++q) {
+            int kk[3] = {kx, ky, kz};
+            for (int d = 0; d < 3; ++d) {
+              X[3 * q + d] = mid[d] + half[d] * gx[kk[d]];
+              XI[3 * q + d] = 2.0 * (X[3 * q + d] - eb.lo[d]) / S.h[d] - 1.0;
+            }
+            Wt[q] = gw[kx] * gw[ky] * gw[kz] * half[0] * half[1] * half[2];
+          }
+    }
+  });
+
+  // ---- element DOF lists, column descriptors, alpha slots ------------------
+  std::vector<int64_t> doff(nelem + 1, 0), toff(nelem + 1, 0);
+  std::vector<int32_t> aoff(nelem + 1, 0);
+  std::vector<int32_t> n_e(nelem), q_e(nelem);
+  for (int64_t e = 0; e < nelem; ++e) {
+    n_e[e] = 64 + (int32_t)cols[e].size();
+    q_e[e] = (int32_t)(qoff[e + 1] - qoff[e]);
+    doff[e + 1] = doff[e] + n_e[e];
+    aoff[e + 1] = aoff[e] + (int32_t)ealpha[e].size();
+    toff[e + 1] = toff[e] + (int64_t)q_e[e] * (int64_t)ealpha[e].size();
+  }
+  std::vector<int32_t> dofs(doff[nelem]), ecol(doff[nelem] - 64 * nelem), alist(aoff[nelem]);
+  int64_t ecpos = 0;
+  for (int64_t e = 0; e < nelem; ++e) {
+    int ex = (int)(e % nx), ey = (int)((e / nx) % ny), ez = (int)(e / ((int64_t)nx * ny));
+    int32_t *d = &dofs[doff[e]];
+    for (int c = 0; c < 4; ++c)
+      for (int b = 0; b < 4; ++b)
+        for (int a = 0; a < 4; ++a) {
+          int64_t gx = (3 * ex + a) % mx, gy = (3 * ey + b) % my, gz = (3 * ez + c) % mz;
+          d[a + 4 * b + 16 * c] = (int32_t)(gx + mx * (gy + (int64_t)my * gz));
+        }
+    for (size_t k = 0; k < ealpha[e].size(); ++k) alist[aoff[e] + k] = ealpha[e][k];
+    for (size_t j = 0; j < cols[e].size(); ++j) {
+      d[64 + j] = (int32_t)cols[e][j].dof;
+      int slot = (int)(std::lower_bound(ealpha[e].begin(), ealpha[e].end(), cols[e][j].alpha) -
+                       ealpha[e].begin());
+      ecol[ecpos++] = (slot << 3) | cols[e][j].lv;
+    }
+  }
+
+  // ---- CSR pattern (union of element blocks) ------------------------------
+  std::vector<std::vector<int32_t>> rows(n_dof);
+  {
+    // row lists built per element, then sorted/uniqued per row
+    for (int64_t e = 0; e < nelem; ++e) {
+      const int32_t *d = &dofs[doff[e]];
+      int n = n_e[e];
+      for (int i = 0; i < n; ++i) {
+        std::vector<int32_t> &r = rows[d[i]];
+        r.insert(r.end(), d, d + n);
+      }
+    }
+    parallel_for(n_dof, [&](int64_t r) {
+      std::vector<int32_t> &v = rows[r];
+      std::sort(v.begin(), v.end());
+      v.erase(std::unique(v.begin(), v.end()), v.end());
+      v.shrink_to_fit();
+    });
+  }
+  std::vector<int64_t> rowptr(n_dof + 1, 0);
+  for (int64_t r = 0; r < n_dof; ++r) rowptr[r + 1] = rowptr[r] + (int64_t)rows[r].size();
+  const int64_t nnz = rowptr[n_dof];
+  if (nnz > INT32_MAX) return fail(PUFE_EINVAL, "nnz exceeds int32 scatter slots");
+  std::vector<int32_t> colv(nnz);
+  parallel_for(n_dof, [&](int64_t r) {
+    std::copy(rows[r].begin(), rows[r].end(), colv.begin() + rowptr[r]);
+  });
+  rows.clear();
+  rows.shrink_to_fit();
+
+  std::vector<int64_t> soff(nelem + 1, 0);
+  for (int64_t e = 0; e < nelem; ++e) soff[e + 1] = soff[e] + (int64_t)n_e[e] * n_e[e];
+  std::vector<int32_t> smap(soff[nelem]);
+  parallel_for(nelem, [&](int64_t e) {
+    const int32_t *d = &dofs[doff[e]];
+    int n = n_e[e];
+    int32_t *m = &smap[soff[e]];
+    for (int i = 0; i < n; ++i) {
+      const int32_t *b = colv.data() + rowptr[d[i]], *en = colv.data() + rowptr[d[i] + 1];
+      for (int j = 0; j < n; ++j) {
+        const int32_t *f = std::lower_bound(b, en, d[j]);
+        m[(int64_t)i * n + j] = (int32_t)(f - colv.data());
+      }
+    }
+  });
+
+  // ---- work order: big elements first ----------------------------------------
+  std::vector<int32_t> order(nelem);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
+    int64_t cx = (int64_t)n_e[x] * n_e[x] * q_e[x], cy = (int64_t)n_e[y] * n_e[y] * q_e[y];
+    return cx > cy;
+  });
+
+  // ---- fill the context and upload ----------------------------------------
+  for (int k = 0; k < 3; ++k) {
+    ctx->a[k] = S.a[k];
+    ctx->h[k] = S.h[k];
+    ctx->nel[k] = S.nel[k];
+    ctx->images[k] = S.img[k];
+  }
+  ctx->nelem = nelem;
+  ctx->nq = nq;
+  ctx->n_dof = n_dof;
+  ctx->n_fe = n_fe;
+  ctx->nnz = nnz;
+  ctx->n_alpha = (int64_t)S.orb.size();
+  ctx->psi_len = 4 * toff[nelem];
+  ctx->smap_len = soff[nelem];
+  ctx->dof_len = doff[nelem];
+  ctx->max_basis = *std::max_element(n_e.begin(), n_e.end());
+  ctx->max_q = *std::max_element(q_e.begin(), q_e.end());
+  ctx->max_alpha = 0;
+  for (auto &v : ealpha) ctx->max_alpha = std::max(ctx->max_alpha, (int)v.size());
+
+  // Device copies: made here when a CUDA device is present.  Without one the
+  // context keeps its host-side description only (getters work, compute
+  // calls report PUFE_ESTATE).
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    ctx->on_device = false;
+  } else {
+    PUFE_CUDA_TRY(cudaGetDevice(&ctx->device));
+    ctx->on_device = true;
+  }
+  pufe_status st;
+  auto &D = ctx->d;
+  if (ctx->on_device) {
+  if ((st = upload(&D.qoff, qoff)) != PUFE_OK) return st;
+  if ((st = upload(&D.x, X)) != PUFE_OK) return st;
+  if ((st = upload(&D.w, Wt)) != PUFE_OK) return st;
+  if ((st = upload(&D.xi, XI)) != PUFE_OK) return st;
+  if ((st = upload(&D.doff, doff)) != PUFE_OK) return st;
+  if ((st = upload(&D.dofs, dofs)) != PUFE_OK) return st;
+  if ((st = upload(&D.ecol, ecol)) != PUFE_OK) return st;
+  if ((st = upload(&D.aoff, aoff)) != PUFE_OK) return st;
+  if ((st = upload(&D.alist, alist)) != PUFE_OK) return st;
+  if ((st = upload(&D.toff, toff)) != PUFE_OK) return st;
+  if ((st = upload(&D.orb, S.orb)) != PUFE_OK) return st;
+  if ((st = upload(&D.rowptr, rowptr)) != PUFE_OK) return st;
+  if ((st = upload(&D.col, colv)) != PUFE_OK) return st;
+  if ((st = upload(&D.soff, soff)) != PUFE_OK) return st;
+  if ((st = upload(&D.smap, smap)) != PUFE_OK) return st;
+  if ((st = upload(&D.order, order)) != PUFE_OK) return st;
+  PUFE_CUDA_TRY(cudaMalloc((void **)&D.psi, std::max<int64_t>(1, ctx->psi_len) * sizeof(double)));
+  PUFE_CUDA_TRY(cudaMalloc((void **)&D.err, sizeof(unsigned)));
+  PUFE_CUDA_TRY(cudaMemset(D.err, 0, sizeof(unsigned)));
+  }
+
+  ctx->qoff = std::move(qoff);
+  ctx->rowptr = std::move(rowptr);
+  ctx->col = std::move(colv);
+  ctx->doff = std::move(doff);
+  ctx->dofs = std::move(dofs);
+  ctx->n_e = std::move(n_e);
+  ctx->q_e = std::move(q_e);
+  ctx->order = std::move(order);
+  ctx->x = std::move(X);
+  ctx->w = std::move(Wt);
+  return PUFE_OK;
+}
+
+static void free_device(pufe_ctx *ctx) {
+  auto &D = ctx->d;
+  void *ptrs[] = {D.qoff, D.x, D.w, D.xi, D.doff, D.dofs, D.ecol, D.aoff, D.alist,
+                  D.toff, D.psi, D.orb, D.rowptr, D.col, D.soff, D.smap, D.order, D.err};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  D = DeviceArrays();
+}
+
+}  // namespace pufe
+
+using namespace pufe;
+
+extern "C" {
+
+pufe_status pufe_build_mesh(const pufe_cell *cell, const pufe_species *species, int nspecies,
+                            const pufe_quad *quad, pufe_ctx **out) {
+  if (!out) return fail(PUFE_EINVAL, "out must not be NULL");
+  *out = nullptr;
+  pufe_ctx *ctx = nullptr;
+  try {
+    ctx = new pufe_ctx();
+    pufe_status st = build(cell, species, nspecies, quad, ctx);
+    if (st != PUFE_OK) {
+      free_device(ctx);
+      delete ctx;
+      return st;
+    }
+  } catch (const std::bad_alloc &) {
+    if (ctx) {
+      free_device(ctx);
+      delete ctx;
+    }
+    return fail(PUFE_ENOMEM, "host allocation failed in pufe_build_mesh");
+  } catch (const std::exception &ex) {
+    if (ctx) {
+      free_device(ctx);
+      delete ctx;
+    }
+    return fail(PUFE_EINVAL, std::string("pufe_build_mesh: ") + ex.what());
+  }
+  *out = ctx;
+  return PUFE_OK;
+}
+
+pufe_status pufe_get_sizes(const pufe_ctx *ctx, int64_t *n_dof, int64_t *nnz, int64_t *n_q,
+                           int64_t *n_elem, int64_t *max_basis) {
+  if (!ctx) return fail(PUFE_EINVAL, "ctx is NULL");
+  if (n_dof) *n_dof = ctx->n_dof;
+  if (nnz) *nnz = ctx->nnz;
+  if (n_q) *n_q = ctx->nq;
+  if (n_elem) *n_elem = ctx->nelem;
+  if (max_basis) *max_basis = ctx->max_basis;
+  return PUFE_OK;
+}
+
+pufe_status pufe_get_quadrature(const pufe_ctx *ctx, double *x, double *w,
+                                int64_t *elem_offsets) {
+  if (!ctx) return fail(PUFE_EINVAL, "ctx is NULL");
+  if (x) std::memcpy(x, ctx->x.data(), ctx->x.size() * sizeof(double));
+  if (w) std::memcpy(w, ctx->w.data(), ctx->w.size() * sizeof(double));
+  if (elem_offsets) std::memcpy(elem_offsets, ctx->qoff.data(), ctx->qoff.size() * sizeof(int64_t));
+  return PUFE_OK;
+}
+
+pufe_status pufe_get_pattern(const pufe_ctx *ctx, int64_t *rowptr, int32_t *col) {
+  if (!ctx) return fail(PUFE_EINVAL, "ctx is NULL");
+  if (rowptr) std::memcpy(rowptr, ctx->rowptr.data(), ctx->rowptr.size() * sizeof(int64_t));
+  if (col) std::memcpy(col, ctx->col.data(), ctx->col.size() * sizeof(int32_t));
+  return PUFE_OK;
+}
+
+pufe_status pufe_get_element_basis(const pufe_ctx *ctx, int32_t *n_e, int32_t *dofs) {
+  if (!ctx) return fail(PUFE_EINVAL, "ctx is NULL");
+  if (n_e) std::memcpy(n_e, ctx->n_e.data(), ctx->n_e.size() * sizeof(int32_t));
+  if (dofs) std::memcpy(dofs, ctx->dofs.data(), ctx->dofs.size() * sizeof(int32_t));
+  return PUFE_OK;
+}
+
+void pufe_destroy(pufe_ctx *ctx) {
+  if (!ctx) return;
+  if (!ctx->on_device) {
+    delete ctx;
+    return;
+  }
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(ctx->device);
+  free_device(ctx);
+  cudaSetDevice(cur);
+  delete ctx;
+}
+
+const char *pufe_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,227 @@
+"""Thin Python binding of the ``libpufe.so`` C ABI (see ``include/pufe.h``).
+
+Argument marshalling only: every step of the hot path runs in the library's
+CUDA kernels.  PyTorch supplies device memory and streams.  The binding
+raises if the library cannot be loaded; there is no fallback.
+
+Functions carry the C names: ``pufe_build_mesh`` returns a :class:`Context`
+whose methods ``pufe_tabulate``, ``pufe_assemble_HS``, ``pufe_density``,
+``pufe_assemble_HV_adjoint`` and ``pufe_sync_status`` wrap the calls of the
+same name on that context.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import workloads as W
+
+PUFE_FP64, PUFE_TF32X3 = 0, 1
+PUFE_WANT_H, PUFE_WANT_S = 1, 2
+STATUS = {0: "PUFE_OK", 1: "PUFE_EINVAL", 2: "PUFE_ENOMEM", 3: "PUFE_ECUDA",
+          4: "PUFE_ENOTSPD", 5: "PUFE_ENOTCONV", 6: "PUFE_ETIMEOUT",
+          7: "PUFE_EDEVICE", 8: "PUFE_ESTATE"}
+
+# every symbol that include/pufe.h declares
+EXPORTS = ["pufe_build_mesh", "pufe_get_sizes", "pufe_get_quadrature", "pufe_get_pattern",
+           "pufe_get_element_basis", "pufe_tabulate", "pufe_assemble_HS", "pufe_density",
+           "pufe_assemble_HV_adjoint", "pufe_sync_status", "pufe_destroy", "pufe_last_error"]
+
+
+class PufeError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Cell(C.Structure):
+    _fields_ = [("a", C.c_double * 3), ("nel", C.c_int * 3), ("natoms", C.c_int),
+                ("tau", C.POINTER(C.c_double)), ("species", C.POINTER(C.c_int))]
+
+
+class _Species(C.Structure):
+    _fields_ = [("norb", C.c_int), ("n", C.POINTER(C.c_int)), ("l", C.POINTER(C.c_int)),
+                ("m", C.POINTER(C.c_int)), ("zeta", C.POINTER(C.c_double)),
+                ("r_c", C.c_double), ("r_e", C.c_double)]
+
+
+class _Quad(C.Structure):
+    _fields_ = [("mode", C.c_int), ("p_far", C.c_int), ("p_near", C.c_int),
+                ("p_min", C.c_int), ("p_max", C.c_int), ("tol", C.c_double),
+                ("max_depth", C.c_int)]
+
+
+_LIB = None
+
+
+def library_path():
+    from .build import LIBPATH
+    return LIBPATH
+
+
+def load_library(build_if_missing: bool = True):
+    """Load libpufe.so (building it in-tree with nvcc if it is missing)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = library_path()
+    if not os.path.exists(path) and build_if_missing:
+        from .build import build_library
+        build_library()
+    if not os.path.exists(path):
+        raise ImportError(f"libpufe.so not found at {path}; run __graft_entry__.build()")
+    lib = C.CDLL(path)
+    vp, i64p, i32p, dp = C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int32), C.POINTER(C.c_double)
+    lib.pufe_build_mesh.argtypes = [C.POINTER(_Cell), C.POINTER(_Species), C.c_int,
+                                    C.POINTER(_Quad), C.POINTER(vp)]
+    lib.pufe_get_sizes.argtypes = [vp, i64p, i64p, i64p, i64p, i64p]
+    lib.pufe_get_quadrature.argtypes = [vp, dp, dp, i64p]
+    lib.pufe_get_pattern.argtypes = [vp, i64p, i32p]
+    lib.pufe_get_element_basis.argtypes = [vp, i32p, i32p]
+    lib.pufe_tabulate.argtypes = [vp, vp]
+    lib.pufe_assemble_HS.argtypes = [vp, vp, C.c_int, C.c_int, vp, vp, vp]
+    lib.pufe_density.argtypes = [vp, vp, C.c_int64, vp, C.c_int, C.c_int, vp, vp]
+    lib.pufe_assemble_HV_adjoint.argtypes = [vp, vp, vp, vp]
+    lib.pufe_sync_status.argtypes = [vp, vp]
+    lib.pufe_destroy.argtypes = [vp]
+    lib.pufe_destroy.restype = None
+    lib.pufe_last_error.restype = C.c_char_p
+    for name in EXPORTS:
+        if name not in ("pufe_destroy", "pufe_last_error"):
+            getattr(lib, name).restype = C.c_int
+    _LIB = lib
+    return lib
+
+
+def _check(st):
+    if st != 0:
+        raise PufeError(st, _LIB.pufe_last_error().decode())
+
+
+def _ptr(t, dtype=None):
+    """Device pointer of a contiguous CUDA tensor (None -> NULL)."""
+    if t is None:
+        return None
+    import torch
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"expected {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+class Context:
+    """Owns a pufe_ctx; methods wrap the C calls on it."""
+
+    def __init__(self, handle, wl):
+        self._h = handle
+        self.wl = wl
+        n, nnz, nq, ne, mb = (C.c_int64() for _ in range(5))
+        _check(_LIB.pufe_get_sizes(self._h, C.byref(n), C.byref(nnz), C.byref(nq),
+                                   C.byref(ne), C.byref(mb)))
+        self.n_dof, self.nnz, self.n_q = n.value, nnz.value, nq.value
+        self.n_elem, self.max_basis = ne.value, mb.value
+
+    # -- getters ---------------------------------------------------------------
+    def quadrature(self):
+        x = np.empty((self.n_q, 3))
+        w = np.empty(self.n_q)
+        off = np.empty(self.n_elem + 1, dtype=np.int64)
+        _check(_LIB.pufe_get_quadrature(self._h, x.ctypes.data_as(C.POINTER(C.c_double)),
+                                        w.ctypes.data_as(C.POINTER(C.c_double)),
+                                        off.ctypes.data_as(C.POINTER(C.c_int64))))
+        return x, w, off
+
+    def pattern(self):
+        rowptr = np.empty(self.n_dof + 1, dtype=np.int64)
+        col = np.empty(self.nnz, dtype=np.int32)
+        _check(_LIB.pufe_get_pattern(self._h, rowptr.ctypes.data_as(C.POINTER(C.c_int64)),
+                                     col.ctypes.data_as(C.POINTER(C.c_int32))))
+        return rowptr, col
+
+    def element_basis(self):
+        n_e = np.empty(self.n_elem, dtype=np.int32)
+        _check(_LIB.pufe_get_element_basis(self._h, n_e.ctypes.data_as(C.POINTER(C.c_int32)), None))
+        dofs = np.empty(int(n_e.sum()), dtype=np.int32)
+        _check(_LIB.pufe_get_element_basis(self._h, None, dofs.ctypes.data_as(C.POINTER(C.c_int32))))
+        return n_e, dofs
+
+    # -- compute calls --------------------------------------------------------
+    def pufe_tabulate(self, stream=None):
+        _check(_LIB.pufe_tabulate(self._h, _stream(stream)))
+
+    def pufe_assemble_HS(self, V, H=None, S=None, prec=PUFE_FP64, what=None, stream=None):
+        import torch
+        if what is None:
+            what = (PUFE_WANT_H if H is not None else 0) | (PUFE_WANT_S if S is not None else 0)
+        _check(_LIB.pufe_assemble_HS(self._h, _ptr(V, torch.float64), int(prec), int(what),
+                                     _ptr(H, torch.float64), _ptr(S, torch.float64),
+                                     _stream(stream)))
+
+    def pufe_density(self, Cmat, f, rho, prec=PUFE_FP64, stream=None):
+        import torch
+        nocc = Cmat.shape[1]
+        _check(_LIB.pufe_density(self._h, _ptr(Cmat, torch.float64), int(Cmat.stride(0)),
+                                 _ptr(f, torch.float64), int(nocc), int(prec),
+                                 _ptr(rho, torch.float64), _stream(stream)))
+
+    def pufe_assemble_HV_adjoint(self, Hbar, Vbar, stream=None):
+        import torch
+        _check(_LIB.pufe_assemble_HV_adjoint(self._h, _ptr(Hbar, torch.float64),
+                                             _ptr(Vbar, torch.float64), _stream(stream)))
+
+    def pufe_sync_status(self, stream=None):
+        _check(_LIB.pufe_sync_status(self._h, _stream(stream)))
+
+    def close(self):
+        if self._h:
+            _LIB.pufe_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pufe_build_mesh(wl: dict) -> Context:
+    """Build a context from a workload dict (see workloads.workload)."""
+    lib = load_library()
+    natoms = len(wl["atoms"])
+    tau = (C.c_double * max(1, 3 * natoms))(*[c for _, t in wl["atoms"] for c in t])
+    spec = (C.c_int * max(1, natoms))(*[int(s) for s, _ in wl["atoms"]])
+    a = float(wl["a"])
+    nel = int(wl["nel"])
+    cell = _Cell((C.c_double * 3)(a, a, a), (C.c_int * 3)(nel, nel, nel), natoms, tau, spec)
+    keep = []
+    sp = (_Species * max(1, len(wl["species"])))()
+    for i, s in enumerate(wl["species"]):
+        orbs = s["orbitals"]
+        n = (C.c_int * max(1, len(orbs)))(*[o[0] for o in orbs])
+        l = (C.c_int * max(1, len(orbs)))(*[o[1] for o in orbs])
+        m = (C.c_int * max(1, len(orbs)))(*[o[2] for o in orbs])
+        z = (C.c_double * max(1, len(orbs)))(*[o[3] for o in orbs])
+        keep += [n, l, m, z]
+        sp[i] = _Species(len(orbs), n, l, m, z, float(s["r_c"]), float(s["r_e"]))
+    q = wl["quad"]
+    quad = _Quad(int(q["mode"]), int(q["p_far"]), int(q["p_near"]), int(q["p_min"]),
+                 int(q["p_max"]), float(q["tol"]), int(q["max_depth"]))
+    h = C.c_void_p()
+    _check(lib.pufe_build_mesh(C.byref(cell), sp, len(wl["species"]), C.byref(quad), C.byref(h)))
+    return Context(h, wl)
+
+
+def pufe_workload(name: str) -> Context:
+    return pufe_build_mesh(W.workload(name))
