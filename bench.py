@@ -1,0 +1,330 @@
+"""Benchmark of the PUFE hot path on one GB300 (replicas across GPUs).
+
+One step = one pass of the whole hot path over the workload's quadrature
+points: K0 tabulation, H+S assembly (K1-K3), density (K4) and the adjoint of
+V -> H (K5).  The metric is quadrature-point contractions per second: the
+number of quadrature points that went through the step, divided by its time.
+
+Prints one JSON line (rank 0).  Multi-GPU runs are independent replicas of
+the same workload (no collective on the data path; a barrier brackets the
+timed region) and report the aggregate rate.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec tf32x3|fp64]
+                  [--workload c2_rocksalt_12cube] [--impl pufe|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "quadrature-point contractions/s for H/S assembly + density"
+UNIT = "QPC/s"
+L2_BYTES = 129 * 1024 * 1024
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def run_pufe(args):
+    import numpy as np
+    import torch
+
+    from paper_1611_00731_gb300 import pufe, workloads as W
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    prec = {"fp64": pufe.PUFE_FP64, "tf32x3": pufe.PUFE_TF32X3}[args.prec]
+
+    wl = W.workload(args.workload)
+    t0 = time.time()
+    ctx = pufe.pufe_build_mesh(wl)
+    build_s = time.time() - t0
+    n_e, _ = ctx.element_basis()
+    _, _, qoff = ctx.quadrature()
+    Qe = np.diff(qoff)
+    nocc = int(wl["nocc"])
+    flops_asm = float(5.0 * (Qe * n_e * (n_e + 1.0)).sum())
+
+    V_h = torch.tensor(W.random_potential(ctx.n_q, seed=rank), dtype=torch.float64).pin_memory()
+    C_h = torch.tensor(W.random_coefficients(ctx.n_dof, nocc, seed=rank)).pin_memory()
+    f_h = torch.tensor(W.random_occupations(nocc, seed=rank)).pin_memory()
+    V = V_h.to(dev)
+    Cm = C_h.to(dev)
+    f = f_h.to(dev)
+    H = torch.empty(ctx.nnz, dtype=torch.float64, device=dev)
+    S = torch.empty_like(H)
+    rho = torch.empty(ctx.n_q, dtype=torch.float64, device=dev)
+    vbar = torch.empty_like(rho)
+    rho_h = torch.empty(ctx.n_q, dtype=torch.float64).pin_memory()
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    ev_a = torch.cuda.Event(enable_timing=True)
+    ev_b = torch.cuda.Event(enable_timing=True)
+
+    def step(timing=None):
+        ctx.pufe_tabulate()
+        if timing is not None:
+            timing[0].record(stream)
+        ctx.pufe_assemble_HS(V, H, S, prec=prec)
+        if timing is not None:
+            timing[1].record(stream)
+        ctx.pufe_density(Cm, f, rho, prec=prec)
+        ctx.pufe_assemble_HV_adjoint(H, vbar)
+
+    for _ in range(args.warmup):
+        step()
+    ctx.pufe_sync_status()
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # device-resident timing: each step bracketed by events, L2 flushed between
+    sampler = ClockSampler(local)
+    barrier()
+    sampler.start()
+    step_ms, asm_ms = [], []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        ka = torch.cuda.Event(enable_timing=True)
+        kb = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step((ka, kb))
+        b.record(stream)
+        b.synchronize()
+        step_ms.append(a.elapsed_time(b))
+        asm_ms.append(ka.elapsed_time(kb))
+    barrier()
+    clocks = sampler.stop()
+    ctx.pufe_sync_status()
+    total_ms = sum(step_ms)
+
+    # end to end through the C ABI with host buffers: H2D of V and C, the
+    # step, D2H of the density
+    barrier()
+    ev_a.record(stream)
+    for _ in range(args.steps):
+        V.copy_(V_h, non_blocking=True)
+        Cm.copy_(C_h, non_blocking=True)
+        f.copy_(f_h, non_blocking=True)
+        step()
+        rho_h.copy_(rho, non_blocking=True)
+    ev_b.record(stream)
+    ev_b.synchronize()
+    e2e_ms = ev_a.elapsed_time(ev_b)
+    ctx.pufe_sync_status()
+    barrier()
+
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms, e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms, e2e_ms = float(t[0]), float(t[1])
+    if rank != 0:
+        return None
+
+    ms_per_step = total_ms / args.steps
+    value = ws * ctx.n_q * args.steps / (total_ms * 1e-3)
+    peaks, src = _peaks()
+    if args.prec == "fp64":
+        # FP64 contraction: the recipe's nominal FP64 rate scaled like the
+        # measured bf16 figure (measured bf16 x nominal FP64/bf16 ratio)
+        peak = peaks["bf16_tflops"] * (1.25 / 2250.0)
+        bound, dtype = "alu", "f64"
+    else:
+        peak = peaks["bf16_tflops"] * (1.1 / 2.25)   # tf32 dense / bf16 dense nominal
+        bound, dtype = "tensor", "tf32x3+f64"
+    asm_avg = statistics.mean(asm_ms)
+    achieved = flops_asm / (asm_avg * 1e-3) / 1e12
+    roof = {"kernel": "assemble_HS", "bound": bound, "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+            "peak_source": f"{src} bf16 x nominal ratio",
+            "flops_per_launch": flops_asm, "avg_launch_ms": asm_avg}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+        "config": {"workload": args.workload, "n_dof": ctx.n_dof, "n_q": ctx.n_q,
+                   "n_elem": ctx.n_elem, "nnz": ctx.nnz, "nocc": nocc, "prec": args.prec,
+                   "l2": "flushed between steps (2x L2 buffer written)",
+                   "parallelism": f"replicas x{ws}", "build_s": round(build_s, 3)},
+        "roofline": roof,
+        "e2e": {"value": ws * ctx.n_q * args.steps / (e2e_ms * 1e-3), "unit": UNIT,
+                "h2d_bytes_per_step": int(V_h.numel() * 8 + C_h.numel() * 8 + f_h.numel() * 8),
+                "d2h_bytes_per_step": int(rho_h.numel() * 8)},
+        "gpu_launches": 4 * args.steps,
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_elems)
+    return line
+
+
+# --------------------------------------------------------------------------
+# the oracle as the CPU baseline / reference arm
+# --------------------------------------------------------------------------
+_ORACLE_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, sys.argv[1])
+import numpy as np
+from paper_1611_00731_gb300 import workloads as W
+from oracle import assemble as oasm, mesh as omesh, quadrature as oq
+wl = W.workload(sys.argv[2]); nel = int(sys.argv[3]); steps = int(sys.argv[4])
+m = omesh.Mesh(wl)
+rng = np.random.default_rng(0)
+elems = [int(e) for e in rng.choice(m.nelem, size=min(nel, m.nelem), replace=False)]
+rules = {e: oq.element_rule(m, e) for e in elems}
+C = W.random_coefficients(m.n_dof, wl["nocc"]); f = W.random_occupations(wl["nocc"])
+out = []
+for _ in range(steps):
+    nq = 0
+    t0 = time.perf_counter()
+    for e in elems:
+        p, w = rules[e]
+        V = W.random_potential(len(w), seed=e)
+        He, Se = oasm.element_HS(m, e, p, w, V)           # tabulation + basis + H/S
+        B, _ = oasm.element_basis(m, e, p)
+        Y = B @ C[m.elem_dofs(e)]
+        rho = (Y * Y) @ f                                  # density
+        vbar = w * np.einsum("qi,ij,qj->q", B, He, B)      # adjoint
+        nq += len(w)
+    out.append((nq, time.perf_counter() - t0))
+print(json.dumps(out))
+"""
+
+
+def _oracle_steps(workload, nelem, steps):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", _ORACLE_SNIPPET, ROOT, workload, str(nelem),
+                        str(steps)], capture_output=True, text=True, env=env)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr.strip()[-400:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline(workload, nelem):
+    try:
+        (nq, sec), = _oracle_steps(workload, nelem, 1)
+    except RuntimeError as ex:
+        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": f"failed: {ex}"}
+    return {"value": nq / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{nelem} random elements of {workload} (seed 0): tabulation and "
+                      f"basis, element H/S, density, adjoint; {nq} points in {sec:.1f} s, "
+                      "1 thread"}
+
+
+def run_reference(args):
+    """The oracle as the reference arm: each step is the bounded sample."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return None
+    res = _oracle_steps(args.workload, args.ref_elems, args.warmup + args.steps)[args.warmup:]
+    nq = sum(r[0] for r in res)
+    sec = sum(r[1] for r in res)
+    value = nq / sec
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / len(res),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "prec": "fp64 oracle (CPU)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.ref_elems} random elements of {args.workload} "
+                                       f"(seed 0) per step, 1 thread"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="pufe", choices=["pufe", "reference"])
+    ap.add_argument("--prec", default="tf32x3", choices=["tf32x3", "fp64"])
+    ap.add_argument("--workload", default="c2_rocksalt_12cube")
+    ap.add_argument("--cpu-elems", type=int, default=160)
+    ap.add_argument("--ref-elems", type=int, default=24)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3) if args.impl == "pufe" else max(args.warmup, 0)
+    line = run_reference(args) if args.impl == "reference" else run_pufe(args)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()
