@@ -130,14 +130,14 @@ def run_pufe(args):
     ev_b = torch.cuda.Event(enable_timing=True)
 
     def step(timing=None):
-        ctx.pufe_tabulate()
+        ctx.pufe_tabulate(prec)
         if timing is not None:
             timing[0].record(stream)
         ctx.pufe_assemble_HS(V, H, S, prec=prec)
         if timing is not None:
             timing[1].record(stream)
         ctx.pufe_density(Cm, f, rho, prec=prec)
-        ctx.pufe_assemble_HV_adjoint(H, vbar)
+        ctx.pufe_assemble_HV_adjoint(H, vbar, prec=prec)
 
     for _ in range(args.warmup):
         step()

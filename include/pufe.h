@@ -64,9 +64,12 @@ typedef enum {
 /* Arithmetic of the element contractions. */
 typedef enum {
   PUFE_FP64 = 0,   /* FP64 everywhere (plain CUDA cores) */
-  PUFE_TF32X3 = 1  /* tcgen05 kind::tf32 with a 3-term hi/lo split, FP32
-                      accumulation in TMEM; FP64 kept for the enrichment-
-                      enrichment block of S and for global accumulation */
+  PUFE_TF32X3 = 1  /* element contractions on the tensor cores (tcgen05
+                      kind::tf32) with every operand split into two TF32
+                      terms (hi*hi + hi*lo + lo*hi), FP32 accumulation per
+                      element, FP64 global accumulation; the constant FE-FE
+                      blocks of T and S are exact FP64 constants; FP32
+                      tabulation, density and adjoint */
 } pufe_prec;
 
 /* Quadrature modes (Sec. 5.2). */
@@ -139,22 +142,28 @@ pufe_status pufe_get_element_basis(const pufe_ctx *ctx, int32_t *n_e, int32_t *d
 /* K0 (Sec. 5.1, eqs. Psitilde/Psi): tabulate Psi_alpha and grad Psi_alpha at
  * every quadrature point of every element for the enrichments that appear in
  * that element's basis.  The table lives in the context and is read by the
- * assembly, density and adjoint kernels.  Asynchronous on `stream`. */
-pufe_status pufe_tabulate(pufe_ctx *ctx, void *stream);
+ * assembly, density and adjoint kernels of the same precision: `prec` =
+ * PUFE_FP64 fills the FP64 table, PUFE_TF32X3 the FP32 table.  Asynchronous
+ * on `stream`. */
+pufe_status pufe_tabulate(pufe_ctx *ctx, int prec, void *stream);
 
 /* K1-K3 (Sec. 4, eq. disceig3d): H and/or S values into caller-owned device
  * arrays of nnz float64 each (pattern of pufe_get_pattern).  V (n_q float64,
  * device) is the local potential at the quadrature points; it may be NULL
- * when only S is wanted.  The arrays are overwritten (zeroed, then
- * accumulated).  `what` is a mask of PUFE_WANT_H | PUFE_WANT_S.
- * Requires a prior pufe_tabulate.  Asynchronous. */
+ * when only S is wanted.  The arrays are overwritten.  `what` is a mask of
+ * PUFE_WANT_H | PUFE_WANT_S.  Requires a prior pufe_tabulate of the same
+ * precision.  PUFE_TF32X3 additionally needs every (sub)cell rule to have at
+ * least 4 points per axis (so that the FE-FE blocks of T and S are exact
+ * constants) and n_e <= 256; otherwise it returns PUFE_EINVAL.
+ * Asynchronous. */
 pufe_status pufe_assemble_HS(pufe_ctx *ctx, const double *V, int prec, int what,
                              double *H, double *S, void *stream);
 
 /* K4 (Sec. 3, eq. rhoe): n_q = sum_k f_k (sum_j B_qj C_jk)^2 for every
  * quadrature point.  C: device float64, N x nocc, row-major with leading
  * dimension ldc >= nocc (C[j * ldc + k]); f: device float64 (nocc);
- * rho: device float64 (n_q), overwritten.  1 <= nocc <= 64.  Asynchronous. */
+ * rho: device float64 (n_q), overwritten.  1 <= nocc <= 64.  PUFE_TF32X3
+ * evaluates in FP32 on the CUDA cores.  Asynchronous. */
 pufe_status pufe_density(pufe_ctx *ctx, const double *C, int64_t ldc,
                          const double *f, int nocc, int prec, double *rho,
                          void *stream);
@@ -162,8 +171,8 @@ pufe_status pufe_density(pufe_ctx *ctx, const double *C, int64_t ldc,
 /* K5, adjoint of V -> H (Sec. 4): Vbar_q = w_q b_q^T Hbar_e b_q for a
  * cotangent Hbar given as nnz float64 values on the CSR pattern (device).
  * Vbar: device float64 (n_q), overwritten.  With Hbar = sum_k f_k c_k c_k^T
- * this equals w_q n_q.  Asynchronous. */
-pufe_status pufe_assemble_HV_adjoint(pufe_ctx *ctx, const double *Hbar, double *Vbar,
+ * this equals w_q n_q.  PUFE_TF32X3 evaluates in FP32.  Asynchronous. */
+pufe_status pufe_assemble_HV_adjoint(pufe_ctx *ctx, const double *Hbar, int prec, double *Vbar,
                                      void *stream);
 
 /* Wait for `stream`, then report (and clear) any device-side error flag. */

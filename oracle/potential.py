@@ -43,8 +43,9 @@ def ionic_potential(wl, pts):
     for s, tau in wl["atoms"]:
         sp = wl["species"][s]
         amp = -(4.0 * math.pi / Omega) * sp["Z"] * np.exp(-G2 * sp["sigma"] ** 2 / 4.0) / G2
-        phase = (pts - np.asarray(tau)) @ G.T
-        out += np.cos(phase) @ amp
+        for i in range(0, pts.shape[0], 512):   # blocks of points bound the memory
+            phase = (pts[i:i + 512] - np.asarray(tau)) @ G.T
+            out[i:i + 512] += np.cos(phase) @ amp
     return out
 
 

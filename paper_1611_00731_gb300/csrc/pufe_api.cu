@@ -32,53 +32,71 @@ using namespace pufe;
 
 extern "C" {
 
-pufe_status pufe_tabulate(pufe_ctx *ctx, void *stream) {
+pufe_status pufe_tabulate(pufe_ctx *ctx, int prec, void *stream) {
   if (pufe_status e0 = need_device(ctx)) return e0;
+  if (prec != PUFE_FP64 && prec != PUFE_TF32X3) return fail(PUFE_EINVAL, "unknown precision");
   DeviceGuard g(ctx->device);
   if (!g.ok) return fail(PUFE_ECUDA, "cudaSetDevice failed");
-  pufe_status st = launch_tabulate(ctx, (cudaStream_t)stream);
-  if (st == PUFE_OK) ctx->tabulated = true;
+  pufe_status st;
+  if (prec == PUFE_FP64) {
+    st = launch_tabulate(ctx, (cudaStream_t)stream);
+    if (st == PUFE_OK) ctx->tabulated = true;
+  } else {
+    st = launch_tabulate_f32(ctx, (cudaStream_t)stream);
+    if (st == PUFE_OK) ctx->tabulated32 = true;
+  }
   return st;
+}
+
+static pufe_status need_table(const pufe_ctx *ctx, int prec) {
+  if (ctx->psi_len == 0) return PUFE_OK;
+  if (prec == PUFE_FP64 && !ctx->tabulated)
+    return fail(PUFE_ESTATE, "call pufe_tabulate(PUFE_FP64) first");
+  if (prec == PUFE_TF32X3 && !ctx->tabulated32)
+    return fail(PUFE_ESTATE, "call pufe_tabulate(PUFE_TF32X3) first");
+  return PUFE_OK;
 }
 
 pufe_status pufe_assemble_HS(pufe_ctx *ctx, const double *V, int prec, int what, double *H,
                              double *S, void *stream) {
   if (pufe_status e0 = need_device(ctx)) return e0;
-  if (!ctx->tabulated && ctx->psi_len > 0) return fail(PUFE_ESTATE, "call pufe_tabulate first");
+  if (prec != PUFE_FP64 && prec != PUFE_TF32X3) return fail(PUFE_EINVAL, "unknown precision");
+  if (pufe_status e1 = need_table(ctx, prec)) return e1;
   if (what <= 0 || what > (PUFE_WANT_H | PUFE_WANT_S)) return fail(PUFE_EINVAL, "bad `what` mask");
   if ((what & PUFE_WANT_H) && (!H || !V)) return fail(PUFE_EINVAL, "H wanted: need H and V");
   if ((what & PUFE_WANT_S) && !S) return fail(PUFE_EINVAL, "S wanted: need S");
-  if (prec != PUFE_FP64 && prec != PUFE_TF32X3) return fail(PUFE_EINVAL, "unknown precision");
   DeviceGuard g(ctx->device);
   if (!g.ok) return fail(PUFE_ECUDA, "cudaSetDevice failed");
   cudaStream_t st = (cudaStream_t)stream;
+  if (prec == PUFE_TF32X3) return launch_assemble_tc(ctx, V, what, H, S, st);
   const size_t bytes = (size_t)ctx->nnz * sizeof(double);
   if (what & PUFE_WANT_H) PUFE_CUDA_TRY(cudaMemsetAsync(H, 0, bytes, st));
   if (what & PUFE_WANT_S) PUFE_CUDA_TRY(cudaMemsetAsync(S, 0, bytes, st));
-  if (prec == PUFE_FP64) return launch_assemble_fp64(ctx, V, what, H, S, st);
-  return launch_assemble_tc(ctx, V, what, H, S, st);
+  return launch_assemble_fp64(ctx, V, what, H, S, st);
 }
 
 pufe_status pufe_density(pufe_ctx *ctx, const double *C, int64_t ldc, const double *f, int nocc,
                          int prec, double *rho, void *stream) {
   if (pufe_status e0 = need_device(ctx)) return e0;
-  if (!ctx->tabulated && ctx->psi_len > 0) return fail(PUFE_ESTATE, "call pufe_tabulate first");
+  if (prec != PUFE_FP64 && prec != PUFE_TF32X3) return fail(PUFE_EINVAL, "unknown precision");
+  if (pufe_status e1 = need_table(ctx, prec)) return e1;
   if (!C || !f || !rho) return fail(PUFE_EINVAL, "C, f and rho must not be NULL");
   if (nocc < 1 || nocc > 64 || ldc < nocc) return fail(PUFE_EINVAL, "need 1 <= nocc <= 64 and ldc >= nocc");
-  if (prec != PUFE_FP64 && prec != PUFE_TF32X3) return fail(PUFE_EINVAL, "unknown precision");
   DeviceGuard g(ctx->device);
   if (!g.ok) return fail(PUFE_ECUDA, "cudaSetDevice failed");
   if (prec == PUFE_FP64) return launch_density_fp64(ctx, C, ldc, f, nocc, rho, (cudaStream_t)stream);
   return launch_density_tc(ctx, C, ldc, f, nocc, rho, (cudaStream_t)stream);
 }
 
-pufe_status pufe_assemble_HV_adjoint(pufe_ctx *ctx, const double *Hbar, double *Vbar,
+pufe_status pufe_assemble_HV_adjoint(pufe_ctx *ctx, const double *Hbar, int prec, double *Vbar,
                                      void *stream) {
   if (pufe_status e0 = need_device(ctx)) return e0;
-  if (!ctx->tabulated && ctx->psi_len > 0) return fail(PUFE_ESTATE, "call pufe_tabulate first");
+  if (prec != PUFE_FP64 && prec != PUFE_TF32X3) return fail(PUFE_EINVAL, "unknown precision");
+  if (pufe_status e1 = need_table(ctx, prec)) return e1;
   if (!Hbar || !Vbar) return fail(PUFE_EINVAL, "Hbar and Vbar must not be NULL");
   DeviceGuard g(ctx->device);
   if (!g.ok) return fail(PUFE_ECUDA, "cudaSetDevice failed");
+  if (prec == PUFE_TF32X3) return launch_adjoint_tc(ctx, Hbar, Vbar, (cudaStream_t)stream);
   return launch_adjoint_fp64(ctx, Hbar, Vbar, (cudaStream_t)stream);
 }
 

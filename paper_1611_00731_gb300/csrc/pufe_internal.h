@@ -61,6 +61,9 @@ struct DeviceArrays {
   int32_t *alist = nullptr;   // element enrichment list (global alpha ids)
   int64_t *toff = nullptr;    // nelem + 1: offsets into psi (units of q*alpha)
   double *psi = nullptr;      // 4 * sum Q_e A_e: [aslot][comp][q] per element
+  float *psi32 = nullptr;     // same layout, FP32 (mixed-precision path)
+  double *T0 = nullptr;       // nnz: global FE-FE kinetic blocks (constant)
+  double *S0 = nullptr;       // nnz: global FE-FE overlap blocks (constant)
   Orbital *orb = nullptr;     // n_alpha
   // global sparse storage
   int64_t *rowptr = nullptr;  // N + 1
@@ -83,7 +86,10 @@ struct pufe_ctx {
   int64_t nelem = 0, nq = 0, n_dof = 0, n_fe = 0, nnz = 0;
   int64_t n_alpha = 0, psi_len = 0, smap_len = 0, dof_len = 0;
   int max_basis = 0, max_q = 0, max_alpha = 0;
-  bool tabulated = false;
+  bool tabulated = false;     // FP64 enrichment table is current
+  bool tabulated32 = false;   // FP32 enrichment table is current
+  bool fe_exact = false;      // every rule has >= 4 points per axis per (sub)cell
+  int n_big = 0;              // elements with n_e > 128 (listed first in `order`)
   bool on_device = false;   // device copies exist (a CUDA device was present)
   // host copies kept for getters
   std::vector<int64_t> qoff, rowptr, doff;
@@ -112,20 +118,22 @@ __host__ __device__ inline void lagrange3(double t, double L[4], double dL[4]) {
 }
 
 // Real solid harmonic r^l Y_lm(r^) (unit-normalised Y, no Condon-Shortley
-// phase, m < 0 <-> sin) and its gradient, for l <= 3.
-__host__ __device__ inline double solid_harmonic(int l, int m, double x, double y, double z,
-                                                 double g[3]) {
-  const double PI = 3.14159265358979323846;
-  g[0] = g[1] = g[2] = 0.0;
-  if (l == 0) return 0.5 / sqrt(PI);
+// phase, m < 0 <-> sin) and its gradient, for l <= 3.  T = double or float.
+template <class T>
+__host__ __device__ inline T solid_harmonic(int l, int m, T x, T y, T z, T g[3]) {
+  const T PI = T(3.14159265358979323846);
+  g[0] = g[1] = g[2] = T(0);
+  if (l == 0) return T(0.28209479177387814);  // 1 / (2 sqrt(pi))
   if (l == 1) {
-    const double c = sqrt(3.0 / (4.0 * PI));
+    const T c = T(0.48860251190291992);       // sqrt(3 / (4 pi))
     if (m == -1) { g[1] = c; return c * y; }
     if (m == 0) { g[2] = c; return c * z; }
     g[0] = c; return c * x;
   }
   if (l == 2) {
-    const double A = 0.5 * sqrt(15.0 / PI), B = 0.25 * sqrt(5.0 / PI), C = 0.25 * sqrt(15.0 / PI);
+    const T A = T(1.0925484305920792);        // sqrt(15/pi) / 2
+    const T B = T(0.31539156525252005);       // sqrt(5/pi) / 4
+    const T C = T(0.54627421529603959);       // sqrt(15/pi) / 4
     switch (m) {
       case -2: g[0] = A * y; g[1] = A * x; return A * x * y;
       case -1: g[1] = A * z; g[2] = A * y; return A * y * z;
@@ -135,9 +143,12 @@ __host__ __device__ inline double solid_harmonic(int l, int m, double x, double 
       default: g[0] = 2 * C * x; g[1] = -2 * C * y; return C * (x * x - y * y);
     }
   }
-  const double D = 0.25 * sqrt(35.0 / (2.0 * PI)), E = 0.5 * sqrt(105.0 / PI);
-  const double F = 0.25 * sqrt(21.0 / (2.0 * PI)), G = 0.25 * sqrt(7.0 / PI);
-  const double H = 0.25 * sqrt(105.0 / PI);
+  (void)PI;
+  const T D = T(0.59004358992664352);         // sqrt(35/(2 pi)) / 4
+  const T E = T(2.8906114426405538);          // sqrt(105/pi) / 2
+  const T F = T(0.45704579946446572);         // sqrt(21/(2 pi)) / 4
+  const T G = T(0.37317633259011540);         // sqrt(7/pi) / 4
+  const T H = T(1.4453057213202769);          // sqrt(105/pi) / 4
   switch (m) {
     case -3: g[0] = 6 * D * x * y; g[1] = 3 * D * (x * x - y * y); return D * y * (3 * x * x - y * y);
     case -2: g[0] = E * y * z; g[1] = E * x * z; g[2] = E * x * y; return E * x * y * z;
@@ -153,8 +164,9 @@ __host__ __device__ inline double solid_harmonic(int l, int m, double x, double 
   }
 }
 
-__host__ __device__ inline double ipow(double r, int k) {
-  double p = 1.0;
+template <class T>
+__host__ __device__ inline T ipow(T r, int k) {
+  T p = T(1);
   for (int i = 0; i < k; ++i) p *= r;
   return p;
 }
@@ -162,27 +174,29 @@ __host__ __device__ inline double ipow(double r, int k) {
 // Psi~(d) h(|d|, r_c) for one image displacement d, plus its gradient
 // (accumulated into psi and g).  Psi~ = N r^(n-1) e^(-zeta r) Y_lm, written
 // as f(r) S_lm(d) with f = N r^(n-1-l) e^(-zeta r) h(r) and S_lm = r^l Y_lm.
-__host__ __device__ inline void orbital_accumulate(const Orbital &o, double dx, double dy,
-                                                   double dz, double &psi, double g[3]) {
-  const double r2 = dx * dx + dy * dy + dz * dz;
-  if (r2 >= o.rc * o.rc) return;
-  const double r = sqrt(r2);
-  const double x = r / o.rc;
-  const double x3 = x * x * x;
-  const double hc = 1.0 + x3 * x * (-35.0 + x * (84.0 + x * (-70.0 + 20.0 * x)));
-  const double omx = 1.0 - x;
-  const double dh = -140.0 * x3 * omx * omx * omx / o.rc;
+template <class T>
+__host__ __device__ inline void orbital_accumulate(const Orbital &o, T dx, T dy, T dz, T &psi,
+                                                   T g[3]) {
+  const T rc = T(o.rc);
+  const T r2 = dx * dx + dy * dy + dz * dz;
+  if (r2 >= rc * rc) return;
+  const T r = sqrt(r2);
+  const T x = r / rc;
+  const T x3 = x * x * x;
+  const T hc = T(1) + x3 * x * (T(-35) + x * (T(84) + x * (T(-70) + T(20) * x)));
+  const T omx = T(1) - x;
+  const T dh = T(-140) * x3 * omx * omx * omx / rc;
   const int k = o.n - 1 - o.l;  // >= 0
-  const double ez = o.norm * exp(-o.zeta * r);
-  const double rk = ipow(r, k);
-  const double f = ez * rk * hc;
-  const double rkm1 = (k > 0) ? ipow(r, k - 1) : 0.0;
-  const double df = ez * ((double)k * rkm1 * hc - o.zeta * rk * hc + rk * dh);
-  double gs[3];
-  const double S = solid_harmonic(o.l, o.m, dx, dy, dz, gs);
+  const T ez = T(o.norm) * exp(-T(o.zeta) * r);
+  const T rk = ipow(r, k);
+  const T f = ez * rk * hc;
+  const T rkm1 = (k > 0) ? ipow(r, k - 1) : T(0);
+  const T df = ez * (T(k) * rkm1 * hc - T(o.zeta) * rk * hc + rk * dh);
+  T gs[3];
+  const T S = solid_harmonic<T>(o.l, o.m, dx, dy, dz, gs);
   psi += f * S;
-  if (r > 1e-14) {
-    const double s = df * S / r;
+  if (r > T(1e-14)) {
+    const T s = df * S / r;
     g[0] += s * dx + f * gs[0];
     g[1] += s * dy + f * gs[1];
     g[2] += s * dz + f * gs[2];
@@ -194,12 +208,14 @@ __host__ __device__ inline void orbital_accumulate(const Orbital &o, double dx, 
 }
 
 // Periodic enrichment Psi_alpha(p) (eq. Psi with f(R) = 1): all images of the
-// atom within r_c of p.  `img` = image half-width per axis.
+// atom within r_c of p.  `img` = image half-width per axis.  The displacement
+// to the nearest image is formed in double precision, then evaluated in T.
+template <class T>
 __host__ __device__ inline void enrichment_eval(const Orbital &o, const double p[3],
-                                                const double a[3], const int img[3],
-                                                double &psi, double g[3]) {
-  psi = 0.0;
-  g[0] = g[1] = g[2] = 0.0;
+                                                const double a[3], const int img[3], T &psi,
+                                                T g[3]) {
+  psi = T(0);
+  g[0] = g[1] = g[2] = T(0);
   double d0[3];
   for (int k = 0; k < 3; ++k) {
     double d = p[k] - o.tau[k];
@@ -209,7 +225,8 @@ __host__ __device__ inline void enrichment_eval(const Orbital &o, const double p
   for (int i = -img[0]; i <= img[0]; ++i)
     for (int j = -img[1]; j <= img[1]; ++j)
       for (int k = -img[2]; k <= img[2]; ++k)
-        orbital_accumulate(o, d0[0] + i * a[0], d0[1] + j * a[1], d0[2] + k * a[2], psi, g);
+        orbital_accumulate<T>(o, T(d0[0] + i * a[0]), T(d0[1] + j * a[1]), T(d0[2] + k * a[2]),
+                              psi, g);
 }
 
 // launchers implemented in the .cu files
@@ -219,6 +236,8 @@ pufe_status launch_assemble_fp64(pufe_ctx *ctx, const double *V, int what, doubl
 pufe_status launch_density_fp64(pufe_ctx *ctx, const double *C, int64_t ldc, const double *f,
                                 int nocc, double *rho, cudaStream_t s);
 pufe_status launch_adjoint_fp64(pufe_ctx *ctx, const double *Hbar, double *Vbar, cudaStream_t s);
+pufe_status launch_tabulate_f32(pufe_ctx *ctx, cudaStream_t s);
+pufe_status launch_adjoint_tc(pufe_ctx *ctx, const double *Hbar, double *Vbar, cudaStream_t s);
 pufe_status launch_assemble_tc(pufe_ctx *ctx, const double *V, int what, double *H, double *S,
                                cudaStream_t s);
 pufe_status launch_density_tc(pufe_ctx *ctx, const double *C, int64_t ldc, const double *f,

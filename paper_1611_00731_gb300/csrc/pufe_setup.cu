@@ -512,13 +512,61 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
     }
   });
 
-  // ---- work order: big elements first ----------------------------------------
+  // ---- work order: elements with n_e > 128 first, then by cost ---------------
   std::vector<int32_t> order(nelem);
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
+    const bool bx = n_e[x] > 128, by = n_e[y] > 128;
+    if (bx != by) return bx;
     int64_t cx = (int64_t)n_e[x] * n_e[x] * q_e[x], cy = (int64_t)n_e[y] * n_e[y] * q_e[y];
     return cx > cy;
   });
+  int n_big = 0;
+  for (int64_t e = 0; e < nelem; ++e) n_big += n_e[e] > 128 ? 1 : 0;
+
+  // ---- constant FE-FE blocks (exact for rules with >= 4 points per axis) -----
+  // 1D cubic Lagrange mass/stiffness on [-1, 1] by the 4-point Gauss rule,
+  // which is exact for their degree-6 integrands.
+  int min_p = 1 << 30;
+  for (auto &parts : rule)
+    for (auto &pt : parts) min_p = std::min(min_p, pt.p);
+  const bool fe_exact = min_p >= 4;
+  std::vector<double> T0, S0;
+  if (fe_exact) {
+    double M1[4][4] = {{0}}, K1[4][4] = {{0}};
+    for (int g = 0; g < 4; ++g) {
+      double L[4], dL[4];
+      lagrange3(S.gx[4][g], L, dL);
+      for (int a = 0; a < 4; ++a)
+        for (int b = 0; b < 4; ++b) {
+          M1[a][b] += S.gw[4][g] * L[a] * L[b];
+          K1[a][b] += S.gw[4][g] * dL[a] * dL[b];
+        }
+    }
+    const double J = 0.125 * S.h[0] * S.h[1] * S.h[2];
+    const double s2[3] = {4.0 / (S.h[0] * S.h[0]), 4.0 / (S.h[1] * S.h[1]), 4.0 / (S.h[2] * S.h[2])};
+    std::vector<double> TF(64 * 64), SF(64 * 64);
+    for (int i = 0; i < 64; ++i)
+      for (int j = 0; j < 64; ++j) {
+        const int ia[3] = {i & 3, (i >> 2) & 3, i >> 4}, ja[3] = {j & 3, (j >> 2) & 3, j >> 4};
+        const double mx = M1[ia[0]][ja[0]], my = M1[ia[1]][ja[1]], mz = M1[ia[2]][ja[2]];
+        SF[i * 64 + j] = J * mx * my * mz;
+        TF[i * 64 + j] = 0.5 * J * (s2[0] * K1[ia[0]][ja[0]] * my * mz +
+                                    s2[1] * mx * K1[ia[1]][ja[1]] * mz +
+                                    s2[2] * mx * my * K1[ia[2]][ja[2]]);
+      }
+    T0.assign(nnz, 0.0);
+    S0.assign(nnz, 0.0);
+    for (int64_t e = 0; e < nelem; ++e) {
+      const int n = n_e[e];
+      const int32_t *m = &smap[soff[e]];
+      for (int i = 0; i < 64; ++i)
+        for (int j = 0; j < 64; ++j) {
+          T0[m[(int64_t)i * n + j]] += TF[i * 64 + j];
+          S0[m[(int64_t)i * n + j]] += SF[i * 64 + j];
+        }
+    }
+  }
 
   // ---- fill the context and upload ----------------------------------------
   for (int k = 0; k < 3; ++k) {
@@ -538,6 +586,8 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
   ctx->dof_len = doff[nelem];
   ctx->max_basis = *std::max_element(n_e.begin(), n_e.end());
   ctx->max_q = *std::max_element(q_e.begin(), q_e.end());
+  ctx->fe_exact = fe_exact;
+  ctx->n_big = n_big;
   ctx->max_alpha = 0;
   for (auto &v : ealpha) ctx->max_alpha = std::max(ctx->max_alpha, (int)v.size());
 
@@ -571,7 +621,12 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
   if ((st = upload(&D.soff, soff)) != PUFE_OK) return st;
   if ((st = upload(&D.smap, smap)) != PUFE_OK) return st;
   if ((st = upload(&D.order, order)) != PUFE_OK) return st;
+  if (fe_exact) {
+    if ((st = upload(&D.T0, T0)) != PUFE_OK) return st;
+    if ((st = upload(&D.S0, S0)) != PUFE_OK) return st;
+  }
   PUFE_CUDA_TRY(cudaMalloc((void **)&D.psi, std::max<int64_t>(1, ctx->psi_len) * sizeof(double)));
+  PUFE_CUDA_TRY(cudaMalloc((void **)&D.psi32, std::max<int64_t>(1, ctx->psi_len) * sizeof(float)));
   PUFE_CUDA_TRY(cudaMalloc((void **)&D.err, sizeof(unsigned)));
   PUFE_CUDA_TRY(cudaMemset(D.err, 0, sizeof(unsigned)));
   }
@@ -592,7 +647,8 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
 static void free_device(pufe_ctx *ctx) {
   auto &D = ctx->d;
   void *ptrs[] = {D.qoff, D.x, D.w, D.xi, D.doff, D.dofs, D.ecol, D.aoff, D.alist,
-                  D.toff, D.psi, D.orb, D.rowptr, D.col, D.soff, D.smap, D.order, D.err};
+                  D.toff, D.psi, D.psi32, D.T0, D.S0, D.orb, D.rowptr, D.col, D.soff,
+                  D.smap, D.order, D.err};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   D = DeviceArrays();

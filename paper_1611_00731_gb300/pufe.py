@@ -80,10 +80,10 @@ def load_library(build_if_missing: bool = True):
     lib.pufe_get_quadrature.argtypes = [vp, dp, dp, i64p]
     lib.pufe_get_pattern.argtypes = [vp, i64p, i32p]
     lib.pufe_get_element_basis.argtypes = [vp, i32p, i32p]
-    lib.pufe_tabulate.argtypes = [vp, vp]
+    lib.pufe_tabulate.argtypes = [vp, C.c_int, vp]
     lib.pufe_assemble_HS.argtypes = [vp, vp, C.c_int, C.c_int, vp, vp, vp]
     lib.pufe_density.argtypes = [vp, vp, C.c_int64, vp, C.c_int, C.c_int, vp, vp]
-    lib.pufe_assemble_HV_adjoint.argtypes = [vp, vp, vp, vp]
+    lib.pufe_assemble_HV_adjoint.argtypes = [vp, vp, C.c_int, vp, vp]
     lib.pufe_sync_status.argtypes = [vp, vp]
     lib.pufe_destroy.argtypes = [vp]
     lib.pufe_destroy.restype = None
@@ -158,8 +158,8 @@ class Context:
         return n_e, dofs
 
     # -- compute calls --------------------------------------------------------
-    def pufe_tabulate(self, stream=None):
-        _check(_LIB.pufe_tabulate(self._h, _stream(stream)))
+    def pufe_tabulate(self, prec=PUFE_FP64, stream=None):
+        _check(_LIB.pufe_tabulate(self._h, int(prec), _stream(stream)))
 
     def pufe_assemble_HS(self, V, H=None, S=None, prec=PUFE_FP64, what=None, stream=None):
         import torch
@@ -176,9 +176,9 @@ class Context:
                                  _ptr(f, torch.float64), int(nocc), int(prec),
                                  _ptr(rho, torch.float64), _stream(stream)))
 
-    def pufe_assemble_HV_adjoint(self, Hbar, Vbar, stream=None):
+    def pufe_assemble_HV_adjoint(self, Hbar, Vbar, prec=PUFE_FP64, stream=None):
         import torch
-        _check(_LIB.pufe_assemble_HV_adjoint(self._h, _ptr(Hbar, torch.float64),
+        _check(_LIB.pufe_assemble_HV_adjoint(self._h, _ptr(Hbar, torch.float64), int(prec),
                                              _ptr(Vbar, torch.float64), _stream(stream)))
 
     def pufe_sync_status(self, stream=None):

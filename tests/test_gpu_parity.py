@@ -43,7 +43,7 @@ def _gpu_HS(ctx, V, prec=pufe.PUFE_FP64):
     dev = _dev()
     H = torch.empty(ctx.nnz, dtype=torch.float64, device=dev)
     S = torch.empty_like(H)
-    ctx.pufe_tabulate()
+    ctx.pufe_tabulate(prec)
     ctx.pufe_assemble_HS(torch.tensor(V, device=dev), H, S, prec=prec)
     ctx.pufe_sync_status()
     return _csr(ctx, H.cpu().numpy()), _csr(ctx, S.cpu().numpy())
@@ -180,3 +180,96 @@ def test_full_size_rocksalt_sampled_rows():
         sg = Sg[r].toarray().ravel()
         assert np.abs(hg - Hr[k]).max() < TOL64 * np.abs(Hr[k]).max()
         assert np.abs(sg - Sr[k]).max() < TOL64 * np.abs(Sr[k]).max()
+
+
+# ---------------------------------------------------------------------------
+# Mixed precision (PUFE_TF32X3).  Tolerances from the arithmetic: every operand
+# carries ~22 significant bits after the two-term TF32 split and the element
+# sums accumulate in FP32 (2^-24 per addition over Q <= 4096 terms), so matrix
+# entries carry ~1e-7 relative error of the largest entry; 5e-6 leaves margin.
+# Eigenvalues must meet the 1e-5 Ha target; density and adjoint are FP32 sums.
+# ---------------------------------------------------------------------------
+TOL_MAT_TF32 = 5e-6
+TOL_EIG_TF32 = 1e-5
+
+
+TF32_CASES = dict(CASES, one_element=lambda: W.small_two_atom(nel=1, quad_p=4))
+
+
+@pytest.mark.parametrize("name", list(TF32_CASES))
+def test_tf32x3_assembly_matches_oracle(name):
+    wl = TF32_CASES[name]()
+    m = omesh.Mesh(wl)
+    rules = oq.all_rules(m)
+    ctx = pufe.pufe_build_mesh(wl)
+    V = W.random_potential(len(rules[1]), seed=11)
+    Ho, So = oasm.assemble_HS(m, rules, V)
+    Hg, Sg = _gpu_HS(ctx, V, pufe.PUFE_TF32X3)
+    eh, es = _rel(Hg, Ho), _rel(Sg, So)
+    print(f"{name}: TF32X3 rel err H {eh:.2e} S {es:.2e}")
+    assert eh < TOL_MAT_TF32 and es < TOL_MAT_TF32
+
+
+def test_tf32x3_c1_eigenvalues_and_density():
+    wl = W.workload("c1_two_atom_4cube")
+    m = omesh.Mesh(wl)
+    rules = oq.all_rules(m)
+    ctx = pufe.pufe_build_mesh(wl)
+    V = opot.ionic_potential(wl, rules[0])
+    Hg, Sg = _gpu_HS(ctx, V, pufe.PUFE_TF32X3)
+    Ho, So = oasm.assemble_HS(m, rules, V)
+    wg, _ = oeig.lowest_eigs(Hg, Sg, 4)
+    wo, co = oeig.lowest_eigs(Ho, So, 4)
+    print("TF32X3 C1 eigenvalue errors", np.abs(wg - wo))
+    assert np.abs(wg - wo).max() < TOL_EIG_TF32
+    dev = _dev()
+    f = np.array([2.0, 2.0])
+    rho = torch.empty(ctx.n_q, dtype=torch.float64, device=dev)
+    ctx.pufe_density(torch.tensor(np.ascontiguousarray(co[:, :2]), device=dev),
+                     torch.tensor(f, device=dev), rho, prec=pufe.PUFE_TF32X3)
+    ctx.pufe_sync_status()
+    ro = oasm.density(m, rules, co[:, :2], f)
+    assert _rel(rho.cpu().numpy(), ro) < 1e-5
+
+
+def test_tf32x3_adjoint_and_density_random(case):
+    name, wl, m, rules, ctx = case
+    if name == "one_element":
+        pytest.skip("3-point rule: TF32X3 needs >= 4 points per axis")
+    dev = _dev()
+    V = W.random_potential(len(rules[1]), seed=5)
+    Ho, _ = oasm.assemble_HS(m, rules, V)
+    Hbar = Ho.copy()
+    Hbar.data = W.random_symmetric_values(Ho.nnz, seed=9)
+    go = oasm.adjoint_V(m, rules, Hbar)
+    out = torch.empty(ctx.n_q, dtype=torch.float64, device=dev)
+    ctx.pufe_tabulate(pufe.PUFE_TF32X3)
+    ctx.pufe_assemble_HV_adjoint(torch.tensor(Hbar.data, device=dev), out, prec=pufe.PUFE_TF32X3)
+    Cm = W.random_coefficients(m.n_dof, 7, seed=2)
+    f = W.random_occupations(7, seed=2)
+    rho = torch.empty(ctx.n_q, dtype=torch.float64, device=dev)
+    ctx.pufe_density(torch.tensor(Cm, device=dev), torch.tensor(f, device=dev), rho,
+                     prec=pufe.PUFE_TF32X3)
+    ctx.pufe_sync_status()
+    ro = oasm.density(m, rules, Cm, f)
+    assert _rel(out.cpu().numpy(), go) < 1e-4, name
+    assert _rel(rho.cpu().numpy(), ro) < 1e-5, name
+
+
+def test_tf32x3_c3_like_large_elements():
+    """n_e > 128 takes the two-pass 256-row tile (fixed 5^3 rule keeps the
+    oracle quick)."""
+    wl = W.workload("c3_cscl_4cube")
+    wl["species"][0]["orbitals"] = [o for o in wl["species"][0]["orbitals"] if o[0] >= 3]
+    wl["species"][0]["r_e"] = 1.5
+    wl["quad"] = dict(wl["quad"], mode=W.QUAD_FIXED, p_far=5, p_near=5)
+    m = omesh.Mesh(wl)
+    rules = oq.all_rules(m)
+    ctx = pufe.pufe_build_mesh(wl)
+    assert ctx.max_basis > 128
+    V = W.random_potential(len(rules[1]), seed=3)
+    Ho, So = oasm.assemble_HS(m, rules, V)
+    Hg, Sg = _gpu_HS(ctx, V, pufe.PUFE_TF32X3)
+    eh, es = _rel(Hg, Ho), _rel(Sg, So)
+    print(f"c3-like: TF32X3 rel err H {eh:.2e} S {es:.2e}")
+    assert eh < TOL_MAT_TF32 and es < TOL_MAT_TF32
