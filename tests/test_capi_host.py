@@ -89,5 +89,5 @@ def test_compute_calls_need_a_device_context(lib):
     if torch.cuda.is_available():
         pytest.skip("a CUDA device is present")
     ctx = pufe.pufe_build_mesh(W.small_two_atom(nel=2))
-    assert pufe._LIB.pufe_tabulate(ctx._h, None) == 8  # PUFE_ESTATE
+    assert pufe._LIB.pufe_tabulate(ctx._h, 0, None) == 8  # PUFE_ESTATE
     assert b"without a CUDA device" in pufe._LIB.pufe_last_error()
