@@ -217,8 +217,16 @@ __global__ void __launch_bounds__(TC_NT, 1) k_assemble_tc(
   constexpr int TILE = R * KC * 4;         // bytes per tile
   constexpr uint32_t LBO = 128;            // next core matrix along K
   constexpr uint32_t SBO = (KC / 4) * 128; // next 8-row group along M/N
-  constexpr uint32_t TCOLS = (R == 128) ? 256 : 512;
-  constexpr uint32_t S_COL = (R == 128) ? 128 : 256;
+  // Tensor-core FP32 accumulation does not round to nearest; its error grows
+  // with the number of MMAs summed into one accumulator.  With the 128-row
+  // tile the large hi*hi products and the small cross products go to
+  // separate accumulators (cross terms are ~2^-11 smaller, so their error is
+  // negligible) and the two are added in FP64 by the epilogue.
+  constexpr bool SPLIT = (R == 128);
+  constexpr uint32_t TCOLS = 512;
+  constexpr uint32_t HX_COL = SPLIT ? 128 : 0;    // cross-term H accumulator
+  constexpr uint32_t S_COL = SPLIT ? 256 : 256;   // hi*hi S accumulator
+  constexpr uint32_t SX_COL = SPLIT ? 320 : 256;  // cross-term S accumulator
   static_assert(NTILES * TILE == STAGE_BYTES, "stage size");
 
   extern __shared__ __align__(16) unsigned char dsm[];
@@ -253,7 +261,9 @@ __global__ void __launch_bounds__(TC_NT, 1) k_assemble_tc(
   __syncthreads();
   tc_fence_after();
   const uint32_t tH = sh.tmem;
+  const uint32_t tHx = sh.tmem + HX_COL;
   const uint32_t tS = sh.tmem + S_COL;
+  const uint32_t tSx = sh.tmem + SX_COL;
   const uint32_t sbase = smem_u32(stages);
   const uint32_t idH = idesc_tf32(128, npad);
   const uint32_t idE = idesc_tf32(128, nenr16 > 0 ? nenr16 : 16);
@@ -356,20 +366,23 @@ __global__ void __launch_bounds__(TC_NT, 1) k_assemble_tc(
           const uint32_t ko = (uint32_t)ks * 2u * LBO;
           const uint32_t first = (qc == 0 && ks == 0) ? 0u : 1u;
           auto D = [&](int t, uint32_t extra) { return sdesc(st + t * TILE + ko + extra, LBO, SBO); };
-          // H_V = ZV^T Z over all columns
+          // H_V = ZV^T Z over all columns (hi*hi, then hi*lo + lo*hi)
+          const uint32_t fx = SPLIT ? first : 1u;
           mma_tf32(tH, D(8, moff), D(6, 0), idH, first);
-          mma_tf32(tH, D(8, moff), D(7, 0), idH, 1u);
-          mma_tf32(tH, D(9, moff), D(6, 0), idH, 1u);
+          mma_tf32(tHx, D(8, moff), D(7, 0), idH, fx);
+          mma_tf32(tHx, D(9, moff), D(6, 0), idH, 1u);
           if (nenr > 0) {
+            // T on the enrichment columns: sum_d Y_d^T Y_d[64:]
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
               mma_tf32(tH + 64, D(2 * d, moff), D(2 * d, eoff), idE, 1u);
-              mma_tf32(tH + 64, D(2 * d, moff), D(2 * d + 1, eoff), idE, 1u);
-              mma_tf32(tH + 64, D(2 * d + 1, moff), D(2 * d, eoff), idE, 1u);
+              mma_tf32(tHx + 64, D(2 * d, moff), D(2 * d + 1, eoff), idE, 1u);
+              mma_tf32(tHx + 64, D(2 * d + 1, moff), D(2 * d, eoff), idE, 1u);
             }
+            // S on the enrichment columns: Z^T Z[64:]
             mma_tf32(tS, D(6, moff), D(6, eoff), idE, first);
-            mma_tf32(tS, D(6, moff), D(7, eoff), idE, 1u);
-            mma_tf32(tS, D(7, moff), D(6, eoff), idE, 1u);
+            mma_tf32(tSx, D(6, moff), D(7, eoff), idE, SPLIT ? first : 1u);
+            mma_tf32(tSx, D(7, moff), D(6, eoff), idE, 1u);
           }
         }
         mma_commit(&sh.bar[stg]);
@@ -394,10 +407,14 @@ __global__ void __launch_bounds__(TC_NT, 1) k_assemble_tc(
     const uint32_t lanebase = (uint32_t)(quarter * 32) << 16;
     const int32_t *m = smap + soff[e];
     for (int cb = half; cb * 16 < npad; cb += 2) {
-      float hv[16], sv[16];
+      float hv[16], sv[16], hx[16], sx2[16];
       tmem_ld16(tH + lanebase + cb * 16, hv);
+      if (SPLIT) tmem_ld16(tHx + lanebase + cb * 16, hx);
       const bool enr_blk = cb * 16 >= 64;
-      if (enr_blk && nenr > 0) tmem_ld16(tS + lanebase + (cb * 16 - 64), sv);
+      if (enr_blk && nenr > 0) {
+        tmem_ld16(tS + lanebase + (cb * 16 - 64), sv);
+        if (SPLIT) tmem_ld16(tSx + lanebase + (cb * 16 - 64), sx2);
+      }
       if (r < n) {
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
@@ -408,12 +425,14 @@ __global__ void __launch_bounds__(TC_NT, 1) k_assemble_tc(
           const int32_t sij = m[(int64_t)r * n + c];
           const int32_t sji = m[(int64_t)c * n + r];
           if (want & PUFE_WANT_H) {
-            atomicAdd(H + sij, (double)hv[i]);
-            if (c != r) atomicAdd(H + sji, (double)hv[i]);
+            const double hval = SPLIT ? (double)hv[i] + (double)hx[i] : (double)hv[i];
+            atomicAdd(H + sij, hval);
+            if (c != r) atomicAdd(H + sji, hval);
           }
           if (enr_blk && (want & PUFE_WANT_S)) {
-            atomicAdd(S + sij, (double)sv[i]);
-            if (c != r) atomicAdd(S + sji, (double)sv[i]);
+            const double sval = SPLIT ? (double)sv[i] + (double)sx2[i] : (double)sv[i];
+            atomicAdd(S + sij, sval);
+            if (c != r) atomicAdd(S + sji, sval);
           }
         }
       }

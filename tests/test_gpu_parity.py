@@ -184,12 +184,15 @@ def test_full_size_rocksalt_sampled_rows():
 
 # ---------------------------------------------------------------------------
 # Mixed precision (PUFE_TF32X3).  Tolerances from the arithmetic: every operand
-# carries ~22 significant bits after the two-term TF32 split and the element
-# sums accumulate in FP32 (2^-24 per addition over Q <= 4096 terms), so matrix
-# entries carry ~1e-7 relative error of the largest entry; 5e-6 leaves margin.
-# Eigenvalues must meet the 1e-5 Ha target; density and adjoint are FP32 sums.
+# carries ~22 significant bits after the two-term TF32 split, and each element
+# sum is accumulated by the tensor cores in FP32 without round-to-nearest, so
+# an entry built from n accumulations carries up to ~n 2^-25 relative error
+# (biased, not a random walk).  The largest entries (enrichment kinetic terms)
+# take n = 3 Q / 8 + 1 hi*hi accumulations: Q = 512 gives ~6e-6; the bound
+# below allows 5x that.  Eigenvalues must meet the 1e-5 Ha target; density and
+# adjoint are FP32 sums on the CUDA cores (round to nearest).
 # ---------------------------------------------------------------------------
-TOL_MAT_TF32 = 5e-6
+TOL_MAT_TF32 = 3e-5
 TOL_EIG_TF32 = 1e-5
 
 
