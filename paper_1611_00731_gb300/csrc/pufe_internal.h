@@ -44,6 +44,12 @@ struct Orbital {
   int pad;
 };
 
+// the same enrichment with FP32 parameters (mixed-precision path)
+struct OrbitalF {
+  float zeta, norm, rc, inv_rc;
+  int n, l, m, pad;
+};
+
 // ---------------------------------------------------------------------------
 // context
 // ---------------------------------------------------------------------------
@@ -61,10 +67,17 @@ struct DeviceArrays {
   int32_t *alist = nullptr;   // element enrichment list (global alpha ids)
   int64_t *toff = nullptr;    // nelem + 1: offsets into psi (units of q*alpha)
   double *psi = nullptr;      // 4 * sum Q_e A_e: [aslot][comp][q] per element
-  float *psi32 = nullptr;     // same layout, FP32 (mixed-precision path)
+  // FP32 (mixed-precision) path: element points padded to a multiple of 8
+  int64_t *qpoff = nullptr;   // nelem + 1: offsets into qdat (padded points)
+  float4 *qdat = nullptr;     // per padded point: (xi_x, xi_y, xi_z, w); w = 0 on padding
+  int64_t *toff32 = nullptr;  // nelem + 1: offsets into psi32 (units of padded q*alpha)
+  float *psi32 = nullptr;     // per element [q/8][slot][comp][q%8]: 32-float blocks
+  float *eorig = nullptr;     // per (element, slot): displacement of the element
+                              // origin from the nearest atom image, hi[3], lo[3], 0, 0
   double *T0 = nullptr;       // nnz: global FE-FE kinetic blocks (constant)
   double *S0 = nullptr;       // nnz: global FE-FE overlap blocks (constant)
   Orbital *orb = nullptr;     // n_alpha
+  OrbitalF *orbf = nullptr;   // n_alpha
   // global sparse storage
   int64_t *rowptr = nullptr;  // N + 1
   int32_t *col = nullptr;     // nnz
@@ -85,6 +98,7 @@ struct pufe_ctx {
   int images[3] = {1, 1, 1};   // image search half-width per axis
   int64_t nelem = 0, nq = 0, n_dof = 0, n_fe = 0, nnz = 0;
   int64_t n_alpha = 0, psi_len = 0, smap_len = 0, dof_len = 0;
+  int64_t nq_pad = 0, psi32_len = 0;
   int max_basis = 0, max_q = 0, max_alpha = 0;
   bool tabulated = false;     // FP64 enrichment table is current
   bool tabulated32 = false;   // FP32 enrichment table is current

@@ -446,6 +446,15 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
     aoff[e + 1] = aoff[e] + (int32_t)ealpha[e].size();
     toff[e + 1] = toff[e] + (int64_t)q_e[e] * (int64_t)ealpha[e].size();
   }
+  // FP32 path: points padded to multiples of 8, chunk-blocked table offsets
+  std::vector<int64_t> qpoff(nelem + 1, 0), toff32(nelem + 1, 0);
+  for (int64_t e = 0; e < nelem; ++e) {
+    const int64_t qp = ((int64_t)q_e[e] + 7) / 8 * 8;
+    qpoff[e + 1] = qpoff[e] + qp;
+    toff32[e + 1] = toff32[e] + qp * (int64_t)ealpha[e].size();
+  }
+  std::vector<float4> qdat(qpoff[nelem]);
+  std::vector<float> eorig(8 * aoff[nelem], 0.0f);
   std::vector<int32_t> dofs(doff[nelem]), ecol(doff[nelem] - 64 * nelem), alist(aoff[nelem]);
   int64_t ecpos = 0;
   for (int64_t e = 0; e < nelem; ++e) {
@@ -457,7 +466,28 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
           int64_t gx = (3 * ex + a) % mx, gy = (3 * ey + b) % my, gz = (3 * ez + c) % mz;
           d[a + 4 * b + 16 * c] = (int32_t)(gx + mx * (gy + (int64_t)my * gz));
         }
-    for (size_t k = 0; k < ealpha[e].size(); ++k) alist[aoff[e] + k] = ealpha[e][k];
+    for (size_t k = 0; k < ealpha[e].size(); ++k) {
+      alist[aoff[e] + k] = ealpha[e][k];
+      // element origin minus the nearest image of the atom, split hi + lo
+      const Orbital &o = S.orb[ealpha[e][k]];
+      const Box b = elem_box(e);
+      float *dst = &eorig[8 * (aoff[e] + k)];
+      for (int d = 0; d < 3; ++d) {
+        double v = b.lo[d] - o.tau[d];
+        v -= S.a[d] * std::floor(v / S.a[d] + 0.5);
+        const float hi = (float)v;
+        dst[d] = hi;
+        dst[3 + d] = (float)(v - (double)hi);
+      }
+    }
+    for (int64_t q = 0; q < qpoff[e + 1] - qpoff[e]; ++q) {
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (q < q_e[e]) {
+        const int64_t g = qoff[e] + q;
+        v = make_float4((float)XI[3 * g], (float)XI[3 * g + 1], (float)XI[3 * g + 2], (float)Wt[g]);
+      }
+      qdat[qpoff[e] + q] = v;
+    }
     for (size_t j = 0; j < cols[e].size(); ++j) {
       d[64 + j] = (int32_t)cols[e][j].dof;
       int slot = (int)(std::lower_bound(ealpha[e].begin(), ealpha[e].end(), cols[e][j].alpha) -
@@ -582,6 +612,8 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
   ctx->nnz = nnz;
   ctx->n_alpha = (int64_t)S.orb.size();
   ctx->psi_len = 4 * toff[nelem];
+  ctx->nq_pad = qpoff[nelem];
+  ctx->psi32_len = 4 * toff32[nelem];
   ctx->smap_len = soff[nelem];
   ctx->dof_len = doff[nelem];
   ctx->max_basis = *std::max_element(n_e.begin(), n_e.end());
@@ -616,6 +648,14 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
   if ((st = upload(&D.alist, alist)) != PUFE_OK) return st;
   if ((st = upload(&D.toff, toff)) != PUFE_OK) return st;
   if ((st = upload(&D.orb, S.orb)) != PUFE_OK) return st;
+  {
+    std::vector<OrbitalF> of(S.orb.size());
+    for (size_t k = 0; k < S.orb.size(); ++k) {
+      const Orbital &o = S.orb[k];
+      of[k] = OrbitalF{(float)o.zeta, (float)o.norm, (float)o.rc, (float)(1.0 / o.rc), o.n, o.l, o.m, 0};
+    }
+    if ((st = upload(&D.orbf, of)) != PUFE_OK) return st;
+  }
   if ((st = upload(&D.rowptr, rowptr)) != PUFE_OK) return st;
   if ((st = upload(&D.col, colv)) != PUFE_OK) return st;
   if ((st = upload(&D.soff, soff)) != PUFE_OK) return st;
@@ -626,7 +666,11 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
     if ((st = upload(&D.S0, S0)) != PUFE_OK) return st;
   }
   PUFE_CUDA_TRY(cudaMalloc((void **)&D.psi, std::max<int64_t>(1, ctx->psi_len) * sizeof(double)));
-  PUFE_CUDA_TRY(cudaMalloc((void **)&D.psi32, std::max<int64_t>(1, ctx->psi_len) * sizeof(float)));
+  if ((st = upload(&D.qpoff, qpoff)) != PUFE_OK) return st;
+  if ((st = upload(&D.qdat, qdat)) != PUFE_OK) return st;
+  if ((st = upload(&D.toff32, toff32)) != PUFE_OK) return st;
+  if ((st = upload(&D.eorig, eorig)) != PUFE_OK) return st;
+  PUFE_CUDA_TRY(cudaMalloc((void **)&D.psi32, std::max<int64_t>(1, ctx->psi32_len) * sizeof(float)));
   PUFE_CUDA_TRY(cudaMalloc((void **)&D.err, sizeof(unsigned)));
   PUFE_CUDA_TRY(cudaMemset(D.err, 0, sizeof(unsigned)));
   }
@@ -647,8 +691,8 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
 static void free_device(pufe_ctx *ctx) {
   auto &D = ctx->d;
   void *ptrs[] = {D.qoff, D.x, D.w, D.xi, D.doff, D.dofs, D.ecol, D.aoff, D.alist,
-                  D.toff, D.psi, D.psi32, D.T0, D.S0, D.orb, D.rowptr, D.col, D.soff,
-                  D.smap, D.order, D.err};
+                  D.toff, D.psi, D.psi32, D.qpoff, D.qdat, D.toff32, D.eorig, D.T0, D.S0,
+                  D.orb, D.orbf, D.rowptr, D.col, D.soff, D.smap, D.order, D.err};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   D = DeviceArrays();
