@@ -16,16 +16,15 @@
 // pairs and T, S only for the pairs that involve an enrichment column.
 #include <math.h>
 
+#include <algorithm>
+
 #include "pufe_internal.h"
 
 namespace pufe {
 
 namespace {
 
-constexpr int TC_NT = 256;          // 8 warps: all fill, warp 0 issues, all drain
 constexpr int NTILES = 10;          // Y0,Y1,Y2,Z,ZV x (hi, lo)
-constexpr int STAGE_BYTES = 81920;  // 10 tiles x (R x KC) fp32 with R x KC = 2048
-constexpr int NSTAGE = 2;
 constexpr uint64_t WAIT_NS = 2000000000ull;  // bounded waits: 2 s
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -249,42 +248,98 @@ __global__ void k_tabulate_f32(const int64_t *__restrict__ qpoff, const float4 *
 }
 
 // ---------------------------------------------------------------------------
-// Tensor-core element contraction.
+// Tensor-core element contraction: persistent, warp-specialized.
+//
 // Operand tiles: row c of a tile = basis column c of the element, K = the
-// chunk's quadrature points; 10 tiles per stage:
+// chunk's 8 quadrature points; 10 tiles per stage:
 //   0/1 Y0 hi/lo, 2/3 Y1, 4/5 Y2 (Y_d = sqrt(w/2) dphi/dx_d), 6/7 Z (sqrt(w) phi),
 //   8/9 ZV (V sqrt(w) phi).
-// Per 8-point K-step and M-tile:  H += ZV^T Z (all columns),
+// Per chunk and M-tile:  H += ZV^T Z (all columns),
 //   H[:, 64:] += sum_d Y_d^T Y_d[64:],  S[:, 64:] += Z^T Z[64:].
-// Inputs of each chunk (the FP32 Psi table block and the point data) are
-// brought into shared memory one chunk ahead by the TMA engine (1D bulk
-// copies completing on an mbarrier), so the fill reads shared memory only.
+//
+// Roles (one CTA per SM, elements taken round-robin from the work list):
+//   warps 0-7  fill: per chunk, wait for a free operand stage and the chunk's
+//              inputs (brought into shared memory one chunk ahead by 1D TMA
+//              bulk copies), build the 10 tiles, signal "stage full";
+//   warp 8     MMA: one lane issues tcgen05.mma per full stage and commits
+//              to "stage empty"; at the end of an element, to "acc full";
+//   warps 9-12 epilogue: drain TMEM (each warp owns one 32-lane quarter),
+//              transpose 32x16 blocks through shared memory so that each
+//              half-warp scatters along one CSR row, add into FP64 CSR
+//              values, then signal "acc empty".
+// All waits are bounded (2 s); a timeout sets the device error flag and every
+// role leaves its loop.
 // ---------------------------------------------------------------------------
-struct TcShared {
-  uint64_t sbar[NSTAGE];  // operand stage free (MMA commit)
-  uint64_t ibar[NSTAGE];  // chunk inputs arrived (bulk copy)
+constexpr int WS_MMA_WARP = 8;
+constexpr int WS_EPI_WARP0 = 9;       // warps 9-12
+constexpr int WS_NT = 13 * 32;
+constexpr int WS_KC = 8;              // quadrature points per chunk (one K-step)
+constexpr int WS_NIN = 6;             // input buffers (loads run NIN-1 chunks ahead)
+
+struct WsShared {
+  uint64_t sfull[4], sempty[4], ibar[WS_NIN], afull, aempty;
   uint32_t tmem;
-  int pad;
-  float L[16][3][4];   // per chunk point: 1D Lagrange values
-  float dL[16][3][4];  // and slopes (times 2/h)
-  float xi[16][3];
-  float sw2[16], sw[16], v[16];
+  int abort;      // any role gave up: everyone leaves
+  int fill_go;    // written by fill thread 0 only: proceed with this chunk
+  float L[WS_KC][3][4];
+  float dL[WS_KC][3][4];
+  float xi[WS_KC][3];
+  float sw2[WS_KC], sw[WS_KC], v[WS_KC];
+  int ecs[192];   // the element's enrichment column codes
+};
+// after WsShared: the 128-row tile's FP32 staging of the accumulators
+// (128 x 193 floats), or the 256-row tile's per-warp transpose buffers
+// (4 x 32 x 17 float2)
+
+struct ElemInfo {
+  int e, Q, Qp, A, n, nenr, npad, nenr16, nch, nmt;
+  int64_t q0;
+  bool ok;
 };
 
 template <int R>
-__global__ void __launch_bounds__(TC_NT, 1) k_assemble_tc(
+__device__ __forceinline__ ElemInfo elem_info(const int32_t *order, int k, const int64_t *qoff,
+                                              const int64_t *qpoff, const int32_t *aoff,
+                                              const int64_t *doff, int amax) {
+  ElemInfo I;
+  I.e = order[k];
+  I.q0 = qoff[I.e];
+  I.Q = (int)(qoff[I.e + 1] - I.q0);
+  I.Qp = (int)(qpoff[I.e + 1] - qpoff[I.e]);
+  I.A = aoff[I.e + 1] - aoff[I.e];
+  I.n = (int)(doff[I.e + 1] - doff[I.e]);
+  I.nenr = I.n - 64;
+  I.npad = (I.n + 15) & ~15;
+  I.nenr16 = (I.nenr + 15) & ~15;
+  I.nch = I.Qp / WS_KC;
+  I.nmt = (I.n + 127) / 128;
+  I.ok = I.n <= R && I.A <= amax && I.nch > 0;
+  return I;
+}
+
+__device__ __forceinline__ void fill_bar() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+
+template <int R>
+__global__ void __launch_bounds__(WS_NT, 1) k_assemble_tc(
     const int32_t *__restrict__ order, const int64_t *__restrict__ qoff,
     const int64_t *__restrict__ qpoff, const float4 *__restrict__ qdat,
     const int64_t *__restrict__ doff, const int32_t *__restrict__ ecol,
     const int32_t *__restrict__ aoff, const int64_t *__restrict__ toff32,
     const float *__restrict__ psi, const int64_t *__restrict__ soff,
     const int32_t *__restrict__ smap, const double *__restrict__ V, float sx, float sy, float sz,
-    int nelem_list, int in_bytes, int want, double *__restrict__ H, double *__restrict__ S,
-    unsigned *err) {
-  constexpr int KC = 2048 / R;             // chunk of quadrature points (16 or 8)
-  constexpr int TILE = R * KC * 4;         // bytes per tile
-  constexpr uint32_t LBO = 128;            // next core matrix along K
-  constexpr uint32_t SBO = (KC / 4) * 128; // next 8-row group along M/N
+    int nelem_list, int amax, int in_bytes, int want, double *__restrict__ H,
+    double *__restrict__ S, unsigned *err) {
+  constexpr int KC = WS_KC;
+  constexpr int TILE = R * KC * 4;           // bytes per tile
+  constexpr int STG = NTILES * TILE;         // bytes per stage
+  constexpr int NSTG = 2;                    // operand stages
+  // 128-row tile: the epilogue copies the accumulators to shared memory,
+  // releases TMEM at once and scatters from there while the next element's
+  // MMAs run.  256-row tile: scatter straight from TMEM.
+  constexpr bool STAGED = (R == 128);
+  constexpr int SROW = 193;                  // staging row stride (floats), 1 mod 32
+  constexpr uint32_t LBO = 128;              // next core matrix along K
+  constexpr uint32_t SBO = (KC / 4) * 128;   // next 8-row group along M/N
   // Tensor-core FP32 accumulation does not round to nearest; its error grows
   // with the number of MMAs summed into one accumulator.  With the 128-row
   // tile the large hi*hi products and the small cross products go to
@@ -292,265 +347,412 @@ __global__ void __launch_bounds__(TC_NT, 1) k_assemble_tc(
   // negligible) and the two are added in FP64 by the epilogue.
   constexpr bool SPLIT = (R == 128);
   constexpr uint32_t TCOLS = 512;
-  constexpr uint32_t HX_COL = SPLIT ? 128 : 0;    // cross-term H accumulator
-  constexpr uint32_t S_COL = 256;                 // hi*hi S accumulator
-  constexpr uint32_t SX_COL = SPLIT ? 320 : 256;  // cross-term S accumulator
-  static_assert(NTILES * TILE == STAGE_BYTES, "stage size");
+  constexpr uint32_t HX_COL = SPLIT ? 128 : 0;
+  constexpr uint32_t S_COL = 256;
+  constexpr uint32_t SX_COL = SPLIT ? 320 : 256;
+  static_assert(NSTG * STG <= 163840, "stage memory");
 
   extern __shared__ __align__(16) unsigned char dsm[];
   unsigned char *stages = dsm + ((1024u - (smem_u32(dsm) & 1023u)) & 1023u);
-  unsigned char *inbuf = stages + NSTAGE * STAGE_BYTES;   // NSTAGE x in_bytes
-  TcShared &sh = *reinterpret_cast<TcShared *>(inbuf + NSTAGE * in_bytes);
+  unsigned char *inbuf = stages + NSTG * STG;
+  WsShared &sh = *reinterpret_cast<WsShared *>(inbuf + WS_NIN * in_bytes);
+  float *staging = reinterpret_cast<float *>(reinterpret_cast<unsigned char *>(&sh) + sizeof(WsShared));
+  float2(*epi)[32][17] = reinterpret_cast<float2(*)[32][17]>(staging);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  if (blockIdx.x >= (unsigned)nelem_list) return;
-  const int e = order[blockIdx.x];
-  const int64_t q0 = qoff[e];
-  const int Q = (int)(qoff[e + 1] - q0);
-  const int Qp = (int)(qpoff[e + 1] - qpoff[e]);
-  const int A = aoff[e + 1] - aoff[e];
-  const int n = (int)(doff[e + 1] - doff[e]);
-  const int nenr = n - 64;
-  const int npad = (n + 15) & ~15;
-  const int nenr16 = (nenr + 15) & ~15;
-  if (n > R || A * 4 * KC * 4 + KC * 16 > in_bytes) {
-    if (tid == 0) set_err(err, DEVERR_SHAPE);
-    return;
-  }
-  const int32_t *ec = ecol + (doff[e] - 64ll * e);
-  const float *pe = psi + 4 * toff32[e];
-  const float4 *qe = qdat + qpoff[e];
   const float s3[3] = {sx, sy, sz};
-  const int psi_off = A * 4 * KC * 4;  // bytes of the Psi block inside an input buffer
+  const int G = gridDim.x;
 
-  // zero the input buffers once (stale but finite data is harmless later)
-  for (int i = tid; i < NSTAGE * in_bytes / 16; i += TC_NT)
+  // ---- set-up ---------------------------------------------------------------
+  for (int i = tid; i < WS_NIN * in_bytes / 16; i += WS_NT)
     reinterpret_cast<float4 *>(inbuf)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (warp == 0) tmem_alloc(&sh.tmem, TCOLS);
+  if (warp == WS_MMA_WARP) tmem_alloc(&sh.tmem, TCOLS);
   if (tid == 0) {
-    for (int s = 0; s < NSTAGE; ++s) {
-      mbar_init(&sh.sbar[s], 1);
-      mbar_init(&sh.ibar[s], 1);
+    for (int i = 0; i < NSTG; ++i) {
+      mbar_init(&sh.sfull[i], 1);
+      mbar_init(&sh.sempty[i], 1);
     }
+    for (int i = 0; i < WS_NIN; ++i) mbar_init(&sh.ibar[i], 1);
+    mbar_init(&sh.afull, 1);
+    mbar_init(&sh.aempty, 4);
+    sh.abort = 0;
+    sh.fill_go = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   fence_proxy_async();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  const uint32_t tH = sh.tmem;
-  const uint32_t tHx = sh.tmem + HX_COL;
-  const uint32_t tS = sh.tmem + S_COL;
-  const uint32_t tSx = sh.tmem + SX_COL;
-  const uint32_t sbase = smem_u32(stages);
-  const uint32_t idH = idesc_tf32(128, npad);
-  const uint32_t idE = idesc_tf32(128, nenr16 > 0 ? nenr16 : 16);
+  const uint32_t tmem = sh.tmem;
 
-  const int nch = (Qp + KC - 1) / KC;       // chunks per pass
-  const int nmt = (n + 127) / 128;          // M-tile passes
-  const int NJ = nch * nmt;
-  // thread 0: bulk-load the inputs of flat chunk j into buffer j % 2
-  auto issue_load = [&](int j) {
-    const int qc = (j % nch) * KC;
-    const int npt = min(KC, Qp - qc);        // a multiple of 8
-    unsigned char *dst = inbuf + (j & 1) * in_bytes;
-    const uint32_t pbytes = (uint32_t)(A * 4 * npt * 4);
-    const uint32_t qbytes = (uint32_t)(npt * 16);
-    mbar_expect_tx(&sh.ibar[j & 1], pbytes + qbytes);
-    if (pbytes) bulk_g2s(dst, pe + (int64_t)(qc >> 3) * A * 32, pbytes, &sh.ibar[j & 1]);
-    bulk_g2s(dst + psi_off, qe + qc, qbytes, &sh.ibar[j & 1]);
-  };
-  if (tid == 0) issue_load(0);
-
-  bool ok = true;
-  for (int j = 0; j < NJ && ok; ++j) {
-    const int stg = j & 1;
-    const int mt = j / nch;
-    const int qc = (j % nch) * KC;
-    unsigned char *sp = stages + stg * STAGE_BYTES;
-    const float *ip = reinterpret_cast<const float *>(inbuf + stg * in_bytes);
-    const float4 *iq = reinterpret_cast<const float4 *>(inbuf + stg * in_bytes + psi_off);
-    // V of this chunk (plain loads, consumed after the barrier below)
-    float vload = 0.0f;
-    if (tid >= 64 && tid < 64 + KC) {
-      const int q = qc + tid - 64;
-      if (V && q < Q) vload = (float)V[q0 + q];
-    }
-    int good = 1;
-    if (tid == 0) {
-      // operand stage free: MMAs of chunk j-2 done; inputs of chunk j here
-      if (j >= 2 && !mbar_wait(&sh.sbar[stg], ((j >> 1) - 1) & 1)) good = 0;
-      if (good && !mbar_wait(&sh.ibar[stg], (j >> 1) & 1)) good = 0;
-      if (good && j + 1 < NJ) issue_load(j + 1);
-    }
-    if (!__syncthreads_and(good)) {
-      ok = false;
-      break;
-    }
-    // per-point tables of the chunk
-    if (tid < KC * 3) {
-      const int qq = tid / 3, d = tid - 3 * qq;
-      const float4 xq = iq[qq];
-      const float xv = d == 0 ? xq.x : (d == 1 ? xq.y : xq.z);
-      float L[4], dL[4];
-      lagrange3f(xv, L, dL);
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        sh.L[qq][d][c] = L[c];
-        sh.dL[qq][d][c] = dL[c] * s3[d];
-      }
-      sh.xi[qq][d] = xv;
-    } else if (tid >= 64 && tid < 64 + KC) {
-      const int qq = tid - 64;
-      const float ww = (qc + qq < Qp) ? iq[qq].w : 0.0f;
-      sh.sw2[qq] = sqrtf(0.5f * ww);
-      sh.sw[qq] = sqrtf(ww);
-      sh.v[qq] = vload;
-    }
-    __syncthreads();
-    // fill rows < npad: each warp writes whole core matrices (8 rows x 4
-    // points): lane -> (row c%8 = lane/4, point q%4 = lane%4), conflict-free
-    const int ncm = (npad / 8) * (KC / 4);
-    for (int cm = warp; cm < ncm; cm += TC_NT / 32) {
-      const int rg = cm / (KC / 4), kg = cm - rg * (KC / 4);
-      const int c = rg * 8 + (lane >> 2);
-      const int qq = kg * 4 + (lane & 3);
-      float b = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
-      if (c < 64) {
-        const int ia = c & 3, ib = (c >> 2) & 3, ic = c >> 4;
-        const float lx = sh.L[qq][0][ia], ly = sh.L[qq][1][ib], lz = sh.L[qq][2][ic];
-        b = lx * ly * lz;
-        gx = sh.dL[qq][0][ia] * ly * lz;
-        gy = lx * sh.dL[qq][1][ib] * lz;
-        gz = lx * ly * sh.dL[qq][2][ic];
-      } else if (c < n) {
-        const int code = ec[c - 64];
-        const int slot = code >> 3, lv = code & 7;
-        const float *pp = ip + (((qq >> 3) * A + slot) * 4) * 8 + (qq & 7);
-        const float p0 = pp[0], p1 = pp[8], p2 = pp[16], p3 = pp[24];
-        float hh[3], dh[3];
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-          const int bit = (lv >> d) & 1;
-          const float xv = sh.xi[qq][d];
-          hh[d] = bit ? 0.5f * (1.0f + xv) : 0.5f * (1.0f - xv);
-          dh[d] = (bit ? 0.5f : -0.5f) * s3[d];
+  if (warp < 8) {
+    // ======================= fill warps =======================
+    // load cursor (thread 0): next chunk whose inputs to fetch
+    int lk = blockIdx.x, lmt = 0, lc = 0, lt = 0;
+    ElemInfo LI{};
+    const float *lpsi = nullptr;   // cursor element's Psi table and point data
+    const float4 *lqd = nullptr;
+    auto cursor_elem = [&]() {
+      LI = elem_info<R>(order, lk, qoff, qpoff, aoff, doff, amax);
+      lpsi = psi + 4 * toff32[LI.e];
+      lqd = qdat + qpoff[LI.e];
+    };
+    if (tid == 0 && lk < nelem_list) cursor_elem();
+    auto advance_cursor = [&]() {
+      for (;;) {
+        if (lk >= nelem_list) return;
+        if (LI.ok) {
+          if (++lc < LI.nch) return;
+          lc = 0;
+          if (++lmt < LI.nmt) return;
         }
-        const float phi = hh[0] * hh[1] * hh[2];
-        b = phi * p0;
-        gx = dh[0] * hh[1] * hh[2] * p0 + phi * p1;
-        gy = hh[0] * dh[1] * hh[2] * p0 + phi * p2;
-        gz = hh[0] * hh[1] * dh[2] * p0 + phi * p3;
+        lmt = 0;
+        lc = 0;
+        lk += G;
+        if (lk >= nelem_list) return;
+        cursor_elem();
+        if (LI.ok) return;
       }
-      const float r2 = sh.sw2[qq], r1 = sh.sw[qq];
-      const float val[5] = {r2 * gx, r2 * gy, r2 * gz, r1 * b, sh.v[qq] * (r1 * b)};
-      const uint32_t off = (uint32_t)rg * SBO + (uint32_t)kg * LBO + (uint32_t)lane * 4;
-#pragma unroll
-      for (int t = 0; t < 5; ++t) {
-        const float hi = tf32_rn(val[t]);
-        const float lo = tf32_rn(val[t] - hi);
-        *reinterpret_cast<float *>(sp + (2 * t) * TILE + off) = hi;
-        *reinterpret_cast<float *>(sp + (2 * t + 1) * TILE + off) = lo;
+    };
+    auto skip_invalid = [&]() {
+      while (lk < nelem_list && !LI.ok) {
+        lk += G;
+        if (lk < nelem_list) cursor_elem();
       }
-    }
-    fence_proxy_async();
-    __syncthreads();
+    };
+    auto issue_load = [&]() {  // inputs of the cursor chunk into buffer lt % WS_NIN
+      const int b = lt % WS_NIN;
+      const int qc = lc * KC;
+      unsigned char *dst = inbuf + b * in_bytes;
+      const uint32_t pbytes = (uint32_t)(LI.A * 4 * KC * 4);
+      mbar_expect_tx(&sh.ibar[b], pbytes + KC * 16);
+      if (pbytes) bulk_g2s(dst, lpsi + (int64_t)(qc >> 3) * LI.A * 32, pbytes, &sh.ibar[b]);
+      bulk_g2s(dst + LI.A * 4 * KC * 4, lqd + qc, KC * 16, &sh.ibar[b]);
+      ++lt;
+      advance_cursor();
+    };
     if (tid == 0) {
-      tc_fence_after();
-      const uint32_t st = sbase + stg * STAGE_BYTES;
-      const uint32_t moff = (uint32_t)mt * 16u * SBO;   // M-tile: 128 rows
-      const uint32_t eoff = 8u * SBO;                   // enrichment rows start at 64
-#pragma unroll
-      for (int ks = 0; ks < KC / 8; ++ks) {
-        const uint32_t ko = (uint32_t)ks * 2u * LBO;
-        const uint32_t first = (qc == 0 && ks == 0) ? 0u : 1u;
-        auto D = [&](int t, uint32_t extra) { return sdesc(st + t * TILE + ko + extra, LBO, SBO); };
-        // H_V = ZV^T Z over all columns (hi*hi, then hi*lo + lo*hi)
-        const uint32_t fx = SPLIT ? first : 1u;
-        mma_tf32(tH, D(8, moff), D(6, 0), idH, first);
-        mma_tf32(tHx, D(8, moff), D(7, 0), idH, fx);
-        mma_tf32(tHx, D(9, moff), D(6, 0), idH, 1u);
-        if (nenr > 0) {
-          // T on the enrichment columns: sum_d Y_d^T Y_d[64:]
-#pragma unroll
-          for (int d = 0; d < 3; ++d) {
-            mma_tf32(tH + 64, D(2 * d, moff), D(2 * d, eoff), idE, 1u);
-            mma_tf32(tHx + 64, D(2 * d, moff), D(2 * d + 1, eoff), idE, 1u);
-            mma_tf32(tHx + 64, D(2 * d + 1, moff), D(2 * d, eoff), idE, 1u);
+      skip_invalid();
+      for (int i = 0; i < WS_NIN - 1 && lk < nelem_list; ++i) issue_load();
+    }
+    int t = 0;
+    bool run = true;
+    for (int k = blockIdx.x; k < nelem_list && run; k += G) {
+      const ElemInfo I = elem_info<R>(order, k, qoff, qpoff, aoff, doff, amax);
+      if (!I.ok) {
+        if (tid == 0) set_err(err, DEVERR_SHAPE);
+        continue;
+      }
+      const int32_t *ec = ecol + (doff[I.e] - 64ll * I.e);
+      for (int i = tid; i < I.nenr; i += 256) sh.ecs[i] = ec[i];
+      fill_bar();
+      const int *ecs = sh.ecs;
+      for (int mt = 0; mt < I.nmt && run; ++mt) {
+        for (int c = 0; c < I.nch; ++c, ++t) {
+          const int s = t % NSTG, b = t % WS_NIN;
+          const int qc = c * KC;
+          unsigned char *sp = stages + s * STG;
+          const float *ip = reinterpret_cast<const float *>(inbuf + b * in_bytes);
+          const float4 *iq = reinterpret_cast<const float4 *>(inbuf + b * in_bytes + I.A * 4 * KC * 4);
+          float vload = 0.0f;
+          if (tid >= 224 && tid < 224 + KC) {
+            const int q = qc + tid - 224;
+            if (V && q < I.Q) vload = (float)V[I.q0 + q];
           }
-          // S on the enrichment columns: Z^T Z[64:]
-          mma_tf32(tS, D(6, moff), D(6, eoff), idE, first);
-          mma_tf32(tSx, D(6, moff), D(7, eoff), idE, SPLIT ? first : 1u);
-          mma_tf32(tSx, D(7, moff), D(6, eoff), idE, 1u);
+          if (tid == 0) {
+            bool good = !*(volatile int *)&sh.abort;
+            if (good && t >= NSTG) good = mbar_wait(&sh.sempty[s], ((t / NSTG) - 1) & 1);
+            if (good) good = mbar_wait(&sh.ibar[b], (t / WS_NIN) & 1);
+            if (good && lk < nelem_list) issue_load();
+            if (!good) {
+              set_err(err, DEVERR_TIMEOUT);
+              atomicExch(&sh.abort, 1);
+            }
+            sh.fill_go = good ? 1 : 0;  // the only writer; read by all after the barrier
+          }
+          fill_bar();
+          if (!*(volatile int *)&sh.fill_go) {
+            run = false;
+            break;
+          }
+          if (tid < KC * 3) {
+            const int qq = tid / 3, d = tid - 3 * qq;
+            const float4 xq = iq[qq];
+            const float xv = d == 0 ? xq.x : (d == 1 ? xq.y : xq.z);
+            float L[4], dL[4];
+            lagrange3f(xv, L, dL);
+#pragma unroll
+            for (int cc = 0; cc < 4; ++cc) {
+              sh.L[qq][d][cc] = L[cc];
+              sh.dL[qq][d][cc] = dL[cc] * s3[d];
+            }
+            sh.xi[qq][d] = xv;
+          } else if (tid >= 224 && tid < 224 + KC) {
+            const int qq = tid - 224;
+            const float ww = iq[qq].w;  // zero on padding points
+            sh.sw2[qq] = sqrtf(0.5f * ww);
+            sh.sw[qq] = sqrtf(ww);
+            sh.v[qq] = vload;
+          }
+          fill_bar();
+          // rows < npad: each warp writes whole core matrices (8 rows x 4
+          // points): lane -> (row = lane/4, point = lane%4), conflict-free.
+          // A warp owns core matrices warp, warp+8, ... (at most R/32); all
+          // their inputs are read first so the latencies overlap.
+          constexpr int CMW = R / 32;
+          const int ncm = (I.npad / 8) * (KC / 4);
+          float bv[CMW], gxv[CMW], gyv[CMW], gzv[CMW];
+#pragma unroll
+          for (int u = 0; u < CMW; ++u) {
+            const int cm = warp + 8 * u;
+            const int rg = cm >> 1, kg = cm & 1;
+            const int cidx = rg * 8 + (lane >> 2);
+            const int qq = kg * 4 + (lane & 3);
+            float b = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+            if (cm < ncm) {
+              if (cidx < 64) {
+                const int ia = cidx & 3, ib = (cidx >> 2) & 3, ic = cidx >> 4;
+                const float lx = sh.L[qq][0][ia], ly = sh.L[qq][1][ib], lz = sh.L[qq][2][ic];
+                b = lx * ly * lz;
+                gx = sh.dL[qq][0][ia] * ly * lz;
+                gy = lx * sh.dL[qq][1][ib] * lz;
+                gz = lx * ly * sh.dL[qq][2][ic];
+              } else if (cidx < I.n) {
+                const int code = ecs[cidx - 64];
+                const int slot = code >> 3, lv = code & 7;
+                const float *pp = ip + (slot * 4) * 8 + qq;
+                const float p0 = pp[0], p1 = pp[8], p2 = pp[16], p3 = pp[24];
+                float hh[3], dh[3];
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                  const int bit = (lv >> d) & 1;
+                  const float xv = sh.xi[qq][d];
+                  hh[d] = bit ? 0.5f * (1.0f + xv) : 0.5f * (1.0f - xv);
+                  dh[d] = (bit ? 0.5f : -0.5f) * s3[d];
+                }
+                const float phi = hh[0] * hh[1] * hh[2];
+                b = phi * p0;
+                gx = dh[0] * hh[1] * hh[2] * p0 + phi * p1;
+                gy = hh[0] * dh[1] * hh[2] * p0 + phi * p2;
+                gz = hh[0] * hh[1] * dh[2] * p0 + phi * p3;
+              }
+            }
+            bv[u] = b;
+            gxv[u] = gx;
+            gyv[u] = gy;
+            gzv[u] = gz;
+          }
+#pragma unroll
+          for (int u = 0; u < CMW; ++u) {
+            const int cm = warp + 8 * u;
+            if (cm >= ncm) break;
+            const int rg = cm >> 1, kg = cm & 1;
+            const int qq = kg * 4 + (lane & 3);
+            const float r2 = sh.sw2[qq], r1 = sh.sw[qq];
+            const float val[5] = {r2 * gxv[u], r2 * gyv[u], r2 * gzv[u], r1 * bv[u],
+                                  sh.v[qq] * (r1 * bv[u])};
+            const uint32_t off = (uint32_t)rg * SBO + (uint32_t)kg * LBO + (uint32_t)lane * 4;
+#pragma unroll
+            for (int tt = 0; tt < 5; ++tt) {
+              const float hi = tf32_rn(val[tt]);
+              const float lo = tf32_rn(val[tt] - hi);
+              *reinterpret_cast<float *>(sp + (2 * tt) * TILE + off) = hi;
+              *reinterpret_cast<float *>(sp + (2 * tt + 1) * TILE + off) = lo;
+            }
+          }
+          fence_proxy_async();
+          fill_bar();
+          if (tid == 0) {
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&sh.sfull[s]))
+                         : "memory");
+          }
         }
       }
-      mma_commit(&sh.sbar[stg]);
     }
-    if (j % nch != nch - 1) continue;
-    // ---- end of an M-tile pass: drain the accumulators ----
-    {
-      int good2 = 1;
-      if (tid == 0) good2 = mbar_wait(&sh.sbar[stg], (j >> 1) & 1) ? 1 : 0;
-      if (!__syncthreads_and(good2)) {
-        ok = false;
-        break;
+  } else if (warp == WS_MMA_WARP) {
+    // ======================= MMA warp =======================
+    if (lane == 0) {
+      const uint32_t sbase = smem_u32(stages);
+      int t = 0, a = 0;
+      bool run = true;
+      for (int k = blockIdx.x; k < nelem_list && run; k += G) {
+        const ElemInfo I = elem_info<R>(order, k, qoff, qpoff, aoff, doff, amax);
+        if (!I.ok) continue;
+        const uint32_t idH = idesc_tf32(128, I.npad);
+        const uint32_t idE = idesc_tf32(128, I.nenr16 > 0 ? I.nenr16 : 16);
+        const uint32_t tH = tmem, tHx = tmem + HX_COL, tS = tmem + S_COL, tSx = tmem + SX_COL;
+        for (int mt = 0; mt < I.nmt && run; ++mt, ++a) {
+          if (a > 0 && !mbar_wait(&sh.aempty, (a - 1) & 1)) {
+            run = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t moff = (uint32_t)mt * 16u * SBO;
+          const uint32_t eoff = 8u * SBO;
+          for (int c = 0; c < I.nch; ++c, ++t) {
+            const int s = t % NSTG;
+            if (*(volatile int *)&sh.abort || !mbar_wait(&sh.sfull[s], (t / NSTG) & 1)) {
+              run = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t st = sbase + s * STG;
+            const uint32_t first = (c == 0) ? 0u : 1u;
+            auto D = [&](int tt, uint32_t extra) { return sdesc(st + tt * TILE + extra, LBO, SBO); };
+            const uint32_t fx = SPLIT ? first : 1u;
+            mma_tf32(tH, D(8, moff), D(6, 0), idH, first);
+            mma_tf32(tHx, D(8, moff), D(7, 0), idH, fx);
+            mma_tf32(tHx, D(9, moff), D(6, 0), idH, 1u);
+            if (I.nenr > 0) {
+#pragma unroll
+              for (int d = 0; d < 3; ++d) {
+                mma_tf32(tH + 64, D(2 * d, moff), D(2 * d, eoff), idE, 1u);
+                mma_tf32(tHx + 64, D(2 * d, moff), D(2 * d + 1, eoff), idE, 1u);
+                mma_tf32(tHx + 64, D(2 * d + 1, moff), D(2 * d, eoff), idE, 1u);
+              }
+              mma_tf32(tS, D(6, moff), D(6, eoff), idE, first);
+              mma_tf32(tSx, D(6, moff), D(7, eoff), idE, SPLIT ? first : 1u);
+              mma_tf32(tSx, D(7, moff), D(6, eoff), idE, 1u);
+            }
+            mma_commit(&sh.sempty[s]);
+          }
+          if (!run) break;
+          mma_commit(&sh.afull);
+        }
+      }
+      if (!run) {
+        set_err(err, DEVERR_TIMEOUT);
+        atomicExch(&sh.abort, 1);
       }
     }
-    tc_fence_after();
-    // epilogue: warp w reads TMEM lanes 32*(w%4).. (rows), column blocks
-    // of 16 alternate between warps w and w+4
-    const int quarter = warp & 3, half = warp >> 2;
-    const int r = mt * 128 + quarter * 32 + lane;
+    __syncwarp();
+  } else {
+    // ======================= epilogue warps =======================
+    const int quarter = warp & 3;
+    const int ew = warp - WS_EPI_WARP0;
     const uint32_t lanebase = (uint32_t)(quarter * 32) << 16;
-    const int32_t *m = smap + soff[e];
-    for (int cb = half; cb * 16 < npad; cb += 2) {
-      float hv[16], sv[16], hx[16], sx2[16];
-      tmem_ld16(tH + lanebase + cb * 16, hv);
-      if (SPLIT) tmem_ld16(tHx + lanebase + cb * 16, hx);
-      const bool enr_blk = cb * 16 >= 64;
-      if (enr_blk && nenr > 0) {
-        tmem_ld16(tS + lanebase + (cb * 16 - 64), sv);
-        if (SPLIT) tmem_ld16(tSx + lanebase + (cb * 16 - 64), sx2);
-      }
-      if (r < n) {
+    float2(*stg)[17] = epi[ew];
+    int a = 0;
+    bool run = true;
+    // Scatter one 32-row x 16-column block of owned pairs (r, c) into both
+    // CSR slots, in two passes that each keep a warp's slots together:
+    // direct slots (r, c): half-warp h takes row 2*it + h, lanes run along 16
+    // consecutive columns; mirror slots (c, r): lane = row, loop over the 16
+    // columns.  All slot loads of a pass are issued before its atomics.
+    auto owned = [&](int r, int cc, int n, bool is_s) {
+      bool ok = r < n && cc < n;
+      if (ok) ok = (cc < 64) ? (cc <= r && r < 64) : (r < 64 || cc <= r);
+      if (ok && is_s) ok = cc >= 64;
+      return ok;
+    };
+    auto scatter_block = [&](const int32_t *m, int n, int rbase, int cb, bool is_s, double *out,
+                             auto value_of) {
+      int sd[16];
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          const int c = cb * 16 + i;
-          if (c >= n) break;
-          const bool own = (c < 64) ? (c <= r && r < 64) : (r < 64 || c <= r);
-          if (!own) continue;
-          const int32_t sij = m[(int64_t)r * n + c];
-          const int32_t sji = m[(int64_t)c * n + r];
-          if (want & PUFE_WANT_H) {
-            const double hval = SPLIT ? (double)hv[i] + (double)hx[i] : (double)hv[i];
-            atomicAdd(H + sij, hval);
-            if (c != r) atomicAdd(H + sji, hval);
+      for (int it = 0; it < 16; ++it) {
+        const int rl = 2 * it + (lane >> 4);
+        const int r = rbase + rl, cc = cb * 16 + (lane & 15);
+        sd[it] = owned(r, cc, n, is_s) ? m[(int64_t)r * n + cc] : -1;
+      }
+#pragma unroll
+      for (int it = 0; it < 16; ++it)
+        if (sd[it] >= 0) atomicAdd(out + sd[it], value_of(2 * it + (lane >> 4), lane & 15));
+      const int r = rbase + lane;
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int cc = cb * 16 + i;
+        sd[i] = (cc != r && owned(r, cc, n, is_s)) ? m[(int64_t)cc * n + r] : -1;
+      }
+#pragma unroll
+      for (int i = 0; i < 16; ++i)
+        if (sd[i] >= 0) atomicAdd(out + sd[i], value_of(lane, i));
+    };
+    for (int k = blockIdx.x; k < nelem_list && run; k += G) {
+      const ElemInfo I = elem_info<R>(order, k, qoff, qpoff, aoff, doff, amax);
+      if (!I.ok) continue;
+      const int32_t *m = smap + soff[I.e];
+      const int n = I.n;
+      for (int mt = 0; mt < I.nmt; ++mt, ++a) {
+        int good = 1;
+        if (lane == 0) good = (!*(volatile int *)&sh.abort && mbar_wait(&sh.afull, a & 1)) ? 1 : 0;
+        good = __shfl_sync(0xffffffffu, good, 0);
+        if (!good) {
+          run = false;
+          break;
+        }
+        tc_fence_after();
+        const int rbase = mt * 128 + quarter * 32;
+        if constexpr (STAGED) {
+          // drain this warp's 32 rows: H columns [0, npad), then S columns
+          float *row = staging + (quarter * 32 + lane) * SROW;
+          for (int cb = 0; cb * 16 < I.npad; ++cb) {
+            float hv[16], hx[16];
+            tmem_ld16(tmem + lanebase + cb * 16, hv);
+            tmem_ld16(tmem + HX_COL + lanebase + cb * 16, hx);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) row[cb * 16 + i] = hv[i] + hx[i];
           }
-          if (enr_blk && (want & PUFE_WANT_S)) {
-            const double sval = SPLIT ? (double)sv[i] + (double)sx2[i] : (double)sv[i];
-            atomicAdd(S + sij, sval);
-            if (c != r) atomicAdd(S + sji, sval);
+          for (int cb = 0; cb * 16 < I.nenr16; ++cb) {
+            float hv[16], hx[16];
+            tmem_ld16(tmem + S_COL + lanebase + cb * 16, hv);
+            tmem_ld16(tmem + SX_COL + lanebase + cb * 16, hx);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) row[I.npad + cb * 16 + i] = hv[i] + hx[i];
           }
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0)
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&sh.aempty))
+                         : "memory");
+          // scatter from shared memory while the next element's MMAs run
+          const float *blk = staging + (quarter * 32) * SROW;
+          for (int cb = 0; cb * 16 < I.npad; ++cb) {
+            if (want & PUFE_WANT_H)
+              scatter_block(m, n, rbase, cb, false, H, [&](int rl, int cl) {
+                return (double)blk[rl * SROW + cb * 16 + cl];
+              });
+            if ((want & PUFE_WANT_S) && cb * 16 >= 64 && I.nenr > 0)
+              scatter_block(m, n, rbase, cb, true, S, [&](int rl, int cl) {
+                return (double)blk[rl * SROW + I.npad + cb * 16 - 64 + cl];
+              });
+          }
+          __syncwarp();
+        } else {
+          for (int cb = 0; cb * 16 < I.npad; ++cb) {
+            const bool enr_blk = cb * 16 >= 64;
+            for (int which = 0; which < ((enr_blk && I.nenr > 0) ? 2 : 1); ++which) {
+              if (which == 1 && !(want & PUFE_WANT_S)) continue;
+              if (which == 0 && !(want & PUFE_WANT_H)) continue;
+              float hv[16], hx[16];
+              const uint32_t c0 = which == 0 ? (uint32_t)(cb * 16) : (uint32_t)(cb * 16 - 64);
+              tmem_ld16((which == 0 ? tmem : tmem + S_COL) + lanebase + c0, hv);
+              if (SPLIT) tmem_ld16((which == 0 ? tmem + HX_COL : tmem + SX_COL) + lanebase + c0, hx);
+#pragma unroll
+              for (int i = 0; i < 16; ++i) stg[lane][i] = make_float2(hv[i], SPLIT ? hx[i] : 0.0f);
+              __syncwarp();
+              scatter_block(m, n, rbase, cb, which == 1, which == 0 ? H : S, [&](int rl, int cl) {
+                const float2 v2 = stg[rl][cl];
+                return (double)v2.x + (double)v2.y;
+              });
+              __syncwarp();
+            }
+          }
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0)
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&sh.aempty))
+                         : "memory");
         }
       }
     }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
   }
-  if (!ok && tid == 0) {
-    set_err(err, DEVERR_TIMEOUT);
-    // give copies and MMAs still in flight one more bounded wait
-    for (int s = 0; s < NSTAGE; ++s) {
-      mbar_wait(&sh.sbar[s], 0);
-      mbar_wait(&sh.ibar[s], 0);
-    }
-  }
+
+  // ---- teardown -------------------------------------------------------------
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) {
+  if (warp == WS_MMA_WARP) {
     tc_fence_after();
-    tmem_dealloc(sh.tmem, TCOLS);
+    tmem_dealloc(tmem, TCOLS);
   }
 }
 
@@ -764,34 +966,40 @@ pufe_status launch_assemble_tc(pufe_ctx *ctx, const double *V, int what, double 
   if (what & PUFE_WANT_S) PUFE_CUDA_TRY(cudaMemcpyAsync(S, D.S0, bytes, cudaMemcpyDeviceToDevice, st));
   const float sx = (float)(2.0 / ctx->h[0]), sy = (float)(2.0 / ctx->h[1]),
               sz = (float)(2.0 / ctx->h[2]);
-  auto smem_for = [&](int KC, int &in_bytes) {
-    in_bytes = ((ctx->max_alpha * 4 * KC * 4 + KC * 16) + 127) & ~127;
-    return (size_t)1024 + NSTAGE * STAGE_BYTES + NSTAGE * in_bytes + sizeof(TcShared);
-  };
+  const int amax = std::max(1, ctx->max_alpha);
+  const int inb = ((amax * 4 * WS_KC * 4 + WS_KC * 16) + 127) & ~127;
+  // 128-row tile: 2 stages of 40 KB + 128 x 193 FP32 staging; 256-row: 2 x 80 KB
+  // + per-warp transpose buffers
+  const size_t sm128 = (size_t)1024 + 2 * 40960 + WS_NIN * (size_t)inb + sizeof(WsShared) +
+                       (size_t)128 * 193 * 4;
+  const size_t sm256 = (size_t)1024 + 2 * 81920 + WS_NIN * (size_t)inb + sizeof(WsShared) +
+                       (size_t)4 * 32 * 17 * 8;
+  int nsm = 0;
+  PUFE_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device));
   // elements are ordered with n_e > 128 first (256-row tile), then the rest
   const int nbig = ctx->n_big;
   if (nbig > 0) {
-    int inb = 0;
-    const size_t sm = smem_for(8, inb);
+    const size_t sm = sm256;
     if (sm > 227 * 1024) return fail(PUFE_EINVAL, "too many enrichments per element for TF32X3");
     PUFE_CUDA_TRY(cudaFuncSetAttribute(k_assemble_tc<256>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    k_assemble_tc<256><<<nbig, TC_NT, sm, st>>>(D.order, D.qoff, D.qpoff, D.qdat, D.doff, D.ecol,
+    const int grid = std::min(nbig, nsm);
+    k_assemble_tc<256><<<grid, WS_NT, sm, st>>>(D.order, D.qoff, D.qpoff, D.qdat, D.doff, D.ecol,
                                                 D.aoff, D.toff32, D.psi32, D.soff, D.smap, V, sx,
-                                                sy, sz, nbig, inb, what, H, S, D.err);
+                                                sy, sz, nbig, amax, inb, what, H, S, D.err);
     PUFE_CUDA_TRY(cudaGetLastError());
   }
   const int nsmall = (int)ctx->nelem - nbig;
   if (nsmall > 0) {
-    int inb = 0;
-    const size_t sm = smem_for(16, inb);
+    const size_t sm = sm128;
     if (sm > 227 * 1024) return fail(PUFE_EINVAL, "too many enrichments per element for TF32X3");
     PUFE_CUDA_TRY(cudaFuncSetAttribute(k_assemble_tc<128>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    k_assemble_tc<128><<<nsmall, TC_NT, sm, st>>>(D.order + nbig, D.qoff, D.qpoff, D.qdat,
-                                                  D.doff, D.ecol, D.aoff, D.toff32, D.psi32,
-                                                  D.soff, D.smap, V, sx, sy, sz, nsmall, inb,
-                                                  what, H, S, D.err);
+    const int grid = std::min(nsmall, nsm);
+    k_assemble_tc<128><<<grid, WS_NT, sm, st>>>(D.order + nbig, D.qoff, D.qpoff, D.qdat, D.doff,
+                                                D.ecol, D.aoff, D.toff32, D.psi32, D.soff,
+                                                D.smap, V, sx, sy, sz, nsmall, amax, inb, what, H,
+                                                S, D.err);
     PUFE_CUDA_TRY(cudaGetLastError());
   }
   return PUFE_OK;
