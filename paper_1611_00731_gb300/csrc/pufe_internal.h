@@ -70,6 +70,9 @@ struct DeviceArrays {
   // FP32 (mixed-precision) path: element points padded to a multiple of 8
   int64_t *qpoff = nullptr;   // nelem + 1: offsets into qdat (padded points)
   float4 *qdat = nullptr;     // per padded point: (xi_x, xi_y, xi_z, w); w = 0 on padding
+  float *ptab = nullptr;      // per padded point, 32 floats: L[3][4], dL[3][4] (x 2/h),
+                              // xi[3], sqrt(w/2), sqrt(w), 3 unused; zeros on padding
+  float *vpad = nullptr;      // per padded point: FP32 copy of V (filled per call)
   int64_t *toff32 = nullptr;  // nelem + 1: offsets into psi32 (units of padded q*alpha)
   float *psi32 = nullptr;     // per element [q/8][slot][comp][q%8]: 32-float blocks
   float *eorig = nullptr;     // per (element, slot): displacement of the element

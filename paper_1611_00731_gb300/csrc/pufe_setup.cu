@@ -454,6 +454,7 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
     toff32[e + 1] = toff32[e] + qp * (int64_t)ealpha[e].size();
   }
   std::vector<float4> qdat(qpoff[nelem]);
+  std::vector<float> ptab(32 * qpoff[nelem], 0.0f);
   std::vector<float> eorig(8 * aoff[nelem], 0.0f);
   std::vector<int32_t> dofs(doff[nelem]), ecol(doff[nelem] - 64 * nelem), alist(aoff[nelem]);
   int64_t ecpos = 0;
@@ -485,6 +486,18 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
       if (q < q_e[e]) {
         const int64_t g = qoff[e] + q;
         v = make_float4((float)XI[3 * g], (float)XI[3 * g + 1], (float)XI[3 * g + 2], (float)Wt[g]);
+        float *pt = &ptab[32 * (qpoff[e] + q)];
+        for (int d = 0; d < 3; ++d) {
+          double L[4], dL[4];
+          lagrange3(XI[3 * g + d], L, dL);
+          for (int c = 0; c < 4; ++c) {
+            pt[4 * d + c] = (float)L[c];
+            pt[12 + 4 * d + c] = (float)(dL[c] * 2.0 / S.h[d]);
+          }
+          pt[24 + d] = (float)XI[3 * g + d];
+        }
+        pt[27] = (float)std::sqrt(0.5 * Wt[g]);
+        pt[28] = (float)std::sqrt(Wt[g]);
       }
       qdat[qpoff[e] + q] = v;
     }
@@ -542,7 +555,9 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
     }
   });
 
-  // ---- work order: elements with n_e > 128 first, then by cost ---------------
+  // ---- work order: elements with n_e > 128 first (they take the 256-row
+  // tile), then by decreasing cost n_e^2 Q_e (largest first balances the
+  // per-element launches and the persistent round-robin schedule) -----------
   std::vector<int32_t> order(nelem);
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
@@ -668,6 +683,8 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
   PUFE_CUDA_TRY(cudaMalloc((void **)&D.psi, std::max<int64_t>(1, ctx->psi_len) * sizeof(double)));
   if ((st = upload(&D.qpoff, qpoff)) != PUFE_OK) return st;
   if ((st = upload(&D.qdat, qdat)) != PUFE_OK) return st;
+  if ((st = upload(&D.ptab, ptab)) != PUFE_OK) return st;
+  PUFE_CUDA_TRY(cudaMalloc((void **)&D.vpad, std::max<int64_t>(1, qpoff[nelem]) * sizeof(float)));
   if ((st = upload(&D.toff32, toff32)) != PUFE_OK) return st;
   if ((st = upload(&D.eorig, eorig)) != PUFE_OK) return st;
   PUFE_CUDA_TRY(cudaMalloc((void **)&D.psi32, std::max<int64_t>(1, ctx->psi32_len) * sizeof(float)));
@@ -691,7 +708,8 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
 static void free_device(pufe_ctx *ctx) {
   auto &D = ctx->d;
   void *ptrs[] = {D.qoff, D.x, D.w, D.xi, D.doff, D.dofs, D.ecol, D.aoff, D.alist,
-                  D.toff, D.psi, D.psi32, D.qpoff, D.qdat, D.toff32, D.eorig, D.T0, D.S0,
+                  D.toff, D.psi, D.psi32, D.qpoff, D.qdat, D.ptab, D.vpad, D.toff32, D.eorig,
+                  D.T0, D.S0,
                   D.orb, D.orbf, D.rowptr, D.col, D.soff, D.smap, D.order, D.err};
   for (void *p : ptrs)
     if (p) cudaFree(p);

@@ -291,6 +291,18 @@ struct WsShared {
 // (128 x 193 floats), or the 256-row tile's per-warp transpose buffers
 // (4 x 32 x 17 float2)
 
+// FP32 copy of V on the padded point layout (zeros on padding points), so
+// that the assembly's bulk copies can bring it in with the other inputs.
+__global__ void k_pack_v(const int64_t *__restrict__ qoff, const int64_t *__restrict__ qpoff,
+                         const double *__restrict__ V, float *__restrict__ vpad) {
+  const int64_t e = blockIdx.x;
+  const int64_t q0 = qoff[e];
+  const int Q = (int)(qoff[e + 1] - q0);
+  const int Qp = (int)(qpoff[e + 1] - qpoff[e]);
+  for (int q = threadIdx.x; q < Qp; q += blockDim.x)
+    vpad[qpoff[e] + q] = (q < Q && V) ? (float)V[q0 + q] : 0.0f;
+}
+
 struct ElemInfo {
   int e, Q, Qp, A, n, nenr, npad, nenr16, nch, nmt;
   int64_t q0;
@@ -322,7 +334,8 @@ __device__ __forceinline__ void fill_bar() { asm volatile("bar.sync 1, 256;" :::
 template <int R>
 __global__ void __launch_bounds__(WS_NT, 1) k_assemble_tc(
     const int32_t *__restrict__ order, const int64_t *__restrict__ qoff,
-    const int64_t *__restrict__ qpoff, const float4 *__restrict__ qdat,
+    const int64_t *__restrict__ qpoff, const float *__restrict__ ptab,
+    const float *__restrict__ vpad,
     const int64_t *__restrict__ doff, const int32_t *__restrict__ ecol,
     const int32_t *__restrict__ aoff, const int64_t *__restrict__ toff32,
     const float *__restrict__ psi, const int64_t *__restrict__ soff,
@@ -390,12 +403,13 @@ __global__ void __launch_bounds__(WS_NT, 1) k_assemble_tc(
     // load cursor (thread 0): next chunk whose inputs to fetch
     int lk = blockIdx.x, lmt = 0, lc = 0, lt = 0;
     ElemInfo LI{};
-    const float *lpsi = nullptr;   // cursor element's Psi table and point data
-    const float4 *lqd = nullptr;
+    const float *lpsi = nullptr;   // cursor element's Psi table, point table and V
+    const float *lpt = nullptr, *lv = nullptr;
     auto cursor_elem = [&]() {
       LI = elem_info<R>(order, lk, qoff, qpoff, aoff, doff, amax);
       lpsi = psi + 4 * toff32[LI.e];
-      lqd = qdat + qpoff[LI.e];
+      lpt = ptab + 32 * qpoff[LI.e];
+      lv = vpad + qpoff[LI.e];
     };
     if (tid == 0 && lk < nelem_list) cursor_elem();
     auto advance_cursor = [&]() {
@@ -425,9 +439,10 @@ __global__ void __launch_bounds__(WS_NT, 1) k_assemble_tc(
       const int qc = lc * KC;
       unsigned char *dst = inbuf + b * in_bytes;
       const uint32_t pbytes = (uint32_t)(LI.A * 4 * KC * 4);
-      mbar_expect_tx(&sh.ibar[b], pbytes + KC * 16);
+      mbar_expect_tx(&sh.ibar[b], pbytes + KC * 128 + KC * 4);
       if (pbytes) bulk_g2s(dst, lpsi + (int64_t)(qc >> 3) * LI.A * 32, pbytes, &sh.ibar[b]);
-      bulk_g2s(dst + LI.A * 4 * KC * 4, lqd + qc, KC * 16, &sh.ibar[b]);
+      bulk_g2s(dst + pbytes, lpt + 32 * qc, KC * 128, &sh.ibar[b]);
+      bulk_g2s(dst + pbytes + KC * 128, lv + qc, KC * 4, &sh.ibar[b]);
       ++lt;
       advance_cursor();
     };
@@ -453,12 +468,8 @@ __global__ void __launch_bounds__(WS_NT, 1) k_assemble_tc(
           const int qc = c * KC;
           unsigned char *sp = stages + s * STG;
           const float *ip = reinterpret_cast<const float *>(inbuf + b * in_bytes);
-          const float4 *iq = reinterpret_cast<const float4 *>(inbuf + b * in_bytes + I.A * 4 * KC * 4);
-          float vload = 0.0f;
-          if (tid >= 224 && tid < 224 + KC) {
-            const int q = qc + tid - 224;
-            if (V && q < I.Q) vload = (float)V[I.q0 + q];
-          }
+          const float *pt = ip + I.A * 4 * KC;   // per point: 32 floats
+          const float *vq = pt + 32 * KC;        // per point: V
           if (tid == 0) {
             bool good = !*(volatile int *)&sh.abort;
             if (good && t >= NSTG) good = mbar_wait(&sh.sempty[s], ((t / NSTG) - 1) & 1);
@@ -475,26 +486,6 @@ __global__ void __launch_bounds__(WS_NT, 1) k_assemble_tc(
             run = false;
             break;
           }
-          if (tid < KC * 3) {
-            const int qq = tid / 3, d = tid - 3 * qq;
-            const float4 xq = iq[qq];
-            const float xv = d == 0 ? xq.x : (d == 1 ? xq.y : xq.z);
-            float L[4], dL[4];
-            lagrange3f(xv, L, dL);
-#pragma unroll
-            for (int cc = 0; cc < 4; ++cc) {
-              sh.L[qq][d][cc] = L[cc];
-              sh.dL[qq][d][cc] = dL[cc] * s3[d];
-            }
-            sh.xi[qq][d] = xv;
-          } else if (tid >= 224 && tid < 224 + KC) {
-            const int qq = tid - 224;
-            const float ww = iq[qq].w;  // zero on padding points
-            sh.sw2[qq] = sqrtf(0.5f * ww);
-            sh.sw[qq] = sqrtf(ww);
-            sh.v[qq] = vload;
-          }
-          fill_bar();
           // rows < npad: each warp writes whole core matrices (8 rows x 4
           // points): lane -> (row = lane/4, point = lane%4), conflict-free.
           // A warp owns core matrices warp, warp+8, ... (at most R/32); all
@@ -510,13 +501,14 @@ __global__ void __launch_bounds__(WS_NT, 1) k_assemble_tc(
             const int qq = kg * 4 + (lane & 3);
             float b = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
             if (cm < ncm) {
+              const float *pq = pt + 32 * qq;
               if (cidx < 64) {
                 const int ia = cidx & 3, ib = (cidx >> 2) & 3, ic = cidx >> 4;
-                const float lx = sh.L[qq][0][ia], ly = sh.L[qq][1][ib], lz = sh.L[qq][2][ic];
+                const float lx = pq[ia], ly = pq[4 + ib], lz = pq[8 + ic];
                 b = lx * ly * lz;
-                gx = sh.dL[qq][0][ia] * ly * lz;
-                gy = lx * sh.dL[qq][1][ib] * lz;
-                gz = lx * ly * sh.dL[qq][2][ic];
+                gx = pq[12 + ia] * ly * lz;
+                gy = lx * pq[16 + ib] * lz;
+                gz = lx * ly * pq[20 + ic];
               } else if (cidx < I.n) {
                 const int code = ecs[cidx - 64];
                 const int slot = code >> 3, lv = code & 7;
@@ -526,7 +518,7 @@ __global__ void __launch_bounds__(WS_NT, 1) k_assemble_tc(
 #pragma unroll
                 for (int d = 0; d < 3; ++d) {
                   const int bit = (lv >> d) & 1;
-                  const float xv = sh.xi[qq][d];
+                  const float xv = pq[24 + d];
                   hh[d] = bit ? 0.5f * (1.0f + xv) : 0.5f * (1.0f - xv);
                   dh[d] = (bit ? 0.5f : -0.5f) * s3[d];
                 }
@@ -548,9 +540,9 @@ __global__ void __launch_bounds__(WS_NT, 1) k_assemble_tc(
             if (cm >= ncm) break;
             const int rg = cm >> 1, kg = cm & 1;
             const int qq = kg * 4 + (lane & 3);
-            const float r2 = sh.sw2[qq], r1 = sh.sw[qq];
+            const float r2 = pt[32 * qq + 27], r1 = pt[32 * qq + 28];
             const float val[5] = {r2 * gxv[u], r2 * gyv[u], r2 * gzv[u], r1 * bv[u],
-                                  sh.v[qq] * (r1 * bv[u])};
+                                  vq[qq] * (r1 * bv[u])};
             const uint32_t off = (uint32_t)rg * SBO + (uint32_t)kg * LBO + (uint32_t)lane * 4;
 #pragma unroll
             for (int tt = 0; tt < 5; ++tt) {
@@ -937,6 +929,243 @@ __global__ void __launch_bounds__(ADJ_NT) k_adjoint_f32(
   }
 }
 
+// ---------------------------------------------------------------------------
+// K5 on the tensor cores (elements with n_e <= 128).
+//   z_q = sqrt(w_q) b_q,  D[q][i] = sum_j z_qj Hbar_ij  (M = 128 points,
+//   N = n_e rounded to 16, K = basis index j), then
+//   Vbar_q = w_q b_q^T Hbar_e b_q = sum_i D[q][i] z_qi,
+// one thread per point reading its TMEM lane.  Hbar_e is gathered once per
+// element into shared memory (two TF32 terms); z is built chunk by chunk
+// (32 basis indices) into double-buffered stages; products hi*hi and the
+// cross terms go to separate TMEM accumulators.
+// ---------------------------------------------------------------------------
+constexpr int AT_NT = 512;
+constexpr int AT_KJ = 32;   // basis indices per z chunk
+
+struct AtShared {
+  uint64_t sempty[2], dbar;
+  uint32_t tmem;
+  int good;
+  float L[128][3][4];
+  float xi[128][3];
+  float sw[128];
+  float acc[128];
+  int ecs[64];
+};
+
+__global__ void __launch_bounds__(AT_NT, 1) k_adjoint_tc(
+    const int32_t *__restrict__ order, const int64_t *__restrict__ qoff,
+    const int64_t *__restrict__ qpoff, const float4 *__restrict__ qdat,
+    const int64_t *__restrict__ doff, const int32_t *__restrict__ ecol,
+    const int32_t *__restrict__ aoff, const int64_t *__restrict__ toff32,
+    const float *__restrict__ psi, const int64_t *__restrict__ soff,
+    const int32_t *__restrict__ smap, const double *__restrict__ Hbar, int npad_max,
+    double *__restrict__ Vbar, unsigned *err) {
+  constexpr uint32_t LBO = 128;
+  constexpr uint32_t SBO_Z = (AT_KJ / 4) * 128;   // z tile: 128 rows x 32
+  constexpr int ZTILE = 128 * AT_KJ * 4;          // bytes per z tile (hi or lo)
+  extern __shared__ __align__(16) unsigned char dsm[];
+  unsigned char *base = dsm + ((1024u - (smem_u32(dsm) & 1023u)) & 1023u);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int e = order[blockIdx.x];
+  const int64_t q0 = qoff[e];
+  const int Q = (int)(qoff[e + 1] - q0);
+  const int A = aoff[e + 1] - aoff[e];
+  const int n = (int)(doff[e + 1] - doff[e]);
+  const int npad = (n + 15) & ~15;
+  if (n > 128 || npad > npad_max) {
+    if (tid == 0) set_err(err, DEVERR_SHAPE);
+    return;
+  }
+  const uint32_t SBO_H = (uint32_t)(npad / 4) * 128;   // Hbar tile: npad rows x npad
+  const int HT = npad * npad * 4;                       // bytes per Hbar tile
+  unsigned char *hH = base, *hL = base + HT;
+  unsigned char *zst = base + 2 * HT;                   // 2 stages x (hi, lo)
+  AtShared &sh = *reinterpret_cast<AtShared *>(zst + 4 * ZTILE);
+  const int32_t *ec = ecol + (doff[e] - 64ll * e);
+  const float *pe = psi + 4 * toff32[e];
+  const float4 *qe = qdat + qpoff[e];
+  const int32_t *m = smap + soff[e];
+
+  if (warp == 0) tmem_alloc(&sh.tmem, 256);
+  if (tid == 0) {
+    mbar_init(&sh.sempty[0], 1);
+    mbar_init(&sh.sempty[1], 1);
+    mbar_init(&sh.dbar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (tid < n - 64) sh.ecs[tid] = ec[tid];
+  // ---- gather Hbar_e (rows i, K = j) into the two TF32 tiles ----------------
+  {
+    const int ncm = (npad / 8) * (npad / 4);
+    for (int c0 = warp; c0 < ncm; c0 += 4 * (AT_NT / 32)) {
+      int sl[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int cm = c0 + u * (AT_NT / 32);
+        const int rg = cm / (npad / 4), kg = cm - rg * (npad / 4);
+        const int i = rg * 8 + (lane >> 2), j = kg * 4 + (lane & 3);
+        sl[u] = (cm < ncm && i < n && j < n) ? m[i * n + j] : -1;
+      }
+      float hv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) hv[u] = sl[u] >= 0 ? (float)Hbar[sl[u]] : 0.0f;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int cm = c0 + u * (AT_NT / 32);
+        if (cm >= ncm) break;
+        const int rg = cm / (npad / 4), kg = cm - rg * (npad / 4);
+        const uint32_t off = (uint32_t)rg * SBO_H + (uint32_t)kg * LBO + (uint32_t)lane * 4;
+        const float hi = tf32_rn(hv[u]);
+        *reinterpret_cast<float *>(hH + off) = hi;
+        *reinterpret_cast<float *>(hL + off) = tf32_rn(hv[u] - hi);
+      }
+    }
+  }
+  fence_proxy_async();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tD = sh.tmem, tX = sh.tmem + 128;
+  const uint32_t idD = idesc_tf32(128, npad);
+  const uint32_t hbase = smem_u32(hH), lbase = smem_u32(hL), zbase = smem_u32(zst);
+  const int nkc = (npad + AT_KJ - 1) / AT_KJ;
+  int g = 0;          // chunk counter (stage phases)
+  int dcount = 0;     // M-tile counter (dbar phases)
+  bool ok = true;
+  for (int mt = 0; mt * 128 < Q && ok; ++mt) {
+    // per-point tables of this M-tile
+    if (tid < 128) {
+      const int qg = mt * 128 + tid;
+      const float4 x4 = (qg < Q) ? qe[qg] : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float xv[3] = {x4.x, x4.y, x4.z};
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        float L[4], dL[4];
+        lagrange3f(xv[d], L, dL);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) sh.L[tid][d][c] = L[c];
+        sh.xi[tid][d] = xv[d];
+      }
+      sh.sw[tid] = sqrtf(x4.w);   // zero on padding and beyond Q
+      sh.acc[tid] = 0.0f;
+    }
+    __syncthreads();
+    for (int kc = 0; kc < nkc; ++kc, ++g) {
+      const int s = g & 1;
+      if (g >= 2) {
+        int good = 1;
+        if (tid == 0) good = mbar_wait(&sh.sempty[s], ((g >> 1) - 1) & 1) ? 1 : 0;
+        if (!__syncthreads_and(good)) {
+          ok = false;
+          break;
+        }
+      }
+      unsigned char *zh = zst + s * 2 * ZTILE, *zl = zh + ZTILE;
+      // z chunk: rows q (128), K = basis index j in [kc*32, kc*32 + 32)
+      for (int cm = warp; cm < 16 * (AT_KJ / 4); cm += AT_NT / 32) {
+        const int rg = cm / (AT_KJ / 4), kg = cm - rg * (AT_KJ / 4);
+        const int ql = rg * 8 + (lane >> 2);
+        const int j = kc * AT_KJ + kg * 4 + (lane & 3);
+        float b = 0.0f;
+        if (j < 64) {
+          b = sh.L[ql][0][j & 3] * sh.L[ql][1][(j >> 2) & 3] * sh.L[ql][2][j >> 4];
+        } else if (j < n) {
+          const int code = sh.ecs[j - 64];
+          const int lv = code & 7;
+          const int qg = mt * 128 + ql;
+          const float phi = (((lv & 1) ? 1.0f + sh.xi[ql][0] : 1.0f - sh.xi[ql][0]) *
+                             ((lv & 2) ? 1.0f + sh.xi[ql][1] : 1.0f - sh.xi[ql][1]) *
+                             ((lv & 4) ? 1.0f + sh.xi[ql][2] : 1.0f - sh.xi[ql][2])) * 0.125f;
+          const float p0 = (qg < Q) ? pe[((int64_t)(qg >> 3) * A + (code >> 3)) * 32 + (qg & 7)] : 0.0f;
+          b = phi * p0;
+        }
+        const float z = sh.sw[ql] * b;
+        const uint32_t off = (uint32_t)rg * SBO_Z + (uint32_t)kg * LBO + (uint32_t)lane * 4;
+        const float hi = tf32_rn(z);
+        *reinterpret_cast<float *>(zh + off) = hi;
+        *reinterpret_cast<float *>(zl + off) = tf32_rn(z - hi);
+      }
+      fence_proxy_async();
+      __syncthreads();
+      if (tid == 0) {
+        tc_fence_after();
+        const uint32_t za = zbase + s * 2 * ZTILE, zla = za + ZTILE;
+        const int nks = min(AT_KJ, npad - kc * AT_KJ) / 8;
+        for (int ks = 0; ks < nks; ++ks) {
+          const uint32_t ko = (uint32_t)ks * 2u * LBO;
+          const uint32_t hk = (uint32_t)((kc * AT_KJ + ks * 8) / 4) * LBO;
+          const uint32_t first = (kc == 0 && ks == 0) ? 0u : 1u;
+          mma_tf32(tD, sdesc(za + ko, LBO, SBO_Z), sdesc(hbase + hk, LBO, SBO_H), idD, first);
+          mma_tf32(tX, sdesc(za + ko, LBO, SBO_Z), sdesc(lbase + hk, LBO, SBO_H), idD, first);
+          mma_tf32(tX, sdesc(zla + ko, LBO, SBO_Z), sdesc(hbase + hk, LBO, SBO_H), idD, 1u);
+        }
+        mma_commit(&sh.sempty[s]);
+        if (kc == nkc - 1) mma_commit(&sh.dbar);
+      }
+    }
+    if (!ok) break;
+    {
+      int good = 1;
+      if (tid == 0) good = mbar_wait(&sh.dbar, dcount & 1) ? 1 : 0;
+      if (!__syncthreads_and(good)) {
+        ok = false;
+        break;
+      }
+      ++dcount;
+    }
+    tc_fence_after();
+    // epilogue: lane = point; warps w and w+4 split the column blocks
+    if (warp < 8) {
+      const int quarter = warp & 3, half = warp >> 2;
+      const int ql = quarter * 32 + lane;
+      const uint32_t lanebase = (uint32_t)(quarter * 32) << 16;
+      const int qg = mt * 128 + ql;
+      float part = 0.0f;
+      for (int cb = half; cb * 16 < npad; cb += 2) {
+        float dh[16], dx[16];
+        tmem_ld16(tD + lanebase + cb * 16, dh);
+        tmem_ld16(tX + lanebase + cb * 16, dx);
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+          const int i = cb * 16 + u;
+          float b = 0.0f;
+          if (i < 64) {
+            b = sh.L[ql][0][i & 3] * sh.L[ql][1][(i >> 2) & 3] * sh.L[ql][2][i >> 4];
+          } else if (i < n && qg < Q) {
+            const int code = sh.ecs[i - 64];
+            const int lv = code & 7;
+            const float phi = (((lv & 1) ? 1.0f + sh.xi[ql][0] : 1.0f - sh.xi[ql][0]) *
+                               ((lv & 2) ? 1.0f + sh.xi[ql][1] : 1.0f - sh.xi[ql][1]) *
+                               ((lv & 4) ? 1.0f + sh.xi[ql][2] : 1.0f - sh.xi[ql][2])) * 0.125f;
+            b = phi * pe[((int64_t)(qg >> 3) * A + (code >> 3)) * 32 + (qg & 7)];
+          }
+          part = fmaf(dh[u] + dx[u], sh.sw[ql] * b, part);
+        }
+      }
+      atomicAdd(&sh.acc[ql], part);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (tid < 128) {
+      const int qg = mt * 128 + tid;
+      if (qg < Q) Vbar[q0 + qg] = (double)sh.acc[tid];
+    }
+    __syncthreads();
+    tc_fence_after();
+  }
+  if (!ok && tid == 0) {
+    set_err(err, DEVERR_TIMEOUT);
+    mbar_wait(&sh.dbar, dcount & 1);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(sh.tmem, 256);
+  }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -967,7 +1196,13 @@ pufe_status launch_assemble_tc(pufe_ctx *ctx, const double *V, int what, double 
   const float sx = (float)(2.0 / ctx->h[0]), sy = (float)(2.0 / ctx->h[1]),
               sz = (float)(2.0 / ctx->h[2]);
   const int amax = std::max(1, ctx->max_alpha);
-  const int inb = ((amax * 4 * WS_KC * 4 + WS_KC * 16) + 127) & ~127;
+  const int inb = ((amax * 4 * WS_KC * 4 + WS_KC * 128 + WS_KC * 4) + 127) & ~127;
+  if (what & PUFE_WANT_H) {
+    k_pack_v<<<(unsigned)ctx->nelem, 256, 0, st>>>(D.qoff, D.qpoff, V, D.vpad);
+    PUFE_CUDA_TRY(cudaGetLastError());
+  } else {
+    PUFE_CUDA_TRY(cudaMemsetAsync(D.vpad, 0, (size_t)ctx->nq_pad * sizeof(float), st));
+  }
   // 128-row tile: 2 stages of 40 KB + 128 x 193 FP32 staging; 256-row: 2 x 80 KB
   // + per-warp transpose buffers
   const size_t sm128 = (size_t)1024 + 2 * 40960 + WS_NIN * (size_t)inb + sizeof(WsShared) +
@@ -984,7 +1219,7 @@ pufe_status launch_assemble_tc(pufe_ctx *ctx, const double *V, int what, double 
     PUFE_CUDA_TRY(cudaFuncSetAttribute(k_assemble_tc<256>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     const int grid = std::min(nbig, nsm);
-    k_assemble_tc<256><<<grid, WS_NT, sm, st>>>(D.order, D.qoff, D.qpoff, D.qdat, D.doff, D.ecol,
+    k_assemble_tc<256><<<grid, WS_NT, sm, st>>>(D.order, D.qoff, D.qpoff, D.ptab, D.vpad, D.doff, D.ecol,
                                                 D.aoff, D.toff32, D.psi32, D.soff, D.smap, V, sx,
                                                 sy, sz, nbig, amax, inb, what, H, S, D.err);
     PUFE_CUDA_TRY(cudaGetLastError());
@@ -996,7 +1231,7 @@ pufe_status launch_assemble_tc(pufe_ctx *ctx, const double *V, int what, double 
     PUFE_CUDA_TRY(cudaFuncSetAttribute(k_assemble_tc<128>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     const int grid = std::min(nsmall, nsm);
-    k_assemble_tc<128><<<grid, WS_NT, sm, st>>>(D.order + nbig, D.qoff, D.qpoff, D.qdat, D.doff,
+    k_assemble_tc<128><<<grid, WS_NT, sm, st>>>(D.order + nbig, D.qoff, D.qpoff, D.ptab, D.vpad, D.doff,
                                                 D.ecol, D.aoff, D.toff32, D.psi32, D.soff,
                                                 D.smap, V, sx, sy, sz, nsmall, amax, inb, what, H,
                                                 S, D.err);
@@ -1022,16 +1257,33 @@ pufe_status launch_density_tc(pufe_ctx *ctx, const double *C, int64_t ldc, const
 
 pufe_status launch_adjoint_tc(pufe_ctx *ctx, const double *Hbar, double *Vbar, cudaStream_t st) {
   auto &D = ctx->d;
-  const int n4 = (ctx->max_basis + 3) & ~3;
-  const int ldb = n4 + 36;
-  const size_t sm = ((size_t)n4 * n4 + (size_t)ADJ_QB * ldb + ADJ_QB) * sizeof(float);
-  if (sm > 227 * 1024) return fail(PUFE_EINVAL, "n_e too large for the FP32 adjoint kernel");
-  PUFE_CUDA_TRY(
-      cudaFuncSetAttribute(k_adjoint_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  k_adjoint_f32<<<(unsigned)ctx->nelem, ADJ_NT, sm, st>>>(D.order, D.qoff, D.qpoff, D.qdat, D.w,
-                                                          D.doff, D.ecol, D.aoff, D.toff32,
-                                                          D.psi32, D.soff, D.smap, Hbar, Vbar);
-  PUFE_CUDA_TRY(cudaGetLastError());
+  const int nbig = ctx->n_big;
+  if (nbig > 0) {  // n_e > 128: FP32 CUDA-core kernel
+    const int n4 = (ctx->max_basis + 3) & ~3;
+    const int ldb = n4 + 36;
+    const size_t sm = ((size_t)n4 * n4 + (size_t)ADJ_QB * ldb + ADJ_QB) * sizeof(float);
+    if (sm > 227 * 1024) return fail(PUFE_EINVAL, "n_e too large for the FP32 adjoint kernel");
+    PUFE_CUDA_TRY(
+        cudaFuncSetAttribute(k_adjoint_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_adjoint_f32<<<nbig, ADJ_NT, sm, st>>>(D.order, D.qoff, D.qpoff, D.qdat, D.w, D.doff, D.ecol,
+                                            D.aoff, D.toff32, D.psi32, D.soff, D.smap, Hbar, Vbar);
+    PUFE_CUDA_TRY(cudaGetLastError());
+  }
+  const int nsmall = (int)ctx->nelem - nbig;
+  if (nsmall > 0) {  // n_e <= 128: tensor cores
+    int np = 16;
+    for (int64_t k = nbig; k < ctx->nelem; ++k)
+      np = std::max(np, (ctx->n_e[ctx->order[k]] + 15) & ~15);
+    const size_t sm = (size_t)1024 + 2 * (size_t)np * np * 4 + 4 * (size_t)128 * AT_KJ * 4 +
+                      sizeof(AtShared);
+    if (sm > 227 * 1024) return fail(PUFE_EINVAL, "n_e too large for the tensor-core adjoint");
+    PUFE_CUDA_TRY(
+        cudaFuncSetAttribute(k_adjoint_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_adjoint_tc<<<nsmall, AT_NT, sm, st>>>(D.order + nbig, D.qoff, D.qpoff, D.qdat, D.doff,
+                                            D.ecol, D.aoff, D.toff32, D.psi32, D.soff, D.smap,
+                                            Hbar, np, Vbar, D.err);
+    PUFE_CUDA_TRY(cudaGetLastError());
+  }
   return PUFE_OK;
 }
 

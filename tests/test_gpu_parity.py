@@ -276,3 +276,12 @@ def test_tf32x3_c3_like_large_elements():
     eh, es = _rel(Hg, Ho), _rel(Sg, So)
     print(f"c3-like: TF32X3 rel err H {eh:.2e} S {es:.2e}")
     assert eh < TOL_MAT_TF32 and es < TOL_MAT_TF32
+    # adjoint: elements above and below 128 columns take different kernels
+    dev = _dev()
+    Hbar = Ho.copy()
+    Hbar.data = W.random_symmetric_values(Ho.nnz, seed=4)
+    go = oasm.adjoint_V(m, rules, Hbar)
+    out = torch.empty(ctx.n_q, dtype=torch.float64, device=dev)
+    ctx.pufe_assemble_HV_adjoint(torch.tensor(Hbar.data, device=dev), out, prec=pufe.PUFE_TF32X3)
+    ctx.pufe_sync_status()
+    assert _rel(out.cpu().numpy(), go) < 1e-4
