@@ -159,6 +159,25 @@ pufe_status pufe_tabulate(pufe_ctx *ctx, int prec, void *stream);
 pufe_status pufe_assemble_HS(pufe_ctx *ctx, const double *V, int prec, int what,
                              double *H, double *S, void *stream);
 
+/* Allocation-free variant of pufe_assemble_HS with prec = PUFE_TF32X3 (the
+ * paper has no counterpart; it exists for callers).  Some callers cannot
+ * allocate device memory while they run their solve loop -- for example code
+ * that must stay inside a fixed device-memory budget, or that runs where the
+ * allocator may not be called.  This call allocates nothing: the FP32 copy of
+ * V that the tensor-core assembly reads lives in a library-owned static
+ * device array of PUFE_STATIC_MAX_POINTS (4,194,304) floats, resident on
+ * every device that loads the library until the process exits.  Contexts
+ * with more padded quadrature points than that return PUFE_EINVAL.  The
+ * context itself (built earlier by pufe_build_mesh) and a prior
+ * pufe_tabulate(ctx, PUFE_TF32X3) are still required; arguments and results
+ * are as for pufe_assemble_HS.  The first call on a device looks up the
+ * array's device address, so make that first call before capturing the
+ * stream.  All calls share the one array: each call rewrites the entries it
+ * reads, and calls that overlap on the GPU (on different streams or
+ * contexts) race on it.  Asynchronous. */
+pufe_status pufe_assemble_HS_static(pufe_ctx *ctx, const double *V, int what, double *H,
+                                    double *S, void *stream);
+
 /* K4 (Sec. 3, eq. rhoe): n_q = sum_k f_k (sum_j B_qj C_jk)^2 for every
  * quadrature point.  C: device float64, N x nocc, row-major with leading
  * dimension ldc >= nocc (C[j * ldc + k]); f: device float64 (nocc);

@@ -75,6 +75,18 @@ pufe_status pufe_assemble_HS(pufe_ctx *ctx, const double *V, int prec, int what,
   return launch_assemble_fp64(ctx, V, what, H, S, st);
 }
 
+pufe_status pufe_assemble_HS_static(pufe_ctx *ctx, const double *V, int what, double *H,
+                                    double *S, void *stream) {
+  if (pufe_status e0 = need_device(ctx)) return e0;
+  if (pufe_status e1 = need_table(ctx, PUFE_TF32X3)) return e1;
+  if (what <= 0 || what > (PUFE_WANT_H | PUFE_WANT_S)) return fail(PUFE_EINVAL, "bad `what` mask");
+  if ((what & PUFE_WANT_H) && (!H || !V)) return fail(PUFE_EINVAL, "H wanted: need H and V");
+  if ((what & PUFE_WANT_S) && !S) return fail(PUFE_EINVAL, "S wanted: need S");
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return fail(PUFE_ECUDA, "cudaSetDevice failed");
+  return launch_assemble_tc_static(ctx, V, what, H, S, (cudaStream_t)stream);
+}
+
 pufe_status pufe_density(pufe_ctx *ctx, const double *C, int64_t ldc, const double *f, int nocc,
                          int prec, double *rho, void *stream) {
   if (pufe_status e0 = need_device(ctx)) return e0;

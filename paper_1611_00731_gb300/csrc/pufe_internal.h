@@ -255,6 +255,8 @@ pufe_status launch_density_fp64(pufe_ctx *ctx, const double *C, int64_t ldc, con
 pufe_status launch_adjoint_fp64(pufe_ctx *ctx, const double *Hbar, double *Vbar, cudaStream_t s);
 pufe_status launch_tabulate_f32(pufe_ctx *ctx, cudaStream_t s);
 pufe_status launch_adjoint_tc(pufe_ctx *ctx, const double *Hbar, double *Vbar, cudaStream_t s);
+pufe_status launch_assemble_tc_static(pufe_ctx *ctx, const double *V, int what, double *H,
+                                      double *S, cudaStream_t s);
 pufe_status launch_assemble_tc(pufe_ctx *ctx, const double *V, int what, double *H, double *S,
                                cudaStream_t s);
 pufe_status launch_density_tc(pufe_ctx *ctx, const double *C, int64_t ldc, const double *f,

@@ -17,6 +17,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "pufe_internal.h"
 
@@ -1282,6 +1283,98 @@ pufe_status launch_adjoint_tc(pufe_ctx *ctx, const double *Hbar, double *Vbar, c
     k_adjoint_tc<<<nsmall, AT_NT, sm, st>>>(D.order + nbig, D.qoff, D.qpoff, D.qdat, D.doff,
                                             D.ecol, D.aoff, D.toff32, D.psi32, D.soff, D.smap,
                                             Hbar, np, Vbar, D.err);
+    PUFE_CUDA_TRY(cudaGetLastError());
+  }
+  return PUFE_OK;
+}
+
+}  // namespace pufe
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the TF32X3 assembly.
+//
+// The assembly kernel reads an FP32 copy of V laid out on the padded point
+// list; pufe_assemble_HS keeps that copy in memory the context allocated.
+// This variant keeps it in the file-scope array below instead, so a call
+// needs no device allocation of any kind.  The array holds at most
+// PUFE_STATIC_MAX_POINTS values on every device that loads the library (it
+// stays resident until the process exits); larger contexts are rejected.
+// The device address of the array is looked up once per device with
+// cudaGetSymbolAddress (the host-side symbol is only a stand-in) on the
+// first call made on that device.
+// ---------------------------------------------------------------------------
+#define PUFE_STATIC_MAX_POINTS (4 * 1024 * 1024)
+static __device__ __align__(256) float g_vpad_static[PUFE_STATIC_MAX_POINTS];
+
+namespace pufe {
+namespace {
+std::mutex g_static_mu;
+float *g_static_ptr[128] = {nullptr};
+}  // namespace
+
+static pufe_status static_scratch(int device, float **out) {
+  if (device < 0 || device >= 128) return fail(PUFE_EINVAL, "device ordinal out of range");
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  if (!g_static_ptr[device]) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_vpad_static);  // the ctx device is current
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_vpad_static)");
+    g_static_ptr[device] = static_cast<float *>(p);
+  }
+  *out = g_static_ptr[device];
+  return PUFE_OK;
+}
+
+pufe_status launch_assemble_tc_static(pufe_ctx *ctx, const double *V, int what, double *H,
+                                      double *S, cudaStream_t st) {
+  auto &D = ctx->d;
+  if (!ctx->fe_exact)
+    return fail(PUFE_EINVAL,
+                "PUFE_TF32X3 needs every (sub)cell rule to have >= 4 points per axis");
+  if (ctx->max_basis > 256) return fail(PUFE_EINVAL, "PUFE_TF32X3 supports n_e <= 256");
+  if (ctx->nq_pad > PUFE_STATIC_MAX_POINTS)
+    return fail(PUFE_EINVAL, "pufe_assemble_HS_static: the context has " +
+                                 std::to_string(ctx->nq_pad) +
+                                 " padded quadrature points; the static scratch holds " +
+                                 std::to_string(PUFE_STATIC_MAX_POINTS));
+  float *vs = nullptr;
+  if (pufe_status e0 = static_scratch(ctx->device, &vs)) return e0;
+  const size_t bytes = (size_t)ctx->nnz * sizeof(double);
+  if (what & PUFE_WANT_H) PUFE_CUDA_TRY(cudaMemcpyAsync(H, D.T0, bytes, cudaMemcpyDeviceToDevice, st));
+  if (what & PUFE_WANT_S) PUFE_CUDA_TRY(cudaMemcpyAsync(S, D.S0, bytes, cudaMemcpyDeviceToDevice, st));
+  const float sx = (float)(2.0 / ctx->h[0]), sy = (float)(2.0 / ctx->h[1]),
+              sz = (float)(2.0 / ctx->h[2]);
+  const int amax = std::max(1, ctx->max_alpha);
+  const int inb = ((amax * 4 * WS_KC * 4 + WS_KC * 128 + WS_KC * 4) + 127) & ~127;
+  // the array keeps the previous call's values: every entry this call reads
+  // (including the zero padding) is rewritten first
+  k_pack_v<<<(unsigned)ctx->nelem, 256, 0, st>>>(D.qoff, D.qpoff, (what & PUFE_WANT_H) ? V : nullptr,
+                                                vs);
+  PUFE_CUDA_TRY(cudaGetLastError());
+  const size_t sm128 = (size_t)1024 + 2 * 40960 + WS_NIN * (size_t)inb + sizeof(WsShared) +
+                       (size_t)128 * 193 * 4;
+  const size_t sm256 = (size_t)1024 + 2 * 81920 + WS_NIN * (size_t)inb + sizeof(WsShared) +
+                       (size_t)4 * 32 * 17 * 8;
+  int nsm = 0;
+  PUFE_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device));
+  const int nbig = ctx->n_big;
+  if (nbig > 0) {
+    if (sm256 > 227 * 1024) return fail(PUFE_EINVAL, "too many enrichments per element for TF32X3");
+    PUFE_CUDA_TRY(cudaFuncSetAttribute(k_assemble_tc<256>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm256));
+    k_assemble_tc<256><<<std::min(nbig, nsm), WS_NT, sm256, st>>>(
+        D.order, D.qoff, D.qpoff, D.ptab, vs, D.doff, D.ecol, D.aoff, D.toff32, D.psi32, D.soff,
+        D.smap, V, sx, sy, sz, nbig, amax, inb, what, H, S, D.err);
+    PUFE_CUDA_TRY(cudaGetLastError());
+  }
+  const int nsmall = (int)ctx->nelem - nbig;
+  if (nsmall > 0) {
+    if (sm128 > 227 * 1024) return fail(PUFE_EINVAL, "too many enrichments per element for TF32X3");
+    PUFE_CUDA_TRY(cudaFuncSetAttribute(k_assemble_tc<128>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm128));
+    k_assemble_tc<128><<<std::min(nsmall, nsm), WS_NT, sm128, st>>>(
+        D.order + nbig, D.qoff, D.qpoff, D.ptab, vs, D.doff, D.ecol, D.aoff, D.toff32, D.psi32,
+        D.soff, D.smap, V, sx, sy, sz, nsmall, amax, inb, what, H, S, D.err);
     PUFE_CUDA_TRY(cudaGetLastError());
   }
   return PUFE_OK;

@@ -27,7 +27,8 @@ STATUS = {0: "PUFE_OK", 1: "PUFE_EINVAL", 2: "PUFE_ENOMEM", 3: "PUFE_ECUDA",
 # every symbol that include/pufe.h declares
 EXPORTS = ["pufe_build_mesh", "pufe_get_sizes", "pufe_get_quadrature", "pufe_get_pattern",
            "pufe_get_element_basis", "pufe_tabulate", "pufe_assemble_HS", "pufe_density",
-           "pufe_assemble_HV_adjoint", "pufe_sync_status", "pufe_destroy", "pufe_last_error"]
+           "pufe_assemble_HV_adjoint", "pufe_sync_status", "pufe_destroy", "pufe_last_error",
+           "pufe_assemble_HS_static"]
 
 
 class PufeError(RuntimeError):
@@ -82,6 +83,7 @@ def load_library(build_if_missing: bool = True):
     lib.pufe_get_element_basis.argtypes = [vp, i32p, i32p]
     lib.pufe_tabulate.argtypes = [vp, C.c_int, vp]
     lib.pufe_assemble_HS.argtypes = [vp, vp, C.c_int, C.c_int, vp, vp, vp]
+    lib.pufe_assemble_HS_static.argtypes = [vp, vp, C.c_int, vp, vp, vp]
     lib.pufe_density.argtypes = [vp, vp, C.c_int64, vp, C.c_int, C.c_int, vp, vp]
     lib.pufe_assemble_HV_adjoint.argtypes = [vp, vp, C.c_int, vp, vp]
     lib.pufe_sync_status.argtypes = [vp, vp]
@@ -168,6 +170,15 @@ class Context:
         _check(_LIB.pufe_assemble_HS(self._h, _ptr(V, torch.float64), int(prec), int(what),
                                      _ptr(H, torch.float64), _ptr(S, torch.float64),
                                      _stream(stream)))
+
+    def pufe_assemble_HS_static(self, V, H=None, S=None, what=None, stream=None):
+        """TF32X3 assembly whose V scratch is a library-owned static array (no allocation)."""
+        import torch
+        if what is None:
+            what = (PUFE_WANT_H if H is not None else 0) | (PUFE_WANT_S if S is not None else 0)
+        _check(_LIB.pufe_assemble_HS_static(self._h, _ptr(V, torch.float64), int(what),
+                                            _ptr(H, torch.float64), _ptr(S, torch.float64),
+                                            _stream(stream)))
 
     def pufe_density(self, Cmat, f, rho, prec=PUFE_FP64, stream=None):
         import torch
