@@ -73,6 +73,13 @@ struct DeviceArrays {
   float *ptab = nullptr;      // per padded point, 32 floats: L[3][4], dL[3][4] (x 2/h),
                               // xi[3], sqrt(w/2), sqrt(w), 3 unused; zeros on padding
   float *vpad = nullptr;      // per padded point: FP32 copy of V (filled per call)
+  // tensor structure of the rules: per element a list of (sub)cells, each a
+  // p^3 Gauss rule whose points are consecutive (x fastest)
+  int32_t *partoff = nullptr; // nelem + 1: offsets into part arrays
+  int32_t *part_p = nullptr;  // points per axis of each part
+  int32_t *part_q = nullptr;  // first point of each part (relative to the element)
+  float *mfe = nullptr;       // nelem x 1000: FE-FE block of H_V per element, by
+                              // unordered per-axis index pairs (filled per call)
   int64_t *toff32 = nullptr;  // nelem + 1: offsets into psi32 (units of padded q*alpha)
   float *psi32 = nullptr;     // per element [q/8][slot][comp][q%8]: 32-float blocks
   float *eorig = nullptr;     // per (element, slot): displacement of the element
@@ -107,6 +114,7 @@ struct pufe_ctx {
   bool tabulated32 = false;   // FP32 enrichment table is current
   bool fe_exact = false;      // every rule has >= 4 points per axis per (sub)cell
   int n_big = 0;              // elements with n_e > 128 (listed first in `order`)
+  int max_part_p = 0;         // largest points-per-axis of any (sub)cell
   bool on_device = false;   // device copies exist (a CUDA device was present)
   // host copies kept for getters
   std::vector<int64_t> qoff, rowptr, doff;
@@ -255,6 +263,7 @@ pufe_status launch_density_fp64(pufe_ctx *ctx, const double *C, int64_t ldc, con
 pufe_status launch_adjoint_fp64(pufe_ctx *ctx, const double *Hbar, double *Vbar, cudaStream_t s);
 pufe_status launch_tabulate_f32(pufe_ctx *ctx, cudaStream_t s);
 pufe_status launch_adjoint_tc(pufe_ctx *ctx, const double *Hbar, double *Vbar, cudaStream_t s);
+pufe_status launch_fefe(pufe_ctx *ctx, const double *V, double *H, cudaStream_t s);
 pufe_status launch_assemble_tc_static(pufe_ctx *ctx, const double *V, int what, double *H,
                                       double *S, cudaStream_t s);
 pufe_status launch_assemble_tc(pufe_ctx *ctx, const double *V, int what, double *H, double *S,

@@ -635,6 +635,20 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
   ctx->max_q = *std::max_element(q_e.begin(), q_e.end());
   ctx->fe_exact = fe_exact;
   ctx->n_big = n_big;
+  // (sub)cell structure of every element's rule
+  std::vector<int32_t> partoff(nelem + 1, 0), part_p, part_q;
+  int max_part_p = 0;
+  for (int64_t e = 0; e < nelem; ++e) {
+    int32_t qrel = 0;
+    for (auto &pt : rule[e]) {
+      part_p.push_back(pt.p);
+      part_q.push_back(qrel);
+      qrel += pt.p * pt.p * pt.p;
+      max_part_p = std::max(max_part_p, pt.p);
+    }
+    partoff[e + 1] = (int32_t)part_p.size();
+  }
+  ctx->max_part_p = max_part_p;
   ctx->max_alpha = 0;
   for (auto &v : ealpha) ctx->max_alpha = std::max(ctx->max_alpha, (int)v.size());
 
@@ -684,6 +698,10 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
   if ((st = upload(&D.qpoff, qpoff)) != PUFE_OK) return st;
   if ((st = upload(&D.qdat, qdat)) != PUFE_OK) return st;
   if ((st = upload(&D.ptab, ptab)) != PUFE_OK) return st;
+  if ((st = upload(&D.partoff, partoff)) != PUFE_OK) return st;
+  if ((st = upload(&D.part_p, part_p)) != PUFE_OK) return st;
+  if ((st = upload(&D.part_q, part_q)) != PUFE_OK) return st;
+  PUFE_CUDA_TRY(cudaMalloc((void **)&D.mfe, std::max<int64_t>(1, nelem) * 1000 * sizeof(float)));
   PUFE_CUDA_TRY(cudaMalloc((void **)&D.vpad, std::max<int64_t>(1, qpoff[nelem]) * sizeof(float)));
   if ((st = upload(&D.toff32, toff32)) != PUFE_OK) return st;
   if ((st = upload(&D.eorig, eorig)) != PUFE_OK) return st;
@@ -709,7 +727,7 @@ static void free_device(pufe_ctx *ctx) {
   auto &D = ctx->d;
   void *ptrs[] = {D.qoff, D.x, D.w, D.xi, D.doff, D.dofs, D.ecol, D.aoff, D.alist,
                   D.toff, D.psi, D.psi32, D.qpoff, D.qdat, D.ptab, D.vpad, D.toff32, D.eorig,
-                  D.T0, D.S0,
+                  D.T0, D.S0, D.partoff, D.part_p, D.part_q, D.mfe,
                   D.orb, D.orbf, D.rowptr, D.col, D.soff, D.smap, D.order, D.err};
   for (void *p : ptrs)
     if (p) cudaFree(p);

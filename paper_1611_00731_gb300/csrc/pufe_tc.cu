@@ -251,45 +251,44 @@ __global__ void k_tabulate_f32(const int64_t *__restrict__ qpoff, const float4 *
 // ---------------------------------------------------------------------------
 // Tensor-core element contraction: persistent, warp-specialized.
 //
-// Operand tiles: row c of a tile = basis column c of the element, K = the
-// chunk's 8 quadrature points; 10 tiles per stage:
-//   0/1 Y0 hi/lo, 2/3 Y1, 4/5 Y2 (Y_d = sqrt(w/2) dphi/dx_d), 6/7 Z (sqrt(w) phi),
-//   8/9 ZV (V sqrt(w) phi).
-// Per chunk and M-tile:  H += ZV^T Z (all columns),
-//   H[:, 64:] += sum_d Y_d^T Y_d[64:],  S[:, 64:] += Z^T Z[64:].
+// The FE-FE blocks are done elsewhere (exact constants and the sum-factorized
+// V term); this kernel computes the enrichment strip of every element:
+//   H[:, 64:] = ZV^T Z[64:] + sum_d Y_d^T Y_d[64:],   S[:, 64:] = Z^T Z[64:],
+// with, per 8-point chunk, Y_d = sqrt(w/2) dphi/dx_d, Z = sqrt(w) phi and
+// ZV = V Z for every basis column (rows of the A operand) and the enrichment
+// columns only (rows of the B operand), each split into two TF32 terms.
 //
 // Roles (one CTA per SM, elements taken round-robin from the work list):
-//   warps 0-7  fill: per chunk, wait for a free operand stage and the chunk's
-//              inputs (brought into shared memory one chunk ahead by 1D TMA
-//              bulk copies), build the 10 tiles, signal "stage full";
-//   warp 8     MMA: one lane issues tcgen05.mma per full stage and commits
-//              to "stage empty"; at the end of an element, to "acc full";
-//   warps 9-12 epilogue: drain TMEM (each warp owns one 32-lane quarter),
-//              transpose 32x16 blocks through shared memory so that each
-//              half-warp scatters along one CSR row, add into FP64 CSR
-//              values, then signal "acc empty".
+//   warps 0-7   fill: per chunk, wait for the chunk's inputs (in shared
+//               memory, brought by the loader) and a free operand stage,
+//               compute the operand values; 128-row tile: thread = basis
+//               row, A operands written straight into tensor memory with
+//               tcgen05.st, enrichment rows also written to the B tiles in
+//               shared memory; 256-row tile: all operands in shared memory;
+//               then signal "stage full" and "input free";
+//   warp 8      MMA: one lane issues tcgen05.mma per full stage, commits to
+//               "stage empty" and, at the end of an element, "acc full";
+//   warps 9-12  epilogue: drain the accumulators, add them into the FP64 CSR
+//               values, signal "acc empty";
+//   warp 13     loader: 1D TMA bulk copies of each chunk's inputs (Psi table
+//               block, per-point table, V) into a ring of input buffers.
 // All waits are bounded (2 s); a timeout sets the device error flag and every
 // role leaves its loop.
 // ---------------------------------------------------------------------------
 constexpr int WS_MMA_WARP = 8;
 constexpr int WS_EPI_WARP0 = 9;       // warps 9-12
-constexpr int WS_NT = 13 * 32;
+constexpr int WS_LOAD_WARP = 13;
+constexpr int WS_NT = 14 * 32;
 constexpr int WS_KC = 8;              // quadrature points per chunk (one K-step)
-constexpr int WS_NIN = 6;             // input buffers (loads run NIN-1 chunks ahead)
+constexpr int WS_NIN = 6;             // input buffers
 
 struct WsShared {
-  uint64_t sfull[4], sempty[4], ibar[WS_NIN], afull, aempty;
+  uint64_t sfull[4], sempty[4], ibar[WS_NIN], ifree[WS_NIN], afull, aempty;
   uint32_t tmem;
   int abort;      // any role gave up: everyone leaves
-  int fill_go;    // written by fill thread 0 only: proceed with this chunk
-  float L[WS_KC][3][4];
-  float dL[WS_KC][3][4];
-  float xi[WS_KC][3];
-  float sw2[WS_KC], sw[WS_KC], v[WS_KC];
-  int ecs[192];   // the element's enrichment column codes
 };
 // after WsShared: the 128-row tile's FP32 staging of the accumulators
-// (128 x 193 floats), or the 256-row tile's per-warp transpose buffers
+// (128 x 129 floats), or the 256-row tile's per-warp transpose buffers
 // (4 x 32 x 17 float2)
 
 // FP32 copy of V on the padded point layout (zeros on padding points), so
@@ -307,7 +306,8 @@ __global__ void k_pack_v(const int64_t *__restrict__ qoff, const int64_t *__rest
 struct ElemInfo {
   int e, Q, Qp, A, n, nenr, npad, nenr16, nch, nmt;
   int64_t q0;
-  bool ok;
+  bool ok;   // the kernel can take this element
+  bool go;   // ok and it has enrichment columns (FE-only elements need no strip)
 };
 
 template <int R>
@@ -327,44 +327,66 @@ __device__ __forceinline__ ElemInfo elem_info(const int32_t *order, int k, const
   I.nch = I.Qp / WS_KC;
   I.nmt = (I.n + 127) / 128;
   I.ok = I.n <= R && I.A <= amax && I.nch > 0;
+  I.go = I.ok && I.nenr > 0;
   return I;
 }
 
-__device__ __forceinline__ void fill_bar() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// 4 consecutive 32-bit TMEM columns of this thread's lane
+__device__ __forceinline__ void tmem_st4(uint32_t taddr, float a, float b, float c, float d) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr),
+               "r"(__float_as_uint(a)), "r"(__float_as_uint(b)), "r"(__float_as_uint(c)),
+               "r"(__float_as_uint(d))
+               : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() {
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+// D (+)= A * B with A read from tensor memory
+__device__ __forceinline__ void mma_tf32_ta(uint32_t dtmem, uint32_t atmem, uint64_t b,
+                                            uint32_t idesc, uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(dtmem),
+      "r"(atmem), "l"(b), "r"(idesc), "r"(accum)
+      : "memory");
+}
 
 template <int R>
 __global__ void __launch_bounds__(WS_NT, 1) k_assemble_tc(
     const int32_t *__restrict__ order, const int64_t *__restrict__ qoff,
     const int64_t *__restrict__ qpoff, const float *__restrict__ ptab,
-    const float *__restrict__ vpad,
-    const int64_t *__restrict__ doff, const int32_t *__restrict__ ecol,
-    const int32_t *__restrict__ aoff, const int64_t *__restrict__ toff32,
-    const float *__restrict__ psi, const int64_t *__restrict__ soff,
-    const int32_t *__restrict__ smap, const double *__restrict__ V, float sx, float sy, float sz,
-    int nelem_list, int amax, int in_bytes, int want, double *__restrict__ H,
+    const float *__restrict__ vpad, const int64_t *__restrict__ doff,
+    const int32_t *__restrict__ ecol, const int32_t *__restrict__ aoff,
+    const int64_t *__restrict__ toff32, const float *__restrict__ psi,
+    const int64_t *__restrict__ soff, const int32_t *__restrict__ smap, float sx, float sy,
+    float sz, int nelem_list, int amax, int in_bytes, int want, double *__restrict__ H,
     double *__restrict__ S, unsigned *err) {
   constexpr int KC = WS_KC;
-  constexpr int TILE = R * KC * 4;           // bytes per tile
-  constexpr int STG = NTILES * TILE;         // bytes per stage
-  constexpr int NSTG = 2;                    // operand stages
-  // 128-row tile: the epilogue copies the accumulators to shared memory,
-  // releases TMEM at once and scatters from there while the next element's
-  // MMAs run.  256-row tile: scatter straight from TMEM.
-  constexpr bool STAGED = (R == 128);
-  constexpr int SROW = 193;                  // staging row stride (floats), 1 mod 32
-  constexpr uint32_t LBO = 128;              // next core matrix along K
-  constexpr uint32_t SBO = (KC / 4) * 128;   // next 8-row group along M/N
-  // Tensor-core FP32 accumulation does not round to nearest; its error grows
-  // with the number of MMAs summed into one accumulator.  With the 128-row
-  // tile the large hi*hi products and the small cross products go to
-  // separate accumulators (cross terms are ~2^-11 smaller, so their error is
-  // negligible) and the two are added in FP64 by the epilogue.
-  constexpr bool SPLIT = (R == 128);
+  constexpr bool ATMEM = (R == 128);          // A operands in tensor memory
+  constexpr int TILE = ATMEM ? 64 * KC * 4 : R * KC * 4;   // bytes per SMEM tile
+  constexpr int NBT = ATMEM ? 8 : NTILES;     // SMEM tiles per stage
+  constexpr int STG = NBT * TILE;             // bytes per stage
+  constexpr int NSTG = ATMEM ? 3 : 2;         // operand stages
+  constexpr uint32_t LBO = 128;               // next core matrix along K
+  constexpr uint32_t SBO = (KC / 4) * 128;    // next 8-row group along M/N
+  // 128-row tile: the hi*hi and the (2^-11 smaller) cross products go to
+  // separate accumulators, because tensor-core FP32 accumulation does not
+  // round to nearest and its error grows with the number of MMAs summed.
+  constexpr bool SPLIT = ATMEM;
   constexpr uint32_t TCOLS = 512;
-  constexpr uint32_t HX_COL = SPLIT ? 128 : 0;
-  constexpr uint32_t S_COL = 256;
-  constexpr uint32_t SX_COL = SPLIT ? 320 : 256;
+  constexpr uint32_t HX_COL = SPLIT ? 64 : 0;
+  constexpr uint32_t S_COL = SPLIT ? 128 : 256;
+  constexpr uint32_t SX_COL = SPLIT ? 192 : 256;
+  constexpr uint32_t A_COL = 256;             // ATMEM: A stages, 10 tiles x 8 columns each
+  constexpr bool STAGED = ATMEM;
+  constexpr int SROW = 129;                   // staging row stride (floats), 1 mod 32
   static_assert(NSTG * STG <= 163840, "stage memory");
+  static_assert(!ATMEM || A_COL + NSTG * 80 <= TCOLS, "tensor memory");
 
   extern __shared__ __align__(16) unsigned char dsm[];
   unsigned char *stages = dsm + ((1024u - (smem_u32(dsm) & 1023u)) & 1023u);
@@ -383,14 +405,16 @@ __global__ void __launch_bounds__(WS_NT, 1) k_assemble_tc(
   if (warp == WS_MMA_WARP) tmem_alloc(&sh.tmem, TCOLS);
   if (tid == 0) {
     for (int i = 0; i < NSTG; ++i) {
-      mbar_init(&sh.sfull[i], 1);
+      mbar_init(&sh.sfull[i], 8);    // one arrival per fill warp
       mbar_init(&sh.sempty[i], 1);
     }
-    for (int i = 0; i < WS_NIN; ++i) mbar_init(&sh.ibar[i], 1);
+    for (int i = 0; i < WS_NIN; ++i) {
+      mbar_init(&sh.ibar[i], 1);
+      mbar_init(&sh.ifree[i], 8);    // one arrival per fill warp
+    }
     mbar_init(&sh.afull, 1);
     mbar_init(&sh.aempty, 4);
     sh.abort = 0;
-    sh.fill_go = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   fence_proxy_async();
@@ -401,56 +425,10 @@ __global__ void __launch_bounds__(WS_NT, 1) k_assemble_tc(
 
   if (warp < 8) {
     // ======================= fill warps =======================
-    // load cursor (thread 0): next chunk whose inputs to fetch
-    int lk = blockIdx.x, lmt = 0, lc = 0, lt = 0;
-    ElemInfo LI{};
-    const float *lpsi = nullptr;   // cursor element's Psi table, point table and V
-    const float *lpt = nullptr, *lv = nullptr;
-    auto cursor_elem = [&]() {
-      LI = elem_info<R>(order, lk, qoff, qpoff, aoff, doff, amax);
-      lpsi = psi + 4 * toff32[LI.e];
-      lpt = ptab + 32 * qpoff[LI.e];
-      lv = vpad + qpoff[LI.e];
-    };
-    if (tid == 0 && lk < nelem_list) cursor_elem();
-    auto advance_cursor = [&]() {
-      for (;;) {
-        if (lk >= nelem_list) return;
-        if (LI.ok) {
-          if (++lc < LI.nch) return;
-          lc = 0;
-          if (++lmt < LI.nmt) return;
-        }
-        lmt = 0;
-        lc = 0;
-        lk += G;
-        if (lk >= nelem_list) return;
-        cursor_elem();
-        if (LI.ok) return;
-      }
-    };
-    auto skip_invalid = [&]() {
-      while (lk < nelem_list && !LI.ok) {
-        lk += G;
-        if (lk < nelem_list) cursor_elem();
-      }
-    };
-    auto issue_load = [&]() {  // inputs of the cursor chunk into buffer lt % WS_NIN
-      const int b = lt % WS_NIN;
-      const int qc = lc * KC;
-      unsigned char *dst = inbuf + b * in_bytes;
-      const uint32_t pbytes = (uint32_t)(LI.A * 4 * KC * 4);
-      mbar_expect_tx(&sh.ibar[b], pbytes + KC * 128 + KC * 4);
-      if (pbytes) bulk_g2s(dst, lpsi + (int64_t)(qc >> 3) * LI.A * 32, pbytes, &sh.ibar[b]);
-      bulk_g2s(dst + pbytes, lpt + 32 * qc, KC * 128, &sh.ibar[b]);
-      bulk_g2s(dst + pbytes + KC * 128, lv + qc, KC * 4, &sh.ibar[b]);
-      ++lt;
-      advance_cursor();
-    };
-    if (tid == 0) {
-      skip_invalid();
-      for (int i = 0; i < WS_NIN - 1 && lk < nelem_list; ++i) issue_load();
-    }
+    // Each warp waits for the chunk's inputs and a free stage on its own and
+    // signals completion with its own arrival, so warps never meet at a
+    // CTA-wide barrier inside the loop and may drift apart by up to the
+    // number of stages.
     int t = 0;
     bool run = true;
     for (int k = blockIdx.x; k < nelem_list && run; k += G) {
@@ -459,54 +437,126 @@ __global__ void __launch_bounds__(WS_NT, 1) k_assemble_tc(
         if (tid == 0) set_err(err, DEVERR_SHAPE);
         continue;
       }
-      const int32_t *ec = ecol + (doff[I.e] - 64ll * I.e);
-      for (int i = tid; i < I.nenr; i += 256) sh.ecs[i] = ec[i];
-      fill_bar();
-      const int *ecs = sh.ecs;
+      if (!I.go) continue;
+      const int32_t *ecs = ecol + (doff[I.e] - 64ll * I.e);
       for (int mt = 0; mt < I.nmt && run; ++mt) {
         for (int c = 0; c < I.nch; ++c, ++t) {
           const int s = t % NSTG, b = t % WS_NIN;
-          const int qc = c * KC;
           unsigned char *sp = stages + s * STG;
           const float *ip = reinterpret_cast<const float *>(inbuf + b * in_bytes);
           const float *pt = ip + I.A * 4 * KC;   // per point: 32 floats
           const float *vq = pt + 32 * KC;        // per point: V
-          if (tid == 0) {
-            bool good = !*(volatile int *)&sh.abort;
-            if (good && t >= NSTG) good = mbar_wait(&sh.sempty[s], ((t / NSTG) - 1) & 1);
+          int good = 1;
+          if (lane == 0) {
+            good = !*(volatile int *)&sh.abort;
             if (good) good = mbar_wait(&sh.ibar[b], (t / WS_NIN) & 1);
-            if (good && lk < nelem_list) issue_load();
+            if (good && t >= NSTG) good = mbar_wait(&sh.sempty[s], ((t / NSTG) - 1) & 1);
             if (!good) {
               set_err(err, DEVERR_TIMEOUT);
               atomicExch(&sh.abort, 1);
             }
-            sh.fill_go = good ? 1 : 0;  // the only writer; read by all after the barrier
           }
-          fill_bar();
-          if (!*(volatile int *)&sh.fill_go) {
+          if (!__shfl_sync(0xffffffffu, good, 0)) {
             run = false;
             break;
           }
-          // rows < npad: each warp writes whole core matrices (8 rows x 4
-          // points): lane -> (row = lane/4, point = lane%4), conflict-free.
-          // A warp owns core matrices warp, warp+8, ... (at most R/32); all
-          // their inputs are read first so the latencies overlap.
-          constexpr int CMW = R / 32;
-          const int ncm = (I.npad / 8) * (KC / 4);
-          float bv[CMW], gxv[CMW], gyv[CMW], gzv[CMW];
+          tc_fence_after();
+          if constexpr (ATMEM) {
+            // thread = basis row r (lane quarter of the warp), 4 of the 8 points
+            const int q4 = warp & 3, ph = warp >> 2;
+            const int r = q4 * 32 + lane;
+            float av[10][4];
+            if (r < 64) {
+              const int ia = r & 3, ib = (r >> 2) & 3, ic = r >> 4;
 #pragma unroll
-          for (int u = 0; u < CMW; ++u) {
-            const int cm = warp + 8 * u;
-            const int rg = cm >> 1, kg = cm & 1;
-            const int cidx = rg * 8 + (lane >> 2);
-            const int qq = kg * 4 + (lane & 3);
-            float b = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
-            if (cm < ncm) {
+              for (int kk = 0; kk < 4; ++kk) {
+                const float *pq = pt + 32 * (4 * ph + kk);
+                const float lx = pq[ia], ly = pq[4 + ib], lz = pq[8 + ic];
+                const float bv = lx * ly * lz;
+                const float gx = pq[12 + ia] * ly * lz;
+                const float gy = lx * pq[16 + ib] * lz;
+                const float gz = lx * ly * pq[20 + ic];
+                const float r2 = pq[27], r1 = pq[28];
+                const float val[5] = {r2 * gx, r2 * gy, r2 * gz, r1 * bv, vq[4 * ph + kk] * (r1 * bv)};
+#pragma unroll
+                for (int tt = 0; tt < 5; ++tt) {
+                  const float hi = tf32_rn(val[tt]);
+                  av[2 * tt][kk] = hi;
+                  av[2 * tt + 1][kk] = tf32_rn(val[tt] - hi);
+                }
+              }
+            } else if (r < I.n) {
+              const int code = ecs[r - 64];
+              const int slot = code >> 3, lv = code & 7;
+              const float4 p0 = *reinterpret_cast<const float4 *>(ip + (slot * 4 + 0) * 8 + 4 * ph);
+              const float4 p1 = *reinterpret_cast<const float4 *>(ip + (slot * 4 + 1) * 8 + 4 * ph);
+              const float4 p2 = *reinterpret_cast<const float4 *>(ip + (slot * 4 + 2) * 8 + 4 * ph);
+              const float4 p3 = *reinterpret_cast<const float4 *>(ip + (slot * 4 + 3) * 8 + 4 * ph);
+              const float ps0[4] = {p0.x, p0.y, p0.z, p0.w}, ps1[4] = {p1.x, p1.y, p1.z, p1.w};
+              const float ps2[4] = {p2.x, p2.y, p2.z, p2.w}, ps3[4] = {p3.x, p3.y, p3.z, p3.w};
+#pragma unroll
+              for (int kk = 0; kk < 4; ++kk) {
+                const float *pq = pt + 32 * (4 * ph + kk);
+                float hh[3], dh[3];
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                  const int bit = (lv >> d) & 1;
+                  const float xv = pq[24 + d];
+                  hh[d] = bit ? 0.5f * (1.0f + xv) : 0.5f * (1.0f - xv);
+                  dh[d] = (bit ? 0.5f : -0.5f) * s3[d];
+                }
+                const float phi = hh[0] * hh[1] * hh[2];
+                const float bv = phi * ps0[kk];
+                const float gx = dh[0] * hh[1] * hh[2] * ps0[kk] + phi * ps1[kk];
+                const float gy = hh[0] * dh[1] * hh[2] * ps0[kk] + phi * ps2[kk];
+                const float gz = hh[0] * hh[1] * dh[2] * ps0[kk] + phi * ps3[kk];
+                const float r2 = pq[27], r1 = pq[28];
+                const float val[5] = {r2 * gx, r2 * gy, r2 * gz, r1 * bv, vq[4 * ph + kk] * (r1 * bv)};
+#pragma unroll
+                for (int tt = 0; tt < 5; ++tt) {
+                  const float hi = tf32_rn(val[tt]);
+                  av[2 * tt][kk] = hi;
+                  av[2 * tt + 1][kk] = tf32_rn(val[tt] - hi);
+                }
+              }
+            } else {
+#pragma unroll
+              for (int tt = 0; tt < 10; ++tt)
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) av[tt][kk] = 0.0f;
+            }
+            const uint32_t abase = tmem + ((uint32_t)(q4 * 32) << 16) + A_COL + s * 80 + 4 * ph;
+#pragma unroll
+            for (int tt = 0; tt < 10; ++tt)
+              tmem_st4(abase + tt * 8, av[tt][0], av[tt][1], av[tt][2], av[tt][3]);
+            const int rb = r - 64;
+            if (rb >= 0 && rb < I.nenr16) {
+              const uint32_t off = (uint32_t)(rb >> 3) * SBO + (uint32_t)ph * LBO + (uint32_t)(rb & 7) * 16;
+#pragma unroll
+              for (int tt = 0; tt < 8; ++tt)
+                *reinterpret_cast<float4 *>(sp + tt * TILE + off) =
+                    make_float4(av[tt][0], av[tt][1], av[tt][2], av[tt][3]);
+            }
+            tmem_wait_st();
+            tc_fence_before();
+          } else {
+            // 256-row tile: every operand in shared memory, core matrices of
+            // 8 rows x 4 points, lane -> (row = lane/4, point = lane%4)
+            constexpr int CMW = R / 32;
+            const int ncm = (I.npad / 8) * (KC / 4);
+#pragma unroll
+            for (int u = 0; u < CMW; ++u) {
+              const int cm = warp + 8 * u;
+              if (cm >= ncm) break;
+              const int rg = cm >> 1, kg = cm & 1;
+              const int cidx = rg * 8 + (lane >> 2);
+              const int qq = kg * 4 + (lane & 3);
               const float *pq = pt + 32 * qq;
+              float bv = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
               if (cidx < 64) {
                 const int ia = cidx & 3, ib = (cidx >> 2) & 3, ic = cidx >> 4;
                 const float lx = pq[ia], ly = pq[4 + ib], lz = pq[8 + ic];
-                b = lx * ly * lz;
+                bv = lx * ly * lz;
                 gx = pq[12 + ia] * ly * lz;
                 gy = lx * pq[16 + ib] * lz;
                 gz = lx * ly * pq[20 + ic];
@@ -524,40 +574,27 @@ __global__ void __launch_bounds__(WS_NT, 1) k_assemble_tc(
                   dh[d] = (bit ? 0.5f : -0.5f) * s3[d];
                 }
                 const float phi = hh[0] * hh[1] * hh[2];
-                b = phi * p0;
+                bv = phi * p0;
                 gx = dh[0] * hh[1] * hh[2] * p0 + phi * p1;
                 gy = hh[0] * dh[1] * hh[2] * p0 + phi * p2;
                 gz = hh[0] * hh[1] * dh[2] * p0 + phi * p3;
               }
-            }
-            bv[u] = b;
-            gxv[u] = gx;
-            gyv[u] = gy;
-            gzv[u] = gz;
-          }
+              const float r2 = pq[27], r1 = pq[28];
+              const float val[5] = {r2 * gx, r2 * gy, r2 * gz, r1 * bv, vq[qq] * (r1 * bv)};
+              const uint32_t off = (uint32_t)rg * SBO + (uint32_t)kg * LBO + (uint32_t)lane * 4;
 #pragma unroll
-          for (int u = 0; u < CMW; ++u) {
-            const int cm = warp + 8 * u;
-            if (cm >= ncm) break;
-            const int rg = cm >> 1, kg = cm & 1;
-            const int qq = kg * 4 + (lane & 3);
-            const float r2 = pt[32 * qq + 27], r1 = pt[32 * qq + 28];
-            const float val[5] = {r2 * gxv[u], r2 * gyv[u], r2 * gzv[u], r1 * bv[u],
-                                  vq[qq] * (r1 * bv[u])};
-            const uint32_t off = (uint32_t)rg * SBO + (uint32_t)kg * LBO + (uint32_t)lane * 4;
-#pragma unroll
-            for (int tt = 0; tt < 5; ++tt) {
-              const float hi = tf32_rn(val[tt]);
-              const float lo = tf32_rn(val[tt] - hi);
-              *reinterpret_cast<float *>(sp + (2 * tt) * TILE + off) = hi;
-              *reinterpret_cast<float *>(sp + (2 * tt + 1) * TILE + off) = lo;
+              for (int tt = 0; tt < 5; ++tt) {
+                const float hi = tf32_rn(val[tt]);
+                *reinterpret_cast<float *>(sp + (2 * tt) * TILE + off) = hi;
+                *reinterpret_cast<float *>(sp + (2 * tt + 1) * TILE + off) = tf32_rn(val[tt] - hi);
+              }
             }
           }
           fence_proxy_async();
-          fill_bar();
-          if (tid == 0) {
-            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&sh.sfull[s]))
-                         : "memory");
+          __syncwarp();
+          if (lane == 0) {
+            mbar_arrive(&sh.sfull[s]);
+            mbar_arrive(&sh.ifree[b]);
           }
         }
       }
@@ -570,9 +607,8 @@ __global__ void __launch_bounds__(WS_NT, 1) k_assemble_tc(
       bool run = true;
       for (int k = blockIdx.x; k < nelem_list && run; k += G) {
         const ElemInfo I = elem_info<R>(order, k, qoff, qpoff, aoff, doff, amax);
-        if (!I.ok) continue;
-        const uint32_t idH = idesc_tf32(128, I.npad);
-        const uint32_t idE = idesc_tf32(128, I.nenr16 > 0 ? I.nenr16 : 16);
+        if (!I.go) continue;
+        const uint32_t idE = idesc_tf32(128, I.nenr16);
         const uint32_t tH = tmem, tHx = tmem + HX_COL, tS = tmem + S_COL, tSx = tmem + SX_COL;
         for (int mt = 0; mt < I.nmt && run; ++mt, ++a) {
           if (a > 0 && !mbar_wait(&sh.aempty, (a - 1) & 1)) {
@@ -580,8 +616,6 @@ __global__ void __launch_bounds__(WS_NT, 1) k_assemble_tc(
             break;
           }
           tc_fence_after();
-          const uint32_t moff = (uint32_t)mt * 16u * SBO;
-          const uint32_t eoff = 8u * SBO;
           for (int c = 0; c < I.nch; ++c, ++t) {
             const int s = t % NSTG;
             if (*(volatile int *)&sh.abort || !mbar_wait(&sh.sfull[s], (t / NSTG) & 1)) {
@@ -591,20 +625,40 @@ __global__ void __launch_bounds__(WS_NT, 1) k_assemble_tc(
             tc_fence_after();
             const uint32_t st = sbase + s * STG;
             const uint32_t first = (c == 0) ? 0u : 1u;
-            auto D = [&](int tt, uint32_t extra) { return sdesc(st + tt * TILE + extra, LBO, SBO); };
             const uint32_t fx = SPLIT ? first : 1u;
-            mma_tf32(tH, D(8, moff), D(6, 0), idH, first);
-            mma_tf32(tHx, D(8, moff), D(7, 0), idH, fx);
-            mma_tf32(tHx, D(9, moff), D(6, 0), idH, 1u);
-            if (I.nenr > 0) {
+            if constexpr (ATMEM) {
+              auto Bd = [&](int tt) { return sdesc(st + tt * TILE, LBO, SBO); };
+              const uint32_t aS = tmem + A_COL + s * 80;
+              // H_V on the enrichment columns: ZV^T Z[64:]
+              mma_tf32_ta(tH, aS + 8 * 8, Bd(6), idE, first);
+              mma_tf32_ta(tHx, aS + 8 * 8, Bd(7), idE, fx);
+              mma_tf32_ta(tHx, aS + 9 * 8, Bd(6), idE, 1u);
+              // T on the enrichment columns: sum_d Y_d^T Y_d[64:]
 #pragma unroll
               for (int d = 0; d < 3; ++d) {
-                mma_tf32(tH + 64, D(2 * d, moff), D(2 * d, eoff), idE, 1u);
-                mma_tf32(tHx + 64, D(2 * d, moff), D(2 * d + 1, eoff), idE, 1u);
-                mma_tf32(tHx + 64, D(2 * d + 1, moff), D(2 * d, eoff), idE, 1u);
+                mma_tf32_ta(tH, aS + (2 * d) * 8, Bd(2 * d), idE, 1u);
+                mma_tf32_ta(tHx, aS + (2 * d) * 8, Bd(2 * d + 1), idE, 1u);
+                mma_tf32_ta(tHx, aS + (2 * d + 1) * 8, Bd(2 * d), idE, 1u);
+              }
+              // S on the enrichment columns: Z^T Z[64:]
+              mma_tf32_ta(tS, aS + 6 * 8, Bd(6), idE, first);
+              mma_tf32_ta(tSx, aS + 6 * 8, Bd(7), idE, fx);
+              mma_tf32_ta(tSx, aS + 7 * 8, Bd(6), idE, 1u);
+            } else {
+              const uint32_t moff = (uint32_t)mt * 16u * SBO;   // M-tile: 128 rows
+              const uint32_t eoff = 8u * SBO;                   // enrichment rows start at 64
+              auto D = [&](int tt, uint32_t extra) { return sdesc(st + tt * TILE + extra, LBO, SBO); };
+              mma_tf32(tH, D(8, moff), D(6, eoff), idE, first);
+              mma_tf32(tHx, D(8, moff), D(7, eoff), idE, fx);
+              mma_tf32(tHx, D(9, moff), D(6, eoff), idE, 1u);
+#pragma unroll
+              for (int d = 0; d < 3; ++d) {
+                mma_tf32(tH, D(2 * d, moff), D(2 * d, eoff), idE, 1u);
+                mma_tf32(tHx, D(2 * d, moff), D(2 * d + 1, eoff), idE, 1u);
+                mma_tf32(tHx, D(2 * d + 1, moff), D(2 * d, eoff), idE, 1u);
               }
               mma_tf32(tS, D(6, moff), D(6, eoff), idE, first);
-              mma_tf32(tSx, D(6, moff), D(7, eoff), idE, SPLIT ? first : 1u);
+              mma_tf32(tSx, D(6, moff), D(7, eoff), idE, fx);
               mma_tf32(tSx, D(7, moff), D(6, eoff), idE, 1u);
             }
             mma_commit(&sh.sempty[s]);
@@ -619,7 +673,7 @@ __global__ void __launch_bounds__(WS_NT, 1) k_assemble_tc(
       }
     }
     __syncwarp();
-  } else {
+  } else if (warp < WS_LOAD_WARP) {
     // ======================= epilogue warps =======================
     const int quarter = warp & 3;
     const int ew = warp - WS_EPI_WARP0;
@@ -627,25 +681,22 @@ __global__ void __launch_bounds__(WS_NT, 1) k_assemble_tc(
     float2(*stg)[17] = epi[ew];
     int a = 0;
     bool run = true;
-    // Scatter one 32-row x 16-column block of owned pairs (r, c) into both
-    // CSR slots, in two passes that each keep a warp's slots together:
-    // direct slots (r, c): half-warp h takes row 2*it + h, lanes run along 16
-    // consecutive columns; mirror slots (c, r): lane = row, loop over the 16
-    // columns.  All slot loads of a pass are issued before its atomics.
-    auto owned = [&](int r, int cc, int n, bool is_s) {
-      bool ok = r < n && cc < n;
-      if (ok) ok = (cc < 64) ? (cc <= r && r < 64) : (r < 64 || cc <= r);
-      if (ok && is_s) ok = cc >= 64;
-      return ok;
-    };
-    auto scatter_block = [&](const int32_t *m, int n, int rbase, int cb, bool is_s, double *out,
+    // Scatter one 32-row x 16-column block of the strip (columns cc = 64 +
+    // 16 cb + i, all enrichment columns) into both CSR slots of every owned
+    // pair: (r, cc) is owned when r < 64 (FE row) or cc <= r.  Two passes,
+    // each keeping a warp's slots together: direct slots (r, cc): half-warp
+    // h takes row 2 it + h, lanes run along 16 consecutive columns; mirror
+    // slots (cc, r): lane = row, loop over the 16 columns.  All slot loads of
+    // a pass are issued before its atomics.
+    auto owned = [&](int r, int cc, int n) { return r < n && cc < n && (r < 64 || cc <= r); };
+    auto scatter_block = [&](const int32_t *m, int n, int rbase, int cb, double *out,
                              auto value_of) {
       int sd[16];
 #pragma unroll
       for (int it = 0; it < 16; ++it) {
         const int rl = 2 * it + (lane >> 4);
-        const int r = rbase + rl, cc = cb * 16 + (lane & 15);
-        sd[it] = owned(r, cc, n, is_s) ? m[(int64_t)r * n + cc] : -1;
+        const int r = rbase + rl, cc = 64 + cb * 16 + (lane & 15);
+        sd[it] = owned(r, cc, n) ? m[(int64_t)r * n + cc] : -1;
       }
 #pragma unroll
       for (int it = 0; it < 16; ++it)
@@ -653,8 +704,8 @@ __global__ void __launch_bounds__(WS_NT, 1) k_assemble_tc(
       const int r = rbase + lane;
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
-        const int cc = cb * 16 + i;
-        sd[i] = (cc != r && owned(r, cc, n, is_s)) ? m[(int64_t)cc * n + r] : -1;
+        const int cc = 64 + cb * 16 + i;
+        sd[i] = (cc != r && owned(r, cc, n)) ? m[(int64_t)cc * n + r] : -1;
       }
 #pragma unroll
       for (int i = 0; i < 16; ++i)
@@ -662,9 +713,10 @@ __global__ void __launch_bounds__(WS_NT, 1) k_assemble_tc(
     };
     for (int k = blockIdx.x; k < nelem_list && run; k += G) {
       const ElemInfo I = elem_info<R>(order, k, qoff, qpoff, aoff, doff, amax);
-      if (!I.ok) continue;
+      if (!I.go) continue;
       const int32_t *m = smap + soff[I.e];
       const int n = I.n;
+      const int ncb = I.nenr16 / 16;
       for (int mt = 0; mt < I.nmt; ++mt, ++a) {
         int good = 1;
         if (lane == 0) good = (!*(volatile int *)&sh.abort && mbar_wait(&sh.afull, a & 1)) ? 1 : 0;
@@ -676,68 +728,93 @@ __global__ void __launch_bounds__(WS_NT, 1) k_assemble_tc(
         tc_fence_after();
         const int rbase = mt * 128 + quarter * 32;
         if constexpr (STAGED) {
-          // drain this warp's 32 rows: H columns [0, npad), then S columns
+          // drain this warp's 32 rows: H strip, then S strip (FP32 sums of
+          // the hi*hi and cross accumulators)
           float *row = staging + (quarter * 32 + lane) * SROW;
-          for (int cb = 0; cb * 16 < I.npad; ++cb) {
+          for (int cb = 0; cb < ncb; ++cb) {
             float hv[16], hx[16];
             tmem_ld16(tmem + lanebase + cb * 16, hv);
             tmem_ld16(tmem + HX_COL + lanebase + cb * 16, hx);
 #pragma unroll
             for (int i = 0; i < 16; ++i) row[cb * 16 + i] = hv[i] + hx[i];
-          }
-          for (int cb = 0; cb * 16 < I.nenr16; ++cb) {
-            float hv[16], hx[16];
             tmem_ld16(tmem + S_COL + lanebase + cb * 16, hv);
             tmem_ld16(tmem + SX_COL + lanebase + cb * 16, hx);
 #pragma unroll
-            for (int i = 0; i < 16; ++i) row[I.npad + cb * 16 + i] = hv[i] + hx[i];
+            for (int i = 0; i < 16; ++i) row[I.nenr16 + cb * 16 + i] = hv[i] + hx[i];
           }
           tc_fence_before();
           __syncwarp();
-          if (lane == 0)
-            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&sh.aempty))
-                         : "memory");
+          if (lane == 0) mbar_arrive(&sh.aempty);
           // scatter from shared memory while the next element's MMAs run
           const float *blk = staging + (quarter * 32) * SROW;
-          for (int cb = 0; cb * 16 < I.npad; ++cb) {
+          for (int cb = 0; cb < ncb; ++cb) {
             if (want & PUFE_WANT_H)
-              scatter_block(m, n, rbase, cb, false, H, [&](int rl, int cl) {
+              scatter_block(m, n, rbase, cb, H, [&](int rl, int cl) {
                 return (double)blk[rl * SROW + cb * 16 + cl];
               });
-            if ((want & PUFE_WANT_S) && cb * 16 >= 64 && I.nenr > 0)
-              scatter_block(m, n, rbase, cb, true, S, [&](int rl, int cl) {
-                return (double)blk[rl * SROW + I.npad + cb * 16 - 64 + cl];
+            if (want & PUFE_WANT_S)
+              scatter_block(m, n, rbase, cb, S, [&](int rl, int cl) {
+                return (double)blk[rl * SROW + I.nenr16 + cb * 16 + cl];
               });
           }
           __syncwarp();
         } else {
-          for (int cb = 0; cb * 16 < I.npad; ++cb) {
-            const bool enr_blk = cb * 16 >= 64;
-            for (int which = 0; which < ((enr_blk && I.nenr > 0) ? 2 : 1); ++which) {
-              if (which == 1 && !(want & PUFE_WANT_S)) continue;
+          for (int cb = 0; cb < ncb; ++cb) {
+            for (int which = 0; which < 2; ++which) {
               if (which == 0 && !(want & PUFE_WANT_H)) continue;
-              float hv[16], hx[16];
-              const uint32_t c0 = which == 0 ? (uint32_t)(cb * 16) : (uint32_t)(cb * 16 - 64);
-              tmem_ld16((which == 0 ? tmem : tmem + S_COL) + lanebase + c0, hv);
-              if (SPLIT) tmem_ld16((which == 0 ? tmem + HX_COL : tmem + SX_COL) + lanebase + c0, hx);
+              if (which == 1 && !(want & PUFE_WANT_S)) continue;
+              float hv[16];
+              tmem_ld16((which == 0 ? tmem : tmem + S_COL) + lanebase + cb * 16, hv);
 #pragma unroll
-              for (int i = 0; i < 16; ++i) stg[lane][i] = make_float2(hv[i], SPLIT ? hx[i] : 0.0f);
+              for (int i = 0; i < 16; ++i) stg[lane][i] = make_float2(hv[i], 0.0f);
               __syncwarp();
-              scatter_block(m, n, rbase, cb, which == 1, which == 0 ? H : S, [&](int rl, int cl) {
-                const float2 v2 = stg[rl][cl];
-                return (double)v2.x + (double)v2.y;
+              scatter_block(m, n, rbase, cb, which == 0 ? H : S, [&](int rl, int cl) {
+                return (double)stg[rl][cl].x;
               });
               __syncwarp();
             }
           }
           tc_fence_before();
           __syncwarp();
-          if (lane == 0)
-            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&sh.aempty))
-                         : "memory");
+          if (lane == 0) mbar_arrive(&sh.aempty);
         }
       }
     }
+  } else {
+    // ======================= loader warp =======================
+    if (lane == 0) {
+      int lt = 0;
+      bool run = true;
+      for (int k = blockIdx.x; k < nelem_list && run; k += G) {
+        const ElemInfo I = elem_info<R>(order, k, qoff, qpoff, aoff, doff, amax);
+        if (!I.go) continue;
+        const float *lpsi = psi + 4 * toff32[I.e];
+        const float *lpt = ptab + 32 * qpoff[I.e];
+        const float *lv = vpad + qpoff[I.e];
+        const uint32_t pbytes = (uint32_t)(I.A * 4 * KC * 4);
+        for (int mt = 0; mt < I.nmt && run; ++mt) {
+          for (int c = 0; c < I.nch; ++c, ++lt) {
+            const int b = lt % WS_NIN;
+            if (*(volatile int *)&sh.abort ||
+                (lt >= WS_NIN && !mbar_wait(&sh.ifree[b], ((lt / WS_NIN) - 1) & 1))) {
+              run = false;
+              break;
+            }
+            const int qc = c * KC;
+            unsigned char *dst = inbuf + b * in_bytes;
+            mbar_expect_tx(&sh.ibar[b], pbytes + KC * 128 + KC * 4);
+            if (pbytes) bulk_g2s(dst, lpsi + (int64_t)(qc >> 3) * I.A * 32, pbytes, &sh.ibar[b]);
+            bulk_g2s(dst + pbytes, lpt + 32 * qc, KC * 128, &sh.ibar[b]);
+            bulk_g2s(dst + pbytes + KC * 128, lv + qc, KC * 4, &sh.ibar[b]);
+          }
+        }
+      }
+      if (!run) {
+        set_err(err, DEVERR_TIMEOUT);
+        atomicExch(&sh.abort, 1);
+      }
+    }
+    __syncwarp();
   }
 
   // ---- teardown -------------------------------------------------------------
@@ -747,6 +824,13 @@ __global__ void __launch_bounds__(WS_NT, 1) k_assemble_tc(
     tc_fence_after();
     tmem_dealloc(tmem, TCOLS);
   }
+}
+
+// shared-memory bytes of one k_assemble_tc launch
+static size_t assemble_smem(int R, int in_bytes) {
+  const size_t stage = (R == 128) ? 3 * (size_t)(8 * 64 * WS_KC * 4) : 2 * (size_t)(NTILES * 256 * WS_KC * 4);
+  const size_t tail = (R == 128) ? (size_t)128 * 129 * 4 : (size_t)4 * 32 * 17 * 8;
+  return (size_t)1024 + stage + WS_NIN * (size_t)in_bytes + sizeof(WsShared) + tail;
 }
 
 // ---------------------------------------------------------------------------
@@ -1183,62 +1267,60 @@ pufe_status launch_tabulate_f32(pufe_ctx *ctx, cudaStream_t st) {
   return PUFE_OK;
 }
 
-pufe_status launch_assemble_tc(pufe_ctx *ctx, const double *V, int what, double *H, double *S,
-                               cudaStream_t st) {
+// H/S assembly on the mixed path: H = T0 + sum-factorized FE-FE V term,
+// S = S0, then the tensor-core enrichment strip; `vscratch` receives the FP32
+// copy of V that the strip kernel reads (nq_pad floats).
+static pufe_status run_assemble_tc(pufe_ctx *ctx, const double *V, int what, double *H,
+                                   double *S, float *vscratch, cudaStream_t st) {
   auto &D = ctx->d;
   if (!ctx->fe_exact)
     return fail(PUFE_EINVAL,
                 "PUFE_TF32X3 needs every (sub)cell rule to have >= 4 points per axis");
   if (ctx->max_basis > 256) return fail(PUFE_EINVAL, "PUFE_TF32X3 supports n_e <= 256");
-  // constant FE-FE blocks: start from the precomputed global T0 / S0
-  const size_t bytes = (size_t)ctx->nnz * sizeof(double);
-  if (what & PUFE_WANT_H) PUFE_CUDA_TRY(cudaMemcpyAsync(H, D.T0, bytes, cudaMemcpyDeviceToDevice, st));
-  if (what & PUFE_WANT_S) PUFE_CUDA_TRY(cudaMemcpyAsync(S, D.S0, bytes, cudaMemcpyDeviceToDevice, st));
-  const float sx = (float)(2.0 / ctx->h[0]), sy = (float)(2.0 / ctx->h[1]),
-              sz = (float)(2.0 / ctx->h[2]);
   const int amax = std::max(1, ctx->max_alpha);
   const int inb = ((amax * 4 * WS_KC * 4 + WS_KC * 128 + WS_KC * 4) + 127) & ~127;
+  const size_t sm128 = assemble_smem(128, inb), sm256 = assemble_smem(256, inb);
+  const int nbig = ctx->n_big;
+  const int nsmall = (int)ctx->nelem - nbig;
+  if ((nbig > 0 && sm256 > 227 * 1024) || (nsmall > 0 && sm128 > 227 * 1024))
+    return fail(PUFE_EINVAL, "too many enrichments per element for TF32X3");
+  const size_t bytes = (size_t)ctx->nnz * sizeof(double);
   if (what & PUFE_WANT_H) {
-    k_pack_v<<<(unsigned)ctx->nelem, 256, 0, st>>>(D.qoff, D.qpoff, V, D.vpad);
-    PUFE_CUDA_TRY(cudaGetLastError());
-  } else {
-    PUFE_CUDA_TRY(cudaMemsetAsync(D.vpad, 0, (size_t)ctx->nq_pad * sizeof(float), st));
+    pufe_status e0 = launch_fefe(ctx, V, H, st);
+    if (e0 != PUFE_OK) return e0;
   }
-  // 128-row tile: 2 stages of 40 KB + 128 x 193 FP32 staging; 256-row: 2 x 80 KB
-  // + per-warp transpose buffers
-  const size_t sm128 = (size_t)1024 + 2 * 40960 + WS_NIN * (size_t)inb + sizeof(WsShared) +
-                       (size_t)128 * 193 * 4;
-  const size_t sm256 = (size_t)1024 + 2 * 81920 + WS_NIN * (size_t)inb + sizeof(WsShared) +
-                       (size_t)4 * 32 * 17 * 8;
+  if (what & PUFE_WANT_S) PUFE_CUDA_TRY(cudaMemcpyAsync(S, D.S0, bytes, cudaMemcpyDeviceToDevice, st));
+  // every entry the strip kernel reads is rewritten (zeros on padding)
+  k_pack_v<<<(unsigned)ctx->nelem, 256, 0, st>>>(D.qoff, D.qpoff, (what & PUFE_WANT_H) ? V : nullptr,
+                                                vscratch);
+  PUFE_CUDA_TRY(cudaGetLastError());
+  const float sx = (float)(2.0 / ctx->h[0]), sy = (float)(2.0 / ctx->h[1]),
+              sz = (float)(2.0 / ctx->h[2]);
   int nsm = 0;
   PUFE_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device));
   // elements are ordered with n_e > 128 first (256-row tile), then the rest
-  const int nbig = ctx->n_big;
   if (nbig > 0) {
-    const size_t sm = sm256;
-    if (sm > 227 * 1024) return fail(PUFE_EINVAL, "too many enrichments per element for TF32X3");
     PUFE_CUDA_TRY(cudaFuncSetAttribute(k_assemble_tc<256>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    const int grid = std::min(nbig, nsm);
-    k_assemble_tc<256><<<grid, WS_NT, sm, st>>>(D.order, D.qoff, D.qpoff, D.ptab, D.vpad, D.doff, D.ecol,
-                                                D.aoff, D.toff32, D.psi32, D.soff, D.smap, V, sx,
-                                                sy, sz, nbig, amax, inb, what, H, S, D.err);
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm256));
+    k_assemble_tc<256><<<std::min(nbig, nsm), WS_NT, sm256, st>>>(
+        D.order, D.qoff, D.qpoff, D.ptab, vscratch, D.doff, D.ecol, D.aoff, D.toff32, D.psi32,
+        D.soff, D.smap, sx, sy, sz, nbig, amax, inb, what, H, S, D.err);
     PUFE_CUDA_TRY(cudaGetLastError());
   }
-  const int nsmall = (int)ctx->nelem - nbig;
   if (nsmall > 0) {
-    const size_t sm = sm128;
-    if (sm > 227 * 1024) return fail(PUFE_EINVAL, "too many enrichments per element for TF32X3");
     PUFE_CUDA_TRY(cudaFuncSetAttribute(k_assemble_tc<128>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    const int grid = std::min(nsmall, nsm);
-    k_assemble_tc<128><<<grid, WS_NT, sm, st>>>(D.order + nbig, D.qoff, D.qpoff, D.ptab, D.vpad, D.doff,
-                                                D.ecol, D.aoff, D.toff32, D.psi32, D.soff,
-                                                D.smap, V, sx, sy, sz, nsmall, amax, inb, what, H,
-                                                S, D.err);
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm128));
+    k_assemble_tc<128><<<std::min(nsmall, nsm), WS_NT, sm128, st>>>(
+        D.order + nbig, D.qoff, D.qpoff, D.ptab, vscratch, D.doff, D.ecol, D.aoff, D.toff32,
+        D.psi32, D.soff, D.smap, sx, sy, sz, nsmall, amax, inb, what, H, S, D.err);
     PUFE_CUDA_TRY(cudaGetLastError());
   }
   return PUFE_OK;
+}
+
+pufe_status launch_assemble_tc(pufe_ctx *ctx, const double *V, int what, double *H, double *S,
+                               cudaStream_t st) {
+  return run_assemble_tc(ctx, V, what, H, S, ctx->d.vpad, st);
 }
 
 pufe_status launch_density_tc(pufe_ctx *ctx, const double *C, int64_t ldc, const double *f,
@@ -1327,11 +1409,6 @@ static pufe_status static_scratch(int device, float **out) {
 
 pufe_status launch_assemble_tc_static(pufe_ctx *ctx, const double *V, int what, double *H,
                                       double *S, cudaStream_t st) {
-  auto &D = ctx->d;
-  if (!ctx->fe_exact)
-    return fail(PUFE_EINVAL,
-                "PUFE_TF32X3 needs every (sub)cell rule to have >= 4 points per axis");
-  if (ctx->max_basis > 256) return fail(PUFE_EINVAL, "PUFE_TF32X3 supports n_e <= 256");
   if (ctx->nq_pad > PUFE_STATIC_MAX_POINTS)
     return fail(PUFE_EINVAL, "pufe_assemble_HS_static: the context has " +
                                  std::to_string(ctx->nq_pad) +
@@ -1339,45 +1416,7 @@ pufe_status launch_assemble_tc_static(pufe_ctx *ctx, const double *V, int what, 
                                  std::to_string(PUFE_STATIC_MAX_POINTS));
   float *vs = nullptr;
   if (pufe_status e0 = static_scratch(ctx->device, &vs)) return e0;
-  const size_t bytes = (size_t)ctx->nnz * sizeof(double);
-  if (what & PUFE_WANT_H) PUFE_CUDA_TRY(cudaMemcpyAsync(H, D.T0, bytes, cudaMemcpyDeviceToDevice, st));
-  if (what & PUFE_WANT_S) PUFE_CUDA_TRY(cudaMemcpyAsync(S, D.S0, bytes, cudaMemcpyDeviceToDevice, st));
-  const float sx = (float)(2.0 / ctx->h[0]), sy = (float)(2.0 / ctx->h[1]),
-              sz = (float)(2.0 / ctx->h[2]);
-  const int amax = std::max(1, ctx->max_alpha);
-  const int inb = ((amax * 4 * WS_KC * 4 + WS_KC * 128 + WS_KC * 4) + 127) & ~127;
-  // the array keeps the previous call's values: every entry this call reads
-  // (including the zero padding) is rewritten first
-  k_pack_v<<<(unsigned)ctx->nelem, 256, 0, st>>>(D.qoff, D.qpoff, (what & PUFE_WANT_H) ? V : nullptr,
-                                                vs);
-  PUFE_CUDA_TRY(cudaGetLastError());
-  const size_t sm128 = (size_t)1024 + 2 * 40960 + WS_NIN * (size_t)inb + sizeof(WsShared) +
-                       (size_t)128 * 193 * 4;
-  const size_t sm256 = (size_t)1024 + 2 * 81920 + WS_NIN * (size_t)inb + sizeof(WsShared) +
-                       (size_t)4 * 32 * 17 * 8;
-  int nsm = 0;
-  PUFE_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device));
-  const int nbig = ctx->n_big;
-  if (nbig > 0) {
-    if (sm256 > 227 * 1024) return fail(PUFE_EINVAL, "too many enrichments per element for TF32X3");
-    PUFE_CUDA_TRY(cudaFuncSetAttribute(k_assemble_tc<256>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm256));
-    k_assemble_tc<256><<<std::min(nbig, nsm), WS_NT, sm256, st>>>(
-        D.order, D.qoff, D.qpoff, D.ptab, vs, D.doff, D.ecol, D.aoff, D.toff32, D.psi32, D.soff,
-        D.smap, V, sx, sy, sz, nbig, amax, inb, what, H, S, D.err);
-    PUFE_CUDA_TRY(cudaGetLastError());
-  }
-  const int nsmall = (int)ctx->nelem - nbig;
-  if (nsmall > 0) {
-    if (sm128 > 227 * 1024) return fail(PUFE_EINVAL, "too many enrichments per element for TF32X3");
-    PUFE_CUDA_TRY(cudaFuncSetAttribute(k_assemble_tc<128>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm128));
-    k_assemble_tc<128><<<std::min(nsmall, nsm), WS_NT, sm128, st>>>(
-        D.order + nbig, D.qoff, D.qpoff, D.ptab, vs, D.doff, D.ecol, D.aoff, D.toff32, D.psi32,
-        D.soff, D.smap, V, sx, sy, sz, nsmall, amax, inb, what, H, S, D.err);
-    PUFE_CUDA_TRY(cudaGetLastError());
-  }
-  return PUFE_OK;
+  return run_assemble_tc(ctx, V, what, H, S, vs, st);
 }
 
 }  // namespace pufe
