@@ -10,10 +10,11 @@
 // element contraction.  (Sec. 4 eq. disceig3d, local potential term; the rule
 // is the element's shared rule of Sec. 5.2.)
 //
-// k_h_init then writes every CSR value of H: the precomputed constant kinetic
-// FE-FE sum T0 plus, for FE-FE slots, the sum of M over the (at most 8)
-// elements that contain both nodes.  Enrichment slots start at T0 = 0; the
-// tensor-core strip kernel adds their values afterwards.
+// H starts as the precomputed constant kinetic FE-FE sum T0; each element then
+// adds its 64 x 64 block of M through the scatter map.  Enrichment slots start
+// at T0 = 0; the tensor-core strip kernel adds their values afterwards.
+#include <algorithm>
+
 #include "pufe_internal.h"
 
 namespace pufe {
@@ -39,7 +40,8 @@ __global__ void __launch_bounds__(SF_NT) k_fefe_sumfac(
     const int64_t *__restrict__ qoff, const double *__restrict__ w, const double *__restrict__ V,
     const double *__restrict__ xi_all, const int32_t *__restrict__ partoff,
     const int32_t *__restrict__ part_p, const int32_t *__restrict__ part_q,
-    float *__restrict__ mfe, unsigned *err) {
+    const int64_t *__restrict__ doff, const int64_t *__restrict__ soff,
+    const int32_t *__restrict__ smap, double *__restrict__ H, unsigned *err) {
   __shared__ float Wq[SF_PMAX * SF_PMAX * SF_PMAX];
   __shared__ float P[3][10][SF_PMAX];          // pair products per axis
   __shared__ float G1[SF_PMAX * SF_PMAX * 10];  // [qx + p qy][cc]
@@ -89,62 +91,93 @@ __global__ void __launch_bounds__(SF_NT) k_fefe_sumfac(
     }
   }
   __syncthreads();
-  for (int o = tid; o < 1000; o += SF_NT) mfe[(int64_t)e * 1000 + o] = M[o];
+  // add the 64 x 64 block into H through the scatter map: thread pairs
+  // (i, j) run along j, so consecutive lanes hit neighbouring CSR columns
+  const int n = (int)(doff[e + 1] - doff[e]);
+  const int32_t *m = smap + soff[e];
+  for (int o = tid; o < 64 * 64; o += SF_NT) {
+    const int i = o >> 6, j = o & 63;
+    const float v = M[pidx(i & 3, j & 3) * 100 + pidx((i >> 2) & 3, (j >> 2) & 3) * 10 +
+                      pidx(i >> 4, j >> 4)];
+    atomicAdd(H + m[i * n + j], (double)v);
+  }
 }
 
-// the (element index, local node index) pairs of a node coordinate along one
-// axis (a vertex node belongs to two elements; with one element per axis the
-// node appears twice in it)
-__device__ __forceinline__ int node_elems(int x, int nel, int ex[2], int a[2]) {
-  ex[0] = x / 3;
-  a[0] = x - 3 * ex[0];
-  if (a[0] != 0) return 1;
-  ex[1] = (ex[0] - 1 + nel) % nel;
-  a[1] = 3;
-  return 2;
-}
-
-__device__ __forceinline__ int axis_matches(int x1, int x2, int nel, int ex[4], int pr[4]) {
-  int e1[2], a1[2], e2[2], a2[2];
-  const int c1 = node_elems(x1, nel, e1, a1), c2 = node_elems(x2, nel, e2, a2);
-  int c = 0;
-  for (int i = 0; i < c1; ++i)
-    for (int j = 0; j < c2; ++j)
-      if (e1[i] == e2[j]) {
-        ex[c] = e1[i];
-        pr[c] = pidx(a1[i], a2[j]);
-        ++c;
-      }
-  return c;
-}
-
-__global__ void k_h_init(int64_t nrow, int64_t n_fe, int nx, int ny, int nz,
-                         const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
-                         const double *__restrict__ T0, const float *__restrict__ mfe,
-                         double *__restrict__ H) {
-  const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (row >= nrow) return;
-  const int mx = 3 * nx, my = 3 * ny;
-  const bool fe_row = row < n_fe;
-  const int x1 = (int)(row % mx), y1 = (int)((row / mx) % my), z1 = (int)(row / ((int64_t)mx * my));
-  for (int64_t k = rowptr[row] + lane; k < rowptr[row + 1]; k += 32) {
-    double v = T0[k];
-    const int g2 = col[k];
-    if (fe_row && g2 < n_fe) {
-      const int x2 = g2 % mx, y2 = (g2 / mx) % my, z2 = g2 / (mx * my);
-      int exs[4], pxs[4], eys[4], pys[4], ezs[4], pzs[4];
-      const int cx = axis_matches(x1, x2, nx, exs, pxs);
-      const int cy = axis_matches(y1, y2, ny, eys, pys);
-      const int cz = axis_matches(z1, z2, nz, ezs, pzs);
-      for (int i = 0; i < cx; ++i)
-        for (int j = 0; j < cy; ++j)
-          for (int l = 0; l < cz; ++l) {
-            const int64_t e = exs[i] + (int64_t)nx * (eys[j] + (int64_t)ny * ezs[l]);
-            v += (double)mfe[e * 1000 + pxs[i] * 100 + pys[j] * 10 + pzs[l]];
-          }
+// FE-FE part of the adjoint of V -> H on a tensor-product (sub)cell:
+//   f(q) = sum_{(abc),(a'b'c')} L_a L_a' L_b L_b' L_c L_c' Hbar[(abc),(a'b'c')]
+// (Hbar restricted to the element's 64 FE columns, general, not symmetric),
+// contracted axis by axis: 4096 p + 256 p^2 + 16 p^3 multiply-adds per cell,
+// then Vbar_q = w_q f(q) is stored (the strip kernel adds the enrichment part).
+__global__ void __launch_bounds__(SF_NT) k_adjoint_fefe(
+    const int32_t *__restrict__ order, const int64_t *__restrict__ qoff,
+    const double *__restrict__ w, const double *__restrict__ xi_all,
+    const int32_t *__restrict__ partoff, const int32_t *__restrict__ part_p,
+    const int32_t *__restrict__ part_q, const int64_t *__restrict__ doff,
+    const int64_t *__restrict__ soff, const int32_t *__restrict__ smap,
+    const double *__restrict__ Hbar, int pm, double *__restrict__ Vbar, unsigned *err) {
+  // dynamic shared memory, sized for the largest per-axis count pm:
+  // Hs[64][64], L1[3][4][pm], G1[256 pm] = [(a,b),(a',b')][qz],
+  // G2[16 pm^2] = [(a,a')][qy + p qz]
+  extern __shared__ float sm_adj[];
+  float *Hs = sm_adj, *L1 = Hs + 4096, *G1 = L1 + 12 * pm, *G2 = G1 + 256 * pm;
+  const int e = order[blockIdx.x], tid = threadIdx.x;
+  const int n = (int)(doff[e + 1] - doff[e]);
+  const int32_t *m = smap + soff[e];
+  for (int o = tid; o < 4096; o += SF_NT) Hs[o] = (float)Hbar[m[(o >> 6) * n + (o & 63)]];
+  for (int k = partoff[e]; k < partoff[e + 1]; ++k) {
+    const int p = part_p[k];
+    if (p > pm) {
+      if (tid == 0) atomicOr(err, DEVERR_SHAPE);
+      return;
     }
-    H[k] = v;
+    const int64_t qs = qoff[e] + part_q[k];
+    const int p2 = p * p, p3 = p2 * p;
+    __syncthreads();
+    for (int o = tid; o < 3 * p; o += SF_NT) {
+      const int d = o / p, t = o - d * p;
+      const int stride = d == 0 ? 1 : (d == 1 ? p : p2);
+      float L[4];
+      lag3((float)xi_all[3 * (qs + (int64_t)t * stride) + d], L);
+      for (int a = 0; a < 4; ++a) L1[(d * 4 + a) * pm + t] = L[a];
+    }
+    __syncthreads();
+    // contract (c, c') for each qz: G1[(a,b),(a',b')][qz]
+    for (int o = tid; o < 256 * p; o += SF_NT) {
+      const int pr = o / p, qz = o - pr * p;
+      const int ab = pr >> 4, apbp = pr & 15;   // (a + 4b), (a' + 4b')
+      float s = 0.0f;
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int cp = 0; cp < 4; ++cp)
+          s = fmaf(L1[(8 + c) * pm + qz] * L1[(8 + cp) * pm + qz], Hs[(ab + 16 * c) * 64 + apbp + 16 * cp], s);
+      G1[o] = s;
+    }
+    __syncthreads();
+    // contract (b, b') for each (qy, qz): G2[(a,a')][qy + p qz]
+    for (int o = tid; o < 16 * p2; o += SF_NT) {
+      const int aa = o / p2, r = o - aa * p2, qy = r % p, qz = r / p;
+      const int a = aa >> 2, ap = aa & 3;
+      float s = 0.0f;
+#pragma unroll
+      for (int b = 0; b < 4; ++b)
+#pragma unroll
+        for (int bp = 0; bp < 4; ++bp)
+          s = fmaf(L1[(4 + b) * pm + qy] * L1[(4 + bp) * pm + qy], G1[((a + 4 * b) * 16 + ap + 4 * bp) * p + qz], s);
+      G2[o] = s;
+    }
+    __syncthreads();
+    // contract (a, a') for each point, store w_q f(q)
+    for (int q = tid; q < p3; q += SF_NT) {
+      const int qx = q % p, r = q / p;
+      float s = 0.0f;
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int ap = 0; ap < 4; ++ap)
+          s = fmaf(L1[a * pm + qx] * L1[ap * pm + qx], G2[(a * 4 + ap) * p2 + r], s);
+      Vbar[qs + q] = w[qs + q] * (double)s;
+    }
   }
 }
 
@@ -154,18 +187,32 @@ __global__ void k_h_init(int64_t nrow, int64_t n_fe, int nx, int ny, int nz,
 pufe_status launch_fefe(pufe_ctx *ctx, const double *V, double *H, cudaStream_t st) {
   auto &D = ctx->d;
   if (ctx->max_part_p > SF_PMAX) return fail(PUFE_EINVAL, "rule with more than 16 points per axis");
+  PUFE_CUDA_TRY(cudaMemcpyAsync(H, D.T0, (size_t)ctx->nnz * sizeof(double), cudaMemcpyDeviceToDevice, st));
   if (V) {
     k_fefe_sumfac<<<(unsigned)ctx->nelem, SF_NT, 0, st>>>(D.qoff, D.w, V, D.xi, D.partoff, D.part_p,
-                                                          D.part_q, D.mfe, D.err);
+                                                          D.part_q, D.doff, D.soff, D.smap, H, D.err);
     PUFE_CUDA_TRY(cudaGetLastError());
-  } else {
-    PUFE_CUDA_TRY(cudaMemsetAsync(D.mfe, 0, (size_t)ctx->nelem * 1000 * sizeof(float), st));
   }
-  const int64_t threads = ctx->n_dof * 32;
-  k_h_init<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(
-      ctx->n_dof, ctx->n_fe, ctx->nel[0], ctx->nel[1], ctx->nel[2], D.rowptr, D.col, D.T0, D.mfe, H);
-  PUFE_CUDA_TRY(cudaGetLastError());
   return PUFE_OK;
 }
 
+}  // namespace pufe
+
+namespace pufe {
+// Vbar = w_q (FE part of b^T Hbar b) for elements order[first .. first+count)
+pufe_status launch_adjoint_fefe(pufe_ctx *ctx, const double *Hbar, double *Vbar, int first,
+                                int count, cudaStream_t st) {
+  auto &D = ctx->d;
+  if (ctx->max_part_p > SF_PMAX) return fail(PUFE_EINVAL, "rule with more than 16 points per axis");
+  if (count <= 0) return PUFE_OK;
+  const int pm = std::max(1, ctx->max_part_p);
+  const size_t sm = (size_t)(4096 + 12 * pm + 256 * pm + 16 * pm * pm) * sizeof(float);
+  PUFE_CUDA_TRY(
+      cudaFuncSetAttribute(k_adjoint_fefe, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  k_adjoint_fefe<<<(unsigned)count, SF_NT, sm, st>>>(D.order + first, D.qoff, D.w, D.xi, D.partoff,
+                                                     D.part_p, D.part_q, D.doff, D.soff, D.smap,
+                                                     Hbar, pm, Vbar, D.err);
+  PUFE_CUDA_TRY(cudaGetLastError());
+  return PUFE_OK;
+}
 }  // namespace pufe

@@ -78,8 +78,6 @@ struct DeviceArrays {
   int32_t *partoff = nullptr; // nelem + 1: offsets into part arrays
   int32_t *part_p = nullptr;  // points per axis of each part
   int32_t *part_q = nullptr;  // first point of each part (relative to the element)
-  float *mfe = nullptr;       // nelem x 1000: FE-FE block of H_V per element, by
-                              // unordered per-axis index pairs (filled per call)
   int64_t *toff32 = nullptr;  // nelem + 1: offsets into psi32 (units of padded q*alpha)
   float *psi32 = nullptr;     // per element [q/8][slot][comp][q%8]: 32-float blocks
   float *eorig = nullptr;     // per (element, slot): displacement of the element
@@ -264,6 +262,8 @@ pufe_status launch_adjoint_fp64(pufe_ctx *ctx, const double *Hbar, double *Vbar,
 pufe_status launch_tabulate_f32(pufe_ctx *ctx, cudaStream_t s);
 pufe_status launch_adjoint_tc(pufe_ctx *ctx, const double *Hbar, double *Vbar, cudaStream_t s);
 pufe_status launch_fefe(pufe_ctx *ctx, const double *V, double *H, cudaStream_t s);
+pufe_status launch_adjoint_fefe(pufe_ctx *ctx, const double *Hbar, double *Vbar, int first,
+                                int count, cudaStream_t s);
 pufe_status launch_assemble_tc_static(pufe_ctx *ctx, const double *V, int what, double *H,
                                       double *S, cudaStream_t s);
 pufe_status launch_assemble_tc(pufe_ctx *ctx, const double *V, int what, double *H, double *S,

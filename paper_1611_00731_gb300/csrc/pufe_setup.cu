@@ -701,7 +701,6 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
   if ((st = upload(&D.partoff, partoff)) != PUFE_OK) return st;
   if ((st = upload(&D.part_p, part_p)) != PUFE_OK) return st;
   if ((st = upload(&D.part_q, part_q)) != PUFE_OK) return st;
-  PUFE_CUDA_TRY(cudaMalloc((void **)&D.mfe, std::max<int64_t>(1, nelem) * 1000 * sizeof(float)));
   PUFE_CUDA_TRY(cudaMalloc((void **)&D.vpad, std::max<int64_t>(1, qpoff[nelem]) * sizeof(float)));
   if ((st = upload(&D.toff32, toff32)) != PUFE_OK) return st;
   if ((st = upload(&D.eorig, eorig)) != PUFE_OK) return st;
@@ -727,7 +726,7 @@ static void free_device(pufe_ctx *ctx) {
   auto &D = ctx->d;
   void *ptrs[] = {D.qoff, D.x, D.w, D.xi, D.doff, D.dofs, D.ecol, D.aoff, D.alist,
                   D.toff, D.psi, D.psi32, D.qpoff, D.qdat, D.ptab, D.vpad, D.toff32, D.eorig,
-                  D.T0, D.S0, D.partoff, D.part_p, D.part_q, D.mfe,
+                  D.T0, D.S0, D.partoff, D.part_p, D.part_q,
                   D.orb, D.orbf, D.rowptr, D.col, D.soff, D.smap, D.order, D.err};
   for (void *p : ptrs)
     if (p) cudaFree(p);

@@ -1015,11 +1015,16 @@ __global__ void __launch_bounds__(ADJ_NT) k_adjoint_f32(
 }
 
 // ---------------------------------------------------------------------------
-// K5 on the tensor cores (elements with n_e <= 128).
-//   z_q = sqrt(w_q) b_q,  D[q][i] = sum_j z_qj Hbar_ij  (M = 128 points,
-//   N = n_e rounded to 16, K = basis index j), then
-//   Vbar_q = w_q b_q^T Hbar_e b_q = sum_i D[q][i] z_qi,
-// one thread per point reading its TMEM lane.  Hbar_e is gathered once per
+// K5 enrichment strip on the tensor cores (elements with n_e <= 128).
+// With b = (b_F, b_E) split into the 64 FE functions and the enrichments,
+//   b^T Hbar b = b_F^T Hbar_FF b_F + sum_{r in E} b_r sum_j B[r][j] b_j,
+//   B[r][j] = Hbar_rj + Hbar_jr (j in F),  B[r][j] = Hbar_rj (j in E).
+// The FE-FE form is done by sum factorization (k_adjoint_fefe, which stores
+// Vbar); this kernel adds the rest:
+//   z_q = sqrt(w_q) b_q,  D[q][r] = sum_j z_qj B[r][j]  (M = 128 points,
+//   N = n_E rounded to 16, K = every basis index j), then
+//   Vbar_q += sum_r D[q][r] z_qr,
+// one thread per point reading its TMEM lane.  B is gathered once per
 // element into shared memory (two TF32 terms); z is built chunk by chunk
 // (32 basis indices) into double-buffered stages; products hi*hi and the
 // cross terms go to separate TMEM accumulators.
@@ -1038,7 +1043,7 @@ struct AtShared {
   int ecs[64];
 };
 
-__global__ void __launch_bounds__(AT_NT, 1) k_adjoint_tc(
+__global__ void __launch_bounds__(AT_NT, 1) k_adjoint_strip(
     const int32_t *__restrict__ order, const int64_t *__restrict__ qoff,
     const int64_t *__restrict__ qpoff, const float4 *__restrict__ qdat,
     const int64_t *__restrict__ doff, const int32_t *__restrict__ ecol,
@@ -1058,43 +1063,48 @@ __global__ void __launch_bounds__(AT_NT, 1) k_adjoint_tc(
   const int A = aoff[e + 1] - aoff[e];
   const int n = (int)(doff[e + 1] - doff[e]);
   const int npad = (n + 15) & ~15;
+  const int ne = n - 64, ne16 = (ne + 15) & ~15;
   if (n > 128 || npad > npad_max) {
     if (tid == 0) set_err(err, DEVERR_SHAPE);
     return;
   }
-  const uint32_t SBO_H = (uint32_t)(npad / 4) * 128;   // Hbar tile: npad rows x npad
-  const int HT = npad * npad * 4;                       // bytes per Hbar tile
+  if (ne <= 0) return;   // FE-only element: Vbar is already complete
+  const uint32_t SBO_H = (uint32_t)(npad / 4) * 128;   // B tile: ne16 rows x npad
+  const int HT = ne16 * npad * 4;                       // bytes per B tile
   unsigned char *hH = base, *hL = base + HT;
-  unsigned char *zst = base + 2 * HT;                   // 2 stages x (hi, lo)
+  unsigned char *zst = base + ((2 * HT + 1023) & ~1023);   // 2 stages x (hi, lo)
   AtShared &sh = *reinterpret_cast<AtShared *>(zst + 4 * ZTILE);
   const int32_t *ec = ecol + (doff[e] - 64ll * e);
   const float *pe = psi + 4 * toff32[e];
   const float4 *qe = qdat + qpoff[e];
   const int32_t *m = smap + soff[e];
 
-  if (warp == 0) tmem_alloc(&sh.tmem, 256);
+  if (warp == 0) tmem_alloc(&sh.tmem, 128);
   if (tid == 0) {
     mbar_init(&sh.sempty[0], 1);
     mbar_init(&sh.sempty[1], 1);
     mbar_init(&sh.dbar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (tid < n - 64) sh.ecs[tid] = ec[tid];
-  // ---- gather Hbar_e (rows i, K = j) into the two TF32 tiles ----------------
+  if (tid < ne) sh.ecs[tid] = ec[tid];
+  // ---- gather B (rows r = enrichment, K = j) into the two TF32 tiles --------
   {
-    const int ncm = (npad / 8) * (npad / 4);
+    const int ncm = (ne16 / 8) * (npad / 4);
     for (int c0 = warp; c0 < ncm; c0 += 4 * (AT_NT / 32)) {
-      int sl[4];
+      int sl[4], st[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int cm = c0 + u * (AT_NT / 32);
         const int rg = cm / (npad / 4), kg = cm - rg * (npad / 4);
-        const int i = rg * 8 + (lane >> 2), j = kg * 4 + (lane & 3);
-        sl[u] = (cm < ncm && i < n && j < n) ? m[i * n + j] : -1;
+        const int r = rg * 8 + (lane >> 2), j = kg * 4 + (lane & 3);
+        const bool in = cm < ncm && r < ne && j < n;
+        sl[u] = in ? m[(64 + r) * n + j] : -1;
+        st[u] = (in && j < 64) ? m[j * n + 64 + r] : -1;
       }
       float hv[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) hv[u] = sl[u] >= 0 ? (float)Hbar[sl[u]] : 0.0f;
+      for (int u = 0; u < 4; ++u)
+        hv[u] = (sl[u] >= 0 ? (float)Hbar[sl[u]] : 0.0f) + (st[u] >= 0 ? (float)Hbar[st[u]] : 0.0f);
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int cm = c0 + u * (AT_NT / 32);
@@ -1111,8 +1121,8 @@ __global__ void __launch_bounds__(AT_NT, 1) k_adjoint_tc(
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  const uint32_t tD = sh.tmem, tX = sh.tmem + 128;
-  const uint32_t idD = idesc_tf32(128, npad);
+  const uint32_t tD = sh.tmem, tX = sh.tmem + 64;
+  const uint32_t idD = idesc_tf32(128, ne16);
   const uint32_t hbase = smem_u32(hH), lbase = smem_u32(hL), zbase = smem_u32(zst);
   const int nkc = (npad + AT_KJ - 1) / AT_KJ;
   int g = 0;          // chunk counter (stage phases)
@@ -1207,18 +1217,16 @@ __global__ void __launch_bounds__(AT_NT, 1) k_adjoint_tc(
       const uint32_t lanebase = (uint32_t)(quarter * 32) << 16;
       const int qg = mt * 128 + ql;
       float part = 0.0f;
-      for (int cb = half; cb * 16 < npad; cb += 2) {
+      for (int cb = half; cb * 16 < ne16; cb += 2) {
         float dh[16], dx[16];
         tmem_ld16(tD + lanebase + cb * 16, dh);
         tmem_ld16(tX + lanebase + cb * 16, dx);
 #pragma unroll
         for (int u = 0; u < 16; ++u) {
-          const int i = cb * 16 + u;
+          const int r = cb * 16 + u;
           float b = 0.0f;
-          if (i < 64) {
-            b = sh.L[ql][0][i & 3] * sh.L[ql][1][(i >> 2) & 3] * sh.L[ql][2][i >> 4];
-          } else if (i < n && qg < Q) {
-            const int code = sh.ecs[i - 64];
+          if (r < ne && qg < Q) {
+            const int code = sh.ecs[r];
             const int lv = code & 7;
             const float phi = (((lv & 1) ? 1.0f + sh.xi[ql][0] : 1.0f - sh.xi[ql][0]) *
                                ((lv & 2) ? 1.0f + sh.xi[ql][1] : 1.0f - sh.xi[ql][1]) *
@@ -1234,7 +1242,7 @@ __global__ void __launch_bounds__(AT_NT, 1) k_adjoint_tc(
     __syncthreads();
     if (tid < 128) {
       const int qg = mt * 128 + tid;
-      if (qg < Q) Vbar[q0 + qg] = (double)sh.acc[tid];
+      if (qg < Q) Vbar[q0 + qg] += (double)sh.acc[tid];
     }
     __syncthreads();
     tc_fence_after();
@@ -1247,7 +1255,7 @@ __global__ void __launch_bounds__(AT_NT, 1) k_adjoint_tc(
   __syncthreads();
   if (warp == 0) {
     tc_fence_after();
-    tmem_dealloc(sh.tmem, 256);
+    tmem_dealloc(sh.tmem, 128);
   }
 }
 
@@ -1353,18 +1361,23 @@ pufe_status launch_adjoint_tc(pufe_ctx *ctx, const double *Hbar, double *Vbar, c
     PUFE_CUDA_TRY(cudaGetLastError());
   }
   const int nsmall = (int)ctx->nelem - nbig;
-  if (nsmall > 0) {  // n_e <= 128: tensor cores
-    int np = 16;
-    for (int64_t k = nbig; k < ctx->nelem; ++k)
-      np = std::max(np, (ctx->n_e[ctx->order[k]] + 15) & ~15);
-    const size_t sm = (size_t)1024 + 2 * (size_t)np * np * 4 + 4 * (size_t)128 * AT_KJ * 4 +
-                      sizeof(AtShared);
+  if (nsmall > 0) {  // n_e <= 128: FE-FE by sum factorization, strip on tensor cores
+    int np = 16, ne16 = 16;
+    for (int64_t k = nbig; k < ctx->nelem; ++k) {
+      const int ne = ctx->n_e[ctx->order[k]];
+      np = std::max(np, (ne + 15) & ~15);
+      ne16 = std::max(ne16, (ne - 64 + 15) & ~15);
+    }
+    const size_t sm = (size_t)1024 + (((size_t)2 * ne16 * np * 4 + 1023) & ~(size_t)1023) +
+                      4 * (size_t)128 * AT_KJ * 4 + sizeof(AtShared);
     if (sm > 227 * 1024) return fail(PUFE_EINVAL, "n_e too large for the tensor-core adjoint");
+    pufe_status e0 = launch_adjoint_fefe(ctx, Hbar, Vbar, nbig, nsmall, st);
+    if (e0 != PUFE_OK) return e0;
     PUFE_CUDA_TRY(
-        cudaFuncSetAttribute(k_adjoint_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    k_adjoint_tc<<<nsmall, AT_NT, sm, st>>>(D.order + nbig, D.qoff, D.qpoff, D.qdat, D.doff,
-                                            D.ecol, D.aoff, D.toff32, D.psi32, D.soff, D.smap,
-                                            Hbar, np, Vbar, D.err);
+        cudaFuncSetAttribute(k_adjoint_strip, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_adjoint_strip<<<nsmall, AT_NT, sm, st>>>(D.order + nbig, D.qoff, D.qpoff, D.qdat, D.doff,
+                                               D.ecol, D.aoff, D.toff32, D.psi32, D.soff, D.smap,
+                                               Hbar, np, Vbar, D.err);
     PUFE_CUDA_TRY(cudaGetLastError());
   }
   return PUFE_OK;
