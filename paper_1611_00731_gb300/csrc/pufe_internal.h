@@ -113,6 +113,8 @@ struct pufe_ctx {
   bool fe_exact = false;      // every rule has >= 4 points per axis per (sub)cell
   int n_big = 0;              // elements with n_e > 128 (listed first in `order`)
   int max_part_p = 0;         // largest points-per-axis of any (sub)cell
+  int strip_stage = 0;        // floats of the strip kernel's shared-memory stage
+  uint32_t strip_pmask = 0;   // per-axis counts (bit p) of the strip kernel's cells
   bool on_device = false;   // device copies exist (a CUDA device was present)
   // host copies kept for getters
   std::vector<int64_t> qoff, rowptr, doff;
@@ -262,6 +264,8 @@ pufe_status launch_adjoint_fp64(pufe_ctx *ctx, const double *Hbar, double *Vbar,
 pufe_status launch_tabulate_f32(pufe_ctx *ctx, cudaStream_t s);
 pufe_status launch_adjoint_tc(pufe_ctx *ctx, const double *Hbar, double *Vbar, cudaStream_t s);
 pufe_status launch_fefe(pufe_ctx *ctx, const double *V, double *H, cudaStream_t s);
+pufe_status launch_strip_sf(pufe_ctx *ctx, const double *V, int what, double *H, double *S,
+                            int first, int count, cudaStream_t s);
 pufe_status launch_adjoint_fefe(pufe_ctx *ctx, const double *Hbar, double *Vbar, int first,
                                 int count, cudaStream_t s);
 pufe_status launch_assemble_tc_static(pufe_ctx *ctx, const double *V, int what, double *H,

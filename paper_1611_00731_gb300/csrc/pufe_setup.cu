@@ -651,6 +651,21 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
   ctx->max_part_p = max_part_p;
   ctx->max_alpha = 0;
   for (auto &v : ealpha) ctx->max_alpha = std::max(ctx->max_alpha, (int)v.size());
+  // shared-memory stage of the strip kernel: the largest (sub)cell's Psi
+  // rows (odd pitch), points and V among enriched elements with
+  // n_e <= 128, capped at 10240 floats (larger cells read global memory)
+  ctx->strip_stage = 0;
+  ctx->strip_pmask = 0;
+  for (int64_t e = 0; e < nelem; ++e) {
+    if (n_e[e] <= 64 || n_e[e] > 128) continue;
+    const int A = (int)ealpha[e].size();
+    for (int32_t j = partoff[e]; j < partoff[e + 1]; ++j) {
+      if (part_p[j] < 32) ctx->strip_pmask |= 1u << part_p[j];
+      const int p3 = part_p[j] * part_p[j] * part_p[j];
+      const int need = ((A * 4 * (p3 | 1) + 3) & ~3) + 5 * p3;
+      if (need <= 10240) ctx->strip_stage = std::max(ctx->strip_stage, need);
+    }
+  }
 
   // Device copies: made here when a CUDA device is present.  Without one the
   // context keeps its host-side description only (getters work, compute

@@ -291,11 +291,13 @@ struct WsShared {
 // (128 x 129 floats), or the 256-row tile's per-warp transpose buffers
 // (4 x 32 x 17 float2)
 
-// FP32 copy of V on the padded point layout (zeros on padding points), so
-// that the assembly's bulk copies can bring it in with the other inputs.
-__global__ void k_pack_v(const int64_t *__restrict__ qoff, const int64_t *__restrict__ qpoff,
-                         const double *__restrict__ V, float *__restrict__ vpad) {
-  const int64_t e = blockIdx.x;
+// FP32 copy of V on the padded point layout (zeros on padding points) for the
+// elements order[0 .. gridDim.x), so that the tensor-core kernel's bulk
+// copies can bring it in with the other inputs.
+__global__ void k_pack_v(const int32_t *__restrict__ order, const int64_t *__restrict__ qoff,
+                         const int64_t *__restrict__ qpoff, const double *__restrict__ V,
+                         float *__restrict__ vpad) {
+  const int64_t e = order[blockIdx.x];
   const int64_t q0 = qoff[e];
   const int Q = (int)(qoff[e + 1] - q0);
   const int Qp = (int)(qpoff[e + 1] - qpoff[e]);
@@ -1259,6 +1261,128 @@ __global__ void __launch_bounds__(AT_NT, 1) k_adjoint_strip(
   }
 }
 
+// ---------------------------------------------------------------------------
+// K5 enrichment strip on the CUDA cores (elements with n_e <= 128): the same
+// split as above, one thread per point, in FP32 with round to nearest.
+//   FE columns:  g_r += sum_(abc) B[r][(abc)] L_a(x) L_b(y) L_c(z), factorized
+//                per point (84 multiply-adds per r instead of 128);
+//   E columns:   the E-E form is symmetric in (r, s), so only s >= r is kept:
+//                Be[s][r] = Hbar_rr (s = r), Hbar_rs + Hbar_sr (s > r).
+// Rows r go in register blocks of 8, so each broadcast read of B feeds 8 FMAs.
+// ---------------------------------------------------------------------------
+constexpr int AS_NT = 256;
+
+__global__ void __launch_bounds__(AS_NT) k_adjoint_strip_f32(
+    const int32_t *__restrict__ order, const int64_t *__restrict__ qoff,
+    const int64_t *__restrict__ qpoff, const float4 *__restrict__ qdat,
+    const double *__restrict__ w, const int64_t *__restrict__ doff,
+    const int32_t *__restrict__ ecol, const int32_t *__restrict__ aoff,
+    const int64_t *__restrict__ toff32, const float *__restrict__ psi,
+    const int64_t *__restrict__ soff, const int32_t *__restrict__ smap,
+    const double *__restrict__ Hbar, double *__restrict__ Vbar) {
+  extern __shared__ float4 sm_as4[];
+  const int e = order[blockIdx.x], tid = threadIdx.x;
+  const int n = (int)(doff[e + 1] - doff[e]);
+  const int ne = n - 64;
+  if (ne <= 0) return;   // FE-only element: Vbar is already complete
+  const int ne8 = (ne + 7) & ~7;
+  float *Bf = reinterpret_cast<float *>(sm_as4);   // [64][ne8]: B[r][j], j in F
+  float *Be = Bf + 64 * ne8;                       // [ne8][ne8]: s >= r half
+  float *bE = Be + ne8 * ne8;                      // [ne8][AS_NT]: b_s at each point
+  int *ecs = reinterpret_cast<int *>(bE + ne8 * AS_NT);
+  const int64_t q0 = qoff[e];
+  const int Q = (int)(qoff[e + 1] - q0);
+  const int A = aoff[e + 1] - aoff[e];
+  const int32_t *m = smap + soff[e];
+  const float *pe = psi + 4 * toff32[e];
+  const float4 *qe = qdat + qpoff[e];
+  if (tid < ne) ecs[tid] = ecol[(doff[e] - 64ll * e) + tid];
+  for (int o = tid; o < 64 * ne8; o += AS_NT) {
+    const int j = o / ne8, r = o - j * ne8;
+    Bf[o] = r < ne ? (float)(Hbar[m[(64 + r) * n + j]] + Hbar[m[j * n + 64 + r]]) : 0.0f;
+  }
+  for (int o = tid; o < ne8 * ne8; o += AS_NT) {
+    const int sr = o / ne8, r = o - sr * ne8;
+    float v = 0.0f;
+    if (sr < ne && sr > r) v = (float)(Hbar[m[(64 + r) * n + 64 + sr]] + Hbar[m[(64 + sr) * n + 64 + r]]);
+    else if (sr < ne && sr == r) v = (float)Hbar[m[(64 + r) * n + 64 + r]];
+    Be[o] = v;
+  }
+  __syncthreads();
+  for (int t0 = 0; t0 < Q; t0 += AS_NT) {
+    const int ql = t0 + tid;
+    if (ql >= Q) break;   // no block-wide barrier below
+    const float4 x4 = qe[ql];
+    float Lx[4], Ly[4], Lz[4], dL[4];
+    lagrange3f(x4.x, Lx, dL);
+    lagrange3f(x4.y, Ly, dL);
+    lagrange3f(x4.z, Lz, dL);
+    const float *pq = pe + (int64_t)(ql >> 3) * A * 32 + (ql & 7);
+    for (int sr = 0; sr < ne8; ++sr) {   // this thread's own column only
+      float b = 0.0f;
+      if (sr < ne) {
+        const int code = ecs[sr], lv = code & 7;
+        const float phi = ((lv & 1) ? 1.0f + x4.x : 1.0f - x4.x) *
+                          ((lv & 2) ? 1.0f + x4.y : 1.0f - x4.y) *
+                          ((lv & 4) ? 1.0f + x4.z : 1.0f - x4.z);
+        b = 0.125f * phi * pq[(code >> 3) * 32];
+      }
+      bE[sr * AS_NT + tid] = b;
+    }
+    float acc = 0.0f;
+    for (int r0 = 0; r0 < ne8; r0 += 8) {
+      float g[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) g[k] = 0.0f;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        float tb[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) tb[k] = 0.0f;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          float ta[8];
+#pragma unroll
+          for (int k = 0; k < 8; ++k) ta[k] = 0.0f;
+#pragma unroll
+          for (int a = 0; a < 4; ++a) {
+            const float4 *bp = reinterpret_cast<const float4 *>(Bf + (a + 4 * b + 16 * c) * ne8 + r0);
+            const float4 u = bp[0], v = bp[1];
+            ta[0] = fmaf(Lx[a], u.x, ta[0]);
+            ta[1] = fmaf(Lx[a], u.y, ta[1]);
+            ta[2] = fmaf(Lx[a], u.z, ta[2]);
+            ta[3] = fmaf(Lx[a], u.w, ta[3]);
+            ta[4] = fmaf(Lx[a], v.x, ta[4]);
+            ta[5] = fmaf(Lx[a], v.y, ta[5]);
+            ta[6] = fmaf(Lx[a], v.z, ta[6]);
+            ta[7] = fmaf(Lx[a], v.w, ta[7]);
+          }
+#pragma unroll
+          for (int k = 0; k < 8; ++k) tb[k] = fmaf(Ly[b], ta[k], tb[k]);
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) g[k] = fmaf(Lz[c], tb[k], g[k]);
+      }
+      for (int sr = r0; sr < ne8; ++sr) {
+        const float bs = bE[sr * AS_NT + tid];
+        const float4 *bp = reinterpret_cast<const float4 *>(Be + sr * ne8 + r0);
+        const float4 u = bp[0], v = bp[1];
+        g[0] = fmaf(u.x, bs, g[0]);
+        g[1] = fmaf(u.y, bs, g[1]);
+        g[2] = fmaf(u.z, bs, g[2]);
+        g[3] = fmaf(u.w, bs, g[3]);
+        g[4] = fmaf(v.x, bs, g[4]);
+        g[5] = fmaf(v.y, bs, g[5]);
+        g[6] = fmaf(v.z, bs, g[6]);
+        g[7] = fmaf(v.w, bs, g[7]);
+      }
+#pragma unroll
+      for (int k = 0; k < 8; ++k) acc = fmaf(bE[(r0 + k) * AS_NT + tid], g[k], acc);
+    }
+    Vbar[q0 + ql] += w[q0 + ql] * (double)acc;
+  }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -1287,10 +1411,10 @@ static pufe_status run_assemble_tc(pufe_ctx *ctx, const double *V, int what, dou
   if (ctx->max_basis > 256) return fail(PUFE_EINVAL, "PUFE_TF32X3 supports n_e <= 256");
   const int amax = std::max(1, ctx->max_alpha);
   const int inb = ((amax * 4 * WS_KC * 4 + WS_KC * 128 + WS_KC * 4) + 127) & ~127;
-  const size_t sm128 = assemble_smem(128, inb), sm256 = assemble_smem(256, inb);
+  const size_t sm256 = assemble_smem(256, inb);
   const int nbig = ctx->n_big;
   const int nsmall = (int)ctx->nelem - nbig;
-  if ((nbig > 0 && sm256 > 227 * 1024) || (nsmall > 0 && sm128 > 227 * 1024))
+  if (nbig > 0 && sm256 > 227 * 1024)
     return fail(PUFE_EINVAL, "too many enrichments per element for TF32X3");
   const size_t bytes = (size_t)ctx->nnz * sizeof(double);
   if (what & PUFE_WANT_H) {
@@ -1298,16 +1422,17 @@ static pufe_status run_assemble_tc(pufe_ctx *ctx, const double *V, int what, dou
     if (e0 != PUFE_OK) return e0;
   }
   if (what & PUFE_WANT_S) PUFE_CUDA_TRY(cudaMemcpyAsync(S, D.S0, bytes, cudaMemcpyDeviceToDevice, st));
-  // every entry the strip kernel reads is rewritten (zeros on padding)
-  k_pack_v<<<(unsigned)ctx->nelem, 256, 0, st>>>(D.qoff, D.qpoff, (what & PUFE_WANT_H) ? V : nullptr,
-                                                vscratch);
-  PUFE_CUDA_TRY(cudaGetLastError());
-  const float sx = (float)(2.0 / ctx->h[0]), sy = (float)(2.0 / ctx->h[1]),
-              sz = (float)(2.0 / ctx->h[2]);
-  int nsm = 0;
-  PUFE_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device));
-  // elements are ordered with n_e > 128 first (256-row tile), then the rest
+  // elements are ordered with n_e > 128 first (256-row tensor-core tile),
+  // then the rest (sum-factorized strip on the CUDA cores)
   if (nbig > 0) {
+    // every entry the tensor-core kernel reads is rewritten (zeros on padding)
+    k_pack_v<<<(unsigned)nbig, 256, 0, st>>>(D.order, D.qoff, D.qpoff,
+                                             (what & PUFE_WANT_H) ? V : nullptr, vscratch);
+    PUFE_CUDA_TRY(cudaGetLastError());
+    const float sx = (float)(2.0 / ctx->h[0]), sy = (float)(2.0 / ctx->h[1]),
+                sz = (float)(2.0 / ctx->h[2]);
+    int nsm = 0;
+    PUFE_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device));
     PUFE_CUDA_TRY(cudaFuncSetAttribute(k_assemble_tc<256>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm256));
     k_assemble_tc<256><<<std::min(nbig, nsm), WS_NT, sm256, st>>>(
@@ -1315,15 +1440,7 @@ static pufe_status run_assemble_tc(pufe_ctx *ctx, const double *V, int what, dou
         D.soff, D.smap, sx, sy, sz, nbig, amax, inb, what, H, S, D.err);
     PUFE_CUDA_TRY(cudaGetLastError());
   }
-  if (nsmall > 0) {
-    PUFE_CUDA_TRY(cudaFuncSetAttribute(k_assemble_tc<128>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm128));
-    k_assemble_tc<128><<<std::min(nsmall, nsm), WS_NT, sm128, st>>>(
-        D.order + nbig, D.qoff, D.qpoff, D.ptab, vscratch, D.doff, D.ecol, D.aoff, D.toff32,
-        D.psi32, D.soff, D.smap, sx, sy, sz, nsmall, amax, inb, what, H, S, D.err);
-    PUFE_CUDA_TRY(cudaGetLastError());
-  }
-  return PUFE_OK;
+  return launch_strip_sf(ctx, (what & PUFE_WANT_H) ? V : nullptr, what, H, S, nbig, nsmall, st);
 }
 
 pufe_status launch_assemble_tc(pufe_ctx *ctx, const double *V, int what, double *H, double *S,
@@ -1361,23 +1478,19 @@ pufe_status launch_adjoint_tc(pufe_ctx *ctx, const double *Hbar, double *Vbar, c
     PUFE_CUDA_TRY(cudaGetLastError());
   }
   const int nsmall = (int)ctx->nelem - nbig;
-  if (nsmall > 0) {  // n_e <= 128: FE-FE by sum factorization, strip on tensor cores
-    int np = 16, ne16 = 16;
-    for (int64_t k = nbig; k < ctx->nelem; ++k) {
-      const int ne = ctx->n_e[ctx->order[k]];
-      np = std::max(np, (ne + 15) & ~15);
-      ne16 = std::max(ne16, (ne - 64 + 15) & ~15);
-    }
-    const size_t sm = (size_t)1024 + (((size_t)2 * ne16 * np * 4 + 1023) & ~(size_t)1023) +
-                      4 * (size_t)128 * AT_KJ * 4 + sizeof(AtShared);
-    if (sm > 227 * 1024) return fail(PUFE_EINVAL, "n_e too large for the tensor-core adjoint");
+  if (nsmall > 0) {  // n_e <= 128: FE-FE by sum factorization, then the enrichment strip
+    int ne8 = 8;
+    for (int64_t k = nbig; k < ctx->nelem; ++k)
+      ne8 = std::max(ne8, (ctx->n_e[ctx->order[k]] - 64 + 7) & ~7);
+    const size_t sm = ((size_t)64 * ne8 + (size_t)ne8 * ne8 + (size_t)ne8 * AS_NT + ne8) * 4;
+    if (sm > 227 * 1024) return fail(PUFE_EINVAL, "n_e too large for the strip adjoint");
     pufe_status e0 = launch_adjoint_fefe(ctx, Hbar, Vbar, nbig, nsmall, st);
     if (e0 != PUFE_OK) return e0;
-    PUFE_CUDA_TRY(
-        cudaFuncSetAttribute(k_adjoint_strip, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    k_adjoint_strip<<<nsmall, AT_NT, sm, st>>>(D.order + nbig, D.qoff, D.qpoff, D.qdat, D.doff,
-                                               D.ecol, D.aoff, D.toff32, D.psi32, D.soff, D.smap,
-                                               Hbar, np, Vbar, D.err);
+    PUFE_CUDA_TRY(cudaFuncSetAttribute(k_adjoint_strip_f32,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_adjoint_strip_f32<<<nsmall, AS_NT, sm, st>>>(D.order + nbig, D.qoff, D.qpoff, D.qdat, D.w,
+                                                   D.doff, D.ecol, D.aoff, D.toff32, D.psi32,
+                                                   D.soff, D.smap, Hbar, Vbar);
     PUFE_CUDA_TRY(cudaGetLastError());
   }
   return PUFE_OK;
