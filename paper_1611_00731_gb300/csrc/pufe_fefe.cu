@@ -10,9 +10,10 @@
 // element contraction.  (Sec. 4 eq. disceig3d, local potential term; the rule
 // is the element's shared rule of Sec. 5.2.)
 //
-// H starts as the precomputed constant kinetic FE-FE sum T0; each element then
-// adds its 64 x 64 block of M through the scatter map.  Enrichment slots start
-// at T0 = 0; the tensor-core strip kernel adds their values afterwards.
+// H starts at zero; each element adds the constant 64 x 64 kinetic block of
+// the tricubic functions (the same on every element of the cubic mesh, exact
+// for rules with >= 4 points per axis, precomputed in FP64) plus its block of
+// M through the scatter map.  The enrichment strip kernel adds the rest.
 #include <algorithm>
 
 #include "pufe_internal.h"
@@ -41,7 +42,8 @@ __global__ void __launch_bounds__(SF_NT) k_fefe_sumfac(
     const double *__restrict__ xi_all, const int32_t *__restrict__ partoff,
     const int32_t *__restrict__ part_p, const int32_t *__restrict__ part_q,
     const int64_t *__restrict__ doff, const int64_t *__restrict__ soff,
-    const int32_t *__restrict__ smap, double *__restrict__ H, unsigned *err) {
+    const int32_t *__restrict__ smap, const double *__restrict__ Tfe, double *__restrict__ H,
+    unsigned *err) {
   __shared__ float Wq[SF_PMAX * SF_PMAX * SF_PMAX];
   __shared__ float P[3][10][SF_PMAX];          // pair products per axis
   __shared__ float G1[SF_PMAX * SF_PMAX * 10];  // [qx + p qy][cc]
@@ -49,7 +51,7 @@ __global__ void __launch_bounds__(SF_NT) k_fefe_sumfac(
   __shared__ float M[1000];
   const int e = blockIdx.x, tid = threadIdx.x;
   for (int o = tid; o < 1000; o += SF_NT) M[o] = 0.0f;
-  for (int k = partoff[e]; k < partoff[e + 1]; ++k) {
+  for (int k = partoff[e]; V != nullptr && k < partoff[e + 1]; ++k) {
     const int p = part_p[k];
     if (p > SF_PMAX) {
       if (tid == 0) atomicOr(err, DEVERR_SHAPE);
@@ -99,7 +101,7 @@ __global__ void __launch_bounds__(SF_NT) k_fefe_sumfac(
     const int i = o >> 6, j = o & 63;
     const float v = M[pidx(i & 3, j & 3) * 100 + pidx((i >> 2) & 3, (j >> 2) & 3) * 10 +
                       pidx(i >> 4, j >> 4)];
-    atomicAdd(H + m[i * n + j], (double)v);
+    atomicAdd(H + m[i * n + j], __ldg(Tfe + o) + (double)v);
   }
 }
 
@@ -183,16 +185,17 @@ __global__ void __launch_bounds__(SF_NT) k_adjoint_fefe(
 
 }  // namespace
 
-// H = T0 + (FE-FE block of H_V) on every CSR slot; V == NULL means V = 0.
+// H = 0, then every element adds its kinetic FE-FE block and the FE-FE block
+// of H_V; V == NULL means V = 0.
 pufe_status launch_fefe(pufe_ctx *ctx, const double *V, double *H, cudaStream_t st) {
   auto &D = ctx->d;
   if (ctx->max_part_p > SF_PMAX) return fail(PUFE_EINVAL, "rule with more than 16 points per axis");
-  PUFE_CUDA_TRY(cudaMemcpyAsync(H, D.T0, (size_t)ctx->nnz * sizeof(double), cudaMemcpyDeviceToDevice, st));
-  if (V) {
-    k_fefe_sumfac<<<(unsigned)ctx->nelem, SF_NT, 0, st>>>(D.qoff, D.w, V, D.xi, D.partoff, D.part_p,
-                                                          D.part_q, D.doff, D.soff, D.smap, H, D.err);
-    PUFE_CUDA_TRY(cudaGetLastError());
-  }
+  if (!D.Tfe) return fail(PUFE_ESTATE, "no exact FE-FE blocks (a rule has < 4 points per axis)");
+  PUFE_CUDA_TRY(cudaMemsetAsync(H, 0, (size_t)ctx->nnz * sizeof(double), st));
+  k_fefe_sumfac<<<(unsigned)ctx->nelem, SF_NT, 0, st>>>(D.qoff, D.w, V, D.xi, D.partoff, D.part_p,
+                                                        D.part_q, D.doff, D.soff, D.smap, D.Tfe, H,
+                                                        D.err);
+  PUFE_CUDA_TRY(cudaGetLastError());
   return PUFE_OK;
 }
 

@@ -82,7 +82,7 @@ struct DeviceArrays {
   float *psi32 = nullptr;     // per element [q/8][slot][comp][q%8]: 32-float blocks
   float *eorig = nullptr;     // per (element, slot): displacement of the element
                               // origin from the nearest atom image, hi[3], lo[3], 0, 0
-  double *T0 = nullptr;       // nnz: global FE-FE kinetic blocks (constant)
+  double *Tfe = nullptr;      // 64 x 64: kinetic block of the tricubic functions (any element)
   double *S0 = nullptr;       // nnz: global FE-FE overlap blocks (constant)
   Orbital *orb = nullptr;     // n_alpha
   OrbitalF *orbf = nullptr;   // n_alpha

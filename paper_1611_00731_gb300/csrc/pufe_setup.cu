@@ -576,7 +576,7 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
   for (auto &parts : rule)
     for (auto &pt : parts) min_p = std::min(min_p, pt.p);
   const bool fe_exact = min_p >= 4;
-  std::vector<double> T0, S0;
+  std::vector<double> TF, S0;
   if (fe_exact) {
     double M1[4][4] = {{0}}, K1[4][4] = {{0}};
     for (int g = 0; g < 4; ++g) {
@@ -590,7 +590,8 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
     }
     const double J = 0.125 * S.h[0] * S.h[1] * S.h[2];
     const double s2[3] = {4.0 / (S.h[0] * S.h[0]), 4.0 / (S.h[1] * S.h[1]), 4.0 / (S.h[2] * S.h[2])};
-    std::vector<double> TF(64 * 64), SF(64 * 64);
+    std::vector<double> SF(64 * 64);
+    TF.assign(64 * 64, 0.0);
     for (int i = 0; i < 64; ++i)
       for (int j = 0; j < 64; ++j) {
         const int ia[3] = {i & 3, (i >> 2) & 3, i >> 4}, ja[3] = {j & 3, (j >> 2) & 3, j >> 4};
@@ -600,16 +601,12 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
                                     s2[1] * mx * K1[ia[1]][ja[1]] * mz +
                                     s2[2] * mx * my * K1[ia[2]][ja[2]]);
       }
-    T0.assign(nnz, 0.0);
     S0.assign(nnz, 0.0);
     for (int64_t e = 0; e < nelem; ++e) {
       const int n = n_e[e];
       const int32_t *m = &smap[soff[e]];
       for (int i = 0; i < 64; ++i)
-        for (int j = 0; j < 64; ++j) {
-          T0[m[(int64_t)i * n + j]] += TF[i * 64 + j];
-          S0[m[(int64_t)i * n + j]] += SF[i * 64 + j];
-        }
+        for (int j = 0; j < 64; ++j) S0[m[(int64_t)i * n + j]] += SF[i * 64 + j];
     }
   }
 
@@ -706,7 +703,7 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
   if ((st = upload(&D.smap, smap)) != PUFE_OK) return st;
   if ((st = upload(&D.order, order)) != PUFE_OK) return st;
   if (fe_exact) {
-    if ((st = upload(&D.T0, T0)) != PUFE_OK) return st;
+    if ((st = upload(&D.Tfe, TF)) != PUFE_OK) return st;
     if ((st = upload(&D.S0, S0)) != PUFE_OK) return st;
   }
   PUFE_CUDA_TRY(cudaMalloc((void **)&D.psi, std::max<int64_t>(1, ctx->psi_len) * sizeof(double)));
@@ -741,7 +738,7 @@ static void free_device(pufe_ctx *ctx) {
   auto &D = ctx->d;
   void *ptrs[] = {D.qoff, D.x, D.w, D.xi, D.doff, D.dofs, D.ecol, D.aoff, D.alist,
                   D.toff, D.psi, D.psi32, D.qpoff, D.qdat, D.ptab, D.vpad, D.toff32, D.eorig,
-                  D.T0, D.S0, D.partoff, D.part_p, D.part_q,
+                  D.Tfe, D.S0, D.partoff, D.part_p, D.part_q,
                   D.orb, D.orbf, D.rowptr, D.col, D.soff, D.smap, D.order, D.err};
   for (void *p : ptrs)
     if (p) cudaFree(p);

@@ -249,25 +249,24 @@ __global__ void k_tabulate_f32(const int64_t *__restrict__ qpoff, const float4 *
 }
 
 // ---------------------------------------------------------------------------
-// Tensor-core element contraction: persistent, warp-specialized.
+// Tensor-core element contraction for elements with n_e > 128 (up to 256
+// basis functions): persistent, warp-specialized.
 //
-// The FE-FE blocks are done elsewhere (exact constants and the sum-factorized
-// V term); this kernel computes the enrichment strip of every element:
+// The FE-FE blocks are done elsewhere (exact kinetic constants and the
+// sum-factorized V term); this kernel computes the enrichment strip:
 //   H[:, 64:] = ZV^T Z[64:] + sum_d Y_d^T Y_d[64:],   S[:, 64:] = Z^T Z[64:],
 // with, per 8-point chunk, Y_d = sqrt(w/2) dphi/dx_d, Z = sqrt(w) phi and
-// ZV = V Z for every basis column (rows of the A operand) and the enrichment
-// columns only (rows of the B operand), each split into two TF32 terms.
+// ZV = V Z for every basis column (rows of the A operand, two 128-row
+// M-tiles) and the enrichment columns only (rows of the B operand), each
+// split into two TF32 terms (three MMAs per product: hi*hi, hi*lo, lo*hi).
 //
 // Roles (one CTA per SM, elements taken round-robin from the work list):
 //   warps 0-7   fill: per chunk, wait for the chunk's inputs (in shared
 //               memory, brought by the loader) and a free operand stage,
-//               compute the operand values; 128-row tile: thread = basis
-//               row, A operands written straight into tensor memory with
-//               tcgen05.st, enrichment rows also written to the B tiles in
-//               shared memory; 256-row tile: all operands in shared memory;
-//               then signal "stage full" and "input free";
+//               write the operand core matrices into shared memory, then
+//               signal "stage full" and "input free";
 //   warp 8      MMA: one lane issues tcgen05.mma per full stage, commits to
-//               "stage empty" and, at the end of an element, "acc full";
+//               "stage empty" and, at the end of an M-tile, "acc full";
 //   warps 9-12  epilogue: drain the accumulators, add them into the FP64 CSR
 //               values, signal "acc empty";
 //   warp 13     loader: 1D TMA bulk copies of each chunk's inputs (Psi table
@@ -287,9 +286,7 @@ struct WsShared {
   uint32_t tmem;
   int abort;      // any role gave up: everyone leaves
 };
-// after WsShared: the 128-row tile's FP32 staging of the accumulators
-// (128 x 129 floats), or the 256-row tile's per-warp transpose buffers
-// (4 x 32 x 17 float2)
+// after WsShared: the epilogue warps' transpose buffers (4 x 32 x 17 float2)
 
 // FP32 copy of V on the padded point layout (zeros on padding points) for the
 // elements order[0 .. gridDim.x), so that the tensor-core kernel's bulk
@@ -312,7 +309,6 @@ struct ElemInfo {
   bool go;   // ok and it has enrichment columns (FE-only elements need no strip)
 };
 
-template <int R>
 __device__ __forceinline__ ElemInfo elem_info(const int32_t *order, int k, const int64_t *qoff,
                                               const int64_t *qpoff, const int32_t *aoff,
                                               const int64_t *doff, int amax) {
@@ -328,7 +324,7 @@ __device__ __forceinline__ ElemInfo elem_info(const int32_t *order, int k, const
   I.nenr16 = (I.nenr + 15) & ~15;
   I.nch = I.Qp / WS_KC;
   I.nmt = (I.n + 127) / 128;
-  I.ok = I.n <= R && I.A <= amax && I.nch > 0;
+  I.ok = I.n <= 256 && I.A <= amax && I.nch > 0;
   I.go = I.ok && I.nenr > 0;
   return I;
 }
@@ -337,28 +333,8 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// 4 consecutive 32-bit TMEM columns of this thread's lane
-__device__ __forceinline__ void tmem_st4(uint32_t taddr, float a, float b, float c, float d) {
-  asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr),
-               "r"(__float_as_uint(a)), "r"(__float_as_uint(b)), "r"(__float_as_uint(c)),
-               "r"(__float_as_uint(d))
-               : "memory");
-}
-__device__ __forceinline__ void tmem_wait_st() {
-  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-}
 
-// D (+)= A * B with A read from tensor memory
-__device__ __forceinline__ void mma_tf32_ta(uint32_t dtmem, uint32_t atmem, uint64_t b,
-                                            uint32_t idesc, uint32_t accum) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(dtmem),
-      "r"(atmem), "l"(b), "r"(idesc), "r"(accum)
-      : "memory");
-}
 
-template <int R>
 __global__ void __launch_bounds__(WS_NT, 1) k_assemble_tc(
     const int32_t *__restrict__ order, const int64_t *__restrict__ qoff,
     const int64_t *__restrict__ qpoff, const float *__restrict__ ptab,
@@ -368,34 +344,24 @@ __global__ void __launch_bounds__(WS_NT, 1) k_assemble_tc(
     const int64_t *__restrict__ soff, const int32_t *__restrict__ smap, float sx, float sy,
     float sz, int nelem_list, int amax, int in_bytes, int want, double *__restrict__ H,
     double *__restrict__ S, unsigned *err) {
+  constexpr int R = 256;                      // basis rows of the tile (n_e <= 256)
   constexpr int KC = WS_KC;
-  constexpr bool ATMEM = (R == 128);          // A operands in tensor memory
-  constexpr int TILE = ATMEM ? 64 * KC * 4 : R * KC * 4;   // bytes per SMEM tile
-  constexpr int NBT = ATMEM ? 8 : NTILES;     // SMEM tiles per stage
+  constexpr int TILE = R * KC * 4;            // bytes per SMEM tile
+  constexpr int NBT = NTILES;                 // SMEM tiles per stage
   constexpr int STG = NBT * TILE;             // bytes per stage
-  constexpr int NSTG = ATMEM ? 3 : 2;         // operand stages
+  constexpr int NSTG = 2;                     // operand stages
   constexpr uint32_t LBO = 128;               // next core matrix along K
   constexpr uint32_t SBO = (KC / 4) * 128;    // next 8-row group along M/N
-  // 128-row tile: the hi*hi and the (2^-11 smaller) cross products go to
-  // separate accumulators, because tensor-core FP32 accumulation does not
-  // round to nearest and its error grows with the number of MMAs summed.
-  constexpr bool SPLIT = ATMEM;
   constexpr uint32_t TCOLS = 512;
-  constexpr uint32_t HX_COL = SPLIT ? 64 : 0;
-  constexpr uint32_t S_COL = SPLIT ? 128 : 256;
-  constexpr uint32_t SX_COL = SPLIT ? 192 : 256;
-  constexpr uint32_t A_COL = 256;             // ATMEM: A stages, 10 tiles x 8 columns each
-  constexpr bool STAGED = ATMEM;
-  constexpr int SROW = 129;                   // staging row stride (floats), 1 mod 32
+  constexpr uint32_t S_COL = 256;
   static_assert(NSTG * STG <= 163840, "stage memory");
-  static_assert(!ATMEM || A_COL + NSTG * 80 <= TCOLS, "tensor memory");
 
   extern __shared__ __align__(16) unsigned char dsm[];
   unsigned char *stages = dsm + ((1024u - (smem_u32(dsm) & 1023u)) & 1023u);
   unsigned char *inbuf = stages + NSTG * STG;
   WsShared &sh = *reinterpret_cast<WsShared *>(inbuf + WS_NIN * in_bytes);
-  float *staging = reinterpret_cast<float *>(reinterpret_cast<unsigned char *>(&sh) + sizeof(WsShared));
-  float2(*epi)[32][17] = reinterpret_cast<float2(*)[32][17]>(staging);
+  float2(*epi)[32][17] = reinterpret_cast<float2(*)[32][17]>(reinterpret_cast<unsigned char *>(&sh) +
+                                                            sizeof(WsShared));
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const float s3[3] = {sx, sy, sz};
@@ -434,7 +400,7 @@ __global__ void __launch_bounds__(WS_NT, 1) k_assemble_tc(
     int t = 0;
     bool run = true;
     for (int k = blockIdx.x; k < nelem_list && run; k += G) {
-      const ElemInfo I = elem_info<R>(order, k, qoff, qpoff, aoff, doff, amax);
+      const ElemInfo I = elem_info(order, k, qoff, qpoff, aoff, doff, amax);
       if (!I.ok) {
         if (tid == 0) set_err(err, DEVERR_SHAPE);
         continue;
@@ -463,133 +429,53 @@ __global__ void __launch_bounds__(WS_NT, 1) k_assemble_tc(
             break;
           }
           tc_fence_after();
-          if constexpr (ATMEM) {
-            // thread = basis row r (lane quarter of the warp), 4 of the 8 points
-            const int q4 = warp & 3, ph = warp >> 2;
-            const int r = q4 * 32 + lane;
-            float av[10][4];
-            if (r < 64) {
-              const int ia = r & 3, ib = (r >> 2) & 3, ic = r >> 4;
+          // 256-row tile: every operand in shared memory, core matrices of
+          // 8 rows x 4 points, lane -> (row = lane/4, point = lane%4)
+          constexpr int CMW = R / 32;
+          const int ncm = (I.npad / 8) * (KC / 4);
 #pragma unroll
-              for (int kk = 0; kk < 4; ++kk) {
-                const float *pq = pt + 32 * (4 * ph + kk);
-                const float lx = pq[ia], ly = pq[4 + ib], lz = pq[8 + ic];
-                const float bv = lx * ly * lz;
-                const float gx = pq[12 + ia] * ly * lz;
-                const float gy = lx * pq[16 + ib] * lz;
-                const float gz = lx * ly * pq[20 + ic];
-                const float r2 = pq[27], r1 = pq[28];
-                const float val[5] = {r2 * gx, r2 * gy, r2 * gz, r1 * bv, vq[4 * ph + kk] * (r1 * bv)};
-#pragma unroll
-                for (int tt = 0; tt < 5; ++tt) {
-                  const float hi = tf32_rn(val[tt]);
-                  av[2 * tt][kk] = hi;
-                  av[2 * tt + 1][kk] = tf32_rn(val[tt] - hi);
-                }
-              }
-            } else if (r < I.n) {
-              const int code = ecs[r - 64];
+          for (int u = 0; u < CMW; ++u) {
+            const int cm = warp + 8 * u;
+            if (cm >= ncm) break;
+            const int rg = cm >> 1, kg = cm & 1;
+            const int cidx = rg * 8 + (lane >> 2);
+            const int qq = kg * 4 + (lane & 3);
+            const float *pq = pt + 32 * qq;
+            float bv = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+            if (cidx < 64) {
+              const int ia = cidx & 3, ib = (cidx >> 2) & 3, ic = cidx >> 4;
+              const float lx = pq[ia], ly = pq[4 + ib], lz = pq[8 + ic];
+              bv = lx * ly * lz;
+              gx = pq[12 + ia] * ly * lz;
+              gy = lx * pq[16 + ib] * lz;
+              gz = lx * ly * pq[20 + ic];
+            } else if (cidx < I.n) {
+              const int code = ecs[cidx - 64];
               const int slot = code >> 3, lv = code & 7;
-              const float4 p0 = *reinterpret_cast<const float4 *>(ip + (slot * 4 + 0) * 8 + 4 * ph);
-              const float4 p1 = *reinterpret_cast<const float4 *>(ip + (slot * 4 + 1) * 8 + 4 * ph);
-              const float4 p2 = *reinterpret_cast<const float4 *>(ip + (slot * 4 + 2) * 8 + 4 * ph);
-              const float4 p3 = *reinterpret_cast<const float4 *>(ip + (slot * 4 + 3) * 8 + 4 * ph);
-              const float ps0[4] = {p0.x, p0.y, p0.z, p0.w}, ps1[4] = {p1.x, p1.y, p1.z, p1.w};
-              const float ps2[4] = {p2.x, p2.y, p2.z, p2.w}, ps3[4] = {p3.x, p3.y, p3.z, p3.w};
+              const float *pp = ip + (slot * 4) * 8 + qq;
+              const float p0 = pp[0], p1 = pp[8], p2 = pp[16], p3 = pp[24];
+              float hh[3], dh[3];
 #pragma unroll
-              for (int kk = 0; kk < 4; ++kk) {
-                const float *pq = pt + 32 * (4 * ph + kk);
-                float hh[3], dh[3];
-#pragma unroll
-                for (int d = 0; d < 3; ++d) {
-                  const int bit = (lv >> d) & 1;
-                  const float xv = pq[24 + d];
-                  hh[d] = bit ? 0.5f * (1.0f + xv) : 0.5f * (1.0f - xv);
-                  dh[d] = (bit ? 0.5f : -0.5f) * s3[d];
-                }
-                const float phi = hh[0] * hh[1] * hh[2];
-                const float bv = phi * ps0[kk];
-                const float gx = dh[0] * hh[1] * hh[2] * ps0[kk] + phi * ps1[kk];
-                const float gy = hh[0] * dh[1] * hh[2] * ps0[kk] + phi * ps2[kk];
-                const float gz = hh[0] * hh[1] * dh[2] * ps0[kk] + phi * ps3[kk];
-                const float r2 = pq[27], r1 = pq[28];
-                const float val[5] = {r2 * gx, r2 * gy, r2 * gz, r1 * bv, vq[4 * ph + kk] * (r1 * bv)};
-#pragma unroll
-                for (int tt = 0; tt < 5; ++tt) {
-                  const float hi = tf32_rn(val[tt]);
-                  av[2 * tt][kk] = hi;
-                  av[2 * tt + 1][kk] = tf32_rn(val[tt] - hi);
-                }
+              for (int d = 0; d < 3; ++d) {
+                const int bit = (lv >> d) & 1;
+                const float xv = pq[24 + d];
+                hh[d] = bit ? 0.5f * (1.0f + xv) : 0.5f * (1.0f - xv);
+                dh[d] = (bit ? 0.5f : -0.5f) * s3[d];
               }
-            } else {
-#pragma unroll
-              for (int tt = 0; tt < 10; ++tt)
-#pragma unroll
-                for (int kk = 0; kk < 4; ++kk) av[tt][kk] = 0.0f;
+              const float phi = hh[0] * hh[1] * hh[2];
+              bv = phi * p0;
+              gx = dh[0] * hh[1] * hh[2] * p0 + phi * p1;
+              gy = hh[0] * dh[1] * hh[2] * p0 + phi * p2;
+              gz = hh[0] * hh[1] * dh[2] * p0 + phi * p3;
             }
-            const uint32_t abase = tmem + ((uint32_t)(q4 * 32) << 16) + A_COL + s * 80 + 4 * ph;
+            const float r2 = pq[27], r1 = pq[28];
+            const float val[5] = {r2 * gx, r2 * gy, r2 * gz, r1 * bv, vq[qq] * (r1 * bv)};
+            const uint32_t off = (uint32_t)rg * SBO + (uint32_t)kg * LBO + (uint32_t)lane * 4;
 #pragma unroll
-            for (int tt = 0; tt < 10; ++tt)
-              tmem_st4(abase + tt * 8, av[tt][0], av[tt][1], av[tt][2], av[tt][3]);
-            const int rb = r - 64;
-            if (rb >= 0 && rb < I.nenr16) {
-              const uint32_t off = (uint32_t)(rb >> 3) * SBO + (uint32_t)ph * LBO + (uint32_t)(rb & 7) * 16;
-#pragma unroll
-              for (int tt = 0; tt < 8; ++tt)
-                *reinterpret_cast<float4 *>(sp + tt * TILE + off) =
-                    make_float4(av[tt][0], av[tt][1], av[tt][2], av[tt][3]);
-            }
-            tmem_wait_st();
-            tc_fence_before();
-          } else {
-            // 256-row tile: every operand in shared memory, core matrices of
-            // 8 rows x 4 points, lane -> (row = lane/4, point = lane%4)
-            constexpr int CMW = R / 32;
-            const int ncm = (I.npad / 8) * (KC / 4);
-#pragma unroll
-            for (int u = 0; u < CMW; ++u) {
-              const int cm = warp + 8 * u;
-              if (cm >= ncm) break;
-              const int rg = cm >> 1, kg = cm & 1;
-              const int cidx = rg * 8 + (lane >> 2);
-              const int qq = kg * 4 + (lane & 3);
-              const float *pq = pt + 32 * qq;
-              float bv = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
-              if (cidx < 64) {
-                const int ia = cidx & 3, ib = (cidx >> 2) & 3, ic = cidx >> 4;
-                const float lx = pq[ia], ly = pq[4 + ib], lz = pq[8 + ic];
-                bv = lx * ly * lz;
-                gx = pq[12 + ia] * ly * lz;
-                gy = lx * pq[16 + ib] * lz;
-                gz = lx * ly * pq[20 + ic];
-              } else if (cidx < I.n) {
-                const int code = ecs[cidx - 64];
-                const int slot = code >> 3, lv = code & 7;
-                const float *pp = ip + (slot * 4) * 8 + qq;
-                const float p0 = pp[0], p1 = pp[8], p2 = pp[16], p3 = pp[24];
-                float hh[3], dh[3];
-#pragma unroll
-                for (int d = 0; d < 3; ++d) {
-                  const int bit = (lv >> d) & 1;
-                  const float xv = pq[24 + d];
-                  hh[d] = bit ? 0.5f * (1.0f + xv) : 0.5f * (1.0f - xv);
-                  dh[d] = (bit ? 0.5f : -0.5f) * s3[d];
-                }
-                const float phi = hh[0] * hh[1] * hh[2];
-                bv = phi * p0;
-                gx = dh[0] * hh[1] * hh[2] * p0 + phi * p1;
-                gy = hh[0] * dh[1] * hh[2] * p0 + phi * p2;
-                gz = hh[0] * hh[1] * dh[2] * p0 + phi * p3;
-              }
-              const float r2 = pq[27], r1 = pq[28];
-              const float val[5] = {r2 * gx, r2 * gy, r2 * gz, r1 * bv, vq[qq] * (r1 * bv)};
-              const uint32_t off = (uint32_t)rg * SBO + (uint32_t)kg * LBO + (uint32_t)lane * 4;
-#pragma unroll
-              for (int tt = 0; tt < 5; ++tt) {
-                const float hi = tf32_rn(val[tt]);
-                *reinterpret_cast<float *>(sp + (2 * tt) * TILE + off) = hi;
-                *reinterpret_cast<float *>(sp + (2 * tt + 1) * TILE + off) = tf32_rn(val[tt] - hi);
-              }
+            for (int tt = 0; tt < 5; ++tt) {
+              const float hi = tf32_rn(val[tt]);
+              *reinterpret_cast<float *>(sp + (2 * tt) * TILE + off) = hi;
+              *reinterpret_cast<float *>(sp + (2 * tt + 1) * TILE + off) = tf32_rn(val[tt] - hi);
             }
           }
           fence_proxy_async();
@@ -608,10 +494,10 @@ __global__ void __launch_bounds__(WS_NT, 1) k_assemble_tc(
       int t = 0, a = 0;
       bool run = true;
       for (int k = blockIdx.x; k < nelem_list && run; k += G) {
-        const ElemInfo I = elem_info<R>(order, k, qoff, qpoff, aoff, doff, amax);
+        const ElemInfo I = elem_info(order, k, qoff, qpoff, aoff, doff, amax);
         if (!I.go) continue;
         const uint32_t idE = idesc_tf32(128, I.nenr16);
-        const uint32_t tH = tmem, tHx = tmem + HX_COL, tS = tmem + S_COL, tSx = tmem + SX_COL;
+        const uint32_t tH = tmem, tS = tmem + S_COL;
         for (int mt = 0; mt < I.nmt && run; ++mt, ++a) {
           if (a > 0 && !mbar_wait(&sh.aempty, (a - 1) & 1)) {
             run = false;
@@ -627,42 +513,21 @@ __global__ void __launch_bounds__(WS_NT, 1) k_assemble_tc(
             tc_fence_after();
             const uint32_t st = sbase + s * STG;
             const uint32_t first = (c == 0) ? 0u : 1u;
-            const uint32_t fx = SPLIT ? first : 1u;
-            if constexpr (ATMEM) {
-              auto Bd = [&](int tt) { return sdesc(st + tt * TILE, LBO, SBO); };
-              const uint32_t aS = tmem + A_COL + s * 80;
-              // H_V on the enrichment columns: ZV^T Z[64:]
-              mma_tf32_ta(tH, aS + 8 * 8, Bd(6), idE, first);
-              mma_tf32_ta(tHx, aS + 8 * 8, Bd(7), idE, fx);
-              mma_tf32_ta(tHx, aS + 9 * 8, Bd(6), idE, 1u);
-              // T on the enrichment columns: sum_d Y_d^T Y_d[64:]
+            const uint32_t moff = (uint32_t)mt * 16u * SBO;   // M-tile: 128 rows
+            const uint32_t eoff = 8u * SBO;                   // enrichment rows start at 64
+            auto D = [&](int tt, uint32_t extra) { return sdesc(st + tt * TILE + extra, LBO, SBO); };
+            mma_tf32(tH, D(8, moff), D(6, eoff), idE, first);
+            mma_tf32(tH, D(8, moff), D(7, eoff), idE, 1u);
+            mma_tf32(tH, D(9, moff), D(6, eoff), idE, 1u);
 #pragma unroll
-              for (int d = 0; d < 3; ++d) {
-                mma_tf32_ta(tH, aS + (2 * d) * 8, Bd(2 * d), idE, 1u);
-                mma_tf32_ta(tHx, aS + (2 * d) * 8, Bd(2 * d + 1), idE, 1u);
-                mma_tf32_ta(tHx, aS + (2 * d + 1) * 8, Bd(2 * d), idE, 1u);
-              }
-              // S on the enrichment columns: Z^T Z[64:]
-              mma_tf32_ta(tS, aS + 6 * 8, Bd(6), idE, first);
-              mma_tf32_ta(tSx, aS + 6 * 8, Bd(7), idE, fx);
-              mma_tf32_ta(tSx, aS + 7 * 8, Bd(6), idE, 1u);
-            } else {
-              const uint32_t moff = (uint32_t)mt * 16u * SBO;   // M-tile: 128 rows
-              const uint32_t eoff = 8u * SBO;                   // enrichment rows start at 64
-              auto D = [&](int tt, uint32_t extra) { return sdesc(st + tt * TILE + extra, LBO, SBO); };
-              mma_tf32(tH, D(8, moff), D(6, eoff), idE, first);
-              mma_tf32(tHx, D(8, moff), D(7, eoff), idE, fx);
-              mma_tf32(tHx, D(9, moff), D(6, eoff), idE, 1u);
-#pragma unroll
-              for (int d = 0; d < 3; ++d) {
-                mma_tf32(tH, D(2 * d, moff), D(2 * d, eoff), idE, 1u);
-                mma_tf32(tHx, D(2 * d, moff), D(2 * d + 1, eoff), idE, 1u);
-                mma_tf32(tHx, D(2 * d + 1, moff), D(2 * d, eoff), idE, 1u);
-              }
-              mma_tf32(tS, D(6, moff), D(6, eoff), idE, first);
-              mma_tf32(tSx, D(6, moff), D(7, eoff), idE, fx);
-              mma_tf32(tSx, D(7, moff), D(6, eoff), idE, 1u);
+            for (int d = 0; d < 3; ++d) {
+              mma_tf32(tH, D(2 * d, moff), D(2 * d, eoff), idE, 1u);
+              mma_tf32(tH, D(2 * d, moff), D(2 * d + 1, eoff), idE, 1u);
+              mma_tf32(tH, D(2 * d + 1, moff), D(2 * d, eoff), idE, 1u);
             }
+            mma_tf32(tS, D(6, moff), D(6, eoff), idE, first);
+            mma_tf32(tS, D(6, moff), D(7, eoff), idE, 1u);
+            mma_tf32(tS, D(7, moff), D(6, eoff), idE, 1u);
             mma_commit(&sh.sempty[s]);
           }
           if (!run) break;
@@ -714,7 +579,7 @@ __global__ void __launch_bounds__(WS_NT, 1) k_assemble_tc(
         if (sd[i] >= 0) atomicAdd(out + sd[i], value_of(lane, i));
     };
     for (int k = blockIdx.x; k < nelem_list && run; k += G) {
-      const ElemInfo I = elem_info<R>(order, k, qoff, qpoff, aoff, doff, amax);
+      const ElemInfo I = elem_info(order, k, qoff, qpoff, aoff, doff, amax);
       if (!I.go) continue;
       const int32_t *m = smap + soff[I.e];
       const int n = I.n;
@@ -729,57 +594,24 @@ __global__ void __launch_bounds__(WS_NT, 1) k_assemble_tc(
         }
         tc_fence_after();
         const int rbase = mt * 128 + quarter * 32;
-        if constexpr (STAGED) {
-          // drain this warp's 32 rows: H strip, then S strip (FP32 sums of
-          // the hi*hi and cross accumulators)
-          float *row = staging + (quarter * 32 + lane) * SROW;
-          for (int cb = 0; cb < ncb; ++cb) {
-            float hv[16], hx[16];
-            tmem_ld16(tmem + lanebase + cb * 16, hv);
-            tmem_ld16(tmem + HX_COL + lanebase + cb * 16, hx);
+        for (int cb = 0; cb < ncb; ++cb) {
+          for (int which = 0; which < 2; ++which) {
+            if (which == 0 && !(want & PUFE_WANT_H)) continue;
+            if (which == 1 && !(want & PUFE_WANT_S)) continue;
+            float hv[16];
+            tmem_ld16((which == 0 ? tmem : tmem + S_COL) + lanebase + cb * 16, hv);
 #pragma unroll
-            for (int i = 0; i < 16; ++i) row[cb * 16 + i] = hv[i] + hx[i];
-            tmem_ld16(tmem + S_COL + lanebase + cb * 16, hv);
-            tmem_ld16(tmem + SX_COL + lanebase + cb * 16, hx);
-#pragma unroll
-            for (int i = 0; i < 16; ++i) row[I.nenr16 + cb * 16 + i] = hv[i] + hx[i];
+            for (int i = 0; i < 16; ++i) stg[lane][i] = make_float2(hv[i], 0.0f);
+            __syncwarp();
+            scatter_block(m, n, rbase, cb, which == 0 ? H : S, [&](int rl, int cl) {
+              return (double)stg[rl][cl].x;
+            });
+            __syncwarp();
           }
-          tc_fence_before();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(&sh.aempty);
-          // scatter from shared memory while the next element's MMAs run
-          const float *blk = staging + (quarter * 32) * SROW;
-          for (int cb = 0; cb < ncb; ++cb) {
-            if (want & PUFE_WANT_H)
-              scatter_block(m, n, rbase, cb, H, [&](int rl, int cl) {
-                return (double)blk[rl * SROW + cb * 16 + cl];
-              });
-            if (want & PUFE_WANT_S)
-              scatter_block(m, n, rbase, cb, S, [&](int rl, int cl) {
-                return (double)blk[rl * SROW + I.nenr16 + cb * 16 + cl];
-              });
-          }
-          __syncwarp();
-        } else {
-          for (int cb = 0; cb < ncb; ++cb) {
-            for (int which = 0; which < 2; ++which) {
-              if (which == 0 && !(want & PUFE_WANT_H)) continue;
-              if (which == 1 && !(want & PUFE_WANT_S)) continue;
-              float hv[16];
-              tmem_ld16((which == 0 ? tmem : tmem + S_COL) + lanebase + cb * 16, hv);
-#pragma unroll
-              for (int i = 0; i < 16; ++i) stg[lane][i] = make_float2(hv[i], 0.0f);
-              __syncwarp();
-              scatter_block(m, n, rbase, cb, which == 0 ? H : S, [&](int rl, int cl) {
-                return (double)stg[rl][cl].x;
-              });
-              __syncwarp();
-            }
-          }
-          tc_fence_before();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(&sh.aempty);
         }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&sh.aempty);
       }
     }
   } else {
@@ -788,7 +620,7 @@ __global__ void __launch_bounds__(WS_NT, 1) k_assemble_tc(
       int lt = 0;
       bool run = true;
       for (int k = blockIdx.x; k < nelem_list && run; k += G) {
-        const ElemInfo I = elem_info<R>(order, k, qoff, qpoff, aoff, doff, amax);
+        const ElemInfo I = elem_info(order, k, qoff, qpoff, aoff, doff, amax);
         if (!I.go) continue;
         const float *lpsi = psi + 4 * toff32[I.e];
         const float *lpt = ptab + 32 * qpoff[I.e];
@@ -829,9 +661,9 @@ __global__ void __launch_bounds__(WS_NT, 1) k_assemble_tc(
 }
 
 // shared-memory bytes of one k_assemble_tc launch
-static size_t assemble_smem(int R, int in_bytes) {
-  const size_t stage = (R == 128) ? 3 * (size_t)(8 * 64 * WS_KC * 4) : 2 * (size_t)(NTILES * 256 * WS_KC * 4);
-  const size_t tail = (R == 128) ? (size_t)128 * 129 * 4 : (size_t)4 * 32 * 17 * 8;
+static size_t assemble_smem(int in_bytes) {
+  const size_t stage = 2 * (size_t)(NTILES * 256 * WS_KC * 4);
+  const size_t tail = (size_t)4 * 32 * 17 * 8;
   return (size_t)1024 + stage + WS_NIN * (size_t)in_bytes + sizeof(WsShared) + tail;
 }
 
@@ -1017,253 +849,13 @@ __global__ void __launch_bounds__(ADJ_NT) k_adjoint_f32(
 }
 
 // ---------------------------------------------------------------------------
-// K5 enrichment strip on the tensor cores (elements with n_e <= 128).
+// K5 enrichment strip on the CUDA cores (elements with n_e <= 128).
 // With b = (b_F, b_E) split into the 64 FE functions and the enrichments,
-//   b^T Hbar b = b_F^T Hbar_FF b_F + sum_{r in E} b_r sum_j B[r][j] b_j,
-//   B[r][j] = Hbar_rj + Hbar_jr (j in F),  B[r][j] = Hbar_rj (j in E).
-// The FE-FE form is done by sum factorization (k_adjoint_fefe, which stores
-// Vbar); this kernel adds the rest:
-//   z_q = sqrt(w_q) b_q,  D[q][r] = sum_j z_qj B[r][j]  (M = 128 points,
-//   N = n_E rounded to 16, K = every basis index j), then
-//   Vbar_q += sum_r D[q][r] z_qr,
-// one thread per point reading its TMEM lane.  B is gathered once per
-// element into shared memory (two TF32 terms); z is built chunk by chunk
-// (32 basis indices) into double-buffered stages; products hi*hi and the
-// cross terms go to separate TMEM accumulators.
-// ---------------------------------------------------------------------------
-constexpr int AT_NT = 512;
-constexpr int AT_KJ = 32;   // basis indices per z chunk
-
-struct AtShared {
-  uint64_t sempty[2], dbar;
-  uint32_t tmem;
-  int good;
-  float L[128][3][4];
-  float xi[128][3];
-  float sw[128];
-  float acc[128];
-  int ecs[64];
-};
-
-__global__ void __launch_bounds__(AT_NT, 1) k_adjoint_strip(
-    const int32_t *__restrict__ order, const int64_t *__restrict__ qoff,
-    const int64_t *__restrict__ qpoff, const float4 *__restrict__ qdat,
-    const int64_t *__restrict__ doff, const int32_t *__restrict__ ecol,
-    const int32_t *__restrict__ aoff, const int64_t *__restrict__ toff32,
-    const float *__restrict__ psi, const int64_t *__restrict__ soff,
-    const int32_t *__restrict__ smap, const double *__restrict__ Hbar, int npad_max,
-    double *__restrict__ Vbar, unsigned *err) {
-  constexpr uint32_t LBO = 128;
-  constexpr uint32_t SBO_Z = (AT_KJ / 4) * 128;   // z tile: 128 rows x 32
-  constexpr int ZTILE = 128 * AT_KJ * 4;          // bytes per z tile (hi or lo)
-  extern __shared__ __align__(16) unsigned char dsm[];
-  unsigned char *base = dsm + ((1024u - (smem_u32(dsm) & 1023u)) & 1023u);
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int e = order[blockIdx.x];
-  const int64_t q0 = qoff[e];
-  const int Q = (int)(qoff[e + 1] - q0);
-  const int A = aoff[e + 1] - aoff[e];
-  const int n = (int)(doff[e + 1] - doff[e]);
-  const int npad = (n + 15) & ~15;
-  const int ne = n - 64, ne16 = (ne + 15) & ~15;
-  if (n > 128 || npad > npad_max) {
-    if (tid == 0) set_err(err, DEVERR_SHAPE);
-    return;
-  }
-  if (ne <= 0) return;   // FE-only element: Vbar is already complete
-  const uint32_t SBO_H = (uint32_t)(npad / 4) * 128;   // B tile: ne16 rows x npad
-  const int HT = ne16 * npad * 4;                       // bytes per B tile
-  unsigned char *hH = base, *hL = base + HT;
-  unsigned char *zst = base + ((2 * HT + 1023) & ~1023);   // 2 stages x (hi, lo)
-  AtShared &sh = *reinterpret_cast<AtShared *>(zst + 4 * ZTILE);
-  const int32_t *ec = ecol + (doff[e] - 64ll * e);
-  const float *pe = psi + 4 * toff32[e];
-  const float4 *qe = qdat + qpoff[e];
-  const int32_t *m = smap + soff[e];
-
-  if (warp == 0) tmem_alloc(&sh.tmem, 128);
-  if (tid == 0) {
-    mbar_init(&sh.sempty[0], 1);
-    mbar_init(&sh.sempty[1], 1);
-    mbar_init(&sh.dbar, 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  if (tid < ne) sh.ecs[tid] = ec[tid];
-  // ---- gather B (rows r = enrichment, K = j) into the two TF32 tiles --------
-  {
-    const int ncm = (ne16 / 8) * (npad / 4);
-    for (int c0 = warp; c0 < ncm; c0 += 4 * (AT_NT / 32)) {
-      int sl[4], st[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int cm = c0 + u * (AT_NT / 32);
-        const int rg = cm / (npad / 4), kg = cm - rg * (npad / 4);
-        const int r = rg * 8 + (lane >> 2), j = kg * 4 + (lane & 3);
-        const bool in = cm < ncm && r < ne && j < n;
-        sl[u] = in ? m[(64 + r) * n + j] : -1;
-        st[u] = (in && j < 64) ? m[j * n + 64 + r] : -1;
-      }
-      float hv[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-        hv[u] = (sl[u] >= 0 ? (float)Hbar[sl[u]] : 0.0f) + (st[u] >= 0 ? (float)Hbar[st[u]] : 0.0f);
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int cm = c0 + u * (AT_NT / 32);
-        if (cm >= ncm) break;
-        const int rg = cm / (npad / 4), kg = cm - rg * (npad / 4);
-        const uint32_t off = (uint32_t)rg * SBO_H + (uint32_t)kg * LBO + (uint32_t)lane * 4;
-        const float hi = tf32_rn(hv[u]);
-        *reinterpret_cast<float *>(hH + off) = hi;
-        *reinterpret_cast<float *>(hL + off) = tf32_rn(hv[u] - hi);
-      }
-    }
-  }
-  fence_proxy_async();
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tD = sh.tmem, tX = sh.tmem + 64;
-  const uint32_t idD = idesc_tf32(128, ne16);
-  const uint32_t hbase = smem_u32(hH), lbase = smem_u32(hL), zbase = smem_u32(zst);
-  const int nkc = (npad + AT_KJ - 1) / AT_KJ;
-  int g = 0;          // chunk counter (stage phases)
-  int dcount = 0;     // M-tile counter (dbar phases)
-  bool ok = true;
-  for (int mt = 0; mt * 128 < Q && ok; ++mt) {
-    // per-point tables of this M-tile
-    if (tid < 128) {
-      const int qg = mt * 128 + tid;
-      const float4 x4 = (qg < Q) ? qe[qg] : make_float4(0.f, 0.f, 0.f, 0.f);
-      const float xv[3] = {x4.x, x4.y, x4.z};
-#pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        float L[4], dL[4];
-        lagrange3f(xv[d], L, dL);
-#pragma unroll
-        for (int c = 0; c < 4; ++c) sh.L[tid][d][c] = L[c];
-        sh.xi[tid][d] = xv[d];
-      }
-      sh.sw[tid] = sqrtf(x4.w);   // zero on padding and beyond Q
-      sh.acc[tid] = 0.0f;
-    }
-    __syncthreads();
-    for (int kc = 0; kc < nkc; ++kc, ++g) {
-      const int s = g & 1;
-      if (g >= 2) {
-        int good = 1;
-        if (tid == 0) good = mbar_wait(&sh.sempty[s], ((g >> 1) - 1) & 1) ? 1 : 0;
-        if (!__syncthreads_and(good)) {
-          ok = false;
-          break;
-        }
-      }
-      unsigned char *zh = zst + s * 2 * ZTILE, *zl = zh + ZTILE;
-      // z chunk: rows q (128), K = basis index j in [kc*32, kc*32 + 32)
-      for (int cm = warp; cm < 16 * (AT_KJ / 4); cm += AT_NT / 32) {
-        const int rg = cm / (AT_KJ / 4), kg = cm - rg * (AT_KJ / 4);
-        const int ql = rg * 8 + (lane >> 2);
-        const int j = kc * AT_KJ + kg * 4 + (lane & 3);
-        float b = 0.0f;
-        if (j < 64) {
-          b = sh.L[ql][0][j & 3] * sh.L[ql][1][(j >> 2) & 3] * sh.L[ql][2][j >> 4];
-        } else if (j < n) {
-          const int code = sh.ecs[j - 64];
-          const int lv = code & 7;
-          const int qg = mt * 128 + ql;
-          const float phi = (((lv & 1) ? 1.0f + sh.xi[ql][0] : 1.0f - sh.xi[ql][0]) *
-                             ((lv & 2) ? 1.0f + sh.xi[ql][1] : 1.0f - sh.xi[ql][1]) *
-                             ((lv & 4) ? 1.0f + sh.xi[ql][2] : 1.0f - sh.xi[ql][2])) * 0.125f;
-          const float p0 = (qg < Q) ? pe[((int64_t)(qg >> 3) * A + (code >> 3)) * 32 + (qg & 7)] : 0.0f;
-          b = phi * p0;
-        }
-        const float z = sh.sw[ql] * b;
-        const uint32_t off = (uint32_t)rg * SBO_Z + (uint32_t)kg * LBO + (uint32_t)lane * 4;
-        const float hi = tf32_rn(z);
-        *reinterpret_cast<float *>(zh + off) = hi;
-        *reinterpret_cast<float *>(zl + off) = tf32_rn(z - hi);
-      }
-      fence_proxy_async();
-      __syncthreads();
-      if (tid == 0) {
-        tc_fence_after();
-        const uint32_t za = zbase + s * 2 * ZTILE, zla = za + ZTILE;
-        const int nks = min(AT_KJ, npad - kc * AT_KJ) / 8;
-        for (int ks = 0; ks < nks; ++ks) {
-          const uint32_t ko = (uint32_t)ks * 2u * LBO;
-          const uint32_t hk = (uint32_t)((kc * AT_KJ + ks * 8) / 4) * LBO;
-          const uint32_t first = (kc == 0 && ks == 0) ? 0u : 1u;
-          mma_tf32(tD, sdesc(za + ko, LBO, SBO_Z), sdesc(hbase + hk, LBO, SBO_H), idD, first);
-          mma_tf32(tX, sdesc(za + ko, LBO, SBO_Z), sdesc(lbase + hk, LBO, SBO_H), idD, first);
-          mma_tf32(tX, sdesc(zla + ko, LBO, SBO_Z), sdesc(hbase + hk, LBO, SBO_H), idD, 1u);
-        }
-        mma_commit(&sh.sempty[s]);
-        if (kc == nkc - 1) mma_commit(&sh.dbar);
-      }
-    }
-    if (!ok) break;
-    {
-      int good = 1;
-      if (tid == 0) good = mbar_wait(&sh.dbar, dcount & 1) ? 1 : 0;
-      if (!__syncthreads_and(good)) {
-        ok = false;
-        break;
-      }
-      ++dcount;
-    }
-    tc_fence_after();
-    // epilogue: lane = point; warps w and w+4 split the column blocks
-    if (warp < 8) {
-      const int quarter = warp & 3, half = warp >> 2;
-      const int ql = quarter * 32 + lane;
-      const uint32_t lanebase = (uint32_t)(quarter * 32) << 16;
-      const int qg = mt * 128 + ql;
-      float part = 0.0f;
-      for (int cb = half; cb * 16 < ne16; cb += 2) {
-        float dh[16], dx[16];
-        tmem_ld16(tD + lanebase + cb * 16, dh);
-        tmem_ld16(tX + lanebase + cb * 16, dx);
-#pragma unroll
-        for (int u = 0; u < 16; ++u) {
-          const int r = cb * 16 + u;
-          float b = 0.0f;
-          if (r < ne && qg < Q) {
-            const int code = sh.ecs[r];
-            const int lv = code & 7;
-            const float phi = (((lv & 1) ? 1.0f + sh.xi[ql][0] : 1.0f - sh.xi[ql][0]) *
-                               ((lv & 2) ? 1.0f + sh.xi[ql][1] : 1.0f - sh.xi[ql][1]) *
-                               ((lv & 4) ? 1.0f + sh.xi[ql][2] : 1.0f - sh.xi[ql][2])) * 0.125f;
-            b = phi * pe[((int64_t)(qg >> 3) * A + (code >> 3)) * 32 + (qg & 7)];
-          }
-          part = fmaf(dh[u] + dx[u], sh.sw[ql] * b, part);
-        }
-      }
-      atomicAdd(&sh.acc[ql], part);
-    }
-    tc_fence_before();
-    __syncthreads();
-    if (tid < 128) {
-      const int qg = mt * 128 + tid;
-      if (qg < Q) Vbar[q0 + qg] += (double)sh.acc[tid];
-    }
-    __syncthreads();
-    tc_fence_after();
-  }
-  if (!ok && tid == 0) {
-    set_err(err, DEVERR_TIMEOUT);
-    mbar_wait(&sh.dbar, dcount & 1);
-  }
-  tc_fence_before();
-  __syncthreads();
-  if (warp == 0) {
-    tc_fence_after();
-    tmem_dealloc(sh.tmem, 128);
-  }
-}
-
-// ---------------------------------------------------------------------------
-// K5 enrichment strip on the CUDA cores (elements with n_e <= 128): the same
-// split as above, one thread per point, in FP32 with round to nearest.
+//   b^T Hbar b = b_F^T Hbar_FF b_F + sum_{r in E} b_r g_r,
+//   g_r = sum_j B[r][j] b_j,  B[r][j] = Hbar_rj + Hbar_jr (j in F),
+// where the FE-FE form is done by sum factorization (k_adjoint_fefe, which
+// stores Vbar) and this kernel adds w_q sum_r b_r g_r, one thread per point,
+// in FP32 with round to nearest:
 //   FE columns:  g_r += sum_(abc) B[r][(abc)] L_a(x) L_b(y) L_c(z), factorized
 //                per point (84 multiply-adds per r instead of 128);
 //   E columns:   the E-E form is symmetric in (r, s), so only s >= r is kept:
@@ -1399,9 +991,10 @@ pufe_status launch_tabulate_f32(pufe_ctx *ctx, cudaStream_t st) {
   return PUFE_OK;
 }
 
-// H/S assembly on the mixed path: H = T0 + sum-factorized FE-FE V term,
-// S = S0, then the tensor-core enrichment strip; `vscratch` receives the FP32
-// copy of V that the strip kernel reads (nq_pad floats).
+// H/S assembly on the mixed path: H = kinetic + sum-factorized V term on the
+// FE-FE blocks, S = S0, then the enrichment strips (tensor cores for
+// n_e > 128, CUDA cores otherwise); `vscratch` receives the FP32
+// copy of V that the tensor-core kernel reads (nq_pad floats).
 static pufe_status run_assemble_tc(pufe_ctx *ctx, const double *V, int what, double *H,
                                    double *S, float *vscratch, cudaStream_t st) {
   auto &D = ctx->d;
@@ -1411,7 +1004,7 @@ static pufe_status run_assemble_tc(pufe_ctx *ctx, const double *V, int what, dou
   if (ctx->max_basis > 256) return fail(PUFE_EINVAL, "PUFE_TF32X3 supports n_e <= 256");
   const int amax = std::max(1, ctx->max_alpha);
   const int inb = ((amax * 4 * WS_KC * 4 + WS_KC * 128 + WS_KC * 4) + 127) & ~127;
-  const size_t sm256 = assemble_smem(256, inb);
+  const size_t sm256 = assemble_smem(inb);
   const int nbig = ctx->n_big;
   const int nsmall = (int)ctx->nelem - nbig;
   if (nbig > 0 && sm256 > 227 * 1024)
@@ -1433,9 +1026,9 @@ static pufe_status run_assemble_tc(pufe_ctx *ctx, const double *V, int what, dou
                 sz = (float)(2.0 / ctx->h[2]);
     int nsm = 0;
     PUFE_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device));
-    PUFE_CUDA_TRY(cudaFuncSetAttribute(k_assemble_tc<256>,
+    PUFE_CUDA_TRY(cudaFuncSetAttribute(k_assemble_tc,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm256));
-    k_assemble_tc<256><<<std::min(nbig, nsm), WS_NT, sm256, st>>>(
+    k_assemble_tc<<<std::min(nbig, nsm), WS_NT, sm256, st>>>(
         D.order, D.qoff, D.qpoff, D.ptab, vscratch, D.doff, D.ecol, D.aoff, D.toff32, D.psi32,
         D.soff, D.smap, sx, sy, sz, nbig, amax, inb, what, H, S, D.err);
     PUFE_CUDA_TRY(cudaGetLastError());
