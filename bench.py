@@ -28,6 +28,7 @@ sys.path.insert(0, ROOT)
 METRIC = "quadrature-point contractions/s for H/S assembly + density"
 UNIT = "QPC/s"
 L2_BYTES = 129 * 1024 * 1024
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
 def _dist():
@@ -129,19 +130,29 @@ def run_pufe(args):
     ev_a = torch.cuda.Event(enable_timing=True)
     ev_b = torch.cuda.Event(enable_timing=True)
 
-    def step(timing=None):
+    def step():
         ctx.pufe_tabulate(prec)
-        if timing is not None:
-            timing[0].record(stream)
         ctx.pufe_assemble_HS(V, H, S, prec=prec)
-        if timing is not None:
-            timing[1].record(stream)
         ctx.pufe_density(Cm, f, rho, prec=prec)
         ctx.pufe_assemble_HV_adjoint(H, vbar, prec=prec)
 
     for _ in range(args.warmup):
         step()
     ctx.pufe_sync_status()
+    graph = None
+    if args.launch == "graph":
+        # the whole step captured once into a CUDA graph and replayed: same
+        # kernels, same arguments, no per-launch host overhead
+        graph = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream()
+        side.wait_stream(stream)
+        with torch.cuda.stream(side):
+            step()
+        stream.wait_stream(side)
+        with torch.cuda.graph(graph):
+            step()
+        torch.cuda.synchronize()
+        ctx.pufe_sync_status()
 
     def barrier():
         if ws > 1:
@@ -158,13 +169,23 @@ def run_pufe(args):
         flush.fill_(1.0)
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
-        ka = torch.cuda.Event(enable_timing=True)
-        kb = torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        step((ka, kb))
+        if graph is not None:
+            graph.replay()
+        else:
+            step()
         b.record(stream)
         b.synchronize()
         step_ms.append(a.elapsed_time(b))
+    # the assembly call on its own (stream launches), for the roofline
+    for _ in range(max(3, min(args.steps, 10))):
+        flush.fill_(1.0)
+        ka = torch.cuda.Event(enable_timing=True)
+        kb = torch.cuda.Event(enable_timing=True)
+        ka.record(stream)
+        ctx.pufe_assemble_HS(V, H, S, prec=prec)
+        kb.record(stream)
+        kb.synchronize()
         asm_ms.append(ka.elapsed_time(kb))
     barrier()
     clocks = sampler.stop()
@@ -198,20 +219,37 @@ def run_pufe(args):
     ms_per_step = total_ms / args.steps
     value = ws * ctx.n_q * args.steps / (total_ms * 1e-3)
     peaks, src = _peaks()
+    asm_avg = statistics.mean(asm_ms)
+    achieved = flops_asm / (asm_avg * 1e-3) / 1e12
+    n_big = int((n_e > 128).sum())
     if args.prec == "fp64":
         # FP64 contraction: the recipe's nominal FP64 rate scaled like the
         # measured bf16 figure (measured bf16 x nominal FP64/bf16 ratio)
         peak = peaks["bf16_tflops"] * (1.25 / 2250.0)
         bound, dtype = "alu", "f64"
+        peak_source = f"{src} bf16 x nominal FP64/bf16 ratio"
+        kernels = "k_assemble_fp64"
+        launches_per_step = 4
+    elif n_big == 0:
+        # every element takes the CUDA-core strip: FP32 FMA peak of 152 SMs x
+        # 128 FP32 lanes x 2 flops at the 2070 MHz maximum SM clock
+        peak = FP32_PEAK_TFLOPS
+        bound, dtype = "alu", "f32+f64"
+        peak_source = "derived: 152 SM x 128 FP32 FMA/clk x 2 x 2.07 GHz"
+        kernels = "memset + k_fefe_sumfac + S0 copy + k_strip_sf"
+        # tabulate, fefe, strip, density, adjoint_fefe, adjoint_strip
+        launches_per_step = 6
     else:
         peak = peaks["bf16_tflops"] * (1.1 / 2.25)   # tf32 dense / bf16 dense nominal
-        bound, dtype = "tensor", "tf32x3+f64"
-    asm_avg = statistics.mean(asm_ms)
-    achieved = flops_asm / (asm_avg * 1e-3) / 1e12
-    roof = {"kernel": "assemble_HS", "bound": bound, "achieved": achieved, "peak": peak,
-            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-            "peak_source": f"{src} bf16 x nominal ratio",
-            "flops_per_launch": flops_asm, "avg_launch_ms": asm_avg}
+        bound, dtype = "tensor", "tf32x3+f32+f64"
+        peak_source = f"{src} bf16 x nominal TF32/bf16 ratio"
+        kernels = "memset + k_fefe_sumfac + S0 copy + k_pack_v + k_assemble_tc + k_strip_sf"
+        launches_per_step = 9
+    roof = {"kernel": f"pufe_assemble_HS ({kernels})", "bound": bound, "achieved": achieved,
+            "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+            "peak_source": peak_source,
+            "flops_per_launch": flops_asm, "flops_count": "sum_e 5 Q_e n_e (n_e + 1)",
+            "avg_launch_ms": asm_avg}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -220,12 +258,13 @@ def run_pufe(args):
         "config": {"workload": args.workload, "n_dof": ctx.n_dof, "n_q": ctx.n_q,
                    "n_elem": ctx.n_elem, "nnz": ctx.nnz, "nocc": nocc, "prec": args.prec,
                    "l2": "flushed between steps (2x L2 buffer written)",
+                   "launch": "cuda graph of the step" if graph is not None else "stream",
                    "parallelism": f"replicas x{ws}", "build_s": round(build_s, 3)},
         "roofline": roof,
         "e2e": {"value": ws * ctx.n_q * args.steps / (e2e_ms * 1e-3), "unit": UNIT,
                 "h2d_bytes_per_step": int(V_h.numel() * 8 + C_h.numel() * 8 + f_h.numel() * 8),
                 "d2h_bytes_per_step": int(rho_h.numel() * 8)},
-        "gpu_launches": 4 * args.steps,
+        "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
     }
     if not args.no_cpu_baseline:
@@ -315,6 +354,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="pufe", choices=["pufe", "reference"])
     ap.add_argument("--prec", default="tf32x3", choices=["tf32x3", "fp64"])
+    ap.add_argument("--launch", default="stream", choices=["graph", "stream"],
+                    help="replay the step as a captured CUDA graph, or launch call by call")
     ap.add_argument("--workload", default="c2_rocksalt_12cube")
     ap.add_argument("--cpu-elems", type=int, default=160)
     ap.add_argument("--ref-elems", type=int, default=24)
