@@ -53,14 +53,17 @@ struct EnrVal {
   float b, bx, by, bz;
 };
 
-// floor(x / d) for 0 <= x <= 2^16 and 1 <= d < 2^16 by a multiply-high with
-// ceil(2^32 / d): the rounding error is below x 2^-32 <= 2^-16 < 1/d, so it
-// cannot carry the quotient past the next integer
+// floor(x / d) for 0 <= x <= 2^16 and 1 <= d < 2^16: the high word of
+// x * ceil(2^32 / d) (one __umulhi); the rounding error is below
+// x 2^-32 <= 2^-16 < 1/d, so it cannot carry the quotient past the next
+// integer.  d = 1 (multiplier 2^32) is taken apart.
 struct FastDiv {
-  unsigned long long m;
-  __device__ explicit FastDiv(int d) : m((0x100000000ull + (unsigned)d - 1) / (unsigned)d) {}
+  unsigned m;
+  bool one;
+  __device__ explicit FastDiv(int d)
+      : m(d > 1 ? (unsigned)((0x100000000ull + (unsigned)d - 1) / (unsigned)d) : 0u), one(d <= 1) {}
   __device__ __forceinline__ int div(int x) const {
-    return (int)(((unsigned long long)(unsigned)x * m) >> 32);
+    return one ? x : (int)__umulhi((unsigned)x, m);
   }
 };
 
@@ -455,3 +458,4 @@ pufe_status launch_strip_sf(pufe_ctx *ctx, const double *V, int what, double *H,
 }
 
 }  // namespace pufe
+
