@@ -64,12 +64,16 @@ typedef enum {
 /* Arithmetic of the element contractions. */
 typedef enum {
   PUFE_FP64 = 0,   /* FP64 everywhere (plain CUDA cores) */
-  PUFE_TF32X3 = 1  /* element contractions on the tensor cores (tcgen05
-                      kind::tf32) with every operand split into two TF32
-                      terms (hi*hi + hi*lo + lo*hi), FP32 accumulation per
-                      element, FP64 global accumulation; the constant FE-FE
-                      blocks of T and S are exact FP64 constants; FP32
-                      tabulation, density and adjoint */
+  PUFE_TF32X3 = 1  /* mixed precision: element contractions in FP32 with
+                      FP64 global accumulation.  Elements with n_e <= 128
+                      run on the CUDA cores (FP32 FMA, round to nearest),
+                      the FE-FE V block and the FE-enrichment blocks by sum
+                      factorization over the tensor-product rule; elements
+                      with 128 < n_e <= 256 run their enrichment strip on
+                      the tensor cores (tcgen05 kind::tf32, every operand
+                      split into two TF32 terms, hi*hi + hi*lo + lo*hi).
+                      The constant FE-FE blocks of T and S are exact FP64
+                      constants.  FP32 tabulation, density and adjoint. */
 } pufe_prec;
 
 /* Quadrature modes (Sec. 5.2). */
@@ -152,9 +156,9 @@ pufe_status pufe_tabulate(pufe_ctx *ctx, int prec, void *stream);
  * device) is the local potential at the quadrature points; it may be NULL
  * when only S is wanted.  The arrays are overwritten.  `what` is a mask of
  * PUFE_WANT_H | PUFE_WANT_S.  Requires a prior pufe_tabulate of the same
- * precision.  PUFE_TF32X3 additionally needs every (sub)cell rule to have at
- * least 4 points per axis (so that the FE-FE blocks of T and S are exact
- * constants) and n_e <= 256; otherwise it returns PUFE_EINVAL.
+ * precision.  PUFE_TF32X3 additionally needs every (sub)cell rule to have
+ * between 4 points per axis (so that the FE-FE blocks of T and S are exact
+ * constants) and 16, and n_e <= 256; otherwise it returns PUFE_EINVAL.
  * Asynchronous. */
 pufe_status pufe_assemble_HS(pufe_ctx *ctx, const double *V, int prec, int what,
                              double *H, double *S, void *stream);
@@ -164,8 +168,9 @@ pufe_status pufe_assemble_HS(pufe_ctx *ctx, const double *V, int prec, int what,
  * allocate device memory while they run their solve loop -- for example code
  * that must stay inside a fixed device-memory budget, or that runs where the
  * allocator may not be called.  This call allocates nothing: the FP32 copy of
- * V that the tensor-core assembly reads lives in a library-owned static
- * device array of PUFE_STATIC_MAX_POINTS (4,194,304) floats, resident on
+ * V that the tensor-core assembly reads (elements with n_e > 128) lives in a
+ * library-owned static device array of PUFE_STATIC_MAX_POINTS (4,194,304)
+ * floats, resident on
  * every device that loads the library until the process exits.  Contexts
  * with more padded quadrature points than that return PUFE_EINVAL.  The
  * context itself (built earlier by pufe_build_mesh) and a prior
