@@ -35,6 +35,10 @@
  *   pufe_destroy.  Device pointers must be on the context's device.
  *   Streams: `stream` is a cudaStream_t (NULL = legacy default stream).
  *   Compute calls are asynchronous on that stream; they never synchronise.
+ *   The mixed-precision assembly forks part of its work onto a stream the
+ *   context owns and joins it back into `stream` before returning, so its
+ *   results are ordered on `stream` like any other call.  Issue the calls on
+ *   one context from one host thread at a time.
  *   Errors: every call returns a pufe_status; pufe_last_error() gives a
  *   message for the calling thread.  No call aborts or throws.
  */

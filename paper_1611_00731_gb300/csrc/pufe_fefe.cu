@@ -185,13 +185,12 @@ __global__ void __launch_bounds__(SF_NT) k_adjoint_fefe(
 
 }  // namespace
 
-// H = 0, then every element adds its kinetic FE-FE block and the FE-FE block
-// of H_V; V == NULL means V = 0.
+// Every element adds its kinetic FE-FE block and the FE-FE block of H_V into
+// H (which the caller has zeroed); V == NULL means V = 0.
 pufe_status launch_fefe(pufe_ctx *ctx, const double *V, double *H, cudaStream_t st) {
   auto &D = ctx->d;
   if (ctx->max_part_p > SF_PMAX) return fail(PUFE_EINVAL, "rule with more than 16 points per axis");
   if (!D.Tfe) return fail(PUFE_ESTATE, "no exact FE-FE blocks (a rule has < 4 points per axis)");
-  PUFE_CUDA_TRY(cudaMemsetAsync(H, 0, (size_t)ctx->nnz * sizeof(double), st));
   k_fefe_sumfac<<<(unsigned)ctx->nelem, SF_NT, 0, st>>>(D.qoff, D.w, V, D.xi, D.partoff, D.part_p,
                                                         D.part_q, D.doff, D.soff, D.smap, D.Tfe, H,
                                                         D.err);

@@ -94,6 +94,10 @@ struct DeviceArrays {
   // work list: elements sorted by (n_e, Q_e) class, largest first
   int32_t *order = nullptr;   // nelem
   unsigned *err = nullptr;    // device error flag
+  // side stream and events: the FE-FE kernel of the mixed assembly runs on
+  // `side`, forked from and joined back into the caller's stream
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 }  // namespace pufe
@@ -263,7 +267,7 @@ pufe_status launch_density_fp64(pufe_ctx *ctx, const double *C, int64_t ldc, con
 pufe_status launch_adjoint_fp64(pufe_ctx *ctx, const double *Hbar, double *Vbar, cudaStream_t s);
 pufe_status launch_tabulate_f32(pufe_ctx *ctx, cudaStream_t s);
 pufe_status launch_adjoint_tc(pufe_ctx *ctx, const double *Hbar, double *Vbar, cudaStream_t s);
-pufe_status launch_fefe(pufe_ctx *ctx, const double *V, double *H, cudaStream_t s);
+pufe_status launch_fefe(pufe_ctx *ctx, const double *V, double *H, cudaStream_t s);  // H must be zeroed
 pufe_status launch_strip_sf(pufe_ctx *ctx, const double *V, int what, double *H, double *S,
                             int first, int count, cudaStream_t s);
 pufe_status launch_adjoint_fefe(pufe_ctx *ctx, const double *Hbar, double *Vbar, int first,

@@ -719,6 +719,9 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
   PUFE_CUDA_TRY(cudaMalloc((void **)&D.psi32, std::max<int64_t>(1, ctx->psi32_len) * sizeof(float)));
   PUFE_CUDA_TRY(cudaMalloc((void **)&D.err, sizeof(unsigned)));
   PUFE_CUDA_TRY(cudaMemset(D.err, 0, sizeof(unsigned)));
+  PUFE_CUDA_TRY(cudaStreamCreateWithFlags(&D.side, cudaStreamNonBlocking));
+  PUFE_CUDA_TRY(cudaEventCreateWithFlags(&D.ev_fork, cudaEventDisableTiming));
+  PUFE_CUDA_TRY(cudaEventCreateWithFlags(&D.ev_join, cudaEventDisableTiming));
   }
 
   ctx->qoff = std::move(qoff);
@@ -742,6 +745,9 @@ static void free_device(pufe_ctx *ctx) {
                   D.orb, D.orbf, D.rowptr, D.col, D.soff, D.smap, D.order, D.err};
   for (void *p : ptrs)
     if (p) cudaFree(p);
+  if (D.ev_fork) cudaEventDestroy(D.ev_fork);
+  if (D.ev_join) cudaEventDestroy(D.ev_join);
+  if (D.side) cudaStreamDestroy(D.side);
   D = DeviceArrays();
 }
 

@@ -1011,8 +1011,15 @@ static pufe_status run_assemble_tc(pufe_ctx *ctx, const double *V, int what, dou
     return fail(PUFE_EINVAL, "too many enrichments per element for TF32X3");
   const size_t bytes = (size_t)ctx->nnz * sizeof(double);
   if (what & PUFE_WANT_H) {
-    pufe_status e0 = launch_fefe(ctx, V, H, st);
+    // H = 0; the FE-FE kernel then runs on the context's side stream,
+    // concurrently with the strip kernels below (both only add into H)
+    if (ctx->max_part_p > 16) return fail(PUFE_EINVAL, "rule with more than 16 points per axis");
+    PUFE_CUDA_TRY(cudaMemsetAsync(H, 0, bytes, st));
+    PUFE_CUDA_TRY(cudaEventRecord(D.ev_fork, st));
+    PUFE_CUDA_TRY(cudaStreamWaitEvent(D.side, D.ev_fork, 0));
+    pufe_status e0 = launch_fefe(ctx, V, H, D.side);
     if (e0 != PUFE_OK) return e0;
+    PUFE_CUDA_TRY(cudaEventRecord(D.ev_join, D.side));
   }
   if (what & PUFE_WANT_S) PUFE_CUDA_TRY(cudaMemcpyAsync(S, D.S0, bytes, cudaMemcpyDeviceToDevice, st));
   // elements are ordered with n_e > 128 first (256-row tensor-core tile),
@@ -1033,7 +1040,10 @@ static pufe_status run_assemble_tc(pufe_ctx *ctx, const double *V, int what, dou
         D.soff, D.smap, sx, sy, sz, nbig, amax, inb, what, H, S, D.err);
     PUFE_CUDA_TRY(cudaGetLastError());
   }
-  return launch_strip_sf(ctx, (what & PUFE_WANT_H) ? V : nullptr, what, H, S, nbig, nsmall, st);
+  pufe_status e1 = launch_strip_sf(ctx, (what & PUFE_WANT_H) ? V : nullptr, what, H, S, nbig, nsmall, st);
+  if (e1 != PUFE_OK) return e1;
+  if (what & PUFE_WANT_H) PUFE_CUDA_TRY(cudaStreamWaitEvent(st, D.ev_join, 0));
+  return PUFE_OK;
 }
 
 pufe_status launch_assemble_tc(pufe_ctx *ctx, const double *V, int what, double *H, double *S,
