@@ -130,10 +130,21 @@ def run_pufe(args):
     ev_a = torch.cuda.Event(enable_timing=True)
     ev_b = torch.cuda.Event(enable_timing=True)
 
+    side = torch.cuda.Stream() if args.density_stream == "side" else None
+
     def step():
         ctx.pufe_tabulate(prec)
-        ctx.pufe_assemble_HS(V, H, S, prec=prec)
-        ctx.pufe_density(Cm, f, rho, prec=prec)
+        if side is not None:
+            # the density needs only the table and C: run it on a second
+            # stream, concurrently with the assembly, and join before the end
+            cur = torch.cuda.current_stream()
+            side.wait_stream(cur)
+            ctx.pufe_density(Cm, f, rho, prec=prec, stream=side)
+            ctx.pufe_assemble_HS(V, H, S, prec=prec)
+            cur.wait_stream(side)
+        else:
+            ctx.pufe_assemble_HS(V, H, S, prec=prec)
+            ctx.pufe_density(Cm, f, rho, prec=prec)
         ctx.pufe_assemble_HV_adjoint(H, vbar, prec=prec)
 
     for _ in range(args.warmup):
@@ -259,6 +270,7 @@ def run_pufe(args):
                    "n_elem": ctx.n_elem, "nnz": ctx.nnz, "nocc": nocc, "prec": args.prec,
                    "l2": "flushed between steps (2x L2 buffer written)",
                    "launch": "cuda graph of the step" if graph is not None else "stream",
+                   "density_stream": args.density_stream,
                    "parallelism": f"replicas x{ws}", "build_s": round(build_s, 3)},
         "roofline": roof,
         "e2e": {"value": ws * ctx.n_q * args.steps / (e2e_ms * 1e-3), "unit": UNIT,
@@ -354,6 +366,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="pufe", choices=["pufe", "reference"])
     ap.add_argument("--prec", default="tf32x3", choices=["tf32x3", "fp64"])
+    ap.add_argument("--density-stream", default="side", choices=["same", "side"],
+                    help="run the density on the step's stream or concurrently on a second one")
     ap.add_argument("--launch", default="stream", choices=["graph", "stream"],
                     help="replay the step as a captured CUDA graph, or launch call by call")
     ap.add_argument("--workload", default="c2_rocksalt_12cube")
