@@ -285,3 +285,106 @@ def test_tf32x3_c3_like_large_elements():
     ctx.pufe_assemble_HV_adjoint(torch.tensor(Hbar.data, device=dev), out, prec=pufe.PUFE_TF32X3)
     ctx.pufe_sync_status()
     assert _rel(out.cpu().numpy(), go) < 1e-4
+
+
+def _restricted_rules(m, off, x, elems, V=None):
+    """Oracle rules for `elems` only (other elements get no points), with the
+    GPU's point layout checked against the oracle's; V (full length) is
+    returned cut to the same points."""
+    pts_l, wts_l, off_l, v_l = [], [], [0], []
+    for e in range(m.nelem):
+        if e in elems:
+            p, ww = oq.element_rule(m, e)
+            assert off[e + 1] - off[e] == len(ww)
+            assert np.abs(x[off[e]:off[e + 1]] - p).max() < 1e-13
+            if V is not None:
+                v_l.append(V[off[e]:off[e + 1]])
+        else:
+            p, ww = np.zeros((0, 3)), np.zeros(0)
+        pts_l.append(p)
+        wts_l.append(ww)
+        off_l.append(off_l[-1] + len(ww))
+    rules = (np.concatenate(pts_l), np.concatenate(wts_l), np.array(off_l))
+    return rules, (np.concatenate(v_l) if V is not None else None)
+
+
+def test_full_size_rocksalt_mixed_sampled():
+    """The bench's configuration (12^3 rocksalt, mixed precision, the same
+    calls bench.py times): rows of H and S, and the density and the adjoint
+    on the points of one element of every (n_e, Q_e) class, against the
+    oracle."""
+    wl = W.workload("c2_rocksalt_12cube")
+    ctx = pufe.pufe_build_mesh(wl)
+    x, w, off = ctx.quadrature()
+    n_e, _ = ctx.element_basis()
+    Q = np.diff(off)
+    dev = _dev()
+    P = pufe.PUFE_TF32X3
+    V = W.random_potential(ctx.n_q, seed=4)
+    Hg, Sg = _gpu_HS(ctx, V, P)
+    m = omesh.Mesh(wl)
+    # rows: FE nodes at and next to an atom, enrichment DOFs
+    rows = [0, 5 * 37, m.n_fe + 3, m.n_fe + 1000, ctx.n_dof - 1]
+    want = set(rows)
+    elems = {e for e in range(m.nelem) if want & set(m.elem_dofs(e).tolist())}
+    rules, Vr = _restricted_rules(m, off, x, elems, V)
+    Hr, Sr = oasm.assemble_rows(m, rules, Vr, rows)
+    # the whole-matrix measure: max |error| over max |X| of the matrix
+    hmax, smax = abs(Hg).max(), abs(Sg).max()
+    for k, r in enumerate(rows):
+        hg, sg = Hg[r].toarray().ravel(), Sg[r].toarray().ravel()
+        assert np.abs(hg - Hr[k]).max() < TOL_MAT_TF32 * hmax, r
+        assert np.abs(sg - Sr[k]).max() < TOL_MAT_TF32 * smax, r
+    classes = {}
+    for e in range(m.nelem):
+        classes.setdefault((int(n_e[e]), int(Q[e])), e)
+    pick = sorted(classes.values())
+    rules, _ = _restricted_rules(m, off, x, set(pick))
+    nocc = int(wl["nocc"])
+    Cm = W.random_coefficients(ctx.n_dof, nocc, seed=6)
+    f = W.random_occupations(nocc, seed=6)
+    rho = torch.empty(ctx.n_q, dtype=torch.float64, device=dev)
+    ctx.pufe_density(torch.tensor(Cm, device=dev), torch.tensor(f, device=dev), rho, prec=P)
+    Hbar = Hg.copy()
+    Hbar.data = W.random_symmetric_values(Hg.nnz, seed=8)
+    vbar = torch.empty_like(rho)
+    ctx.pufe_assemble_HV_adjoint(torch.tensor(Hbar.data, device=dev), vbar, prec=P)
+    ctx.pufe_sync_status()
+    ro = oasm.density(m, rules, Cm, f)
+    vo = oasm.adjoint_V(m, rules, Hbar)
+    rg, vg = rho.cpu().numpy(), vbar.cpu().numpy()
+    ro_off = rules[2]
+    for e in pick:
+        g = slice(off[e], off[e + 1])
+        o = slice(ro_off[e], ro_off[e + 1])
+        assert np.abs(rg[g] - ro[o]).max() < 1e-5 * np.abs(ro[o]).max(), e
+        assert np.abs(vg[g] - vo[o]).max() < 1e-4 * np.abs(vo[o]).max(), e
+
+
+@pytest.mark.parametrize("prec", [pufe.PUFE_FP64, pufe.PUFE_TF32X3])
+def test_largest_rule_and_occupation_count(prec):
+    """Limits of the interface: 16 Gauss points per axis (the largest rule the
+    mixed path takes; 4,096 points per element), 64 occupied states in the
+    density, S alone with V = NULL."""
+    wl = W.small_two_atom(nel=2, quad_p=16)
+    m = omesh.Mesh(wl)
+    rules = oq.all_rules(m)
+    ctx = pufe.pufe_build_mesh(wl)
+    dev = _dev()
+    V = W.random_potential(len(rules[1]), seed=12)
+    Ho, So = oasm.assemble_HS(m, rules, V)
+    Hg, Sg = _gpu_HS(ctx, V, prec)
+    tol = TOL64 if prec == pufe.PUFE_FP64 else TOL_MAT_TF32
+    assert _rel(Hg, Ho) < tol and _rel(Sg, So) < tol
+    S = torch.empty(ctx.nnz, dtype=torch.float64, device=dev)
+    ctx.pufe_assemble_HS(None, None, S, prec=prec, what=pufe.PUFE_WANT_S)
+    ctx.pufe_sync_status()
+    assert _rel(_csr(ctx, S.cpu().numpy()), So) < tol
+    nocc = 64
+    Cm = W.random_coefficients(m.n_dof, nocc, seed=13)
+    f = W.random_occupations(nocc, seed=13)
+    rho = torch.empty(ctx.n_q, dtype=torch.float64, device=dev)
+    ctx.pufe_density(torch.tensor(Cm, device=dev), torch.tensor(f, device=dev), rho, prec=prec)
+    ctx.pufe_sync_status()
+    ro = oasm.density(m, rules, Cm, f)
+    assert _rel(rho.cpu().numpy(), ro) < (TOL64 if prec == pufe.PUFE_FP64 else 1e-5)
