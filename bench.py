@@ -29,6 +29,11 @@ METRIC = "quadrature-point contractions/s for H/S assembly + density"
 UNIT = "QPC/s"
 L2_BYTES = 129 * 1024 * 1024
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# DRAM bytes (read + write) of the assembly call's kernels, k_fefe_sumfac +
+# k_strip_sf, per launch, from the ncu capture summarised in
+# profiles/step_mixed_c2_rocksalt_12cube.md; the memset of H and the copy of
+# the overlap constants into S (232 MB by construction) are not counted
+ASM_TRAFFIC = {("c2_rocksalt_12cube", "tf32x3"): 95_971_840 + 171_247_616}
 
 
 def _dist():
@@ -257,7 +262,8 @@ def run_pufe(args):
         kernels = "memset + k_fefe_sumfac + S0 copy + k_pack_v + k_assemble_tc + k_strip_sf"
         launches_per_step = 9
     roof = {"kernel": f"pufe_assemble_HS ({kernels})", "bound": bound, "achieved": achieved,
-            "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+            "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": ASM_TRAFFIC.get((args.workload, args.prec)),
             "peak_source": peak_source,
             "flops_per_launch": flops_asm, "flops_count": "sum_e 5 Q_e n_e (n_e + 1)",
             "avg_launch_ms": asm_avg}
