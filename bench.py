@@ -160,11 +160,11 @@ def run_pufe(args):
         # the whole step captured once into a CUDA graph and replayed: same
         # kernels, same arguments, no per-launch host overhead
         graph = torch.cuda.CUDAGraph()
-        side = torch.cuda.Stream()
-        side.wait_stream(stream)
-        with torch.cuda.stream(side):
+        warm = torch.cuda.Stream()
+        warm.wait_stream(stream)
+        with torch.cuda.stream(warm):
             step()
-        stream.wait_stream(side)
+        stream.wait_stream(warm)
         with torch.cuda.graph(graph):
             step()
         torch.cuda.synchronize()
