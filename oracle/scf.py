@@ -25,7 +25,9 @@ Poisson in the classical FE space (Sec. 3: the tricubic functions of the
 mesh): weak form  -K v = 4 pi b  with  K_ij = int grad phi_i . grad phi_j
 (exact: a 4-point Gauss rule per element) and  b_i = int phi_i rho  (shared
 rule), solved by a sparse direct solve with one DOF pinned, then shifted to
-zero cell average (int V = m^T v, m_i = int phi_i).
+zero cell average (int V = m^T v, m_i = int phi_i).  The net charge that the
+quadrature leaves (the rule integrates the ionic Gaussians only to its
+accuracy) is spread as a uniform background: b -= (sum_i b_i / Omega) m.
 
 Pins (tests/test_oracle_scf.py): the LDA's exchange constant in its
 (9 pi / 4)^(1/3) form, v_xc = d(n eps_xc)/dn by complex-step
@@ -152,6 +154,12 @@ def coulomb_potential(mesh, rules, rho, K=None):
     if K is None:
         K = fe_stiffness(mesh)
     b = fe_load(mesh, rules, rho)
+    # the shared rule integrates the ionic Gaussians only approximately, so
+    # the discrete total charge sum_i b_i may differ slightly from zero: it
+    # is spread as a uniform background (b -= (sum b / Omega) m), the
+    # compatibility condition of the periodic problem
+    m = fe_load(mesh, rules, np.ones(len(rules[1])))      # m_i = int phi_i
+    b = b - (b.sum() / m.sum()) * m
     rhs = -4.0 * math.pi * b
     # pin DOF 0 (K is singular: constants), then shift to zero average
     Kp = K.tolil()
@@ -161,7 +169,6 @@ def coulomb_potential(mesh, rules, rho, K=None):
     rhs = rhs.copy()
     rhs[0] = 0.0
     v = spla.spsolve(Kp.tocsc(), rhs)
-    m = fe_load(mesh, rules, np.ones(len(rules[1])))      # m_i = int phi_i
     v = v - (m @ v) / m.sum()
     return v, fe_interp(mesh, rules, v)
 
