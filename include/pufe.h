@@ -203,6 +203,61 @@ pufe_status pufe_density(pufe_ctx *ctx, const double *C, int64_t ldc,
 pufe_status pufe_assemble_HV_adjoint(pufe_ctx *ctx, const double *Hbar, int prec, double *Vbar,
                                      void *stream);
 
+/* ---- self-consistent field (Sec. 3) ------------------------------------ */
+
+/* Ionic charge density at every quadrature point (Sec. 3: the ionic
+ * potentials are generated by localized ionic charges): Gaussian charges
+ * Z_a exp(-r^2/sigma_a^2) / (pi^(3/2) sigma_a^3) of natoms atoms summed over
+ * periodic images.  tau: natoms x 3 Cartesian positions, Z, sigma: natoms
+ * values (host).  rho_I: device float64 (n_q), overwritten.  The context
+ * keeps sum_a Z_a^2 / (sigma_a sqrt(2 pi)), the Gaussians' self-energy, for
+ * pufe_scf_step.  The first SCF call of a context allocates its work arrays
+ * (a few n_q and N_fe float64 vectors).  Asynchronous apart from a blocking
+ * copy of the atom list. */
+pufe_status pufe_ion_density(pufe_ctx *ctx, int natoms, const double *tau, const double *Z,
+                             const double *sigma, double *rho_I, void *stream);
+
+/* Effective potential V_eff = V_C + v_xc at the quadrature points (Sec. 3,
+ * eqs. veff, poisson).  V_C is the total Coulomb potential of the charge
+ * rho = rho_I - n, from del^2 V_C = 4 pi rho in the tricubic FE space of the
+ * mesh (weak form on the shared element rule, zero cell average; the charge
+ * must be neutral); v_xc is the LDA (Dirac exchange with the Perdew-Zunger
+ * 1981 correlation, unpolarised).  n, rho_I: device float64 (n_q); V_eff:
+ * device float64 (n_q), overwritten; V_C and eps_xc (the LDA energy per
+ * electron) are optional outputs (NULL skips).  FP64.  Asynchronous. */
+pufe_status pufe_effective_potential(pufe_ctx *ctx, const double *n, const double *rho_I,
+                                     double *V_eff, double *V_C, double *eps_xc, void *stream);
+
+/* Energies of one SCF step (hartree) and its density residual. */
+typedef struct {
+  double mu;        /* Fermi level of the occupations */
+  double e_band;    /* sum_k f_k eps_k */
+  double e_dc;      /* -int n_out V_eff,in */
+  double e_es;      /* -1/2 int (rho_I - n_out) V_C[n_out] */
+  double e_self;    /* self-energy of the Gaussian ions (subtracted) */
+  double e_xc;      /* int n_out eps_xc(n_out) */
+  double e_ts;      /* -kT S of the occupations */
+  double e_total;   /* e_band + e_dc + e_es - e_self + e_xc + e_ts */
+  double residual;  /* int |n_out - n_in| */
+} pufe_scf_info;
+
+/* One fixed-point step of the SCF iteration (Sec. 3, fig. scf) after the
+ * caller's eigensolve of H[V_eff,in] c = eps S c (assembled with
+ * pufe_assemble_HS).  eps: nstates eigenvalues (host, 1 <= nstates <= 64);
+ * C: device float64 eigenvectors, N x nstates with leading dimension ldc,
+ * S-orthonormal.  Occupations f_k = 2 / (1 + exp((eps_k - mu)/kT)) with
+ * sum f = nelec (kT > 0); the output density n_out = sum f |psi|^2 (through
+ * pufe_density with `prec`); energies of n_out (pufe_scf_info); linear
+ * mixing n <- n + alpha (n_out - n) in place (n: device float64, n_q, the
+ * input density on entry); V_eff_out = V_eff[n] of the mixed density.
+ * rho_I, V_eff_in: device float64 (n_q).  f_out (host, nstates) and info may
+ * be NULL.  Needs a prior pufe_ion_density and pufe_tabulate(prec).
+ * Blocking: returns after the step has finished on `stream`. */
+pufe_status pufe_scf_step(pufe_ctx *ctx, int nstates, const double *eps, const double *C,
+                          int64_t ldc, double nelec, double kT, double alpha, int prec,
+                          const double *rho_I, const double *V_eff_in, double *n,
+                          double *V_eff_out, double *f_out, pufe_scf_info *info, void *stream);
+
 /* Wait for `stream`, then report (and clear) any device-side error flag. */
 pufe_status pufe_sync_status(pufe_ctx *ctx, void *stream);
 

@@ -112,6 +112,47 @@ pufe_status pufe_assemble_HV_adjoint(pufe_ctx *ctx, const double *Hbar, int prec
   return launch_adjoint_fp64(ctx, Hbar, Vbar, (cudaStream_t)stream);
 }
 
+pufe_status pufe_ion_density(pufe_ctx *ctx, int natoms, const double *tau, const double *Z,
+                             const double *sigma, double *rho_I, void *stream) {
+  if (pufe_status e0 = need_device(ctx)) return e0;
+  if (natoms < 0 || !rho_I || (natoms > 0 && (!tau || !Z || !sigma)))
+    return fail(PUFE_EINVAL, "need natoms >= 0, rho_I, and tau, Z, sigma for the atoms");
+  for (int a = 0; a < natoms; ++a)
+    if (!(sigma[a] > 0.0)) return fail(PUFE_EINVAL, "sigma must be > 0");
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return fail(PUFE_ECUDA, "cudaSetDevice failed");
+  return launch_ion_density(ctx, natoms, tau, Z, sigma, rho_I, (cudaStream_t)stream);
+}
+
+pufe_status pufe_effective_potential(pufe_ctx *ctx, const double *n, const double *rho_I,
+                                     double *V_eff, double *V_C, double *eps_xc, void *stream) {
+  if (pufe_status e0 = need_device(ctx)) return e0;
+  if (!n || !rho_I || !V_eff) return fail(PUFE_EINVAL, "n, rho_I and V_eff must not be NULL");
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return fail(PUFE_ECUDA, "cudaSetDevice failed");
+  return launch_effective_potential(ctx, n, rho_I, V_eff, V_C, eps_xc, (cudaStream_t)stream);
+}
+
+pufe_status pufe_scf_step(pufe_ctx *ctx, int nstates, const double *eps, const double *C,
+                          int64_t ldc, double nelec, double kT, double alpha, int prec,
+                          const double *rho_I, const double *V_eff_in, double *n,
+                          double *V_eff_out, double *f_out, pufe_scf_info *info, void *stream) {
+  if (pufe_status e0 = need_device(ctx)) return e0;
+  if (prec != PUFE_FP64 && prec != PUFE_TF32X3) return fail(PUFE_EINVAL, "unknown precision");
+  if (pufe_status e1 = need_table(ctx, prec)) return e1;
+  if (nstates < 1 || nstates > 64 || ldc < nstates)
+    return fail(PUFE_EINVAL, "need 1 <= nstates <= 64 and ldc >= nstates");
+  if (!eps || !C || !rho_I || !V_eff_in || !n || !V_eff_out)
+    return fail(PUFE_EINVAL, "eps, C, rho_I, V_eff_in, n and V_eff_out must not be NULL");
+  if (!(kT > 0.0) || !(nelec > 0.0) || nelec > 2.0 * nstates)
+    return fail(PUFE_EINVAL, "need kT > 0 and 0 < nelec <= 2 nstates");
+  if (!ctx->scf) return fail(PUFE_ESTATE, "call pufe_ion_density first");
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return fail(PUFE_ECUDA, "cudaSetDevice failed");
+  return launch_scf_step(ctx, nstates, eps, C, ldc, nelec, kT, alpha, prec, rho_I, V_eff_in, n,
+                         V_eff_out, f_out, info, (cudaStream_t)stream);
+}
+
 pufe_status pufe_sync_status(pufe_ctx *ctx, void *stream) {
   if (pufe_status e0 = need_device(ctx)) return e0;
   DeviceGuard g(ctx->device);

@@ -102,6 +102,10 @@ struct DeviceArrays {
 
 }  // namespace pufe
 
+namespace pufe {
+struct ScfState;
+}
+
 struct pufe_ctx {
   int device = 0;
   double a[3] = {0, 0, 0};
@@ -125,6 +129,7 @@ struct pufe_ctx {
   std::vector<int32_t> col, dofs, n_e, q_e, order;
   std::vector<double> x, w;
   pufe::DeviceArrays d;
+  pufe::ScfState *scf = nullptr;   // SCF work arrays, made on first use
 };
 
 namespace pufe {
@@ -270,6 +275,16 @@ pufe_status launch_adjoint_tc(pufe_ctx *ctx, const double *Hbar, double *Vbar, c
 pufe_status launch_fefe(pufe_ctx *ctx, const double *V, double *H, cudaStream_t s);  // H must be zeroed
 pufe_status launch_strip_sf(pufe_ctx *ctx, const double *V, int what, double *H, double *S,
                             int first, int count, cudaStream_t s);
+pufe_status scf_prepare(pufe_ctx *ctx);
+void scf_free(pufe_ctx *ctx);
+pufe_status launch_ion_density(pufe_ctx *ctx, int natoms, const double *tau, const double *Z,
+                               const double *sigma, double *rho, cudaStream_t s);
+pufe_status launch_effective_potential(pufe_ctx *ctx, const double *n, const double *rho_I,
+                                       double *V_eff, double *V_C, double *eps_xc, cudaStream_t s);
+pufe_status launch_scf_step(pufe_ctx *ctx, int nstates, const double *eps, const double *C,
+                            int64_t ldc, double nelec, double kT, double alpha, int prec,
+                            const double *rho_I, const double *V_eff_in, double *n, double *V_eff_out,
+                            double *f_out, pufe_scf_info *info, cudaStream_t s);
 pufe_status launch_adjoint_fefe(pufe_ctx *ctx, const double *Hbar, double *Vbar, int first,
                                 int count, cudaStream_t s);
 pufe_status launch_assemble_tc_static(pufe_ctx *ctx, const double *V, int what, double *H,

@@ -738,6 +738,7 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
 }
 
 static void free_device(pufe_ctx *ctx) {
+  scf_free(ctx);
   auto &D = ctx->d;
   void *ptrs[] = {D.qoff, D.x, D.w, D.xi, D.doff, D.dofs, D.ecol, D.aoff, D.alist,
                   D.toff, D.psi, D.psi32, D.qpoff, D.qdat, D.ptab, D.vpad, D.toff32, D.eorig,

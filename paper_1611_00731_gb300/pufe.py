@@ -28,7 +28,8 @@ STATUS = {0: "PUFE_OK", 1: "PUFE_EINVAL", 2: "PUFE_ENOMEM", 3: "PUFE_ECUDA",
 EXPORTS = ["pufe_build_mesh", "pufe_get_sizes", "pufe_get_quadrature", "pufe_get_pattern",
            "pufe_get_element_basis", "pufe_tabulate", "pufe_assemble_HS", "pufe_density",
            "pufe_assemble_HV_adjoint", "pufe_sync_status", "pufe_destroy", "pufe_last_error",
-           "pufe_assemble_HS_static"]
+           "pufe_assemble_HS_static", "pufe_ion_density", "pufe_effective_potential",
+           "pufe_scf_step"]
 
 
 class PufeError(RuntimeError):
@@ -52,6 +53,15 @@ class _Quad(C.Structure):
     _fields_ = [("mode", C.c_int), ("p_far", C.c_int), ("p_near", C.c_int),
                 ("p_min", C.c_int), ("p_max", C.c_int), ("tol", C.c_double),
                 ("max_depth", C.c_int)]
+
+
+class ScfInfo(C.Structure):
+    """pufe_scf_info: energies (hartree) and residual of one SCF step."""
+    _fields_ = [(k, C.c_double) for k in ("mu", "e_band", "e_dc", "e_es", "e_self", "e_xc",
+                                          "e_ts", "e_total", "residual")]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 _LIB = None
@@ -87,6 +97,10 @@ def load_library(build_if_missing: bool = True):
     lib.pufe_density.argtypes = [vp, vp, C.c_int64, vp, C.c_int, C.c_int, vp, vp]
     lib.pufe_assemble_HV_adjoint.argtypes = [vp, vp, C.c_int, vp, vp]
     lib.pufe_sync_status.argtypes = [vp, vp]
+    lib.pufe_ion_density.argtypes = [vp, C.c_int, dp, dp, dp, vp, vp]
+    lib.pufe_effective_potential.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+    lib.pufe_scf_step.argtypes = [vp, C.c_int, dp, vp, C.c_int64, C.c_double, C.c_double,
+                                  C.c_double, C.c_int, vp, vp, vp, vp, dp, C.POINTER(ScfInfo), vp]
     lib.pufe_destroy.argtypes = [vp]
     lib.pufe_destroy.restype = None
     lib.pufe_last_error.restype = C.c_char_p
@@ -191,6 +205,42 @@ class Context:
         import torch
         _check(_LIB.pufe_assemble_HV_adjoint(self._h, _ptr(Hbar, torch.float64), int(prec),
                                              _ptr(Vbar, torch.float64), _stream(stream)))
+
+    def pufe_ion_density(self, tau, Z, sigma, rho_I, stream=None):
+        """Gaussian ionic charges (host arrays) at the quadrature points."""
+        import numpy as np
+        import torch
+        tau = np.ascontiguousarray(tau, dtype=np.float64).reshape(-1, 3)
+        Z = np.ascontiguousarray(Z, dtype=np.float64)
+        sigma = np.ascontiguousarray(sigma, dtype=np.float64)
+        dp = C.POINTER(C.c_double)
+        _check(_LIB.pufe_ion_density(self._h, int(len(Z)), tau.ctypes.data_as(dp),
+                                     Z.ctypes.data_as(dp), sigma.ctypes.data_as(dp),
+                                     _ptr(rho_I, torch.float64), _stream(stream)))
+
+    def pufe_effective_potential(self, n, rho_I, V_eff, V_C=None, eps_xc=None, stream=None):
+        import torch
+        _check(_LIB.pufe_effective_potential(self._h, _ptr(n, torch.float64),
+                                             _ptr(rho_I, torch.float64), _ptr(V_eff, torch.float64),
+                                             _ptr(V_C, torch.float64), _ptr(eps_xc, torch.float64),
+                                             _stream(stream)))
+
+    def pufe_scf_step(self, eps, Cmat, nelec, kT, alpha, rho_I, V_eff_in, n, V_eff_out,
+                      prec=PUFE_FP64, stream=None):
+        """One SCF step; returns (occupations, info dict).  Blocking."""
+        import numpy as np
+        import torch
+        eps = np.ascontiguousarray(eps, dtype=np.float64)
+        f = np.zeros(len(eps))
+        info = ScfInfo()
+        dp = C.POINTER(C.c_double)
+        _check(_LIB.pufe_scf_step(self._h, int(len(eps)), eps.ctypes.data_as(dp),
+                                  _ptr(Cmat, torch.float64), int(Cmat.stride(0)), float(nelec),
+                                  float(kT), float(alpha), int(prec), _ptr(rho_I, torch.float64),
+                                  _ptr(V_eff_in, torch.float64), _ptr(n, torch.float64),
+                                  _ptr(V_eff_out, torch.float64), f.ctypes.data_as(dp),
+                                  C.byref(info), _stream(stream)))
+        return f, info.as_dict()
 
     def pufe_sync_status(self, stream=None):
         _check(_LIB.pufe_sync_status(self._h, _stream(stream)))
