@@ -94,6 +94,58 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def scf_timing(ctx, wl, prec, dev, reps=10):
+    """Times of the SCF calls on the same workload (Sec. 3): the effective
+    potential of a density (ionic charge + FE Poisson + LDA) and one SCF step
+    (occupations, output density, energies, mixing, new potential) with
+    synthetic states; CUDA events on the launching stream."""
+    import numpy as np
+    import torch
+
+    from paper_1611_00731_gb300 import workloads as W
+
+    tau = np.array([t for _, t in wl["atoms"]], dtype=np.float64).reshape(-1, 3)
+    Z = np.array([wl["species"][s]["Z"] for s, _ in wl["atoms"]], dtype=np.float64)
+    sig = np.array([wl["species"][s]["sigma"] for s, _ in wl["atoms"]], dtype=np.float64)
+    rho_I = torch.empty(ctx.n_q, dtype=torch.float64, device=dev)
+    ctx.pufe_ion_density(tau, Z, sig, rho_I)
+    nelec = float(wl["nelec"])
+    n = torch.full((ctx.n_q,), nelec / wl["a"] ** 3, dtype=torch.float64, device=dev)
+    V = torch.empty_like(n)
+    V2 = torch.empty_like(n)
+    nst = int(wl["nocc"])
+    eps = np.sort(np.random.default_rng(7).uniform(-1.0, 0.0, nst))
+    Cm = torch.tensor(W.random_coefficients(ctx.n_dof, nst, seed=7), device=dev)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.median(ts)
+
+    t_pot = timed(lambda: ctx.pufe_effective_potential(n, rho_I, V))
+    n0 = n.clone()
+
+    def one_step():
+        n.copy_(n0)
+        ctx.pufe_scf_step(eps, Cm, nelec, 0.01, 0.5, rho_I, V, n, V2, prec=prec)
+
+    t_step = timed(one_step)
+    ctx.pufe_sync_status()
+    return {"effective_potential_ms": t_pot, "scf_step_ms": t_step, "states": nst,
+            "note": "ionic charge + FE Poisson (fast diagonalization) + PZ81; the step adds "
+                    "occupations, output density, energies, mixing and the new potential"}
+
+
 def run_pufe(args):
     import numpy as np
     import torch
@@ -224,6 +276,8 @@ def run_pufe(args):
     ctx.pufe_sync_status()
     barrier()
 
+    scf = scf_timing(ctx, wl, prec, dev) if args.scf else None
+
     if ws > 1:
         import torch.distributed as dist
         t = torch.tensor([total_ms, e2e_ms], device=dev)
@@ -283,6 +337,7 @@ def run_pufe(args):
                 "h2d_bytes_per_step": int(V_h.numel() * 8 + C_h.numel() * 8 + f_h.numel() * 8),
                 "d2h_bytes_per_step": int(rho_h.numel() * 8)},
         "gpu_launches": launches_per_step * args.steps,
+        "scf": scf,
         "clocks": clocks,
     }
     if not args.no_cpu_baseline:
@@ -372,6 +427,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="pufe", choices=["pufe", "reference"])
     ap.add_argument("--prec", default="tf32x3", choices=["tf32x3", "fp64"])
+    ap.add_argument("--no-scf", dest="scf", action="store_false",
+                    help="skip the timing of the SCF calls")
     ap.add_argument("--density-stream", default="side", choices=["same", "side"],
                     help="run the density on the step's stream or concurrently on a second one")
     ap.add_argument("--launch", default="stream", choices=["graph", "stream"],

@@ -207,32 +207,72 @@ __global__ void k_ion_density(int64_t nq, const double *__restrict__ x, int nato
   rho[q] = s;
 }
 
+constexpr int SCF_PMAX = 16;   // largest points per axis of a (sub)cell
+
+// 1D Lagrange factors of one p^3 (sub)cell along its three axes:
+// L1[(d * 4 + a) * SCF_PMAX + t] for axis d, function a, axis point t
+__device__ __forceinline__ void cell_tables(const double *__restrict__ xi, int64_t qs, int p,
+                                            double *L1) {
+  for (int o = threadIdx.x; o < 3 * p; o += blockDim.x) {
+    const int d = o / p, t = o - d * p;
+    const int64_t stride = d == 0 ? 1 : (d == 1 ? p : (int64_t)p * p);
+    double L[4], dL[4];
+    lagrange3(xi[3 * (qs + t * stride) + d], L, dL);
+    for (int a = 0; a < 4; ++a) L1[(d * 4 + a) * SCF_PMAX + t] = L[a];
+  }
+}
+
 // b_i += scale sum_q w_q phi_i(x_q) f_q over the 64 FE functions of every
-// element; the 1D factors of 64 points at a time go through shared memory
-__global__ void __launch_bounds__(64) k_fe_load(
+// element, by sum factorization over each p^3 (sub)cell (contract z, then
+// y, then x: 4 p^3 + 16 p^2 + 64 p multiply-adds per cell)
+__global__ void __launch_bounds__(128) k_fe_load(
     const int64_t *__restrict__ qoff, const double *__restrict__ w, const double *__restrict__ xi,
-    const int64_t *__restrict__ doff, const int32_t *__restrict__ dofs,
-    const double *__restrict__ f, double scale, double *__restrict__ b) {
-  __shared__ double Lt[64][13];   // L_x[4], L_y[4], L_z[4], w f
-  const int e = blockIdx.x, t = threadIdx.x;
-  const int64_t q0 = qoff[e], q1 = qoff[e + 1];
-  const int ia = t & 3, ib = (t >> 2) & 3, ic = t >> 4;
-  double s = 0.0;
-  for (int64_t c0 = q0; c0 < q1; c0 += 64) {
-    const int cnt = (int)min((int64_t)64, q1 - c0);
+    const int32_t *__restrict__ partoff, const int32_t *__restrict__ part_p,
+    const int32_t *__restrict__ part_q, const int64_t *__restrict__ doff,
+    const int32_t *__restrict__ dofs, const double *__restrict__ f, double scale,
+    double *__restrict__ b, unsigned *err) {
+  __shared__ double L1[12 * SCF_PMAX];
+  __shared__ double T1[SCF_PMAX * SCF_PMAX * 4];   // [qx + p qy][c]
+  __shared__ double T2[SCF_PMAX * 16];             // [qx][b + 4 c]
+  __shared__ double bl[64];
+  const int e = blockIdx.x, tid = threadIdx.x;
+  if (tid < 64) bl[tid] = 0.0;
+  for (int k = partoff[e]; k < partoff[e + 1]; ++k) {
+    const int p = part_p[k], p2 = p * p;
+    if (p > SCF_PMAX) {
+      if (tid == 0) atomicOr(err, DEVERR_SHAPE);
+      return;
+    }
+    const int64_t qs = qoff[e] + part_q[k];
     __syncthreads();
-    if (t < cnt) {
-      const int64_t q = c0 + t;
-      double dL[4];
-      lagrange3(xi[3 * q], &Lt[t][0], dL);
-      lagrange3(xi[3 * q + 1], &Lt[t][4], dL);
-      lagrange3(xi[3 * q + 2], &Lt[t][8], dL);
-      Lt[t][12] = w[q] * f[q];
+    cell_tables(xi, qs, p, L1);
+    __syncthreads();
+    for (int it = tid; it < p2 * 4; it += blockDim.x) {   // z
+      const int qxy = it >> 2, c = it & 3;
+      double s = 0.0;
+      for (int qz = 0; qz < p; ++qz) {
+        const int64_t q = qs + qxy + (int64_t)p2 * qz;
+        s += w[q] * f[q] * L1[(8 + c) * SCF_PMAX + qz];
+      }
+      T1[it] = s;
     }
     __syncthreads();
-    for (int k = 0; k < cnt; ++k) s += Lt[k][12] * Lt[k][ia] * Lt[k][4 + ib] * Lt[k][8 + ic];
+    for (int it = tid; it < p * 16; it += blockDim.x) {   // y
+      const int qx = it >> 4, bc = it & 15, bb = bc & 3, c = bc >> 2;
+      double s = 0.0;
+      for (int qy = 0; qy < p; ++qy) s += T1[(qx + p * qy) * 4 + c] * L1[(4 + bb) * SCF_PMAX + qy];
+      T2[it] = s;
+    }
+    __syncthreads();
+    if (tid < 64) {                                       // x
+      const int a = tid & 3, bc = tid >> 2;
+      double s = 0.0;
+      for (int qx = 0; qx < p; ++qx) s += T2[qx * 16 + bc] * L1[a * SCF_PMAX + qx];
+      bl[tid] += s;
+    }
   }
-  atomicAdd(b + dofs[doff[e] + t], scale * s);
+  __syncthreads();
+  if (tid < 64) atomicAdd(b + dofs[doff[e] + tid], scale * bl[tid]);
 }
 
 // out = A applied along axis `axis` of the (n0, n1, n2) node array (x fastest):
@@ -267,26 +307,50 @@ __global__ void k_modal_scale(int n0, int n1, int n2, const double *__restrict__
   c[id] = (id == 0) ? 0.0 : c[id] / (l0[i0] + l1[i1] + l2[i2]);
 }
 
-// V(x_q) = sum_i v_i phi_i(x_q) over the 64 FE functions
-__global__ void k_fe_interp(const int64_t *__restrict__ qoff, const double *__restrict__ xi,
-                            const int64_t *__restrict__ doff, const int32_t *__restrict__ dofs,
-                            const double *__restrict__ v, double *__restrict__ out) {
+// V(x_q) = sum_i v_i phi_i(x_q) over the 64 FE functions, by sum
+// factorization over each p^3 (sub)cell (x, then y, then z)
+__global__ void __launch_bounds__(128) k_fe_interp(
+    const int64_t *__restrict__ qoff, const double *__restrict__ xi,
+    const int32_t *__restrict__ partoff, const int32_t *__restrict__ part_p,
+    const int32_t *__restrict__ part_q, const int64_t *__restrict__ doff,
+    const int32_t *__restrict__ dofs, const double *__restrict__ v, double *__restrict__ out,
+    unsigned *err) {
+  __shared__ double L1[12 * SCF_PMAX];
   __shared__ double ve[64];
-  const int e = blockIdx.x;
-  if (threadIdx.x < 64) ve[threadIdx.x] = v[dofs[doff[e] + threadIdx.x]];
-  __syncthreads();
-  for (int64_t q = qoff[e] + threadIdx.x; q < qoff[e + 1]; q += blockDim.x) {
-    double L[4], M[4], N[4], dL[4];
-    lagrange3(xi[3 * q], L, dL);
-    lagrange3(xi[3 * q + 1], M, dL);
-    lagrange3(xi[3 * q + 2], N, dL);
-    double s = 0.0;
-    for (int c = 0; c < 4; ++c)
-      for (int b = 0; b < 4; ++b) {
-        const double mn = M[b] * N[c];
-        for (int a = 0; a < 4; ++a) s += ve[a + 4 * b + 16 * c] * L[a] * mn;
-      }
-    out[q] = s;
+  __shared__ double T1[16 * SCF_PMAX];              // [b + 4 c][qx]
+  __shared__ double T2[4 * SCF_PMAX * SCF_PMAX];    // [c][qx + p qy]
+  const int e = blockIdx.x, tid = threadIdx.x;
+  if (tid < 64) ve[tid] = v[dofs[doff[e] + tid]];
+  for (int k = partoff[e]; k < partoff[e + 1]; ++k) {
+    const int p = part_p[k], p2 = p * p;
+    if (p > SCF_PMAX) {
+      if (tid == 0) atomicOr(err, DEVERR_SHAPE);
+      return;
+    }
+    const int64_t qs = qoff[e] + part_q[k];
+    __syncthreads();
+    cell_tables(xi, qs, p, L1);
+    __syncthreads();
+    for (int it = tid; it < 16 * p; it += blockDim.x) {   // x
+      const int bc = it / p, qx = it - bc * p;
+      double s = 0.0;
+      for (int a = 0; a < 4; ++a) s += ve[a + 4 * bc] * L1[a * SCF_PMAX + qx];
+      T1[it] = s;
+    }
+    __syncthreads();
+    for (int it = tid; it < 4 * p2; it += blockDim.x) {   // y
+      const int c = it / p2, qxy = it - c * p2, qy = qxy / p, qx = qxy - qy * p;
+      double s = 0.0;
+      for (int bb = 0; bb < 4; ++bb) s += T1[(bb + 4 * c) * p + qx] * L1[(4 + bb) * SCF_PMAX + qy];
+      T2[it] = s;
+    }
+    __syncthreads();
+    for (int it = tid; it < p2 * p; it += blockDim.x) {   // z
+      const int qz = it / p2, qxy = it - qz * p2;
+      double s = 0.0;
+      for (int c = 0; c < 4; ++c) s += T2[c * p2 + qxy] * L1[(8 + c) * SCF_PMAX + qz];
+      out[qs + it] = s;
+    }
   }
 }
 
@@ -373,6 +437,7 @@ inline unsigned blocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 pufe_status scf_prepare(pufe_ctx *ctx) {
   if (ctx->scf) return PUFE_OK;
+  if (ctx->max_part_p > SCF_PMAX) return fail(PUFE_EINVAL, "rule with more than 16 points per axis");
   auto *S = new ScfState();
   ctx->scf = S;
   auto &D = ctx->d;
@@ -449,8 +514,9 @@ static pufe_status coulomb(pufe_ctx *ctx, const double *n, const double *rho_I, 
   k_diff<<<blocks(ctx->nq, 256), 256, 0, st>>>(ctx->nq, n, rho_I, VC);
   PUFE_CUDA_TRY(cudaMemsetAsync(S->b, 0, nfe * sizeof(double), st));
   // -K v = 4 pi int phi (rho_I - n)  <=>  K v = 4 pi int phi (n - rho_I)
-  k_fe_load<<<(unsigned)ctx->nelem, 64, 0, st>>>(D.qoff, D.w, D.xi, D.doff, D.dofs, VC, 4.0 * PI,
-                                                 S->b);
+  k_fe_load<<<(unsigned)ctx->nelem, 128, 0, st>>>(D.qoff, D.w, D.xi, D.partoff, D.part_p,
+                                                  D.part_q, D.doff, D.dofs, VC, 4.0 * PI, S->b,
+                                                  D.err);
   const unsigned nb = blocks(nfe, 256);
   k_axis<<<nb, 256, 0, st>>>(n0, n1, n2, 0, S->X[0], true, S->b, S->t0);
   k_axis<<<nb, 256, 0, st>>>(n0, n1, n2, 1, S->X[1], true, S->t0, S->t1);
@@ -459,7 +525,8 @@ static pufe_status coulomb(pufe_ctx *ctx, const double *n, const double *rho_I, 
   k_axis<<<nb, 256, 0, st>>>(n0, n1, n2, 2, S->X[2], false, S->t0, S->t1);
   k_axis<<<nb, 256, 0, st>>>(n0, n1, n2, 1, S->X[1], false, S->t1, S->t0);
   k_axis<<<nb, 256, 0, st>>>(n0, n1, n2, 0, S->X[0], false, S->t0, S->t1);
-  k_fe_interp<<<(unsigned)ctx->nelem, 128, 0, st>>>(D.qoff, D.xi, D.doff, D.dofs, S->t1, VC);
+  k_fe_interp<<<(unsigned)ctx->nelem, 128, 0, st>>>(D.qoff, D.xi, D.partoff, D.part_p,
+                                                    D.part_q, D.doff, D.dofs, S->t1, VC, D.err);
   PUFE_CUDA_TRY(cudaGetLastError());
   return PUFE_OK;
 }
