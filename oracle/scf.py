@@ -9,8 +9,8 @@ periodic solution exists; it is fixed by a zero cell average.  V_xc is the
 LDA (the paper names the LDA, not its parametrisation): Perdew-Zunger 1981
 fit of the Ceperley-Alder correlation, unpolarised, plus Dirac exchange.
 The fixed-point (SCF) iteration of Sec. 3 (fig. scf) is taken one step at a
-time: occupations by Fermi-Dirac smearing, the output density, linear
-mixing, the new effective potential, and the total energy
+time: occupations by Fermi-Dirac smearing, the output density, linear or
+Pulay mixing, the new effective potential, and the total energy
 
     E = sum_k f_k eps_k - int n_out V_eff,in + E_es[n_out] - E_self
         + E_xc[n_out] - kT S,
@@ -197,11 +197,42 @@ def entropy(f):
     return -2.0 * t.sum()
 
 
-def scf_step(mesh, rules, wl, eps, C, nelec, kT, alpha, n_in, V_eff_in, rho_I, K=None):
+class PulayMixer:
+    """Pulay (DIIS / Anderson) density mixing: with the last `depth` input
+    densities n_i and residuals R_i = n_out,i - n_i, the coefficients c
+    minimise || sum_i c_i R_i ||_w (w: the quadrature weights) subject to
+    sum_i c_i = 1, and n_new = sum_i c_i (n_i + alpha R_i).  depth = 1 is
+    linear mixing."""
+
+    def __init__(self, depth):
+        self.depth = int(depth)
+        self.n, self.R = [], []
+
+    def mix(self, n_in, n_out, w, alpha):
+        self.n.append(np.array(n_in, copy=True))
+        self.R.append(np.asarray(n_out) - n_in)
+        if len(self.n) > self.depth:
+            self.n.pop(0)
+            self.R.pop(0)
+        m = len(self.R)
+        A = np.array([[w @ (self.R[i] * self.R[j]) for j in range(m)] for i in range(m)])
+        A += 1e-12 * np.trace(A) / m * np.eye(m)          # keeps near-parallel residuals solvable
+        M = np.zeros((m + 1, m + 1))
+        M[:m, :m] = A
+        M[:m, m] = M[m, :m] = 1.0
+        rhs = np.zeros(m + 1)
+        rhs[m] = 1.0
+        c = np.linalg.solve(M, rhs)[:m]
+        return sum(c[i] * (self.n[i] + alpha * self.R[i]) for i in range(m))
+
+
+def scf_step(mesh, rules, wl, eps, C, nelec, kT, alpha, n_in, V_eff_in, rho_I, K=None,
+             mixer=None):
     """One fixed-point step (Sec. 3, fig. scf) after the eigensolve.
 
     eps (k,), C (N, k): the lowest states of H[V_eff_in].  Returns a dict with
-    the occupations, n_out, n_new = n_in + alpha (n_out - n_in), V_eff[n_new],
+    the occupations, n_out, n_new = n_in + alpha (n_out - n_in) (or the Pulay
+    mix of `mixer`), V_eff[n_new],
     the energy terms of n_out and the residual int |n_out - n_in|."""
     w = rules[1]
     f, mu = fermi_occupations(eps, nelec, kT)
@@ -214,7 +245,10 @@ def scf_step(mesh, rules, wl, eps, C, nelec, kT, alpha, n_in, V_eff_in, rho_I, K
     e_xc = float(w @ (n_out * exc_out))
     e_ts = -kT * entropy(f)
     e_self = self_energy(wl)
-    n_new = n_in + alpha * (n_out - n_in)
+    if mixer is None:
+        n_new = n_in + alpha * (n_out - n_in)
+    else:
+        n_new = mixer.mix(n_in, n_out, w, alpha)
     V_new, _, _ = effective_potential(mesh, rules, n_new, rho_I, K)
     return dict(f=f, mu=mu, n_out=n_out, n_new=n_new, V_eff=V_new, e_band=e_band, e_dc=e_dc,
                 e_es=e_es, e_self=e_self, e_xc=e_xc, e_ts=e_ts,

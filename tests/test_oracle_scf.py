@@ -112,3 +112,22 @@ def test_energy_invariant_under_a_constant_potential_shift(c1_step_inputs):
     assert a["e_es"] >= 0.0                                   # neutral total charge
     assert abs(rules[1] @ a["n_out"] - wl["nelec"]) < 1e-8    # sum f = N_e, C S-orthonormal
     assert np.allclose(a["n_new"], n0 + 0.5 * (a["n_out"] - n0))
+
+
+def test_pulay_solves_a_linear_fixed_point_in_dimension_plus_one_steps():
+    # n -> G(n) = A n + b on R^3: Anderson/Pulay mixing with enough history
+    # reaches the fixed point after at most dim + 1 residual evaluations
+    rng = np.random.default_rng(1)
+    A = 0.5 * rng.standard_normal((3, 3))
+    b = rng.standard_normal(3)
+    fixed = np.linalg.solve(np.eye(3) - A, b)
+    w = np.ones(3)
+    mix = oscf.PulayMixer(depth=5)
+    n = np.zeros(3)
+    for _ in range(4):
+        n = mix.mix(n, A @ n + b, w, 0.3)
+    assert np.abs(n - fixed).max() < 1e-8 * np.abs(fixed).max()
+    # depth 1 is linear mixing
+    one = oscf.PulayMixer(depth=1)
+    x = rng.standard_normal(3)
+    assert np.allclose(one.mix(x, A @ x + b, w, 0.3), x + 0.3 * (A @ x + b - x))
