@@ -247,16 +247,24 @@ typedef struct {
  * C: device float64 eigenvectors, N x nstates with leading dimension ldc,
  * S-orthonormal.  Occupations f_k = 2 / (1 + exp((eps_k - mu)/kT)) with
  * sum f = nelec (kT > 0); the output density n_out = sum f |psi|^2 (through
- * pufe_density with `prec`); energies of n_out (pufe_scf_info); linear
- * mixing n <- n + alpha (n_out - n) in place (n: device float64, n_q, the
- * input density on entry); V_eff_out = V_eff[n] of the mixed density.
+ * pufe_density with `prec`); energies of n_out (pufe_scf_info); density
+ * mixing in place (n: device float64, n_q, the input density on entry):
+ * pulay <= 1: linear, n <- n + alpha (n_out - n); 2 <= pulay <= 8: Pulay
+ * (DIIS) over the last `pulay` steps of this context (input densities and
+ * residuals R = n_out - n kept in the context, cleared by pufe_scf_reset):
+ * n <- sum_i c_i (n_i + alpha R_i) with sum c_i = 1 minimising
+ * || sum_i c_i R_i || in the quadrature-weighted norm.  V_eff_out =
+ * V_eff[n] of the mixed density.
  * rho_I, V_eff_in: device float64 (n_q).  f_out (host, nstates) and info may
  * be NULL.  Needs a prior pufe_ion_density and pufe_tabulate(prec).
  * Blocking: returns after the step has finished on `stream`. */
 pufe_status pufe_scf_step(pufe_ctx *ctx, int nstates, const double *eps, const double *C,
-                          int64_t ldc, double nelec, double kT, double alpha, int prec,
+                          int64_t ldc, double nelec, double kT, double alpha, int pulay, int prec,
                           const double *rho_I, const double *V_eff_in, double *n,
                           double *V_eff_out, double *f_out, pufe_scf_info *info, void *stream);
+
+/* Forget the Pulay history of the context (start of a new SCF run). */
+pufe_status pufe_scf_reset(pufe_ctx *ctx);
 
 /* Wait for `stream`, then report (and clear) any device-side error flag. */
 pufe_status pufe_sync_status(pufe_ctx *ctx, void *stream);

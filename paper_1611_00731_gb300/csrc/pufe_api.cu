@@ -134,7 +134,7 @@ pufe_status pufe_effective_potential(pufe_ctx *ctx, const double *n, const doubl
 }
 
 pufe_status pufe_scf_step(pufe_ctx *ctx, int nstates, const double *eps, const double *C,
-                          int64_t ldc, double nelec, double kT, double alpha, int prec,
+                          int64_t ldc, double nelec, double kT, double alpha, int pulay, int prec,
                           const double *rho_I, const double *V_eff_in, double *n,
                           double *V_eff_out, double *f_out, pufe_scf_info *info, void *stream) {
   if (pufe_status e0 = need_device(ctx)) return e0;
@@ -147,10 +147,17 @@ pufe_status pufe_scf_step(pufe_ctx *ctx, int nstates, const double *eps, const d
   if (!(kT > 0.0) || !(nelec > 0.0) || nelec > 2.0 * nstates)
     return fail(PUFE_EINVAL, "need kT > 0 and 0 < nelec <= 2 nstates");
   if (!ctx->scf) return fail(PUFE_ESTATE, "call pufe_ion_density first");
+  if (pulay < 0 || pulay > 8) return fail(PUFE_EINVAL, "need 0 <= pulay <= 8");
   DeviceGuard g(ctx->device);
   if (!g.ok) return fail(PUFE_ECUDA, "cudaSetDevice failed");
-  return launch_scf_step(ctx, nstates, eps, C, ldc, nelec, kT, alpha, prec, rho_I, V_eff_in, n,
+  return launch_scf_step(ctx, nstates, eps, C, ldc, nelec, kT, alpha, pulay, prec, rho_I, V_eff_in, n,
                          V_eff_out, f_out, info, (cudaStream_t)stream);
+}
+
+pufe_status pufe_scf_reset(pufe_ctx *ctx) {
+  if (pufe_status e0 = need_device(ctx)) return e0;
+  scf_reset(ctx);
+  return PUFE_OK;
 }
 
 pufe_status pufe_sync_status(pufe_ctx *ctx, void *stream) {

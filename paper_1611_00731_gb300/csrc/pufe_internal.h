@@ -281,8 +281,9 @@ pufe_status launch_ion_density(pufe_ctx *ctx, int natoms, const double *tau, con
                                const double *sigma, double *rho, cudaStream_t s);
 pufe_status launch_effective_potential(pufe_ctx *ctx, const double *n, const double *rho_I,
                                        double *V_eff, double *V_C, double *eps_xc, cudaStream_t s);
+void scf_reset(pufe_ctx *ctx);
 pufe_status launch_scf_step(pufe_ctx *ctx, int nstates, const double *eps, const double *C,
-                            int64_t ldc, double nelec, double kT, double alpha, int prec,
+                            int64_t ldc, double nelec, double kT, double alpha, int pulay, int prec,
                             const double *rho_I, const double *V_eff_in, double *n, double *V_eff_out,
                             double *f_out, pufe_scf_info *info, cudaStream_t s);
 pufe_status launch_adjoint_fefe(pufe_ctx *ctx, const double *Hbar, double *Vbar, int first,

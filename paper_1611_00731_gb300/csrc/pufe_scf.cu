@@ -38,6 +38,11 @@ struct ScfState {
   double *atoms = nullptr;  // 5 per atom: tau (3), Z, sigma
   int atoms_cap = 0;
   double e_self = 0.0;      // self-energy of the last ionic charge set
+  // Pulay history: ring of PULAY_MAX (input density, residual) pairs
+  double *hist_n = nullptr, *hist_R = nullptr, *dots = nullptr;
+  std::vector<int> slots;   // active slots, oldest first
+  double gram[8][8] = {{0}};
+  int next_slot = 0;
 };
 
 namespace {
@@ -431,6 +436,89 @@ __global__ void k_energy_mix(int64_t nq, const double *__restrict__ w, const dou
   }
 }
 
+constexpr int PULAY_MAX = 8;
+struct SlotList {
+  int m;
+  int s[PULAY_MAX];
+  double c[PULAY_MAX];
+};
+
+// store (n_in, n_out - n_in) in slot `slot` of the history and accumulate
+// dots[j] += sum_q w_q R_new R_j for the active slots
+__global__ void k_pulay_store(int64_t nq, const double *__restrict__ w,
+                              const double *__restrict__ n_in, const double *__restrict__ n_out,
+                              int slot, SlotList L, double *__restrict__ hn, double *__restrict__ hR,
+                              double *__restrict__ dots) {
+  __shared__ double red[PULAY_MAX][8];
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double r = 0.0, wq = 0.0;
+  if (q < nq) {
+    r = n_out[q] - n_in[q];
+    wq = w[q];
+    hn[(int64_t)slot * nq + q] = n_in[q];
+    hR[(int64_t)slot * nq + q] = r;
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int j = 0; j < L.m; ++j) {
+    double t = 0.0;
+    if (q < nq) t = wq * r * (L.s[j] == slot ? r : hR[(int64_t)L.s[j] * nq + q]);
+    for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+    if (lane == 0) red[j][warp] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x < L.m) {
+    double t = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[threadIdx.x][i];
+    atomicAdd(dots + threadIdx.x, t);
+  }
+}
+
+// n = sum_i c_i (n_i + alpha R_i) over the active slots
+__global__ void k_pulay_mix(int64_t nq, SlotList L, double alpha, const double *__restrict__ hn,
+                            const double *__restrict__ hR, double *__restrict__ n) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nq) return;
+  double s = 0.0;
+  for (int i = 0; i < L.m; ++i)
+    s += L.c[i] * (hn[(int64_t)L.s[i] * nq + q] + alpha * hR[(int64_t)L.s[i] * nq + q]);
+  n[q] = s;
+}
+
+// solve the (m + 1) bordered system [A 1; 1^T 0] [c; l] = [0; 1] by Gaussian
+// elimination with partial pivoting (m <= 8)
+static bool pulay_coefficients(int m, const double A[8][8], double *c) {
+  double M[9][10] = {{0}};
+  double tr = 0.0;
+  for (int i = 0; i < m; ++i) tr += A[i][i];
+  const double ridge = 1e-12 * tr / m;
+  for (int i = 0; i < m; ++i) {
+    for (int j = 0; j < m; ++j) M[i][j] = A[i][j] + (i == j ? ridge : 0.0);
+    M[i][m] = 1.0;
+    M[m][i] = 1.0;
+  }
+  M[m][m + 1] = 1.0;
+  const int n = m + 1;
+  for (int k = 0; k < n; ++k) {
+    int piv = k;
+    for (int i = k + 1; i < n; ++i)
+      if (std::fabs(M[i][k]) > std::fabs(M[piv][k])) piv = i;
+    if (std::fabs(M[piv][k]) < 1e-300) return false;
+    for (int j = 0; j <= n; ++j) std::swap(M[k][j], M[piv][j]);
+    for (int i = k + 1; i < n; ++i) {
+      const double f = M[i][k] / M[k][k];
+      for (int j = k; j <= n; ++j) M[i][j] -= f * M[k][j];
+    }
+  }
+  double x[9];
+  for (int i = n - 1; i >= 0; --i) {
+    double t = M[i][n];
+    for (int j = i + 1; j < n; ++j) t -= M[i][j] * x[j];
+    x[i] = t / M[i][i];
+  }
+  for (int i = 0; i < m; ++i) c[i] = x[i];
+  return true;
+}
+
 inline unsigned blocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
@@ -469,7 +557,8 @@ void scf_free(pufe_ctx *ctx) {
   ScfState *S = ctx->scf;
   if (!S) return;
   void *ptrs[] = {S->X[0], S->X[1], S->X[2], S->lam[0], S->lam[1], S->lam[2], S->b, S->t0,
-                  S->t1, S->n_out, S->vc, S->exc, S->vxc, S->sums, S->f, S->atoms};
+                  S->t1, S->n_out, S->vc, S->exc, S->vxc, S->sums, S->f, S->atoms,
+                  S->hist_n, S->hist_R, S->dots};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   delete S;
@@ -544,8 +633,14 @@ pufe_status launch_effective_potential(pufe_ctx *ctx, const double *n, const dou
   return PUFE_OK;
 }
 
+void scf_reset(pufe_ctx *ctx) {
+  if (!ctx->scf) return;
+  ctx->scf->slots.clear();
+  ctx->scf->next_slot = 0;
+}
+
 pufe_status launch_scf_step(pufe_ctx *ctx, int nstates, const double *eps, const double *C,
-                            int64_t ldc, double nelec, double kT, double alpha, int prec,
+                            int64_t ldc, double nelec, double kT, double alpha, int pulay, int prec,
                             const double *rho_I, const double *V_eff_in, double *n, double *V_eff_out,
                             double *f_out, pufe_scf_info *info, cudaStream_t st) {
   if (pufe_status e0 = scf_prepare(ctx)) return e0;
@@ -594,9 +689,41 @@ pufe_status launch_scf_step(pufe_ctx *ctx, int nstates, const double *eps, const
   if (pufe_status e2 = coulomb(ctx, S->n_out, rho_I, S->vc, st)) return e2;
   k_xc<<<blocks(ctx->nq, 256), 256, 0, st>>>(ctx->nq, S->n_out, S->exc, nullptr);
   PUFE_CUDA_TRY(cudaMemsetAsync(S->sums, 0, 8 * sizeof(double), st));
+  const bool use_pulay = pulay > 1;
   k_energy_mix<<<blocks(ctx->nq, 256), 256, 0, st>>>(ctx->nq, ctx->d.w, S->n_out, V_eff_in, rho_I,
-                                                     S->vc, S->exc, alpha, n, S->sums);
+                                                     S->vc, S->exc, use_pulay ? 0.0 : alpha, n,
+                                                     S->sums);
   PUFE_CUDA_TRY(cudaGetLastError());
+  if (use_pulay) {
+    const int depth = std::min(pulay, PULAY_MAX);
+    if (!S->hist_n) {
+      PUFE_CUDA_TRY(cudaMalloc((void **)&S->hist_n, (size_t)PULAY_MAX * ctx->nq * sizeof(double)));
+      PUFE_CUDA_TRY(cudaMalloc((void **)&S->hist_R, (size_t)PULAY_MAX * ctx->nq * sizeof(double)));
+      PUFE_CUDA_TRY(cudaMalloc((void **)&S->dots, PULAY_MAX * sizeof(double)));
+    }
+    // drop the oldest entries beyond depth - 1, then add this one
+    while ((int)S->slots.size() > depth - 1) S->slots.erase(S->slots.begin());
+    int slot = 0;
+    while (std::find(S->slots.begin(), S->slots.end(), slot) != S->slots.end()) ++slot;
+    S->slots.push_back(slot);
+    SlotList L;
+    L.m = (int)S->slots.size();
+    for (int i = 0; i < L.m; ++i) L.s[i] = S->slots[i];
+    PUFE_CUDA_TRY(cudaMemsetAsync(S->dots, 0, PULAY_MAX * sizeof(double), st));
+    k_pulay_store<<<blocks(ctx->nq, 256), 256, 0, st>>>(ctx->nq, ctx->d.w, n, S->n_out, slot, L,
+                                                        S->hist_n, S->hist_R, S->dots);
+    PUFE_CUDA_TRY(cudaGetLastError());
+    double dots[PULAY_MAX];
+    PUFE_CUDA_TRY(cudaMemcpyAsync(dots, S->dots, L.m * sizeof(double), cudaMemcpyDeviceToHost, st));
+    PUFE_CUDA_TRY(cudaStreamSynchronize(st));
+    for (int j = 0; j < L.m; ++j) S->gram[slot][L.s[j]] = S->gram[L.s[j]][slot] = dots[j];
+    double A[8][8];
+    for (int i = 0; i < L.m; ++i)
+      for (int j = 0; j < L.m; ++j) A[i][j] = S->gram[L.s[i]][L.s[j]];
+    if (!pulay_coefficients(L.m, A, L.c)) return fail(PUFE_EINVAL, "Pulay system is singular");
+    k_pulay_mix<<<blocks(ctx->nq, 256), 256, 0, st>>>(ctx->nq, L, alpha, S->hist_n, S->hist_R, n);
+    PUFE_CUDA_TRY(cudaGetLastError());
+  }
   // the new effective potential of the mixed density
   if (pufe_status e3 = launch_effective_potential(ctx, n, rho_I, V_eff_out, nullptr, nullptr, st))
     return e3;

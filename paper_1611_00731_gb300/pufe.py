@@ -29,7 +29,7 @@ EXPORTS = ["pufe_build_mesh", "pufe_get_sizes", "pufe_get_quadrature", "pufe_get
            "pufe_get_element_basis", "pufe_tabulate", "pufe_assemble_HS", "pufe_density",
            "pufe_assemble_HV_adjoint", "pufe_sync_status", "pufe_destroy", "pufe_last_error",
            "pufe_assemble_HS_static", "pufe_ion_density", "pufe_effective_potential",
-           "pufe_scf_step"]
+           "pufe_scf_step", "pufe_scf_reset"]
 
 
 class PufeError(RuntimeError):
@@ -100,7 +100,9 @@ def load_library(build_if_missing: bool = True):
     lib.pufe_ion_density.argtypes = [vp, C.c_int, dp, dp, dp, vp, vp]
     lib.pufe_effective_potential.argtypes = [vp, vp, vp, vp, vp, vp, vp]
     lib.pufe_scf_step.argtypes = [vp, C.c_int, dp, vp, C.c_int64, C.c_double, C.c_double,
-                                  C.c_double, C.c_int, vp, vp, vp, vp, dp, C.POINTER(ScfInfo), vp]
+                                  C.c_double, C.c_int, C.c_int, vp, vp, vp, vp, dp,
+                                  C.POINTER(ScfInfo), vp]
+    lib.pufe_scf_reset.argtypes = [vp]
     lib.pufe_destroy.argtypes = [vp]
     lib.pufe_destroy.restype = None
     lib.pufe_last_error.restype = C.c_char_p
@@ -226,7 +228,7 @@ class Context:
                                              _stream(stream)))
 
     def pufe_scf_step(self, eps, Cmat, nelec, kT, alpha, rho_I, V_eff_in, n, V_eff_out,
-                      prec=PUFE_FP64, stream=None):
+                      prec=PUFE_FP64, pulay=0, stream=None):
         """One SCF step; returns (occupations, info dict).  Blocking."""
         import numpy as np
         import torch
@@ -236,11 +238,15 @@ class Context:
         dp = C.POINTER(C.c_double)
         _check(_LIB.pufe_scf_step(self._h, int(len(eps)), eps.ctypes.data_as(dp),
                                   _ptr(Cmat, torch.float64), int(Cmat.stride(0)), float(nelec),
-                                  float(kT), float(alpha), int(prec), _ptr(rho_I, torch.float64),
+                                  float(kT), float(alpha), int(pulay), int(prec),
+                                  _ptr(rho_I, torch.float64),
                                   _ptr(V_eff_in, torch.float64), _ptr(n, torch.float64),
                                   _ptr(V_eff_out, torch.float64), f.ctypes.data_as(dp),
                                   C.byref(info), _stream(stream)))
         return f, info.as_dict()
+
+    def pufe_scf_reset(self):
+        _check(_LIB.pufe_scf_reset(self._h))
 
     def pufe_sync_status(self, stream=None):
         _check(_LIB.pufe_sync_status(self._h, _stream(stream)))

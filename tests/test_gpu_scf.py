@@ -111,11 +111,12 @@ def test_scf_step_matches_oracle(setup, prec):
     assert abs(info["residual"] - ref["residual"]) < tol * max(1.0, ref["residual"]) + 1e-12
 
 
-def test_scf_loop_matches_oracle_loop():
-    """Five SCF iterations on the 2^3 two-atom cell, both sides from the same
+@pytest.mark.parametrize("pulay", [0, 4])
+def test_scf_loop_matches_oracle_loop(pulay):
+    """Six SCF iterations on the 2^3 two-atom cell, both sides from the same
     start: GPU = pufe_assemble_HS + host eigensolve + pufe_scf_step, oracle =
-    its own assembly, eigensolve and step.  Eigenvalues, energy and residual
-    agree, and the residual falls."""
+    its own assembly, eigensolve and step; linear and Pulay mixing.
+    Eigenvalues, energy and residual agree, and the residual falls."""
     wl = W.small_two_atom(nel=2, quad_p=6)
     m = omesh.Mesh(wl)
     rules = oq.all_rules(m)
@@ -135,11 +136,14 @@ def test_scf_loop_matches_oracle_loop():
     H = torch.empty(ctx.nnz, dtype=torch.float64, device=dev)
     S = torch.empty_like(H)
     rowptr, col = ctx.pattern()
+    mixer = oscf.PulayMixer(pulay) if pulay > 1 else None
+    ctx.pufe_scf_reset()
     res = []
-    for it in range(5):
+    for it in range(6):
         Ho, So = oasm.assemble_HS(m, rules, V_o)
         eo, Co = oeig.lowest_eigs(Ho, So, nst)
-        ro = oscf.scf_step(m, rules, wl, eo, Co, wl["nelec"], kT, alpha, n_o, V_o, rho_h, K)
+        ro = oscf.scf_step(m, rules, wl, eo, Co, wl["nelec"], kT, alpha, n_o, V_o, rho_h, K,
+                           mixer=mixer)
         n_o, V_o = ro["n_new"], ro["V_eff"]
         ctx.pufe_assemble_HS(V_g, H, S)
         ctx.pufe_sync_status()
@@ -147,7 +151,8 @@ def test_scf_loop_matches_oracle_loop():
         Sg = sp.csr_matrix((S.cpu().numpy(), col, rowptr), shape=(ctx.n_dof, ctx.n_dof))
         eg, Cg = oeig.lowest_eigs(Hg, Sg, nst)
         _, info = ctx.pufe_scf_step(eg, torch.tensor(np.ascontiguousarray(Cg), device=dev),
-                                    wl["nelec"], kT, alpha, rho_I, V_g, n_g, V_next)
+                                    wl["nelec"], kT, alpha, rho_I, V_g, n_g, V_next,
+                                    pulay=pulay)
         V_g, V_next = V_next, V_g
         assert np.abs(eg - eo).max() < 1e-9, it
         assert abs(info["e_total"] - ro["e_total"]) < 1e-9, it
@@ -155,3 +160,4 @@ def test_scf_loop_matches_oracle_loop():
         res.append(info["residual"])
     assert res[-1] < res[0]
     assert _rel(n_g.cpu().numpy(), n_o) < 1e-9
+    print(f"pulay={pulay}: residuals", ["%.2e" % r for r in res])
