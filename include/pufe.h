@@ -203,6 +203,36 @@ pufe_status pufe_density(pufe_ctx *ctx, const double *C, int64_t ldc,
 pufe_status pufe_assemble_HV_adjoint(pufe_ctx *ctx, const double *Hbar, int prec, double *Vbar,
                                      void *stream);
 
+/* ---- Bloch-periodic states, k != 0 (Sec. 4, eqs. bloch, strong) --------- */
+
+/* H(k) and/or S(k) of the Bloch-periodic basis at wavevector k (host,
+ * 3 components, 1/bohr): the same element matrices as pufe_assemble_HS,
+ * scattered with the phase exp(i k.(R_j - R_i)) of each column pair, where
+ * R_i is the lattice translation that maps the column's node or PU vertex
+ * onto its representative in the cell (the enrichments themselves are
+ * periodic, Sec. 5.1 eq. Psi with f(R) = 1).  Outputs are the real and
+ * imaginary parts, each nnz float64 on the CSR pattern (device,
+ * overwritten; H(k) and S(k) are Hermitian).  FP64 only: needs
+ * pufe_tabulate(ctx, PUFE_FP64).  k = 0 gives the Gamma-point matrices with
+ * zero imaginary parts.  Asynchronous. */
+pufe_status pufe_assemble_HS_bloch(pufe_ctx *ctx, const double *k, const double *V, int what,
+                                   double *H_re, double *H_im, double *S_re, double *S_im,
+                                   void *stream);
+
+/* Density of complex Bloch states: n_q = sum_j f_j |sum_l B_ql
+ * exp(i k.R_l) C_lj|^2 with C = C_re + i C_im (device float64, N x nocc, row
+ * stride ldc).  Other arguments as pufe_density; FP64 only.  Asynchronous. */
+pufe_status pufe_density_bloch(pufe_ctx *ctx, const double *k, const double *C_re,
+                               const double *C_im, int64_t ldc, const double *f, int nocc,
+                               double *rho, void *stream);
+
+/* Adjoint of V -> H(k) for a complex cotangent Hbar = Hbar_re + i Hbar_im
+ * (device, nnz each): Vbar_q = w_q Re sum_ij conj(Hbar[g_i, g_j])
+ * exp(i k.(R_j - R_i)) b_i b_j, the derivative of Re sum conj(Hbar) H(k).
+ * FP64 only.  Asynchronous. */
+pufe_status pufe_assemble_HV_adjoint_bloch(pufe_ctx *ctx, const double *k, const double *Hbar_re,
+                                           const double *Hbar_im, double *Vbar, void *stream);
+
 /* ---- self-consistent field (Sec. 3) ------------------------------------ */
 
 /* Ionic charge density at every quadrature point (Sec. 3: the ionic

@@ -112,6 +112,55 @@ pufe_status pufe_assemble_HV_adjoint(pufe_ctx *ctx, const double *Hbar, int prec
   return launch_adjoint_fp64(ctx, Hbar, Vbar, (cudaStream_t)stream);
 }
 
+pufe_status pufe_assemble_HS_bloch(pufe_ctx *ctx, const double *k, const double *V, int what,
+                                   double *H_re, double *H_im, double *S_re, double *S_im,
+                                   void *stream) {
+  if (pufe_status e0 = need_device(ctx)) return e0;
+  if (!k) return fail(PUFE_EINVAL, "k must not be NULL");
+  if (pufe_status e1 = need_table(ctx, PUFE_FP64)) return e1;
+  if (what <= 0 || what > (PUFE_WANT_H | PUFE_WANT_S)) return fail(PUFE_EINVAL, "bad `what` mask");
+  if ((what & PUFE_WANT_H) && (!H_re || !H_im || !V))
+    return fail(PUFE_EINVAL, "H wanted: need H_re, H_im and V");
+  if ((what & PUFE_WANT_S) && (!S_re || !S_im)) return fail(PUFE_EINVAL, "S wanted: need S_re, S_im");
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return fail(PUFE_ECUDA, "cudaSetDevice failed");
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t bytes = (size_t)ctx->nnz * sizeof(double);
+  if (what & PUFE_WANT_H) {
+    PUFE_CUDA_TRY(cudaMemsetAsync(H_re, 0, bytes, st));
+    PUFE_CUDA_TRY(cudaMemsetAsync(H_im, 0, bytes, st));
+  }
+  if (what & PUFE_WANT_S) {
+    PUFE_CUDA_TRY(cudaMemsetAsync(S_re, 0, bytes, st));
+    PUFE_CUDA_TRY(cudaMemsetAsync(S_im, 0, bytes, st));
+  }
+  return launch_assemble_fp64_bloch(ctx, phase_table(ctx, k), V, what, H_re, H_im, S_re, S_im, st);
+}
+
+pufe_status pufe_density_bloch(pufe_ctx *ctx, const double *k, const double *C_re,
+                               const double *C_im, int64_t ldc, const double *f, int nocc,
+                               double *rho, void *stream) {
+  if (pufe_status e0 = need_device(ctx)) return e0;
+  if (pufe_status e1 = need_table(ctx, PUFE_FP64)) return e1;
+  if (!k || !C_re || !C_im || !f || !rho) return fail(PUFE_EINVAL, "k, C_re, C_im, f and rho must not be NULL");
+  if (nocc < 1 || nocc > 64 || ldc < nocc) return fail(PUFE_EINVAL, "need 1 <= nocc <= 64 and ldc >= nocc");
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return fail(PUFE_ECUDA, "cudaSetDevice failed");
+  return launch_density_fp64_bloch(ctx, phase_table(ctx, k), C_re, C_im, ldc, f, nocc, rho,
+                                   (cudaStream_t)stream);
+}
+
+pufe_status pufe_assemble_HV_adjoint_bloch(pufe_ctx *ctx, const double *k, const double *Hbar_re,
+                                           const double *Hbar_im, double *Vbar, void *stream) {
+  if (pufe_status e0 = need_device(ctx)) return e0;
+  if (pufe_status e1 = need_table(ctx, PUFE_FP64)) return e1;
+  if (!k || !Hbar_re || !Hbar_im || !Vbar) return fail(PUFE_EINVAL, "k, Hbar_re, Hbar_im and Vbar must not be NULL");
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return fail(PUFE_ECUDA, "cudaSetDevice failed");
+  return launch_adjoint_fp64_bloch(ctx, phase_table(ctx, k), Hbar_re, Hbar_im, Vbar,
+                                   (cudaStream_t)stream);
+}
+
 pufe_status pufe_ion_density(pufe_ctx *ctx, int natoms, const double *tau, const double *Z,
                              const double *sigma, double *rho_I, void *stream) {
   if (pufe_status e0 = need_device(ctx)) return e0;

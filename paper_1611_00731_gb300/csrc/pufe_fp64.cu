@@ -93,6 +93,10 @@ __device__ __forceinline__ void pu_column(const double xi[3], int lv, const doub
 //   H += sum_d y_d y_d^T + zv z^T,   S += z z^T,
 // then adds its entries into the CSR values through the scatter map.
 // ---------------------------------------------------------------------------
+// BLOCH: the scatter carries the phase exp(i k.(R_j - R_i)) of the column
+// pair (lattice shifts from `eshift`, phases of the 8 shift codes in `ph`)
+// into separate real and imaginary outputs (Sec. 4, eq. bloch).
+template <bool BLOCH>
 __global__ void __launch_bounds__(ASM_NT) k_assemble_fp64(
     const int32_t *__restrict__ order, const int64_t *__restrict__ qoff,
     const double *__restrict__ w, const double *__restrict__ xi_all,
@@ -100,7 +104,9 @@ __global__ void __launch_bounds__(ASM_NT) k_assemble_fp64(
     const int64_t *__restrict__ toff, const double *__restrict__ psi,
     const int64_t *__restrict__ soff, const int32_t *__restrict__ smap,
     const double *__restrict__ V, double sx, double sy, double sz, int npad_max, int want,
-    double *__restrict__ H, double *__restrict__ S, unsigned *err) {
+    double *__restrict__ H, double *__restrict__ S, unsigned *err,
+    const uint8_t *__restrict__ eshift, PhaseTab ph, double *__restrict__ Hi,
+    double *__restrict__ Si) {
   extern __shared__ __align__(16) double smem[];
   const int e = order[blockIdx.x];
   const int64_t q0 = qoff[e];
@@ -224,6 +230,32 @@ __global__ void __launch_bounds__(ASM_NT) k_assemble_fp64(
           if (i >= n || j >= n || j > i) continue;
           const int32_t sij = m[(int64_t)i * n + j];
           const int32_t sji = m[(int64_t)j * n + i];
+          if (BLOCH) {
+            // (i, j) gets conj(ph_i) ph_j, (j, i) its conjugate
+            const int ci = eshift[doff[e] + i], cj = eshift[doff[e] + j];
+            double pr = 1.0, pim = 0.0;
+            if (ci != cj) {
+              pr = ph.re[ci] * ph.re[cj] + ph.im[ci] * ph.im[cj];
+              pim = ph.re[ci] * ph.im[cj] - ph.im[ci] * ph.re[cj];
+            }
+            if (want & PUFE_WANT_H) {
+              atomicAdd(H + sij, h[a][b] * pr);
+              atomicAdd(Hi + sij, h[a][b] * pim);
+              if (i != j) {
+                atomicAdd(H + sji, h[a][b] * pr);
+                atomicAdd(Hi + sji, -h[a][b] * pim);
+              }
+            }
+            if (want & PUFE_WANT_S) {
+              atomicAdd(S + sij, sv[a][b] * pr);
+              atomicAdd(Si + sij, sv[a][b] * pim);
+              if (i != j) {
+                atomicAdd(S + sji, sv[a][b] * pr);
+                atomicAdd(Si + sji, -sv[a][b] * pim);
+              }
+            }
+            continue;
+          }
           if (want & PUFE_WANT_H) {
             atomicAdd(H + sij, h[a][b]);
             if (i != j) atomicAdd(H + sji, h[a][b]);
@@ -283,13 +315,17 @@ __device__ __forceinline__ double density_point(const double xi[3], int q, int Q
   return r;
 }
 
+// BLOCH: complex coefficients C + i Ci; each element block is gathered with
+// the column phases applied, and n = sum_k f_k (Re psi_k^2 + Im psi_k^2).
+template <bool BLOCH>
 __global__ void __launch_bounds__(DEN_NT) k_density_fp64(
     const int32_t *__restrict__ order, const int64_t *__restrict__ qoff,
     const double *__restrict__ xi_all, const int64_t *__restrict__ doff,
     const int32_t *__restrict__ dofs, const int32_t *__restrict__ ecol,
     const int64_t *__restrict__ toff, const double *__restrict__ psi,
     const double *__restrict__ C, int64_t ldc, const double *__restrict__ f, int nocc,
-    int noccp, double *__restrict__ rho) {
+    int noccp, double *__restrict__ rho, const uint8_t *__restrict__ eshift, PhaseTab ph,
+    const double *__restrict__ Ci) {
   extern __shared__ __align__(16) double smem[];
   const int e = order[blockIdx.x];
   const int64_t q0 = qoff[e];
@@ -301,17 +337,32 @@ __global__ void __launch_bounds__(DEN_NT) k_density_fp64(
   const double *pe = psi + 4 * toff[e];
   double *Cs = smem;             // n x noccp
   double *fs = Cs + n * noccp;   // noccp
+  double *Cz = fs + noccp;       // n x noccp, imaginary parts (BLOCH)
   for (int k = threadIdx.x; k < n * noccp; k += DEN_NT) {
     const int j = k / noccp, kk = k - j * noccp;
-    Cs[k] = (kk < nocc) ? C[(int64_t)dl[j] * ldc + kk] : 0.0;
+    if (BLOCH) {
+      double cr = 0.0, ci = 0.0;
+      if (kk < nocc) {
+        const double ar = C[(int64_t)dl[j] * ldc + kk], ai = Ci[(int64_t)dl[j] * ldc + kk];
+        const int c = eshift[doff[e] + j];
+        cr = ph.re[c] * ar - ph.im[c] * ai;
+        ci = ph.re[c] * ai + ph.im[c] * ar;
+      }
+      Cs[k] = cr;
+      Cz[k] = ci;
+    } else {
+      Cs[k] = (kk < nocc) ? C[(int64_t)dl[j] * ldc + kk] : 0.0;
+    }
   }
   for (int k = threadIdx.x; k < noccp; k += DEN_NT) fs[k] = (k < nocc) ? f[k] : 0.0;
   __syncthreads();
   for (int q = threadIdx.x; q < Q; q += DEN_NT) {
     const double xq[3] = {xi_all[3 * (q0 + q)], xi_all[3 * (q0 + q) + 1], xi_all[3 * (q0 + q) + 2]};
     double r = 0.0;
-    for (int k0 = 0; k0 < noccp; k0 += 8)
+    for (int k0 = 0; k0 < noccp; k0 += 8) {
       r += density_point<8>(xq, q, Q, nenr, ec, pe, Cs, fs, noccp, k0);
+      if (BLOCH) r += density_point<8>(xq, q, Q, nenr, ec, pe, Cz, fs, noccp, k0);
+    }
     rho[q0 + q] = r;
   }
 }
@@ -322,13 +373,17 @@ __global__ void __launch_bounds__(DEN_NT) k_density_fp64(
 // map when it does not fit); per chunk of QC points the basis rows are built
 // in shared memory and each thread reduces one (q, i) pair over j.
 // ---------------------------------------------------------------------------
+// BLOCH: complex cotangent Hbar + i Hbi; the element block used is
+// Re(conj(Hbar) exp(i k.(R_j - R_i))) = Hbar pr + Hbi pi.
+template <bool BLOCH>
 __global__ void __launch_bounds__(ADJ_NT) k_adjoint_fp64(
     const int32_t *__restrict__ order, const int64_t *__restrict__ qoff,
     const double *__restrict__ w, const double *__restrict__ xi_all,
     const int64_t *__restrict__ doff, const int32_t *__restrict__ ecol,
     const int64_t *__restrict__ toff, const double *__restrict__ psi,
     const int64_t *__restrict__ soff, const int32_t *__restrict__ smap,
-    const double *__restrict__ Hbar, int hs_in_smem, double *__restrict__ Vbar) {
+    const double *__restrict__ Hbar, int hs_in_smem, double *__restrict__ Vbar,
+    const uint8_t *__restrict__ eshift, PhaseTab ph, const double *__restrict__ Hbi) {
   extern __shared__ __align__(16) double smem[];
   const int e = order[blockIdx.x];
   const int64_t q0 = qoff[e];
@@ -341,8 +396,20 @@ __global__ void __launch_bounds__(ADJ_NT) k_adjoint_fp64(
   double *acc = Bc + QC * n;         // QC
   Tab1D *tab = reinterpret_cast<Tab1D *>(acc + QC);
   double *Hs = reinterpret_cast<double *>(tab + QC);  // n x n when it fits
+  // element entry (i, j) of the cotangent (phased real part for BLOCH)
+  auto hval = [&](int i, int j) -> double {
+    const int32_t sl = m[(int64_t)i * n + j];
+    if (!BLOCH) return Hbar[sl];
+    const int ci = eshift[doff[e] + i], cj = eshift[doff[e] + j];
+    double pr = 1.0, pim = 0.0;
+    if (ci != cj) {
+      pr = ph.re[ci] * ph.re[cj] + ph.im[ci] * ph.im[cj];
+      pim = ph.re[ci] * ph.im[cj] - ph.im[ci] * ph.re[cj];
+    }
+    return Hbar[sl] * pr + Hbi[sl] * pim;
+  };
   if (hs_in_smem)
-    for (int k = threadIdx.x; k < n * n; k += ADJ_NT) Hs[k] = Hbar[m[k]];
+    for (int k = threadIdx.x; k < n * n; k += ADJ_NT) Hs[k] = hval(k / n, k % n);
   const double s[3] = {0, 0, 0};
   for (int qc = 0; qc < Q; qc += QC) {
     __syncthreads();
@@ -389,8 +456,7 @@ __global__ void __launch_bounds__(ADJ_NT) k_adjoint_fp64(
         const double *hr = Hs + (int64_t)i * n;
         for (int j = 0; j < n; ++j) t = fma(hr[j], brow[j], t);
       } else {
-        const int32_t *mr = m + (int64_t)i * n;
-        for (int j = 0; j < n; ++j) t = fma(Hbar[mr[j]], brow[j], t);
+        for (int j = 0; j < n; ++j) t = fma(hval(i, j), brow[j], t);
       }
       atomicAdd(acc + qq, brow[i] * t);
     }
@@ -422,11 +488,12 @@ pufe_status launch_assemble_fp64(pufe_ctx *ctx, const double *V, int what, doubl
   const int npad = (ctx->max_basis + 3) & ~3;
   const size_t sm = (size_t)5 * QC * npad * sizeof(double) + QC * sizeof(Tab1D);
   if (sm > 227 * 1024) return fail(PUFE_EINVAL, "element basis too large for the FP64 kernel");
-  PUFE_CUDA_TRY(cudaFuncSetAttribute(k_assemble_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)sm));
-  k_assemble_fp64<<<(unsigned)ctx->nelem, ASM_NT, sm, st>>>(
+  PUFE_CUDA_TRY(cudaFuncSetAttribute(k_assemble_fp64<false>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  k_assemble_fp64<false><<<(unsigned)ctx->nelem, ASM_NT, sm, st>>>(
       D.order, D.qoff, D.w, D.xi, D.doff, D.ecol, D.toff, D.psi, D.soff, D.smap, V,
-      2.0 / ctx->h[0], 2.0 / ctx->h[1], 2.0 / ctx->h[2], npad, what, H, S, D.err);
+      2.0 / ctx->h[0], 2.0 / ctx->h[1], 2.0 / ctx->h[2], npad, what, H, S, D.err, nullptr,
+      PhaseTab{}, nullptr, nullptr);
   PUFE_CUDA_TRY(cudaGetLastError());
   return PUFE_OK;
 }
@@ -437,11 +504,11 @@ pufe_status launch_density_fp64(pufe_ctx *ctx, const double *C, int64_t ldc, con
   const int noccp = (nocc + 7) & ~7;
   const size_t sm = ((size_t)ctx->max_basis * noccp + noccp) * sizeof(double);
   if (sm > 227 * 1024) return fail(PUFE_EINVAL, "n_e * nocc too large for the density kernel");
-  PUFE_CUDA_TRY(cudaFuncSetAttribute(k_density_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)sm));
-  k_density_fp64<<<(unsigned)ctx->nelem, DEN_NT, sm, st>>>(D.order, D.qoff, D.xi, D.doff, D.dofs,
-                                                           D.ecol, D.toff, D.psi, C, ldc, f, nocc,
-                                                           noccp, rho);
+  PUFE_CUDA_TRY(cudaFuncSetAttribute(k_density_fp64<false>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  k_density_fp64<false><<<(unsigned)ctx->nelem, DEN_NT, sm, st>>>(
+      D.order, D.qoff, D.xi, D.doff, D.dofs, D.ecol, D.toff, D.psi, C, ldc, f, nocc, noccp, rho,
+      nullptr, PhaseTab{}, nullptr);
   PUFE_CUDA_TRY(cudaGetLastError());
   return PUFE_OK;
 }
@@ -453,11 +520,76 @@ pufe_status launch_adjoint_fp64(pufe_ctx *ctx, const double *Hbar, double *Vbar,
   const size_t hs = (size_t)n * n * sizeof(double);
   int in_smem = (sm + hs <= 200 * 1024) ? 1 : 0;
   if (in_smem) sm += hs;
-  PUFE_CUDA_TRY(cudaFuncSetAttribute(k_adjoint_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)sm));
-  k_adjoint_fp64<<<(unsigned)ctx->nelem, ADJ_NT, sm, st>>>(D.order, D.qoff, D.w, D.xi, D.doff,
-                                                           D.ecol, D.toff, D.psi, D.soff, D.smap,
-                                                           Hbar, in_smem, Vbar);
+  PUFE_CUDA_TRY(cudaFuncSetAttribute(k_adjoint_fp64<false>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  k_adjoint_fp64<false><<<(unsigned)ctx->nelem, ADJ_NT, sm, st>>>(
+      D.order, D.qoff, D.w, D.xi, D.doff, D.ecol, D.toff, D.psi, D.soff, D.smap, Hbar, in_smem,
+      Vbar, nullptr, PhaseTab{}, nullptr);
+  PUFE_CUDA_TRY(cudaGetLastError());
+  return PUFE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Bloch (k != 0) launchers
+// ---------------------------------------------------------------------------
+PhaseTab phase_table(const pufe_ctx *ctx, const double k[3]) {
+  PhaseTab t;
+  for (int c = 0; c < 8; ++c) {
+    double th = 0.0;
+    for (int d = 0; d < 3; ++d)
+      if ((c >> d) & 1) th += k[d] * ctx->a[d];
+    t.re[c] = cos(th);
+    t.im[c] = sin(th);
+  }
+  return t;
+}
+
+pufe_status launch_assemble_fp64_bloch(pufe_ctx *ctx, const PhaseTab &ph, const double *V,
+                                       int what, double *H, double *Hi, double *S, double *Si,
+                                       cudaStream_t st) {
+  auto &D = ctx->d;
+  const int npad = (ctx->max_basis + 3) & ~3;
+  const size_t sm = (size_t)5 * QC * npad * sizeof(double) + QC * sizeof(Tab1D);
+  if (sm > 227 * 1024) return fail(PUFE_EINVAL, "element basis too large for the FP64 kernel");
+  PUFE_CUDA_TRY(cudaFuncSetAttribute(k_assemble_fp64<true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  k_assemble_fp64<true><<<(unsigned)ctx->nelem, ASM_NT, sm, st>>>(
+      D.order, D.qoff, D.w, D.xi, D.doff, D.ecol, D.toff, D.psi, D.soff, D.smap, V,
+      2.0 / ctx->h[0], 2.0 / ctx->h[1], 2.0 / ctx->h[2], npad, what, H, S, D.err, D.eshift, ph,
+      Hi, Si);
+  PUFE_CUDA_TRY(cudaGetLastError());
+  return PUFE_OK;
+}
+
+pufe_status launch_density_fp64_bloch(pufe_ctx *ctx, const PhaseTab &ph, const double *Cr,
+                                      const double *Ci, int64_t ldc, const double *f, int nocc,
+                                      double *rho, cudaStream_t st) {
+  auto &D = ctx->d;
+  const int noccp = (nocc + 7) & ~7;
+  const size_t sm = ((size_t)2 * ctx->max_basis * noccp + noccp) * sizeof(double);
+  if (sm > 227 * 1024) return fail(PUFE_EINVAL, "n_e * nocc too large for the density kernel");
+  PUFE_CUDA_TRY(cudaFuncSetAttribute(k_density_fp64<true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  k_density_fp64<true><<<(unsigned)ctx->nelem, DEN_NT, sm, st>>>(
+      D.order, D.qoff, D.xi, D.doff, D.dofs, D.ecol, D.toff, D.psi, Cr, ldc, f, nocc, noccp, rho,
+      D.eshift, ph, Ci);
+  PUFE_CUDA_TRY(cudaGetLastError());
+  return PUFE_OK;
+}
+
+pufe_status launch_adjoint_fp64_bloch(pufe_ctx *ctx, const PhaseTab &ph, const double *Hr,
+                                      const double *Hi, double *Vbar, cudaStream_t st) {
+  auto &D = ctx->d;
+  const int n = ctx->max_basis;
+  size_t sm = (size_t)QC * n * sizeof(double) + QC * sizeof(double) + QC * sizeof(Tab1D);
+  const size_t hs = (size_t)n * n * sizeof(double);
+  int in_smem = (sm + hs <= 200 * 1024) ? 1 : 0;
+  if (in_smem) sm += hs;
+  PUFE_CUDA_TRY(cudaFuncSetAttribute(k_adjoint_fp64<true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  k_adjoint_fp64<true><<<(unsigned)ctx->nelem, ADJ_NT, sm, st>>>(
+      D.order, D.qoff, D.w, D.xi, D.doff, D.ecol, D.toff, D.psi, D.soff, D.smap, Hr, in_smem,
+      Vbar, D.eshift, ph, Hi);
   PUFE_CUDA_TRY(cudaGetLastError());
   return PUFE_OK;
 }

@@ -63,6 +63,7 @@ struct DeviceArrays {
   int64_t *doff = nullptr;    // nelem + 1: offsets into dofs (n_e each)
   int32_t *dofs = nullptr;    // sum n_e: global DOF of each element column
   int32_t *ecol = nullptr;    // sum (n_e - 64): (aslot << 3) | local vertex
+  uint8_t *eshift = nullptr;  // sum n_e: lattice shift bits of each column (Bloch phases)
   int32_t *aoff = nullptr;    // nelem + 1: offsets into alist
   int32_t *alist = nullptr;   // element enrichment list (global alpha ids)
   int64_t *toff = nullptr;    // nelem + 1: offsets into psi (units of q*alpha)
@@ -270,6 +271,19 @@ pufe_status launch_assemble_fp64(pufe_ctx *ctx, const double *V, int what, doubl
 pufe_status launch_density_fp64(pufe_ctx *ctx, const double *C, int64_t ldc, const double *f,
                                 int nocc, double *rho, cudaStream_t s);
 pufe_status launch_adjoint_fp64(pufe_ctx *ctx, const double *Hbar, double *Vbar, cudaStream_t s);
+// Bloch (k != 0) FP64 variants: phases exp(i k . R) of the 8 shift codes
+struct PhaseTab {
+  double re[8], im[8];
+};
+PhaseTab phase_table(const pufe_ctx *ctx, const double k[3]);
+pufe_status launch_assemble_fp64_bloch(pufe_ctx *ctx, const PhaseTab &ph, const double *V,
+                                       int what, double *H, double *Hi, double *S, double *Si,
+                                       cudaStream_t s);
+pufe_status launch_density_fp64_bloch(pufe_ctx *ctx, const PhaseTab &ph, const double *Cr,
+                                      const double *Ci, int64_t ldc, const double *f, int nocc,
+                                      double *rho, cudaStream_t s);
+pufe_status launch_adjoint_fp64_bloch(pufe_ctx *ctx, const PhaseTab &ph, const double *Hr,
+                                      const double *Hi, double *Vbar, cudaStream_t s);
 pufe_status launch_tabulate_f32(pufe_ctx *ctx, cudaStream_t s);
 pufe_status launch_adjoint_tc(pufe_ctx *ctx, const double *Hbar, double *Vbar, cudaStream_t s);
 pufe_status launch_fefe(pufe_ctx *ctx, const double *V, double *H, cudaStream_t s);  // H must be zeroed

@@ -457,6 +457,9 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
   std::vector<float> ptab(32 * qpoff[nelem], 0.0f);
   std::vector<float> eorig(8 * aoff[nelem], 0.0f);
   std::vector<int32_t> dofs(doff[nelem]), ecol(doff[nelem] - 64 * nelem), alist(aoff[nelem]);
+  // lattice shift of every element column's node or vertex (bit d: one cell
+  // along axis d), for the Bloch phases at k != 0
+  std::vector<uint8_t> eshift(doff[nelem]);
   int64_t ecpos = 0;
   for (int64_t e = 0; e < nelem; ++e) {
     int ex = (int)(e % nx), ey = (int)((e / nx) % ny), ez = (int)(e / ((int64_t)nx * ny));
@@ -466,6 +469,9 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
         for (int a = 0; a < 4; ++a) {
           int64_t gx = (3 * ex + a) % mx, gy = (3 * ey + b) % my, gz = (3 * ez + c) % mz;
           d[a + 4 * b + 16 * c] = (int32_t)(gx + mx * (gy + (int64_t)my * gz));
+          eshift[doff[e] + a + 4 * b + 16 * c] =
+              (uint8_t)((3 * ex + a >= mx ? 1 : 0) | (3 * ey + b >= my ? 2 : 0) |
+                        (3 * ez + c >= mz ? 4 : 0));
         }
     for (size_t k = 0; k < ealpha[e].size(); ++k) {
       alist[aoff[e] + k] = ealpha[e][k];
@@ -506,6 +512,10 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
       int slot = (int)(std::lower_bound(ealpha[e].begin(), ealpha[e].end(), cols[e][j].alpha) -
                        ealpha[e].begin());
       ecol[ecpos++] = (slot << 3) | cols[e][j].lv;
+      const int lv = cols[e][j].lv;
+      eshift[doff[e] + 64 + j] = (uint8_t)((ex + (lv & 1) >= nx ? 1 : 0) |
+                                           (ey + ((lv >> 1) & 1) >= ny ? 2 : 0) |
+                                           (ez + (lv >> 2) >= nz ? 4 : 0));
     }
   }
 
@@ -685,6 +695,7 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
   if ((st = upload(&D.doff, doff)) != PUFE_OK) return st;
   if ((st = upload(&D.dofs, dofs)) != PUFE_OK) return st;
   if ((st = upload(&D.ecol, ecol)) != PUFE_OK) return st;
+  if ((st = upload(&D.eshift, eshift)) != PUFE_OK) return st;
   if ((st = upload(&D.aoff, aoff)) != PUFE_OK) return st;
   if ((st = upload(&D.alist, alist)) != PUFE_OK) return st;
   if ((st = upload(&D.toff, toff)) != PUFE_OK) return st;
@@ -740,7 +751,7 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
 static void free_device(pufe_ctx *ctx) {
   scf_free(ctx);
   auto &D = ctx->d;
-  void *ptrs[] = {D.qoff, D.x, D.w, D.xi, D.doff, D.dofs, D.ecol, D.aoff, D.alist,
+  void *ptrs[] = {D.qoff, D.x, D.w, D.xi, D.doff, D.dofs, D.ecol, D.eshift, D.aoff, D.alist,
                   D.toff, D.psi, D.psi32, D.qpoff, D.qdat, D.ptab, D.vpad, D.toff32, D.eorig,
                   D.Tfe, D.S0, D.partoff, D.part_p, D.part_q,
                   D.orb, D.orbf, D.rowptr, D.col, D.soff, D.smap, D.order, D.err};

@@ -29,7 +29,8 @@ EXPORTS = ["pufe_build_mesh", "pufe_get_sizes", "pufe_get_quadrature", "pufe_get
            "pufe_get_element_basis", "pufe_tabulate", "pufe_assemble_HS", "pufe_density",
            "pufe_assemble_HV_adjoint", "pufe_sync_status", "pufe_destroy", "pufe_last_error",
            "pufe_assemble_HS_static", "pufe_ion_density", "pufe_effective_potential",
-           "pufe_scf_step", "pufe_scf_reset"]
+           "pufe_scf_step", "pufe_scf_reset", "pufe_assemble_HS_bloch", "pufe_density_bloch",
+           "pufe_assemble_HV_adjoint_bloch"]
 
 
 class PufeError(RuntimeError):
@@ -103,6 +104,9 @@ def load_library(build_if_missing: bool = True):
                                   C.c_double, C.c_int, C.c_int, vp, vp, vp, vp, dp,
                                   C.POINTER(ScfInfo), vp]
     lib.pufe_scf_reset.argtypes = [vp]
+    lib.pufe_assemble_HS_bloch.argtypes = [vp, dp, vp, C.c_int, vp, vp, vp, vp, vp]
+    lib.pufe_density_bloch.argtypes = [vp, dp, vp, vp, C.c_int64, vp, C.c_int, vp, vp]
+    lib.pufe_assemble_HV_adjoint_bloch.argtypes = [vp, dp, vp, vp, vp, vp]
     lib.pufe_destroy.argtypes = [vp]
     lib.pufe_destroy.restype = None
     lib.pufe_last_error.restype = C.c_char_p
@@ -244,6 +248,37 @@ class Context:
                                   _ptr(V_eff_out, torch.float64), f.ctypes.data_as(dp),
                                   C.byref(info), _stream(stream)))
         return f, info.as_dict()
+
+    def pufe_assemble_HS_bloch(self, k, V, H=None, S=None, what=None, stream=None):
+        """H(k), S(k) at wavevector k: H and S are (re, im) pairs of nnz tensors."""
+        import torch
+        kk = (C.c_double * 3)(*[float(x) for x in k])
+        if what is None:
+            what = (PUFE_WANT_H if H is not None else 0) | (PUFE_WANT_S if S is not None else 0)
+        Hr, Hi = H if H is not None else (None, None)
+        Sr, Si = S if S is not None else (None, None)
+        f64 = torch.float64
+        _check(_LIB.pufe_assemble_HS_bloch(self._h, kk, _ptr(V, f64), int(what), _ptr(Hr, f64),
+                                           _ptr(Hi, f64), _ptr(Sr, f64), _ptr(Si, f64),
+                                           _stream(stream)))
+
+    def pufe_density_bloch(self, k, Cre, Cim, f, rho, stream=None):
+        import torch
+        kk = (C.c_double * 3)(*[float(x) for x in k])
+        if Cre.shape != Cim.shape or Cre.stride() != Cim.stride():
+            raise ValueError("C_re and C_im must have the same shape and strides")
+        f64 = torch.float64
+        _check(_LIB.pufe_density_bloch(self._h, kk, _ptr(Cre, f64), _ptr(Cim, f64),
+                                       int(Cre.stride(0)), _ptr(f, f64), int(Cre.shape[1]),
+                                       _ptr(rho, f64), _stream(stream)))
+
+    def pufe_assemble_HV_adjoint_bloch(self, k, Hbar_re, Hbar_im, Vbar, stream=None):
+        import torch
+        kk = (C.c_double * 3)(*[float(x) for x in k])
+        f64 = torch.float64
+        _check(_LIB.pufe_assemble_HV_adjoint_bloch(self._h, kk, _ptr(Hbar_re, f64),
+                                                   _ptr(Hbar_im, f64), _ptr(Vbar, f64),
+                                                   _stream(stream)))
 
     def pufe_scf_reset(self):
         _check(_LIB.pufe_scf_reset(self._h))
