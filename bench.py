@@ -146,6 +146,34 @@ def scf_timing(ctx, wl, prec, dev, reps=10):
                     "occupations, output density, energies, mixing and the new potential"}
 
 
+def bloch_timing(ctx, wl, V, dev, reps=3):
+    """Time of the FP64 Bloch assembly H(k), S(k) (real and imaginary parts) at
+    k = (1/4, 1/4, 1/4) 2 pi / a on the same workload."""
+    import math
+
+    import torch
+
+    from paper_1611_00731_gb300 import pufe
+
+    ctx.pufe_tabulate(pufe.PUFE_FP64)
+    k = [0.25 * 2.0 * math.pi / wl["a"]] * 3
+    mk = lambda: torch.empty(ctx.nnz, dtype=torch.float64, device=dev)
+    H, S = (mk(), mk()), (mk(), mk())
+    ctx.pufe_assemble_HS_bloch(k, V, H, S)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        ctx.pufe_assemble_HS_bloch(k, V, H, S)
+        b.record()
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    ctx.pufe_sync_status()
+    return statistics.median(ts)
+
+
 def run_pufe(args):
     import numpy as np
     import torch
@@ -277,6 +305,8 @@ def run_pufe(args):
     barrier()
 
     scf = scf_timing(ctx, wl, prec, dev) if args.scf else None
+    bloch = ({"assemble_HS_ms": bloch_timing(ctx, wl, V, dev), "prec": "fp64",
+              "k": "(1/4, 1/4, 1/4) 2 pi / a"} if args.scf else None)
 
     if ws > 1:
         import torch.distributed as dist
@@ -338,6 +368,7 @@ def run_pufe(args):
                 "d2h_bytes_per_step": int(rho_h.numel() * 8)},
         "gpu_launches": launches_per_step * args.steps,
         "scf": scf,
+        "bloch": bloch,
         "clocks": clocks,
     }
     if not args.no_cpu_baseline:
@@ -428,7 +459,7 @@ def main():
     ap.add_argument("--impl", default="pufe", choices=["pufe", "reference"])
     ap.add_argument("--prec", default="tf32x3", choices=["tf32x3", "fp64"])
     ap.add_argument("--no-scf", dest="scf", action="store_false",
-                    help="skip the timing of the SCF calls")
+                    help="skip the timing of the SCF and Bloch calls")
     ap.add_argument("--density-stream", default="side", choices=["same", "side"],
                     help="run the density on the step's stream or concurrently on a second one")
     ap.add_argument("--launch", default="stream", choices=["graph", "stream"],
