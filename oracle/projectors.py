@@ -55,9 +55,13 @@ def projector_values(proj, a, pts):
                     continue
                 dd = d[near]
                 r = np.sqrt(r2[near])
-                y = real_ylm(l, m, dd[:, 0], dd[:, 1], dd[:, 2]) if l > 0 else \
-                    np.full(len(r), 1.0 / math.sqrt(4.0 * math.pi))
-                out[near] += N * r ** l * np.exp(-r2[near] / (2.0 * rp * rp)) * y
+                # r^l Y_lm, which tends to 0 at the centre for l >= 1
+                rly = np.full(len(r), 1.0 / math.sqrt(4.0 * math.pi))
+                if l > 0:
+                    rly = np.zeros(len(r))
+                    pos = r > 0.0
+                    rly[pos] = r[pos] ** l * real_ylm(l, m, dd[pos, 0], dd[pos, 1], dd[pos, 2])
+                out[near] += N * np.exp(-r2[near] / (2.0 * rp * rp)) * rly
     return out
 
 
