@@ -233,6 +233,29 @@ pufe_status pufe_density_bloch(pufe_ctx *ctx, const double *k, const double *C_r
 pufe_status pufe_assemble_HV_adjoint_bloch(pufe_ctx *ctx, const double *k, const double *Hbar_re,
                                            const double *Hbar_im, double *Vbar, void *stream);
 
+/* ---- separable nonlocal projectors (Sec. 4, eq. disceig3d) -------------- */
+
+/* A Gaussian projector v(x) = N r^l exp(-r^2 / (2 r_p^2)) Y_lm(r_hat),
+ * r = |x - tau - R| summed over lattice translations R, with
+ * N = sqrt(2 / (Gamma(l + 3/2) r_p^(2l+3))) so that int v^2 = 1 (the paper's
+ * projectors come from pseudopotential tables not used here). */
+typedef struct {
+  double tau[3];  /* centre (bohr) */
+  int l, m;       /* 0 <= l <= 3, -l <= m <= l (real Y_lm, as the enrichments) */
+  double r_p;     /* width (bohr), > 0 */
+} pufe_projector;
+
+/* Projections F[i, p] = int phi_i v_p of every basis function onto nproj
+ * projectors (1 <= nproj <= 64; host array), on the shared element rule, at
+ * the Gamma point: the nonlocal term of H is F h F^T for the caller's
+ * projector weights h (a rank-nproj update that may fill entries outside the
+ * sparse pattern, so it is returned as F).  F: device float64, N x nproj
+ * row-major (F[i * nproj + p]), overwritten.  Needs pufe_tabulate(ctx,
+ * PUFE_FP64).  Asynchronous apart from a blocking copy of the projector
+ * list. */
+pufe_status pufe_nonlocal_projections(pufe_ctx *ctx, int nproj, const pufe_projector *proj,
+                                      double *F, void *stream);
+
 /* ---- self-consistent field (Sec. 3) ------------------------------------ */
 
 /* Ionic charge density at every quadrature point (Sec. 3: the ionic

@@ -1,5 +1,8 @@
 // C ABI entry points of the compute calls: argument checks, device guard,
 // output zeroing and dispatch to the FP64 or tensor-core kernels.
+#include <cmath>
+#include <vector>
+
 #include "pufe_internal.h"
 
 namespace pufe {
@@ -159,6 +162,34 @@ pufe_status pufe_assemble_HV_adjoint_bloch(pufe_ctx *ctx, const double *k, const
   if (!g.ok) return fail(PUFE_ECUDA, "cudaSetDevice failed");
   return launch_adjoint_fp64_bloch(ctx, phase_table(ctx, k), Hbar_re, Hbar_im, Vbar,
                                    (cudaStream_t)stream);
+}
+
+pufe_status pufe_nonlocal_projections(pufe_ctx *ctx, int nproj, const pufe_projector *proj,
+                                      double *F, void *stream) {
+  if (pufe_status e0 = need_device(ctx)) return e0;
+  if (pufe_status e1 = need_table(ctx, PUFE_FP64)) return e1;
+  if (nproj < 1 || nproj > 64 || !proj || !F) return fail(PUFE_EINVAL, "need 1 <= nproj <= 64, proj and F");
+  std::vector<ProjDev> pd(nproj);
+  for (int p = 0; p < nproj; ++p) {
+    const pufe_projector &q = proj[p];
+    if (q.l < 0 || q.l > 3 || q.m < -q.l || q.m > q.l || !(q.r_p > 0.0))
+      return fail(PUFE_EINVAL, "projector needs 0 <= l <= 3, |m| <= l, r_p > 0");
+    ProjDev d;
+    for (int c = 0; c < 3; ++c) d.tau[c] = q.tau[c];
+    d.l = q.l;
+    d.m = q.m;
+    d.rp = q.r_p;
+    d.N = std::sqrt(2.0 / (std::tgamma(q.l + 1.5) * std::pow(q.r_p, 2 * q.l + 3)));
+    d.rcut = q.r_p * std::sqrt(2.0 * 20.0 * std::log(10.0));   // Gaussian below 1e-20
+    pd[p] = d;
+  }
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return fail(PUFE_ECUDA, "cudaSetDevice failed");
+  if (!ctx->d.proj) PUFE_CUDA_TRY(cudaMalloc((void **)&ctx->d.proj, 64 * sizeof(ProjDev)));
+  PUFE_CUDA_TRY(cudaMemcpy(ctx->d.proj, pd.data(), nproj * sizeof(ProjDev), cudaMemcpyHostToDevice));
+  cudaStream_t st = (cudaStream_t)stream;
+  PUFE_CUDA_TRY(cudaMemsetAsync(F, 0, (size_t)ctx->n_dof * nproj * sizeof(double), st));
+  return launch_projections(ctx, ctx->d.proj, nproj, F, st);
 }
 
 pufe_status pufe_ion_density(pufe_ctx *ctx, int natoms, const double *tau, const double *Z,

@@ -466,6 +466,111 @@ __global__ void __launch_bounds__(ADJ_NT) k_adjoint_fp64(
   }
 }
 
+// ---------------------------------------------------------------------------
+// Projections of the basis onto separable nonlocal projectors (Sec. 4):
+// F[g_i, p] = sum_e sum_q w_q b_i(x_q) v_p(x_q), with the Gaussian projectors
+// v_p = N r^l exp(-r^2 / (2 r_p^2)) Y_lm summed over the periodic images
+// within r_cut.  One CTA per element; per chunk of QC points the basis rows
+// and w v_p go to shared memory; the element's n x P block accumulates in
+// shared memory and is added into F at the end.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(ASM_NT) k_projections(
+    const int64_t *__restrict__ qoff, const double *__restrict__ w,
+    const double *__restrict__ xi_all, const double *__restrict__ x,
+    const int64_t *__restrict__ doff, const int32_t *__restrict__ dofs,
+    const int32_t *__restrict__ ecol, const int64_t *__restrict__ toff,
+    const double *__restrict__ psi, const ProjDev *__restrict__ pj, int P, double a0, double a1,
+    double a2, double *__restrict__ F) {
+  extern __shared__ __align__(16) double smem[];
+  const int e = blockIdx.x;
+  const int64_t q0 = qoff[e];
+  const int Q = (int)(qoff[e + 1] - q0);
+  const int n = (int)(doff[e + 1] - doff[e]);
+  const int32_t *ec = ecol + (doff[e] - 64ll * e);
+  const double *pe = psi + 4 * toff[e];
+  double *Bc = smem;               // QC x n
+  double *Vp = Bc + QC * n;        // QC x P
+  double *acc = Vp + QC * P;       // n x P
+  Tab1D *tab = reinterpret_cast<Tab1D *>(acc + (size_t)n * P);
+  const double av[3] = {a0, a1, a2};
+  const double s[3] = {0, 0, 0};
+  for (int k = threadIdx.x; k < n * P; k += ASM_NT) acc[k] = 0.0;
+  for (int qc = 0; qc < Q; qc += QC) {
+    __syncthreads();
+    for (int k = threadIdx.x; k < QC * 3; k += ASM_NT) {
+      const int qq = k / 3, d = k - 3 * qq;
+      const int q = qc + qq;
+      const double xv = (q < Q) ? xi_all[3 * (q0 + q) + d] : 0.0;
+      double L[4], dL[4];
+      lagrange3(xv, L, dL);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        tab[qq].L[d][c] = L[c];
+        tab[qq].dL[d][c] = dL[c];
+      }
+    }
+    for (int k = threadIdx.x; k < QC * P; k += ASM_NT) {
+      const int qq = k / P, p = k - qq * P;
+      const int q = qc + qq;
+      double v = 0.0;
+      if (q < Q) {
+        const ProjDev pr = pj[p];
+        double d[3];
+        int lo[3], hi[3];
+        for (int c = 0; c < 3; ++c) {
+          d[c] = x[3 * (q0 + q) + c] - pr.tau[c];
+          lo[c] = (int)ceil((-pr.rcut - d[c]) / av[c]);
+          hi[c] = (int)floor((pr.rcut - d[c]) / av[c]);
+        }
+        const double i2 = 1.0 / (2.0 * pr.rp * pr.rp);
+        for (int i = lo[0]; i <= hi[0]; ++i)
+          for (int j = lo[1]; j <= hi[1]; ++j)
+            for (int l = lo[2]; l <= hi[2]; ++l) {
+              const double dx = d[0] + i * av[0], dy = d[1] + j * av[1], dz = d[2] + l * av[2];
+              const double r2 = dx * dx + dy * dy + dz * dz;
+              if (r2 >= pr.rcut * pr.rcut) continue;
+              double g[3];
+              v += pr.N * exp(-r2 * i2) * solid_harmonic(pr.l, pr.m, dx, dy, dz, g);
+            }
+        v *= w[q0 + q];
+      }
+      Vp[k] = v;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < QC * n; k += ASM_NT) {
+      const int qq = k / n, c = k - qq * n;
+      const int q = qc + qq;
+      double b = 0, gx, gy, gz;
+      if (q < Q) {
+        if (c < 64) {
+          fe_column(tab[qq], c, s, b, gx, gy, gz);
+        } else {
+          const int code = ec[c - 64];
+          const int slot = code >> 3, lv = code & 7;
+          const double ps[4] = {pe[(int64_t)slot * 4 * Q + q], 0.0, 0.0, 0.0};
+          const double xq[3] = {xi_all[3 * (q0 + q)], xi_all[3 * (q0 + q) + 1],
+                                xi_all[3 * (q0 + q) + 2]};
+          pu_column(xq, lv, s, ps, b, gx, gy, gz);
+        }
+      }
+      Bc[k] = b;
+    }
+    __syncthreads();
+    const int qn = min(QC, Q - qc);
+    for (int k = threadIdx.x; k < n * P; k += ASM_NT) {
+      const int i = k / P, p = k - i * P;
+      double t = acc[k];
+      for (int qq = 0; qq < qn; ++qq) t = fma(Bc[qq * n + i], Vp[qq * P + p], t);
+      acc[k] = t;
+    }
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < n * P; k += ASM_NT) {
+    const int i = k / P, p = k - i * P;
+    atomicAdd(F + (int64_t)dofs[doff[e] + i] * P + p, acc[k]);
+  }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -590,6 +695,22 @@ pufe_status launch_adjoint_fp64_bloch(pufe_ctx *ctx, const PhaseTab &ph, const d
   k_adjoint_fp64<true><<<(unsigned)ctx->nelem, ADJ_NT, sm, st>>>(
       D.order, D.qoff, D.w, D.xi, D.doff, D.ecol, D.toff, D.psi, D.soff, D.smap, Hr, in_smem,
       Vbar, D.eshift, ph, Hi);
+  PUFE_CUDA_TRY(cudaGetLastError());
+  return PUFE_OK;
+}
+
+pufe_status launch_projections(pufe_ctx *ctx, const ProjDev *pj, int P, double *F,
+                               cudaStream_t st) {
+  auto &D = ctx->d;
+  const int n = ctx->max_basis;
+  const size_t sm = ((size_t)QC * n + (size_t)QC * P + (size_t)n * P) * sizeof(double) +
+                    QC * sizeof(Tab1D);
+  if (sm > 227 * 1024) return fail(PUFE_EINVAL, "n_e * nproj too large for the projection kernel");
+  PUFE_CUDA_TRY(
+      cudaFuncSetAttribute(k_projections, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  k_projections<<<(unsigned)ctx->nelem, ASM_NT, sm, st>>>(D.qoff, D.w, D.xi, D.x, D.doff, D.dofs,
+                                                          D.ecol, D.toff, D.psi, pj, P, ctx->a[0],
+                                                          ctx->a[1], ctx->a[2], F);
   PUFE_CUDA_TRY(cudaGetLastError());
   return PUFE_OK;
 }

@@ -53,6 +53,8 @@ struct OrbitalF {
 // ---------------------------------------------------------------------------
 // context
 // ---------------------------------------------------------------------------
+struct ProjDev;
+
 struct DeviceArrays {
   // quadrature
   int64_t *qoff = nullptr;    // nelem + 1
@@ -98,6 +100,7 @@ struct DeviceArrays {
   // side stream and events: the FE-FE kernel of the mixed assembly runs on
   // `side`, forked from and joined back into the caller's stream
   cudaStream_t side = nullptr;
+  ProjDev *proj = nullptr;     // 64 projector descriptions (allocated on first use)
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
@@ -271,6 +274,14 @@ pufe_status launch_assemble_fp64(pufe_ctx *ctx, const double *V, int what, doubl
 pufe_status launch_density_fp64(pufe_ctx *ctx, const double *C, int64_t ldc, const double *f,
                                 int nocc, double *rho, cudaStream_t s);
 pufe_status launch_adjoint_fp64(pufe_ctx *ctx, const double *Hbar, double *Vbar, cudaStream_t s);
+// Gaussian nonlocal projector on the device: N r^l exp(-r^2/(2 rp^2)) Y_lm,
+// images within rcut
+struct ProjDev {
+  double tau[3];
+  double rp, N, rcut;
+  int l, m;
+};
+pufe_status launch_projections(pufe_ctx *ctx, const ProjDev *pj, int P, double *F, cudaStream_t s);
 // Bloch (k != 0) FP64 variants: phases exp(i k . R) of the 8 shift codes
 struct PhaseTab {
   double re[8], im[8];

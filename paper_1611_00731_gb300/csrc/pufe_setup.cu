@@ -760,6 +760,7 @@ static void free_device(pufe_ctx *ctx) {
   if (D.ev_fork) cudaEventDestroy(D.ev_fork);
   if (D.ev_join) cudaEventDestroy(D.ev_join);
   if (D.side) cudaStreamDestroy(D.side);
+  if (D.proj) cudaFree(D.proj);
   D = DeviceArrays();
 }
 

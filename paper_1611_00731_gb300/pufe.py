@@ -30,7 +30,7 @@ EXPORTS = ["pufe_build_mesh", "pufe_get_sizes", "pufe_get_quadrature", "pufe_get
            "pufe_assemble_HV_adjoint", "pufe_sync_status", "pufe_destroy", "pufe_last_error",
            "pufe_assemble_HS_static", "pufe_ion_density", "pufe_effective_potential",
            "pufe_scf_step", "pufe_scf_reset", "pufe_assemble_HS_bloch", "pufe_density_bloch",
-           "pufe_assemble_HV_adjoint_bloch"]
+           "pufe_assemble_HV_adjoint_bloch", "pufe_nonlocal_projections"]
 
 
 class PufeError(RuntimeError):
@@ -54,6 +54,11 @@ class _Quad(C.Structure):
     _fields_ = [("mode", C.c_int), ("p_far", C.c_int), ("p_near", C.c_int),
                 ("p_min", C.c_int), ("p_max", C.c_int), ("tol", C.c_double),
                 ("max_depth", C.c_int)]
+
+
+class Projector(C.Structure):
+    """pufe_projector: Gaussian projector centre, (l, m) and width."""
+    _fields_ = [("tau", C.c_double * 3), ("l", C.c_int), ("m", C.c_int), ("r_p", C.c_double)]
 
 
 class ScfInfo(C.Structure):
@@ -104,6 +109,7 @@ def load_library(build_if_missing: bool = True):
                                   C.c_double, C.c_int, C.c_int, vp, vp, vp, vp, dp,
                                   C.POINTER(ScfInfo), vp]
     lib.pufe_scf_reset.argtypes = [vp]
+    lib.pufe_nonlocal_projections.argtypes = [vp, C.c_int, C.POINTER(Projector), vp, vp]
     lib.pufe_assemble_HS_bloch.argtypes = [vp, dp, vp, C.c_int, vp, vp, vp, vp, vp]
     lib.pufe_density_bloch.argtypes = [vp, dp, vp, vp, C.c_int64, vp, C.c_int, vp, vp]
     lib.pufe_assemble_HV_adjoint_bloch.argtypes = [vp, dp, vp, vp, vp, vp]
@@ -279,6 +285,17 @@ class Context:
         _check(_LIB.pufe_assemble_HV_adjoint_bloch(self._h, kk, _ptr(Hbar_re, f64),
                                                    _ptr(Hbar_im, f64), _ptr(Vbar, f64),
                                                    _stream(stream)))
+
+    def pufe_nonlocal_projections(self, projs, F, stream=None):
+        """F (N x P device tensor) <- projections onto projs: list of
+        dict(tau, l, m, rp)."""
+        import torch
+        arr = (Projector * len(projs))()
+        for i, p in enumerate(projs):
+            arr[i].tau = (C.c_double * 3)(*[float(t) for t in p["tau"]])
+            arr[i].l, arr[i].m, arr[i].r_p = int(p["l"]), int(p["m"]), float(p["rp"])
+        _check(_LIB.pufe_nonlocal_projections(self._h, len(projs), arr, _ptr(F, torch.float64),
+                                              _stream(stream)))
 
     def pufe_scf_reset(self):
         _check(_LIB.pufe_scf_reset(self._h))
