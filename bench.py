@@ -174,6 +174,34 @@ def bloch_timing(ctx, wl, V, dev, reps=3):
     return statistics.median(ts)
 
 
+def projection_timing(ctx, wl, dev, reps=3):
+    """Time of the projections onto s + p Gaussian projectors (r_p = 0.8) on
+    every atom of the workload (FP64, Gamma point)."""
+    import torch
+
+    from paper_1611_00731_gb300 import pufe
+
+    ctx.pufe_tabulate(pufe.PUFE_FP64)
+    ps = []
+    for _, tau in wl["atoms"]:
+        ps.append(dict(tau=tau, l=0, m=0, rp=0.8))
+        ps += [dict(tau=tau, l=1, m=m, rp=0.8) for m in (-1, 0, 1)]
+    F = torch.empty(ctx.n_dof, len(ps), dtype=torch.float64, device=dev)
+    ctx.pufe_nonlocal_projections(ps, F)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        ctx.pufe_nonlocal_projections(ps, F)
+        b.record()
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    ctx.pufe_sync_status()
+    return {"projections_ms": statistics.median(ts), "projectors": len(ps), "prec": "fp64"}
+
+
 def run_pufe(args):
     import numpy as np
     import torch
@@ -307,6 +335,7 @@ def run_pufe(args):
     scf = scf_timing(ctx, wl, prec, dev) if args.scf else None
     bloch = ({"assemble_HS_ms": bloch_timing(ctx, wl, V, dev), "prec": "fp64",
               "k": "(1/4, 1/4, 1/4) 2 pi / a"} if args.scf else None)
+    nonlocal_ = projection_timing(ctx, wl, dev) if args.scf else None
 
     if ws > 1:
         import torch.distributed as dist
@@ -369,6 +398,7 @@ def run_pufe(args):
         "gpu_launches": launches_per_step * args.steps,
         "scf": scf,
         "bloch": bloch,
+        "nonlocal": nonlocal_,
         "clocks": clocks,
     }
     if not args.no_cpu_baseline:
@@ -459,7 +489,7 @@ def main():
     ap.add_argument("--impl", default="pufe", choices=["pufe", "reference"])
     ap.add_argument("--prec", default="tf32x3", choices=["tf32x3", "fp64"])
     ap.add_argument("--no-scf", dest="scf", action="store_false",
-                    help="skip the timing of the SCF and Bloch calls")
+                    help="skip the timing of the SCF, Bloch and projector calls")
     ap.add_argument("--density-stream", default="side", choices=["same", "side"],
                     help="run the density on the step's stream or concurrently on a second one")
     ap.add_argument("--launch", default="stream", choices=["graph", "stream"],

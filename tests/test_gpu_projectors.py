@@ -41,3 +41,40 @@ def test_projections_match_oracle(name):
     ctx.pufe_sync_status()
     Fg = F.cpu().numpy()
     assert np.abs(Fg - Fo).max() < 1e-12 * np.abs(Fo).max(), name
+
+
+def test_nonlocal_term_in_the_eigenproblem():
+    """C1 with a separable nonlocal term: eigenvalues of H + F h F^T (GPU H
+    and F) against the oracle's, and the term shifts the spectrum."""
+    import scipy.linalg as sla
+    import scipy.sparse as sp
+
+    from oracle import assemble as oasm
+    wl = W.workload("c1_two_atom_4cube")
+    m = omesh.Mesh(wl)
+    rules = oq.all_rules(m)
+    ctx = pufe.pufe_build_mesh(wl)
+    ctx.pufe_tabulate(pufe.PUFE_FP64)
+    dev = torch.device("cuda:0")
+    V = W.random_potential(len(rules[1]), seed=31)
+    H = torch.empty(ctx.nnz, dtype=torch.float64, device=dev)
+    S = torch.empty_like(H)
+    ctx.pufe_assemble_HS(torch.tensor(V, device=dev), H, S)
+    ps = _projs(wl)[:8]
+    F = torch.empty(ctx.n_dof, len(ps), dtype=torch.float64, device=dev)
+    ctx.pufe_nonlocal_projections(ps, F)
+    ctx.pufe_sync_status()
+    h = np.linspace(0.5, 1.5, len(ps))
+    rowptr, col = ctx.pattern()
+    N = ctx.n_dof
+    Hg = sp.csr_matrix((H.cpu().numpy(), col, rowptr), shape=(N, N)).toarray()
+    Sg = sp.csr_matrix((S.cpu().numpy(), col, rowptr), shape=(N, N)).toarray()
+    Fg = F.cpu().numpy()
+    wg = sla.eigh(Hg + Fg @ np.diag(h) @ Fg.T, Sg, eigvals_only=True, subset_by_index=[0, 5])
+    Ho, So = oasm.assemble_HS(m, rules, V)
+    Fo = onl.projections(m, rules, ps)
+    wo = sla.eigh(Ho.toarray() + Fo @ np.diag(h) @ Fo.T, So.toarray(), eigvals_only=True,
+                  subset_by_index=[0, 5])
+    w0 = sla.eigh(Ho.toarray(), So.toarray(), eigvals_only=True, subset_by_index=[0, 5])
+    assert np.abs(wg - wo).max() < 1e-10
+    assert np.all(wo >= w0 - 1e-12) and (wo - w0).max() > 1e-3   # h > 0 raises the levels
