@@ -127,6 +127,7 @@ struct pufe_ctx {
   int max_part_p = 0;         // largest points-per-axis of any (sub)cell
   int strip_stage = 0;        // floats of the strip kernel's shared-memory stage
   uint32_t strip_pmask = 0;   // per-axis counts (bit p) of the strip kernel's cells
+  int strip_npair_max = 0;    // most enrichment pairs A (A + 1) / 2 of a strip element, A <= 8
   bool on_device = false;   // device copies exist (a CUDA device was present)
   // host copies kept for getters
   std::vector<int64_t> qoff, rowptr, doff;

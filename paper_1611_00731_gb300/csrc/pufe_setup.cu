@@ -663,9 +663,11 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
   // n_e <= 128, capped at 10240 floats (larger cells read global memory)
   ctx->strip_stage = 0;
   ctx->strip_pmask = 0;
+  ctx->strip_npair_max = 0;
   for (int64_t e = 0; e < nelem; ++e) {
     if (n_e[e] <= 64 || n_e[e] > 128) continue;
     const int A = (int)ealpha[e].size();
+    if (A <= 8) ctx->strip_npair_max = std::max(ctx->strip_npair_max, A * (A + 1) / 2);
     for (int32_t j = partoff[e]; j < partoff[e + 1]; ++j) {
       if (part_p[j] < 32) ctx->strip_pmask |= 1u << part_p[j];
       const int p3 = part_p[j] * part_p[j] * part_p[j];

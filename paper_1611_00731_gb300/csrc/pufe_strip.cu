@@ -18,10 +18,30 @@
 //   x: H_abc = sum (L'_a X_bc + L_a W_bc),     S_abc = sum L_a S_bc
 // against 5 * 64 p^3 for the direct product.
 //
-// E x E block: a small dense product over the element's points, symmetric in
-// (r, s), so only 4 x 4 tiles with r-block <= s-block are formed:
+// E x E block, direct form: a small dense product over the element's points,
+// symmetric in (r, s), so only 4 x 4 tiles with r-block <= s-block are formed:
 //   H_rs = sum_q [sum_d y_dr y_ds + V_q z_r z_s],  S_rs = sum_q z_r z_s,
 //   y_dr = sqrt(w/2) d b_r / d x_d,  z_r = sqrt(w) b_r.
+//
+// E x E block, enrichment-pair form: for r = (v, alpha), s = (v', beta) the
+// PU factors are trilinear, phi_v = 1/8 prod_d (1 + s_d x_d) with s_d = +-1,
+// so along each axis phi_v phi_v' is one of u_0 = (1-x)^2, u_1 = 1 - x^2,
+// u_2 = (1+x)^2 (index b_d + b'_d, b = (s + 1) / 2), d phi_v / dx_d is a
+// constant and phi_v' is one of l_0 = 1 - x, l_1 = 1 + x.  Expanding
+// grad b_r . grad b_s, every entry of the pair's 64 vertex pairs is a signed
+// sum of projections of eight per-point fields of (alpha, beta) alone,
+//   A = w Psi_a Psi_b,  E = w (V Psi_a Psi_b + 1/2 grad Psi_a . grad Psi_b),
+//   B_d = w Psi_b d_d Psi_a,  C_d = w Psi_a d_d Psi_b,
+// onto tensor products of {u_k, 1, l_t}:
+//   64 S_rs = <A, u u u>,
+//   64 H_rs = <E, u u u> + 1/2 sum_d (2/h_d)^2 s_d s'_d <A, u u with 1 on d>
+//           + 1/2 sum_d (2/h_d) (s_d <C_d, u u with l_b'd on d>
+//                                + s'_d <B_d, u u with l_bd on d>).
+// The 189 projections of a pair are contracted axis by axis (z: 23 per
+// column, y: 66 per line, x: 189), about 56 p^3 + 200 p^2 operations against
+// 5 x 64 p^3 for the direct products of the pair's vertex pairs.  An element
+// takes this form when its enrichments have at most 8 slots and the form's
+// operation count is below the direct one.
 //
 // Every product is an FP32 fused multiply-add with round to nearest; the
 // element block is added into the FP64 CSR values with atomics (both
@@ -81,10 +101,45 @@ struct StripElem {
   float *stage, *work, *HE, *SE, *L1, *D1;
   const int *ecs;
   int pm, wfloats;
-  // E x E tile of this thread
+  // E x E tile of this thread (direct form)
   int rb, sb, pg, PG;
   bool act;
+  // enrichment-pair form: pair list (alpha | beta << 8), projections
+  // [pair][189] and the 1D factors [axis][u_0, u_1, u_2, 1, l_0, l_1][pm]
+  bool sp;
+  int npair;
+  const int *pairs;
+  float *PE;
+  const float *F1;
 };
+
+// Row groups of the enrichment-pair contraction.  z-stage outputs (rows a):
+// 0-2 A u_k, 3 A, 4-6 E u_k, 7-9 B_x u_k, 10-12 C_x u_k, 13-15 B_y u_k,
+// 16-18 C_y u_k, 19-20 B_z l_t, 21-22 C_z l_t.  Factor index f: 0-2 u_k,
+// 3 the constant, 4-5 l_t.  Row a of the z stage feeds y outputs j0 .. j0+n-1
+// with factors f0 .. f0+n-1, and rows 0-2 also feed j = 9 + a with f = 3:
+//   y outputs 0-8 A(u,u), 9-11 A(u,1), 12-14 A(1,u), 15-23 E(u,u),
+//   24-32 B_x(u,u), 33-41 C_x(u,u), 42-47 B_y(u,l), 48-53 C_y(u,l),
+//   54-59 B_z(l,u), 60-65 C_z(l,u)    (z factor first).
+__device__ __forceinline__ void sp_yrow(int a, int &j0, int &f0, int &n) {
+  if (a < 3) { j0 = 3 * a; f0 = 0; n = 3; }
+  else if (a == 3) { j0 = 12; f0 = 0; n = 3; }
+  else if (a < 13) { j0 = 15 + 3 * (a - 4); f0 = 0; n = 3; }
+  else if (a < 19) { j0 = 42 + 2 * (a - 13); f0 = 4; n = 2; }
+  else { j0 = 54 + 3 * (a - 19); f0 = 0; n = 3; }
+}
+
+// Row j of the y stage feeds projections i0 .. i0+n-1 with x factors
+// f0 .. f0+n-1, and rows 0-8 also feed i = 27 + j with f = 3; projections:
+//   0-26 <A,u u u> (z,y,x), 27-35 <A,u u 1>, 36-44 <A,u 1 u>, 45-53 <A,1 u u>,
+//   54-80 <E,u u u>, 81-98 <B_x,u u l>, 99-116 <C_x,u u l>,
+//   117-134 <B_y,u l u>, 135-152 <C_y,u l u>, 153-170 <B_z,l u u>, 171-188 <C_z,l u u>
+__device__ __forceinline__ void sp_xrow(int j, int &i0, int &f0, int &n) {
+  if (j < 9) { i0 = 3 * j; f0 = 0; n = 3; }
+  else if (j < 24) { i0 = 36 + 3 * (j - 9); f0 = 0; n = 3; }
+  else if (j < 42) { i0 = 81 + 2 * (j - 24); f0 = 4; n = 2; }
+  else { i0 = 117 + 3 * (j - 42); f0 = 0; n = 3; }
+}
 
 // one (sub)cell of p^3 points starting at element point qs; STAGED: its Psi
 // rows ([slot][comp][point], pitch P), points and V are in shared memory
@@ -209,6 +264,115 @@ __device__ __forceinline__ void strip_part(const StripElem &E, double *__restric
     }
   }
 
+  // ---- E x E block, enrichment-pair form -------------------------------------
+  if (E.sp) {
+    const int per = 24 * p2 + 66 * p;            // work floats of one pair
+    const int fit = max(1, E.wfloats / per);     // the caller checked per <= wfloats
+    const int nch = (E.npair + fit - 1) / fit;
+    const int npc = (E.npair + nch - 1) / nch;   // pairs per chunk, balanced
+    const float *Fy = E.F1 + 6 * pm, *Fx = E.F1;
+    const FastDiv dp23(p * 23), d23(23), d66(66);
+    for (int c0 = 0; c0 < E.npair; c0 += npc) {
+      const int nc = min(npc, E.npair - c0);
+      float *T1 = E.work;                        // [nc][p^2][24]: z outputs, pad
+      float *T2 = E.work + nc * p2 * 24;         // [nc][p][66]: y outputs
+      __syncthreads();
+      // z: one thread per (pair, qx, qy) column
+      for (int it = tid; it < nc * p2; it += ST_NT) {
+        const int g = dp2.div(it), qxy = it - g * p2;
+        const int pr = E.pairs[c0 + g], al = pr & 0xff, be = pr >> 8;
+        float o[24];
+#pragma unroll
+        for (int u = 0; u < 24; ++u) o[u] = 0.0f;
+        for (int qz = 0; qz < p; ++qz) {
+          const int lq = qxy + p2 * qz;
+          const float4 x4 = xval(lq);
+          const float vq = vval(lq);
+          const float a0 = psv(lq, al, 0), a1 = psv(lq, al, 1), a2 = psv(lq, al, 2),
+                      a3 = psv(lq, al, 3);
+          const float b0 = psv(lq, be, 0), b1 = psv(lq, be, 1), b2 = psv(lq, be, 2),
+                      b3 = psv(lq, be, 3);
+          const float wa = x4.w * a0, wb = x4.w * b0;
+          const float fA = wa * b0;
+          const float fE = fmaf(vq, fA, 0.5f * x4.w * fmaf(a1, b1, fmaf(a2, b2, a3 * b3)));
+          const float l0 = 1.0f - x4.z, l1 = 1.0f + x4.z;
+          const float u0 = l0 * l0, u1 = l0 * l1, u2 = l1 * l1;
+          const float f3[4] = {wb * a1, wa * b1, wb * a2, wa * b2};   // B_x C_x B_y C_y
+          o[0] = fmaf(fA, u0, o[0]);
+          o[1] = fmaf(fA, u1, o[1]);
+          o[2] = fmaf(fA, u2, o[2]);
+          o[3] += fA;
+          o[4] = fmaf(fE, u0, o[4]);
+          o[5] = fmaf(fE, u1, o[5]);
+          o[6] = fmaf(fE, u2, o[6]);
+#pragma unroll
+          for (int f = 0; f < 4; ++f) {
+            o[7 + 3 * f] = fmaf(f3[f], u0, o[7 + 3 * f]);
+            o[8 + 3 * f] = fmaf(f3[f], u1, o[8 + 3 * f]);
+            o[9 + 3 * f] = fmaf(f3[f], u2, o[9 + 3 * f]);
+          }
+          const float Bz = wb * a3, Cz = wa * b3;
+          o[19] = fmaf(Bz, l0, o[19]);
+          o[20] = fmaf(Bz, l1, o[20]);
+          o[21] = fmaf(Cz, l0, o[21]);
+          o[22] = fmaf(Cz, l1, o[22]);
+        }
+        float4 *t1 = reinterpret_cast<float4 *>(T1 + (size_t)it * 24);
+#pragma unroll
+        for (int u = 0; u < 6; ++u) t1[u] = make_float4(o[4 * u], o[4 * u + 1], o[4 * u + 2], o[4 * u + 3]);
+      }
+      __syncthreads();
+      // y: one thread per (pair, qx, z row); 2-4 outputs each
+      for (int it = tid; it < nc * p * 23; it += ST_NT) {
+        const int g = dp23.div(it), rem = it - g * p * 23;
+        const int qx = d23.div(rem), a = rem - qx * 23;
+        int j0, f0, n;
+        sp_yrow(a, j0, f0, n);
+        const float *t1 = T1 + ((size_t)g * p2 + qx) * 24 + a;
+        const float *fy0 = Fy + f0 * pm, *fy1 = fy0 + pm, *fy2 = Fy + min(f0 + 2, 5) * pm,
+                    *fy3 = Fy + 3 * pm;
+        float c0v = 0.0f, c1v = 0.0f, c2v = 0.0f, c3v = 0.0f;
+        for (int qy = 0; qy < p; ++qy) {
+          const float t = t1[qy * p * 24];
+          c0v = fmaf(fy0[qy], t, c0v);
+          c1v = fmaf(fy1[qy], t, c1v);
+          c2v = fmaf(fy2[qy], t, c2v);
+          c3v = fmaf(fy3[qy], t, c3v);
+        }
+        float *t2 = T2 + (g * p + qx) * 66;
+        t2[j0] = c0v;
+        t2[j0 + 1] = c1v;
+        if (n > 2) t2[j0 + 2] = c2v;
+        if (a < 3) t2[9 + a] = c3v;
+      }
+      __syncthreads();
+      // x: one thread per (pair, y row); 2-4 projections each, the (sub)cells
+      // of the element add up
+      for (int it = tid; it < nc * 66; it += ST_NT) {
+        const int g = d66.div(it), j = it - g * 66;
+        int i0, f0, n;
+        sp_xrow(j, i0, f0, n);
+        const float *t2 = T2 + (size_t)g * p * 66 + j;
+        const float *fx0 = Fx + f0 * pm, *fx1 = fx0 + pm, *fx2 = Fx + min(f0 + 2, 5) * pm,
+                    *fx3 = Fx + 3 * pm;
+        float c0v = 0.0f, c1v = 0.0f, c2v = 0.0f, c3v = 0.0f;
+        for (int qx = 0; qx < p; ++qx) {
+          const float t = t2[qx * 66];
+          c0v = fmaf(fx0[qx], t, c0v);
+          c1v = fmaf(fx1[qx], t, c1v);
+          c2v = fmaf(fx2[qx], t, c2v);
+          c3v = fmaf(fx3[qx], t, c3v);
+        }
+        float *pe = E.PE + (c0 + g) * 189;
+        pe[i0] += c0v;
+        pe[i0 + 1] += c1v;
+        if (n > 2) pe[i0 + 2] += c2v;
+        if (j < 9) pe[27 + j] += c3v;
+      }
+    }
+    return;
+  }
+
   // ---- E x E block over this (sub)cell's points --------------------------------
   float h16[16], s16[16];
 #pragma unroll
@@ -295,7 +459,8 @@ __global__ void __launch_bounds__(ST_NT, 2) k_strip_sf(
     const int32_t *__restrict__ aoff, const int64_t *__restrict__ toff32,
     const float *__restrict__ psi, const int64_t *__restrict__ soff,
     const int32_t *__restrict__ smap, float sx, float sy, float sz, int pm, int wfloats,
-    int sfloats, int what, double *__restrict__ H, double *__restrict__ S, unsigned *err) {
+    int sfloats, int eefloats, int what, double *__restrict__ H, double *__restrict__ S,
+    unsigned *err) {
   extern __shared__ float4 sm_st4[];
   const int e = order[blockIdx.x], tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   StripElem E;
@@ -323,18 +488,53 @@ __global__ void __launch_bounds__(ST_NT, 2) k_strip_sf(
   E.pm = pm;
   E.wfloats = wfloats;
 
-  // shared memory: [stage: sfloats][work: wfloats][HE, SE: ne8^2 each]
-  //                [L1, D1: 12 pm each][ecs: ne]
+  // shared memory: [stage: sfloats][work: wfloats][E x E: eefloats]
+  //                [L1, D1: 12 pm each][F1: 18 pm][ecs: 64 ints][pairs: 36 ints]
+  // E x E area: HE, SE ([ne8][ne8] each, entries r <= s; direct form) or
+  // the pair projections [npair][189] (enrichment-pair form)
   E.stage = reinterpret_cast<float *>(sm_st4);
   E.work = E.stage + sfloats;
-  E.HE = E.work + wfloats;   // [ne8][ne8], entries r <= s
+  E.HE = E.work + wfloats;
   E.SE = E.HE + ne8 * ne8;
-  E.L1 = E.SE + ne8 * ne8;   // [3][4][pm]
+  E.PE = E.HE;
+  E.L1 = E.HE + eefloats;    // [3][4][pm]
   E.D1 = E.L1 + 12 * pm;     // [3][4][pm]
-  int *ecs = reinterpret_cast<int *>(E.D1 + 12 * pm);
+  float *F1 = E.D1 + 12 * pm;
+  E.F1 = F1;
+  int *ecs = reinterpret_cast<int *>(F1 + 18 * pm);
+  int *pairs = ecs + 64;
   E.ecs = ecs;
+  E.pairs = pairs;
   if (tid < ne) ecs[tid] = ecol[(doff[e] - 64ll * e) + tid];
-  for (int o = tid; o < 2 * ne8 * ne8; o += ST_NT) E.HE[o] = 0.0f;
+
+  // E x E form: the pair form when the element has at most 8 slots, its
+  // projections fit the E x E area, every (sub)cell's pair work fits the work
+  // area, and its estimated operation count (per pair and point: ~56 in z,
+  // ~200 / p in y, ~570 / p^2 in x) is below the direct one (~100 per 4 x 4
+  // tile and point, plus ~35 per column and point for the chunk tables)
+  {
+    const int A = E.A, npair = A * (A + 1) / 2;
+    bool sp = A <= 8 && npair * 189 <= eefloats;
+    for (int k = partoff[e]; k < partoff[e + 1] && sp; ++k) {
+      const int p = part_p[k];
+      sp = 24 * p * p + 66 * p <= wfloats;
+    }
+    if (sp) {
+      const int p = part_p[partoff[e]];
+      const int nb = ne8 >> 2;
+      const long long cost_sp = (long long)npair * (56 * p * p * p + 200 * p * p + 570 * p + 2835);
+      const long long cost_dir = (long long)(nb * (nb + 1) / 2 * 100 + 35 * ne8) * p * p * p;
+      sp = cost_sp < cost_dir;
+    }
+    E.sp = sp;
+    E.npair = sp ? npair : 0;
+    if (sp && tid < A) {
+      int k = tid * A - tid * (tid - 1) / 2;   // pairs (alpha, beta), alpha <= beta, alpha-major
+      for (int b = tid; b < A; ++b) pairs[k++] = tid | (b << 8);
+    }
+  }
+  const int ee_zero = E.sp ? E.npair * 189 : 2 * ne8 * ne8;
+  for (int o = tid; o < ee_zero; o += ST_NT) E.HE[o] = 0.0f;
 
   // E x E tiles: 4 x 4 blocks (rb <= sb), one per lane; WG warps cover the
   // tiles, the PG = 8 / WG warp groups split the points, so the lanes of a
@@ -392,13 +592,22 @@ __global__ void __launch_bounds__(ST_NT, 2) k_strip_sf(
       const int d = o / p, t = o - d * p;
       const int stride = d == 0 ? 1 : (d == 1 ? p : p2);
       const float4 x4 = E.qe[qs + t * stride];
+      const float xd = d == 0 ? x4.x : (d == 1 ? x4.y : x4.z);
       float L[4], dL[4];
-      lag3vd(d == 0 ? x4.x : (d == 1 ? x4.y : x4.z), L, dL);
+      lag3vd(xd, L, dL);
 #pragma unroll
       for (int a = 0; a < 4; ++a) {
         E.L1[(d * 4 + a) * pm + t] = L[a];
         E.D1[(d * 4 + a) * pm + t] = dL[a];
       }
+      const float l0 = 1.0f - xd, l1 = 1.0f + xd;
+      float *f1 = F1 + d * 6 * pm + t;
+      f1[0] = l0 * l0;
+      f1[pm] = l0 * l1;
+      f1[2 * pm] = l1 * l1;
+      f1[3 * pm] = 1.0f;
+      f1[4 * pm] = l0;
+      f1[5 * pm] = l1;
     }
     if (staged)
       strip_part<true>(E, H, S);
@@ -408,6 +617,41 @@ __global__ void __launch_bounds__(ST_NT, 2) k_strip_sf(
   __syncthreads();
   // ---- E x E into the FP64 CSR values, both triangles ---------------------------
   const FastDiv dne(ne);
+  if (E.sp) {   // entries from the pair projections (slot of r <= slot of s by symmetry)
+    const float hx = 0.5f * sx, hy = 0.5f * sy, hz = 0.5f * sz;
+    const int A = E.A;
+    for (int o = tid; o < ne * ne; o += ST_NT) {
+      const int r = dne.div(o), sc = o - r * ne;
+      int cr = ecs[r], cs = ecs[sc];
+      if ((cr >> 3) > (cs >> 3)) {
+        const int t = cr;
+        cr = cs;
+        cs = t;
+      }
+      const int al = cr >> 3, be = cs >> 3;
+      const float *P = E.PE + (al * A - al * (al - 1) / 2 + (be - al)) * 189;
+      const int bx = cr & 1, by = (cr >> 1) & 1, bz = (cr >> 2) & 1;
+      const int cx = cs & 1, cy = (cs >> 1) & 1, cz = (cs >> 2) & 1;
+      const float px = bx ? 1.0f : -1.0f, py = by ? 1.0f : -1.0f, pz = bz ? 1.0f : -1.0f;
+      const float qx = cx ? 1.0f : -1.0f, qy = cy ? 1.0f : -1.0f, qz = cz ? 1.0f : -1.0f;
+      const int kx = bx + cx, ky = by + cy, kz = bz + cz;
+      const int kzy = kz * 3 + ky;
+      float h = P[54 + kzy * 3 + kx];
+      h = fmaf(hx * sx * px * qx, P[27 + kzy], h);
+      h = fmaf(hy * sy * py * qy, P[36 + kz * 3 + kx], h);
+      h = fmaf(hz * sz * pz * qz, P[45 + ky * 3 + kx], h);
+      h = fmaf(hx * px, P[99 + kzy * 2 + cx], h);
+      h = fmaf(hx * qx, P[81 + kzy * 2 + bx], h);
+      h = fmaf(hy * py, P[135 + (kz * 2 + cy) * 3 + kx], h);
+      h = fmaf(hy * qy, P[117 + (kz * 2 + by) * 3 + kx], h);
+      h = fmaf(hz * pz, P[171 + (cz * 3 + ky) * 3 + kx], h);
+      h = fmaf(hz * qz, P[153 + (bz * 3 + ky) * 3 + kx], h);
+      const int slot = E.m[(64 + r) * E.n + 64 + sc];
+      if (E.wantH) atomicAdd(H + slot, (double)(h * (1.0f / 64.0f)));
+      if (E.wantS) atomicAdd(S + slot, (double)(P[kzy * 3 + kx] * (1.0f / 64.0f)));
+    }
+    return;
+  }
   for (int o = tid; o < ne * ne; o += ST_NT) {
     const int r = dne.div(o), sc = o - r * ne;
     const int lo = min(r, sc), hi = max(r, sc);
@@ -446,13 +690,14 @@ pufe_status launch_strip_sf(pufe_ctx *ctx, const double *V, int what, double *H,
   const int pm = std::max(1, ctx->max_part_p);
   const int wf = strip_work_floats(ctx->strip_pmask, ne8);
   const int sf = (sneed + 3) & ~3;
-  const size_t sm = ((size_t)sf + wf + 2 * ne8 * ne8 + 24 * pm + ne8) * sizeof(float);
+  const int ee = std::max(2 * ne8 * ne8, 189 * ctx->strip_npair_max);
+  const size_t sm = ((size_t)sf + wf + ee + 42 * pm + 64 + 36) * sizeof(float);
   if (sm > 227 * 1024) return fail(PUFE_EINVAL, "strip kernel: shared memory above 227 KB");
   PUFE_CUDA_TRY(cudaFuncSetAttribute(k_strip_sf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
   k_strip_sf<<<(unsigned)count, ST_NT, sm, st>>>(
       D.order + first, D.qoff, D.qpoff, D.qdat, V, D.partoff, D.part_p, D.part_q, D.doff, D.ecol,
       D.aoff, D.toff32, D.psi32, D.soff, D.smap, (float)(2.0 / ctx->h[0]),
-      (float)(2.0 / ctx->h[1]), (float)(2.0 / ctx->h[2]), pm, wf, sf, what, H, S, D.err);
+      (float)(2.0 / ctx->h[1]), (float)(2.0 / ctx->h[2]), pm, wf, sf, ee, what, H, S, D.err);
   PUFE_CUDA_TRY(cudaGetLastError());
   return PUFE_OK;
 }
