@@ -128,6 +128,8 @@ struct pufe_ctx {
   int strip_stage = 0;        // floats of the strip kernel's shared-memory stage
   uint32_t strip_pmask = 0;   // per-axis counts (bit p) of the strip kernel's cells
   int strip_npair_max = 0;    // most enrichment pairs A (A + 1) / 2 of a strip element, A <= 8
+  int adj_sf_floats = 0;      // shared floats of the slot-form adjoint strip's coefficients and Psi
+  bool adj_sf_all = true;     // every strip element takes the slot-form adjoint
   bool on_device = false;   // device copies exist (a CUDA device was present)
   // host copies kept for getters
   std::vector<int64_t> qoff, rowptr, doff;
@@ -138,6 +140,10 @@ struct pufe_ctx {
 };
 
 namespace pufe {
+
+// Elements (n_e <= 128) whose enrichment strip of the adjoint runs in the
+// slot form: at most 16 enrichment slots and 10 points per axis per (sub)cell.
+__host__ __device__ inline bool adjoint_sf_fits(int A, int pmax) { return A <= 16 && pmax <= 10; }
 
 // ---------------------------------------------------------------------------
 // basis functions shared by host setup and device kernels
@@ -314,6 +320,8 @@ pufe_status launch_scf_step(pufe_ctx *ctx, int nstates, const double *eps, const
                             double *f_out, pufe_scf_info *info, cudaStream_t s);
 pufe_status launch_adjoint_fefe(pufe_ctx *ctx, const double *Hbar, double *Vbar, int first,
                                 int count, cudaStream_t s);
+pufe_status launch_adjoint_strip_sf(pufe_ctx *ctx, const double *Hbar, double *Vbar, int first,
+                                    int count, cudaStream_t s);
 pufe_status launch_assemble_tc_static(pufe_ctx *ctx, const double *V, int what, double *H,
                                       double *S, cudaStream_t s);
 pufe_status launch_assemble_tc(pufe_ctx *ctx, const double *V, int what, double *H, double *S,

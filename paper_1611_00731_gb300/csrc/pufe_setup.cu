@@ -664,10 +664,19 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
   ctx->strip_stage = 0;
   ctx->strip_pmask = 0;
   ctx->strip_npair_max = 0;
+  ctx->adj_sf_floats = 0;
+  ctx->adj_sf_all = true;
   for (int64_t e = 0; e < nelem; ++e) {
     if (n_e[e] <= 64 || n_e[e] > 128) continue;
     const int A = (int)ealpha[e].size();
     if (A <= 8) ctx->strip_npair_max = std::max(ctx->strip_npair_max, A * (A + 1) / 2);
+    int pmax = 0;
+    for (int32_t j = partoff[e]; j < partoff[e + 1]; ++j) pmax = std::max(pmax, (int)part_p[j]);
+    if (adjoint_sf_fits(A, pmax))
+      ctx->adj_sf_floats = std::max(ctx->adj_sf_floats,
+                                    A * 512 + A * (A + 1) / 2 * 27 + A * pmax * pmax * pmax);
+    else
+      ctx->adj_sf_all = false;
     for (int32_t j = partoff[e]; j < partoff[e + 1]; ++j) {
       if (part_p[j] < 32) ctx->strip_pmask |= 1u << part_p[j];
       const int p3 = part_p[j] * part_p[j] * part_p[j];

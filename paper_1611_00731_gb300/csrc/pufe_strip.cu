@@ -702,5 +702,293 @@ pufe_status launch_strip_sf(pufe_ctx *ctx, const double *V, int what, double *H,
   return PUFE_OK;
 }
 
-}  // namespace pufe
+// ---------------------------------------------------------------------------
+// Enrichment strip of the adjoint of V -> H (mixed path, n_e <= 128).
+//
+// dL/dV_q = w_q b_q^T Hbar_e b_q; the FE-FE form is done by k_adjoint_fefe
+// (which stores Vbar), this kernel adds the enrichment terms
+//   w_q [ sum_{r in E} sum_{j in F} (Hbar_rj + Hbar_jr) b_r phi_j
+//         + sum_{r, s in E} Hbar_rs b_r b_s ].
+// With b_r = phi_v Psi_alpha and trilinear phi_v = 1/8 prod_d (1 + s_d x_d),
+// both sums regroup by enrichment slot, so every point needs only Psi values:
+//   F x E:  sum_alpha Psi_alpha(q) G_alpha(q),
+//           G_alpha = sum K_alpha[c tz][b ty][a tx] m_{c,tz}(z) m_{b,ty}(y) m_{a,tx}(x),
+//           m_{a,t}(x) = L_a(x) (1 -+ x),
+//           K_alpha = (Hbar_rj + Hbar_jr) / 8 for r = (v(tx,ty,tz), alpha), j = a + 4b + 16c;
+//   E x E:  sum_{alpha <= beta} Psi_alpha Psi_beta P_ab(q),
+//           P_ab = sum_k D_ab[kz ky kx] u_kz(z) u_ky(y) u_kx(x),  u_k as in the assembly,
+//           D_ab[k] = 1/64 sum over vertex pairs (v, v') with b_d + b'_d = k_d of
+//                     Hbar_rs (+ Hbar_sr when alpha != beta).
+// G and P are evaluated on each p^3 (sub)cell axis by axis (x, then y, then
+// z at the point): 8 and 3 multiply-adds per point and slot or pair, against
+// 84 per column and point for the direct FE sum.  FP32 with round to nearest.
+// ---------------------------------------------------------------------------
+namespace {
 
+constexpr int AJ_NT = 256;
+constexpr int AJ_W = 4096;   // work floats: x and y stage outputs of one chunk, or the E x E block
+
+__global__ void __launch_bounds__(AJ_NT, 4) k_adjoint_strip_sf(
+    const int32_t *__restrict__ order, const int64_t *__restrict__ qoff,
+    const int64_t *__restrict__ qpoff, const float4 *__restrict__ qdat,
+    const double *__restrict__ w, const int64_t *__restrict__ doff,
+    const int32_t *__restrict__ ecol, const int32_t *__restrict__ aoff,
+    const int64_t *__restrict__ toff32, const float *__restrict__ psi,
+    const int32_t *__restrict__ partoff, const int32_t *__restrict__ part_p,
+    const int32_t *__restrict__ part_q, const int64_t *__restrict__ soff,
+    const int32_t *__restrict__ smap, const double *__restrict__ Hbar, int pm, int cfloats,
+    double *__restrict__ Vbar, unsigned *err) {
+  extern __shared__ float4 sm_aj4[];
+  const int e = order[blockIdx.x], tid = threadIdx.x;
+  const int n = (int)(doff[e + 1] - doff[e]);
+  const int ne = n - 64;
+  if (ne <= 0) return;   // FE-only element: Vbar is already complete
+  const int A = aoff[e + 1] - aoff[e], npair = A * (A + 1) / 2;
+  int p3max = 0, pmax = 0;
+  for (int k = partoff[e]; k < partoff[e + 1]; ++k) {
+    pmax = max(pmax, part_p[k]);
+    p3max = max(p3max, part_p[k] * part_p[k] * part_p[k]);
+  }
+  if (!adjoint_sf_fits(A, pmax)) return;   // left to the direct kernel
+  if (n > 128 || pmax > pm || A * 512 + npair * 27 + A * p3max > cfloats) {
+    if (tid == 0) atomicOr(err, DEVERR_SHAPE);
+    return;
+  }
+  // shared memory: [K: A*512][D: npair*27][Ps: A*p3max][cfloats end]
+  //                [M1: 3*8*pm][U1: 3*3*pm][work: AJ_W][cmap: A*8 ints][pairs: npair ints]
+  float *K = reinterpret_cast<float *>(sm_aj4);
+  float *Dp = K + A * 512;
+  float *Ps = Dp + npair * 27;
+  float *M1 = K + cfloats;
+  float *U1 = M1 + 24 * pm;
+  float *work = U1 + 9 * pm;
+  int *cmap = reinterpret_cast<int *>(work + AJ_W);
+  int *pairs = cmap + A * 8;
+  const int64_t q0 = qoff[e];
+  const int32_t *m = smap + soff[e];
+  const float *pe = psi + 4 * toff32[e];
+  const float4 *qe = qdat + qpoff[e];
+  const int32_t *ec = ecol + (doff[e] - 64ll * e);
+
+  // column of (slot, vertex), -1 where the element has none; pair list
+  for (int o = tid; o < A * 8; o += AJ_NT) cmap[o] = -1;
+  if (tid < A) {
+    int k = tid * A - tid * (tid - 1) / 2;
+    for (int b = tid; b < A; ++b) pairs[k++] = tid | (b << 8);
+  }
+  __syncthreads();
+  if (tid < ne) cmap[ec[tid]] = tid;   // code = slot * 8 + vertex
+  __syncthreads();
+  // coefficients from Hbar.  The CSR values are gathered with eight
+  // independent (map, value) load chains in flight per thread, each half of
+  // K with the lanes of a warp along one CSR row: Hbar_rj (row of enrichment
+  // r, FE columns j) first, then Hbar_jr (row of FE j, enrichment columns r)
+  // added in; the E x E block goes into the work area
+  for (int o = tid; o < A * 512; o += AJ_NT) K[o] = 0.0f;   // absent vertices stay 0
+  __syncthreads();
+  for (int half = 0; half < 2; ++half) {
+    for (int o0 = tid; o0 < ne * 64; o0 += 8 * AJ_NT) {
+      int s1[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int o = o0 + u * AJ_NT;
+        const int r = half ? o % ne : o >> 6, j = half ? o / ne : o & 63;
+        s1[u] = o < ne * 64 ? m[half ? j * n + 64 + r : (64 + r) * n + j] : 0;
+      }
+      double h[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) h[u] = o0 + u * AJ_NT < ne * 64 ? Hbar[s1[u]] : 0.0;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int o = o0 + u * AJ_NT;
+        if (o >= ne * 64) break;
+        const int r = half ? o % ne : o >> 6, j = half ? o / ne : o & 63;
+        const int code = ec[r], v = code & 7;
+        const int atx = 2 * (j & 3) + (v & 1), bty = 2 * ((j >> 2) & 3) + ((v >> 1) & 1),
+                  ctz = 2 * (j >> 4) + (v >> 2);
+        float *kk = K + (code >> 3) * 512 + ctz * 64 + bty * 8 + atx;
+        *kk = half ? *kk + (float)(0.125 * h[u]) : (float)(0.125 * h[u]);
+      }
+    }
+    __syncthreads();
+  }
+  float *HE = work;   // [ne][ne]: Hbar_rs, r, s in E
+  for (int o0 = tid; o0 < ne * ne; o0 += 8 * AJ_NT) {
+    int s1[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int o = o0 + u * AJ_NT, r = o / ne, sc = o - r * ne;
+      s1[u] = o < ne * ne ? m[(64 + r) * n + 64 + sc] : 0;
+    }
+    double h[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) h[u] = o0 + u * AJ_NT < ne * ne ? Hbar[s1[u]] : 0.0;
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (o0 + u * AJ_NT < ne * ne) HE[o0 + u * AJ_NT] = (float)h[u];
+  }
+  __syncthreads();
+  for (int o = tid; o < npair * 27; o += AJ_NT) {
+    const int pi = o / 27, k = o - pi * 27;
+    const int al = pairs[pi] & 0xff, be = pairs[pi] >> 8;
+    const int kd[3] = {k % 3, (k / 3) % 3, k / 9};   // x, y, z
+    float sum = 0.0f;
+    for (int v = 0; v < 8; ++v) {
+      int v2 = 0;
+      bool ok = true;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const int b2 = kd[d] - ((v >> d) & 1);
+        ok = ok && (b2 == 0 || b2 == 1);
+        v2 |= (b2 & 1) << d;
+      }
+      if (!ok) continue;
+      const int r = cmap[al * 8 + v], sc = cmap[be * 8 + v2];
+      if (r < 0 || sc < 0) continue;
+      sum += HE[r * ne + sc];
+      if (al != be) sum += HE[sc * ne + r];
+    }
+    Dp[o] = sum * (1.0f / 64.0f);
+  }
+
+  const int nsc_w = AJ_W;
+  for (int kp = partoff[e]; kp < partoff[e + 1]; ++kp) {
+    const int p = part_p[kp], p2 = p * p, p3 = p2 * p, qs = part_q[kp];
+    const FastDiv dp(p), dp2(p2);
+    __syncthreads();   // coefficients ready; previous part's readers done
+    // Psi values of the (sub)cell's points and the 1D factors per axis
+    for (int o = tid; o < A * p3; o += AJ_NT) {
+      const int al = o / p3, lq = o - al * p3, ql = qs + lq;
+      Ps[o] = pe[((int64_t)(ql >> 3) * A + al) * 32 + (ql & 7)];
+    }
+    for (int o = tid; o < 3 * p; o += AJ_NT) {
+      const int d = o / p, t = o - d * p;
+      const int stride = d == 0 ? 1 : (d == 1 ? p : p2);
+      const float4 x4 = qe[qs + t * stride];
+      const float xd = d == 0 ? x4.x : (d == 1 ? x4.y : x4.z);
+      const float a = xd + 1.0f, b = xd + (1.0f / 3.0f), c = xd - (1.0f / 3.0f), dd = xd - 1.0f;
+      const float L[4] = {-0.5625f * b * c * dd, 1.6875f * a * c * dd, -1.6875f * a * b * dd,
+                          0.5625f * a * b * c};
+      const float l0 = 1.0f - xd, l1 = 1.0f + xd;
+#pragma unroll
+      for (int aa = 0; aa < 4; ++aa) {
+        M1[(d * 8 + 2 * aa) * pm + t] = L[aa] * l0;
+        M1[(d * 8 + 2 * aa + 1) * pm + t] = L[aa] * l1;
+      }
+      U1[(d * 3 + 0) * pm + t] = l0 * l0;
+      U1[(d * 3 + 1) * pm + t] = l0 * l1;
+      U1[(d * 3 + 2) * pm + t] = l1 * l1;
+    }
+    float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};   // points tid + 256 k (p^3 <= 1024)
+
+    // ---- F x E: slots in chunks ------------------------------------------------
+    const int per_s = 64 * p + 8 * p2;
+    const int nsc = max(1, nsc_w / per_s);
+    for (int s0 = 0; s0 < A; s0 += nsc) {
+      const int nc = min(nsc, A - s0);
+      float *X = work;                 // [nc][64][p]: (c tz, b ty) rows at x points
+      float *Y = work + nc * 64 * p;   // [nc][8][p^2]: c tz rows at (x, y) points
+      __syncthreads();
+      for (int it = tid; it < nc * 64 * p; it += AJ_NT) {
+        const int row = dp.div(it), qx = it - row * p;   // row = g * 64 + (c tz) * 8 + (b ty)
+        const float *k8 = K + (s0 * 64 + row) * 8;
+        float sum = 0.0f;
+#pragma unroll
+        for (int t = 0; t < 8; ++t) sum = fmaf(k8[t], M1[t * pm + qx], sum);
+        X[it] = sum;
+      }
+      __syncthreads();
+      for (int it = tid; it < nc * 8 * p2; it += AJ_NT) {
+        const int row = dp2.div(it), qxy = it - row * p2;   // row = g * 8 + (c tz)
+        const int qy = dp.div(qxy), qx = qxy - qy * p;
+        const float *x8 = X + row * 8 * p + qx;
+        float sum = 0.0f;
+#pragma unroll
+        for (int t = 0; t < 8; ++t) sum = fmaf(x8[t * p], M1[(8 + t) * pm + qy], sum);
+        Y[it] = sum;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int lq = tid + AJ_NT * k;
+        if (lq >= p3) break;
+        const int qz = lq / p2, qxy = lq - qz * p2;
+        float a = acc[k];
+        for (int g = 0; g < nc; ++g) {
+          const float *y8 = Y + g * 8 * p2 + qxy;
+          float gs = 0.0f;
+#pragma unroll
+          for (int t = 0; t < 8; ++t) gs = fmaf(y8[t * p2], M1[(16 + t) * pm + qz], gs);
+          a = fmaf(Ps[(s0 + g) * p3 + lq], gs, a);
+        }
+        acc[k] = a;
+      }
+    }
+
+    // ---- E x E: slot pairs in chunks ----------------------------------------------
+    const int per_p = 9 * p + 3 * p2;
+    const int npc = max(1, nsc_w / per_p);
+    for (int c0 = 0; c0 < npair; c0 += npc) {
+      const int nc = min(npc, npair - c0);
+      float *X = work;                // [nc][9][p]: (kz ky) rows at x points
+      float *Y = work + nc * 9 * p;   // [nc][3][p^2]: kz rows at (x, y) points
+      __syncthreads();
+      for (int it = tid; it < nc * 9 * p; it += AJ_NT) {
+        const int row = dp.div(it), qx = it - row * p;   // row = g * 9 + kz * 3 + ky
+        const float *d3 = Dp + (c0 * 9 + row) * 3;
+        X[it] = fmaf(d3[0], U1[qx], fmaf(d3[1], U1[pm + qx], d3[2] * U1[2 * pm + qx]));
+      }
+      __syncthreads();
+      for (int it = tid; it < nc * 3 * p2; it += AJ_NT) {
+        const int row = dp2.div(it), qxy = it - row * p2;   // row = g * 3 + kz
+        const int qy = dp.div(qxy), qx = qxy - qy * p;
+        const float *x3 = X + row * 3 * p + qx;
+        Y[it] = fmaf(x3[0], U1[3 * pm + qy], fmaf(x3[p], U1[4 * pm + qy], x3[2 * p] * U1[5 * pm + qy]));
+      }
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int lq = tid + AJ_NT * k;
+        if (lq >= p3) break;
+        const int qz = lq / p2, qxy = lq - qz * p2;
+        const float uz0 = U1[6 * pm + qz], uz1 = U1[7 * pm + qz], uz2 = U1[8 * pm + qz];
+        float a = acc[k];
+        for (int g = 0; g < nc; ++g) {
+          const float *y3 = Y + g * 3 * p2 + qxy;
+          const float ps = fmaf(y3[0], uz0, fmaf(y3[p2], uz1, y3[2 * p2] * uz2));
+          const int pr = pairs[c0 + g];
+          a = fmaf(Ps[(pr & 0xff) * p3 + lq] * Ps[(pr >> 8) * p3 + lq], ps, a);
+        }
+        acc[k] = a;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int lq = tid + AJ_NT * k;
+      if (lq >= p3) break;
+      const int64_t q = q0 + qs + lq;
+      Vbar[q] += w[q] * (double)acc[k];
+    }
+  }
+}
+
+}  // namespace
+
+pufe_status launch_adjoint_strip_sf(pufe_ctx *ctx, const double *Hbar, double *Vbar, int first,
+                                    int count, cudaStream_t st) {
+  if (count <= 0 || ctx->adj_sf_floats == 0) return PUFE_OK;
+  auto &D = ctx->d;
+  const int pm = std::max(1, ctx->max_part_p);
+  const int cf = (ctx->adj_sf_floats + 3) & ~3;
+  const size_t sm = ((size_t)cf + 33 * pm + AJ_W + 16 * 8 + 136) * sizeof(float);
+  if (sm > 227 * 1024) return fail(PUFE_EINVAL, "adjoint strip: shared memory above 227 KB");
+  PUFE_CUDA_TRY(
+      cudaFuncSetAttribute(k_adjoint_strip_sf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  k_adjoint_strip_sf<<<(unsigned)count, AJ_NT, sm, st>>>(
+      D.order + first, D.qoff, D.qpoff, D.qdat, D.w, D.doff, D.ecol, D.aoff, D.toff32, D.psi32,
+      D.partoff, D.part_p, D.part_q, D.soff, D.smap, Hbar, pm, cf, Vbar, D.err);
+  PUFE_CUDA_TRY(cudaGetLastError());
+  return PUFE_OK;
+}
+
+}  // namespace pufe

@@ -871,12 +871,18 @@ __global__ void __launch_bounds__(AS_NT) k_adjoint_strip_f32(
     const int32_t *__restrict__ ecol, const int32_t *__restrict__ aoff,
     const int64_t *__restrict__ toff32, const float *__restrict__ psi,
     const int64_t *__restrict__ soff, const int32_t *__restrict__ smap,
+    const int32_t *__restrict__ partoff, const int32_t *__restrict__ part_p,
     const double *__restrict__ Hbar, double *__restrict__ Vbar) {
   extern __shared__ float4 sm_as4[];
   const int e = order[blockIdx.x], tid = threadIdx.x;
   const int n = (int)(doff[e + 1] - doff[e]);
   const int ne = n - 64;
   if (ne <= 0) return;   // FE-only element: Vbar is already complete
+  {  // elements of the slot form are done by k_adjoint_strip_sf
+    int pmax = 0;
+    for (int k = partoff[e]; k < partoff[e + 1]; ++k) pmax = max(pmax, part_p[k]);
+    if (adjoint_sf_fits(aoff[e + 1] - aoff[e], pmax)) return;
+  }
   const int ne8 = (ne + 7) & ~7;
   float *Bf = reinterpret_cast<float *>(sm_as4);   // [64][ne8]: B[r][j], j in F
   float *Be = Bf + 64 * ne8;                       // [ne8][ne8]: s >= r half
@@ -1089,12 +1095,18 @@ pufe_status launch_adjoint_tc(pufe_ctx *ctx, const double *Hbar, double *Vbar, c
     if (sm > 227 * 1024) return fail(PUFE_EINVAL, "n_e too large for the strip adjoint");
     pufe_status e0 = launch_adjoint_fefe(ctx, Hbar, Vbar, nbig, nsmall, st);
     if (e0 != PUFE_OK) return e0;
-    PUFE_CUDA_TRY(cudaFuncSetAttribute(k_adjoint_strip_f32,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    k_adjoint_strip_f32<<<nsmall, AS_NT, sm, st>>>(D.order + nbig, D.qoff, D.qpoff, D.qdat, D.w,
-                                                   D.doff, D.ecol, D.aoff, D.toff32, D.psi32,
-                                                   D.soff, D.smap, Hbar, Vbar);
-    PUFE_CUDA_TRY(cudaGetLastError());
+    // the slot form where it fits (all elements of the usual rules), the
+    // direct per-point form for the rest
+    pufe_status e1 = launch_adjoint_strip_sf(ctx, Hbar, Vbar, nbig, nsmall, st);
+    if (e1 != PUFE_OK) return e1;
+    if (!ctx->adj_sf_all) {
+      PUFE_CUDA_TRY(cudaFuncSetAttribute(k_adjoint_strip_f32,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+      k_adjoint_strip_f32<<<nsmall, AS_NT, sm, st>>>(
+          D.order + nbig, D.qoff, D.qpoff, D.qdat, D.w, D.doff, D.ecol, D.aoff, D.toff32,
+          D.psi32, D.soff, D.smap, D.partoff, D.part_p, Hbar, Vbar);
+      PUFE_CUDA_TRY(cudaGetLastError());
+    }
   }
   return PUFE_OK;
 }
