@@ -287,6 +287,40 @@ def test_tf32x3_c3_like_large_elements():
     assert _rel(out.cpu().numpy(), go) < 1e-4
 
 
+def test_tf32x3_mixed_rule_sizes_take_both_strip_forms():
+    """p-adaptive rules between 9 and 11 points per axis: in one call the
+    enriched 10^3 elements take the slot form of the adjoint strip and the
+    11^3 ones (more than 10 points per axis) the per-point form; the 11^3 Psi
+    rows are too large for the assembly strip's shared-memory stage (global
+    reads).  Atoms sit on element vertices, never on a Gauss point."""
+    wl = W.small_two_atom(nel=4, a=6.0, r_c=1.2, r_e=3.0)
+    wl["quad"] = dict(mode=W.QUAD_PADAPT, p_far=6, p_near=10, p_min=9, p_max=11, tol=1e-6,
+                      max_depth=0)
+    m = omesh.Mesh(wl)
+    rules = oq.all_rules(m)
+    enriched = {int(q) for e, q in enumerate(np.diff(rules[2])) if m.elem_cols[e]}
+    assert {1000, 1331} <= enriched, enriched
+    ctx = pufe.pufe_build_mesh(wl)
+    V = W.random_potential(len(rules[1]), seed=21)
+    Ho, So = oasm.assemble_HS(m, rules, V)
+    Hg, Sg = _gpu_HS(ctx, V, pufe.PUFE_TF32X3)
+    assert _rel(Hg, Ho) < TOL_MAT_TF32 and _rel(Sg, So) < TOL_MAT_TF32
+    dev = _dev()
+    Hbar = Ho.copy()
+    Hbar.data = W.random_symmetric_values(Ho.nnz, seed=22)
+    go = oasm.adjoint_V(m, rules, Hbar)
+    out = torch.empty(ctx.n_q, dtype=torch.float64, device=dev)
+    ctx.pufe_assemble_HV_adjoint(torch.tensor(Hbar.data, device=dev), out, prec=pufe.PUFE_TF32X3)
+    ctx.pufe_sync_status()
+    assert _rel(out.cpu().numpy(), go) < 1e-4
+    # a non-symmetric cotangent: the strip adds Hbar_rj and Hbar_jr separately
+    Hbar.data = W.random_potential(Ho.nnz, seed=23)
+    go = oasm.adjoint_V(m, rules, Hbar)
+    ctx.pufe_assemble_HV_adjoint(torch.tensor(Hbar.data, device=dev), out, prec=pufe.PUFE_TF32X3)
+    ctx.pufe_sync_status()
+    assert _rel(out.cpu().numpy(), go) < 1e-4
+
+
 def _restricted_rules(m, off, x, elems, V=None):
     """Oracle rules for `elems` only (other elements get no points), with the
     GPU's point layout checked against the oracle's; V (full length) is
