@@ -256,6 +256,19 @@ typedef struct {
 pufe_status pufe_nonlocal_projections(pufe_ctx *ctx, int nproj, const pufe_projector *proj,
                                       double *F, void *stream);
 
+/* The same projections at wavevector k (host array of 3, 1/bohr; Sec. 4,
+ * eqs. bloch, strong): the projector is the Bloch sum
+ * p^k(x) = sum_n exp(i k.a_n) v(x - tau - a_n) and the basis functions are the
+ * Bloch sums of pufe_assemble_HS_bloch, so
+ * F[g, p] = int conj(phi_g^k) p^k, returned as F_re + i F_im (device float64,
+ * N x nproj row-major each, overwritten); the nonlocal term of H(k) is
+ * F h F^H.  k = 0 gives F_im = 0 and F_re = pufe_nonlocal_projections.
+ * Needs pufe_tabulate(ctx, PUFE_FP64).  Asynchronous apart from a blocking
+ * copy of the projector list. */
+pufe_status pufe_nonlocal_projections_bloch(pufe_ctx *ctx, const double *k, int nproj,
+                                            const pufe_projector *proj, double *F_re,
+                                            double *F_im, void *stream);
+
 /* ---- self-consistent field (Sec. 3) ------------------------------------ */
 
 /* Ionic charge density at every quadrature point (Sec. 3: the ionic

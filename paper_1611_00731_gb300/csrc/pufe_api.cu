@@ -164,11 +164,9 @@ pufe_status pufe_assemble_HV_adjoint_bloch(pufe_ctx *ctx, const double *k, const
                                    (cudaStream_t)stream);
 }
 
-pufe_status pufe_nonlocal_projections(pufe_ctx *ctx, int nproj, const pufe_projector *proj,
-                                      double *F, void *stream) {
-  if (pufe_status e0 = need_device(ctx)) return e0;
-  if (pufe_status e1 = need_table(ctx, PUFE_FP64)) return e1;
-  if (nproj < 1 || nproj > 64 || !proj || !F) return fail(PUFE_EINVAL, "need 1 <= nproj <= 64, proj and F");
+// checks the projector list and copies it to the device (blocking copy)
+static pufe_status upload_projectors(pufe_ctx *ctx, int nproj, const pufe_projector *proj) {
+  if (nproj < 1 || nproj > 64 || !proj) return fail(PUFE_EINVAL, "need 1 <= nproj <= 64 and proj");
   std::vector<ProjDev> pd(nproj);
   for (int p = 0; p < nproj; ++p) {
     const pufe_projector &q = proj[p];
@@ -183,13 +181,38 @@ pufe_status pufe_nonlocal_projections(pufe_ctx *ctx, int nproj, const pufe_proje
     d.rcut = q.r_p * std::sqrt(2.0 * 20.0 * std::log(10.0));   // Gaussian below 1e-20
     pd[p] = d;
   }
-  DeviceGuard g(ctx->device);
-  if (!g.ok) return fail(PUFE_ECUDA, "cudaSetDevice failed");
   if (!ctx->d.proj) PUFE_CUDA_TRY(cudaMalloc((void **)&ctx->d.proj, 64 * sizeof(ProjDev)));
   PUFE_CUDA_TRY(cudaMemcpy(ctx->d.proj, pd.data(), nproj * sizeof(ProjDev), cudaMemcpyHostToDevice));
+  return PUFE_OK;
+}
+
+pufe_status pufe_nonlocal_projections(pufe_ctx *ctx, int nproj, const pufe_projector *proj,
+                                      double *F, void *stream) {
+  if (pufe_status e0 = need_device(ctx)) return e0;
+  if (pufe_status e1 = need_table(ctx, PUFE_FP64)) return e1;
+  if (!F) return fail(PUFE_EINVAL, "F must not be NULL");
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return fail(PUFE_ECUDA, "cudaSetDevice failed");
+  if (pufe_status e2 = upload_projectors(ctx, nproj, proj)) return e2;
   cudaStream_t st = (cudaStream_t)stream;
   PUFE_CUDA_TRY(cudaMemsetAsync(F, 0, (size_t)ctx->n_dof * nproj * sizeof(double), st));
-  return launch_projections(ctx, ctx->d.proj, nproj, F, st);
+  return launch_projections(ctx, ctx->d.proj, nproj, nullptr, F, nullptr, st);
+}
+
+pufe_status pufe_nonlocal_projections_bloch(pufe_ctx *ctx, const double *k, int nproj,
+                                            const pufe_projector *proj, double *F_re,
+                                            double *F_im, void *stream) {
+  if (pufe_status e0 = need_device(ctx)) return e0;
+  if (pufe_status e1 = need_table(ctx, PUFE_FP64)) return e1;
+  if (!k || !F_re || !F_im) return fail(PUFE_EINVAL, "k, F_re and F_im must not be NULL");
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return fail(PUFE_ECUDA, "cudaSetDevice failed");
+  if (pufe_status e2 = upload_projectors(ctx, nproj, proj)) return e2;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t bytes = (size_t)ctx->n_dof * nproj * sizeof(double);
+  PUFE_CUDA_TRY(cudaMemsetAsync(F_re, 0, bytes, st));
+  PUFE_CUDA_TRY(cudaMemsetAsync(F_im, 0, bytes, st));
+  return launch_projections(ctx, ctx->d.proj, nproj, k, F_re, F_im, st);
 }
 
 pufe_status pufe_ion_density(pufe_ctx *ctx, int natoms, const double *tau, const double *Z,

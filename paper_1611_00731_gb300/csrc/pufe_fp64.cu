@@ -473,15 +473,21 @@ __global__ void __launch_bounds__(ADJ_NT) k_adjoint_fp64(
 // within r_cut.  One CTA per element; per chunk of QC points the basis rows
 // and w v_p go to shared memory; the element's n x P block accumulates in
 // shared memory and is added into F at the end.
+// BLOCH (Sec. 4, eqs. bloch, strong): the image at lattice vector a_n carries
+// exp(i k.a_n) and column i of the element the factor exp(-i k.R_i) of its
+// lattice shift R_i, so F is complex (real and imaginary N x P arrays).
 // ---------------------------------------------------------------------------
+template <bool BLOCH>
 __global__ void __launch_bounds__(ASM_NT) k_projections(
     const int64_t *__restrict__ qoff, const double *__restrict__ w,
     const double *__restrict__ xi_all, const double *__restrict__ x,
     const int64_t *__restrict__ doff, const int32_t *__restrict__ dofs,
     const int32_t *__restrict__ ecol, const int64_t *__restrict__ toff,
     const double *__restrict__ psi, const ProjDev *__restrict__ pj, int P, double a0, double a1,
-    double a2, double *__restrict__ F) {
+    double a2, double *__restrict__ F, const uint8_t *__restrict__ eshift, PhaseTab ph,
+    double k0, double k1, double k2, double *__restrict__ Fi) {
   extern __shared__ __align__(16) double smem[];
+  constexpr int NC = BLOCH ? 2 : 1;   // real, imaginary parts
   const int e = blockIdx.x;
   const int64_t q0 = qoff[e];
   const int Q = (int)(qoff[e + 1] - q0);
@@ -489,12 +495,12 @@ __global__ void __launch_bounds__(ASM_NT) k_projections(
   const int32_t *ec = ecol + (doff[e] - 64ll * e);
   const double *pe = psi + 4 * toff[e];
   double *Bc = smem;               // QC x n
-  double *Vp = Bc + QC * n;        // QC x P
-  double *acc = Vp + QC * P;       // n x P
-  Tab1D *tab = reinterpret_cast<Tab1D *>(acc + (size_t)n * P);
+  double *Vp = Bc + QC * n;        // [NC] QC x P
+  double *acc = Vp + NC * QC * P;  // [NC] n x P
+  Tab1D *tab = reinterpret_cast<Tab1D *>(acc + (size_t)NC * n * P);
   const double av[3] = {a0, a1, a2};
   const double s[3] = {0, 0, 0};
-  for (int k = threadIdx.x; k < n * P; k += ASM_NT) acc[k] = 0.0;
+  for (int k = threadIdx.x; k < NC * n * P; k += ASM_NT) acc[k] = 0.0;
   for (int qc = 0; qc < Q; qc += QC) {
     __syncthreads();
     for (int k = threadIdx.x; k < QC * 3; k += ASM_NT) {
@@ -512,7 +518,7 @@ __global__ void __launch_bounds__(ASM_NT) k_projections(
     for (int k = threadIdx.x; k < QC * P; k += ASM_NT) {
       const int qq = k / P, p = k - qq * P;
       const int q = qc + qq;
-      double v = 0.0;
+      double v = 0.0, vi = 0.0;
       if (q < Q) {
         const ProjDev pr = pj[p];
         double d[3];
@@ -530,11 +536,21 @@ __global__ void __launch_bounds__(ASM_NT) k_projections(
               const double r2 = dx * dx + dy * dy + dz * dz;
               if (r2 >= pr.rcut * pr.rcut) continue;
               double g[3];
-              v += pr.N * exp(-r2 * i2) * solid_harmonic(pr.l, pr.m, dx, dy, dz, g);
+              const double val = pr.N * exp(-r2 * i2) * solid_harmonic(pr.l, pr.m, dx, dy, dz, g);
+              if (BLOCH) {   // exp(i k.a_n): this term is v(x - tau - a_n), a_n = -(i a0, j a1, l a2)
+                double sn, cs;
+                sincos(-(k0 * (i * av[0]) + k1 * (j * av[1]) + k2 * (l * av[2])), &sn, &cs);
+                v += val * cs;
+                vi += val * sn;
+              } else {
+                v += val;
+              }
             }
         v *= w[q0 + q];
+        vi *= w[q0 + q];
       }
       Vp[k] = v;
+      if (BLOCH) Vp[QC * P + k] = vi;
     }
     __syncthreads();
     for (int k = threadIdx.x; k < QC * n; k += ASM_NT) {
@@ -559,15 +575,27 @@ __global__ void __launch_bounds__(ASM_NT) k_projections(
     const int qn = min(QC, Q - qc);
     for (int k = threadIdx.x; k < n * P; k += ASM_NT) {
       const int i = k / P, p = k - i * P;
-      double t = acc[k];
-      for (int qq = 0; qq < qn; ++qq) t = fma(Bc[qq * n + i], Vp[qq * P + p], t);
+      double t = acc[k], ti = BLOCH ? acc[n * P + k] : 0.0;
+      for (int qq = 0; qq < qn; ++qq) {
+        t = fma(Bc[qq * n + i], Vp[qq * P + p], t);
+        if (BLOCH) ti = fma(Bc[qq * n + i], Vp[QC * P + qq * P + p], ti);
+      }
       acc[k] = t;
+      if (BLOCH) acc[n * P + k] = ti;
     }
   }
   __syncthreads();
   for (int k = threadIdx.x; k < n * P; k += ASM_NT) {
     const int i = k / P, p = k - i * P;
-    atomicAdd(F + (int64_t)dofs[doff[e] + i] * P + p, acc[k]);
+    const int64_t o = (int64_t)dofs[doff[e] + i] * P + p;
+    if (BLOCH) {   // times conj(exp(i k.R_i))
+      const int c = eshift[doff[e] + i];
+      const double cr = ph.re[c], ci = -ph.im[c], ar = acc[k], ai = acc[n * P + k];
+      atomicAdd(F + o, cr * ar - ci * ai);
+      atomicAdd(Fi + o, cr * ai + ci * ar);
+    } else {
+      atomicAdd(F + o, acc[k]);
+    }
   }
 }
 
@@ -699,18 +727,27 @@ pufe_status launch_adjoint_fp64_bloch(pufe_ctx *ctx, const PhaseTab &ph, const d
   return PUFE_OK;
 }
 
-pufe_status launch_projections(pufe_ctx *ctx, const ProjDev *pj, int P, double *F,
-                               cudaStream_t st) {
+pufe_status launch_projections(pufe_ctx *ctx, const ProjDev *pj, int P, const double *k,
+                               double *F, double *Fi, cudaStream_t st) {
   auto &D = ctx->d;
   const int n = ctx->max_basis;
-  const size_t sm = ((size_t)QC * n + (size_t)QC * P + (size_t)n * P) * sizeof(double) +
+  const int nc = k ? 2 : 1;
+  const size_t sm = ((size_t)QC * n + (size_t)nc * QC * P + (size_t)nc * n * P) * sizeof(double) +
                     QC * sizeof(Tab1D);
   if (sm > 227 * 1024) return fail(PUFE_EINVAL, "n_e * nproj too large for the projection kernel");
-  PUFE_CUDA_TRY(
-      cudaFuncSetAttribute(k_projections, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  k_projections<<<(unsigned)ctx->nelem, ASM_NT, sm, st>>>(D.qoff, D.w, D.xi, D.x, D.doff, D.dofs,
-                                                          D.ecol, D.toff, D.psi, pj, P, ctx->a[0],
-                                                          ctx->a[1], ctx->a[2], F);
+  if (k) {
+    PUFE_CUDA_TRY(cudaFuncSetAttribute(k_projections<true>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_projections<true><<<(unsigned)ctx->nelem, ASM_NT, sm, st>>>(
+        D.qoff, D.w, D.xi, D.x, D.doff, D.dofs, D.ecol, D.toff, D.psi, pj, P, ctx->a[0], ctx->a[1],
+        ctx->a[2], F, D.eshift, phase_table(ctx, k), k[0], k[1], k[2], Fi);
+  } else {
+    PUFE_CUDA_TRY(cudaFuncSetAttribute(k_projections<false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_projections<false><<<(unsigned)ctx->nelem, ASM_NT, sm, st>>>(
+        D.qoff, D.w, D.xi, D.x, D.doff, D.dofs, D.ecol, D.toff, D.psi, pj, P, ctx->a[0], ctx->a[1],
+        ctx->a[2], F, nullptr, PhaseTab{}, 0.0, 0.0, 0.0, nullptr);
+  }
   PUFE_CUDA_TRY(cudaGetLastError());
   return PUFE_OK;
 }

@@ -288,7 +288,9 @@ struct ProjDev {
   double rp, N, rcut;
   int l, m;
 };
-pufe_status launch_projections(pufe_ctx *ctx, const ProjDev *pj, int P, double *F, cudaStream_t s);
+// k == nullptr: Gamma point, F real; else F + i Fi at wavevector k
+pufe_status launch_projections(pufe_ctx *ctx, const ProjDev *pj, int P, const double *k, double *F,
+                               double *Fi, cudaStream_t s);
 // Bloch (k != 0) FP64 variants: phases exp(i k . R) of the 8 shift codes
 struct PhaseTab {
   double re[8], im[8];

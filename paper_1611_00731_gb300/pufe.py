@@ -30,7 +30,16 @@ EXPORTS = ["pufe_build_mesh", "pufe_get_sizes", "pufe_get_quadrature", "pufe_get
            "pufe_assemble_HV_adjoint", "pufe_sync_status", "pufe_destroy", "pufe_last_error",
            "pufe_assemble_HS_static", "pufe_ion_density", "pufe_effective_potential",
            "pufe_scf_step", "pufe_scf_reset", "pufe_assemble_HS_bloch", "pufe_density_bloch",
-           "pufe_assemble_HV_adjoint_bloch", "pufe_nonlocal_projections"]
+           "pufe_assemble_HV_adjoint_bloch", "pufe_nonlocal_projections",
+           "pufe_nonlocal_projections_bloch"]
+
+
+def _projector_array(projs):
+    arr = (Projector * len(projs))()
+    for i, p in enumerate(projs):
+        arr[i].tau = (C.c_double * 3)(*[float(t) for t in p["tau"]])
+        arr[i].l, arr[i].m, arr[i].r_p = int(p["l"]), int(p["m"]), float(p["rp"])
+    return arr
 
 
 class PufeError(RuntimeError):
@@ -110,6 +119,8 @@ def load_library(build_if_missing: bool = True):
                                   C.POINTER(ScfInfo), vp]
     lib.pufe_scf_reset.argtypes = [vp]
     lib.pufe_nonlocal_projections.argtypes = [vp, C.c_int, C.POINTER(Projector), vp, vp]
+    lib.pufe_nonlocal_projections_bloch.argtypes = [vp, dp, C.c_int, C.POINTER(Projector), vp,
+                                                    vp, vp]
     lib.pufe_assemble_HS_bloch.argtypes = [vp, dp, vp, C.c_int, vp, vp, vp, vp, vp]
     lib.pufe_density_bloch.argtypes = [vp, dp, vp, vp, C.c_int64, vp, C.c_int, vp, vp]
     lib.pufe_assemble_HV_adjoint_bloch.argtypes = [vp, dp, vp, vp, vp, vp]
@@ -290,12 +301,20 @@ class Context:
         """F (N x P device tensor) <- projections onto projs: list of
         dict(tau, l, m, rp)."""
         import torch
-        arr = (Projector * len(projs))()
-        for i, p in enumerate(projs):
-            arr[i].tau = (C.c_double * 3)(*[float(t) for t in p["tau"]])
-            arr[i].l, arr[i].m, arr[i].r_p = int(p["l"]), int(p["m"]), float(p["rp"])
+        arr = _projector_array(projs)
         _check(_LIB.pufe_nonlocal_projections(self._h, len(projs), arr, _ptr(F, torch.float64),
                                               _stream(stream)))
+
+    def pufe_nonlocal_projections_bloch(self, k, projs, F, stream=None):
+        """F = (F_re, F_im) (N x P device tensors) <- projections onto the
+        Bloch sums of projs at wavevector k."""
+        import torch
+        kk = (C.c_double * 3)(*[float(x) for x in k])
+        arr = _projector_array(projs)
+        f64 = torch.float64
+        _check(_LIB.pufe_nonlocal_projections_bloch(self._h, kk, len(projs), arr,
+                                                    _ptr(F[0], f64), _ptr(F[1], f64),
+                                                    _stream(stream)))
 
     def pufe_scf_reset(self):
         _check(_LIB.pufe_scf_reset(self._h))

@@ -78,3 +78,30 @@ def test_nonlocal_term_in_the_eigenproblem():
     w0 = sla.eigh(Ho.toarray(), So.toarray(), eigvals_only=True, subset_by_index=[0, 5])
     assert np.abs(wg - wo).max() < 1e-10
     assert np.all(wo >= w0 - 1e-12) and (wo - w0).max() > 1e-3   # h > 0 raises the levels
+
+
+@pytest.mark.parametrize("name", ["two_atom_2cube", "c1_two_atom_4cube"])
+def test_bloch_projections_match_oracle(name):
+    """F(k) at a general k (images and element columns phased) against the
+    oracle's complex F, and k = 0 against the Gamma-point call."""
+    wl = CASES[name]()
+    m = omesh.Mesh(wl)
+    rules = oq.all_rules(m)
+    ctx = pufe.pufe_build_mesh(wl)
+    ctx.pufe_tabulate(pufe.PUFE_FP64)
+    ps = _projs(wl)
+    dev = torch.device("cuda:0")
+    k = 2.0 * np.pi / m.a * np.array([0.25, -0.125, 0.375])
+    Fo = onl.projections_k(m, rules, ps, k)
+    Fr = torch.empty(ctx.n_dof, len(ps), dtype=torch.float64, device=dev)
+    Fi = torch.empty_like(Fr)
+    ctx.pufe_nonlocal_projections_bloch(k, ps, (Fr, Fi))
+    ctx.pufe_sync_status()
+    Fg = Fr.cpu().numpy() + 1j * Fi.cpu().numpy()
+    assert np.abs(Fg - Fo).max() < 1e-12 * np.abs(Fo).max(), name
+    F0 = torch.empty_like(Fr)
+    ctx.pufe_nonlocal_projections(ps, F0)
+    ctx.pufe_nonlocal_projections_bloch((0.0, 0.0, 0.0), ps, (Fr, Fi))
+    ctx.pufe_sync_status()
+    assert np.abs(Fi.cpu().numpy()).max() == 0.0
+    assert np.abs(Fr.cpu().numpy() - F0.cpu().numpy()).max() < 1e-14 * np.abs(Fo).max()
