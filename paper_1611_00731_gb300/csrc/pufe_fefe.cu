@@ -125,7 +125,21 @@ __global__ void __launch_bounds__(SF_NT) k_adjoint_fefe(
   const int e = order[blockIdx.x], tid = threadIdx.x;
   const int n = (int)(doff[e + 1] - doff[e]);
   const int32_t *m = smap + soff[e];
-  for (int o = tid; o < 4096; o += SF_NT) Hs[o] = (float)Hbar[m[(o >> 6) * n + (o & 63)]];
+  // gather with eight independent (map, value) load chains in flight per thread
+  for (int o0 = tid; o0 < 4096; o0 += 8 * SF_NT) {
+    int s1[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int o = o0 + u * SF_NT;
+      s1[u] = o < 4096 ? m[(o >> 6) * n + (o & 63)] : 0;
+    }
+    double h[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) h[u] = o0 + u * SF_NT < 4096 ? Hbar[s1[u]] : 0.0;
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (o0 + u * SF_NT < 4096) Hs[o0 + u * SF_NT] = (float)h[u];
+  }
   for (int k = partoff[e]; k < partoff[e + 1]; ++k) {
     const int p = part_p[k];
     if (p > pm) {

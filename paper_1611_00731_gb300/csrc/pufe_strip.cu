@@ -572,16 +572,26 @@ __global__ void __launch_bounds__(ST_NT, 2) k_strip_sf(
       const int blk0 = qs >> 3, nblk = ((qs + p3 + 7) >> 3) - blk0;
       const float4 *src = reinterpret_cast<const float4 *>(E.pe + (int64_t)blk0 * A * 32);
       const FastDiv dA8(A * 8);
-      for (int o = tid; o < nblk * A * 8; o += ST_NT) {   // one float4 = 4 points of a row
-        const float4 v4 = src[o];
-        const int blk = dA8.div(o), rem = o - blk * (A * 8);
-        const int row = rem >> 1;   // slot * 4 + comp
-        const int qb = (blk0 + blk) * 8 + (rem & 1) * 4 - qs;
-        float *d = stage + row * P;
-        if (qb >= 0 && qb < p3) d[qb] = v4.x;
-        if (qb + 1 >= 0 && qb + 1 < p3) d[qb + 1] = v4.y;
-        if (qb + 2 >= 0 && qb + 2 < p3) d[qb + 2] = v4.z;
-        if (qb + 3 >= 0 && qb + 3 < p3) d[qb + 3] = v4.w;
+      // one float4 = 4 points of a row; four loads in flight per thread
+      const int nsrc = nblk * A * 8;
+      for (int o0 = tid; o0 < nsrc; o0 += 4 * ST_NT) {
+        float4 v4[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          v4[u] = o0 + u * ST_NT < nsrc ? src[o0 + u * ST_NT] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int o = o0 + u * ST_NT;
+          if (o >= nsrc) break;
+          const int blk = dA8.div(o), rem = o - blk * (A * 8);
+          const int row = rem >> 1;   // slot * 4 + comp
+          const int qb = (blk0 + blk) * 8 + (rem & 1) * 4 - qs;
+          float *d = stage + row * P;
+          if (qb >= 0 && qb < p3) d[qb] = v4[u].x;
+          if (qb + 1 >= 0 && qb + 1 < p3) d[qb + 1] = v4[u].y;
+          if (qb + 2 >= 0 && qb + 2 < p3) d[qb + 2] = v4[u].z;
+          if (qb + 3 >= 0 && qb + 3 < p3) d[qb + 3] = v4[u].w;
+        }
       }
       for (int o = tid; o < p3; o += ST_NT) {
         xd[o] = E.qe[qs + o];
@@ -857,9 +867,16 @@ __global__ void __launch_bounds__(AJ_NT, 4) k_adjoint_strip_sf(
     const FastDiv dp(p), dp2(p2);
     __syncthreads();   // coefficients ready; previous part's readers done
     // Psi values of the (sub)cell's points and the 1D factors per axis
-    for (int o = tid; o < A * p3; o += AJ_NT) {
-      const int al = o / p3, lq = o - al * p3, ql = qs + lq;
-      Ps[o] = pe[((int64_t)(ql >> 3) * A + al) * 32 + (ql & 7)];
+    for (int o0 = tid; o0 < A * p3; o0 += 4 * AJ_NT) {   // four loads in flight per thread
+      float v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int o = o0 + u * AJ_NT, al = o / p3, ql = qs + o - al * p3;
+        v[u] = o < A * p3 ? pe[((int64_t)(ql >> 3) * A + al) * 32 + (ql & 7)] : 0.0f;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (o0 + u * AJ_NT < A * p3) Ps[o0 + u * AJ_NT] = v[u];
     }
     for (int o = tid; o < 3 * p; o += AJ_NT) {
       const int d = o / p, t = o - d * p;
