@@ -34,7 +34,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # k_strip_sf, per launch, from the ncu capture summarised in
 # profiles/step_mixed_c2_rocksalt_12cube.md; the memset of H and the copy of
 # the overlap constants into S (232 MB by construction) are not counted
-ASM_TRAFFIC = {("c2_rocksalt_12cube", "tf32x3"): 95_971_840 + 171_247_616}
+ASM_TRAFFIC = {("c2_rocksalt_12cube", "tf32x3"): 96_017_664 + 170_968_064}
 
 
 def _dist():
