@@ -321,6 +321,44 @@ def test_tf32x3_mixed_rule_sizes_take_both_strip_forms():
     assert _rel(out.cpu().numpy(), go) < 1e-4
 
 
+def _hadapt_case(name):
+    wl = W.workload("c3_cscl_4cube")
+    if name == "few_slots":        # 1-4 slots with up to 8 vertices: enrichment-pair E x E
+        wl["species"][0]["orbitals"] = [o for o in wl["species"][0]["orbitals"]
+                                        if o[0] == 4 and o[1] <= 1]
+        wl["species"][1]["orbitals"] = [o for o in wl["species"][1]["orbitals"]
+                                        if o[0] == 3 and o[1] == 0]
+        wl["species"][0]["r_e"], wl["species"][1]["r_e"] = 2.2, 1.5
+    else:                          # 9 and 25 one-vertex slots: direct E x E, both adjoint forms
+        wl["species"][0]["orbitals"] = [o for o in wl["species"][0]["orbitals"] if o[0] >= 3]
+        wl["species"][0]["r_e"] = 0.8
+    return wl
+
+
+@pytest.mark.parametrize("name", ["few_slots", "many_slots"])
+def test_tf32x3_hadapt_multi_part_elements(name):
+    """h-adaptive rules: enriched elements split into eight 8^3 sub-cells, so
+    the strip's E x E projections (pair form) or tiles (direct form) and the
+    adjoint's slot and pair coefficients carry over from cell to cell."""
+    wl = _hadapt_case(name)
+    m = omesh.Mesh(wl)
+    rules = oq.all_rules(m)
+    assert 4096 in set(np.diff(rules[2]).tolist())
+    ctx = pufe.pufe_build_mesh(wl)
+    V = W.random_potential(len(rules[1]), seed=41)
+    Ho, So = oasm.assemble_HS(m, rules, V)
+    Hg, Sg = _gpu_HS(ctx, V, pufe.PUFE_TF32X3)
+    assert _rel(Hg, Ho) < TOL_MAT_TF32 and _rel(Sg, So) < TOL_MAT_TF32
+    dev = _dev()
+    Hbar = Ho.copy()
+    Hbar.data = W.random_potential(Ho.nnz, seed=42)     # general, non-symmetric
+    go = oasm.adjoint_V(m, rules, Hbar)
+    out = torch.empty(ctx.n_q, dtype=torch.float64, device=dev)
+    ctx.pufe_assemble_HV_adjoint(torch.tensor(Hbar.data, device=dev), out, prec=pufe.PUFE_TF32X3)
+    ctx.pufe_sync_status()
+    assert _rel(out.cpu().numpy(), go) < 1e-4
+
+
 def _restricted_rules(m, off, x, elems, V=None):
     """Oracle rules for `elems` only (other elements get no points), with the
     GPU's point layout checked against the oracle's; V (full length) is
