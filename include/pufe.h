@@ -212,12 +212,16 @@ pufe_status pufe_assemble_HV_adjoint(pufe_ctx *ctx, const double *Hbar, int prec
  * onto its representative in the cell (the enrichments themselves are
  * periodic, Sec. 5.1 eq. Psi with f(R) = 1).  Outputs are the real and
  * imaginary parts, each nnz float64 on the CSR pattern (device,
- * overwritten; H(k) and S(k) are Hermitian).  FP64 only: needs
- * pufe_tabulate(ctx, PUFE_FP64).  k = 0 gives the Gamma-point matrices with
- * zero imaginary parts.  Asynchronous. */
-pufe_status pufe_assemble_HS_bloch(pufe_ctx *ctx, const double *k, const double *V, int what,
-                                   double *H_re, double *H_im, double *S_re, double *S_im,
-                                   void *stream);
+ * overwritten; H(k) and S(k) are Hermitian).  prec PUFE_FP64 needs
+ * pufe_tabulate(ctx, PUFE_FP64); PUFE_TF32X3 (meshes with n_e <= 128) the
+ * PUFE_TF32X3 table and rules of >= 4 points per axis: the element blocks of
+ * the mixed pufe_assemble_HS, the FE-FE blocks (with the exact kinetic and
+ * overlap constants) scattered with FP64 phases and the enrichment blocks with
+ * FP32 phases.  k = 0 gives the Gamma-point matrices with zero imaginary
+ * parts.  Asynchronous. */
+pufe_status pufe_assemble_HS_bloch(pufe_ctx *ctx, const double *k, const double *V, int prec,
+                                   int what, double *H_re, double *H_im, double *S_re,
+                                   double *S_im, void *stream);
 
 /* Density of complex Bloch states: n_q = sum_j f_j |sum_l B_ql
  * exp(i k.R_l) C_lj|^2 with C = C_re + i C_im (device float64, N x nocc, row

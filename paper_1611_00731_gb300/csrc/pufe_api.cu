@@ -115,12 +115,13 @@ pufe_status pufe_assemble_HV_adjoint(pufe_ctx *ctx, const double *Hbar, int prec
   return launch_adjoint_fp64(ctx, Hbar, Vbar, (cudaStream_t)stream);
 }
 
-pufe_status pufe_assemble_HS_bloch(pufe_ctx *ctx, const double *k, const double *V, int what,
-                                   double *H_re, double *H_im, double *S_re, double *S_im,
-                                   void *stream) {
+pufe_status pufe_assemble_HS_bloch(pufe_ctx *ctx, const double *k, const double *V, int prec,
+                                   int what, double *H_re, double *H_im, double *S_re,
+                                   double *S_im, void *stream) {
   if (pufe_status e0 = need_device(ctx)) return e0;
   if (!k) return fail(PUFE_EINVAL, "k must not be NULL");
-  if (pufe_status e1 = need_table(ctx, PUFE_FP64)) return e1;
+  if (prec != PUFE_FP64 && prec != PUFE_TF32X3) return fail(PUFE_EINVAL, "unknown precision");
+  if (pufe_status e1 = need_table(ctx, prec)) return e1;
   if (what <= 0 || what > (PUFE_WANT_H | PUFE_WANT_S)) return fail(PUFE_EINVAL, "bad `what` mask");
   if ((what & PUFE_WANT_H) && (!H_re || !H_im || !V))
     return fail(PUFE_EINVAL, "H wanted: need H_re, H_im and V");
@@ -128,6 +129,9 @@ pufe_status pufe_assemble_HS_bloch(pufe_ctx *ctx, const double *k, const double 
   DeviceGuard g(ctx->device);
   if (!g.ok) return fail(PUFE_ECUDA, "cudaSetDevice failed");
   cudaStream_t st = (cudaStream_t)stream;
+  if (prec == PUFE_TF32X3)
+    return launch_assemble_mixed_bloch(ctx, phase_table(ctx, k), V, what, H_re, H_im, S_re, S_im,
+                                       st);
   const size_t bytes = (size_t)ctx->nnz * sizeof(double);
   if (what & PUFE_WANT_H) {
     PUFE_CUDA_TRY(cudaMemsetAsync(H_re, 0, bytes, st));

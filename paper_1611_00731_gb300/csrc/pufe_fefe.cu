@@ -37,13 +37,19 @@ __device__ __forceinline__ void lag3(float t, float L[4]) {
   L[3] = 0.5625f * a * b * c;
 }
 
+// BLOCH (Sec. 4, eqs. bloch, strong): entry (i, j) goes into H(k) and S(k)
+// with the phase conj(exp(i k.R_i)) exp(i k.R_j) of the columns' lattice
+// shifts, the constant overlap block included (S(k) has no k-independent part).
+template <bool BLOCH>
 __global__ void __launch_bounds__(SF_NT) k_fefe_sumfac(
     const int64_t *__restrict__ qoff, const double *__restrict__ w, const double *__restrict__ V,
     const double *__restrict__ xi_all, const int32_t *__restrict__ partoff,
     const int32_t *__restrict__ part_p, const int32_t *__restrict__ part_q,
     const int64_t *__restrict__ doff, const int64_t *__restrict__ soff,
     const int32_t *__restrict__ smap, const double *__restrict__ Tfe, double *__restrict__ H,
-    unsigned *err) {
+    unsigned *err, const double *__restrict__ Sfe, const uint8_t *__restrict__ eshift,
+    PhaseTab ph, int what, double *__restrict__ Hi, double *__restrict__ S,
+    double *__restrict__ Si) {
   __shared__ float Wq[SF_PMAX * SF_PMAX * SF_PMAX];
   __shared__ float P[3][10][SF_PMAX];          // pair products per axis
   __shared__ float G1[SF_PMAX * SF_PMAX * 10];  // [qx + p qy][cc]
@@ -101,7 +107,24 @@ __global__ void __launch_bounds__(SF_NT) k_fefe_sumfac(
     const int i = o >> 6, j = o & 63;
     const float v = M[pidx(i & 3, j & 3) * 100 + pidx((i >> 2) & 3, (j >> 2) & 3) * 10 +
                       pidx(i >> 4, j >> 4)];
-    atomicAdd(H + m[i * n + j], __ldg(Tfe + o) + (double)v);
+    const int slot = m[i * n + j];
+    if (!BLOCH) {
+      atomicAdd(H + slot, __ldg(Tfe + o) + (double)v);
+    } else {
+      const int ci = eshift[doff[e] + i], cj = eshift[doff[e] + j];
+      const double pr = ph.re[ci] * ph.re[cj] + ph.im[ci] * ph.im[cj];
+      const double pi = ph.re[ci] * ph.im[cj] - ph.im[ci] * ph.re[cj];
+      if (what & PUFE_WANT_H) {
+        const double hv = __ldg(Tfe + o) + (double)v;
+        atomicAdd(H + slot, hv * pr);
+        atomicAdd(Hi + slot, hv * pi);
+      }
+      if (what & PUFE_WANT_S) {
+        const double sv = __ldg(Sfe + o);
+        atomicAdd(S + slot, sv * pr);
+        atomicAdd(Si + slot, sv * pi);
+      }
+    }
   }
 }
 
@@ -205,9 +228,23 @@ pufe_status launch_fefe(pufe_ctx *ctx, const double *V, double *H, cudaStream_t 
   auto &D = ctx->d;
   if (ctx->max_part_p > SF_PMAX) return fail(PUFE_EINVAL, "rule with more than 16 points per axis");
   if (!D.Tfe) return fail(PUFE_ESTATE, "no exact FE-FE blocks (a rule has < 4 points per axis)");
-  k_fefe_sumfac<<<(unsigned)ctx->nelem, SF_NT, 0, st>>>(D.qoff, D.w, V, D.xi, D.partoff, D.part_p,
-                                                        D.part_q, D.doff, D.soff, D.smap, D.Tfe, H,
-                                                        D.err);
+  k_fefe_sumfac<false><<<(unsigned)ctx->nelem, SF_NT, 0, st>>>(
+      D.qoff, D.w, V, D.xi, D.partoff, D.part_p, D.part_q, D.doff, D.soff, D.smap, D.Tfe, H, D.err,
+      nullptr, nullptr, PhaseTab{}, PUFE_WANT_H, nullptr, nullptr, nullptr);
+  PUFE_CUDA_TRY(cudaGetLastError());
+  return PUFE_OK;
+}
+
+// Bloch form: the FE-FE blocks of H(k) (if wanted; V == NULL means V = 0) and
+// S(k) (if wanted) with the column phases, into zeroed outputs
+pufe_status launch_fefe_bloch(pufe_ctx *ctx, const PhaseTab &ph, const double *V, int what,
+                              double *H, double *Hi, double *S, double *Si, cudaStream_t st) {
+  auto &D = ctx->d;
+  if (ctx->max_part_p > SF_PMAX) return fail(PUFE_EINVAL, "rule with more than 16 points per axis");
+  if (!D.Tfe || !D.Sfe) return fail(PUFE_ESTATE, "no exact FE-FE blocks (a rule has < 4 points per axis)");
+  k_fefe_sumfac<true><<<(unsigned)ctx->nelem, SF_NT, 0, st>>>(
+      D.qoff, D.w, (what & PUFE_WANT_H) ? V : nullptr, D.xi, D.partoff, D.part_p, D.part_q,
+      D.doff, D.soff, D.smap, D.Tfe, H, D.err, D.Sfe, D.eshift, ph, what, Hi, S, Si);
   PUFE_CUDA_TRY(cudaGetLastError());
   return PUFE_OK;
 }

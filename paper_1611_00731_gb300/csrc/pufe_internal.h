@@ -86,6 +86,7 @@ struct DeviceArrays {
   float *eorig = nullptr;     // per (element, slot): displacement of the element
                               // origin from the nearest atom image, hi[3], lo[3], 0, 0
   double *Tfe = nullptr;      // 64 x 64: kinetic block of the tricubic functions (any element)
+  double *Sfe = nullptr;      // 64 x 64: overlap block of the tricubic functions (any element)
   double *S0 = nullptr;       // nnz: global FE-FE overlap blocks (constant)
   Orbital *orb = nullptr;     // n_alpha
   OrbitalF *orbf = nullptr;   // n_alpha
@@ -309,6 +310,13 @@ pufe_status launch_adjoint_tc(pufe_ctx *ctx, const double *Hbar, double *Vbar, c
 pufe_status launch_fefe(pufe_ctx *ctx, const double *V, double *H, cudaStream_t s);  // H must be zeroed
 pufe_status launch_strip_sf(pufe_ctx *ctx, const double *V, int what, double *H, double *S,
                             int first, int count, cudaStream_t s);
+pufe_status launch_fefe_bloch(pufe_ctx *ctx, const PhaseTab &ph, const double *V, int what,
+                              double *H, double *Hi, double *S, double *Si, cudaStream_t s);
+// mixed-precision Bloch assembly (n_e <= 128): FE-FE blocks with FP64 phases,
+// the enrichment strip in FP32 with FP32 phases; outputs zeroed here
+pufe_status launch_assemble_mixed_bloch(pufe_ctx *ctx, const PhaseTab &ph, const double *V,
+                                        int what, double *H, double *Hi, double *S, double *Si,
+                                        cudaStream_t s);
 pufe_status scf_prepare(pufe_ctx *ctx);
 void scf_free(pufe_ctx *ctx);
 pufe_status launch_ion_density(pufe_ctx *ctx, int natoms, const double *tau, const double *Z,

@@ -586,7 +586,7 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
   for (auto &parts : rule)
     for (auto &pt : parts) min_p = std::min(min_p, pt.p);
   const bool fe_exact = min_p >= 4;
-  std::vector<double> TF, S0;
+  std::vector<double> TF, S0, SF;
   if (fe_exact) {
     double M1[4][4] = {{0}}, K1[4][4] = {{0}};
     for (int g = 0; g < 4; ++g) {
@@ -600,7 +600,7 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
     }
     const double J = 0.125 * S.h[0] * S.h[1] * S.h[2];
     const double s2[3] = {4.0 / (S.h[0] * S.h[0]), 4.0 / (S.h[1] * S.h[1]), 4.0 / (S.h[2] * S.h[2])};
-    std::vector<double> SF(64 * 64);
+    SF.assign(64 * 64, 0.0);
     TF.assign(64 * 64, 0.0);
     for (int i = 0; i < 64; ++i)
       for (int j = 0; j < 64; ++j) {
@@ -726,6 +726,7 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
   if ((st = upload(&D.order, order)) != PUFE_OK) return st;
   if (fe_exact) {
     if ((st = upload(&D.Tfe, TF)) != PUFE_OK) return st;
+    if ((st = upload(&D.Sfe, SF)) != PUFE_OK) return st;
     if ((st = upload(&D.S0, S0)) != PUFE_OK) return st;
   }
   PUFE_CUDA_TRY(cudaMalloc((void **)&D.psi, std::max<int64_t>(1, ctx->psi_len) * sizeof(double)));
@@ -764,7 +765,7 @@ static void free_device(pufe_ctx *ctx) {
   auto &D = ctx->d;
   void *ptrs[] = {D.qoff, D.x, D.w, D.xi, D.doff, D.dofs, D.ecol, D.eshift, D.aoff, D.alist,
                   D.toff, D.psi, D.psi32, D.qpoff, D.qdat, D.ptab, D.vpad, D.toff32, D.eorig,
-                  D.Tfe, D.S0, D.partoff, D.part_p, D.part_q,
+                  D.Tfe, D.Sfe, D.S0, D.partoff, D.part_p, D.part_q,
                   D.orb, D.orbf, D.rowptr, D.col, D.soff, D.smap, D.order, D.err};
   for (void *p : ptrs)
     if (p) cudaFree(p);

@@ -111,7 +111,18 @@ struct StripElem {
   const int *pairs;
   float *PE;
   const float *F1;
+  // Bloch scatter: lattice-shift code of each column, the 8 phases
+  // exp(i k.R) in FP32, imaginary outputs
+  const uint8_t *esh;
+  const float *phr, *phi;
+  double *Hi, *Si;
 };
+
+// phase conj(exp(i k.R_a)) exp(i k.R_b) of a column pair with shift codes a, b
+__device__ __forceinline__ void pair_phase(const StripElem &E, int a, int b, float &pr, float &pi) {
+  pr = E.phr[a] * E.phr[b] + E.phi[a] * E.phi[b];
+  pi = E.phr[a] * E.phi[b] - E.phi[a] * E.phr[b];
+}
 
 // Row groups of the enrichment-pair contraction.  z-stage outputs (rows a):
 // 0-2 A u_k, 3 A, 4-6 E u_k, 7-9 B_x u_k, 10-12 C_x u_k, 13-15 B_y u_k,
@@ -143,7 +154,7 @@ __device__ __forceinline__ void sp_xrow(int j, int &i0, int &f0, int &n) {
 
 // one (sub)cell of p^3 points starting at element point qs; STAGED: its Psi
 // rows ([slot][comp][point], pitch P), points and V are in shared memory
-template <bool STAGED>
+template <bool STAGED, bool BLOCH>
 __device__ __forceinline__ void strip_part(const StripElem &E, double *__restrict__ H,
                                            double *__restrict__ S) {
   const int tid = threadIdx.x;
@@ -253,13 +264,30 @@ __device__ __forceinline__ void strip_part(const StripElem &E, double *__restric
         ss = fmaf(L1[a * pm + qx], t2[2], ss);
       }
       const int s_ir = m[i * n + 64 + r], s_ri = m[(64 + r) * n + i];
-      if (E.wantH) {
-        atomicAdd(H + s_ir, (double)hs);
-        atomicAdd(H + s_ri, (double)hs);
-      }
-      if (E.wantS) {
-        atomicAdd(S + s_ir, (double)ss);
-        atomicAdd(S + s_ri, (double)ss);
+      if (BLOCH) {   // (i, r) with conj(ph_i) ph_r, (r, i) with its conjugate
+        float pr, pi;
+        pair_phase(E, E.esh[i], E.esh[64 + r], pr, pi);
+        if (E.wantH) {
+          atomicAdd(H + s_ir, (double)(hs * pr));
+          atomicAdd(E.Hi + s_ir, (double)(hs * pi));
+          atomicAdd(H + s_ri, (double)(hs * pr));
+          atomicAdd(E.Hi + s_ri, (double)(-hs * pi));
+        }
+        if (E.wantS) {
+          atomicAdd(S + s_ir, (double)(ss * pr));
+          atomicAdd(E.Si + s_ir, (double)(ss * pi));
+          atomicAdd(S + s_ri, (double)(ss * pr));
+          atomicAdd(E.Si + s_ri, (double)(-ss * pi));
+        }
+      } else {
+        if (E.wantH) {
+          atomicAdd(H + s_ir, (double)hs);
+          atomicAdd(H + s_ri, (double)hs);
+        }
+        if (E.wantS) {
+          atomicAdd(S + s_ir, (double)ss);
+          atomicAdd(S + s_ri, (double)ss);
+        }
       }
     }
   }
@@ -450,6 +478,7 @@ __device__ __forceinline__ void strip_part(const StripElem &E, double *__restric
   }
 }
 
+template <bool BLOCH>
 __global__ void __launch_bounds__(ST_NT, 2) k_strip_sf(
     const int32_t *__restrict__ order, const int64_t *__restrict__ qoff,
     const int64_t *__restrict__ qpoff, const float4 *__restrict__ qdat,
@@ -460,10 +489,26 @@ __global__ void __launch_bounds__(ST_NT, 2) k_strip_sf(
     const float *__restrict__ psi, const int64_t *__restrict__ soff,
     const int32_t *__restrict__ smap, float sx, float sy, float sz, int pm, int wfloats,
     int sfloats, int eefloats, int what, double *__restrict__ H, double *__restrict__ S,
-    unsigned *err) {
+    unsigned *err, const uint8_t *__restrict__ eshift, PhaseTab ph, double *__restrict__ Hi,
+    double *__restrict__ Si) {
   extern __shared__ float4 sm_st4[];
+  __shared__ float s_phr[8], s_phi[8];
   const int e = order[blockIdx.x], tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   StripElem E;
+  if (BLOCH) {
+    if (tid == 0) {
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        s_phr[c] = (float)ph.re[c];
+        s_phi[c] = (float)ph.im[c];
+      }
+    }
+    E.esh = eshift + doff[e];
+    E.phr = s_phr;
+    E.phi = s_phi;
+    E.Hi = Hi;
+    E.Si = Si;
+  }
   E.n = (int)(doff[e + 1] - doff[e]);
   E.ne = E.n - 64;
   if (E.ne <= 0) return;   // FE-only element: no strip
@@ -620,9 +665,9 @@ __global__ void __launch_bounds__(ST_NT, 2) k_strip_sf(
       f1[5 * pm] = l1;
     }
     if (staged)
-      strip_part<true>(E, H, S);
+      strip_part<true, BLOCH>(E, H, S);
     else
-      strip_part<false>(E, H, S);
+      strip_part<false, BLOCH>(E, H, S);
   }
   __syncthreads();
   // ---- E x E into the FP64 CSR values, both triangles ---------------------------
@@ -657,8 +702,22 @@ __global__ void __launch_bounds__(ST_NT, 2) k_strip_sf(
       h = fmaf(hz * pz, P[171 + (cz * 3 + ky) * 3 + kx], h);
       h = fmaf(hz * qz, P[153 + (bz * 3 + ky) * 3 + kx], h);
       const int slot = E.m[(64 + r) * E.n + 64 + sc];
-      if (E.wantH) atomicAdd(H + slot, (double)(h * (1.0f / 64.0f)));
-      if (E.wantS) atomicAdd(S + slot, (double)(P[kzy * 3 + kx] * (1.0f / 64.0f)));
+      const float hv = h * (1.0f / 64.0f), sv = P[kzy * 3 + kx] * (1.0f / 64.0f);
+      if (BLOCH) {
+        float pr, pi;
+        pair_phase(E, E.esh[64 + r], E.esh[64 + sc], pr, pi);
+        if (E.wantH) {
+          atomicAdd(H + slot, (double)(hv * pr));
+          atomicAdd(E.Hi + slot, (double)(hv * pi));
+        }
+        if (E.wantS) {
+          atomicAdd(S + slot, (double)(sv * pr));
+          atomicAdd(E.Si + slot, (double)(sv * pi));
+        }
+      } else {
+        if (E.wantH) atomicAdd(H + slot, (double)hv);
+        if (E.wantS) atomicAdd(S + slot, (double)sv);
+      }
     }
     return;
   }
@@ -666,8 +725,22 @@ __global__ void __launch_bounds__(ST_NT, 2) k_strip_sf(
     const int r = dne.div(o), sc = o - r * ne;
     const int lo = min(r, sc), hi = max(r, sc);
     const int slot = E.m[(64 + r) * E.n + 64 + sc];
-    if (E.wantH) atomicAdd(H + slot, (double)E.HE[lo * ne8 + hi]);
-    if (E.wantS) atomicAdd(S + slot, (double)E.SE[lo * ne8 + hi]);
+    if (BLOCH) {
+      float pr, pi;
+      pair_phase(E, E.esh[64 + r], E.esh[64 + sc], pr, pi);
+      const float hv = E.HE[lo * ne8 + hi], sv = E.SE[lo * ne8 + hi];
+      if (E.wantH) {
+        atomicAdd(H + slot, (double)(hv * pr));
+        atomicAdd(E.Hi + slot, (double)(hv * pi));
+      }
+      if (E.wantS) {
+        atomicAdd(S + slot, (double)(sv * pr));
+        atomicAdd(E.Si + slot, (double)(sv * pi));
+      }
+    } else {
+      if (E.wantH) atomicAdd(H + slot, (double)E.HE[lo * ne8 + hi]);
+      if (E.wantS) atomicAdd(S + slot, (double)E.SE[lo * ne8 + hi]);
+    }
   }
 }
 
@@ -688,8 +761,10 @@ static int strip_work_floats(uint32_t pmask, int ne8) {
   return (w + 3) & ~3;
 }
 
-pufe_status launch_strip_sf(pufe_ctx *ctx, const double *V, int what, double *H, double *S,
-                            int first, int count, cudaStream_t st) {
+// ph == nullptr: Gamma point; else the Bloch scatter into (H, Hi), (S, Si)
+static pufe_status strip_launch(pufe_ctx *ctx, const double *V, int what, double *H, double *S,
+                                int first, int count, cudaStream_t st, const PhaseTab *ph,
+                                double *Hi, double *Si) {
   if (count <= 0) return PUFE_OK;
   auto &D = ctx->d;
   int ne8 = 8;
@@ -703,13 +778,55 @@ pufe_status launch_strip_sf(pufe_ctx *ctx, const double *V, int what, double *H,
   const int ee = std::max(2 * ne8 * ne8, 189 * ctx->strip_npair_max);
   const size_t sm = ((size_t)sf + wf + ee + 42 * pm + 64 + 36) * sizeof(float);
   if (sm > 227 * 1024) return fail(PUFE_EINVAL, "strip kernel: shared memory above 227 KB");
-  PUFE_CUDA_TRY(cudaFuncSetAttribute(k_strip_sf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  k_strip_sf<<<(unsigned)count, ST_NT, sm, st>>>(
-      D.order + first, D.qoff, D.qpoff, D.qdat, V, D.partoff, D.part_p, D.part_q, D.doff, D.ecol,
-      D.aoff, D.toff32, D.psi32, D.soff, D.smap, (float)(2.0 / ctx->h[0]),
-      (float)(2.0 / ctx->h[1]), (float)(2.0 / ctx->h[2]), pm, wf, sf, ee, what, H, S, D.err);
+  const float sx = (float)(2.0 / ctx->h[0]), sy = (float)(2.0 / ctx->h[1]),
+              sz = (float)(2.0 / ctx->h[2]);
+  if (ph) {
+    PUFE_CUDA_TRY(cudaFuncSetAttribute(k_strip_sf<true>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_strip_sf<true><<<(unsigned)count, ST_NT, sm, st>>>(
+        D.order + first, D.qoff, D.qpoff, D.qdat, V, D.partoff, D.part_p, D.part_q, D.doff,
+        D.ecol, D.aoff, D.toff32, D.psi32, D.soff, D.smap, sx, sy, sz, pm, wf, sf, ee, what, H, S,
+        D.err, D.eshift, *ph, Hi, Si);
+  } else {
+    PUFE_CUDA_TRY(cudaFuncSetAttribute(k_strip_sf<false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_strip_sf<false><<<(unsigned)count, ST_NT, sm, st>>>(
+        D.order + first, D.qoff, D.qpoff, D.qdat, V, D.partoff, D.part_p, D.part_q, D.doff,
+        D.ecol, D.aoff, D.toff32, D.psi32, D.soff, D.smap, sx, sy, sz, pm, wf, sf, ee, what, H, S,
+        D.err, nullptr, PhaseTab{}, nullptr, nullptr);
+  }
   PUFE_CUDA_TRY(cudaGetLastError());
   return PUFE_OK;
+}
+
+pufe_status launch_strip_sf(pufe_ctx *ctx, const double *V, int what, double *H, double *S,
+                            int first, int count, cudaStream_t st) {
+  return strip_launch(ctx, V, what, H, S, first, count, st, nullptr, nullptr, nullptr);
+}
+
+// Mixed-precision H(k), S(k) (Sec. 4, eqs. bloch, strong): the element blocks
+// are those of the Gamma-point mixed path; the FE-FE blocks (kinetic and
+// overlap constants plus the FP32 V block) are scattered with FP64 phases, the
+// enrichment strip's FP32 blocks with FP32 phases, all into FP64 values.
+pufe_status launch_assemble_mixed_bloch(pufe_ctx *ctx, const PhaseTab &ph, const double *V,
+                                        int what, double *H, double *Hi, double *S, double *Si,
+                                        cudaStream_t st) {
+  if (!ctx->fe_exact)
+    return fail(PUFE_EINVAL, "PUFE_TF32X3 needs every (sub)cell rule to have >= 4 points per axis");
+  if (ctx->n_big > 0) return fail(PUFE_EINVAL, "the mixed Bloch assembly takes n_e <= 128");
+  const size_t bytes = (size_t)ctx->nnz * sizeof(double);
+  if (what & PUFE_WANT_H) {
+    PUFE_CUDA_TRY(cudaMemsetAsync(H, 0, bytes, st));
+    PUFE_CUDA_TRY(cudaMemsetAsync(Hi, 0, bytes, st));
+  }
+  if (what & PUFE_WANT_S) {
+    PUFE_CUDA_TRY(cudaMemsetAsync(S, 0, bytes, st));
+    PUFE_CUDA_TRY(cudaMemsetAsync(Si, 0, bytes, st));
+  }
+  pufe_status e0 = launch_fefe_bloch(ctx, ph, V, what, H, Hi, S, Si, st);
+  if (e0 != PUFE_OK) return e0;
+  return strip_launch(ctx, (what & PUFE_WANT_H) ? V : nullptr, what, H, S, 0, (int)ctx->nelem, st,
+                      &ph, Hi, Si);
 }
 
 // ---------------------------------------------------------------------------

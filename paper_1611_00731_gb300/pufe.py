@@ -121,7 +121,7 @@ def load_library(build_if_missing: bool = True):
     lib.pufe_nonlocal_projections.argtypes = [vp, C.c_int, C.POINTER(Projector), vp, vp]
     lib.pufe_nonlocal_projections_bloch.argtypes = [vp, dp, C.c_int, C.POINTER(Projector), vp,
                                                     vp, vp]
-    lib.pufe_assemble_HS_bloch.argtypes = [vp, dp, vp, C.c_int, vp, vp, vp, vp, vp]
+    lib.pufe_assemble_HS_bloch.argtypes = [vp, dp, vp, C.c_int, C.c_int, vp, vp, vp, vp, vp]
     lib.pufe_density_bloch.argtypes = [vp, dp, vp, vp, C.c_int64, vp, C.c_int, vp, vp]
     lib.pufe_assemble_HV_adjoint_bloch.argtypes = [vp, dp, vp, vp, vp, vp]
     lib.pufe_destroy.argtypes = [vp]
@@ -266,7 +266,8 @@ class Context:
                                   C.byref(info), _stream(stream)))
         return f, info.as_dict()
 
-    def pufe_assemble_HS_bloch(self, k, V, H=None, S=None, what=None, stream=None):
+    def pufe_assemble_HS_bloch(self, k, V, H=None, S=None, what=None, stream=None,
+                               prec=PUFE_FP64):
         """H(k), S(k) at wavevector k: H and S are (re, im) pairs of nnz tensors."""
         import torch
         kk = (C.c_double * 3)(*[float(x) for x in k])
@@ -275,7 +276,8 @@ class Context:
         Hr, Hi = H if H is not None else (None, None)
         Sr, Si = S if S is not None else (None, None)
         f64 = torch.float64
-        _check(_LIB.pufe_assemble_HS_bloch(self._h, kk, _ptr(V, f64), int(what), _ptr(Hr, f64),
+        _check(_LIB.pufe_assemble_HS_bloch(self._h, kk, _ptr(V, f64), int(prec), int(what),
+                                           _ptr(Hr, f64),
                                            _ptr(Hi, f64), _ptr(Sr, f64), _ptr(Si, f64),
                                            _stream(stream)))
 

@@ -102,3 +102,52 @@ def test_empty_lattice_bands_at_k_on_the_gpu():
     exact = np.sort(0.5 * ((G + k) ** 2).sum(axis=1))[:4]
     assert np.all(w >= exact - 1e-12)
     assert np.abs(w - exact).max() < 2e-4 * exact[1]     # tricubic error at h = 1 bohr
+
+
+# ---- mixed precision (PUFE_TF32X3): FP32 element blocks, phased scatter -----
+TOL_TF32 = 3e-5     # the Gamma-point mixed bound (tests/test_gpu_parity.py)
+
+MIXED_CASES = {
+    "two_atom_2cube": lambda: W.small_two_atom(nel=2, quad_p=6),
+    "c1_two_atom_4cube": lambda: W.workload("c1_two_atom_4cube"),
+}
+
+
+@pytest.mark.parametrize("name", list(MIXED_CASES))
+def test_mixed_bloch_assembly_matches_oracle(name):
+    """H(k), S(k) of the mixed path against the oracle's FP64 ones; k = 0
+    against the Gamma-point mixed assembly; the C1 band energies at k within
+    the 1e-5 Ha eigenvalue target."""
+    wl = MIXED_CASES[name]()
+    m = omesh.Mesh(wl)
+    rules = oq.all_rules(m)
+    ctx = pufe.pufe_build_mesh(wl)
+    ctx.pufe_tabulate(pufe.PUFE_TF32X3)
+    dev = torch.device("cuda:0")
+    k = 2.0 * math.pi / wl["a"] * K_FRAC
+    V = W.random_potential(len(rules[1]), seed=23)
+    Vd = torch.tensor(V, device=dev)
+    mk = lambda: torch.empty(ctx.nnz, dtype=torch.float64, device=dev)
+    Hr, Hi, Sr, Si = mk(), mk(), mk(), mk()
+    ctx.pufe_assemble_HS_bloch(k, Vd, (Hr, Hi), (Sr, Si), prec=pufe.PUFE_TF32X3)
+    ctx.pufe_sync_status()
+    rowptr, col = ctx.pattern()
+    N = ctx.n_dof
+    csr = lambda re, im: sp.csr_matrix((re.cpu().numpy() + 1j * im.cpu().numpy(), col, rowptr),
+                                       shape=(N, N))
+    Hg, Sg = csr(Hr, Hi), csr(Sr, Si)
+    Ho, So = ob.assemble_HS_k(m, rules, V, k)
+    assert _rel(Hg, Ho) < TOL_TF32 and _rel(Sg, So) < TOL_TF32, (_rel(Hg, Ho), _rel(Sg, So))
+    assert abs(Hg - Hg.conj().T).max() < TOL_TF32 * abs(Hg).max()
+    if name == "c1_two_atom_4cube":
+        wg = sla.eigh(Hg.toarray(), Sg.toarray(), eigvals_only=True, subset_by_index=[0, 3])
+        wo = sla.eigh(Ho.toarray(), So.toarray(), eigvals_only=True, subset_by_index=[0, 3])
+        assert np.abs(wg - wo).max() < 1e-5
+    # k = 0: the Gamma-point mixed matrices, imaginary parts zero
+    H0, S0 = mk(), mk()
+    ctx.pufe_assemble_HS(Vd, H0, S0, prec=pufe.PUFE_TF32X3)
+    ctx.pufe_assemble_HS_bloch((0.0, 0.0, 0.0), Vd, (Hr, Hi), (Sr, Si), prec=pufe.PUFE_TF32X3)
+    ctx.pufe_sync_status()
+    assert float(Hi.abs().max()) == 0.0 and float(Si.abs().max()) == 0.0
+    assert _rel(Hr.cpu().numpy(), H0.cpu().numpy()) < 1e-6
+    assert _rel(Sr.cpu().numpy(), S0.cpu().numpy()) < 1e-6
