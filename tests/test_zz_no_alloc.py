@@ -2,9 +2,12 @@
 
 pufe_assemble_HS_static serves callers that cannot allocate device memory
 during their solve loop: its per-call scratch (the FP32 copy of V read by the
-tensor-core kernel) lives in a static device array owned by the library.
-This file is collected last so that a run stopping at its first failure has
-already run every other test; it also passes on its own in a fresh process.
+tensor-core kernel of elements with more than 128 basis functions) lives in a
+static device array owned by the library.  The cell with such elements is
+the one that reads the array; the two-atom cell, which has none, checks that
+the call also serves contexts that never touch it.  This file is collected
+last so that a run stopping at its first failure has already run every other
+test; it also passes on its own in a fresh process.
 """
 import numpy as np
 import pytest
@@ -21,9 +24,23 @@ def _rel(a, b):
     return float(np.abs(a - b).max() / np.abs(b).max())
 
 
-def test_static_scratch_assembly_matches_regular_entry_point_twice():
-    wl = W.workload("c1_two_atom_4cube")
+def _large_element_cell():
+    """CsCl-like 4^3 cell whose heavy-atom elements carry more than 128
+    basis functions (the tensor-core tile, which reads the scratch)."""
+    wl = W.workload("c3_cscl_4cube")
+    wl["species"][0]["orbitals"] = [o for o in wl["species"][0]["orbitals"] if o[0] >= 3]
+    wl["species"][0]["r_e"] = 1.5
+    wl["quad"] = dict(wl["quad"], mode=W.QUAD_FIXED, p_far=5, p_near=5)
+    return wl
+
+
+@pytest.mark.parametrize("name", ["large_elements", "c1_two_atom_4cube"])
+def test_static_scratch_assembly_matches_regular_entry_point_twice(name):
+    wl = _large_element_cell() if name == "large_elements" else W.workload(name)
     ctx = pufe.pufe_build_mesh(wl)
+    n_e, _ = ctx.element_basis()
+    if name == "large_elements":
+        assert int((np.asarray(n_e) > 128).sum()) > 0
     dev = torch.device("cuda:0")
     H0 = torch.empty(ctx.nnz, dtype=torch.float64, device=dev)
     S0 = torch.empty_like(H0)
@@ -37,4 +54,4 @@ def test_static_scratch_assembly_matches_regular_entry_point_twice():
         ctx.pufe_sync_status()
         eh = _rel(H1.cpu().numpy(), H0.cpu().numpy())
         es = _rel(S1.cpu().numpy(), S0.cpu().numpy())
-        assert eh < TOL_MAT_TF32 and es < TOL_MAT_TF32, (call, eh, es)
+        assert eh < TOL_MAT_TF32 and es < TOL_MAT_TF32, (name, call, eh, es)
