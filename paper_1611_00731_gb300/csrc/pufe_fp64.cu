@@ -106,11 +106,14 @@ __global__ void __launch_bounds__(ASM_NT) k_assemble_fp64(
     const double *__restrict__ V, double sx, double sy, double sz, int npad_max, int want,
     double *__restrict__ H, double *__restrict__ S, unsigned *err,
     const uint8_t *__restrict__ eshift, PhaseTab ph, double *__restrict__ Hi,
-    double *__restrict__ Si) {
+    double *__restrict__ Si, const int32_t *__restrict__ wsplit) {
   extern __shared__ __align__(16) double smem[];
-  const int e = order[blockIdx.x];
+  // work item: a whole element, or the point range [qa, qb) of one
+  const int e = wsplit ? wsplit[3 * blockIdx.x] : order[blockIdx.x];
   const int64_t q0 = qoff[e];
   const int Q = (int)(qoff[e + 1] - q0);
+  const int qa = wsplit ? max(wsplit[3 * blockIdx.x + 1], 0) : 0;
+  const int qb = wsplit ? min(wsplit[3 * blockIdx.x + 2], Q) : Q;
   const int n = (int)(doff[e + 1] - doff[e]);
   const int npad = (n + 3) & ~3;
   if (npad > npad_max) {
@@ -144,13 +147,13 @@ __global__ void __launch_bounds__(ASM_NT) k_assemble_fp64(
 #pragma unroll
       for (int b = 0; b < 4; ++b) h[a][b] = sv[a][b] = 0.0;
 
-    for (int qc = 0; qc < Q; qc += QC) {
+    for (int qc = qa; qc < qb; qc += QC) {
       __syncthreads();
       // 1D Lagrange tables of the chunk's points
       for (int k = threadIdx.x; k < QC * 3; k += ASM_NT) {
         const int qq = k / 3, d = k - 3 * qq;
         const int q = qc + qq;
-        const double xv = (q < Q) ? xi_all[3 * (q0 + q) + d] : 0.0;
+        const double xv = (q < qb) ? xi_all[3 * (q0 + q) + d] : 0.0;
         double L[4], dL[4];
         lagrange3(xv, L, dL);
 #pragma unroll
@@ -164,7 +167,7 @@ __global__ void __launch_bounds__(ASM_NT) k_assemble_fp64(
         const int qq = k / npad, c = k - qq * npad;
         const int q = qc + qq;
         double b = 0, gx = 0, gy = 0, gz = 0, sw = 0, vv = 0;
-        if (q < Q && c < n) {
+        if (q < qb && c < n) {
           if (c < 64) {
             fe_column(tab[qq], c, s, b, gx, gy, gz);
           } else {
@@ -188,7 +191,7 @@ __global__ void __launch_bounds__(ASM_NT) k_assemble_fp64(
       }
       __syncthreads();
       if (active) {
-        const int qn = min(QC, Q - qc);
+        const int qn = min(QC, qb - qc);
         for (int qq = 0; qq < qn; ++qq) {
           const int ro = qq * npad;
           double ai[5][4], bj[4][4];
@@ -383,11 +386,15 @@ __global__ void __launch_bounds__(ADJ_NT) k_adjoint_fp64(
     const int64_t *__restrict__ toff, const double *__restrict__ psi,
     const int64_t *__restrict__ soff, const int32_t *__restrict__ smap,
     const double *__restrict__ Hbar, int hs_in_smem, double *__restrict__ Vbar,
-    const uint8_t *__restrict__ eshift, PhaseTab ph, const double *__restrict__ Hbi) {
+    const uint8_t *__restrict__ eshift, PhaseTab ph, const double *__restrict__ Hbi,
+    const int32_t *__restrict__ wsplit) {
   extern __shared__ __align__(16) double smem[];
-  const int e = order[blockIdx.x];
+  // work item: a whole element, or the point range [qa, qb) of one
+  const int e = wsplit ? wsplit[3 * blockIdx.x] : order[blockIdx.x];
   const int64_t q0 = qoff[e];
   const int Q = (int)(qoff[e + 1] - q0);
+  const int qa = wsplit ? max(wsplit[3 * blockIdx.x + 1], 0) : 0;
+  const int qb = wsplit ? min(wsplit[3 * blockIdx.x + 2], Q) : Q;
   const int n = (int)(doff[e + 1] - doff[e]);
   const int32_t *ec = ecol + (doff[e] - 64ll * e);
   const double *pe = psi + 4 * toff[e];
@@ -411,12 +418,12 @@ __global__ void __launch_bounds__(ADJ_NT) k_adjoint_fp64(
   if (hs_in_smem)
     for (int k = threadIdx.x; k < n * n; k += ADJ_NT) Hs[k] = hval(k / n, k % n);
   const double s[3] = {0, 0, 0};
-  for (int qc = 0; qc < Q; qc += QC) {
+  for (int qc = qa; qc < qb; qc += QC) {
     __syncthreads();
     for (int k = threadIdx.x; k < QC * 3; k += ADJ_NT) {
       const int qq = k / 3, d = k - 3 * qq;
       const int q = qc + qq;
-      const double xv = (q < Q) ? xi_all[3 * (q0 + q) + d] : 0.0;
+      const double xv = (q < qb) ? xi_all[3 * (q0 + q) + d] : 0.0;
       double L[4], dL[4];
       lagrange3(xv, L, dL);
 #pragma unroll
@@ -431,7 +438,7 @@ __global__ void __launch_bounds__(ADJ_NT) k_adjoint_fp64(
       const int qq = k / n, c = k - qq * n;
       const int q = qc + qq;
       double b = 0, gx, gy, gz;
-      if (q < Q) {
+      if (q < qb) {
         if (c < 64) {
           fe_column(tab[qq], c, s, b, gx, gy, gz);
         } else {
@@ -449,7 +456,7 @@ __global__ void __launch_bounds__(ADJ_NT) k_adjoint_fp64(
     __syncthreads();
     for (int k = threadIdx.x; k < QC * n; k += ADJ_NT) {
       const int qq = k / n, i = k - qq * n;
-      if (qc + qq >= Q) continue;
+      if (qc + qq >= qb) continue;
       const double *brow = Bc + qq * n;
       double t = 0.0;
       if (hs_in_smem) {
@@ -461,7 +468,7 @@ __global__ void __launch_bounds__(ADJ_NT) k_adjoint_fp64(
       atomicAdd(acc + qq, brow[i] * t);
     }
     __syncthreads();
-    if (threadIdx.x < QC && qc + (int)threadIdx.x < Q)
+    if (threadIdx.x < QC && qc + (int)threadIdx.x < qb)
       Vbar[q0 + qc + threadIdx.x] = w[q0 + qc + threadIdx.x] * acc[threadIdx.x];
   }
 }
@@ -615,6 +622,12 @@ pufe_status launch_tabulate(pufe_ctx *ctx, cudaStream_t st) {
   return PUFE_OK;
 }
 
+// CTAs of the FP64 assembly and adjoint: one per work item of the point-range
+// list when the setup made one, else one per element
+static unsigned fp64_items(const pufe_ctx *ctx) {
+  return ctx->d.wsplit ? (unsigned)ctx->n_wsplit : (unsigned)ctx->nelem;
+}
+
 pufe_status launch_assemble_fp64(pufe_ctx *ctx, const double *V, int what, double *H, double *S,
                                  cudaStream_t st) {
   auto &D = ctx->d;
@@ -623,10 +636,10 @@ pufe_status launch_assemble_fp64(pufe_ctx *ctx, const double *V, int what, doubl
   if (sm > 227 * 1024) return fail(PUFE_EINVAL, "element basis too large for the FP64 kernel");
   PUFE_CUDA_TRY(cudaFuncSetAttribute(k_assemble_fp64<false>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  k_assemble_fp64<false><<<(unsigned)ctx->nelem, ASM_NT, sm, st>>>(
+  k_assemble_fp64<false><<<fp64_items(ctx), ASM_NT, sm, st>>>(
       D.order, D.qoff, D.w, D.xi, D.doff, D.ecol, D.toff, D.psi, D.soff, D.smap, V,
       2.0 / ctx->h[0], 2.0 / ctx->h[1], 2.0 / ctx->h[2], npad, what, H, S, D.err, nullptr,
-      PhaseTab{}, nullptr, nullptr);
+      PhaseTab{}, nullptr, nullptr, D.wsplit);
   PUFE_CUDA_TRY(cudaGetLastError());
   return PUFE_OK;
 }
@@ -655,9 +668,9 @@ pufe_status launch_adjoint_fp64(pufe_ctx *ctx, const double *Hbar, double *Vbar,
   if (in_smem) sm += hs;
   PUFE_CUDA_TRY(cudaFuncSetAttribute(k_adjoint_fp64<false>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  k_adjoint_fp64<false><<<(unsigned)ctx->nelem, ADJ_NT, sm, st>>>(
+  k_adjoint_fp64<false><<<fp64_items(ctx), ADJ_NT, sm, st>>>(
       D.order, D.qoff, D.w, D.xi, D.doff, D.ecol, D.toff, D.psi, D.soff, D.smap, Hbar, in_smem,
-      Vbar, nullptr, PhaseTab{}, nullptr);
+      Vbar, nullptr, PhaseTab{}, nullptr, D.wsplit);
   PUFE_CUDA_TRY(cudaGetLastError());
   return PUFE_OK;
 }
@@ -686,10 +699,10 @@ pufe_status launch_assemble_fp64_bloch(pufe_ctx *ctx, const PhaseTab &ph, const 
   if (sm > 227 * 1024) return fail(PUFE_EINVAL, "element basis too large for the FP64 kernel");
   PUFE_CUDA_TRY(cudaFuncSetAttribute(k_assemble_fp64<true>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  k_assemble_fp64<true><<<(unsigned)ctx->nelem, ASM_NT, sm, st>>>(
+  k_assemble_fp64<true><<<fp64_items(ctx), ASM_NT, sm, st>>>(
       D.order, D.qoff, D.w, D.xi, D.doff, D.ecol, D.toff, D.psi, D.soff, D.smap, V,
       2.0 / ctx->h[0], 2.0 / ctx->h[1], 2.0 / ctx->h[2], npad, what, H, S, D.err, D.eshift, ph,
-      Hi, Si);
+      Hi, Si, D.wsplit);
   PUFE_CUDA_TRY(cudaGetLastError());
   return PUFE_OK;
 }
@@ -720,9 +733,9 @@ pufe_status launch_adjoint_fp64_bloch(pufe_ctx *ctx, const PhaseTab &ph, const d
   if (in_smem) sm += hs;
   PUFE_CUDA_TRY(cudaFuncSetAttribute(k_adjoint_fp64<true>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  k_adjoint_fp64<true><<<(unsigned)ctx->nelem, ADJ_NT, sm, st>>>(
+  k_adjoint_fp64<true><<<fp64_items(ctx), ADJ_NT, sm, st>>>(
       D.order, D.qoff, D.w, D.xi, D.doff, D.ecol, D.toff, D.psi, D.soff, D.smap, Hr, in_smem,
-      Vbar, D.eshift, ph, Hi);
+      Vbar, D.eshift, ph, Hi, D.wsplit);
   PUFE_CUDA_TRY(cudaGetLastError());
   return PUFE_OK;
 }

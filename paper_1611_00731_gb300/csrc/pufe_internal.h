@@ -97,6 +97,9 @@ struct DeviceArrays {
   int32_t *smap = nullptr;    // CSR slot of each local pair (i, j), row-major
   // work list: elements sorted by (n_e, Q_e) class, largest first
   int32_t *order = nullptr;   // nelem
+  // FP64 assembly/adjoint work list, 3 per item (element, first point, end
+  // point), largest first; null when every item is a whole element
+  int32_t *wsplit = nullptr;
   unsigned *err = nullptr;    // device error flag
   // side stream and events: the FE-FE kernel of the mixed assembly runs on
   // `side`, forked from and joined back into the caller's stream
@@ -125,6 +128,7 @@ struct pufe_ctx {
   bool tabulated32 = false;   // FP32 enrichment table is current
   bool fe_exact = false;      // every rule has >= 4 points per axis per (sub)cell
   int n_big = 0;              // elements with n_e > 128 (listed first in `order`)
+  int64_t n_wsplit = 0;       // items of the FP64 point-range work list (0: none)
   int max_part_p = 0;         // largest points-per-axis of any (sub)cell
   int strip_stage = 0;        // floats of the strip kernel's shared-memory stage
   uint32_t strip_pmask = 0;   // per-axis counts (bit p) of the strip kernel's cells

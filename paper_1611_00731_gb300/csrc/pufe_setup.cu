@@ -696,6 +696,68 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
     PUFE_CUDA_TRY(cudaGetDevice(&ctx->device));
     ctx->on_device = true;
   }
+  // ---- FP64 work list ---------------------------------------------------------
+  // The FP64 assembly and adjoint take one CTA per work item.  An element
+  // whose cost Q_e * npad_e^2 exceeds the mean cost of a CTA slot (two per
+  // SM) is cut into point ranges: multiples of 8 points (the kernels' chunk),
+  // at least 64 points each.  The ranges' partial element matrices meet in
+  // the atomic scatter; the adjoint's ranges write disjoint points.  Items
+  // run largest first.  No list (one CTA per element, in `order`) when no
+  // element is cut.
+  std::vector<int32_t> wsplit;
+  {
+    int nsm = 152;
+    if (ctx->on_device) {
+      int v = 0;
+      if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, ctx->device) == cudaSuccess &&
+          v > 0)
+        nsm = v;
+    }
+    auto cost = [&](int64_t e, int64_t npts) {
+      const int64_t np = (n_e[e] + 3) & ~3;
+      return (double)npts * (double)(np * np);
+    };
+    double total = 0.0;
+    for (int64_t e = 0; e < nelem; ++e) total += cost(e, q_e[e]);
+    const double cmax = std::max(1.0, total / (2.0 * nsm));
+    struct Item {
+      int32_t e, qa, qb;
+      double c;
+    };
+    std::vector<Item> items;
+    bool cut = false;
+    for (int64_t e = 0; e < nelem; ++e) {
+      const int32_t Q = q_e[e];
+      int m = (int)std::min<double>(std::ceil(cost(e, Q) / cmax), 1e6);
+      m = std::max(1, std::min(m, Q / 64));
+      if (m > 1) cut = true;
+      int32_t prev = 0;
+      for (int j = 1; j <= m; ++j) {
+        const int32_t b = (j == m) ? Q : (int32_t)(((int64_t)j * Q / m) & ~(int64_t)7);
+        items.push_back(Item{(int32_t)e, prev, b, cost(e, b - prev)});
+        prev = b;
+      }
+    }
+    if (cut) {
+      std::stable_sort(items.begin(), items.end(),
+                       [](const Item &x, const Item &y) { return x.c > y.c; });
+      // every element's points covered exactly once, in ranges inside [0, Q_e)
+      std::vector<int64_t> covered(nelem, 0);
+      for (const Item &it : items) {
+        if (it.qa < 0 || it.qb <= it.qa || it.qb > q_e[it.e])
+          return fail(PUFE_EINVAL, "internal: bad point range in the FP64 work list");
+        covered[it.e] += it.qb - it.qa;
+        wsplit.push_back(it.e);
+        wsplit.push_back(it.qa);
+        wsplit.push_back(it.qb);
+      }
+      for (int64_t e = 0; e < nelem; ++e)
+        if (covered[e] != q_e[e])
+          return fail(PUFE_EINVAL, "internal: the FP64 work list misses points");
+    }
+  }
+  ctx->n_wsplit = (int64_t)(wsplit.size() / 3);
+
   pufe_status st;
   auto &D = ctx->d;
   if (ctx->on_device) {
@@ -724,6 +786,7 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
   if ((st = upload(&D.soff, soff)) != PUFE_OK) return st;
   if ((st = upload(&D.smap, smap)) != PUFE_OK) return st;
   if ((st = upload(&D.order, order)) != PUFE_OK) return st;
+  if (!wsplit.empty() && (st = upload(&D.wsplit, wsplit)) != PUFE_OK) return st;
   if (fe_exact) {
     if ((st = upload(&D.Tfe, TF)) != PUFE_OK) return st;
     if ((st = upload(&D.Sfe, SF)) != PUFE_OK) return st;
@@ -766,7 +829,7 @@ static void free_device(pufe_ctx *ctx) {
   void *ptrs[] = {D.qoff, D.x, D.w, D.xi, D.doff, D.dofs, D.ecol, D.eshift, D.aoff, D.alist,
                   D.toff, D.psi, D.psi32, D.qpoff, D.qdat, D.ptab, D.vpad, D.toff32, D.eorig,
                   D.Tfe, D.Sfe, D.S0, D.partoff, D.part_p, D.part_q,
-                  D.orb, D.orbf, D.rowptr, D.col, D.soff, D.smap, D.order, D.err};
+                  D.orb, D.orbf, D.rowptr, D.col, D.soff, D.smap, D.order, D.wsplit, D.err};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (D.ev_fork) cudaEventDestroy(D.ev_fork);
