@@ -44,6 +44,24 @@ def _dist():
     return ws, rank, local
 
 
+def _max_over_ranks(vals, device):
+    """Each value's maximum over the ranks of the process group (the job's
+    time is its slowest rank's); the values themselves on one rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return [float(v) for v in vals]
+    t = torch.tensor([float(v) for v in vals], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.cpu()]
+
+
+def _job_rate(ws, units_per_rank, steps, ms):
+    """Whole-job throughput: the units every rank processed over `steps`
+    steps, divided by the (slowest rank's) time in milliseconds."""
+    return ws * units_per_rank * steps / (ms * 1e-3)
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -394,15 +412,12 @@ def run_pufe(args):
                if args.scf and args.prec != "fp64" else None)
 
     if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms, e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms, e2e_ms = float(t[0]), float(t[1])
+        total_ms, e2e_ms = _max_over_ranks([total_ms, e2e_ms], dev)
     if rank != 0:
         return None
 
     ms_per_step = total_ms / args.steps
-    value = ws * ctx.n_q * args.steps / (total_ms * 1e-3)
+    value = _job_rate(ws, ctx.n_q, args.steps, total_ms)
     peaks, src = _peaks()
     asm_avg = statistics.mean(asm_ms)
     achieved = flops_asm / (asm_avg * 1e-3) / 1e12
@@ -448,7 +463,7 @@ def run_pufe(args):
                    "density_stream": args.density_stream,
                    "parallelism": f"replicas x{ws}", "build_s": round(build_s, 3)},
         "roofline": roof,
-        "e2e": {"value": ws * ctx.n_q * args.steps / (e2e_ms * 1e-3), "unit": UNIT,
+        "e2e": {"value": _job_rate(ws, ctx.n_q, args.steps, e2e_ms), "unit": UNIT,
                 "h2d_bytes_per_step": int(V_h.numel() * 8 + C_h.numel() * 8 + f_h.numel() * 8),
                 "d2h_bytes_per_step": int(rho_h.numel() * 8)},
         "gpu_launches": launches_per_step * args.steps,
