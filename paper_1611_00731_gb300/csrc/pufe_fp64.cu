@@ -87,11 +87,14 @@ __device__ __forceinline__ void pu_column(const double xi[3], int lv, const doub
 }
 
 // ---------------------------------------------------------------------------
-// K1+K2+K3 (FP64): one CTA per element.  Per chunk of QC points the CTA
-// builds y_d = sqrt(w/2) G_d, z = sqrt(w) B and zv = V z in shared memory;
-// each thread owns 4x4 blocks of the lower triangle and accumulates
+// K1+K2+K3 (FP64): one CTA per work item -- an element, or with the setup's
+// point-range list (`wsplit`) the points [qa, qb) of one.  Per chunk of QC
+// points the CTA builds y_d = sqrt(w/2) G_d, z = sqrt(w) B and zv = V z in
+// shared memory; each thread owns 4x4 blocks of the lower triangle and
+// accumulates
 //   H += sum_d y_d y_d^T + zv z^T,   S += z z^T,
-// then adds its entries into the CSR values through the scatter map.
+// over the item's points, then adds its entries into the CSR values through
+// the scatter map (the ranges of one element meet in these atomics).
 // ---------------------------------------------------------------------------
 // BLOCH: the scatter carries the phase exp(i k.(R_j - R_i)) of the column
 // pair (lattice shifts from `eshift`, phases of the 8 shift codes in `ph`)
@@ -371,10 +374,11 @@ __global__ void __launch_bounds__(DEN_NT) k_density_fp64(
 }
 
 // ---------------------------------------------------------------------------
-// K5 (FP64): Vbar_q = w_q b_q^T Hbar_e b_q.  One CTA per element: the element
-// block Hbar_e is gathered into shared memory (or read through the scatter
-// map when it does not fit); per chunk of QC points the basis rows are built
-// in shared memory and each thread reduces one (q, i) pair over j.
+// K5 (FP64): Vbar_q = w_q b_q^T Hbar_e b_q.  One CTA per work item (an
+// element, or the point range [qa, qb) of one, as in the assembly): the
+// element block Hbar_e is gathered into shared memory (or read through the
+// scatter map when it does not fit); per chunk of QC points the basis rows are
+// built in shared memory and each thread reduces one (q, i) pair over j.
 // ---------------------------------------------------------------------------
 // BLOCH: complex cotangent Hbar + i Hbi; the element block used is
 // Re(conj(Hbar) exp(i k.(R_j - R_i))) = Hbar pr + Hbi pi.
