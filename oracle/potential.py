@@ -63,3 +63,78 @@ def gaussian_charge(wl, pts):
             r2 = (d * d).sum(axis=1)
             out += sp["Z"] * np.exp(-r2 / sp["sigma"] ** 2) / (math.pi ** 1.5 * sp["sigma"] ** 3)
     return out
+
+
+def ionic_potential_ewald(wl, pts, eta=1.5):
+    """The same V_I, evaluated by Ewald's splitting (Ewald 1921) so that large
+    point sets are affordable.
+
+    Each Gaussian ion's potential -Z erf(r/s)/r is split at a wider Gaussian
+    width eta > s into a short-range part -Z (erf(r/s) - erf(r/eta))/r, summed
+    over images in real space, and -Z erf(r/eta)/r, whose reciprocal sum
+    converges after far fewer G vectors.  The short-range part has the mean
+    -pi Z (eta^2 - s^2) / Omega over the cell (its G = 0 Fourier term); V_I
+    drops every G = 0 term, so that mean is added back with the opposite sign:
+
+        V_I = sum_a [ sum_R -Z_a (erf(r/s_a) - erf(r/eta)) / r
+                      + pi Z_a (eta^2 - s_a^2) / Omega ]
+              - (4 pi / Omega) sum_{G != 0} e^{-G^2 eta^2 / 4} / G^2
+                    Re( e^{i G.x} sum_a Z_a e^{-i G.tau_a} ).
+
+    Real-space terms are kept while erfc(r/eta) > 1e-20 (r < 6.6 eta), the
+    reciprocal ones while e^{-G^2 eta^2/4} > 1e-18.  Pinned against
+    ``ionic_potential`` at random points (tests/test_oracle_misc.py).
+    """
+    from scipy.special import erf
+
+    a = float(wl["a"])
+    Omega = a ** 3
+    pts = np.atleast_2d(np.asarray(pts, dtype=np.float64))
+    out = np.zeros(pts.shape[0])
+    if not wl["atoms"]:
+        return out
+    for _, sp in enumerate(wl["species"]):
+        if wl["atoms"] and sp["sigma"] >= eta:
+            raise ValueError("eta must exceed every sigma")
+    rcut = 6.6 * eta
+    reach = int(math.ceil(rcut / a))
+    rng = np.arange(-reach, reach + 1)
+    R = a * np.array(np.meshgrid(rng, rng, rng, indexing="ij")).reshape(3, -1).T
+    # real space: displacements from the nearest image, then the shells around it
+    for s, tau in wl["atoms"]:
+        sp = wl["species"][s]
+        Z, sg = sp["Z"], sp["sigma"]
+        d0 = pts - np.asarray(tau)
+        d0 -= a * np.round(d0 / a)
+        for r_ in R:
+            d = d0 + r_
+            r = np.sqrt((d * d).sum(axis=1))
+            sel = np.nonzero(r < rcut)[0]
+            if sel.size == 0:
+                continue
+            rs = r[sel]
+            small = rs < 1e-12
+            rs_safe = np.where(small, 1.0, rs)
+            val = np.where(small, 2.0 / math.sqrt(math.pi) * (1.0 / sg - 1.0 / eta),
+                           (erf(rs_safe / sg) - erf(rs_safe / eta)) / rs_safe)
+            out[sel] += -Z * val
+        out += math.pi * Z * (eta ** 2 - sg ** 2) / Omega
+    # reciprocal space with the structure factor of the atoms
+    gmax = math.sqrt(4.0 * 18.0 * math.log(10.0)) / eta
+    mmax = int(math.ceil(gmax * a / (2.0 * math.pi)))
+    rg = np.arange(-mmax, mmax + 1)
+    M = np.array(np.meshgrid(rg, rg, rg, indexing="ij")).reshape(3, -1).T
+    M = M[(M != 0).any(axis=1)]
+    G = (2.0 * math.pi / a) * M.astype(np.float64)
+    G2 = (G * G).sum(axis=1)
+    keep = G2 <= gmax * gmax
+    G, G2 = G[keep], G2[keep]
+    sf = np.zeros(len(G), dtype=np.complex128)
+    for s, tau in wl["atoms"]:
+        sf += wl["species"][s]["Z"] * np.exp(-1j * (G @ np.asarray(tau)))
+    amp = -(4.0 * math.pi / Omega) * np.exp(-G2 * eta ** 2 / 4.0) / G2
+    ar, ai = amp * sf.real, amp * sf.imag
+    for i in range(0, pts.shape[0], 512):
+        phase = pts[i:i + 512] @ G.T
+        out[i:i + 512] += np.cos(phase) @ ar - np.sin(phase) @ ai
+    return out

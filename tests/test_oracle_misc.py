@@ -60,3 +60,15 @@ def test_pu1d_reproduces_enrichment_and_beats_fe():
     _, e_pufe = pu1d.project(u, True)
     _, e_fe = pu1d.project(u, False)
     assert e_pufe < 0.2 * e_fe
+
+
+def test_ewald_split_potential_equals_direct_sum():
+    """The Ewald-split evaluation of V_I (real-space short-range part, mean
+    correction, shorter reciprocal sum) equals the direct reciprocal sum."""
+    for name in ("c1_two_atom_4cube", "c2_rocksalt_12cube"):
+        wl = W.workload(name)
+        x = np.random.default_rng(3).uniform(0, wl["a"], size=(150, 3))
+        v0 = opot.ionic_potential(wl, x)
+        for eta in (1.2, 1.5, 2.0):
+            v1 = opot.ionic_potential_ewald(wl, x, eta)
+            assert np.abs(v1 - v0).max() < 1e-13 * np.abs(v0).max(), (name, eta)
