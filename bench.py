@@ -30,11 +30,11 @@ METRIC = "quadrature-point contractions/s for H/S assembly + density"
 UNIT = "QPC/s"
 L2_BYTES = 129 * 1024 * 1024
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-# DRAM bytes (read + write) of the assembly call's kernels, k_fefe_sumfac +
-# k_strip_sf, per launch, from the ncu capture summarised in
-# profiles/step_mixed_c2_rocksalt_12cube.md; the memset of H and the copy of
-# the overlap constants into S (232 MB by construction) are not counted
-ASM_TRAFFIC = {("c2_rocksalt_12cube", "tf32x3"): 96_017_664 + 170_968_064}
+TF32_PER_BF16 = 1.1 / 2.25      # nominal dense TF32 / BF16 tensor rates
+# DRAM bytes (read + write) per launch of the assembly call's kernels, from
+# the ncu capture summarised under profiles/ (None: the kernels changed since
+# the last capture)
+ASM_TRAFFIC = {}
 
 
 def _dist():
@@ -292,6 +292,20 @@ def run_pufe(args):
     Qe = np.diff(qoff)
     nocc = int(wl["nocc"])
     flops_asm = float(5.0 * (Qe * n_e * (n_e + 1.0)).sum())
+    # the strip's share of the direct count: every pair with an enrichment
+    # column, on the elements the CUDA-core strip takes (64 < n_e <= 128)
+    strip = (n_e > 64) & (n_e <= 128)
+    flops_strip = float(5.0 * (Qe[strip] * (n_e[strip] * (n_e[strip] + 1.0) - 64 * 65)).sum())
+    # algorithmic bytes of the recompute form: per point the
+    # weight, V and 4 values per enrichment slot in FP32, plus H and S once
+    slots = ctx.element_slots()
+    rowptr, col = ctx.pattern()
+    bytes_in = float((Qe * (2.0 + 4.0 * slots)).sum() * 4.0)
+    bytes_out = 2.0 * ctx.nnz * 8.0
+    n_fe = (3 * int(wl["nel"])) ** 3
+    row = np.repeat(np.arange(ctx.n_dof), np.diff(rowptr))
+    nnz_e = int(((row >= n_fe) | (col >= n_fe)).sum())
+    bytes_strip = float((Qe[strip] * (2.0 + 4.0 * slots[strip])).sum() * 4.0) + 2.0 * nnz_e * 8.0
 
     V_h = torch.tensor(W.random_potential(ctx.n_q, seed=rank), dtype=torch.float64).pin_memory()
     C_h = torch.tensor(W.random_coefficients(ctx.n_dof, nocc, seed=rank)).pin_memory()
@@ -378,6 +392,17 @@ def run_pufe(args):
         kb.record(stream)
         kb.synchronize()
         asm_ms.append(ka.elapsed_time(kb))
+    # per-kernel times of the mixed assembly (events around each kernel, on
+    # the stream it runs on; separate calls, so the step timing above is not
+    # instrumented)
+    kern_ms = []
+    if args.prec == "tf32x3":
+        ctx.pufe_profile_assembly(True)
+        for _ in range(max(3, min(args.steps, 10))):
+            flush.fill_(1.0)
+            ctx.pufe_assemble_HS(V, H, S, prec=prec)
+            kern_ms.append(ctx.pufe_profile_read())
+        ctx.pufe_profile_assembly(False)
     barrier()
     clocks = sampler.stop()
     ctx.pufe_sync_status()
@@ -422,6 +447,7 @@ def run_pufe(args):
     asm_avg = statistics.mean(asm_ms)
     achieved = flops_asm / (asm_avg * 1e-3) / 1e12
     n_big = int((n_e > 128).sum())
+    hbm = peaks["hbm_gbs"] * 1e9
     if args.prec == "fp64":
         # FP64 contraction: the recipe's nominal FP64 rate scaled like the
         # measured bf16 figure (measured bf16 x nominal FP64/bf16 ratio)
@@ -430,34 +456,61 @@ def run_pufe(args):
         peak_source = f"{src} bf16 x nominal FP64/bf16 ratio"
         kernels = "k_assemble_fp64"
         launches_per_step = 4
-    elif n_big == 0:
-        # every element takes the CUDA-core strip: FP32 FMA peak of 152 SMs x
-        # 128 FP32 lanes x 2 flops at the 2070 MHz maximum SM clock
-        peak = FP32_PEAK_TFLOPS
-        bound, dtype = "alu", "f32+f64"
-        peak_source = "derived: 152 SM x 128 FP32 FMA/clk x 2 x 2.07 GHz"
-        kernels = "memset + k_fefe_sumfac + S0 copy + k_strip_sf"
-        # tabulate, fefe, strip, density, adjoint_fefe, adjoint_strip
-        launches_per_step = 6
+        prec_label = "fp64"
     else:
-        peak = peaks["bf16_tflops"] * (1.1 / 2.25)   # tf32 dense / bf16 dense nominal
-        bound, dtype = "tensor", "tf32x3+f32+f64"
-        peak_source = f"{src} bf16 x nominal TF32/bf16 ratio"
-        kernels = "memset + k_fefe_sumfac + S0 copy + k_pack_v + k_assemble_tc + k_strip_sf"
-        launches_per_step = 9
+        # the binding roof of the recompute form: the tensor
+        # pipe at three TF32 products per product, or the algorithmic bytes
+        # at the measured HBM rate, whichever is lower
+        tf32x3 = peaks["bf16_tflops"] * TF32_PER_BF16 / 3.0
+        ai = flops_asm / (bytes_in + bytes_out)
+        peak = min(tf32x3, ai * hbm / 1e12)
+        bound = "tensor" if tf32x3 <= ai * hbm / 1e12 else "hbm"
+        dtype = "f32+f64"
+        peak_source = (f"min(TF32x3 = {src} bf16 burst x nominal TF32/bf16 / 3 = {tf32x3:.1f}, "
+                       f"AI x {src} HBM = {ai * hbm / 1e12:.1f}) TFLOP/s")
+        if n_big == 0:
+            kernels = "memset + S0 copy + k_fefe_sumfac + k_see64 + k_strip_sf"
+            # tabulate, fefe, see64, strip, density, adjoint_fefe, adjoint_strip
+            launches_per_step = 7
+            prec_label = "fp32 (CUDA-core strip and FE-FE V block) + fp64 (E-E block of S)"
+        else:
+            kernels = ("memset + S0 copy + k_fefe_sumfac + k_see64 + k_pack_v + "
+                       "k_assemble_tc + k_strip_sf")
+            launches_per_step = 10
+            prec_label = ("tf32x3 tensor-core tile (n_e > 128) + fp32 CUDA-core strip + "
+                          "fp64 (E-E block of S)")
     roof = {"kernel": f"pufe_assemble_HS ({kernels})", "bound": bound, "achieved": achieved,
             "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": ASM_TRAFFIC.get((args.workload, args.prec)),
             "peak_source": peak_source,
             "flops_per_launch": flops_asm, "flops_count": "sum_e 5 Q_e n_e (n_e + 1)",
+            "algorithmic_bytes_per_launch": bytes_in + bytes_out,
+            "bytes_count": "sum_e Q_e (2 + 4 A_e) 4 B in + 2 nnz 8 B out",
             "avg_launch_ms": asm_avg}
-
+    if args.prec != "fp64":
+        roof["fp32_cuda_core_frac"] = achieved / FP32_PEAK_TFLOPS
+        roof["fp32_cuda_core_peak"] = FP32_PEAK_TFLOPS
+    if kern_ms:
+        km = {k: statistics.mean(d[k] for d in kern_ms) for k in kern_ms[0]}
+        t_strip = km["strip"]
+        if t_strip > 0:
+            a_strip = flops_strip / (t_strip * 1e-3) / 1e12
+            ai_s = flops_strip / bytes_strip
+            peak_s = min(peaks["bf16_tflops"] * TF32_PER_BF16 / 3.0, ai_s * hbm / 1e12)
+            roof["dominant_kernel"] = {
+                "kernel": "k_strip_sf", "avg_launch_ms": t_strip, "achieved": a_strip,
+                "peak": peak_s, "frac": a_strip / peak_s, "unit": "TFLOP/s",
+                "fp32_cuda_core_frac": a_strip / FP32_PEAK_TFLOPS,
+                "flops_per_launch": flops_strip,
+                "flops_count": "sum over strip elements of 5 Q_e (n_e (n_e + 1) - 64 * 65)",
+                "algorithmic_bytes_per_launch": bytes_strip}
+        roof["kernel_ms"] = km
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
         "config": {"workload": args.workload, "n_dof": ctx.n_dof, "n_q": ctx.n_q,
-                   "n_elem": ctx.n_elem, "nnz": ctx.nnz, "nocc": nocc, "prec": args.prec,
+                   "n_elem": ctx.n_elem, "nnz": ctx.nnz, "nocc": nocc, "prec": prec_label,
                    "l2": "flushed between steps (2x L2 buffer written)",
                    "launch": "cuda graph of the step" if graph is not None else "stream",
                    "density_stream": args.density_stream,
@@ -484,55 +537,111 @@ def run_pufe(args):
 # --------------------------------------------------------------------------
 # the oracle as the CPU baseline / reference arm
 # --------------------------------------------------------------------------
-_ORACLE_SNIPPET = r"""
-import json, sys, time
-sys.path.insert(0, sys.argv[1])
+_ORACLE_SCRIPT = r"""
+import json, multiprocessing as mp, sys, time
 import numpy as np
-from paper_1611_00731_gb300 import workloads as W
-from oracle import assemble as oasm, mesh as omesh, quadrature as oq
-wl = W.workload(sys.argv[2]); nel = int(sys.argv[3]); steps = int(sys.argv[4])
-m = omesh.Mesh(wl)
-rng = np.random.default_rng(0)
-elems = [int(e) for e in rng.choice(m.nelem, size=min(nel, m.nelem), replace=False)]
-rules = {e: oq.element_rule(m, e) for e in elems}
-C = W.random_coefficients(m.n_dof, wl["nocc"]); f = W.random_occupations(wl["nocc"])
-out = []
-for _ in range(steps):
+
+
+def setup(root, workload, elems):
+    sys.path.insert(0, root)
+    from paper_1611_00731_gb300 import workloads as W
+    from oracle import mesh as omesh, quadrature as oq
+    wl = W.workload(workload)
+    m = omesh.Mesh(wl)
+    rules = {e: oq.element_rule(m, e) for e in elems}
+    C = W.random_coefficients(m.n_dof, wl["nocc"])
+    f = W.random_occupations(wl["nocc"])
+    return m, rules, C, f
+
+
+def one_pass(m, elems, rules, C, f):
+    from paper_1611_00731_gb300 import workloads as W
+    from oracle import assemble as oasm
     nq = 0
-    t0 = time.perf_counter()
     for e in elems:
         p, w = rules[e]
         V = W.random_potential(len(w), seed=e)
-        He, Se = oasm.element_HS(m, e, p, w, V)           # tabulation + basis + H/S
+        He, Se = oasm.element_HS(m, e, p, w, V)             # tabulation + basis + H/S
         B, _ = oasm.element_basis(m, e, p)
         Y = B @ C[m.elem_dofs(e)]
-        rho = (Y * Y) @ f                                  # density
-        vbar = w * np.einsum("qi,ij,qj->q", B, He, B)      # adjoint
+        rho = (Y * Y) @ f                                    # density
+        vbar = w * np.einsum("qi,ij,qj->q", B, He, B)        # adjoint
         nq += len(w)
-    out.append((nq, time.perf_counter() - t0))
-print(json.dumps(out))
+    return nq
+
+
+def worker(root, workload, elems, reps, barrier, queue):
+    m, rules, C, f = setup(root, workload, elems)
+    out = []
+    for _ in range(reps):
+        barrier.wait()                                       # every worker starts together
+        t0 = time.perf_counter()
+        nq = one_pass(m, elems, rules, C, f)
+        out.append((nq, time.perf_counter() - t0))
+    queue.put(out)
+
+
+if __name__ == "__main__":
+    root, workload = sys.argv[1], sys.argv[2]
+    nel, reps, nproc = int(sys.argv[3]), int(sys.argv[4]), int(sys.argv[5])
+    sys.path.insert(0, root)
+    from paper_1611_00731_gb300 import workloads as W
+    from oracle import mesh as omesh
+    nelem = omesh.Mesh(W.workload(workload)).nelem
+    rng = np.random.default_rng(0)
+    elems = [int(e) for e in rng.choice(nelem, size=min(nel * nproc, nelem), replace=False)]
+    ctx = mp.get_context("spawn")
+    barrier, queue = ctx.Barrier(nproc), ctx.Queue()
+    parts = [elems[i::nproc] for i in range(nproc)]
+    procs = [ctx.Process(target=worker, args=(root, workload, parts[i], reps, barrier, queue))
+             for i in range(nproc)]
+    for p in procs:
+        p.start()
+    res = [queue.get() for _ in procs]
+    for p in procs:
+        p.join()
+    # per repetition: points of all workers over the slowest worker's time
+    print(json.dumps([(sum(r[k][0] for r in res), max(r[k][1] for r in res))
+                      for k in range(reps)]))
 """
 
 
-def _oracle_steps(workload, nelem, steps):
+def _oracle_steps(workload, nelem, steps, nproc=1):
+    """Runs the oracle's element loop (element H/S, density, adjoint) on
+    `nelem` random elements per process in `nproc` processes (one thread
+    each), `steps` repetitions; returns (points, seconds) per repetition."""
+    import tempfile
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    r = subprocess.run([sys.executable, "-c", _ORACLE_SNIPPET, ROOT, workload, str(nelem),
-                        str(steps)], capture_output=True, text=True, env=env)
+    with tempfile.NamedTemporaryFile("w", suffix=".py", delete=False) as fh:
+        fh.write(_ORACLE_SCRIPT)
+        script = fh.name
+    try:
+        r = subprocess.run([sys.executable, script, ROOT, workload, str(nelem), str(steps),
+                            str(nproc)], capture_output=True, text=True, env=env)
+    finally:
+        os.unlink(script)
     if r.returncode != 0:
         raise RuntimeError(r.stderr.strip()[-400:])
     return json.loads(r.stdout.strip().splitlines()[-1])
 
 
-def cpu_baseline(workload, nelem):
+def cpu_baseline(workload, nelem, reps=5):
+    """The oracle on the host cores, as it stands: one thread, and one
+    single-threaded process per core; best of `reps` repetitions each."""
+    cores = os.cpu_count() or 1
+    out = {"unit": UNIT, "kind": "oracle", "host_cpu_count": cores}
     try:
-        (nq, sec), = _oracle_steps(workload, nelem, 1)
+        one = max(nq / sec for nq, sec in _oracle_steps(workload, nelem, reps, 1))
+        allc = max(nq / sec for nq, sec in _oracle_steps(workload, nelem, reps, cores))
     except RuntimeError as ex:
-        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
-                "sample": f"failed: {ex}"}
-    return {"value": nq / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{nelem} random elements of {workload} (seed 0): tabulation and "
-                      f"basis, element H/S, density, adjoint; {nq} points in {sec:.1f} s, "
-                      "1 thread"}
+        out.update(value=None, cores=1, sample=f"failed: {ex}")
+        return out
+    out.update(value=allc, cores=cores, value_1_thread=one,
+               sample=f"{nelem} random elements of {workload} (seed 0) per process: tabulation "
+                      "and basis, element H/S, density, adjoint; best of "
+                      f"{reps}; {cores} single-threaded processes ({cores * nelem} elements) "
+                      f"and separately 1 thread ({nelem} elements)")
+    return out
 
 
 def run_reference(args):
@@ -540,7 +649,9 @@ def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
         return None
-    res = _oracle_steps(args.workload, args.ref_elems, args.warmup + args.steps)[args.warmup:]
+    cores = os.cpu_count() or 1
+    res = _oracle_steps(args.workload, args.ref_elems, args.warmup + args.steps,
+                        cores)[args.warmup:]
     nq = sum(r[0] for r in res)
     sec = sum(r[1] for r in res)
     value = nq / sec
@@ -549,9 +660,10 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": args.workload, "prec": "fp64 oracle (CPU)"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"{args.ref_elems} random elements of {args.workload} "
-                                       f"(seed 0) per step, 1 thread"},
+                                       f"(seed 0) per process and step, {cores} "
+                                       "single-threaded processes"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
 
@@ -570,7 +682,7 @@ def main():
     ap.add_argument("--launch", default="stream", choices=["graph", "stream"],
                     help="replay the step as a captured CUDA graph, or launch call by call")
     ap.add_argument("--workload", default="c2_rocksalt_12cube")
-    ap.add_argument("--cpu-elems", type=int, default=160)
+    ap.add_argument("--cpu-elems", type=int, default=96)
     ap.add_argument("--ref-elems", type=int, default=24)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

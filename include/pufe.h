@@ -77,7 +77,10 @@ typedef enum {
                       the tensor cores (tcgen05 kind::tf32, every operand
                       split into two TF32 terms, hi*hi + hi*lo + lo*hi).
                       The constant FE-FE blocks of T and S are exact FP64
-                      constants.  FP32 tabulation, density and adjoint. */
+                      constants, and the enrichment-enrichment block of S
+                      (ill-conditioned, Sec. 6.2 Table 1) is computed in
+                      FP64 arithmetic from the FP32 enrichment values.  FP32
+                      tabulation, density and adjoint. */
 } pufe_prec;
 
 /* Quadrature modes (Sec. 5.2). */
@@ -175,13 +178,17 @@ pufe_status pufe_assemble_HS(pufe_ctx *ctx, const double *V, int prec, int what,
  * V that the tensor-core assembly reads (elements with n_e > 128) lives in a
  * library-owned static device array of PUFE_STATIC_MAX_POINTS (4,194,304)
  * floats, resident on
- * every device that loads the library until the process exits.  Contexts
- * with more padded quadrature points than that return PUFE_EINVAL.  The
+ * every device that loads the library until the process exits.  The array
+ * holds V on the padded points of the n_e > 128 elements only: contexts whose
+ * last such element ends beyond PUFE_STATIC_MAX_POINTS padded points return
+ * PUFE_EINVAL (contexts without such elements never touch it).  The
  * context itself (built earlier by pufe_build_mesh) and a prior
  * pufe_tabulate(ctx, PUFE_TF32X3) are still required; arguments and results
  * are as for pufe_assemble_HS.  The first call on a device looks up the
  * array's device address, so make that first call before capturing the
- * stream.  All calls share the one array: each call rewrites the entries it
+ * stream; the address is kept for the life of the device's primary context
+ * (after a cudaDeviceReset the process must not call this entry point
+ * again).  All calls share the one array: each call rewrites the entries it
  * reads, and calls that overlap on the GPU (on different streams or
  * contexts) race on it.  Asynchronous. */
 pufe_status pufe_assemble_HS_static(pufe_ctx *ctx, const double *V, int what, double *H,
@@ -336,7 +343,39 @@ pufe_status pufe_scf_step(pufe_ctx *ctx, int nstates, const double *eps, const d
 /* Forget the Pulay history of the context (start of a new SCF run). */
 pufe_status pufe_scf_reset(pufe_ctx *ctx);
 
-/* Wait for `stream`, then report (and clear) any device-side error flag. */
+/* Number of enrichment functions (slots) in each element's basis: n_elem
+ * int32 (host).  An element's enrichment columns are its slots times their
+ * enriched vertices; its K0 table holds 4 values per slot and point. */
+pufe_status pufe_get_element_slots(const pufe_ctx *ctx, int32_t *n_slot);
+
+/* ---- diagnostics and instrumentation (no counterpart in the paper) ------- */
+
+/* Exercise the timeout path of the device waits: one thread waits, with the
+ * same bounded mbarrier wait the pipelined tensor-core kernels use, on a
+ * barrier that nothing completes; after wait_ns nanoseconds (1e6 <= wait_ns
+ * <= 2e9) it gives up, sets the context's device error flag and returns, so
+ * the next pufe_sync_status reports PUFE_ETIMEOUT (and clears the flag) and
+ * the context stays usable.  Asynchronous on `stream`. */
+pufe_status pufe_selftest_timeout(pufe_ctx *ctx, uint64_t wait_ns, void *stream);
+
+
+/* enable != 0: the following pufe_assemble_HS calls with PUFE_TF32X3 record
+ * CUDA events around each of their kernels, on the stream each kernel runs
+ * on (the first enable creates the events); enable = 0 stops it.  Results
+ * are unchanged.  Not for calls inside a CUDA graph capture. */
+pufe_status pufe_profile_assembly(pufe_ctx *ctx, int enable);
+
+/* Durations in ms of the last instrumented assembly call, ms[5] (host):
+ * [0] the whole call, [1] the FE-FE kernel (V block and kinetic constants of
+ * H), [2] the FP64 enrichment-enrichment kernel of S, [3] the tensor-core
+ * tile kernel, [4] the enrichment strip kernel; 0 for a kernel the call did
+ * not launch.  Waits for the call to finish.  PUFE_ESTATE if no
+ * instrumented call was made. */
+pufe_status pufe_profile_read(pufe_ctx *ctx, double *ms);
+
+/* Wait for `stream`, then report (and clear) any device-side error flag:
+ * PUFE_ETIMEOUT for a bounded wait that gave up, PUFE_EINVAL when an
+ * assembly read a NaN or infinite V, PUFE_EDEVICE for any other flag. */
 pufe_status pufe_sync_status(pufe_ctx *ctx, void *stream);
 
 /* Release the context and everything it owns.  NULL is a no-op. */

@@ -267,6 +267,30 @@ pufe_status pufe_scf_reset(pufe_ctx *ctx) {
   return PUFE_OK;
 }
 
+pufe_status pufe_selftest_timeout(pufe_ctx *ctx, uint64_t wait_ns, void *stream) {
+  if (pufe_status e0 = need_device(ctx)) return e0;
+  if (wait_ns < 1000000ull || wait_ns > 2000000000ull)
+    return fail(PUFE_EINVAL, "wait_ns must be between 1e6 and 2e9");
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return fail(PUFE_ECUDA, "cudaSetDevice failed");
+  return launch_wait_probe(ctx, wait_ns, (cudaStream_t)stream);
+}
+
+pufe_status pufe_profile_assembly(pufe_ctx *ctx, int enable) {
+  if (pufe_status e0 = need_device(ctx)) return e0;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return fail(PUFE_ECUDA, "cudaSetDevice failed");
+  return profile_enable(ctx, enable != 0);
+}
+
+pufe_status pufe_profile_read(pufe_ctx *ctx, double *ms) {
+  if (pufe_status e0 = need_device(ctx)) return e0;
+  if (!ms) return fail(PUFE_EINVAL, "ms must not be NULL");
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return fail(PUFE_ECUDA, "cudaSetDevice failed");
+  return profile_read(ctx, ms);
+}
+
 pufe_status pufe_sync_status(pufe_ctx *ctx, void *stream) {
   if (pufe_status e0 = need_device(ctx)) return e0;
   DeviceGuard g(ctx->device);
@@ -277,6 +301,8 @@ pufe_status pufe_sync_status(pufe_ctx *ctx, void *stream) {
   if (flag) {
     PUFE_CUDA_TRY(cudaMemset(ctx->d.err, 0, sizeof(unsigned)));
     if (flag & DEVERR_TIMEOUT) return fail(PUFE_ETIMEOUT, "a device wait gave up");
+    if (flag == DEVERR_NONFINITE)
+      return fail(PUFE_EINVAL, "V holds a NaN or an infinity (the assembly read it)");
     return fail(PUFE_EDEVICE, "kernel reported device error flag " + std::to_string(flag));
   }
   return PUFE_OK;

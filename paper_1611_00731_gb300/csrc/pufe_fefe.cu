@@ -66,7 +66,13 @@ __global__ void __launch_bounds__(SF_NT) k_fefe_sumfac(
     const int64_t qs = qoff[e] + part_q[k];
     const int p2 = p * p, p3 = p2 * p;
     __syncthreads();
-    for (int q = tid; q < p3; q += SF_NT) Wq[q] = (float)(w[qs + q] * V[qs + q]);
+    bool bad = false;
+    for (int q = tid; q < p3; q += SF_NT) {
+      const double v = V[qs + q];
+      bad |= !isfinite(v);
+      Wq[q] = (float)(w[qs + q] * v);
+    }
+    if (bad) atomicOr(err, DEVERR_NONFINITE);
     for (int o = tid; o < 3 * p; o += SF_NT) {
       const int d = o / p, t = o - d * p;
       const int stride = d == 0 ? 1 : (d == 1 ? p : p2);

@@ -184,6 +184,7 @@ __global__ void __launch_bounds__(ASM_NT) k_assemble_fp64(
           }
           sw = w[q0 + q];
           vv = V ? V[q0 + q] : 0.0;
+          if (!isfinite(vv)) atomicOr(err, DEVERR_NONFINITE);
         }
         const double r2 = sqrt(0.5 * sw), r1 = sqrt(sw);
         Y0[k] = r2 * gx;

@@ -29,7 +29,8 @@ pufe_status cuda_fail(cudaError_t err, const char *what);
 enum : unsigned {
   DEVERR_BOUNDS = 1u,   // an index check failed inside a kernel
   DEVERR_TIMEOUT = 2u,  // a bounded wait gave up
-  DEVERR_SHAPE = 4u     // a kernel met a shape it was not built for
+  DEVERR_SHAPE = 4u,    // a kernel met a shape it was not built for
+  DEVERR_NONFINITE = 8u // an input (V) held a NaN or an infinity
 };
 
 // ---------------------------------------------------------------------------
@@ -128,6 +129,7 @@ struct pufe_ctx {
   bool tabulated32 = false;   // FP32 enrichment table is current
   bool fe_exact = false;      // every rule has >= 4 points per axis per (sub)cell
   int n_big = 0;              // elements with n_e > 128 (listed first in `order`)
+  int64_t big_pad_end = 0;    // end of the last n_e > 128 element's padded points (0: none)
   int64_t n_wsplit = 0;       // items of the FP64 point-range work list (0: none)
   int max_part_p = 0;         // largest points-per-axis of any (sub)cell
   int strip_stage = 0;        // floats of the strip kernel's shared-memory stage
@@ -139,6 +141,15 @@ struct pufe_ctx {
   // host copies kept for getters
   std::vector<int64_t> qoff, rowptr, doff;
   std::vector<int32_t> col, dofs, n_e, q_e, order;
+  std::vector<int32_t> see_stage;   // per element: slots x largest (sub)cell's points (0: no strip)
+  std::vector<int32_t> n_slot;      // per element: enrichments (slots) in its basis
+  // instrumentation of the mixed assembly (pufe_profile_assembly): events
+  // around the call [0, 1], the FE-FE kernel [2, 3], the FP64 E-E kernel of
+  // S [4, 5], the tensor-core tile [6, 7] and the strip [8, 9]
+  bool prof = false;
+  bool prof_ran[5] = {false, false, false, false, false};
+  cudaEvent_t pev[10] = {nullptr, nullptr, nullptr, nullptr, nullptr,
+                         nullptr, nullptr, nullptr, nullptr, nullptr};
   std::vector<double> x, w;
   pufe::DeviceArrays d;
   pufe::ScfState *scf = nullptr;   // SCF work arrays, made on first use
@@ -336,6 +347,16 @@ pufe_status launch_adjoint_fefe(pufe_ctx *ctx, const double *Hbar, double *Vbar,
                                 int count, cudaStream_t s);
 pufe_status launch_adjoint_strip_sf(pufe_ctx *ctx, const double *Hbar, double *Vbar, int first,
                                     int count, cudaStream_t s);
+// S enrichment-enrichment block in FP64 (mixed path): adds into S (and Si at
+// a wavevector: ph != nullptr) for the elements order[first .. first+count)
+pufe_status launch_see64(pufe_ctx *ctx, const PhaseTab *ph, double *S, double *Si, int first,
+                         int count, cudaStream_t st);
+// one bounded mbarrier wait that nothing completes (diagnostics of the
+// timeout path): gives up after wait_ns and sets DEVERR_TIMEOUT
+pufe_status launch_wait_probe(pufe_ctx *ctx, uint64_t wait_ns, cudaStream_t st);
+// instrumentation of the mixed assembly (events around its kernels)
+pufe_status profile_enable(pufe_ctx *ctx, bool on);
+pufe_status profile_read(pufe_ctx *ctx, double ms[5]);
 pufe_status launch_assemble_tc_static(pufe_ctx *ctx, const double *V, int what, double *H,
                                       double *S, cudaStream_t s);
 pufe_status launch_assemble_tc(pufe_ctx *ctx, const double *V, int what, double *H, double *S,

@@ -1,0 +1,252 @@
+// Enrichment-enrichment block of S in FP64 (mixed-precision path).
+//
+// S is ill-conditioned because the enrichments are nearly linearly dependent
+// on each other and on the FE functions (Sec. 6.2, Table 1: cond(S) grows to
+// 1e9 with the support radius), so the mixed path keeps this block of S in
+// FP64 arithmetic while H and the other blocks of S are contracted in FP32.
+//
+// For columns r = (v, alpha) and s = (v', beta) of an element, on one
+// (sub)cell with a p^3 tensor rule (Sec. 4 eq. disceig3d, Sec. 5.2),
+//   S_rs = sum_q w_q Psi_alpha(x_q) Psi_beta(x_q) phi_v(x_q) phi_v'(x_q).
+// The trilinear PU factors give phi_v phi_v' = 1/64 prod_d u_(k_d)(xi_d) with
+// u_0 = (1 - x)^2, u_1 = 1 - x^2, u_2 = (1 + x)^2 and k_d = b_d + b'_d the
+// sum of the two vertices' bits along axis d, so every entry of the pair
+// (alpha, beta) is one of 27 projections
+//   P_ab[kz][ky][kx] = sum_q A_q u_kz(zeta) u_ky(eta) u_kx(xi),
+//   A_q = (sqrt(w_q) Psi_alpha)(sqrt(w_q) Psi_beta),
+// contracted one axis at a time (3 p^3 + 9 p^2 + 27 p multiply-adds per pair
+// and cell, against p^3 per entry for the direct sum):  S_rs = P_ab[k] / 64.
+// Inputs are the FP32 values of the mixed path (enrichment table, reference
+// coordinates, sqrt(w)); each factor sqrt(w) Psi is the exact FP64 product of
+// two FP32 numbers and every operation after that is FP64, so the block is
+// the Gram matrix of the FP32-rounded basis values up to FP64 rounding (no
+// FP32 rounding enters its sums).  The entries go into the FP64 CSR values
+// with FP64 atomics, both triangles; cells of a subdivided element add up
+// there.
+#include <algorithm>
+
+#include "pufe_internal.h"
+
+namespace pufe {
+namespace {
+
+constexpr int SE_NT = 256;
+
+template <bool STAGED, bool BLOCH>
+__global__ void __launch_bounds__(SE_NT) k_see64(
+    const int32_t *__restrict__ order, const int64_t *__restrict__ qpoff,
+    const float4 *__restrict__ qdat, const float *__restrict__ ptab,
+    const int32_t *__restrict__ partoff,
+    const int32_t *__restrict__ part_p, const int32_t *__restrict__ part_q,
+    const int64_t *__restrict__ doff, const int32_t *__restrict__ ecol,
+    const int32_t *__restrict__ aoff, const int64_t *__restrict__ toff32,
+    const float *__restrict__ psi, const int64_t *__restrict__ soff,
+    const int32_t *__restrict__ smap, int pm, int amax, int stage_dbl, int work_dbl,
+    double *__restrict__ S, unsigned *err, const uint8_t *__restrict__ eshift, PhaseTab ph,
+    double *__restrict__ Si) {
+  extern __shared__ double sm64[];
+  const int e = order[blockIdx.x], tid = threadIdx.x;
+  const int n = (int)(doff[e + 1] - doff[e]), ne = n - 64;
+  if (ne <= 0) return;
+  const int A = aoff[e + 1] - aoff[e];
+  if (A > amax || A > 255) {
+    if (tid == 0) atomicOr(err, DEVERR_SHAPE);
+    return;
+  }
+  // shared memory: U [3 axes][u_0, u_1, u_2][pm] | stage [slot][point]
+  //                | work | scol [slot][vertex] | pairs
+  double *U = sm64;
+  double *stg = U + 9 * pm;
+  double *work = stg + stage_dbl;
+  int *scol = reinterpret_cast<int *>(work + work_dbl);
+  int *pairs = scol + amax * 8;
+  __shared__ double s_phr[8], s_phi[8];
+  if (BLOCH && tid < 8) {
+    s_phr[tid] = ph.re[tid];
+    s_phi[tid] = ph.im[tid];
+  }
+  const int32_t *ecs = ecol + (doff[e] - 64ll * e);
+  for (int o = tid; o < A * 8; o += SE_NT) scol[o] = -1;
+  __syncthreads();
+  for (int r = tid; r < ne; r += SE_NT) {
+    const int c = ecs[r];
+    scol[(c >> 3) * 8 + (c & 7)] = r;
+  }
+  const int npair = A * (A + 1) / 2;
+  if (tid < A) {   // pairs (alpha, beta), alpha <= beta, alpha-major
+    int k = tid * A - tid * (tid - 1) / 2;
+    for (int b = tid; b < A; ++b) pairs[k++] = tid | (b << 8);
+  }
+  const float *pe = psi + 4 * toff32[e];
+  const float4 *qe = qdat + qpoff[e];
+  const float *pt = ptab + 32 * qpoff[e];   // per point: ..., [28] sqrt(w)
+  const int32_t *m = smap + soff[e];
+  const uint8_t *esh = BLOCH ? eshift + doff[e] : nullptr;
+
+  for (int k = partoff[e]; k < partoff[e + 1]; ++k) {
+    const int p = part_p[k], p2 = p * p, p3 = p2 * p, qs = part_q[k];
+    const int per = 3 * p2 + 9 * p + 27;   // work doubles of one pair
+    if (p > pm || per > work_dbl || (STAGED && A * p3 > stage_dbl)) {
+      if (tid == 0) atomicOr(err, DEVERR_SHAPE);
+      return;
+    }
+    __syncthreads();   // previous cell's users of U, stage and work are done
+    for (int o = tid; o < 3 * p; o += SE_NT) {
+      const int d = o / p, t = o - d * p;
+      const int stride = d == 0 ? 1 : (d == 1 ? p : p2);
+      const float4 x4 = qe[qs + t * stride];
+      const double x = (double)(d == 0 ? x4.x : (d == 1 ? x4.y : x4.z));
+      const double l0 = 1.0 - x, l1 = 1.0 + x;
+      U[(d * 3 + 0) * pm + t] = l0 * l0;
+      U[(d * 3 + 1) * pm + t] = l0 * l1;
+      U[(d * 3 + 2) * pm + t] = l1 * l1;
+    }
+    // sqrt(w) Psi of every slot at the cell's points (Psi read from the FP32
+    // table [q/8][slot][comp][q%8], component 0): exact in FP64
+    auto swpsi = [&](int slot, int lq) -> double {
+      const int q = qs + lq;
+      return (double)pt[32 * q + 28] * (double)pe[((int64_t)(q >> 3) * A + slot) * 32 + (q & 7)];
+    };
+    if (STAGED) {
+      for (int o = tid; o < A * p3; o += SE_NT) {
+        const int s = o / p3, lq = o - s * p3;
+        stg[o] = swpsi(s, lq);
+      }
+    }
+    __syncthreads();
+    const int npc = max(1, min(npair, work_dbl / per));
+    for (int c0 = 0; c0 < npair; c0 += npc) {
+      const int nc = min(npc, npair - c0);
+      double *T1 = work;                    // [nc][p^2][3]: z outputs
+      double *T2 = T1 + nc * 3 * p2;        // [nc][p][kz][ky]
+      double *P = T2 + nc * 9 * p;          // [nc][kz][ky][kx]
+      // z: one thread per (pair, qx, qy) column
+      for (int it = tid; it < nc * p2; it += SE_NT) {
+        const int g = it / p2, qxy = it - g * p2;
+        const int pr = pairs[c0 + g], al = pr & 0xff, be = pr >> 8;
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+        for (int qz = 0; qz < p; ++qz) {
+          const int lq = qxy + p2 * qz;
+          const double f = STAGED ? stg[al * p3 + lq] * stg[be * p3 + lq]
+                                  : swpsi(al, lq) * swpsi(be, lq);
+          a0 = fma(f, U[6 * pm + qz], a0);
+          a1 = fma(f, U[7 * pm + qz], a1);
+          a2 = fma(f, U[8 * pm + qz], a2);
+        }
+        double *t1 = T1 + (size_t)it * 3;
+        t1[0] = a0;
+        t1[1] = a1;
+        t1[2] = a2;
+      }
+      __syncthreads();
+      // y: one thread per (pair, qx, kz)
+      for (int it = tid; it < nc * p * 3; it += SE_NT) {
+        const int g = it / (3 * p), rem = it - g * 3 * p, qx = rem / 3, kz = rem - qx * 3;
+        const double *t1 = T1 + ((size_t)g * p2 + qx) * 3 + kz;
+        double b0 = 0.0, b1 = 0.0, b2 = 0.0;
+        for (int qy = 0; qy < p; ++qy) {
+          const double t = t1[qy * p * 3];
+          b0 = fma(t, U[3 * pm + qy], b0);
+          b1 = fma(t, U[4 * pm + qy], b1);
+          b2 = fma(t, U[5 * pm + qy], b2);
+        }
+        double *t2 = T2 + ((size_t)g * p + qx) * 9 + kz * 3;
+        t2[0] = b0;
+        t2[1] = b1;
+        t2[2] = b2;
+      }
+      __syncthreads();
+      // x: one thread per (pair, kz, ky)
+      for (int it = tid; it < nc * 9; it += SE_NT) {
+        const int g = it / 9, j = it - g * 9;
+        const double *t2 = T2 + (size_t)g * p * 9 + j;
+        double c0v = 0.0, c1v = 0.0, c2v = 0.0;
+        for (int qx = 0; qx < p; ++qx) {
+          const double t = t2[qx * 9];
+          c0v = fma(t, U[qx], c0v);
+          c1v = fma(t, U[pm + qx], c1v);
+          c2v = fma(t, U[2 * pm + qx], c2v);
+        }
+        double *pp = P + g * 27 + j * 3;
+        pp[0] = c0v;
+        pp[1] = c1v;
+        pp[2] = c2v;
+      }
+      __syncthreads();
+      // scatter: one thread per (pair, vertex of alpha, vertex of beta); a
+      // pair (alpha, alpha) takes each unordered column pair once
+      for (int it = tid; it < nc * 64; it += SE_NT) {
+        const int g = it >> 6, i = (it >> 3) & 7, j = it & 7;
+        const int pr = pairs[c0 + g], al = pr & 0xff, be = pr >> 8;
+        if (al == be && j < i) continue;
+        const int r = scol[al * 8 + i], s = scol[be * 8 + j];
+        if (r < 0 || s < 0) continue;
+        const int kx = (i & 1) + (j & 1), ky = ((i >> 1) & 1) + ((j >> 1) & 1),
+                  kz = (i >> 2) + (j >> 2);
+        const double v = P[g * 27 + (kz * 3 + ky) * 3 + kx] * (1.0 / 64.0);
+        const int s_rs = m[(64 + r) * n + 64 + s], s_sr = m[(64 + s) * n + 64 + r];
+        if (BLOCH) {   // (r, s) with conj(ph_r) ph_s, (s, r) with its conjugate
+          const int a = esh[64 + r], b = esh[64 + s];
+          const double pr_ = s_phr[a] * s_phr[b] + s_phi[a] * s_phi[b];
+          const double pi_ = s_phr[a] * s_phi[b] - s_phi[a] * s_phr[b];
+          atomicAdd(S + s_rs, v * pr_);
+          atomicAdd(Si + s_rs, v * pi_);
+          if (r != s) {
+            atomicAdd(S + s_sr, v * pr_);
+            atomicAdd(Si + s_sr, -v * pi_);
+          }
+        } else {
+          atomicAdd(S + s_rs, v);
+          if (r != s) atomicAdd(S + s_sr, v);
+        }
+      }
+      __syncthreads();   // P and the work area are reused by the next chunk
+    }
+  }
+}
+
+}  // namespace
+
+// Shared-memory budget of the Psi stage; cells of elements with more
+// enrichment values than this read the FP32 table directly.
+static constexpr int SEE_STAGE_MAX_DBL = 8192;
+static constexpr int SEE_WORK_DBL = 4096;
+
+pufe_status launch_see64(pufe_ctx *ctx, const PhaseTab *ph, double *S, double *Si, int first,
+                         int count, cudaStream_t st) {
+  if (count <= 0) return PUFE_OK;
+  auto &D = ctx->d;
+  const int pm = std::max(1, ctx->max_part_p);
+  const int amax = std::max(1, ctx->max_alpha);
+  if (amax > 255) return fail(PUFE_EINVAL, "more than 255 enrichments on one element");
+  const int per_max = 3 * pm * pm + 9 * pm + 27;
+  const int work = std::max(SEE_WORK_DBL, per_max);
+  // stage the cells when every element's largest cell fits the budget
+  int need = 0;
+  for (int64_t k = first; k < first + count; ++k) {
+    const int e = ctx->order[k];
+    need = std::max(need, (int)ctx->see_stage[e]);
+  }
+  const bool staged = need <= SEE_STAGE_MAX_DBL;
+  const int stage = staged ? need : 0;
+  const size_t ints = (size_t)amax * 8 + (size_t)amax * (amax + 1) / 2;
+  const size_t sm = ((size_t)9 * pm + stage + work) * sizeof(double) + ints * sizeof(int);
+  if (sm > 227 * 1024) return fail(PUFE_EINVAL, "FP64 overlap kernel: shared memory above 227 KB");
+  auto go = [&](auto kern, const uint8_t *esh, PhaseTab tab, double *si) -> pufe_status {
+    PUFE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    kern<<<(unsigned)count, SE_NT, sm, st>>>(D.order + first, D.qpoff, D.qdat, D.ptab,
+                                             D.partoff, D.part_p, D.part_q, D.doff, D.ecol, D.aoff,
+                                             D.toff32, D.psi32, D.soff, D.smap, pm, amax, stage,
+                                             work, S, D.err, esh, tab, si);
+    PUFE_CUDA_TRY(cudaGetLastError());
+    return PUFE_OK;
+  };
+  if (ph) {
+    return staged ? go(k_see64<true, true>, D.eshift, *ph, Si)
+                  : go(k_see64<false, true>, D.eshift, *ph, Si);
+  }
+  return staged ? go(k_see64<true, false>, nullptr, PhaseTab{}, nullptr)
+                : go(k_see64<false, false>, nullptr, PhaseTab{}, nullptr);
+}
+
+}  // namespace pufe

@@ -635,6 +635,9 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
   ctx->n_alpha = (int64_t)S.orb.size();
   ctx->psi_len = 4 * toff[nelem];
   ctx->nq_pad = qpoff[nelem];
+  ctx->big_pad_end = 0;
+  for (int64_t e = 0; e < nelem; ++e)
+    if (n_e[e] > 128) ctx->big_pad_end = std::max<int64_t>(ctx->big_pad_end, qpoff[e + 1]);
   ctx->psi32_len = 4 * toff32[nelem];
   ctx->smap_len = soff[nelem];
   ctx->dof_len = doff[nelem];
@@ -666,6 +669,16 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
   ctx->strip_npair_max = 0;
   ctx->adj_sf_floats = 0;
   ctx->adj_sf_all = true;
+  ctx->n_slot.assign(nelem, 0);
+  for (int64_t e = 0; e < nelem; ++e) ctx->n_slot[e] = (int32_t)ealpha[e].size();
+  ctx->see_stage.assign(nelem, 0);
+  for (int64_t e = 0; e < nelem; ++e) {
+    if (n_e[e] <= 64) continue;
+    int p3max = 0;
+    for (int32_t j = partoff[e]; j < partoff[e + 1]; ++j)
+      p3max = std::max(p3max, (int)(part_p[j] * part_p[j] * part_p[j]));
+    ctx->see_stage[e] = (int32_t)ealpha[e].size() * p3max;
+  }
   for (int64_t e = 0; e < nelem; ++e) {
     if (n_e[e] <= 64 || n_e[e] > 128) continue;
     const int A = (int)ealpha[e].size();
@@ -909,6 +922,12 @@ pufe_status pufe_get_element_basis(const pufe_ctx *ctx, int32_t *n_e, int32_t *d
   return PUFE_OK;
 }
 
+pufe_status pufe_get_element_slots(const pufe_ctx *ctx, int32_t *n_slot) {
+  if (!ctx || !n_slot) return fail(PUFE_EINVAL, "ctx and n_slot must not be NULL");
+  std::memcpy(n_slot, ctx->n_slot.data(), ctx->n_slot.size() * sizeof(int32_t));
+  return PUFE_OK;
+}
+
 void pufe_destroy(pufe_ctx *ctx) {
   if (!ctx) return;
   if (!ctx->on_device) {
@@ -918,6 +937,8 @@ void pufe_destroy(pufe_ctx *ctx) {
   int cur = 0;
   cudaGetDevice(&cur);
   cudaSetDevice(ctx->device);
+  for (auto &ev : ctx->pev)
+    if (ev) cudaEventDestroy(ev);
   free_device(ctx);
   cudaSetDevice(cur);
   delete ctx;

@@ -18,12 +18,14 @@
 //   x: H_abc = sum (L'_a X_bc + L_a W_bc),     S_abc = sum L_a S_bc
 // against 5 * 64 p^3 for the direct product.
 //
-// E x E block, direct form: a small dense product over the element's points,
-// symmetric in (r, s), so only 4 x 4 tiles with r-block <= s-block are formed:
-//   H_rs = sum_q [sum_d y_dr y_ds + V_q z_r z_s],  S_rs = sum_q z_r z_s,
+// E x E block of H, direct form: a small dense product over the element's
+// points, symmetric in (r, s), so only 4 x 4 tiles with r-block <= s-block are
+// formed:
+//   H_rs = sum_q [sum_d y_dr y_ds + V_q z_r z_s],
 //   y_dr = sqrt(w/2) d b_r / d x_d,  z_r = sqrt(w) b_r.
+// The E x E block of S is computed in FP64 by its own kernel (pufe_see64.cu).
 //
-// E x E block, enrichment-pair form: for r = (v, alpha), s = (v', beta) the
+// E x E block of H, enrichment-pair form: for r = (v, alpha), s = (v', beta) the
 // PU factors are trilinear, phi_v = 1/8 prod_d (1 + s_d x_d) with s_d = +-1,
 // so along each axis phi_v phi_v' is one of u_0 = (1-x)^2, u_1 = 1 - x^2,
 // u_2 = (1+x)^2 (index b_d + b'_d, b = (s + 1) / 2), d phi_v / dx_d is a
@@ -33,7 +35,6 @@
 //   A = w Psi_a Psi_b,  E = w (V Psi_a Psi_b + 1/2 grad Psi_a . grad Psi_b),
 //   B_d = w Psi_b d_d Psi_a,  C_d = w Psi_a d_d Psi_b,
 // onto tensor products of {u_k, 1, l_t}:
-//   64 S_rs = <A, u u u>,
 //   64 H_rs = <E, u u u> + 1/2 sum_d (2/h_d)^2 s_d s'_d <A, u u with 1 on d>
 //           + 1/2 sum_d (2/h_d) (s_d <C_d, u u with l_b'd on d>
 //                                + s'_d <B_d, u u with l_bd on d>).
@@ -73,10 +74,15 @@ struct EnrVal {
   float b, bx, by, bz;
 };
 
-// floor(x / d) for 0 <= x <= 2^16 and 1 <= d < 2^16: the high word of
-// x * ceil(2^32 / d) (one __umulhi); the rounding error is below
-// x 2^-32 <= 2^-16 < 1/d, so it cannot carry the quotient past the next
-// integer.  d = 1 (multiplier 2^32) is taken apart.
+// floor(x / d) for 0 <= x and 1 <= d with x d < 2^32: the high word of
+// x * ceil(2^32 / d) (one __umulhi).  The multiplier exceeds 2^32 / d by less
+// than 1, so the product exceeds x 2^32 / d by less than x, i.e. the quotient
+// by less than x / 2^32 < 1 / d, which cannot carry it past the next integer
+// (the fractional part of x / d is at most 1 - 1/d).  d = 1 (multiplier
+// 2^32) is taken apart.  Every use below divides a loop index bounded by the
+// launch sizes (p <= 16 points per axis, n_e <= 128, so at most 64
+// enrichment columns and slots); strip_launch and the adjoint launcher check
+// the largest product x d against 2^32 on the host.
 struct FastDiv {
   unsigned m;
   bool one;
@@ -98,7 +104,7 @@ struct StripElem {
   bool wantH, wantS, useV;
   float sx, sy, sz;
   // shared memory
-  float *stage, *work, *HE, *SE, *L1, *D1;
+  float *stage, *work, *HE, *L1, *D1;
   const int *ecs;
   int pm, wfloats;
   // E x E tile of this thread (direct form)
@@ -292,6 +298,8 @@ __device__ __forceinline__ void strip_part(const StripElem &E, double *__restric
     }
   }
 
+  // ---- E x E block of H (S's is computed in FP64 by its own kernel) ----------
+  if (!E.wantH) return;
   // ---- E x E block, enrichment-pair form -------------------------------------
   if (E.sp) {
     const int per = 24 * p2 + 66 * p;            // work floats of one pair
@@ -402,9 +410,9 @@ __device__ __forceinline__ void strip_part(const StripElem &E, double *__restric
   }
 
   // ---- E x E block over this (sub)cell's points --------------------------------
-  float h16[16], s16[16];
+  float h16[16];
 #pragma unroll
-  for (int u = 0; u < 16; ++u) h16[u] = s16[u] = 0.0f;
+  for (int u = 0; u < 16; ++u) h16[u] = 0.0f;
   const int ld = 4 * ne8;   // floats per point in the chunk table
   float *Xt = E.work;       // [ST_KC][4][ne8]: y_0, y_1, y_2, z
   float *Vc = E.work + ST_KC * ld;
@@ -461,20 +469,21 @@ __device__ __forceinline__ void strip_part(const StripElem &E, double *__restric
             h = fmaf(r1v[i], s1v[j], h);
             h = fmaf(r2v[i], s2v[j], h);
             h16[i * 4 + j] = fmaf(rv, s3v[j], h);
-            s16[i * 4 + j] = fmaf(r3v[i], s3v[j], s16[i * 4 + j]);
           }
         }
       }
     }
   }
-  if (E.act) {   // the PG point groups meet in shared memory
+  // the PG point groups meet in shared memory, one group after the other (a
+  // fixed order, so the block is the same on every call)
+  for (int g = 0; g < E.PG; ++g) {
+    if (E.act && E.pg == g) {
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < 4; ++i)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        atomicAdd(&E.HE[(4 * E.rb + i) * ne8 + 4 * E.sb + j], h16[i * 4 + j]);
-        atomicAdd(&E.SE[(4 * E.rb + i) * ne8 + 4 * E.sb + j], s16[i * 4 + j]);
-      }
+        for (int j = 0; j < 4; ++j) E.HE[(4 * E.rb + i) * ne8 + 4 * E.sb + j] += h16[i * 4 + j];
+    }
+    __syncthreads();
   }
 }
 
@@ -535,12 +544,11 @@ __global__ void __launch_bounds__(ST_NT, 2) k_strip_sf(
 
   // shared memory: [stage: sfloats][work: wfloats][E x E: eefloats]
   //                [L1, D1: 12 pm each][F1: 18 pm][ecs: 64 ints][pairs: 36 ints]
-  // E x E area: HE, SE ([ne8][ne8] each, entries r <= s; direct form) or
+  // E x E area: HE ([ne8][ne8], entries r <= s; direct form) or
   // the pair projections [npair][189] (enrichment-pair form)
   E.stage = reinterpret_cast<float *>(sm_st4);
   E.work = E.stage + sfloats;
   E.HE = E.work + wfloats;
-  E.SE = E.HE + ne8 * ne8;
   E.PE = E.HE;
   E.L1 = E.HE + eefloats;    // [3][4][pm]
   E.D1 = E.L1 + 12 * pm;     // [3][4][pm]
@@ -578,7 +586,7 @@ __global__ void __launch_bounds__(ST_NT, 2) k_strip_sf(
       for (int b = tid; b < A; ++b) pairs[k++] = tid | (b << 8);
     }
   }
-  const int ee_zero = E.sp ? E.npair * 189 : 2 * ne8 * ne8;
+  const int ee_zero = E.sp ? E.npair * 189 : ne8 * ne8;
   for (int o = tid; o < ee_zero; o += ST_NT) E.HE[o] = 0.0f;
 
   // E x E tiles: 4 x 4 blocks (rb <= sb), one per lane; WG warps cover the
@@ -670,7 +678,8 @@ __global__ void __launch_bounds__(ST_NT, 2) k_strip_sf(
       strip_part<false, BLOCH>(E, H, S);
   }
   __syncthreads();
-  // ---- E x E into the FP64 CSR values, both triangles ---------------------------
+  // ---- E x E block of H into the FP64 CSR values, both triangles ----------------
+  if (!E.wantH) return;
   const FastDiv dne(ne);
   if (E.sp) {   // entries from the pair projections (slot of r <= slot of s by symmetry)
     const float hx = 0.5f * sx, hy = 0.5f * sy, hz = 0.5f * sz;
@@ -702,21 +711,14 @@ __global__ void __launch_bounds__(ST_NT, 2) k_strip_sf(
       h = fmaf(hz * pz, P[171 + (cz * 3 + ky) * 3 + kx], h);
       h = fmaf(hz * qz, P[153 + (bz * 3 + ky) * 3 + kx], h);
       const int slot = E.m[(64 + r) * E.n + 64 + sc];
-      const float hv = h * (1.0f / 64.0f), sv = P[kzy * 3 + kx] * (1.0f / 64.0f);
+      const float hv = h * (1.0f / 64.0f);
       if (BLOCH) {
         float pr, pi;
         pair_phase(E, E.esh[64 + r], E.esh[64 + sc], pr, pi);
-        if (E.wantH) {
-          atomicAdd(H + slot, (double)(hv * pr));
-          atomicAdd(E.Hi + slot, (double)(hv * pi));
-        }
-        if (E.wantS) {
-          atomicAdd(S + slot, (double)(sv * pr));
-          atomicAdd(E.Si + slot, (double)(sv * pi));
-        }
+        atomicAdd(H + slot, (double)(hv * pr));
+        atomicAdd(E.Hi + slot, (double)(hv * pi));
       } else {
-        if (E.wantH) atomicAdd(H + slot, (double)hv);
-        if (E.wantS) atomicAdd(S + slot, (double)sv);
+        atomicAdd(H + slot, (double)hv);
       }
     }
     return;
@@ -728,18 +730,11 @@ __global__ void __launch_bounds__(ST_NT, 2) k_strip_sf(
     if (BLOCH) {
       float pr, pi;
       pair_phase(E, E.esh[64 + r], E.esh[64 + sc], pr, pi);
-      const float hv = E.HE[lo * ne8 + hi], sv = E.SE[lo * ne8 + hi];
-      if (E.wantH) {
-        atomicAdd(H + slot, (double)(hv * pr));
-        atomicAdd(E.Hi + slot, (double)(hv * pi));
-      }
-      if (E.wantS) {
-        atomicAdd(S + slot, (double)(sv * pr));
-        atomicAdd(E.Si + slot, (double)(sv * pi));
-      }
+      const float hv = E.HE[lo * ne8 + hi];
+      atomicAdd(H + slot, (double)(hv * pr));
+      atomicAdd(E.Hi + slot, (double)(hv * pi));
     } else {
-      if (E.wantH) atomicAdd(H + slot, (double)E.HE[lo * ne8 + hi]);
-      if (E.wantS) atomicAdd(S + slot, (double)E.SE[lo * ne8 + hi]);
+      atomicAdd(H + slot, (double)E.HE[lo * ne8 + hi]);
     }
   }
 }
@@ -773,9 +768,22 @@ static pufe_status strip_launch(pufe_ctx *ctx, const double *V, int what, double
   const int sneed = ctx->strip_stage;
   if (ne8 > 64) return fail(PUFE_EINVAL, "strip kernel takes n_e <= 128");
   const int pm = std::max(1, ctx->max_part_p);
+  {   // FastDiv preconditions, x d < 2^32 for the largest index of each division
+    const int64_t p2 = (int64_t)pm * pm, p3 = p2 * pm, A = ne8;
+    const int64_t xd[][2] = {
+        {std::max<int64_t>(ST_NT, p2), p2},                 // (column, point) pairs
+        {(ST_NT / std::max<int64_t>(1, p2) + 1) * 16 * pm, 16 * pm},   // y stage
+        {36 * 23 * pm, 23 * pm},                            // pair-form y stage
+        {(int64_t)ST_KC * ne8, ne8},                        // E x E chunk table
+        {((p3 + 7) / 8 + 1) * 8 * A, 8 * A},                // Psi staging
+        {(int64_t)ne8 * ne8, ne8}};                         // E x E scatter
+    for (auto &v : xd)
+      if (v[0] * v[1] >= (int64_t(1) << 32))
+        return fail(PUFE_EINVAL, "strip kernel: index range beyond its 32-bit divisions");
+  }
   const int wf = strip_work_floats(ctx->strip_pmask, ne8);
   const int sf = (sneed + 3) & ~3;
-  const int ee = std::max(2 * ne8 * ne8, 189 * ctx->strip_npair_max);
+  const int ee = std::max(ne8 * ne8, 189 * ctx->strip_npair_max);
   const size_t sm = ((size_t)sf + wf + ee + 42 * pm + 64 + 36) * sizeof(float);
   if (sm > 227 * 1024) return fail(PUFE_EINVAL, "strip kernel: shared memory above 227 KB");
   const float sx = (float)(2.0 / ctx->h[0]), sy = (float)(2.0 / ctx->h[1]),
@@ -825,6 +833,10 @@ pufe_status launch_assemble_mixed_bloch(pufe_ctx *ctx, const PhaseTab &ph, const
   }
   pufe_status e0 = launch_fefe_bloch(ctx, ph, V, what, H, Hi, S, Si, st);
   if (e0 != PUFE_OK) return e0;
+  if (what & PUFE_WANT_S) {   // E x E block of S(k) in FP64 with FP64 phases
+    pufe_status e1 = launch_see64(ctx, &ph, S, Si, 0, (int)ctx->nelem, st);
+    if (e1 != PUFE_OK) return e1;
+  }
   return strip_launch(ctx, (what & PUFE_WANT_H) ? V : nullptr, what, H, S, 0, (int)ctx->nelem, st,
                       &ph, Hi, Si);
 }
@@ -1113,6 +1125,10 @@ pufe_status launch_adjoint_strip_sf(pufe_ctx *ctx, const double *Hbar, double *V
   if (count <= 0 || ctx->adj_sf_floats == 0) return PUFE_OK;
   auto &D = ctx->d;
   const int pm = std::max(1, ctx->max_part_p);
+  // FastDiv preconditions: the divided indices stay below the work area
+  // (AJ_W floats), the divisors are p and p^2
+  if ((int64_t)AJ_W * pm * pm >= (int64_t(1) << 32))
+    return fail(PUFE_EINVAL, "adjoint strip: index range beyond its 32-bit divisions");
   const int cf = (ctx->adj_sf_floats + 3) & ~3;
   const size_t sm = ((size_t)cf + 33 * pm + AJ_W + 16 * 8 + 136) * sizeof(float);
   if (sm > 227 * 1024) return fail(PUFE_EINVAL, "adjoint strip: shared memory above 227 KB");

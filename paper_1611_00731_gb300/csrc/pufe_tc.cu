@@ -53,14 +53,35 @@ __device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Wait for completion `parity` of an mbarrier, giving up after WAIT_NS.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+// Wait for completion `parity` of an mbarrier, giving up after `limit` ns.
+__device__ __forceinline__ bool mbar_wait_ns(uint64_t *bar, uint32_t parity, uint64_t limit) {
   if (mbar_try(bar, parity)) return true;
   const uint64_t t0 = globaltimer();
   for (;;) {
     for (int i = 0; i < 64; ++i)
       if (mbar_try(bar, parity)) return true;
-    if (globaltimer() - t0 > WAIT_NS) return false;
+    if (globaltimer() - t0 > limit) return false;
+  }
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+  return mbar_wait_ns(bar, parity, WAIT_NS);
+}
+
+// Diagnostics of the timeout path: one thread waits, with the bounded wait
+// of the pipelined kernels, on an mbarrier that expects one arrival that
+// never comes; when the wait gives up it sets DEVERR_TIMEOUT, completes the
+// phase itself (so nothing is left pending) and returns.
+__global__ void k_wait_probe(uint64_t limit, unsigned *err) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(&bar, 1);
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  if (!mbar_wait_ns(&bar, 0, limit)) {
+    atomicOr(err, DEVERR_TIMEOUT);
+    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(
+                     smem_u32(&bar))
+                 : "memory");
   }
 }
 
@@ -554,16 +575,17 @@ __global__ void __launch_bounds__(WS_NT, 1) k_assemble_tc(
     // each keeping a warp's slots together: direct slots (r, cc): half-warp
     // h takes row 2 it + h, lanes run along 16 consecutive columns; mirror
     // slots (cc, r): lane = row, loop over the 16 columns.  All slot loads of
-    // a pass are issued before its atomics.
+    // a pass are issued before its atomics.  For S only the FE rows are
+    // scattered (fe_only): its E x E block comes from the FP64 kernel.
     auto owned = [&](int r, int cc, int n) { return r < n && cc < n && (r < 64 || cc <= r); };
     auto scatter_block = [&](const int32_t *m, int n, int rbase, int cb, double *out,
-                             auto value_of) {
+                             bool fe_only, auto value_of) {
       int sd[16];
 #pragma unroll
       for (int it = 0; it < 16; ++it) {
         const int rl = 2 * it + (lane >> 4);
         const int r = rbase + rl, cc = 64 + cb * 16 + (lane & 15);
-        sd[it] = owned(r, cc, n) ? m[(int64_t)r * n + cc] : -1;
+        sd[it] = (owned(r, cc, n) && (!fe_only || r < 64)) ? m[(int64_t)r * n + cc] : -1;
       }
 #pragma unroll
       for (int it = 0; it < 16; ++it)
@@ -572,7 +594,7 @@ __global__ void __launch_bounds__(WS_NT, 1) k_assemble_tc(
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
         const int cc = 64 + cb * 16 + i;
-        sd[i] = (cc != r && owned(r, cc, n)) ? m[(int64_t)cc * n + r] : -1;
+        sd[i] = (cc != r && owned(r, cc, n) && (!fe_only || r < 64)) ? m[(int64_t)cc * n + r] : -1;
       }
 #pragma unroll
       for (int i = 0; i < 16; ++i)
@@ -603,7 +625,7 @@ __global__ void __launch_bounds__(WS_NT, 1) k_assemble_tc(
 #pragma unroll
             for (int i = 0; i < 16; ++i) stg[lane][i] = make_float2(hv[i], 0.0f);
             __syncwarp();
-            scatter_block(m, n, rbase, cb, which == 0 ? H : S, [&](int rl, int cl) {
+            scatter_block(m, n, rbase, cb, which == 0 ? H : S, which == 1, [&](int rl, int cl) {
               return (double)stg[rl][cl].x;
             });
             __syncwarp();
@@ -1016,18 +1038,39 @@ static pufe_status run_assemble_tc(pufe_ctx *ctx, const double *V, int what, dou
   if (nbig > 0 && sm256 > 227 * 1024)
     return fail(PUFE_EINVAL, "too many enrichments per element for TF32X3");
   const size_t bytes = (size_t)ctx->nnz * sizeof(double);
+  // H = 0 and S = the constant FE-FE overlap; then the FE-FE kernel (V term
+  // and kinetic constants of H) and the FP64 enrichment-enrichment kernel of
+  // S run on the context's side stream, concurrently with the strip kernels
+  // below (all of them only add into H and S)
+  if (ctx->max_part_p > 16) return fail(PUFE_EINVAL, "rule with more than 16 points per axis");
+  const bool prof = ctx->prof;
+  auto mark = [&](int i, cudaStream_t s) -> pufe_status {
+    if (prof) PUFE_CUDA_TRY(cudaEventRecord(ctx->pev[i], s));
+    return PUFE_OK;
+  };
+  if (prof)
+    for (bool &r : ctx->prof_ran) r = false;
+  if (pufe_status e = mark(0, st)) return e;
+  if (prof) ctx->prof_ran[0] = true;
+  if (what & PUFE_WANT_H) PUFE_CUDA_TRY(cudaMemsetAsync(H, 0, bytes, st));
+  if (what & PUFE_WANT_S) PUFE_CUDA_TRY(cudaMemcpyAsync(S, D.S0, bytes, cudaMemcpyDeviceToDevice, st));
+  PUFE_CUDA_TRY(cudaEventRecord(D.ev_fork, st));
+  PUFE_CUDA_TRY(cudaStreamWaitEvent(D.side, D.ev_fork, 0));
+  if (what & PUFE_WANT_S) {
+    if (pufe_status e = mark(4, D.side)) return e;
+    pufe_status e0 = launch_see64(ctx, nullptr, S, nullptr, 0, (int)ctx->nelem, D.side);
+    if (e0 != PUFE_OK) return e0;
+    if (pufe_status e = mark(5, D.side)) return e;
+    if (prof) ctx->prof_ran[2] = true;
+  }
   if (what & PUFE_WANT_H) {
-    // H = 0; the FE-FE kernel then runs on the context's side stream,
-    // concurrently with the strip kernels below (both only add into H)
-    if (ctx->max_part_p > 16) return fail(PUFE_EINVAL, "rule with more than 16 points per axis");
-    PUFE_CUDA_TRY(cudaMemsetAsync(H, 0, bytes, st));
-    PUFE_CUDA_TRY(cudaEventRecord(D.ev_fork, st));
-    PUFE_CUDA_TRY(cudaStreamWaitEvent(D.side, D.ev_fork, 0));
+    if (pufe_status e = mark(2, D.side)) return e;
     pufe_status e0 = launch_fefe(ctx, V, H, D.side);
     if (e0 != PUFE_OK) return e0;
-    PUFE_CUDA_TRY(cudaEventRecord(D.ev_join, D.side));
+    if (pufe_status e = mark(3, D.side)) return e;
+    if (prof) ctx->prof_ran[1] = true;
   }
-  if (what & PUFE_WANT_S) PUFE_CUDA_TRY(cudaMemcpyAsync(S, D.S0, bytes, cudaMemcpyDeviceToDevice, st));
+  PUFE_CUDA_TRY(cudaEventRecord(D.ev_join, D.side));
   // elements are ordered with n_e > 128 first (256-row tensor-core tile),
   // then the rest (sum-factorized strip on the CUDA cores)
   if (nbig > 0) {
@@ -1041,14 +1084,47 @@ static pufe_status run_assemble_tc(pufe_ctx *ctx, const double *V, int what, dou
     PUFE_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device));
     PUFE_CUDA_TRY(cudaFuncSetAttribute(k_assemble_tc,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm256));
+    if (pufe_status e = mark(6, st)) return e;
     k_assemble_tc<<<std::min(nbig, nsm), WS_NT, sm256, st>>>(
         D.order, D.qoff, D.qpoff, D.ptab, vscratch, D.doff, D.ecol, D.aoff, D.toff32, D.psi32,
         D.soff, D.smap, sx, sy, sz, nbig, amax, inb, what, H, S, D.err);
     PUFE_CUDA_TRY(cudaGetLastError());
+    if (pufe_status e = mark(7, st)) return e;
+    if (prof) ctx->prof_ran[3] = true;
   }
+  if (pufe_status e = mark(8, st)) return e;
   pufe_status e1 = launch_strip_sf(ctx, (what & PUFE_WANT_H) ? V : nullptr, what, H, S, nbig, nsmall, st);
   if (e1 != PUFE_OK) return e1;
-  if (what & PUFE_WANT_H) PUFE_CUDA_TRY(cudaStreamWaitEvent(st, D.ev_join, 0));
+  if (pufe_status e = mark(9, st)) return e;
+  if (prof) ctx->prof_ran[4] = nsmall > 0;
+  PUFE_CUDA_TRY(cudaStreamWaitEvent(st, D.ev_join, 0));
+  if (pufe_status e = mark(1, st)) return e;
+  return PUFE_OK;
+}
+
+pufe_status launch_wait_probe(pufe_ctx *ctx, uint64_t wait_ns, cudaStream_t st) {
+  k_wait_probe<<<1, 32, 0, st>>>(wait_ns, ctx->d.err);
+  PUFE_CUDA_TRY(cudaGetLastError());
+  return PUFE_OK;
+}
+
+pufe_status profile_enable(pufe_ctx *ctx, bool on) {
+  if (on && !ctx->pev[0])
+    for (auto &ev : ctx->pev) PUFE_CUDA_TRY(cudaEventCreate(&ev));
+  ctx->prof = on;
+  return PUFE_OK;
+}
+
+pufe_status profile_read(pufe_ctx *ctx, double ms[5]) {
+  for (int k = 0; k < 5; ++k) ms[k] = 0.0;
+  if (!ctx->pev[0] || !ctx->prof_ran[0]) return fail(PUFE_ESTATE, "no instrumented call to read");
+  PUFE_CUDA_TRY(cudaEventSynchronize(ctx->pev[1]));
+  for (int k = 0; k < 5; ++k) {
+    if (!ctx->prof_ran[k]) continue;
+    float t = 0.0f;
+    PUFE_CUDA_TRY(cudaEventElapsedTime(&t, ctx->pev[2 * k], ctx->pev[2 * k + 1]));
+    ms[k] = t;
+  }
   return PUFE_OK;
 }
 
@@ -1124,7 +1200,8 @@ pufe_status launch_adjoint_tc(pufe_ctx *ctx, const double *Hbar, double *Vbar, c
 // stays resident until the process exits); larger contexts are rejected.
 // The device address of the array is looked up once per device with
 // cudaGetSymbolAddress (the host-side symbol is only a stand-in) on the
-// first call made on that device.
+// first call made on that device; it stays valid while that device's primary
+// context lives (a cudaDeviceReset ends it).
 // ---------------------------------------------------------------------------
 #define PUFE_STATIC_MAX_POINTS (4 * 1024 * 1024)
 static __device__ __align__(256) float g_vpad_static[PUFE_STATIC_MAX_POINTS];
@@ -1150,10 +1227,13 @@ static pufe_status static_scratch(int device, float **out) {
 
 pufe_status launch_assemble_tc_static(pufe_ctx *ctx, const double *V, int what, double *H,
                                       double *S, cudaStream_t st) {
-  if (ctx->nq_pad > PUFE_STATIC_MAX_POINTS)
-    return fail(PUFE_EINVAL, "pufe_assemble_HS_static: the context has " +
-                                 std::to_string(ctx->nq_pad) +
-                                 " padded quadrature points; the static scratch holds " +
+  // the array is indexed by the padded point offsets of the n_e > 128
+  // elements (the only ones whose V it carries)
+  if (ctx->big_pad_end > PUFE_STATIC_MAX_POINTS)
+    return fail(PUFE_EINVAL, "pufe_assemble_HS_static: the elements with more than 128 basis "
+                             "functions end at padded quadrature point " +
+                                 std::to_string(ctx->big_pad_end) +
+                                 "; the static scratch holds " +
                                  std::to_string(PUFE_STATIC_MAX_POINTS));
   float *vs = nullptr;
   if (pufe_status e0 = static_scratch(ctx->device, &vs)) return e0;

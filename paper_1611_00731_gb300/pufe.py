@@ -31,7 +31,8 @@ EXPORTS = ["pufe_build_mesh", "pufe_get_sizes", "pufe_get_quadrature", "pufe_get
            "pufe_assemble_HS_static", "pufe_ion_density", "pufe_effective_potential",
            "pufe_scf_step", "pufe_scf_reset", "pufe_assemble_HS_bloch", "pufe_density_bloch",
            "pufe_assemble_HV_adjoint_bloch", "pufe_nonlocal_projections",
-           "pufe_nonlocal_projections_bloch"]
+           "pufe_nonlocal_projections_bloch", "pufe_get_element_slots",
+           "pufe_profile_assembly", "pufe_profile_read", "pufe_selftest_timeout"]
 
 
 def _projector_array(projs):
@@ -124,6 +125,10 @@ def load_library(build_if_missing: bool = True):
     lib.pufe_assemble_HS_bloch.argtypes = [vp, dp, vp, C.c_int, C.c_int, vp, vp, vp, vp, vp]
     lib.pufe_density_bloch.argtypes = [vp, dp, vp, vp, C.c_int64, vp, C.c_int, vp, vp]
     lib.pufe_assemble_HV_adjoint_bloch.argtypes = [vp, dp, vp, vp, vp, vp]
+    lib.pufe_get_element_slots.argtypes = [vp, i32p]
+    lib.pufe_profile_assembly.argtypes = [vp, C.c_int]
+    lib.pufe_profile_read.argtypes = [vp, dp]
+    lib.pufe_selftest_timeout.argtypes = [vp, C.c_uint64, vp]
     lib.pufe_destroy.argtypes = [vp]
     lib.pufe_destroy.restype = None
     lib.pufe_last_error.restype = C.c_char_p
@@ -195,6 +200,26 @@ class Context:
         dofs = np.empty(int(n_e.sum()), dtype=np.int32)
         _check(_LIB.pufe_get_element_basis(self._h, None, dofs.ctypes.data_as(C.POINTER(C.c_int32))))
         return n_e, dofs
+
+    def element_slots(self):
+        """Enrichment functions (slots) in each element's basis."""
+        a = np.empty(self.n_elem, dtype=np.int32)
+        _check(_LIB.pufe_get_element_slots(self._h, a.ctypes.data_as(C.POINTER(C.c_int32))))
+        return a
+
+    # -- diagnostics and instrumentation -------------------------------------
+    def pufe_selftest_timeout(self, wait_ns=100_000_000, stream=None):
+        _check(_LIB.pufe_selftest_timeout(self._h, int(wait_ns), _stream(stream)))
+
+    def pufe_profile_assembly(self, enable=True):
+        _check(_LIB.pufe_profile_assembly(self._h, int(bool(enable))))
+
+    def pufe_profile_read(self):
+        """ms of the last instrumented mixed assembly: call, FE-FE, FP64 E-E of
+        S, tensor-core tile, strip (0 for kernels that did not run)."""
+        ms = np.zeros(5, dtype=np.float64)
+        _check(_LIB.pufe_profile_read(self._h, ms.ctypes.data_as(C.POINTER(C.c_double))))
+        return dict(zip(("call", "fefe", "see64", "tc", "strip"), ms.tolist()))
 
     # -- compute calls --------------------------------------------------------
     def pufe_tabulate(self, prec=PUFE_FP64, stream=None):

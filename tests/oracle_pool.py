@@ -109,3 +109,42 @@ def ionic_potential(wl, pts, nproc=None):
     with _pool(nproc) as pool:
         parts = pool.map(_potential_chunk, jobs)
     return np.concatenate(parts)
+
+
+def dof_grid_coords(wl):
+    """Integer positions of every DOF on the (3 nel)^3 node grid of the
+    oracle's mesh (FE nodes; enrichment DOFs at their PU vertex), for the
+    oracle's nested-dissection order."""
+    from oracle import mesh as omesh
+    m = omesh.Mesh(wl)
+    nf, n = m.nfe_axis, m.nel
+    g = np.arange(m.n_fe)
+    ev = np.array([v for (_, v) in m.enr_dof_info], dtype=np.int64)
+    fe = np.stack([g % nf, (g // nf) % nf, g // (nf * nf)], axis=1)
+    en = 3 * np.stack([ev % n, (ev // n) % n, ev // (n * n)], axis=1)
+    return np.concatenate([fe, en.reshape(-1, 3)]), nf
+
+
+def _density_chunk(args):
+    wl, lo, hi, pts, C, f, off = args
+    from oracle import assemble as oasm, mesh as omesh
+    m = omesh.Mesh(wl)
+    out = np.zeros(len(pts))
+    for e in range(lo, hi):
+        s = slice(off[e] - off[lo], off[e + 1] - off[lo])
+        B, _ = oasm.element_basis(m, e, pts[s])
+        Y = B @ C[m.elem_dofs(e)]
+        out[s] = (np.abs(Y) ** 2) @ f
+    return out
+
+
+def density(wl, rules, C, f, nproc=None):
+    """The oracle's density n(x_q) = sum_k f_k |psi_k(x_q)|^2 at every point
+    (``oracle.assemble.density``, element ranges in parallel)."""
+    pts, wts, off = rules
+    nproc = nproc or _workers()
+    jobs = [(wl, lo, hi, pts[off[lo]:off[hi]], C, f, off)
+            for lo, hi in _chunks(len(off) - 1, 4 * nproc)]
+    with _pool(nproc) as pool:
+        parts = pool.map(_density_chunk, jobs)
+    return np.concatenate(parts)

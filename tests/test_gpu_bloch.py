@@ -105,7 +105,7 @@ def test_empty_lattice_bands_at_k_on_the_gpu():
 
 
 # ---- mixed precision (PUFE_TF32X3): FP32 element blocks, phased scatter -----
-TOL_TF32 = 3e-5     # the Gamma-point mixed bound (tests/test_gpu_parity.py)
+TOL_TF32 = 5e-6     # the Gamma-point FP32 block bound (tests/test_gpu_parity.py), FP32 phases
 
 MIXED_CASES = {
     "two_atom_2cube": lambda: W.small_two_atom(nel=2, quad_p=6),

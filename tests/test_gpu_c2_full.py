@@ -1,0 +1,153 @@
+"""Full-size parity on the 12^3 rocksalt cell, the configuration bench.py times.
+
+The oracle assembles the whole cell (1,728 elements, 389,664 points,
+N = 51,576) with the physical Gaussian-ion potential (Sec. 3), in a pool of
+host processes, and finds the lowest 12 states by nested-dissection
+shift-invert Lanczos.  Against it:
+
+* FP64 path: H and S element by element, max |dX| / max |X| <= 1e-12 (and the
+  relative Frobenius norm).
+* Mixed path: every block of H and S (FE-FE, FE-E, E-E) against its own
+  largest entry, so that an error in a small block (the enrichment block of
+  S, where cond(S) amplifies it) cannot hide behind the large FE entries.
+  Bounds from the arithmetic: FP32 values (Psi, grad Psi, xi, V, w rounded
+  to 24 bits: ~2^-24 relative each, a few ulp for the tabulated Psi) summed
+  with round-to-nearest FP32 multiply-adds along the three axes of a p^3
+  (sub)cell (p <= 10: at most 3p = 30 roundings per output in the worst
+  case, sqrt(3p) typically): 30 * 2^-24 = 1.8e-6 per unit of the summed
+  magnitudes; the entries of a block are sums of terms no larger than its
+  largest entry times a few, hence 5e-6 for the FP32 blocks.  The FE-FE
+  blocks of S are exact FP64 constants (1e-12); the E-E block of S is FP64
+  arithmetic on the FP32-rounded enrichment values and points, whose own
+  rounding dominates (5e-6, the FP32 input bound).
+* Eigenvalues of the 8 lowest states: the GPU pencils' eigenvalues by
+  Rayleigh-Ritz on the oracle's 12 lowest eigenvectors (exact to second
+  order in the difference of the pencils), FP64 within 1e-10 Ha, mixed within
+  the 1e-5 Ha target.
+* Density of the 8 states (f = 2, closed shells): FP64 1e-12, mixed 1e-5 of
+  max n; sum_q w_q n_q = 16.
+"""
+import os
+import sys
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+sys.path.insert(0, os.path.dirname(__file__))
+import oracle_pool as OP  # noqa: E402
+from oracle import eig as oeig  # noqa: E402
+from paper_1611_00731_gb300 import pufe, workloads as W  # noqa: E402
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+NSTATES = 8
+TOL64 = 1e-12
+TOL_BLOCK = {("H", "FF"): 5e-6, ("H", "FE"): 5e-6, ("H", "EE"): 5e-6,
+             ("S", "FF"): 1e-12, ("S", "FE"): 5e-6, ("S", "EE"): 5e-6}
+TOL_EIG_MIXED = 1e-5
+
+
+def _csr(ctx, vals):
+    rowptr, col = ctx.pattern()
+    return sp.csr_matrix((vals, col, rowptr), shape=(ctx.n_dof, ctx.n_dof))
+
+
+def _gpu_HS(ctx, V, prec):
+    dev = torch.device("cuda:0")
+    H = torch.empty(ctx.nnz, dtype=torch.float64, device=dev)
+    S = torch.empty_like(H)
+    ctx.pufe_tabulate(prec)
+    ctx.pufe_assemble_HS(torch.tensor(V, device=dev), H, S, prec=prec)
+    ctx.pufe_sync_status()
+    return _csr(ctx, H.cpu().numpy()), _csr(ctx, S.cpu().numpy())
+
+
+@pytest.fixture(scope="module")
+def c2():
+    wl = W.workload("c2_rocksalt_12cube")
+    rules = OP.all_rules(wl, wl["nel"] ** 3)
+    V = OP.ionic_potential(wl, rules[0])
+    Ho, So = OP.assemble_HS(wl, rules, V)
+    coords, period = OP.dof_grid_coords(wl)
+    perm = oeig.nested_dissection_order(coords, period)
+    wo, Xo = oeig.lowest_eigs_shift_invert(Ho, So, 12, V.min() - 0.1, perm)
+    f = np.full(NSTATES, 2.0)
+    Cn = np.ascontiguousarray(Xo[:, :NSTATES])
+    rho_o = OP.density(wl, rules, Cn, f)
+    ctx = pufe.pufe_build_mesh(wl)
+    x, w, off = ctx.quadrature()
+    assert np.array_equal(off, rules[2])
+    assert np.abs(x - rules[0]).max() < 1e-13
+    assert np.abs(w - rules[1]).max() < 1e-13 * np.abs(rules[1]).max()
+    gpu = {prec: _gpu_HS(ctx, V, prec) for prec in (pufe.PUFE_FP64, pufe.PUFE_TF32X3)}
+    return dict(wl=wl, rules=rules, V=V, Ho=Ho, So=So, wo=wo, Xo=Xo, f=f, Cn=Cn, rho_o=rho_o,
+                ctx=ctx, gpu=gpu)
+
+
+def _block_max(X, nfe):
+    """Largest |entry| of X on each of its FE-FE, FE-E and E-E blocks."""
+    X = X.tocsr()
+    row = np.repeat(np.arange(X.shape[0]), np.diff(X.indptr))
+    fr, fc = row < nfe, X.indices < nfe
+    out = {}
+    for blk, sel in (("FF", fr & fc), ("FE", fr ^ fc), ("EE", ~fr & ~fc)):
+        out[blk] = float(np.abs(X.data[sel]).max()) if sel.any() else 0.0
+    return out
+
+
+def test_c2_fp64_matrices_elementwise(c2):
+    Hg, Sg = c2["gpu"][pufe.PUFE_FP64]
+    for name, G, O in (("H", Hg, c2["Ho"]), ("S", Sg, c2["So"])):
+        D = G - O
+        e_max = abs(D).max() / abs(O).max()
+        e_fro = sp.linalg.norm(D) / sp.linalg.norm(O)
+        print(f"C2 FP64 {name}: max {e_max:.2e} frobenius {e_fro:.2e}")
+        assert e_max < TOL64 and e_fro < TOL64, name
+
+
+def test_c2_mixed_matrices_per_block(c2):
+    Hg, Sg = c2["gpu"][pufe.PUFE_TF32X3]
+    nfe = (3 * c2["wl"]["nel"]) ** 3
+    out = []
+    for name, G, O in (("H", Hg, c2["Ho"]), ("S", Sg, c2["So"])):
+        # the oracle's summed matrix drops exact zeros (columns whose
+        # enrichment vanishes on every point of an element), so compare the
+        # difference's entries block by block with the oracle's block maxima
+        dmax, omax = _block_max(G - O, nfe), _block_max(O, nfe)
+        for blk in ("FF", "FE", "EE"):
+            out.append((name, blk, dmax[blk] / omax[blk]))
+    print("C2 mixed per-block max |dX| / max |X_block|: " +
+          ", ".join(f"{n}_{b} {e:.2e}" for n, b, e in out))
+    for n, b, e in out:
+        assert e < TOL_BLOCK[(n, b)], (n, b, e)
+
+
+def test_c2_eigenvalues(c2):
+    wo = c2["wo"][:NSTATES]
+    res = {}
+    for prec, tol in ((pufe.PUFE_FP64, 1e-10), (pufe.PUFE_TF32X3, TOL_EIG_MIXED)):
+        Hg, Sg = c2["gpu"][prec]
+        wg = oeig.rayleigh_ritz(Hg, Sg, c2["Xo"])[:NSTATES]
+        res[prec] = np.abs(wg - wo)
+        print(f"C2 eigenvalue errors (prec {prec}):", np.array2string(res[prec], precision=2))
+        assert res[prec].max() < tol, prec
+
+
+def test_c2_density_of_lowest_states(c2):
+    ctx = c2["ctx"]
+    dev = torch.device("cuda:0")
+    ro = c2["rho_o"]
+    w = c2["rules"][1]
+    assert abs(w @ ro - 2.0 * NSTATES) < 1e-9
+    for prec, tol in ((pufe.PUFE_FP64, TOL64), (pufe.PUFE_TF32X3, 1e-5)):
+        rho = torch.empty(ctx.n_q, dtype=torch.float64, device=dev)
+        ctx.pufe_tabulate(prec)
+        ctx.pufe_density(torch.tensor(c2["Cn"], device=dev), torch.tensor(c2["f"], device=dev),
+                         rho, prec=prec)
+        ctx.pufe_sync_status()
+        r = rho.cpu().numpy()
+        err = np.abs(r - ro).max() / np.abs(ro).max()
+        print(f"C2 density (prec {prec}): max {err:.2e}, sum w n - 16 = {w @ r - 16:.2e}")
+        assert err < tol, prec
