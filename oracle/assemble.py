@@ -37,13 +37,11 @@ from .fe import tricubic, trilinear
 
 def element_basis(mesh, e, pts):
     """Basis values B (Q, n) and physical gradients G (3, Q, n) of element e."""
-    lo, _ = mesh.elem_box(e)
-    h = mesh.h
-    xi = 2.0 * (pts - lo) / h - 1.0
+    xi = mesh.to_reference(e, pts)
     N, dN = tricubic(xi)
     P, dP = trilinear(xi)
-    dN = dN * (2.0 / h)
-    dP = dP * (2.0 / h)
+    dN = mesh.grad_to_physical(dN)
+    dP = mesh.grad_to_physical(dP)
     cols = mesh.elem_cols[e]
     n = 64 + len(cols)
     Q = pts.shape[0]
@@ -55,7 +53,7 @@ def element_basis(mesh, e, pts):
     for j, (dof, lv, k) in enumerate(cols):
         if k not in cache:
             al = mesh.alphas[k]
-            cache[k] = enrichment(al["orb"], al["rc"], al["tau"], mesh.a, pts)
+            cache[k] = enrichment(al["orb"], al["rc"], al["tau"], mesh.lattice, pts)
         psi, gpsi = cache[k]
         B[:, 64 + j] = P[:, lv] * psi
         G[:, :, 64 + j] = dP[:, :, lv] * psi + P[:, lv] * gpsi

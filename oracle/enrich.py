@@ -92,10 +92,13 @@ def orbital_value(orb, rc, d):
 
 
 def image_vectors(a, reach=2):
-    """Lattice vectors R = a (i1, i2, i3), i_k = -reach..reach (cubic cell)."""
+    """Lattice vectors R = i1 a1 + i2 a2 + i3 a3, i_k = -reach..reach (eq. Psi).
+    `a` is the cubic edge (a scalar) or the lattice (rows a1, a2, a3)."""
     rng = np.arange(-reach, reach + 1)
-    I = np.array(np.meshgrid(rng, rng, rng, indexing="ij")).reshape(3, -1).T
-    return a * I.astype(np.float64)
+    I = np.array(np.meshgrid(rng, rng, rng, indexing="ij")).reshape(3, -1).T.astype(np.float64)
+    if np.ndim(a) == 0:
+        return a * I
+    return I @ np.asarray(a, dtype=np.float64).reshape(3, 3)
 
 
 def enrichment(orb, rc, tau, a, pts, with_grad=True):

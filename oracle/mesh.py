@@ -23,14 +23,61 @@ when some image of alpha's atom lies at distance < r_c from the element box
 is dropped.  Within an element the enrichment columns are ordered by global
 DOF, then by local vertex.
 
+General (triclinic) cells, the paper's CeAl geometry (Sec. 6.2, eq.
+ceal-primitive): a workload with a "lattice" entry (rows a_1, a_2, a_3)
+divides the cell into nel^3 parallelepipeds in lattice coordinates,
+s_d in [e_d / nel, (e_d + 1) / nel]; an element maps the reference cube by
+x = x_0 + J (xi + 1), J = [a_1, a_2, a_3] / (2 nel) (columns), so the FE and
+PU functions keep their reference form and physical gradients are
+J^-T grad_xi.  Minimum-image distances search the neighbouring images of the
+lattice-coordinate rounding; the distance from an atom image to an element
+is the exact minimum over the parallelepiped (a box-constrained least-squares
+problem solved on each of its 27 faces).
+
 Pins: through the assembled matrices (tests/test_oracle_assembly.py) --
-partition of unity, empty-lattice spectrum, PU reproduction, translation.
+partition of unity, empty-lattice spectrum, PU reproduction, translation;
+for general cells (tests/test_oracle_triclinic.py) the partition of unity on
+mapped elements, the empty-lattice spectrum |G|^2/2 of a sheared cell on the
+reciprocal lattice, and the cubic cell written as a lattice.
 """
 from __future__ import annotations
 
 import numpy as np
 
 from .enrich import image_vectors
+
+
+def parallelepiped_dist(x0, M, P):
+    """Distances from points P (m, 3) to {x0 + M t : t in [0, 1]^3}.
+
+    The squared distance is a convex quadratic in t; its minimiser over the
+    box lies in the relative interior of one of the box's 27 faces (each
+    coordinate free, at 0 or at 1).  On every face the free coordinates solve
+    a small least-squares problem; a face whose minimiser stays inside the
+    box gives a point of the parallelepiped, and the smallest such distance
+    is the exact one (the true minimiser is among them).
+    """
+    P = np.atleast_2d(np.asarray(P, dtype=np.float64))
+    best = np.full(len(P), np.inf)
+    for code in range(27):
+        st = [(code // 3 ** d) % 3 for d in range(3)]   # 0 free, 1 at 0, 2 at 1
+        t = np.zeros((len(P), 3))
+        fixed = np.array([0.0 if c == 1 else 1.0 for c in st])
+        free = [d for d in range(3) if st[d] == 0]
+        base = x0 + M @ np.where(np.array(st) == 0, 0.0, fixed)
+        r = P - base
+        if free:
+            Mf = M[:, free]
+            sol = np.linalg.lstsq(Mf, r.T, rcond=None)[0].T
+            ok = ((sol >= 0.0) & (sol <= 1.0)).all(axis=1)
+            q = base + sol @ Mf.T
+        else:
+            ok = np.ones(len(P), dtype=bool)
+            q = np.broadcast_to(base, P.shape)
+        d = np.sqrt(((P - q) ** 2).sum(axis=1))
+        best = np.where(ok, np.minimum(best, d), best)
+        del t
+    return best
 
 
 def box_distance(lo, hi, p):
@@ -42,9 +89,20 @@ def box_distance(lo, hi, p):
 class Mesh:
     def __init__(self, wl):
         self.wl = wl
-        self.a = float(wl["a"])
         self.nel = int(wl["nel"])
-        self.h = self.a / self.nel
+        self.general = "lattice" in wl
+        if self.general:
+            self.L = np.array(wl["lattice"], dtype=np.float64).reshape(3, 3)   # rows a_d
+            self.a = None            # no cubic edge: cubic-only code paths fail loudly
+            self.h = None
+            self.J = self.L.T / (2.0 * self.nel)                               # columns a_d / 2nel
+            self.Jinv = np.linalg.inv(self.J)
+            self.detJ = abs(float(np.linalg.det(self.J)))
+            self.lattice = self.L
+        else:
+            self.a = float(wl["a"])
+            self.h = self.a / self.nel
+            self.lattice = self.a
         self.nelem = self.nel ** 3
         self.nfe_axis = 3 * self.nel
         self.n_fe = self.nfe_axis ** 3
@@ -56,7 +114,7 @@ class Mesh:
             sp = self.species[s]
             for io, orb in enumerate(sp["orbitals"]):
                 self.alphas.append(dict(atom=ia, orb=tuple(orb), rc=sp["r_c"], tau=tau))
-        self._images = image_vectors(self.a)
+        self._images = image_vectors(self.lattice)
         self._build()
 
     # -- geometry helpers --------------------------------------------------
@@ -69,21 +127,53 @@ class Mesh:
         lo = np.array([ex, ey, ez], dtype=np.float64) * self.h
         return lo, lo + self.h
 
+    def elem_origin(self, e):
+        """Corner x_0 of element e (the image of xi = (-1, -1, -1))."""
+        if not self.general:
+            return self.elem_box(e)[0]
+        return self.L.T @ (np.array(self.elem_coords(e), dtype=np.float64) / self.nel)
+
+    def to_reference(self, e, pts):
+        """Reference coordinates xi in [-1, 1]^3 of physical points of element e."""
+        if not self.general:
+            lo, _ = self.elem_box(e)
+            return 2.0 * (pts - lo) / self.h - 1.0
+        return (np.asarray(pts) - self.elem_origin(e)) @ self.Jinv.T - 1.0
+
+    def grad_to_physical(self, dN):
+        """Physical gradients (3, Q, k) from reference gradients (3, Q, k)."""
+        if not self.general:
+            return dN * (2.0 / self.h)
+        return np.einsum("kd,kqj->dqj", self.Jinv, dN)
+
     def vertex_pos(self, v):
         n = self.nel
-        return np.array([v % n, (v // n) % n, v // (n * n)], dtype=np.float64) * self.h
+        g = np.array([v % n, (v // n) % n, v // (n * n)], dtype=np.float64)
+        if not self.general:
+            return g * self.h
+        return self.L.T @ (g / n)
 
     def min_image_dist(self, x, tau):
         d = x - tau
-        d = d - self.a * np.round(d / self.a)
-        return float(np.sqrt((d * d).sum()))
+        if not self.general:
+            d = d - self.a * np.round(d / self.a)
+            return float(np.sqrt((d * d).sum()))
+        # round in lattice coordinates, then search the neighbouring images
+        s = np.linalg.solve(self.L.T, d)
+        d0 = self.L.T @ (s - np.round(s))
+        off = np.array(np.meshgrid([-1, 0, 1], [-1, 0, 1], [-1, 0, 1], indexing="ij")).reshape(3, -1).T
+        dd = d0 + off @ self.L
+        return float(np.sqrt((dd * dd).sum(axis=1)).min())
 
     def atom_box_dist(self, ia, e):
         """Smallest distance from any image tau + R of atom ia to element e."""
-        lo, hi = self.elem_box(e)
-        P = self.atoms[ia][1] + self._images
-        d = np.maximum(np.maximum(lo - P, P - hi), 0.0)
-        return float(np.sqrt((d * d).sum(axis=1)).min())
+        if not self.general:
+            lo, hi = self.elem_box(e)
+            P = self.atoms[ia][1] + self._images
+            d = np.maximum(np.maximum(lo - P, P - hi), 0.0)
+            return float(np.sqrt((d * d).sum(axis=1)).min())
+        return float(parallelepiped_dist(self.elem_origin(e), 2.0 * self.J,
+                                         self.atoms[ia][1] + self._images).min())
 
     # -- numbering -----------------------------------------------------------
     def fe_dofs(self, e):

@@ -1,4 +1,4 @@
-"""Local ionic potential of Gaussian charges in a periodic cubic cell (oracle).
+"""Local ionic potential of Gaussian charges in a periodic cell (oracle).
 
 Sec. 3 of the paper: the ionic potentials decay as Z_a / r and can be
 generated by localized ionic charge densities rho_I,a.  The workloads use
@@ -9,7 +9,9 @@ Omega, with the G = 0 term dropped (a neutralising background), is
     V_I(x) = -(4 pi / Omega) sum_{G != 0} sum_a Z_a e^{-G^2 sigma_a^2 / 4}
              cos(G . (x - tau_a)) / G^2 ,
 
-summed until the Gaussian factor falls below 1e-18.
+summed until the Gaussian factor falls below 1e-18, G on the reciprocal
+lattice of the cell (the cubic cell a I, or a general cell given by its
+lattice vectors).
 
 Pins (tests/test_oracle_potential.py): the FD Laplacian of V_I equals
 4 pi (rho_I - <rho_I>) (Poisson, Sec. 3 eq. poisson); V_I near an isolated
@@ -22,9 +24,30 @@ import math
 import numpy as np
 
 
+def _lattice(wl):
+    """Rows a_1, a_2, a_3 of the cell (the cubic cell a I unless given)."""
+    if "lattice" in wl:
+        return np.array(wl["lattice"], dtype=np.float64).reshape(3, 3)
+    return float(wl["a"]) * np.eye(3)
+
+
+def reciprocal_vectors(wl, gmax):
+    """Nonzero G = 2 pi L^-1 m (m integer) with |G| <= gmax, and |G|^2.  The
+    m range per axis follows from G . a_k = 2 pi m_k: |m_k| <= gmax |a_k| / 2 pi."""
+    L = _lattice(wl)
+    B = 2.0 * math.pi * np.linalg.inv(L)          # columns b_k, a_i . b_k = 2 pi delta_ik
+    mm = [int(math.ceil(gmax * np.linalg.norm(L[k]) / (2.0 * math.pi))) for k in range(3)]
+    M = np.array(np.meshgrid(*[np.arange(-m, m + 1) for m in mm], indexing="ij")).reshape(3, -1).T
+    M = M[(M != 0).any(axis=1)]
+    G = M.astype(np.float64) @ B.T
+    G2 = (G * G).sum(axis=1)
+    keep = G2 <= gmax * gmax
+    return G[keep], G2[keep]
+
+
 def ionic_potential(wl, pts):
-    a = float(wl["a"])
-    Omega = a ** 3
+    L = _lattice(wl)
+    Omega = abs(float(np.linalg.det(L)))
     pts = np.atleast_2d(np.asarray(pts, dtype=np.float64))
     out = np.zeros(pts.shape[0])
     if not wl["atoms"]:
@@ -32,14 +55,7 @@ def ionic_potential(wl, pts):
     sig_min = min(wl["species"][s]["sigma"] for s, _ in wl["atoms"])
     # e^{-G^2 s^2/4} < 1e-18  <=>  G > sqrt(4 * 18 ln 10) / s
     gmax = math.sqrt(4.0 * 18.0 * math.log(10.0)) / sig_min
-    mmax = int(math.ceil(gmax * a / (2.0 * math.pi)))
-    rng = np.arange(-mmax, mmax + 1)
-    M = np.array(np.meshgrid(rng, rng, rng, indexing="ij")).reshape(3, -1).T
-    M = M[(M != 0).any(axis=1)]
-    G = (2.0 * math.pi / a) * M.astype(np.float64)
-    G2 = (G * G).sum(axis=1)
-    keep = G2 <= gmax * gmax
-    G, G2 = G[keep], G2[keep]
+    G, G2 = reciprocal_vectors(wl, gmax)
     for s, tau in wl["atoms"]:
         sp = wl["species"][s]
         amp = -(4.0 * math.pi / Omega) * sp["Z"] * np.exp(-G2 * sp["sigma"] ** 2 / 4.0) / G2
@@ -51,11 +67,10 @@ def ionic_potential(wl, pts):
 
 def gaussian_charge(wl, pts):
     """Total periodic ionic charge density sum_a Z_a e^{-r^2/s^2}/(pi^1.5 s^3)."""
-    a = float(wl["a"])
     pts = np.atleast_2d(np.asarray(pts, dtype=np.float64))
     out = np.zeros(pts.shape[0])
     rng = np.arange(-2, 3)
-    R = a * np.array(np.meshgrid(rng, rng, rng, indexing="ij")).reshape(3, -1).T
+    R = np.array(np.meshgrid(rng, rng, rng, indexing="ij")).reshape(3, -1).T @ _lattice(wl)
     for s, tau in wl["atoms"]:
         sp = wl["species"][s]
         for r in R:

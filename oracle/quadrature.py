@@ -19,6 +19,10 @@ Three modes:
   rule (the paper does not say which of the two rules is kept; the more
   accurate one is used).  Elements without enrichment take p_far^3.
 
+General (triclinic) cells: the same rules on the reference cube, mapped by
+the element's affine map (weights times |det J|); children are halves of the
+reference cube along each axis.
+
 Point order: tensor rules run x fastest (gauss_box); children are visited
 depth first in the order a + 2 b + 4 c of their (a, b, c) offsets.
 
@@ -36,25 +40,39 @@ from .fe import gauss_box
 FIXED, PADAPT, HADAPT = 0, 1, 2
 
 
-def _integrals(mesh, alphas, lo, hi, p):
+def _box_rule(mesh, e):
+    """p^3 Gauss rule of a sub-box [lo, hi] of element e: physical boxes for
+    cubic cells; for general cells boxes of the reference cube, mapped by the
+    element's affine map (weights times |det J|)."""
+    if not mesh.general:
+        return gauss_box
+    x0 = mesh.elem_origin(e)
+
+    def rule(p, lo, hi):
+        r, w = gauss_box(p, lo, hi)
+        return x0 + (r + 1.0) @ mesh.J.T, w * mesh.detJ
+    return rule
+
+
+def _integrals(mesh, alphas, lo, hi, p, box=gauss_box):
     """I(Psi^2) and I(|grad Psi|^2) on box [lo, hi] with p^3 Gauss, per alpha."""
-    pts, wts = gauss_box(p, lo, hi)
+    pts, wts = box(p, lo, hi)
     out = []
     for k in alphas:
         al = mesh.alphas[k]
-        psi, g = enrichment(al["orb"], al["rc"], al["tau"], mesh.a, pts)
+        psi, g = enrichment(al["orb"], al["rc"], al["tau"], mesh.lattice, pts)
         out.append((float(wts @ (psi * psi)), float(wts @ (g * g).sum(axis=0))))
     return np.array(out).reshape(-1, 2)
 
 
-def _hadapt(mesh, alphas, lo, hi, depth, q):
+def _hadapt(mesh, alphas, lo, hi, depth, q, box=gauss_box):
     tol = q["tol"]
-    i5 = _integrals(mesh, alphas, lo, hi, 5)
-    i8 = _integrals(mesh, alphas, lo, hi, 8)
+    i5 = _integrals(mesh, alphas, lo, hi, 5, box)
+    i8 = _integrals(mesh, alphas, lo, hi, 8, box)
     err = np.abs(i5 - i8)
     failing = [k for k, row in zip(alphas, err) if (row >= tol).any()]
     if not failing or depth >= q["max_depth"]:
-        return [gauss_box(8, lo, hi)]
+        return [box(8, lo, hi)]
     mid = (lo + hi) / 2.0
     parts = []
     for c in range(2):
@@ -63,32 +81,36 @@ def _hadapt(mesh, alphas, lo, hi, depth, q):
                 off = np.array([a, b, c])
                 clo = np.where(off == 0, lo, mid)
                 chi = np.where(off == 0, mid, hi)
-                parts += _hadapt(mesh, failing, clo, chi, depth + 1, q)
+                parts += _hadapt(mesh, failing, clo, chi, depth + 1, q, box)
     return parts
 
 
 def element_rule(mesh, e):
     """Quadrature rule of element e: physical points (Q,3) and weights (Q,)."""
     q = mesh.wl["quad"]
-    lo, hi = mesh.elem_box(e)
+    box = _box_rule(mesh, e)
+    if mesh.general:
+        lo, hi = -np.ones(3), np.ones(3)
+    else:
+        lo, hi = mesh.elem_box(e)
     mode = q["mode"]
     if mode == FIXED:
         p = q["p_near"] if mesh.near[e].any() else q["p_far"]
-        return gauss_box(p, lo, hi)
+        return box(p, lo, hi)
     alphas = mesh.elem_alphas(e)
     if mode == PADAPT:
         if not alphas:
-            return gauss_box(q["p_min"], lo, hi)
+            return box(q["p_min"], lo, hi)
         for p in range(q["p_min"], q["p_max"] + 1):
-            err = np.abs(_integrals(mesh, alphas, lo, hi, p)
-                         - _integrals(mesh, alphas, lo, hi, p + 2))
+            err = np.abs(_integrals(mesh, alphas, lo, hi, p, box)
+                         - _integrals(mesh, alphas, lo, hi, p + 2, box))
             if (err < q["tol"]).all():
-                return gauss_box(p, lo, hi)
-        return gauss_box(q["p_max"], lo, hi)
+                return box(p, lo, hi)
+        return box(q["p_max"], lo, hi)
     if mode == HADAPT:
         if not alphas:
-            return gauss_box(q["p_far"], lo, hi)
-        parts = _hadapt(mesh, alphas, lo, hi, 0, q)
+            return box(q["p_far"], lo, hi)
+        parts = _hadapt(mesh, alphas, lo, hi, 0, q, box)
         return (np.concatenate([p for p, _ in parts]),
                 np.concatenate([w for _, w in parts]))
     raise ValueError(mode)

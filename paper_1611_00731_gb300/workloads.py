@@ -116,6 +116,46 @@ def small_two_atom(nel: int = 2, a: float = 4.0, quad_p: int = 4,
                 nocc=2, nelec=4.0)
 
 
+# The triclinic CeAl cell of Sec. 6.2 (eq. ceal-primitive): lattice vectors
+# and atom positions in lattice coordinates as printed, in units of a.
+CEAL_A = 5.75
+CEAL_LATTICE = ((1.00, 0.02, -0.04), (0.01, 0.98, 0.03), (0.03, -0.06, 1.09))
+CEAL_TAU_LATTICE = ((0.01, 0.02, 0.03), (0.51, 0.47, 0.55))
+
+
+def ceal_like(nel: int = 2, quad_p: int = 6, r_c: float = 2.5, r_e: float = 2.0,
+              full_orbitals: bool = False) -> dict:
+    """The CeAl geometry with the synthetic Ce-like and Al-like species (a
+    reduced orbital set unless `full_orbitals`): a general cell given by its
+    lattice (rows a_1, a_2, a_3, bohr), nel^3 elements in lattice
+    coordinates, a fixed p^3 rule on every element."""
+    L = [[CEAL_A * c for c in row] for row in CEAL_LATTICE]
+    ce, al = dict(CE_LIKE), dict(AL_LIKE)
+    if not full_orbitals:   # 4s 4p (Ce-like), 3s 3p (Al-like)
+        ce["orbitals"] = [o for o in CE_LIKE["orbitals"] if o[0] == 4 and o[1] <= 1]
+        al["orbitals"] = [o for o in AL_LIKE["orbitals"] if o[0] == 3]
+    sp = [_species(ce, r_c, r_e), _species(al, r_c, r_e)]
+    atoms = [(i, tuple(sum(s[k] * L[k][d] for k in range(3)) for d in range(3)))
+             for i, s in enumerate(CEAL_TAU_LATTICE)]
+    return dict(name=f"ceal_like_{nel}cube", lattice=L, a=None, nel=nel, species=sp,
+                atoms=atoms,
+                quad=dict(mode=QUAD_FIXED, p_far=quad_p, p_near=quad_p, p_min=0, p_max=0,
+                          tol=1e-6, max_depth=0),
+                nocc=4, nelec=8.0)
+
+
+def sheared_empty(nel: int = 3, p: int = 4) -> dict:
+    """No atoms, no enrichment, the CeAl lattice: the tricubic space on a
+    general cell (its empty-lattice spectrum is |G|^2 / 2 on the reciprocal
+    lattice)."""
+    L = [[CEAL_A * c for c in row] for row in CEAL_LATTICE]
+    return dict(name=f"sheared_empty_{nel}cube", lattice=L, a=None, nel=nel, species=[],
+                atoms=[],
+                quad=dict(mode=QUAD_FIXED, p_far=p, p_near=p, p_min=0, p_max=0, tol=1e-6,
+                          max_depth=0),
+                nocc=1, nelec=2.0)
+
+
 def empty_lattice(nel: int = 2, a: float = 4.0, p: int = 4) -> dict:
     """No atoms, no enrichment: the classical tricubic space on its own."""
     return dict(name=f"empty_{nel}cube", a=a, nel=nel, species=[], atoms=[],
