@@ -21,7 +21,8 @@
  *     (the paper's rho_e = -n).
  *
  * Conventions
- *   Units: bohr and hartree.  Cubic or orthorhombic cells only.
+ *   Units: bohr and hartree.  Orthorhombic cells, or general (triclinic)
+ *   cells given by their lattice vectors (pufe_cell.lattice).
  *   Numbering: elements e = ex + nx (ey + ny ez).  FE DOFs are the nodes of
  *   the (3nx)(3ny)(3nz) periodic grid, index gx + 3nx (gy + 3ny gz); they are
  *   followed by the enrichment DOFs ordered by (atom, orbital, enriched
@@ -101,11 +102,20 @@ enum {
 enum { PUFE_WANT_H = 1, PUFE_WANT_S = 2 };
 
 typedef struct {
-  double a[3];         /* cell edge lengths (bohr), orthorhombic */
+  double a[3];         /* cell edge lengths (bohr) of an orthorhombic cell */
   int nel[3];          /* elements per axis, each >= 1 */
   int natoms;          /* >= 0 */
   const double *tau;   /* natoms x 3 Cartesian positions (host) */
   const int *species;  /* natoms species indices (host) */
+  const double *lattice; /* NULL: the orthorhombic cell a[].  Else a general
+                            (triclinic) cell (Sec. 6.2, the CeAl cell): 9
+                            values (host), the rows a_1, a_2, a_3 in bohr,
+                            divided into nel[d] elements along a_d; each
+                            element is a parallelepiped x = x_0 + J (xi + 1),
+                            J = [a_1/2nel_1, a_2/2nel_2, a_3/2nel_3], and a[]
+                            is not read.  General cells take the FP64 path
+                            (tabulation, assembly, Bloch assembly, density,
+                            adjoint); the other calls return PUFE_EINVAL. */
 } pufe_cell;
 
 typedef struct {

@@ -47,8 +47,10 @@ def elem_shifts(mesh, e):
 
 
 def elem_phases(mesh, e, k):
-    """exp(i k . R_i) of every element column (cubic cell of edge a)."""
-    R = elem_shifts(mesh, e) * mesh.a
+    """exp(i k . R_i) of every element column, R_i = sum_d shift_d a_d (the
+    cubic cell's edge a, or the lattice vectors of a general cell)."""
+    sh = elem_shifts(mesh, e)
+    R = sh @ mesh.L if mesh.general else sh * mesh.a
     return np.exp(1j * (R @ np.asarray(k, dtype=np.float64)))
 
 

@@ -14,7 +14,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIBDIR = os.path.join(HERE, "_lib")
 LIBPATH = os.path.join(LIBDIR, "libpufe.so")
-SOURCES = ["pufe_setup.cu", "pufe_fp64.cu", "pufe_tc.cu", "pufe_fefe.cu", "pufe_strip.cu", "pufe_see64.cu", "pufe_scf.cu", "pufe_api.cu"]
+SOURCES = ["pufe_setup.cu", "pufe_fp64.cu", "pufe_tc.cu", "pufe_fefe.cu", "pufe_strip.cu", "pufe_see.cu", "pufe_scf.cu", "pufe_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

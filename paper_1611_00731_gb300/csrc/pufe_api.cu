@@ -38,6 +38,8 @@ extern "C" {
 pufe_status pufe_tabulate(pufe_ctx *ctx, int prec, void *stream) {
   if (pufe_status e0 = need_device(ctx)) return e0;
   if (prec != PUFE_FP64 && prec != PUFE_TF32X3) return fail(PUFE_EINVAL, "unknown precision");
+  if (prec == PUFE_TF32X3 && ctx->general)
+    return fail(PUFE_EINVAL, "PUFE_TF32X3 takes orthorhombic cells; general cells take PUFE_FP64");
   DeviceGuard g(ctx->device);
   if (!g.ok) return fail(PUFE_ECUDA, "cudaSetDevice failed");
   pufe_status st;
@@ -52,6 +54,8 @@ pufe_status pufe_tabulate(pufe_ctx *ctx, int prec, void *stream) {
 }
 
 static pufe_status need_table(const pufe_ctx *ctx, int prec) {
+  if (prec == PUFE_TF32X3 && ctx->general)
+    return fail(PUFE_EINVAL, "PUFE_TF32X3 takes orthorhombic cells; general cells take PUFE_FP64");
   if (ctx->psi_len == 0) return PUFE_OK;
   if (prec == PUFE_FP64 && !ctx->tabulated)
     return fail(PUFE_ESTATE, "call pufe_tabulate(PUFE_FP64) first");
@@ -81,6 +85,7 @@ pufe_status pufe_assemble_HS(pufe_ctx *ctx, const double *V, int prec, int what,
 pufe_status pufe_assemble_HS_static(pufe_ctx *ctx, const double *V, int what, double *H,
                                     double *S, void *stream) {
   if (pufe_status e0 = need_device(ctx)) return e0;
+  if (ctx->general) return fail(PUFE_EINVAL, "pufe_assemble_HS_static takes orthorhombic cells");
   if (pufe_status e1 = need_table(ctx, PUFE_TF32X3)) return e1;
   if (what <= 0 || what > (PUFE_WANT_H | PUFE_WANT_S)) return fail(PUFE_EINVAL, "bad `what` mask");
   if ((what & PUFE_WANT_H) && (!H || !V)) return fail(PUFE_EINVAL, "H wanted: need H and V");
@@ -193,6 +198,7 @@ static pufe_status upload_projectors(pufe_ctx *ctx, int nproj, const pufe_projec
 pufe_status pufe_nonlocal_projections(pufe_ctx *ctx, int nproj, const pufe_projector *proj,
                                       double *F, void *stream) {
   if (pufe_status e0 = need_device(ctx)) return e0;
+  if (ctx->general) return fail(PUFE_EINVAL, "this call takes orthorhombic cells");
   if (pufe_status e1 = need_table(ctx, PUFE_FP64)) return e1;
   if (!F) return fail(PUFE_EINVAL, "F must not be NULL");
   DeviceGuard g(ctx->device);
@@ -207,6 +213,7 @@ pufe_status pufe_nonlocal_projections_bloch(pufe_ctx *ctx, const double *k, int 
                                             const pufe_projector *proj, double *F_re,
                                             double *F_im, void *stream) {
   if (pufe_status e0 = need_device(ctx)) return e0;
+  if (ctx->general) return fail(PUFE_EINVAL, "this call takes orthorhombic cells");
   if (pufe_status e1 = need_table(ctx, PUFE_FP64)) return e1;
   if (!k || !F_re || !F_im) return fail(PUFE_EINVAL, "k, F_re and F_im must not be NULL");
   DeviceGuard g(ctx->device);
@@ -222,6 +229,7 @@ pufe_status pufe_nonlocal_projections_bloch(pufe_ctx *ctx, const double *k, int 
 pufe_status pufe_ion_density(pufe_ctx *ctx, int natoms, const double *tau, const double *Z,
                              const double *sigma, double *rho_I, void *stream) {
   if (pufe_status e0 = need_device(ctx)) return e0;
+  if (ctx->general) return fail(PUFE_EINVAL, "this call takes orthorhombic cells");
   if (natoms < 0 || !rho_I || (natoms > 0 && (!tau || !Z || !sigma)))
     return fail(PUFE_EINVAL, "need natoms >= 0, rho_I, and tau, Z, sigma for the atoms");
   for (int a = 0; a < natoms; ++a)
@@ -234,6 +242,7 @@ pufe_status pufe_ion_density(pufe_ctx *ctx, int natoms, const double *tau, const
 pufe_status pufe_effective_potential(pufe_ctx *ctx, const double *n, const double *rho_I,
                                      double *V_eff, double *V_C, double *eps_xc, void *stream) {
   if (pufe_status e0 = need_device(ctx)) return e0;
+  if (ctx->general) return fail(PUFE_EINVAL, "this call takes orthorhombic cells");
   if (!n || !rho_I || !V_eff) return fail(PUFE_EINVAL, "n, rho_I and V_eff must not be NULL");
   DeviceGuard g(ctx->device);
   if (!g.ok) return fail(PUFE_ECUDA, "cudaSetDevice failed");
@@ -245,6 +254,7 @@ pufe_status pufe_scf_step(pufe_ctx *ctx, int nstates, const double *eps, const d
                           const double *rho_I, const double *V_eff_in, double *n,
                           double *V_eff_out, double *f_out, pufe_scf_info *info, void *stream) {
   if (pufe_status e0 = need_device(ctx)) return e0;
+  if (ctx->general) return fail(PUFE_EINVAL, "this call takes orthorhombic cells");
   if (prec != PUFE_FP64 && prec != PUFE_TF32X3) return fail(PUFE_EINVAL, "unknown precision");
   if (pufe_status e1 = need_table(ctx, prec)) return e1;
   if (nstates < 1 || nstates > 64 || ldc < nstates)

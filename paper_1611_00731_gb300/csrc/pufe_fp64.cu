@@ -26,11 +26,12 @@ __device__ __forceinline__ void set_err(unsigned *err, unsigned bit) { atomicOr(
 // K0: Psi and grad Psi for every (enrichment slot, quadrature point) of an element.
 // Layout per element: psi[4*toff[e] + (slot*4 + comp)*Q + q].
 // ---------------------------------------------------------------------------
+// (general cells: `gen` with the lattice `lat`, Sec. 6.2)
 __global__ void k_tabulate(const int64_t *__restrict__ qoff, const double *__restrict__ x,
                            const int32_t *__restrict__ aoff, const int32_t *__restrict__ alist,
                            const int64_t *__restrict__ toff, const Orbital *__restrict__ orb,
                            double a0, double a1, double a2, int i0, int i1, int i2,
-                           double *__restrict__ psi) {
+                           double *__restrict__ psi, int gen, LatticeDev lat) {
   const int64_t e = blockIdx.x;
   const int64_t q0 = qoff[e];
   const int Q = (int)(qoff[e + 1] - q0);
@@ -43,7 +44,10 @@ __global__ void k_tabulate(const int64_t *__restrict__ qoff, const double *__res
     const Orbital o = orb[alist[aoff[e] + slot]];
     const double p[3] = {x[3 * (q0 + q)], x[3 * (q0 + q) + 1], x[3 * (q0 + q) + 2]};
     double v, g[3];
-    enrichment_eval(o, p, av, img, v, g);
+    if (gen)
+      enrichment_eval_lat(o, p, lat, v, g);
+    else
+      enrichment_eval(o, p, av, img, v, g);
     double *dst = out + (int64_t)slot * 4 * Q + q;
     dst[0] = v;
     dst[Q] = g[0];
@@ -98,8 +102,13 @@ __device__ __forceinline__ void pu_column(const double xi[3], int lv, const doub
 // ---------------------------------------------------------------------------
 // BLOCH: the scatter carries the phase exp(i k.(R_j - R_i)) of the column
 // pair (lattice shifts from `eshift`, phases of the 8 shift codes in `ph`)
-// into separate real and imaginary outputs (Sec. 4, eq. bloch).
-template <bool BLOCH>
+// into separate real and imaginary outputs (Sec. 4, eq. bloch).  GEN: a
+// general cell, physical gradients J^-T grad_xi with jit = J^-T (row-major).
+struct Mat3 {
+  double m[9];
+};
+
+template <bool BLOCH, bool GEN>
 __global__ void __launch_bounds__(ASM_NT) k_assemble_fp64(
     const int32_t *__restrict__ order, const int64_t *__restrict__ qoff,
     const double *__restrict__ w, const double *__restrict__ xi_all,
@@ -109,7 +118,7 @@ __global__ void __launch_bounds__(ASM_NT) k_assemble_fp64(
     const double *__restrict__ V, double sx, double sy, double sz, int npad_max, int want,
     double *__restrict__ H, double *__restrict__ S, unsigned *err,
     const uint8_t *__restrict__ eshift, PhaseTab ph, double *__restrict__ Hi,
-    double *__restrict__ Si, const int32_t *__restrict__ wsplit) {
+    double *__restrict__ Si, const int32_t *__restrict__ wsplit, Mat3 jit) {
   extern __shared__ __align__(16) double smem[];
   // work item: a whole element, or the point range [qa, qb) of one
   const int e = wsplit ? wsplit[3 * blockIdx.x] : order[blockIdx.x];
@@ -171,8 +180,17 @@ __global__ void __launch_bounds__(ASM_NT) k_assemble_fp64(
         const int q = qc + qq;
         double b = 0, gx = 0, gy = 0, gz = 0, sw = 0, vv = 0;
         if (q < qb && c < n) {
+          // GEN: reference gradients (unit scales) mapped by J^-T
+          const double one[3] = {1.0, 1.0, 1.0};
+          auto tomap = [&](double &x, double &y, double &z) {
+            const double rx = x, ry = y, rz = z;
+            x = jit.m[0] * rx + jit.m[1] * ry + jit.m[2] * rz;
+            y = jit.m[3] * rx + jit.m[4] * ry + jit.m[5] * rz;
+            z = jit.m[6] * rx + jit.m[7] * ry + jit.m[8] * rz;
+          };
           if (c < 64) {
-            fe_column(tab[qq], c, s, b, gx, gy, gz);
+            fe_column(tab[qq], c, GEN ? one : s, b, gx, gy, gz);
+            if (GEN) tomap(gx, gy, gz);
           } else {
             const int code = ec[c - 64];
             const int slot = code >> 3, lv = code & 7;
@@ -180,7 +198,18 @@ __global__ void __launch_bounds__(ASM_NT) k_assemble_fp64(
             const double ps[4] = {pp[0], pp[Q], pp[2 * Q], pp[3 * Q]};
             const double xq[3] = {xi_all[3 * (q0 + q)], xi_all[3 * (q0 + q) + 1],
                                   xi_all[3 * (q0 + q) + 2]};
-            pu_column(xq, lv, s, ps, b, gx, gy, gz);
+            if (GEN) {   // phi_v and its mapped gradient, then the product rule
+              const double unit[4] = {1.0, 0.0, 0.0, 0.0};
+              double phi;
+              pu_column(xq, lv, one, unit, phi, gx, gy, gz);
+              tomap(gx, gy, gz);
+              b = phi * ps[0];
+              gx = gx * ps[0] + phi * ps[1];
+              gy = gy * ps[0] + phi * ps[2];
+              gz = gz * ps[0] + phi * ps[3];
+            } else {
+              pu_column(xq, lv, s, ps, b, gx, gy, gz);
+            }
           }
           sw = w[q0 + q];
           vv = V ? V[q0 + q] : 0.0;
@@ -616,13 +645,37 @@ __global__ void __launch_bounds__(ASM_NT) k_projections(
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
+// the lattice of a general cell for the image sums
+static LatticeDev lattice_of(const pufe_ctx *ctx) {
+  LatticeDev l{};
+  if (!ctx->general) return l;
+  const double *L = ctx->lat;
+  for (int k = 0; k < 9; ++k) l.L[k] = L[k];
+  const double det = L[0] * (L[4] * L[8] - L[5] * L[7]) - L[1] * (L[3] * L[8] - L[5] * L[6]) +
+                     L[2] * (L[3] * L[7] - L[4] * L[6]);
+  const double C[9] = {L[4] * L[8] - L[5] * L[7], L[5] * L[6] - L[3] * L[8],
+                       L[3] * L[7] - L[4] * L[6], L[2] * L[7] - L[1] * L[8],
+                       L[0] * L[8] - L[2] * L[6], L[1] * L[6] - L[0] * L[7],
+                       L[1] * L[5] - L[2] * L[4], L[2] * L[3] - L[0] * L[5],
+                       L[0] * L[4] - L[1] * L[3]};
+  for (int k = 0; k < 9; ++k) l.Lit[k] = C[k] / det;
+  for (int k = 0; k < 3; ++k) l.img[k] = ctx->images[k];
+  return l;
+}
+
+static Mat3 jit_of(const pufe_ctx *ctx) {
+  Mat3 m{};
+  for (int k = 0; k < 9; ++k) m.m[k] = ctx->Jit[k];
+  return m;
+}
+
 pufe_status launch_tabulate(pufe_ctx *ctx, cudaStream_t st) {
   if (ctx->psi_len == 0) return PUFE_OK;
   auto &D = ctx->d;
   k_tabulate<<<(unsigned)ctx->nelem, 128, 0, st>>>(D.qoff, D.x, D.aoff, D.alist, D.toff, D.orb,
                                                    ctx->a[0], ctx->a[1], ctx->a[2],
                                                    ctx->images[0], ctx->images[1], ctx->images[2],
-                                                   D.psi);
+                                                   D.psi, ctx->general ? 1 : 0, lattice_of(ctx));
   PUFE_CUDA_TRY(cudaGetLastError());
   return PUFE_OK;
 }
@@ -639,12 +692,12 @@ pufe_status launch_assemble_fp64(pufe_ctx *ctx, const double *V, int what, doubl
   const int npad = (ctx->max_basis + 3) & ~3;
   const size_t sm = (size_t)5 * QC * npad * sizeof(double) + QC * sizeof(Tab1D);
   if (sm > 227 * 1024) return fail(PUFE_EINVAL, "element basis too large for the FP64 kernel");
-  PUFE_CUDA_TRY(cudaFuncSetAttribute(k_assemble_fp64<false>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  k_assemble_fp64<false><<<fp64_items(ctx), ASM_NT, sm, st>>>(
+  auto kern = ctx->general ? k_assemble_fp64<false, true> : k_assemble_fp64<false, false>;
+  PUFE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  kern<<<fp64_items(ctx), ASM_NT, sm, st>>>(
       D.order, D.qoff, D.w, D.xi, D.doff, D.ecol, D.toff, D.psi, D.soff, D.smap, V,
       2.0 / ctx->h[0], 2.0 / ctx->h[1], 2.0 / ctx->h[2], npad, what, H, S, D.err, nullptr,
-      PhaseTab{}, nullptr, nullptr, D.wsplit);
+      PhaseTab{}, nullptr, nullptr, D.wsplit, jit_of(ctx));
   PUFE_CUDA_TRY(cudaGetLastError());
   return PUFE_OK;
 }
@@ -688,7 +741,12 @@ PhaseTab phase_table(const pufe_ctx *ctx, const double k[3]) {
   for (int c = 0; c < 8; ++c) {
     double th = 0.0;
     for (int d = 0; d < 3; ++d)
-      if ((c >> d) & 1) th += k[d] * ctx->a[d];
+      if ((c >> d) & 1) {
+        if (ctx->general)   // the lattice vector a_d
+          th += k[0] * ctx->lat[3 * d] + k[1] * ctx->lat[3 * d + 1] + k[2] * ctx->lat[3 * d + 2];
+        else
+          th += k[d] * ctx->a[d];
+      }
     t.re[c] = cos(th);
     t.im[c] = sin(th);
   }
@@ -702,12 +760,12 @@ pufe_status launch_assemble_fp64_bloch(pufe_ctx *ctx, const PhaseTab &ph, const 
   const int npad = (ctx->max_basis + 3) & ~3;
   const size_t sm = (size_t)5 * QC * npad * sizeof(double) + QC * sizeof(Tab1D);
   if (sm > 227 * 1024) return fail(PUFE_EINVAL, "element basis too large for the FP64 kernel");
-  PUFE_CUDA_TRY(cudaFuncSetAttribute(k_assemble_fp64<true>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  k_assemble_fp64<true><<<fp64_items(ctx), ASM_NT, sm, st>>>(
+  auto kern = ctx->general ? k_assemble_fp64<true, true> : k_assemble_fp64<true, false>;
+  PUFE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  kern<<<fp64_items(ctx), ASM_NT, sm, st>>>(
       D.order, D.qoff, D.w, D.xi, D.doff, D.ecol, D.toff, D.psi, D.soff, D.smap, V,
       2.0 / ctx->h[0], 2.0 / ctx->h[1], 2.0 / ctx->h[2], npad, what, H, S, D.err, D.eshift, ph,
-      Hi, Si, D.wsplit);
+      Hi, Si, D.wsplit, jit_of(ctx));
   PUFE_CUDA_TRY(cudaGetLastError());
   return PUFE_OK;
 }

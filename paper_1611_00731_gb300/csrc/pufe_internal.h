@@ -119,6 +119,9 @@ struct pufe_ctx {
   int device = 0;
   double a[3] = {0, 0, 0};
   double h[3] = {0, 0, 0};
+  bool general = false;        // a general (triclinic) cell: lat, Jit below
+  double lat[9] = {0};         // rows a_1, a_2, a_3 (general cells)
+  double Jit[9] = {0};         // J^-T (general cells): physical gradient = Jit grad_xi
   int nel[3] = {0, 0, 0};
   int images[3] = {1, 1, 1};   // image search half-width per axis
   int64_t nelem = 0, nq = 0, n_dof = 0, n_fe = 0, nnz = 0;
@@ -268,6 +271,39 @@ __host__ __device__ inline void orbital_accumulate(const Orbital &o, T dx, T dy,
   }
 }
 
+// A general (triclinic) cell for the image sums: rows a_d of the lattice
+// (L[3 d + c]), L^-T (Lit), and the image half-width per lattice direction.
+struct LatticeDev {
+  double L[9], Lit[9];
+  int img[3];
+};
+
+// Periodic enrichment Psi_alpha(p) of a general cell: the displacement to the
+// atom is rounded in lattice coordinates, s = L^-T d, s <- s - nearest
+// integer, d_0 = L^T s, then every image d_0 + i a_1 + j a_2 + k a_3 within
+// the image half-widths is summed (terms beyond r_c are zero).
+template <class T>
+__host__ __device__ inline void enrichment_eval_lat(const Orbital &o, const double p[3],
+                                                    const LatticeDev &c, T &psi, T g[3]) {
+  psi = T(0);
+  g[0] = g[1] = g[2] = T(0);
+  double d[3], s[3];
+  for (int k = 0; k < 3; ++k) d[k] = p[k] - o.tau[k];
+  for (int k = 0; k < 3; ++k) {
+    s[k] = c.Lit[3 * k] * d[0] + c.Lit[3 * k + 1] * d[1] + c.Lit[3 * k + 2] * d[2];
+    s[k] -= floor(s[k] + 0.5);
+  }
+  double d0[3];
+  for (int k = 0; k < 3; ++k) d0[k] = s[0] * c.L[k] + s[1] * c.L[3 + k] + s[2] * c.L[6 + k];
+  for (int i = -c.img[0]; i <= c.img[0]; ++i)
+    for (int j = -c.img[1]; j <= c.img[1]; ++j)
+      for (int k = -c.img[2]; k <= c.img[2]; ++k) {
+        double r[3];
+        for (int m = 0; m < 3; ++m) r[m] = d0[m] + i * c.L[m] + j * c.L[3 + m] + k * c.L[6 + m];
+        orbital_accumulate<T>(o, T(r[0]), T(r[1]), T(r[2]), psi, g);
+      }
+}
+
 // Periodic enrichment Psi_alpha(p) (eq. Psi with f(R) = 1): all images of the
 // atom within r_c of p.  `img` = image half-width per axis.  The displacement
 // to the nearest image is formed in double precision, then evaluated in T.
@@ -347,9 +383,9 @@ pufe_status launch_adjoint_fefe(pufe_ctx *ctx, const double *Hbar, double *Vbar,
                                 int count, cudaStream_t s);
 pufe_status launch_adjoint_strip_sf(pufe_ctx *ctx, const double *Hbar, double *Vbar, int first,
                                     int count, cudaStream_t s);
-// S enrichment-enrichment block in FP64 (mixed path): adds into S (and Si at
+// S enrichment-enrichment block with FP64-class sums (mixed path): adds into S (and Si at
 // a wavevector: ph != nullptr) for the elements order[first .. first+count)
-pufe_status launch_see64(pufe_ctx *ctx, const PhaseTab *ph, double *S, double *Si, int first,
+pufe_status launch_see(pufe_ctx *ctx, const PhaseTab *ph, double *S, double *Si, int first,
                          int count, cudaStream_t st);
 // one bounded mbarrier wait that nothing completes (diagnostics of the
 // timeout path): gives up after wait_ns and sets DEVERR_TIMEOUT

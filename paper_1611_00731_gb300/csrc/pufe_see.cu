@@ -1,28 +1,36 @@
-// Enrichment-enrichment block of S in FP64 (mixed-precision path).
+// Enrichment-enrichment block of S with FP64-class sums (mixed-precision path).
 //
 // S is ill-conditioned because the enrichments are nearly linearly dependent
 // on each other and on the FE functions (Sec. 6.2, Table 1: cond(S) grows to
-// 1e9 with the support radius), so the mixed path keeps this block of S in
-// FP64 arithmetic while H and the other blocks of S are contracted in FP32.
+// 1e9 with the support radius), so the mixed path keeps this block of S free
+// of FP32 rounding in its sums while H and the other blocks of S are
+// contracted in FP32.
 //
 // For columns r = (v, alpha) and s = (v', beta) of an element, on one
 // (sub)cell with a p^3 tensor rule (Sec. 4 eq. disceig3d, Sec. 5.2),
 //   S_rs = sum_q w_q Psi_alpha(x_q) Psi_beta(x_q) phi_v(x_q) phi_v'(x_q).
 // The trilinear PU factors give phi_v phi_v' = 1/64 prod_d u_(k_d)(xi_d) with
-// u_0 = (1 - x)^2, u_1 = 1 - x^2, u_2 = (1 + x)^2 and k_d = b_d + b'_d the
-// sum of the two vertices' bits along axis d, so every entry of the pair
+// u_0 = (1 - x)^2, u_1 = (1 - x)(1 + x), u_2 = (1 + x)^2 and k_d = b_d + b'_d
+// the sum of the two vertices' bits along axis d, so every entry of the pair
 // (alpha, beta) is one of 27 projections
-//   P_ab[kz][ky][kx] = sum_q A_q u_kz(zeta) u_ky(eta) u_kx(xi),
-//   A_q = (sqrt(w_q) Psi_alpha)(sqrt(w_q) Psi_beta),
+//   P_ab[kz][ky][kx] = sum_q s_alpha(q) s_beta(q) u_kz(zeta) u_ky(eta) u_kx(xi),
+//   s_alpha = sqrt(w) Psi_alpha,
 // contracted one axis at a time (3 p^3 + 9 p^2 + 27 p multiply-adds per pair
 // and cell, against p^3 per entry for the direct sum):  S_rs = P_ab[k] / 64.
-// Inputs are the FP32 values of the mixed path (enrichment table, reference
-// coordinates, sqrt(w)); each factor sqrt(w) Psi is the exact FP64 product of
-// two FP32 numbers and every operation after that is FP64, so the block is
-// the Gram matrix of the FP32-rounded basis values up to FP64 rounding (no
-// FP32 rounding enters its sums).  The entries go into the FP64 CSR values
-// with FP64 atomics, both triangles; cells of a subdivided element add up
-// there.
+//
+// Arithmetic.  The factors are the FP32 values of the mixed path: s rounded
+// once to FP32 from the FP32 sqrt(w) and Psi, the 1D factors 1 -+ x from the
+// FP32 reference coordinate.  Every product of two such values is formed
+// exactly as an unevaluated FP32 pair (hi + lo, hi = fl(a b), lo = fma(a, b,
+// -hi): Dekker's product through the FMA), the u_k are kept exactly that way,
+// and all sums are compensated pair sums (Knuth's two-sum), about 2^-48
+// relative per operation.  So the block is the Gram matrix of the rounded
+// basis values to FP64-class accuracy -- no FP32 rounding enters its sums --
+// while every instruction runs on the FP32 pipes: GB300 issues FP64 at 1/64
+// of the FP32 rate, and the same contraction in plain FP64 took 1.5 times
+// as long as the whole FP32 strip.  The pairs are added as FP64 values
+// (hi + lo) into the FP64 CSR values with FP64 atomics, both triangles;
+// cells of a subdivided element add up there.
 #include <algorithm>
 
 #include "pufe_internal.h"
@@ -30,21 +38,48 @@
 namespace pufe {
 namespace {
 
-constexpr int SE_NT = 256;
+constexpr int SE_NT = 128;
+
+// an unevaluated sum hi + lo of two FP32 numbers (|lo| <= ulp(hi) / 2)
+struct ff {
+  float hi, lo;
+};
+
+// a b exactly (Dekker's product through the FMA)
+__device__ __forceinline__ ff ff_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return {p, __fmaf_rn(a, b, -p)};
+}
+
+// a + b exactly (Knuth's two-sum, no ordering of |a|, |b| needed)
+__device__ __forceinline__ ff ff_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+
+// acc + x y for pairs x, y: the product's hi*hi part exactly, its cross terms
+// by FMA (the lo*lo term is below 2^-96 relative), then compensated sums
+// (two-sum also in the renormalisation, which stays exact under cancellation)
+__device__ __forceinline__ ff ff_fma(ff x, ff y, ff acc) {
+  const ff p = ff_prod(x.hi, y.hi);
+  const float plo = __fmaf_rn(x.hi, y.lo, __fmaf_rn(x.lo, y.hi, p.lo));
+  const ff s = ff_sum(acc.hi, p.hi);
+  return ff_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(acc.lo, plo)));
+}
 
 template <bool STAGED, bool BLOCH>
-__global__ void __launch_bounds__(SE_NT) k_see64(
+__global__ void __launch_bounds__(SE_NT) k_see(
     const int32_t *__restrict__ order, const int64_t *__restrict__ qpoff,
     const float4 *__restrict__ qdat, const float *__restrict__ ptab,
-    const int32_t *__restrict__ partoff,
-    const int32_t *__restrict__ part_p, const int32_t *__restrict__ part_q,
-    const int64_t *__restrict__ doff, const int32_t *__restrict__ ecol,
-    const int32_t *__restrict__ aoff, const int64_t *__restrict__ toff32,
-    const float *__restrict__ psi, const int64_t *__restrict__ soff,
-    const int32_t *__restrict__ smap, int pm, int amax, int stage_dbl, int work_dbl,
-    double *__restrict__ S, unsigned *err, const uint8_t *__restrict__ eshift, PhaseTab ph,
-    double *__restrict__ Si) {
-  extern __shared__ double sm64[];
+    const int32_t *__restrict__ partoff, const int32_t *__restrict__ part_p,
+    const int32_t *__restrict__ part_q, const int64_t *__restrict__ doff,
+    const int32_t *__restrict__ ecol, const int32_t *__restrict__ aoff,
+    const int64_t *__restrict__ toff32, const float *__restrict__ psi,
+    const int64_t *__restrict__ soff, const int32_t *__restrict__ smap, int pm, int amax,
+    int stage_f, int work_ff, double *__restrict__ S, unsigned *err,
+    const uint8_t *__restrict__ eshift, PhaseTab ph, double *__restrict__ Si) {
+  extern __shared__ float4 sm_see4[];
   const int e = order[blockIdx.x], tid = threadIdx.x;
   const int n = (int)(doff[e + 1] - doff[e]), ne = n - 64;
   if (ne <= 0) return;
@@ -53,12 +88,12 @@ __global__ void __launch_bounds__(SE_NT) k_see64(
     if (tid == 0) atomicOr(err, DEVERR_SHAPE);
     return;
   }
-  // shared memory: U [3 axes][u_0, u_1, u_2][pm] | stage [slot][point]
-  //                | work | scol [slot][vertex] | pairs
-  double *U = sm64;
-  double *stg = U + 9 * pm;
-  double *work = stg + stage_dbl;
-  int *scol = reinterpret_cast<int *>(work + work_dbl);
+  // shared memory: U [3 axes][u_0, u_1, u_2][pm] pairs | work pairs
+  //                | stage [slot][point] floats | scol [slot][vertex] | pairs
+  ff *U = reinterpret_cast<ff *>(sm_see4);
+  ff *work = U + 9 * pm;
+  float *stg = reinterpret_cast<float *>(work + work_ff);
+  int *scol = reinterpret_cast<int *>(stg + stage_f);
   int *pairs = scol + amax * 8;
   __shared__ double s_phr[8], s_phi[8];
   if (BLOCH && tid < 8) {
@@ -85,8 +120,8 @@ __global__ void __launch_bounds__(SE_NT) k_see64(
 
   for (int k = partoff[e]; k < partoff[e + 1]; ++k) {
     const int p = part_p[k], p2 = p * p, p3 = p2 * p, qs = part_q[k];
-    const int per = 3 * p2 + 9 * p + 27;   // work doubles of one pair
-    if (p > pm || per > work_dbl || (STAGED && A * p3 > stage_dbl)) {
+    const int per = 3 * p2 + 9 * p + 27;   // work pairs of one enrichment pair
+    if (p > pm || per > work_ff || (STAGED && A * p3 > stage_f)) {
       if (tid == 0) atomicOr(err, DEVERR_SHAPE);
       return;
     }
@@ -95,45 +130,44 @@ __global__ void __launch_bounds__(SE_NT) k_see64(
       const int d = o / p, t = o - d * p;
       const int stride = d == 0 ? 1 : (d == 1 ? p : p2);
       const float4 x4 = qe[qs + t * stride];
-      const double x = (double)(d == 0 ? x4.x : (d == 1 ? x4.y : x4.z));
-      const double l0 = 1.0 - x, l1 = 1.0 + x;
-      U[(d * 3 + 0) * pm + t] = l0 * l0;
-      U[(d * 3 + 1) * pm + t] = l0 * l1;
-      U[(d * 3 + 2) * pm + t] = l1 * l1;
+      const float x = d == 0 ? x4.x : (d == 1 ? x4.y : x4.z);
+      const float l0 = __fsub_rn(1.0f, x), l1 = __fadd_rn(1.0f, x);
+      U[(d * 3 + 0) * pm + t] = ff_prod(l0, l0);
+      U[(d * 3 + 1) * pm + t] = ff_prod(l0, l1);
+      U[(d * 3 + 2) * pm + t] = ff_prod(l1, l1);
     }
-    // sqrt(w) Psi of every slot at the cell's points (Psi read from the FP32
-    // table [q/8][slot][comp][q%8], component 0): exact in FP64
-    auto swpsi = [&](int slot, int lq) -> double {
+    // sqrt(w) Psi of a slot at a point of the cell, rounded once to FP32 (Psi
+    // from the table [q/8][slot][comp][q%8], component 0)
+    auto sval = [&](int slot, int lq) -> float {
       const int q = qs + lq;
-      return (double)pt[32 * q + 28] * (double)pe[((int64_t)(q >> 3) * A + slot) * 32 + (q & 7)];
+      return __fmul_rn(pt[32 * q + 28], pe[((int64_t)(q >> 3) * A + slot) * 32 + (q & 7)]);
     };
-    if (STAGED) {
+    if (STAGED)
       for (int o = tid; o < A * p3; o += SE_NT) {
         const int s = o / p3, lq = o - s * p3;
-        stg[o] = swpsi(s, lq);
+        stg[o] = sval(s, lq);
       }
-    }
     __syncthreads();
-    const int npc = max(1, min(npair, work_dbl / per));
+    const int npc = max(1, min(npair, work_ff / per));
     for (int c0 = 0; c0 < npair; c0 += npc) {
       const int nc = min(npc, npair - c0);
-      double *T1 = work;                    // [nc][p^2][3]: z outputs
-      double *T2 = T1 + nc * 3 * p2;        // [nc][p][kz][ky]
-      double *P = T2 + nc * 9 * p;          // [nc][kz][ky][kx]
+      ff *T1 = work;                    // [nc][p^2][3]: z outputs
+      ff *T2 = T1 + nc * 3 * p2;        // [nc][p][kz][ky]
+      ff *P = T2 + nc * 9 * p;          // [nc][kz][ky][kx]
       // z: one thread per (pair, qx, qy) column
       for (int it = tid; it < nc * p2; it += SE_NT) {
         const int g = it / p2, qxy = it - g * p2;
         const int pr = pairs[c0 + g], al = pr & 0xff, be = pr >> 8;
-        double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+        ff a0 = {0.0f, 0.0f}, a1 = {0.0f, 0.0f}, a2 = {0.0f, 0.0f};
         for (int qz = 0; qz < p; ++qz) {
           const int lq = qxy + p2 * qz;
-          const double f = STAGED ? stg[al * p3 + lq] * stg[be * p3 + lq]
-                                  : swpsi(al, lq) * swpsi(be, lq);
-          a0 = fma(f, U[6 * pm + qz], a0);
-          a1 = fma(f, U[7 * pm + qz], a1);
-          a2 = fma(f, U[8 * pm + qz], a2);
+          const ff f = STAGED ? ff_prod(stg[al * p3 + lq], stg[be * p3 + lq])
+                              : ff_prod(sval(al, lq), sval(be, lq));
+          a0 = ff_fma(f, U[6 * pm + qz], a0);
+          a1 = ff_fma(f, U[7 * pm + qz], a1);
+          a2 = ff_fma(f, U[8 * pm + qz], a2);
         }
-        double *t1 = T1 + (size_t)it * 3;
+        ff *t1 = T1 + (size_t)it * 3;
         t1[0] = a0;
         t1[1] = a1;
         t1[2] = a2;
@@ -142,15 +176,15 @@ __global__ void __launch_bounds__(SE_NT) k_see64(
       // y: one thread per (pair, qx, kz)
       for (int it = tid; it < nc * p * 3; it += SE_NT) {
         const int g = it / (3 * p), rem = it - g * 3 * p, qx = rem / 3, kz = rem - qx * 3;
-        const double *t1 = T1 + ((size_t)g * p2 + qx) * 3 + kz;
-        double b0 = 0.0, b1 = 0.0, b2 = 0.0;
+        const ff *t1 = T1 + ((size_t)g * p2 + qx) * 3 + kz;
+        ff b0 = {0.0f, 0.0f}, b1 = {0.0f, 0.0f}, b2 = {0.0f, 0.0f};
         for (int qy = 0; qy < p; ++qy) {
-          const double t = t1[qy * p * 3];
-          b0 = fma(t, U[3 * pm + qy], b0);
-          b1 = fma(t, U[4 * pm + qy], b1);
-          b2 = fma(t, U[5 * pm + qy], b2);
+          const ff t = t1[qy * p * 3];
+          b0 = ff_fma(t, U[3 * pm + qy], b0);
+          b1 = ff_fma(t, U[4 * pm + qy], b1);
+          b2 = ff_fma(t, U[5 * pm + qy], b2);
         }
-        double *t2 = T2 + ((size_t)g * p + qx) * 9 + kz * 3;
+        ff *t2 = T2 + ((size_t)g * p + qx) * 9 + kz * 3;
         t2[0] = b0;
         t2[1] = b1;
         t2[2] = b2;
@@ -159,15 +193,15 @@ __global__ void __launch_bounds__(SE_NT) k_see64(
       // x: one thread per (pair, kz, ky)
       for (int it = tid; it < nc * 9; it += SE_NT) {
         const int g = it / 9, j = it - g * 9;
-        const double *t2 = T2 + (size_t)g * p * 9 + j;
-        double c0v = 0.0, c1v = 0.0, c2v = 0.0;
+        const ff *t2 = T2 + (size_t)g * p * 9 + j;
+        ff c0v = {0.0f, 0.0f}, c1v = {0.0f, 0.0f}, c2v = {0.0f, 0.0f};
         for (int qx = 0; qx < p; ++qx) {
-          const double t = t2[qx * 9];
-          c0v = fma(t, U[qx], c0v);
-          c1v = fma(t, U[pm + qx], c1v);
-          c2v = fma(t, U[2 * pm + qx], c2v);
+          const ff t = t2[qx * 9];
+          c0v = ff_fma(t, U[qx], c0v);
+          c1v = ff_fma(t, U[pm + qx], c1v);
+          c2v = ff_fma(t, U[2 * pm + qx], c2v);
         }
-        double *pp = P + g * 27 + j * 3;
+        ff *pp = P + g * 27 + j * 3;
         pp[0] = c0v;
         pp[1] = c1v;
         pp[2] = c2v;
@@ -183,7 +217,8 @@ __global__ void __launch_bounds__(SE_NT) k_see64(
         if (r < 0 || s < 0) continue;
         const int kx = (i & 1) + (j & 1), ky = ((i >> 1) & 1) + ((j >> 1) & 1),
                   kz = (i >> 2) + (j >> 2);
-        const double v = P[g * 27 + (kz * 3 + ky) * 3 + kx] * (1.0 / 64.0);
+        const ff pv = P[g * 27 + (kz * 3 + ky) * 3 + kx];
+        const double v = ((double)pv.hi + (double)pv.lo) * (1.0 / 64.0);
         const int s_rs = m[(64 + r) * n + 64 + s], s_sr = m[(64 + s) * n + 64 + r];
         if (BLOCH) {   // (r, s) with conj(ph_r) ph_s, (s, r) with its conjugate
           const int a = esh[64 + r], b = esh[64 + s];
@@ -207,46 +242,44 @@ __global__ void __launch_bounds__(SE_NT) k_see64(
 
 }  // namespace
 
-// Shared-memory budget of the Psi stage; cells of elements with more
+// Shared-memory budget of the Psi stage (floats); cells of elements with more
 // enrichment values than this read the FP32 table directly.
-static constexpr int SEE_STAGE_MAX_DBL = 8192;
-static constexpr int SEE_WORK_DBL = 4096;
+static constexpr int SEE_STAGE_MAX_F = 8192;
+static constexpr int SEE_WORK_FF = 2048;
 
-pufe_status launch_see64(pufe_ctx *ctx, const PhaseTab *ph, double *S, double *Si, int first,
-                         int count, cudaStream_t st) {
+pufe_status launch_see(pufe_ctx *ctx, const PhaseTab *ph, double *S, double *Si, int first,
+                       int count, cudaStream_t st) {
   if (count <= 0) return PUFE_OK;
   auto &D = ctx->d;
   const int pm = std::max(1, ctx->max_part_p);
   const int amax = std::max(1, ctx->max_alpha);
   if (amax > 255) return fail(PUFE_EINVAL, "more than 255 enrichments on one element");
   const int per_max = 3 * pm * pm + 9 * pm + 27;
-  const int work = std::max(SEE_WORK_DBL, per_max);
+  const int work = std::max(SEE_WORK_FF, per_max);
   // stage the cells when every element's largest cell fits the budget
   int need = 0;
-  for (int64_t k = first; k < first + count; ++k) {
-    const int e = ctx->order[k];
-    need = std::max(need, (int)ctx->see_stage[e]);
-  }
-  const bool staged = need <= SEE_STAGE_MAX_DBL;
+  for (int64_t k = first; k < first + count; ++k) need = std::max(need, (int)ctx->see_stage[ctx->order[k]]);
+  const bool staged = need <= SEE_STAGE_MAX_F;
   const int stage = staged ? need : 0;
   const size_t ints = (size_t)amax * 8 + (size_t)amax * (amax + 1) / 2;
-  const size_t sm = ((size_t)9 * pm + stage + work) * sizeof(double) + ints * sizeof(int);
-  if (sm > 227 * 1024) return fail(PUFE_EINVAL, "FP64 overlap kernel: shared memory above 227 KB");
+  const size_t sm = ((size_t)9 * pm + work) * sizeof(ff) + (size_t)stage * sizeof(float) +
+                    ints * sizeof(int);
+  if (sm > 227 * 1024) return fail(PUFE_EINVAL, "E-E overlap kernel: shared memory above 227 KB");
   auto go = [&](auto kern, const uint8_t *esh, PhaseTab tab, double *si) -> pufe_status {
     PUFE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    kern<<<(unsigned)count, SE_NT, sm, st>>>(D.order + first, D.qpoff, D.qdat, D.ptab,
-                                             D.partoff, D.part_p, D.part_q, D.doff, D.ecol, D.aoff,
+    kern<<<(unsigned)count, SE_NT, sm, st>>>(D.order + first, D.qpoff, D.qdat, D.ptab, D.partoff,
+                                             D.part_p, D.part_q, D.doff, D.ecol, D.aoff,
                                              D.toff32, D.psi32, D.soff, D.smap, pm, amax, stage,
                                              work, S, D.err, esh, tab, si);
     PUFE_CUDA_TRY(cudaGetLastError());
     return PUFE_OK;
   };
   if (ph) {
-    return staged ? go(k_see64<true, true>, D.eshift, *ph, Si)
-                  : go(k_see64<false, true>, D.eshift, *ph, Si);
+    return staged ? go(k_see<true, true>, D.eshift, *ph, Si)
+                  : go(k_see<false, true>, D.eshift, *ph, Si);
   }
-  return staged ? go(k_see64<true, false>, nullptr, PhaseTab{}, nullptr)
-                : go(k_see64<false, false>, nullptr, PhaseTab{}, nullptr);
+  return staged ? go(k_see<true, false>, nullptr, PhaseTab{}, nullptr)
+                : go(k_see<false, false>, nullptr, PhaseTab{}, nullptr);
 }
 
 }  // namespace pufe

@@ -81,6 +81,12 @@ struct Setup {
   double a[3], h[3];
   int nel[3];
   int img[3];
+  // general (triclinic) cell: element e maps the reference cube by
+  // x = x0(e) + J (xi + 1), J = [a_d / 2 nel_d] (columns), |det J| = detJ
+  bool gen = false;
+  LatticeDev lat;        // rows a_d, L^-T, image half-widths
+  double J[9], Jit[9];   // J (row-major, J[3 r + c]) and J^-T
+  double detJ = 0.0;
   std::vector<Orbital> orb;          // alpha list
   std::vector<int> orb_atom;         // alpha -> atom
   std::vector<std::array<double, 3>> tau;
@@ -98,6 +104,82 @@ static double box_point_dist(const Box &b, const double p[3]) {
   return std::sqrt(s);
 }
 
+// Distance from point P to the parallelepiped {x0 + M t : t in [0, 1]^3}
+// (M row-major, columns the edges).  The squared distance is convex in t;
+// its minimiser lies in the relative interior of one of the box's 27 faces
+// (each coordinate free, at 0 or at 1).  Each face's free coordinates solve
+// the normal equations of a least-squares problem (Cramer's rule, at most
+// 3 x 3); feasible face minimisers are points of the parallelepiped, and the
+// nearest of them is the exact answer.
+static double parallelepiped_point_dist(const double x0[3], const double M[9], const double P[3]) {
+  double best = 1e300;
+  for (int code = 0; code < 27; ++code) {
+    int st[3] = {code % 3, (code / 3) % 3, code / 9};   // 0 free, 1 at 0, 2 at 1
+    int fr[3], nf = 0;
+    double base[3] = {x0[0], x0[1], x0[2]};
+    for (int d = 0; d < 3; ++d) {
+      if (st[d] == 0) fr[nf++] = d;
+      else if (st[d] == 2)
+        for (int r = 0; r < 3; ++r) base[r] += M[3 * r + d];
+    }
+    double rv[3] = {P[0] - base[0], P[1] - base[1], P[2] - base[2]};
+    double t[3] = {0, 0, 0};
+    bool ok = true;
+    if (nf > 0) {
+      double G[3][3], g[3];
+      for (int i = 0; i < nf; ++i) {
+        g[i] = 0.0;
+        for (int r = 0; r < 3; ++r) g[i] += M[3 * r + fr[i]] * rv[r];
+        for (int j = 0; j < nf; ++j) {
+          G[i][j] = 0.0;
+          for (int r = 0; r < 3; ++r) G[i][j] += M[3 * r + fr[i]] * M[3 * r + fr[j]];
+        }
+      }
+      double sol[3];
+      if (nf == 1) {
+        sol[0] = g[0] / G[0][0];
+      } else if (nf == 2) {
+        const double det = G[0][0] * G[1][1] - G[0][1] * G[1][0];
+        sol[0] = (g[0] * G[1][1] - G[0][1] * g[1]) / det;
+        sol[1] = (G[0][0] * g[1] - g[0] * G[1][0]) / det;
+      } else {
+        const double det = G[0][0] * (G[1][1] * G[2][2] - G[1][2] * G[2][1]) -
+                           G[0][1] * (G[1][0] * G[2][2] - G[1][2] * G[2][0]) +
+                           G[0][2] * (G[1][0] * G[2][1] - G[1][1] * G[2][0]);
+        for (int c = 0; c < 3; ++c) {
+          double A[3][3];
+          for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) A[i][j] = j == c ? g[i] : G[i][j];
+          sol[c] = (A[0][0] * (A[1][1] * A[2][2] - A[1][2] * A[2][1]) -
+                    A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0]) +
+                    A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0])) / det;
+        }
+      }
+      for (int i = 0; i < nf; ++i) {
+        ok = ok && sol[i] >= 0.0 && sol[i] <= 1.0;
+        t[fr[i]] = sol[i];
+      }
+    }
+    if (!ok) continue;
+    double q2 = 0.0;
+    for (int r = 0; r < 3; ++r) {
+      double x = base[r] - P[r];
+      for (int i = 0; i < nf; ++i) x += M[3 * r + fr[i]] * t[fr[i]];
+      q2 += x * x;
+    }
+    best = std::min(best, std::sqrt(q2));
+  }
+  return best;
+}
+
+// corner x0 of element (ex, ey, ez) of a general cell: L^T (e / nel)
+static void elem_origin(const Setup &S, const int idx[3], double x0[3]) {
+  for (int r = 0; r < 3; ++r) {
+    x0[r] = 0.0;
+    for (int d = 0; d < 3; ++d) x0[r] += (double)idx[d] / S.nel[d] * S.lat.L[3 * d + r];
+  }
+}
+
 // smallest distance from any periodic image of atom position t to box b
 static double atom_box_dist(const Setup &S, const double t[3], const Box &b) {
   double best = 1e300;
@@ -113,8 +195,10 @@ static double atom_box_dist(const Setup &S, const double t[3], const Box &b) {
 
 // integrals of Psi^2 and |grad Psi|^2 on a box with the p^3 Gauss rule,
 // for each alpha of `alphas`: out[2*i], out[2*i+1]
+// (general cells: b is a box of the reference cube of the element with
+// corner x0, mapped by J)
 static void box_integrals(Setup &S, const std::vector<int> &alphas, const Box &b, int p,
-                          std::vector<double> &out) {
+                          std::vector<double> &out, const double *x0 = nullptr) {
   out.assign(2 * alphas.size(), 0.0);
   const std::vector<double> &gx = S.gx[p], &gw = S.gw[p];
   double half[3], mid[3];
@@ -132,7 +216,16 @@ static void box_integrals(Setup &S, const std::vector<int> &alphas, const Box &b
                           mid[2] + half[2] * gx[kz]};
           double wt = gw[kx] * gw[ky] * gw[kz] * half[0] * half[1] * half[2];
           double psi, g[3];
-          enrichment_eval(o, pt, S.a, S.img, psi, g);
+          if (S.gen) {
+            double x[3];
+            for (int r = 0; r < 3; ++r)
+              x[r] = x0[r] + S.J[3 * r] * (pt[0] + 1.0) + S.J[3 * r + 1] * (pt[1] + 1.0) +
+                     S.J[3 * r + 2] * (pt[2] + 1.0);
+            enrichment_eval_lat(o, x, S.lat, psi, g);
+            wt *= S.detJ;
+          } else {
+            enrichment_eval(o, pt, S.a, S.img, psi, g);
+          }
           s0 += wt * psi * psi;
           s1 += wt * (g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
         }
@@ -142,10 +235,10 @@ static void box_integrals(Setup &S, const std::vector<int> &alphas, const Box &b
 }
 
 static void hadapt(Setup &S, const std::vector<int> &alphas, const Box &b, int depth,
-                   const pufe_quad &q, std::vector<RulePart> &parts) {
+                   const pufe_quad &q, std::vector<RulePart> &parts, const double *x0) {
   std::vector<double> i5, i8;
-  box_integrals(S, alphas, b, 5, i5);
-  box_integrals(S, alphas, b, 8, i8);
+  box_integrals(S, alphas, b, 5, i5, x0);
+  box_integrals(S, alphas, b, 8, i8, x0);
   std::vector<int> failing;
   for (size_t ia = 0; ia < alphas.size(); ++ia)
     if (std::fabs(i5[2 * ia] - i8[2 * ia]) >= q.tol ||
@@ -166,7 +259,7 @@ static void hadapt(Setup &S, const std::vector<int> &alphas, const Box &b, int d
           ch.lo[k] = off[k] == 0 ? b.lo[k] : mid[k];
           ch.hi[k] = off[k] == 0 ? mid[k] : b.hi[k];
         }
-        hadapt(S, failing, ch, depth + 1, q, parts);
+        hadapt(S, failing, ch, depth + 1, q, parts, x0);
       }
 }
 
@@ -213,7 +306,7 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
     return fail(PUFE_EINVAL, "bad atom arrays");
   if (nspecies < 0 || (nspecies > 0 && !species)) return fail(PUFE_EINVAL, "bad species");
   for (int k = 0; k < 3; ++k) {
-    if (!(cell->a[k] > 0.0) || cell->nel[k] < 1 || cell->nel[k] > 4096)
+    if ((!cell->lattice && !(cell->a[k] > 0.0)) || cell->nel[k] < 1 || cell->nel[k] > 4096)
       return fail(PUFE_EINVAL, "cell edges must be > 0 and nel in [1, 4096]");
   }
   if (quad->mode < PUFE_QUAD_FIXED || quad->mode > PUFE_QUAD_HADAPT)
@@ -232,10 +325,39 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
 
   Setup S;
   double rc_max = 0.0;
-  for (int k = 0; k < 3; ++k) {
-    S.a[k] = cell->a[k];
-    S.nel[k] = cell->nel[k];
-    S.h[k] = cell->a[k] / cell->nel[k];
+  if (cell->lattice) {
+    // general cell: rows a_d; a[] and h[] hold |a_d| and |a_d| / nel_d
+    S.gen = true;
+    const double *L = cell->lattice;
+    for (int k = 0; k < 9; ++k) S.lat.L[k] = L[k];
+    const double det = L[0] * (L[4] * L[8] - L[5] * L[7]) - L[1] * (L[3] * L[8] - L[5] * L[6]) +
+                       L[2] * (L[3] * L[7] - L[4] * L[6]);
+    double scale = 0.0;
+    for (int k = 0; k < 9; ++k) scale = std::max(scale, std::fabs(L[k]));
+    if (!(std::fabs(det) > 1e-9 * scale * scale * scale))
+      return fail(PUFE_EINVAL, "lattice vectors are (nearly) linearly dependent");
+    // L^-T: the cofactor matrix of L over det(L)
+    double C[9] = {L[4] * L[8] - L[5] * L[7], L[5] * L[6] - L[3] * L[8], L[3] * L[7] - L[4] * L[6],
+                   L[2] * L[7] - L[1] * L[8], L[0] * L[8] - L[2] * L[6], L[1] * L[6] - L[0] * L[7],
+                   L[1] * L[5] - L[2] * L[4], L[2] * L[3] - L[0] * L[5], L[0] * L[4] - L[1] * L[3]};
+    for (int k = 0; k < 9; ++k) S.lat.Lit[k] = C[k] / det;
+    for (int k = 0; k < 3; ++k) {
+      S.a[k] = std::sqrt(L[3 * k] * L[3 * k] + L[3 * k + 1] * L[3 * k + 1] + L[3 * k + 2] * L[3 * k + 2]);
+      S.nel[k] = cell->nel[k];
+      S.h[k] = S.a[k] / cell->nel[k];
+    }
+    // J = [a_d / 2 nel_d] as columns, J^-T = 2 nel_d (L^-T row d) ... row-wise
+    for (int r = 0; r < 3; ++r)
+      for (int d = 0; d < 3; ++d) S.J[3 * r + d] = L[3 * d + r] / (2.0 * S.nel[d]);
+    for (int r = 0; r < 3; ++r)
+      for (int d = 0; d < 3; ++d) S.Jit[3 * r + d] = S.lat.Lit[3 * d + r] * (2.0 * S.nel[d]);
+    S.detJ = std::fabs(det) / (8.0 * S.nel[0] * S.nel[1] * S.nel[2]);
+  } else {
+    for (int k = 0; k < 3; ++k) {
+      S.a[k] = cell->a[k];
+      S.nel[k] = cell->nel[k];
+      S.h[k] = cell->a[k] / cell->nel[k];
+    }
   }
   for (int s = 0; s < nspecies; ++s) {
     const pufe_species &sp = species[s];
@@ -252,6 +374,14 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
     rc_max = std::max(rc_max, sp.r_c);
   }
   for (int k = 0; k < 3; ++k) S.img[k] = (int)std::ceil(rc_max / S.a[k] + 0.5);
+  if (S.gen)   // |s_k| <= r_c |row k of L^-T| for |d| <= r_c, plus the rounding's 1/2
+    for (int k = 0; k < 3; ++k) {
+      const double nr = std::sqrt(S.lat.Lit[3 * k] * S.lat.Lit[3 * k] +
+                                  S.lat.Lit[3 * k + 1] * S.lat.Lit[3 * k + 1] +
+                                  S.lat.Lit[3 * k + 2] * S.lat.Lit[3 * k + 2]);
+      S.img[k] = (int)std::ceil(rc_max * nr + 0.5);
+    }
+  for (int k = 0; k < 3; ++k) S.lat.img[k] = S.img[k];
   for (int ia = 0; ia < cell->natoms; ++ia) {
     int s = cell->species[ia];
     if (s < 0 || s >= nspecies) return fail(PUFE_EINVAL, "atom species out of range");
@@ -283,15 +413,21 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
   const int64_t n_fe = (int64_t)mx * my * mz;
   const int natoms = cell->natoms;
 
+  // the element's box: physical for orthorhombic cells, the reference cube
+  // for general ones (mapped by x0(e) + J (xi + 1))
   auto elem_box = [&](int64_t e) {
     int ex = (int)(e % nx), ey = (int)((e / nx) % ny), ez = (int)(e / ((int64_t)nx * ny));
     Box b;
     int idx[3] = {ex, ey, ez};
     for (int k = 0; k < 3; ++k) {
-      b.lo[k] = idx[k] * S.h[k];
-      b.hi[k] = b.lo[k] + S.h[k];
+      b.lo[k] = S.gen ? -1.0 : idx[k] * S.h[k];
+      b.hi[k] = S.gen ? 1.0 : b.lo[k] + S.h[k];
     }
     return b;
+  };
+  auto origin = [&](int64_t e, double x0[3]) {
+    int idx[3] = {(int)(e % nx), (int)((e / nx) % ny), (int)(e / ((int64_t)nx * ny))};
+    elem_origin(S, idx, x0);
   };
   auto elem_vertex = [&](int64_t e, int lv) -> int64_t {
     int ex = (int)(e % nx), ey = (int)((e / nx) % ny), ez = (int)(e / ((int64_t)nx * ny));
@@ -303,8 +439,27 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
   std::vector<uint8_t> near((size_t)nelem * std::max(1, natoms), 0);
   parallel_for(nelem, [&](int64_t e) {
     Box b = elem_box(e);
+    double x0[3], M[9];
+    if (S.gen) {
+      origin(e, x0);
+      for (int k = 0; k < 9; ++k) M[k] = 2.0 * S.J[k];
+    }
     for (int ia = 0; ia < natoms; ++ia) {
-      double d = atom_box_dist(S, S.tau[ia].data(), b);
+      double d;
+      if (S.gen) {   // images within the half-widths, one more for the rounding
+        d = 1e300;
+        const int R0 = S.img[0] + 1, R1 = S.img[1] + 1, R2 = S.img[2] + 1;
+        for (int i = -R0; i <= R0; ++i)
+          for (int j = -R1; j <= R1; ++j)
+            for (int k = -R2; k <= R2; ++k) {
+              double P[3];
+              for (int r = 0; r < 3; ++r)
+                P[r] = S.tau[ia][r] + i * S.lat.L[r] + j * S.lat.L[3 + r] + k * S.lat.L[6 + r];
+              d = std::min(d, parallelepiped_point_dist(x0, M, P));
+            }
+      } else {
+        d = atom_box_dist(S, S.tau[ia].data(), b);
+      }
       near[(size_t)e * natoms + ia] = d < S.rc_species[S.atom_species[ia]] ? 1 : 0;
     }
   });
@@ -317,10 +472,32 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
       int vx = (int)(v % nx), vy = (int)((v / nx) % ny), vz = (int)(v / ((int64_t)nx * ny));
       int vi[3] = {vx, vy, vz};
       double s = 0.0;
-      for (int k = 0; k < 3; ++k) {
-        double d = vi[k] * S.h[k] - S.tau[ia][k];
-        d -= S.a[k] * std::nearbyint(d / S.a[k]);
-        s += d * d;
+      if (S.gen) {   // lattice-coordinate rounding, then the neighbouring images
+        double x[3], d[3], f[3];
+        elem_origin(S, vi, x);
+        for (int k = 0; k < 3; ++k) d[k] = x[k] - S.tau[ia][k];
+        for (int k = 0; k < 3; ++k) {
+          f[k] = S.lat.Lit[3 * k] * d[0] + S.lat.Lit[3 * k + 1] * d[1] + S.lat.Lit[3 * k + 2] * d[2];
+          f[k] -= std::nearbyint(f[k]);
+        }
+        s = 1e300;
+        for (int i = -1; i <= 1; ++i)
+          for (int j = -1; j <= 1; ++j)
+            for (int k = -1; k <= 1; ++k) {
+              double t = 0.0;
+              for (int r = 0; r < 3; ++r) {
+                const double c = (f[0] + i) * S.lat.L[r] + (f[1] + j) * S.lat.L[3 + r] +
+                                 (f[2] + k) * S.lat.L[6 + r];
+                t += c * c;
+              }
+              s = std::min(s, t);
+            }
+      } else {
+        for (int k = 0; k < 3; ++k) {
+          double d = vi[k] * S.h[k] - S.tau[ia][k];
+          d -= S.a[k] * std::nearbyint(d / S.a[k]);
+          s += d * d;
+        }
       }
       if (std::sqrt(s) <= re + 1e-12) enr_verts[ia].push_back(v);
     }
@@ -369,6 +546,9 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
   std::vector<std::vector<RulePart>> rule(nelem);
   parallel_for(nelem, [&](int64_t e) {
     Box b = elem_box(e);
+    double x0v[3];
+    if (S.gen) origin(e, x0v);
+    const double *x0 = S.gen ? x0v : nullptr;
     std::vector<RulePart> &parts = rule[e];
     if (quad->mode == PUFE_QUAD_FIXED) {
       bool nr = false;
@@ -382,7 +562,7 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
       }
       std::vector<std::vector<double>> I(quad->p_max + 3);
       auto get = [&](int p) -> const std::vector<double> & {
-        if (I[p].empty()) box_integrals(S, al, b, p, I[p]);
+        if (I[p].empty()) box_integrals(S, al, b, p, I[p], x0);
         return I[p];
       };
       int chosen = quad->p_max;
@@ -401,7 +581,7 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
         parts.push_back({b, quad->p_far});
         return;
       }
-      hadapt(S, ealpha[e], b, 0, *quad, parts);
+      hadapt(S, ealpha[e], b, 0, *quad, parts, x0);
     }
   });
   std::vector<int64_t> qoff(nelem + 1, 0);
@@ -414,6 +594,8 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
   std::vector<double> X(3 * nq), Wt(nq), XI(3 * nq);
   parallel_for(nelem, [&](int64_t e) {
     Box eb = elem_box(e);
+    double x0[3] = {0, 0, 0};
+    if (S.gen) origin(e, x0);
     int64_t q = qoff[e];
     for (auto &pt : rule[e]) {
       const std::vector<double> &gx = S.gx[pt.p], &gw = S.gw[pt.p];
@@ -426,11 +608,20 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
         for (int ky = 0; ky < pt.p; ++ky)
           for (int kx = 0; kx < pt.p; ++kx, ++q) {
             int kk[3] = {kx, ky, kz};
-            for (int d = 0; d < 3; ++d) {
-              X[3 * q + d] = mid[d] + half[d] * gx[kk[d]];
-              XI[3 * q + d] = 2.0 * (X[3 * q + d] - eb.lo[d]) / S.h[d] - 1.0;
+            if (S.gen) {   // reference point of the sub-box, mapped by the element
+              for (int d = 0; d < 3; ++d) XI[3 * q + d] = mid[d] + half[d] * gx[kk[d]];
+              for (int r = 0; r < 3; ++r)
+                X[3 * q + r] = x0[r] + S.J[3 * r] * (XI[3 * q] + 1.0) +
+                               S.J[3 * r + 1] * (XI[3 * q + 1] + 1.0) +
+                               S.J[3 * r + 2] * (XI[3 * q + 2] + 1.0);
+              Wt[q] = gw[kx] * gw[ky] * gw[kz] * half[0] * half[1] * half[2] * S.detJ;
+            } else {
+              for (int d = 0; d < 3; ++d) {
+                X[3 * q + d] = mid[d] + half[d] * gx[kk[d]];
+                XI[3 * q + d] = 2.0 * (X[3 * q + d] - eb.lo[d]) / S.h[d] - 1.0;
+              }
+              Wt[q] = gw[kx] * gw[ky] * gw[kz] * half[0] * half[1] * half[2];
             }
-            Wt[q] = gw[kx] * gw[ky] * gw[kz] * half[0] * half[1] * half[2];
           }
     }
   });
@@ -479,7 +670,7 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
       const Orbital &o = S.orb[ealpha[e][k]];
       const Box b = elem_box(e);
       float *dst = &eorig[8 * (aoff[e] + k)];
-      for (int d = 0; d < 3; ++d) {
+      for (int d = 0; d < 3 && !S.gen; ++d) {   // (the FP32 path takes orthorhombic cells)
         double v = b.lo[d] - o.tau[d];
         v -= S.a[d] * std::floor(v / S.a[d] + 0.5);
         const float hi = (float)v;
@@ -588,7 +779,7 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
   const bool fe_exact = min_p >= 4;
   std::vector<double> TF, S0, SF;
   if (fe_exact) {
-    double M1[4][4] = {{0}}, K1[4][4] = {{0}};
+    double M1[4][4] = {{0}}, K1[4][4] = {{0}}, D1[4][4] = {{0}};   // D1[a][b] = int L'_a L_b
     for (int g = 0; g < 4; ++g) {
       double L[4], dL[4];
       lagrange3(S.gx[4][g], L, dL);
@@ -596,21 +787,55 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
         for (int b = 0; b < 4; ++b) {
           M1[a][b] += S.gw[4][g] * L[a] * L[b];
           K1[a][b] += S.gw[4][g] * dL[a] * dL[b];
+          D1[a][b] += S.gw[4][g] * dL[a] * L[b];
         }
     }
-    const double J = 0.125 * S.h[0] * S.h[1] * S.h[2];
-    const double s2[3] = {4.0 / (S.h[0] * S.h[0]), 4.0 / (S.h[1] * S.h[1]), 4.0 / (S.h[2] * S.h[2])};
     SF.assign(64 * 64, 0.0);
     TF.assign(64 * 64, 0.0);
-    for (int i = 0; i < 64; ++i)
-      for (int j = 0; j < 64; ++j) {
-        const int ia[3] = {i & 3, (i >> 2) & 3, i >> 4}, ja[3] = {j & 3, (j >> 2) & 3, j >> 4};
-        const double mx = M1[ia[0]][ja[0]], my = M1[ia[1]][ja[1]], mz = M1[ia[2]][ja[2]];
-        SF[i * 64 + j] = J * mx * my * mz;
-        TF[i * 64 + j] = 0.5 * J * (s2[0] * K1[ia[0]][ja[0]] * my * mz +
-                                    s2[1] * mx * K1[ia[1]][ja[1]] * mz +
-                                    s2[2] * mx * my * K1[ia[2]][ja[2]]);
-      }
+    if (!S.gen) {
+      const double J = 0.125 * S.h[0] * S.h[1] * S.h[2];
+      const double s2[3] = {4.0 / (S.h[0] * S.h[0]), 4.0 / (S.h[1] * S.h[1]), 4.0 / (S.h[2] * S.h[2])};
+      for (int i = 0; i < 64; ++i)
+        for (int j = 0; j < 64; ++j) {
+          const int ia[3] = {i & 3, (i >> 2) & 3, i >> 4}, ja[3] = {j & 3, (j >> 2) & 3, j >> 4};
+          const double mx = M1[ia[0]][ja[0]], my = M1[ia[1]][ja[1]], mz = M1[ia[2]][ja[2]];
+          SF[i * 64 + j] = J * mx * my * mz;
+          TF[i * 64 + j] = 0.5 * J * (s2[0] * K1[ia[0]][ja[0]] * my * mz +
+                                      s2[1] * mx * K1[ia[1]][ja[1]] * mz +
+                                      s2[2] * mx * my * K1[ia[2]][ja[2]]);
+        }
+    } else {
+      // grad phi_i . grad phi_j = sum_kl G_kl d_k phi_i d_l phi_j with the
+      // reference metric G = J^-1 J^-T; each term is a product of 1D
+      // integrals: M1 on the other axes, K1 when k = l, D1 (and its
+      // transpose) on axes k and l when k != l
+      double G[3][3];
+      for (int k = 0; k < 3; ++k)
+        for (int l = 0; l < 3; ++l) {
+          G[k][l] = 0.0;
+          for (int r = 0; r < 3; ++r) G[k][l] += S.Jit[3 * r + k] * S.Jit[3 * r + l];
+        }
+      for (int i = 0; i < 64; ++i)
+        for (int j = 0; j < 64; ++j) {
+          const int ia[3] = {i & 3, (i >> 2) & 3, i >> 4}, ja[3] = {j & 3, (j >> 2) & 3, j >> 4};
+          double m = 1.0;
+          for (int d = 0; d < 3; ++d) m *= M1[ia[d]][ja[d]];
+          SF[i * 64 + j] = S.detJ * m;
+          double t = 0.0;
+          for (int k = 0; k < 3; ++k)
+            for (int l = 0; l < 3; ++l) {
+              double f = G[k][l];
+              for (int d = 0; d < 3; ++d) {
+                if (d == k && d == l) f *= K1[ia[d]][ja[d]];
+                else if (d == k) f *= D1[ia[d]][ja[d]];
+                else if (d == l) f *= D1[ja[d]][ia[d]];
+                else f *= M1[ia[d]][ja[d]];
+              }
+              t += f;
+            }
+          TF[i * 64 + j] = 0.5 * S.detJ * t;
+        }
+    }
     S0.assign(nnz, 0.0);
     for (int64_t e = 0; e < nelem; ++e) {
       const int n = n_e[e];
@@ -626,6 +851,11 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
     ctx->h[k] = S.h[k];
     ctx->nel[k] = S.nel[k];
     ctx->images[k] = S.img[k];
+  }
+  ctx->general = S.gen;
+  for (int k = 0; k < 9; ++k) {
+    ctx->lat[k] = S.gen ? S.lat.L[k] : 0.0;
+    ctx->Jit[k] = S.gen ? S.Jit[k] : 0.0;
   }
   ctx->nelem = nelem;
   ctx->nq = nq;

@@ -488,7 +488,7 @@ __device__ __forceinline__ void strip_part(const StripElem &E, double *__restric
 }
 
 template <bool BLOCH>
-__global__ void __launch_bounds__(ST_NT, 2) k_strip_sf(
+__global__ void __maxnreg__(112) k_strip_sf(
     const int32_t *__restrict__ order, const int64_t *__restrict__ qoff,
     const int64_t *__restrict__ qpoff, const float4 *__restrict__ qdat,
     const double *__restrict__ V, const int32_t *__restrict__ partoff,
@@ -834,7 +834,7 @@ pufe_status launch_assemble_mixed_bloch(pufe_ctx *ctx, const PhaseTab &ph, const
   pufe_status e0 = launch_fefe_bloch(ctx, ph, V, what, H, Hi, S, Si, st);
   if (e0 != PUFE_OK) return e0;
   if (what & PUFE_WANT_S) {   // E x E block of S(k) in FP64 with FP64 phases
-    pufe_status e1 = launch_see64(ctx, &ph, S, Si, 0, (int)ctx->nelem, st);
+    pufe_status e1 = launch_see(ctx, &ph, S, Si, 0, (int)ctx->nelem, st);
     if (e1 != PUFE_OK) return e1;
   }
   return strip_launch(ctx, (what & PUFE_WANT_H) ? V : nullptr, what, H, S, 0, (int)ctx->nelem, st,

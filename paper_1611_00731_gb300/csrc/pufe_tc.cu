@@ -1038,10 +1038,10 @@ static pufe_status run_assemble_tc(pufe_ctx *ctx, const double *V, int what, dou
   if (nbig > 0 && sm256 > 227 * 1024)
     return fail(PUFE_EINVAL, "too many enrichments per element for TF32X3");
   const size_t bytes = (size_t)ctx->nnz * sizeof(double);
-  // H = 0 and S = the constant FE-FE overlap; then the FE-FE kernel (V term
-  // and kinetic constants of H) and the FP64 enrichment-enrichment kernel of
-  // S run on the context's side stream, concurrently with the strip kernels
-  // below (all of them only add into H and S)
+  // H = 0 and S = the constant FE-FE overlap; then the strip kernels on the
+  // caller's stream and, on the context's side stream, the E-E kernel of S
+  // and the FE-FE kernel (V term and kinetic constants of H), concurrently
+  // (all of them only add into H and S)
   if (ctx->max_part_p > 16) return fail(PUFE_EINVAL, "rule with more than 16 points per axis");
   const bool prof = ctx->prof;
   auto mark = [&](int i, cudaStream_t s) -> pufe_status {
@@ -1055,24 +1055,8 @@ static pufe_status run_assemble_tc(pufe_ctx *ctx, const double *V, int what, dou
   if (what & PUFE_WANT_H) PUFE_CUDA_TRY(cudaMemsetAsync(H, 0, bytes, st));
   if (what & PUFE_WANT_S) PUFE_CUDA_TRY(cudaMemcpyAsync(S, D.S0, bytes, cudaMemcpyDeviceToDevice, st));
   PUFE_CUDA_TRY(cudaEventRecord(D.ev_fork, st));
-  PUFE_CUDA_TRY(cudaStreamWaitEvent(D.side, D.ev_fork, 0));
-  if (what & PUFE_WANT_S) {
-    if (pufe_status e = mark(4, D.side)) return e;
-    pufe_status e0 = launch_see64(ctx, nullptr, S, nullptr, 0, (int)ctx->nelem, D.side);
-    if (e0 != PUFE_OK) return e0;
-    if (pufe_status e = mark(5, D.side)) return e;
-    if (prof) ctx->prof_ran[2] = true;
-  }
-  if (what & PUFE_WANT_H) {
-    if (pufe_status e = mark(2, D.side)) return e;
-    pufe_status e0 = launch_fefe(ctx, V, H, D.side);
-    if (e0 != PUFE_OK) return e0;
-    if (pufe_status e = mark(3, D.side)) return e;
-    if (prof) ctx->prof_ran[1] = true;
-  }
-  PUFE_CUDA_TRY(cudaEventRecord(D.ev_join, D.side));
-  // elements are ordered with n_e > 128 first (256-row tensor-core tile),
-  // then the rest (sum-factorized strip on the CUDA cores)
+  // the strip kernels go first, so that their CTAs take their share of every
+  // SM; the side stream's kernels are small enough to run beside them
   if (nbig > 0) {
     // every entry the tensor-core kernel reads is rewritten (zeros on padding)
     k_pack_v<<<(unsigned)nbig, 256, 0, st>>>(D.order, D.qoff, D.qpoff,
@@ -1097,6 +1081,22 @@ static pufe_status run_assemble_tc(pufe_ctx *ctx, const double *V, int what, dou
   if (e1 != PUFE_OK) return e1;
   if (pufe_status e = mark(9, st)) return e;
   if (prof) ctx->prof_ran[4] = nsmall > 0;
+  PUFE_CUDA_TRY(cudaStreamWaitEvent(D.side, D.ev_fork, 0));
+  if (what & PUFE_WANT_S) {
+    if (pufe_status e = mark(4, D.side)) return e;
+    pufe_status e0 = launch_see(ctx, nullptr, S, nullptr, 0, (int)ctx->nelem, D.side);
+    if (e0 != PUFE_OK) return e0;
+    if (pufe_status e = mark(5, D.side)) return e;
+    if (prof) ctx->prof_ran[2] = true;
+  }
+  if (what & PUFE_WANT_H) {
+    if (pufe_status e = mark(2, D.side)) return e;
+    pufe_status e0 = launch_fefe(ctx, V, H, D.side);
+    if (e0 != PUFE_OK) return e0;
+    if (pufe_status e = mark(3, D.side)) return e;
+    if (prof) ctx->prof_ran[1] = true;
+  }
+  PUFE_CUDA_TRY(cudaEventRecord(D.ev_join, D.side));
   PUFE_CUDA_TRY(cudaStreamWaitEvent(st, D.ev_join, 0));
   if (pufe_status e = mark(1, st)) return e;
   return PUFE_OK;

@@ -51,7 +51,8 @@ class PufeError(RuntimeError):
 
 class _Cell(C.Structure):
     _fields_ = [("a", C.c_double * 3), ("nel", C.c_int * 3), ("natoms", C.c_int),
-                ("tau", C.POINTER(C.c_double)), ("species", C.POINTER(C.c_int))]
+                ("tau", C.POINTER(C.c_double)), ("species", C.POINTER(C.c_int)),
+                ("lattice", C.POINTER(C.c_double))]
 
 
 class _Species(C.Structure):
@@ -367,9 +368,16 @@ def pufe_build_mesh(wl: dict) -> Context:
     natoms = len(wl["atoms"])
     tau = (C.c_double * max(1, 3 * natoms))(*[c for _, t in wl["atoms"] for c in t])
     spec = (C.c_int * max(1, natoms))(*[int(s) for s, _ in wl["atoms"]])
-    a = float(wl["a"])
     nel = int(wl["nel"])
-    cell = _Cell((C.c_double * 3)(a, a, a), (C.c_int * 3)(nel, nel, nel), natoms, tau, spec)
+    if wl.get("lattice") is not None:   # a general cell: rows a_1, a_2, a_3
+        lat = (C.c_double * 9)(*[float(c) for row in wl["lattice"] for c in row])
+        cell = _Cell((C.c_double * 3)(0.0, 0.0, 0.0), (C.c_int * 3)(nel, nel, nel), natoms, tau,
+                     spec, lat)
+    else:
+        a = float(wl["a"])
+        lat = None
+        cell = _Cell((C.c_double * 3)(a, a, a), (C.c_int * 3)(nel, nel, nel), natoms, tau, spec,
+                     None)
     keep = []
     sp = (_Species * max(1, len(wl["species"])))()
     for i, s in enumerate(wl["species"]):
@@ -385,6 +393,7 @@ def pufe_build_mesh(wl: dict) -> Context:
                  int(q["p_max"]), float(q["tol"]), int(q["max_depth"]))
     h = C.c_void_p()
     _check(lib.pufe_build_mesh(C.byref(cell), sp, len(wl["species"]), C.byref(quad), C.byref(h)))
+    del lat
     return Context(h, wl)
 
 

@@ -67,9 +67,20 @@ def _compare(wl):
     lambda: W.small_two_atom(nel=1, quad_p=3),     # one periodic element: repeated DOFs
     lambda: W.empty_lattice(nel=2),                # no enrichment at all
     lambda: W.workload("c1_two_atom_4cube"),
+    lambda: W.ceal_like(nel=2),                    # general (triclinic) cells, Sec. 6.2
+    lambda: W.ceal_like(nel=3, r_e=2.0),
+    lambda: W.sheared_empty(nel=3),
 ])
 def test_host_setup_matches_oracle(lib, maker):
     _compare(maker())
+
+
+def test_general_cell_adaptive_rules(lib):
+    """p- and h-adaptive rules on the CeAl lattice: mapped reference boxes."""
+    for mode in (W.QUAD_PADAPT, W.QUAD_HADAPT):
+        wl = W.ceal_like(nel=2)
+        wl["quad"] = dict(mode=mode, p_far=4, p_near=8, p_min=4, p_max=8, tol=1e-4, max_depth=1)
+        _compare(wl)
 
 
 def test_host_setup_adaptive_modes(lib):

@@ -179,3 +179,23 @@ def test_ceal_like_cell_pu_reproduction_and_spd():
     psi, g = oenr.enrichment(al["orb"], al["rc"], al["tau"], m.lattice, pts)
     assert abs(c @ (S @ c) - wts @ psi ** 2) < 1e-12 * (wts @ psi ** 2)
     assert abs(c @ (H @ c) - 0.5 * wts @ (g * g).sum(axis=0)) < 1e-12 * abs(c @ (H @ c))
+
+
+def test_general_cell_bloch_hermitian_periodic_gamma_limit():
+    """H(k), S(k) on the CeAl lattice: Hermitian, periodic under k -> k + G
+    for G on the reciprocal lattice, and the real matrices at k = 0."""
+    from oracle import bloch as ob
+    wl = W.ceal_like(nel=2)
+    m, rules = _setup(wl)
+    V = W.random_potential(len(rules[1]), seed=8)
+    L = np.array(wl["lattice"])
+    B = 2.0 * math.pi * np.linalg.inv(L)
+    k = B @ np.array([0.3, -0.2, 0.1])
+    H, S = ob.assemble_HS_k(m, rules, V, k)
+    assert abs(H - H.conj().T).max() < 1e-14 * abs(H).max()
+    assert abs(S - S.conj().T).max() < 1e-14 * abs(S).max()
+    H2, S2 = ob.assemble_HS_k(m, rules, V, k + B @ np.array([1.0, 0.0, -1.0]))
+    assert abs(H2 - H).max() < 1e-13 * abs(H).max() and abs(S2 - S).max() < 1e-13 * abs(S).max()
+    H0, S0 = ob.assemble_HS_k(m, rules, V, np.zeros(3))
+    Hr, Sr = oasm.assemble_HS(m, rules, V)
+    assert abs(H0 - Hr).max() < 1e-14 * abs(Hr).max() and abs(H0.imag).max() == 0.0
