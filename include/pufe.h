@@ -358,6 +358,23 @@ pufe_status pufe_scf_reset(pufe_ctx *ctx);
  * enriched vertices; its K0 table holds 4 values per slot and point. */
 pufe_status pufe_get_element_slots(const pufe_ctx *ctx, int32_t *n_slot);
 
+/* Autotuner of the mixed assembly (the batching of the element classes; the
+ * paper prescribes no kernel).  The enrichment strip forms the
+ * enrichment-enrichment block of H either from slot-pair projections or from
+ * direct 4 x 4 tiles; by default each element takes the form with the lower
+ * operation count.  This call groups the strip elements (64 < n_e <= 128, at
+ * most 8 enrichments) into classes of equal n_e, enrichment count and
+ * (sub)cell rules, times both forms on the GPU on each class (up to 256 of
+ * its elements, best of 3 after a warm-up), and keeps the faster one for
+ * every element of the class.  If the environment variable
+ * PUFE_AUTOTUNE_CACHE names a file, classes listed there (a line "key form",
+ * form 1 = slot pairs, 2 = tiles) are taken without timing and new decisions
+ * are appended.  *nclasses (may be NULL) receives the number of classes set.
+ * Needs pufe_tabulate(ctx, PUFE_TF32X3); allocates and frees scratch (H, S
+ * and V sized arrays); blocking; results of later assemblies are unchanged
+ * up to the forms' FP32 rounding.  Orthorhombic cells only. */
+pufe_status pufe_autotune(pufe_ctx *ctx, int *nclasses, void *stream);
+
 /* ---- diagnostics and instrumentation (no counterpart in the paper) ------- */
 
 /* Exercise the timeout path of the device waits: one thread waits, with the
@@ -376,10 +393,10 @@ pufe_status pufe_selftest_timeout(pufe_ctx *ctx, uint64_t wait_ns, void *stream)
 pufe_status pufe_profile_assembly(pufe_ctx *ctx, int enable);
 
 /* Durations in ms of the last instrumented assembly call, ms[5] (host):
- * [0] the whole call, [1] the FE-FE kernel (V block and kinetic constants of
- * H), [2] the FP64 enrichment-enrichment kernel of S, [3] the tensor-core
- * tile kernel, [4] the enrichment strip kernel; 0 for a kernel the call did
- * not launch.  Waits for the call to finish.  PUFE_ESTATE if no
+ * [0] the whole call, [1] the FE-FE kernels (the V-block table and the row
+ * writer of every CSR entry), [2] the enrichment-enrichment kernel of S, [3]
+ * the tensor-core tile kernel, [4] the enrichment strip kernel; 0 for a
+ * kernel the call did not launch.  Waits for the call to finish.  PUFE_ESTATE if no
  * instrumented call was made. */
 pufe_status pufe_profile_read(pufe_ctx *ctx, double *ms);
 

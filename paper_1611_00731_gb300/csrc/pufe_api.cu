@@ -277,6 +277,14 @@ pufe_status pufe_scf_reset(pufe_ctx *ctx) {
   return PUFE_OK;
 }
 
+pufe_status pufe_autotune(pufe_ctx *ctx, int *nclasses, void *stream) {
+  if (pufe_status e0 = need_device(ctx)) return e0;
+  if (ctx->general) return fail(PUFE_EINVAL, "the mixed path takes orthorhombic cells");
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return fail(PUFE_ECUDA, "cudaSetDevice failed");
+  return autotune_strip(ctx, nclasses, (cudaStream_t)stream);
+}
+
 pufe_status pufe_selftest_timeout(pufe_ctx *ctx, uint64_t wait_ns, void *stream) {
   if (pufe_status e0 = need_device(ctx)) return e0;
   if (wait_ns < 1000000ull || wait_ns > 2000000000ull)

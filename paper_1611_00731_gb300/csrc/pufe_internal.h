@@ -88,7 +88,7 @@ struct DeviceArrays {
                               // origin from the nearest atom image, hi[3], lo[3], 0, 0
   double *Tfe = nullptr;      // 64 x 64: kinetic block of the tricubic functions (any element)
   double *Sfe = nullptr;      // 64 x 64: overlap block of the tricubic functions (any element)
-  double *S0 = nullptr;       // nnz: global FE-FE overlap blocks (constant)
+  double *S0 = nullptr;       // nnz: overlap FE-FE constants summed over elements (mixed path)
   Orbital *orb = nullptr;     // n_alpha
   OrbitalF *orbf = nullptr;   // n_alpha
   // global sparse storage
@@ -101,6 +101,12 @@ struct DeviceArrays {
   // FP64 assembly/adjoint work list, 3 per item (element, first point, end
   // point), largest first; null when every item is a whole element
   int32_t *wsplit = nullptr;
+  // mixed-path work list of the n_e > 128 elements, 3 per item (index into
+  // `order`, first chunk, end chunk; chunks of 8 padded points), largest first
+  int32_t *titems = nullptr;
+  int32_t *sitems = nullptr;   // E-E kernel of S: (order index, first pair, end pair) triples
+  int32_t *citems = nullptr;   // strip kernel: (order index, first cell, end cell) triples
+  int8_t *eeform = nullptr;   // per element: E x E form of the strip (0 model, 1 pair, 2 direct)
   unsigned *err = nullptr;    // device error flag
   // side stream and events: the FE-FE kernel of the mixed assembly runs on
   // `side`, forked from and joined back into the caller's stream
@@ -134,6 +140,9 @@ struct pufe_ctx {
   int n_big = 0;              // elements with n_e > 128 (listed first in `order`)
   int64_t big_pad_end = 0;    // end of the last n_e > 128 element's padded points (0: none)
   int64_t n_wsplit = 0;       // items of the FP64 point-range work list (0: none)
+  int n_titems = 0;           // items of the mixed path's list for the n_e > 128 elements
+  int n_sitems = 0;           // items of the E-E overlap kernel's list (slot-pair ranges)
+  int n_citems = 0;           // items of the strip kernel's list ((sub)cell ranges)
   int max_part_p = 0;         // largest points-per-axis of any (sub)cell
   int strip_stage = 0;        // floats of the strip kernel's shared-memory stage
   uint32_t strip_pmask = 0;   // per-axis counts (bit p) of the strip kernel's cells
@@ -146,6 +155,8 @@ struct pufe_ctx {
   std::vector<int32_t> col, dofs, n_e, q_e, order;
   std::vector<int32_t> see_stage;   // per element: slots x largest (sub)cell's points (0: no strip)
   std::vector<int32_t> n_slot;      // per element: enrichments (slots) in its basis
+  std::vector<std::vector<int32_t>> part_p_host;   // per element: points per axis of each (sub)cell
+  std::vector<int8_t> eeform_host;  // per element: E x E form (0 model, 1 pair, 2 direct)
   // instrumentation of the mixed assembly (pufe_profile_assembly): events
   // around the call [0, 1], the FE-FE kernel [2, 3], the FP64 E-E kernel of
   // S [4, 5], the tensor-core tile [6, 7] and the strip [8, 9]
@@ -358,7 +369,8 @@ pufe_status launch_adjoint_fp64_bloch(pufe_ctx *ctx, const PhaseTab &ph, const d
                                       const double *Hi, double *Vbar, cudaStream_t s);
 pufe_status launch_tabulate_f32(pufe_ctx *ctx, cudaStream_t s);
 pufe_status launch_adjoint_tc(pufe_ctx *ctx, const double *Hbar, double *Vbar, cudaStream_t s);
-pufe_status launch_fefe(pufe_ctx *ctx, const double *V, double *H, cudaStream_t s);  // H must be zeroed
+// adds the FE-FE blocks of H (kinetic constants + V term; V == NULL: V = 0)
+pufe_status launch_fefe(pufe_ctx *ctx, const double *V, double *H, cudaStream_t s);
 pufe_status launch_strip_sf(pufe_ctx *ctx, const double *V, int what, double *H, double *S,
                             int first, int count, cudaStream_t s);
 pufe_status launch_fefe_bloch(pufe_ctx *ctx, const PhaseTab &ph, const double *V, int what,
@@ -384,12 +396,13 @@ pufe_status launch_adjoint_fefe(pufe_ctx *ctx, const double *Hbar, double *Vbar,
 pufe_status launch_adjoint_strip_sf(pufe_ctx *ctx, const double *Hbar, double *Vbar, int first,
                                     int count, cudaStream_t s);
 // S enrichment-enrichment block with FP64-class sums (mixed path): adds into S (and Si at
-// a wavevector: ph != nullptr) for the elements order[first .. first+count)
-pufe_status launch_see(pufe_ctx *ctx, const PhaseTab *ph, double *S, double *Si, int first,
-                         int count, cudaStream_t st);
+// a wavevector: ph != nullptr) for every element, over the slot-pair work list
+pufe_status launch_see(pufe_ctx *ctx, const PhaseTab *ph, double *S, double *Si, cudaStream_t s);
 // one bounded mbarrier wait that nothing completes (diagnostics of the
 // timeout path): gives up after wait_ns and sets DEVERR_TIMEOUT
 pufe_status launch_wait_probe(pufe_ctx *ctx, uint64_t wait_ns, cudaStream_t st);
+// autotuner of the strip's E x E form per element class (blocking)
+pufe_status autotune_strip(pufe_ctx *ctx, int *ntuned, cudaStream_t st);
 // instrumentation of the mixed assembly (events around its kernels)
 pufe_status profile_enable(pufe_ctx *ctx, bool on);
 pufe_status profile_read(pufe_ctx *ctx, double ms[5]);

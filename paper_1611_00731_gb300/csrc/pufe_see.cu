@@ -16,15 +16,16 @@
 //   P_ab[kz][ky][kx] = sum_q s_alpha(q) s_beta(q) u_kz(zeta) u_ky(eta) u_kx(xi),
 //   s_alpha = sqrt(w) Psi_alpha,
 // contracted one axis at a time (3 p^3 + 9 p^2 + 27 p multiply-adds per pair
-// and cell, against p^3 per entry for the direct sum):  S_rs = P_ab[k] / 64.
+// and cell, against p^3 per entry for the direct sum):  S_rs = P_ab[k] / 64
+// (the 1/64 is carried by the 1D factors, halved per axis).
 //
 // Arithmetic.  The factors are the FP32 values of the mixed path: s rounded
-// once to FP32 from the FP32 sqrt(w) and Psi, the 1D factors 1 -+ x from the
-// FP32 reference coordinate.  Every product of two such values is formed
+// once to FP32 from sqrt(w) of the FP32 weight and Psi, the 1D factors
+// 1 -+ x from the FP32 reference coordinate.  Every product of two such values is formed
 // exactly as an unevaluated FP32 pair (hi + lo, hi = fl(a b), lo = fma(a, b,
 // -hi): Dekker's product through the FMA), the u_k are kept exactly that way,
-// and all sums are compensated pair sums (Knuth's two-sum), about 2^-48
-// relative per operation.  So the block is the Gram matrix of the rounded
+// and every sum is compensated (Knuth's two-sum on the high parts, the low
+// parts in FP32), about 2^-48 relative per operation.  So the block is the Gram matrix of the rounded
 // basis values to FP64-class accuracy -- no FP32 rounding enters its sums --
 // while every instruction runs on the FP32 pipes: GB300 issues FP64 at 1/64
 // of the FP32 rate, and the same contraction in plain FP64 took 1.5 times
@@ -59,19 +60,27 @@ __device__ __forceinline__ ff ff_sum(float a, float b) {
 }
 
 // acc + x y for pairs x, y: the product's hi*hi part exactly, its cross terms
-// by FMA (the lo*lo term is below 2^-96 relative), then compensated sums
-// (two-sum also in the renormalisation, which stays exact under cancellation)
+// by FMA (the lo*lo term is below 2^-96 relative), the high parts added
+// exactly (two-sum) and the low parts summed in FP32, whose rounding is
+// ~2^-24 of a ~2^-24 correction; ff_norm folds lo back into hi where a stage
+// stores its results (two-sum, exact under cancellation too)
 __device__ __forceinline__ ff ff_fma(ff x, ff y, ff acc) {
   const ff p = ff_prod(x.hi, y.hi);
   const float plo = __fmaf_rn(x.hi, y.lo, __fmaf_rn(x.lo, y.hi, p.lo));
   const ff s = ff_sum(acc.hi, p.hi);
-  return ff_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(acc.lo, plo)));
+  return {s.hi, __fadd_rn(s.lo, __fadd_rn(acc.lo, plo))};
 }
 
-template <bool STAGED, bool BLOCH>
+__device__ __forceinline__ ff ff_norm(ff a) { return ff_sum(a.hi, a.lo); }
+
+// One CTA per work item: the slot pairs [pb, pe) (alpha-major order) of
+// element order[k], (k, pb, pe) = items[3 b .. 3 b + 2].  A (sub)cell's
+// sqrt(w) Psi values are staged in shared memory when A p^3 <= stage_f, else
+// formed from the table at each use.
+template <bool BLOCH>
 __global__ void __launch_bounds__(SE_NT) k_see(
-    const int32_t *__restrict__ order, const int64_t *__restrict__ qpoff,
-    const float4 *__restrict__ qdat, const float *__restrict__ ptab,
+    const int32_t *__restrict__ order, const int32_t *__restrict__ items,
+    const int64_t *__restrict__ qpoff, const float4 *__restrict__ qdat,
     const int32_t *__restrict__ partoff, const int32_t *__restrict__ part_p,
     const int32_t *__restrict__ part_q, const int64_t *__restrict__ doff,
     const int32_t *__restrict__ ecol, const int32_t *__restrict__ aoff,
@@ -80,7 +89,8 @@ __global__ void __launch_bounds__(SE_NT) k_see(
     int stage_f, int work_ff, double *__restrict__ S, unsigned *err,
     const uint8_t *__restrict__ eshift, PhaseTab ph, double *__restrict__ Si) {
   extern __shared__ float4 sm_see4[];
-  const int e = order[blockIdx.x], tid = threadIdx.x;
+  const int e = order[items[3 * blockIdx.x]], tid = threadIdx.x;
+  const int pb = items[3 * blockIdx.x + 1], pe_ = items[3 * blockIdx.x + 2];
   const int n = (int)(doff[e + 1] - doff[e]), ne = n - 64;
   if (ne <= 0) return;
   const int A = aoff[e + 1] - aoff[e];
@@ -108,20 +118,24 @@ __global__ void __launch_bounds__(SE_NT) k_see(
     scol[(c >> 3) * 8 + (c & 7)] = r;
   }
   const int npair = A * (A + 1) / 2;
+  if (pb < 0 || pe_ > npair || pb >= pe_) {
+    if (tid == 0) atomicOr(err, DEVERR_SHAPE);
+    return;
+  }
   if (tid < A) {   // pairs (alpha, beta), alpha <= beta, alpha-major
     int k = tid * A - tid * (tid - 1) / 2;
     for (int b = tid; b < A; ++b) pairs[k++] = tid | (b << 8);
   }
   const float *pe = psi + 4 * toff32[e];
   const float4 *qe = qdat + qpoff[e];
-  const float *pt = ptab + 32 * qpoff[e];   // per point: ..., [28] sqrt(w)
   const int32_t *m = smap + soff[e];
   const uint8_t *esh = BLOCH ? eshift + doff[e] : nullptr;
 
   for (int k = partoff[e]; k < partoff[e + 1]; ++k) {
     const int p = part_p[k], p2 = p * p, p3 = p2 * p, qs = part_q[k];
     const int per = 3 * p2 + 9 * p + 27;   // work pairs of one enrichment pair
-    if (p > pm || per > work_ff || (STAGED && A * p3 > stage_f)) {
+    const bool staged = A * p3 <= stage_f;
+    if (p > pm || per > work_ff) {
       if (tid == 0) atomicOr(err, DEVERR_SHAPE);
       return;
     }
@@ -131,26 +145,29 @@ __global__ void __launch_bounds__(SE_NT) k_see(
       const int stride = d == 0 ? 1 : (d == 1 ? p : p2);
       const float4 x4 = qe[qs + t * stride];
       const float x = d == 0 ? x4.x : (d == 1 ? x4.y : x4.z);
-      const float l0 = __fsub_rn(1.0f, x), l1 = __fadd_rn(1.0f, x);
+      // the PU factors 1/2 (1 -+ x) per axis (exact halving), so the three
+      // axes' products carry phi_v phi_v' = 1/64 prod u_k exactly
+      const float l0 = 0.5f * __fsub_rn(1.0f, x), l1 = 0.5f * __fadd_rn(1.0f, x);
       U[(d * 3 + 0) * pm + t] = ff_prod(l0, l0);
       U[(d * 3 + 1) * pm + t] = ff_prod(l0, l1);
       U[(d * 3 + 2) * pm + t] = ff_prod(l1, l1);
     }
-    // sqrt(w) Psi of a slot at a point of the cell, rounded once to FP32 (Psi
-    // from the table [q/8][slot][comp][q%8], component 0)
+    // sqrt(w) Psi of a slot at a point of the cell, rounded once to FP32 (w
+    // from the point array, Psi from the table [q/8][slot][comp][q%8],
+    // component 0)
     auto sval = [&](int slot, int lq) -> float {
       const int q = qs + lq;
-      return __fmul_rn(pt[32 * q + 28], pe[((int64_t)(q >> 3) * A + slot) * 32 + (q & 7)]);
+      return __fmul_rn(__fsqrt_rn(qe[q].w), pe[((int64_t)(q >> 3) * A + slot) * 32 + (q & 7)]);
     };
-    if (STAGED)
+    if (staged)
       for (int o = tid; o < A * p3; o += SE_NT) {
         const int s = o / p3, lq = o - s * p3;
         stg[o] = sval(s, lq);
       }
     __syncthreads();
-    const int npc = max(1, min(npair, work_ff / per));
-    for (int c0 = 0; c0 < npair; c0 += npc) {
-      const int nc = min(npc, npair - c0);
+    const int npc = max(1, min(pe_ - pb, work_ff / per));
+    for (int c0 = pb; c0 < pe_; c0 += npc) {
+      const int nc = min(npc, pe_ - c0);
       ff *T1 = work;                    // [nc][p^2][3]: z outputs
       ff *T2 = T1 + nc * 3 * p2;        // [nc][p][kz][ky]
       ff *P = T2 + nc * 9 * p;          // [nc][kz][ky][kx]
@@ -161,16 +178,16 @@ __global__ void __launch_bounds__(SE_NT) k_see(
         ff a0 = {0.0f, 0.0f}, a1 = {0.0f, 0.0f}, a2 = {0.0f, 0.0f};
         for (int qz = 0; qz < p; ++qz) {
           const int lq = qxy + p2 * qz;
-          const ff f = STAGED ? ff_prod(stg[al * p3 + lq], stg[be * p3 + lq])
+          const ff f = staged ? ff_prod(stg[al * p3 + lq], stg[be * p3 + lq])
                               : ff_prod(sval(al, lq), sval(be, lq));
           a0 = ff_fma(f, U[6 * pm + qz], a0);
           a1 = ff_fma(f, U[7 * pm + qz], a1);
           a2 = ff_fma(f, U[8 * pm + qz], a2);
         }
         ff *t1 = T1 + (size_t)it * 3;
-        t1[0] = a0;
-        t1[1] = a1;
-        t1[2] = a2;
+        t1[0] = ff_norm(a0);
+        t1[1] = ff_norm(a1);
+        t1[2] = ff_norm(a2);
       }
       __syncthreads();
       // y: one thread per (pair, qx, kz)
@@ -185,9 +202,9 @@ __global__ void __launch_bounds__(SE_NT) k_see(
           b2 = ff_fma(t, U[5 * pm + qy], b2);
         }
         ff *t2 = T2 + ((size_t)g * p + qx) * 9 + kz * 3;
-        t2[0] = b0;
-        t2[1] = b1;
-        t2[2] = b2;
+        t2[0] = ff_norm(b0);
+        t2[1] = ff_norm(b1);
+        t2[2] = ff_norm(b2);
       }
       __syncthreads();
       // x: one thread per (pair, kz, ky)
@@ -202,9 +219,9 @@ __global__ void __launch_bounds__(SE_NT) k_see(
           c2v = ff_fma(t, U[2 * pm + qx], c2v);
         }
         ff *pp = P + g * 27 + j * 3;
-        pp[0] = c0v;
-        pp[1] = c1v;
-        pp[2] = c2v;
+        pp[0] = ff_norm(c0v);
+        pp[1] = ff_norm(c1v);
+        pp[2] = ff_norm(c2v);
       }
       __syncthreads();
       // scatter: one thread per (pair, vertex of alpha, vertex of beta); a
@@ -218,7 +235,7 @@ __global__ void __launch_bounds__(SE_NT) k_see(
         const int kx = (i & 1) + (j & 1), ky = ((i >> 1) & 1) + ((j >> 1) & 1),
                   kz = (i >> 2) + (j >> 2);
         const ff pv = P[g * 27 + (kz * 3 + ky) * 3 + kx];
-        const double v = ((double)pv.hi + (double)pv.lo) * (1.0 / 64.0);
+        const double v = (double)pv.hi + (double)pv.lo;
         const int s_rs = m[(64 + r) * n + 64 + s], s_sr = m[(64 + s) * n + 64 + r];
         if (BLOCH) {   // (r, s) with conj(ph_r) ph_s, (s, r) with its conjugate
           const int a = esh[64 + r], b = esh[64 + s];
@@ -242,44 +259,37 @@ __global__ void __launch_bounds__(SE_NT) k_see(
 
 }  // namespace
 
-// Shared-memory budget of the Psi stage (floats); cells of elements with more
-// enrichment values than this read the FP32 table directly.
+// Shared-memory budget of the Psi stage (floats); cells with more enrichment
+// values than this read the FP32 table directly.
 static constexpr int SEE_STAGE_MAX_F = 8192;
 static constexpr int SEE_WORK_FF = 2048;
 
-pufe_status launch_see(pufe_ctx *ctx, const PhaseTab *ph, double *S, double *Si, int first,
-                       int count, cudaStream_t st) {
-  if (count <= 0) return PUFE_OK;
+pufe_status launch_see(pufe_ctx *ctx, const PhaseTab *ph, double *S, double *Si, cudaStream_t st) {
+  if (ctx->n_sitems <= 0) return PUFE_OK;
   auto &D = ctx->d;
   const int pm = std::max(1, ctx->max_part_p);
   const int amax = std::max(1, ctx->max_alpha);
   if (amax > 255) return fail(PUFE_EINVAL, "more than 255 enrichments on one element");
   const int per_max = 3 * pm * pm + 9 * pm + 27;
   const int work = std::max(SEE_WORK_FF, per_max);
-  // stage the cells when every element's largest cell fits the budget
-  int need = 0;
-  for (int64_t k = first; k < first + count; ++k) need = std::max(need, (int)ctx->see_stage[ctx->order[k]]);
-  const bool staged = need <= SEE_STAGE_MAX_F;
-  const int stage = staged ? need : 0;
+  // the stage is sized for the largest cell that fits the budget
+  int stage = 0;
+  for (int64_t e = 0; e < ctx->nelem; ++e)
+    if (ctx->see_stage[e] <= SEE_STAGE_MAX_F) stage = std::max(stage, (int)ctx->see_stage[e]);
   const size_t ints = (size_t)amax * 8 + (size_t)amax * (amax + 1) / 2;
   const size_t sm = ((size_t)9 * pm + work) * sizeof(ff) + (size_t)stage * sizeof(float) +
                     ints * sizeof(int);
   if (sm > 227 * 1024) return fail(PUFE_EINVAL, "E-E overlap kernel: shared memory above 227 KB");
   auto go = [&](auto kern, const uint8_t *esh, PhaseTab tab, double *si) -> pufe_status {
     PUFE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    kern<<<(unsigned)count, SE_NT, sm, st>>>(D.order + first, D.qpoff, D.qdat, D.ptab, D.partoff,
-                                             D.part_p, D.part_q, D.doff, D.ecol, D.aoff,
-                                             D.toff32, D.psi32, D.soff, D.smap, pm, amax, stage,
-                                             work, S, D.err, esh, tab, si);
+    kern<<<(unsigned)ctx->n_sitems, SE_NT, sm, st>>>(
+        D.order, D.sitems, D.qpoff, D.qdat, D.partoff, D.part_p, D.part_q, D.doff, D.ecol,
+        D.aoff, D.toff32, D.psi32, D.soff, D.smap, pm, amax, stage, work, S, D.err, esh, tab, si);
     PUFE_CUDA_TRY(cudaGetLastError());
     return PUFE_OK;
   };
-  if (ph) {
-    return staged ? go(k_see<true, true>, D.eshift, *ph, Si)
-                  : go(k_see<false, true>, D.eshift, *ph, Si);
-  }
-  return staged ? go(k_see<true, false>, nullptr, PhaseTab{}, nullptr)
-                : go(k_see<false, false>, nullptr, PhaseTab{}, nullptr);
+  if (ph) return go(k_see<true>, D.eshift, *ph, Si);
+  return go(k_see<false>, nullptr, PhaseTab{}, nullptr);
 }
 
 }  // namespace pufe

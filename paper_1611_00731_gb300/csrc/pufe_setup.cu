@@ -777,7 +777,7 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
   for (auto &parts : rule)
     for (auto &pt : parts) min_p = std::min(min_p, pt.p);
   const bool fe_exact = min_p >= 4;
-  std::vector<double> TF, S0, SF;
+  std::vector<double> TF, SF, S0;
   if (fe_exact) {
     double M1[4][4] = {{0}}, K1[4][4] = {{0}}, D1[4][4] = {{0}};   // D1[a][b] = int L'_a L_b
     for (int g = 0; g < 4; ++g) {
@@ -836,6 +836,7 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
           TF[i * 64 + j] = 0.5 * S.detJ * t;
         }
     }
+    // the overlap constants summed over the elements through the scatter map
     S0.assign(nnz, 0.0);
     for (int64_t e = 0; e < nelem; ++e) {
       const int n = n_e[e];
@@ -899,6 +900,10 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
   ctx->strip_npair_max = 0;
   ctx->adj_sf_floats = 0;
   ctx->adj_sf_all = true;
+  ctx->part_p_host.assign(nelem, {});
+  for (int64_t e = 0; e < nelem; ++e)
+    for (auto &pt : rule[e]) ctx->part_p_host[e].push_back(pt.p);
+  ctx->eeform_host.assign(nelem, 0);
   ctx->n_slot.assign(nelem, 0);
   for (int64_t e = 0; e < nelem; ++e) ctx->n_slot[e] = (int32_t)ealpha[e].size();
   ctx->see_stage.assign(nelem, 0);
@@ -1001,6 +1006,167 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
   }
   ctx->n_wsplit = (int64_t)(wsplit.size() / 3);
 
+  // ---- mixed-path work list of the n_e > 128 elements -------------------------
+  // The tensor-core kernel runs one persistent CTA per SM over these items; an
+  // element's cost is (128-row tiles) x (chunks of 8 padded points).  Elements
+  // costing more than the mean per SM are cut into chunk ranges (at least 8
+  // chunks each) whose partial tiles meet in the FP64 atomics; the FP32
+  // adjoint of these elements takes the same ranges (disjoint points).
+  std::vector<int32_t> titems;
+  {
+    int nsm = 152;
+    if (ctx->on_device) {
+      int v = 0;
+      if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, ctx->device) == cudaSuccess &&
+          v > 0)
+        nsm = v;
+    }
+    struct TItem {
+      int32_t k, c0, c1;
+      int64_t c;
+    };
+    std::vector<TItem> items;
+    int64_t total = 0;
+    for (int k = 0; k < n_big; ++k) {
+      const int64_t e = order[k];
+      total += (int64_t)((n_e[e] + 127) / 128) * ((qpoff[e + 1] - qpoff[e]) / 8);
+    }
+    const double target = std::max(1.0, (double)total / nsm);
+    for (int k = 0; k < n_big; ++k) {
+      const int64_t e = order[k];
+      const int nmt = (n_e[e] + 127) / 128;
+      const int nch = (int)((qpoff[e + 1] - qpoff[e]) / 8);
+      int m = (int)std::ceil((double)nmt * nch / target);
+      m = std::max(1, std::min(m, nch / 8));
+      int prev = 0;
+      for (int j = 1; j <= m; ++j) {
+        const int b = (j == m) ? nch : (int)((int64_t)j * nch / m);
+        items.push_back(TItem{k, prev, b, (int64_t)nmt * (b - prev)});
+        prev = b;
+      }
+    }
+    std::stable_sort(items.begin(), items.end(),
+                     [](const TItem &x, const TItem &y) { return x.c > y.c; });
+    std::vector<int64_t> covered(std::max(1, n_big), 0);
+    for (auto &it : items) {
+      const int64_t e = order[it.k];
+      if (it.c0 < 0 || it.c1 <= it.c0 || (int64_t)it.c1 * 8 > qpoff[e + 1] - qpoff[e])
+        return fail(PUFE_EINVAL, "internal: bad chunk range in the mixed work list");
+      covered[it.k] += it.c1 - it.c0;
+      titems.push_back(it.k);
+      titems.push_back(it.c0);
+      titems.push_back(it.c1);
+    }
+    for (int k = 0; k < n_big; ++k)
+      if (covered[k] * 8 != qpoff[order[k] + 1] - qpoff[order[k]])
+        return fail(PUFE_EINVAL, "internal: the mixed work list misses chunks");
+  }
+  ctx->n_titems = (int)(titems.size() / 3);
+
+  // Work list of the E-E kernel of S: elements with enrichment columns, cut
+  // into ranges of their A (A + 1) / 2 slot pairs so that no range costs
+  // (pairs x points) much more than a quarter of the mean per SM (four CTAs
+  // share an SM); the ranges' entries are disjoint, so no order is implied.
+  std::vector<int32_t> sitems;
+  {
+    int nsm = 152;
+    if (ctx->on_device) {
+      int v = 0;
+      if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, ctx->device) == cudaSuccess &&
+          v > 0)
+        nsm = v;
+    }
+    struct SItem {
+      int32_t k, pb, pe;
+      int64_t c;
+    };
+    std::vector<SItem> items;
+    int64_t total = 0;
+    for (int64_t k = 0; k < nelem; ++k) {
+      const int64_t e = order[k];
+      const int64_t A = (int64_t)ealpha[e].size();
+      if (n_e[e] > 64) total += A * (A + 1) / 2 * (qoff[e + 1] - qoff[e]);
+    }
+    const double target = std::max(1.0, (double)total / (4.0 * nsm));
+    for (int64_t k = 0; k < nelem; ++k) {
+      const int64_t e = order[k];
+      if (n_e[e] <= 64) continue;
+      const int A = (int)ealpha[e].size(), np = A * (A + 1) / 2;
+      const int64_t Q = qoff[e + 1] - qoff[e];
+      const int m = std::max(1, std::min(np, (int)std::ceil((double)np * Q / target)));
+      int prev = 0;
+      for (int j = 1; j <= m; ++j) {
+        const int b = (j == m) ? np : (int)((int64_t)j * np / m);
+        items.push_back(SItem{(int32_t)k, prev, b, (int64_t)(b - prev) * Q});
+        prev = b;
+      }
+    }
+    std::stable_sort(items.begin(), items.end(),
+                     [](const SItem &x, const SItem &y) { return x.c > y.c; });
+    for (auto &it : items) {
+      sitems.push_back(it.k);
+      sitems.push_back(it.pb);
+      sitems.push_back(it.pe);
+    }
+  }
+  ctx->n_sitems = (int)(sitems.size() / 3);
+
+  // Work list of the strip kernel (64 < n_e <= 128, after the n_e > 128
+  // elements in `order`): an element whose cost (points x enrichment columns)
+  // exceeds half the mean per SM (two strip CTAs share an SM) is cut into
+  // ranges of its (sub)cells; the ranges' partial blocks meet in the atomics.
+  std::vector<int32_t> citems;
+  {
+    int nsm = 152;
+    if (ctx->on_device) {
+      int v = 0;
+      if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, ctx->device) == cudaSuccess &&
+          v > 0)
+        nsm = v;
+    }
+    struct CItem {
+      int32_t k, c0, c1;
+      int64_t c;
+    };
+    std::vector<CItem> items;
+    auto cell_cost = [&](int64_t e, int32_t j) {
+      const int64_t p = part_p[j];
+      return p * p * p * (n_e[e] - 64);
+    };
+    int64_t total = 0;
+    for (int64_t k = n_big; k < nelem; ++k) {
+      const int64_t e = order[k];
+      if (n_e[e] <= 64 || n_e[e] > 128) continue;
+      for (int32_t j = partoff[e]; j < partoff[e + 1]; ++j) total += cell_cost(e, j);
+    }
+    const double target = std::max(1.0, (double)total / (2.0 * nsm));
+    for (int64_t k = n_big; k < nelem; ++k) {
+      const int64_t e = order[k];
+      if (n_e[e] <= 64 || n_e[e] > 128) continue;
+      const int32_t nc = partoff[e + 1] - partoff[e];
+      int32_t c0 = 0;
+      int64_t acc = 0;
+      for (int32_t c = 0; c < nc; ++c) {
+        const int64_t cc = cell_cost(e, partoff[e] + c);
+        if (c > c0 && acc + cc > target) {
+          items.push_back(CItem{(int32_t)k, c0, c, acc});
+          c0 = c;
+          acc = 0;
+        }
+        acc += cc;
+      }
+      items.push_back(CItem{(int32_t)k, c0, nc, acc});
+    }
+    std::stable_sort(items.begin(), items.end(),
+                     [](const CItem &x, const CItem &y) { return x.c > y.c; });
+    for (auto &it : items) {
+      citems.push_back(it.k);
+      citems.push_back(it.c0);
+      citems.push_back(it.c1);
+    }
+  }
+  ctx->n_citems = (int)(citems.size() / 3);
+
   pufe_status st;
   auto &D = ctx->d;
   if (ctx->on_device) {
@@ -1030,6 +1196,10 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
   if ((st = upload(&D.smap, smap)) != PUFE_OK) return st;
   if ((st = upload(&D.order, order)) != PUFE_OK) return st;
   if (!wsplit.empty() && (st = upload(&D.wsplit, wsplit)) != PUFE_OK) return st;
+  if (!titems.empty() && (st = upload(&D.titems, titems)) != PUFE_OK) return st;
+  if (!sitems.empty() && (st = upload(&D.sitems, sitems)) != PUFE_OK) return st;
+  if (!citems.empty() && (st = upload(&D.citems, citems)) != PUFE_OK) return st;
+  if ((st = upload(&D.eeform, ctx->eeform_host)) != PUFE_OK) return st;
   if (fe_exact) {
     if ((st = upload(&D.Tfe, TF)) != PUFE_OK) return st;
     if ((st = upload(&D.Sfe, SF)) != PUFE_OK) return st;
@@ -1072,7 +1242,8 @@ static void free_device(pufe_ctx *ctx) {
   void *ptrs[] = {D.qoff, D.x, D.w, D.xi, D.doff, D.dofs, D.ecol, D.eshift, D.aoff, D.alist,
                   D.toff, D.psi, D.psi32, D.qpoff, D.qdat, D.ptab, D.vpad, D.toff32, D.eorig,
                   D.Tfe, D.Sfe, D.S0, D.partoff, D.part_p, D.part_q,
-                  D.orb, D.orbf, D.rowptr, D.col, D.soff, D.smap, D.order, D.wsplit, D.err};
+                  D.orb, D.orbf, D.rowptr, D.col, D.soff, D.smap, D.order, D.wsplit,
+                  D.titems, D.sitems, D.citems, D.eeform, D.err};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (D.ev_fork) cudaEventDestroy(D.ev_fork);

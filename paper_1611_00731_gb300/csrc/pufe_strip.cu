@@ -7,23 +7,22 @@
 //   S_ir = sum_q w_q phi_i b_r,
 // for i in F or E and r in E; the FE-FE block is done elsewhere.
 //
-// F x E block: for fixed r the sum over q is the projection of per-point
-// fields onto the tensor-product functions L_a(x) L_b(y) L_c(z), so on a
-// p^3 (sub)cell it contracts one axis at a time (sum factorization):
-//   f^d = w (d b_r / d x_d) / h_d  (paired with L' along axis d),
-//   f^V = w V b_r,  f^S = w b_r,
-//   z: X_c = sum L_c f^x, Y_c = sum L_c f^y, Z_c = sum (L'_c f^z + L_c f^V),
-//      S_c = sum L_c f^S                       (16 p^3 multiply-adds per r)
-//   y: X_bc = sum L_b X_c, W_bc = sum (L'_b Y_c + L_b Z_c), S_bc = sum L_b S_c
-//   x: H_abc = sum (L'_a X_bc + L_a W_bc),     S_abc = sum L_a S_bc
-// against 5 * 64 p^3 for the direct product.
+// F x E block, slot form: the trilinear PU factor of r = (v, alpha) is a
+// product of linears 1 -+ xi per axis, so all eight vertex columns of a slot
+// alpha are projections of the slot's four per-point fields (w Psi,
+// w V Psi, w grad Psi) onto tensor products of L_a (1 -+ xi), L'_a (1 -+ xi)
+// and L'_a along each axis, contracted one axis at a time on a p^3
+// (sub)cell (sum factorization; the expansion is written out in
+// strip_part), about 48 p^3 multiply-adds per slot against 5 * 64 * 8 p^3
+// for the direct products of its eight columns.
 //
 // E x E block of H, direct form: a small dense product over the element's
 // points, symmetric in (r, s), so only 4 x 4 tiles with r-block <= s-block are
 // formed:
 //   H_rs = sum_q [sum_d y_dr y_ds + V_q z_r z_s],
 //   y_dr = sqrt(w/2) d b_r / d x_d,  z_r = sqrt(w) b_r.
-// The E x E block of S is computed in FP64 by its own kernel (pufe_see64.cu).
+// The E x E block of S is computed with FP64-class sums by its own kernel
+// (pufe_see.cu).
 //
 // E x E block of H, enrichment-pair form: for r = (v, alpha), s = (v', beta) the
 // PU factors are trilinear, phi_v = 1/8 prod_d (1 + s_d x_d) with s_d = +-1,
@@ -48,6 +47,10 @@
 // element block is added into the FP64 CSR values with atomics (both
 // triangles, through the element's scatter map).
 #include <algorithm>
+#include <cstdlib>
+#include <fstream>
+#include <map>
+#include <string>
 
 #include "pufe_internal.h"
 
@@ -56,6 +59,9 @@ namespace {
 
 constexpr int ST_NT = 256;
 constexpr int ST_KC = 32;   // points per E x E chunk
+// registers per thread: 80 lets three 256-thread CTAs share an SM (when
+// their shared memory fits, <= 75 KB each)
+constexpr int ST_MAXREG = 80;
 
 __device__ __forceinline__ void lag3vd(float t, float *L, float *dL) {
   const float a = t + 1.0f, b = t + (1.0f / 3.0f), c = t - (1.0f / 3.0f), d = t - 1.0f;
@@ -104,7 +110,14 @@ struct StripElem {
   bool wantH, wantS, useV;
   float sx, sy, sz;
   // shared memory
-  float *stage, *work, *HE, *L1, *D1;
+  float *stage, *work, *HE;
+  // 1D factors of the F x E slot form per axis d and 1D point t:
+  // T4[(d pm + t) 2 + l] = (L_a l_l)_a, T4[6 pm + (d pm + t) 2 + l] = (L'_a l_l)_a,
+  // T4[12 pm + d pm + t] = (L'_a)_a, T4[15 pm + d pm + t] = (L_a)_a
+  // (a = 0..3 in the four components)
+  const float4 *T4;
+  const int *scol;   // [slot][vertex]: column of (slot, vertex), -1 if absent
+  bool fxs;          // F x E block in the slot form (else column by column)
   const int *ecs;
   int pm, wfloats;
   // E x E tile of this thread (direct form)
@@ -197,108 +210,267 @@ __device__ __forceinline__ void strip_part(const StripElem &E, double *__restric
     o.bz = fmaf(fx * fy * gz, p0, phi * p3v);
     return o;
   };
-  const float ihx = 0.5f * E.sx, ihy = 0.5f * E.sy, ihz = 0.5f * E.sz;   // 1 / h_d
   const int pm = E.pm;
-  const float *L1 = E.L1, *D1 = E.D1;
   const int32_t *m = E.m;
   const int n = E.n;
 
-  // ---- F x E block ---------------------------------------------------------
-  const int per_r = p2 * 20 + p * 48;
-  const int G = max(1, min(min(ne, E.wfloats / per_r), ST_NT / p2));
-  const FastDiv dp2(p2), dp16(p * 16);
-  for (int r0 = 0; r0 < ne; r0 += G) {
-    const int Gc = min(G, ne - r0);
-    float *T1 = E.work;                   // [Gc][p^2][20]: X, Y, Z, S (x4), pad
-    float *T2 = E.work + Gc * p2 * 20;    // [Gc][p][16][3]
-    __syncthreads();
-    // z: one thread per (r, qx, qy) column
-    for (int it = tid; it < Gc * p2; it += ST_NT) {
-      const int g = dp2.div(it), qxy = it - g * p2;
-      const int code = E.ecs[r0 + g];
-      float X[4] = {0.f, 0.f, 0.f, 0.f}, Y[4] = {0.f, 0.f, 0.f, 0.f};
-      float Z[4] = {0.f, 0.f, 0.f, 0.f}, Sa[4] = {0.f, 0.f, 0.f, 0.f};
-      for (int qz = 0; qz < p; ++qz) {
-        const int lq = qxy + p2 * qz;
-        const float4 x4 = xval(lq);
-        const float vq = vval(lq);
-        const EnrVal ev = enr(lq, code, x4);
-        const float fx = x4.w * ev.bx * ihx, fy = x4.w * ev.by * ihy, fz = x4.w * ev.bz * ihz;
-        const float fS = x4.w * ev.b, fV = fS * vq;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          const float Lc = L1[(8 + c) * pm + qz], Dc = D1[(8 + c) * pm + qz];
-          X[c] = fmaf(Lc, fx, X[c]);
-          Y[c] = fmaf(Lc, fy, Y[c]);
-          Z[c] = fmaf(Dc, fz, fmaf(Lc, fV, Z[c]));
-          Sa[c] = fmaf(Lc, fS, Sa[c]);
-        }
+  // one (i, r) entry of the F x E block into both triangles of H and S
+  auto add_fe = [&](int i, int r, float hs, float ss) {
+    const int s_ir = m[i * n + 64 + r], s_ri = m[(64 + r) * n + i];
+    if (BLOCH) {   // (i, r) with conj(ph_i) ph_r, (r, i) with its conjugate
+      float pr, pi;
+      pair_phase(E, E.esh[i], E.esh[64 + r], pr, pi);
+      if (E.wantH) {
+        atomicAdd(H + s_ir, (double)(hs * pr));
+        atomicAdd(E.Hi + s_ir, (double)(hs * pi));
+        atomicAdd(H + s_ri, (double)(hs * pr));
+        atomicAdd(E.Hi + s_ri, (double)(-hs * pi));
       }
-      float4 *t1 = reinterpret_cast<float4 *>(T1 + (size_t)it * 20);
-      t1[0] = make_float4(X[0], X[1], X[2], X[3]);
-      t1[1] = make_float4(Y[0], Y[1], Y[2], Y[3]);
-      t1[2] = make_float4(Z[0], Z[1], Z[2], Z[3]);
-      t1[3] = make_float4(Sa[0], Sa[1], Sa[2], Sa[3]);
+      if (E.wantS) {
+        atomicAdd(S + s_ir, (double)(ss * pr));
+        atomicAdd(E.Si + s_ir, (double)(ss * pi));
+        atomicAdd(S + s_ri, (double)(ss * pr));
+        atomicAdd(E.Si + s_ri, (double)(-ss * pi));
+      }
+    } else {
+      if (E.wantH) {
+        atomicAdd(H + s_ir, (double)hs);
+        atomicAdd(H + s_ri, (double)hs);
+      }
+      if (E.wantS) {
+        atomicAdd(S + s_ir, (double)ss);
+        atomicAdd(S + s_ri, (double)ss);
+      }
     }
-    __syncthreads();
-    // y: one thread per (r, qx, b, c)
-    for (int it = tid; it < Gc * p * 16; it += ST_NT) {
-      const int g = dp16.div(it), rem = it - g * p * 16;
-      const int qx = rem >> 4, bc = rem & 15, b = bc >> 2, c = bc & 3;
-      float x2 = 0.0f, w2 = 0.0f, s2 = 0.0f;
-      const float *t1 = T1 + (size_t)(g * p2 + qx) * 20;
-      for (int qy = 0; qy < p; ++qy, t1 += p * 20) {
-        const float Lb = L1[(4 + b) * pm + qy], Db = D1[(4 + b) * pm + qy];
-        x2 = fmaf(Lb, t1[c], x2);
-        w2 = fmaf(Db, t1[4 + c], fmaf(Lb, t1[8 + c], w2));
-        s2 = fmaf(Lb, t1[12 + c], s2);
+  };
+  const float4 *MT = E.T4, *DT = E.T4 + 6 * pm, *D0T = E.T4 + 12 * pm, *LT = E.T4 + 15 * pm;
+  const FastDiv dp2(p2), dp(p), dp16(p * 16);
+
+  // ---- F x E block, column form ----------------------------------------------
+  // For fixed r the sum over q is the projection of per-point fields onto
+  // L_a(x) L_b(y) L_c(z), contracted one axis at a time:
+  //   f^d = w (d b_r / d x_d) / h_d  (paired with L' along axis d),
+  //   f^V = w V b_r,  f^S = w b_r,
+  //   z: X_c = sum L_c f^x, Y_c = sum L_c f^y, Z_c = sum (L'_c f^z + L_c f^V),
+  //      S_c = sum L_c f^S                       (16 p^3 multiply-adds per r)
+  //   y: X_bc = sum L_b X_c, W_bc = sum (L'_b Y_c + L_b Z_c), S_bc = sum L_b S_c
+  //   x: H_abc = sum (L'_a X_bc + L_a W_bc),     S_abc = sum L_a S_bc
+  // (b_r evaluated at every point for each column); taken when the element's
+  // slots hold few vertex columns each, where the slot form's per-slot y and
+  // x stages would cost more.
+  if (!E.fxs) {
+    const float ihx = 0.5f * E.sx, ihy = 0.5f * E.sy, ihz = 0.5f * E.sz;   // 1 / h_d
+    const int per_r = p2 * 20 + p * 48;
+    const int G = max(1, min(min(ne, E.wfloats / per_r), ST_NT / p2));
+    for (int r0 = 0; r0 < ne; r0 += G) {
+      const int Gc = min(G, ne - r0);
+      float *T1 = E.work;                   // [Gc][p^2][20]: X, Y, Z, S (x4), pad
+      float *T2 = E.work + Gc * p2 * 20;    // [Gc][p][16][3]
+      __syncthreads();
+      // z: one thread per (r, qx, qy) column
+      for (int it = tid; it < Gc * p2; it += ST_NT) {
+        const int g = dp2.div(it), qxy = it - g * p2;
+        const int code = E.ecs[r0 + g];
+        float4 X = make_float4(0.f, 0.f, 0.f, 0.f), Y = X, Z = X, Sa = X;
+        for (int qz = 0; qz < p; ++qz) {
+          const int lq = qxy + p2 * qz;
+          const float4 x4 = xval(lq);
+          const float vq = vval(lq);
+          const EnrVal ev = enr(lq, code, x4);
+          const float fx = x4.w * ev.bx * ihx, fy = x4.w * ev.by * ihy, fz = x4.w * ev.bz * ihz;
+          const float fS = x4.w * ev.b, fV = fS * vq;
+          const float4 Lc = LT[2 * pm + qz], Dc = D0T[2 * pm + qz];
+          X.x = fmaf(Lc.x, fx, X.x);
+          X.y = fmaf(Lc.y, fx, X.y);
+          X.z = fmaf(Lc.z, fx, X.z);
+          X.w = fmaf(Lc.w, fx, X.w);
+          Y.x = fmaf(Lc.x, fy, Y.x);
+          Y.y = fmaf(Lc.y, fy, Y.y);
+          Y.z = fmaf(Lc.z, fy, Y.z);
+          Y.w = fmaf(Lc.w, fy, Y.w);
+          Z.x = fmaf(Dc.x, fz, fmaf(Lc.x, fV, Z.x));
+          Z.y = fmaf(Dc.y, fz, fmaf(Lc.y, fV, Z.y));
+          Z.z = fmaf(Dc.z, fz, fmaf(Lc.z, fV, Z.z));
+          Z.w = fmaf(Dc.w, fz, fmaf(Lc.w, fV, Z.w));
+          Sa.x = fmaf(Lc.x, fS, Sa.x);
+          Sa.y = fmaf(Lc.y, fS, Sa.y);
+          Sa.z = fmaf(Lc.z, fS, Sa.z);
+          Sa.w = fmaf(Lc.w, fS, Sa.w);
+        }
+        float4 *t1 = reinterpret_cast<float4 *>(T1 + (size_t)it * 20);
+        t1[0] = X;
+        t1[1] = Y;
+        t1[2] = Z;
+        t1[3] = Sa;
       }
-      float *t2 = T2 + (size_t)it * 3;
-      t2[0] = x2;
-      t2[1] = w2;
-      t2[2] = s2;
+      __syncthreads();
+      // y: one thread per (r, qx, b, c)
+      for (int it = tid; it < Gc * p * 16; it += ST_NT) {
+        const int g = dp16.div(it), rem = it - g * p * 16;
+        const int qx = rem >> 4, bc = rem & 15, b = bc >> 2, c = bc & 3;
+        float x2 = 0.0f, w2 = 0.0f, s2 = 0.0f;
+        const float *t1 = T1 + (size_t)(g * p2 + qx) * 20;
+        const float *lb = reinterpret_cast<const float *>(LT + pm) + b;
+        const float *db = reinterpret_cast<const float *>(D0T + pm) + b;
+        for (int qy = 0; qy < p; ++qy, t1 += p * 20) {
+          const float Lb = lb[4 * qy], Db = db[4 * qy];
+          x2 = fmaf(Lb, t1[c], x2);
+          w2 = fmaf(Db, t1[4 + c], fmaf(Lb, t1[8 + c], w2));
+          s2 = fmaf(Lb, t1[12 + c], s2);
+        }
+        float *t2 = T2 + (size_t)it * 3;
+        t2[0] = x2;
+        t2[1] = w2;
+        t2[2] = s2;
+      }
+      __syncthreads();
+      // x: one thread per (r, i), i = a + 4b + 16c
+      for (int it = tid; it < Gc * 64; it += ST_NT) {
+        const int g = it >> 6, i = it & 63, r = r0 + g;
+        const int a = i & 3, bc = ((i >> 2) & 3) * 4 + (i >> 4);
+        float hs = 0.0f, ss = 0.0f;
+        const float *t2 = T2 + ((size_t)g * p * 16 + bc) * 3;
+        const float *la = reinterpret_cast<const float *>(LT) + a;
+        const float *da = reinterpret_cast<const float *>(D0T) + a;
+        for (int qx = 0; qx < p; ++qx, t2 += 48) {
+          hs = fmaf(da[4 * qx], t2[0], fmaf(la[4 * qx], t2[1], hs));
+          ss = fmaf(la[4 * qx], t2[2], ss);
+        }
+        add_fe(i, r, hs, ss);
+      }
     }
-    __syncthreads();
-    // x: one thread per (r, i), i = a + 4b + 16c; add into both triangles
-    for (int it = tid; it < Gc * 64; it += ST_NT) {
-      const int g = it >> 6, i = it & 63, r = r0 + g;
-      const int a = i & 3, bc = ((i >> 2) & 3) * 4 + (i >> 4);
-      float hs = 0.0f, ss = 0.0f;
-      const float *t2 = T2 + ((size_t)g * p * 16 + bc) * 3;
-      for (int qx = 0; qx < p; ++qx, t2 += 48) {
-        hs = fmaf(D1[a * pm + qx], t2[0], fmaf(L1[a * pm + qx], t2[1], hs));
-        ss = fmaf(L1[a * pm + qx], t2[2], ss);
+  } else {
+    // ---- F x E block, slot form ------------------------------------------------
+    // For column r = (v, alpha), v = (t_x, t_y, t_z), the PU factor is
+    // phi_v = 1/8 l_tx(x) l_ty(y) l_tz(z) with l_0 = 1 - xi, l_1 = 1 + xi, so
+    //   8 H_ir = <w V Psi, M M M> + sum_d [ 1/2 (2/h_d)^2 s_td <w Psi, D0 on d, M elsewhere>
+    //                                     + 1/2 (2/h_d) <w d_d Psi, D on d, M elsewhere> ],
+    //   8 S_ir = <w Psi, M M M>,
+    // i = (a, b, c), with the 1D factors M = L_a l_t, D = L'_a l_t, D0 = L'_a
+    // (derivatives in xi) and s_t = -1, +1 for t = 0, 1.  All eight vertices of
+    // a slot share the projections of its four fields (w Psi, w V Psi,
+    // w d_d Psi), contracted z, y, x:
+    //   z: Z_S, Z_x, Z_y on M_z; Z_V = M_z (w V Psi) + D_z (1/2 (2/h_z) w d_z Psi)
+    //      + D0_z (1/2 (2/h_z)^2 s_tz w Psi)                    (8 (c, t_z) each)
+    //   y: W1 = M_y Z_V + 1/2 (2/h_y) D_y Z_y + 1/2 (2/h_y)^2 s_ty D0_y Z_S,
+    //      W3 = M_y Z_x, WS = M_y Z_S                          (64 (b t_y, c t_z))
+    //   x: 8 H = M_x W1 + 1/2 (2/h_x) D_x W3 + 1/2 (2/h_x)^2 s_tx D0_x WS,
+    //      8 S = M_x WS                                          (512 per slot)
+    // about 48 p^3 + 320 p^2 + 2048 p multiply-adds per slot, against
+    // 8 (16 p^3 + 48 p^2 + 128 p) plus eight evaluations of b_r per point for
+    // the column-by-column projection.
+    const int per_s = 36 * p2 + 192 * p;
+    const int G = max(1, min(A, E.wfloats / per_s));
+    const float hx2 = 0.5f * E.sx, hy2 = 0.5f * E.sy, hz2 = 0.5f * E.sz;   // 1/2 (2/h_d)
+    const float hxx = hx2 * E.sx, hyy = hy2 * E.sy, hzz = hz2 * E.sz;       // 1/2 (2/h_d)^2
+    for (int s0 = 0; s0 < A; s0 += G) {
+      const int Gc = min(G, A - s0);
+      float *T1 = E.work;                   // [Gc][p^2][36]: Z_S, Z_x, Z_y, Z_V x (t_z, c), pad
+      float *T2 = E.work + Gc * p2 * 36;    // [Gc][p][b + 4 t_y][24]: W1, W3, WS x (t_z, c)
+      __syncthreads();
+      // z: one thread per (slot, qx, qy, t_z)
+      for (int it = tid; it < Gc * p2 * 2; it += ST_NT) {
+        const int tz = it & 1, col = it >> 1;
+        const int g = dp2.div(col), qxy = col - g * p2, slot = s0 + g;
+        const float f0s = tz ? hzz : -hzz;
+        float4 zs = make_float4(0.f, 0.f, 0.f, 0.f), zx = zs, zy = zs, zv = zs;
+        for (int qz = 0; qz < p; ++qz) {
+          const int lq = qxy + p2 * qz;
+          const float w = xval(lq).w;
+          const float fS = w * psv(lq, slot, 0), fx = w * psv(lq, slot, 1),
+                      fy = w * psv(lq, slot, 2), fz = hz2 * (w * psv(lq, slot, 3));
+          const float fV = fS * vval(lq), f0 = f0s * fS;
+          const float4 M = MT[(2 * pm + qz) * 2 + tz], D = DT[(2 * pm + qz) * 2 + tz],
+                       D0 = D0T[2 * pm + qz];
+          zs.x = fmaf(M.x, fS, zs.x);
+          zs.y = fmaf(M.y, fS, zs.y);
+          zs.z = fmaf(M.z, fS, zs.z);
+          zs.w = fmaf(M.w, fS, zs.w);
+          zx.x = fmaf(M.x, fx, zx.x);
+          zx.y = fmaf(M.y, fx, zx.y);
+          zx.z = fmaf(M.z, fx, zx.z);
+          zx.w = fmaf(M.w, fx, zx.w);
+          zy.x = fmaf(M.x, fy, zy.x);
+          zy.y = fmaf(M.y, fy, zy.y);
+          zy.z = fmaf(M.z, fy, zy.z);
+          zy.w = fmaf(M.w, fy, zy.w);
+          zv.x = fmaf(M.x, fV, fmaf(D.x, fz, fmaf(D0.x, f0, zv.x)));
+          zv.y = fmaf(M.y, fV, fmaf(D.y, fz, fmaf(D0.y, f0, zv.y)));
+          zv.z = fmaf(M.z, fV, fmaf(D.z, fz, fmaf(D0.z, f0, zv.z)));
+          zv.w = fmaf(M.w, fV, fmaf(D.w, fz, fmaf(D0.w, f0, zv.w)));
+        }
+        float4 *t1 = reinterpret_cast<float4 *>(T1 + (size_t)col * 36 + tz * 4);
+        t1[0] = zs;
+        t1[2] = zx;
+        t1[4] = zy;
+        t1[6] = zv;
       }
-      const int s_ir = m[i * n + 64 + r], s_ri = m[(64 + r) * n + i];
-      if (BLOCH) {   // (i, r) with conj(ph_i) ph_r, (r, i) with its conjugate
-        float pr, pi;
-        pair_phase(E, E.esh[i], E.esh[64 + r], pr, pi);
-        if (E.wantH) {
-          atomicAdd(H + s_ir, (double)(hs * pr));
-          atomicAdd(E.Hi + s_ir, (double)(hs * pi));
-          atomicAdd(H + s_ri, (double)(hs * pr));
-          atomicAdd(E.Hi + s_ri, (double)(-hs * pi));
+      __syncthreads();
+      // y: one thread per (slot, qx, b, t_y, t_z); four c each
+      for (int it = tid; it < Gc * p * 16; it += ST_NT) {
+        const int tz = it & 1, bty = (it >> 1) & 7, rest = it >> 4;   // rest = g p + qx
+        const int g = dp.div(rest), qx = rest - g * p;
+        const int b = bty & 3, ty = bty >> 2;
+        const float c0s = ty ? hyy : -hyy;
+        float4 w1 = make_float4(0.f, 0.f, 0.f, 0.f), w3 = w1, ws = w1;
+        const float4 *t1 = reinterpret_cast<const float4 *>(T1 + (size_t)(g * p2 + qx) * 36) + tz;
+        for (int qy = 0; qy < p; ++qy, t1 += p * 9) {
+          const float4 m4 = MT[(pm + qy) * 2 + ty], d4 = DT[(pm + qy) * 2 + ty], o4 = D0T[pm + qy];
+          const float My = b == 0 ? m4.x : (b == 1 ? m4.y : (b == 2 ? m4.z : m4.w));
+          const float Dy = hy2 * (b == 0 ? d4.x : (b == 1 ? d4.y : (b == 2 ? d4.z : d4.w)));
+          const float Oy = c0s * (b == 0 ? o4.x : (b == 1 ? o4.y : (b == 2 ? o4.z : o4.w)));
+          const float4 zs = t1[0], zx = t1[2], zy = t1[4], zv = t1[6];
+          w1.x = fmaf(My, zv.x, fmaf(Dy, zy.x, fmaf(Oy, zs.x, w1.x)));
+          w1.y = fmaf(My, zv.y, fmaf(Dy, zy.y, fmaf(Oy, zs.y, w1.y)));
+          w1.z = fmaf(My, zv.z, fmaf(Dy, zy.z, fmaf(Oy, zs.z, w1.z)));
+          w1.w = fmaf(My, zv.w, fmaf(Dy, zy.w, fmaf(Oy, zs.w, w1.w)));
+          w3.x = fmaf(My, zx.x, w3.x);
+          w3.y = fmaf(My, zx.y, w3.y);
+          w3.z = fmaf(My, zx.z, w3.z);
+          w3.w = fmaf(My, zx.w, w3.w);
+          ws.x = fmaf(My, zs.x, ws.x);
+          ws.y = fmaf(My, zs.y, ws.y);
+          ws.z = fmaf(My, zs.z, ws.z);
+          ws.w = fmaf(My, zs.w, ws.w);
         }
-        if (E.wantS) {
-          atomicAdd(S + s_ir, (double)(ss * pr));
-          atomicAdd(E.Si + s_ir, (double)(ss * pi));
-          atomicAdd(S + s_ri, (double)(ss * pr));
-          atomicAdd(E.Si + s_ri, (double)(-ss * pi));
+        float4 *t2 = reinterpret_cast<float4 *>(T2 + ((size_t)rest * 8 + bty) * 24) + tz;
+        t2[0] = w1;
+        t2[2] = w3;
+        t2[4] = ws;
+      }
+      __syncthreads();
+      // x: one thread per (slot, vertex, b, c); the four a, then into both
+      // triangles of the columns that exist
+      for (int it = tid; it < Gc * 128; it += ST_NT) {
+        const int bc = it & 15, v = (it >> 4) & 7, g = it >> 7;
+        const int r = E.scol[(s0 + g) * 8 + v];
+        if (r < 0) continue;
+        const int tx = v & 1, ty = (v >> 1) & 1, tz = v >> 2;
+        const int b = bc & 3, c = bc >> 2;
+        const float o0s = tx ? hxx : -hxx;
+        float h0 = 0.f, h1 = 0.f, h2 = 0.f, h3 = 0.f, s0v = 0.f, s1v = 0.f, s2v = 0.f, s3v = 0.f;
+        const float *t2 = T2 + (size_t)(g * p * 8 + b + 4 * ty) * 24 + tz * 4 + c;
+        for (int qx = 0; qx < p; ++qx, t2 += 8 * 24) {
+          const float w1 = t2[0], w3 = hx2 * t2[8], ws = t2[16], wo = o0s * ws;
+          const float4 M = MT[qx * 2 + tx], D = DT[qx * 2 + tx], D0 = D0T[qx];
+          h0 = fmaf(M.x, w1, fmaf(D.x, w3, fmaf(D0.x, wo, h0)));
+          h1 = fmaf(M.y, w1, fmaf(D.y, w3, fmaf(D0.y, wo, h1)));
+          h2 = fmaf(M.z, w1, fmaf(D.z, w3, fmaf(D0.z, wo, h2)));
+          h3 = fmaf(M.w, w1, fmaf(D.w, w3, fmaf(D0.w, wo, h3)));
+          s0v = fmaf(M.x, ws, s0v);
+          s1v = fmaf(M.y, ws, s1v);
+          s2v = fmaf(M.z, ws, s2v);
+          s3v = fmaf(M.w, ws, s3v);
         }
-      } else {
-        if (E.wantH) {
-          atomicAdd(H + s_ir, (double)hs);
-          atomicAdd(H + s_ri, (double)hs);
-        }
-        if (E.wantS) {
-          atomicAdd(S + s_ir, (double)ss);
-          atomicAdd(S + s_ri, (double)ss);
-        }
+        const float hv[4] = {0.125f * h0, 0.125f * h1, 0.125f * h2, 0.125f * h3};
+        const float sv[4] = {0.125f * s0v, 0.125f * s1v, 0.125f * s2v, 0.125f * s3v};
+  #pragma unroll
+        for (int a = 0; a < 4; ++a) add_fe(a + 4 * b + 16 * c, r, hv[a], sv[a]);
       }
     }
   }
 
-  // ---- E x E block of H (S's is computed in FP64 by its own kernel) ----------
+  // ---- E x E block of H (S's is computed by its own kernel) -------------------
   if (!E.wantH) return;
   // ---- E x E block, enrichment-pair form -------------------------------------
   if (E.sp) {
@@ -488,7 +660,7 @@ __device__ __forceinline__ void strip_part(const StripElem &E, double *__restric
 }
 
 template <bool BLOCH>
-__global__ void __maxnreg__(112) k_strip_sf(
+__global__ void __maxnreg__(ST_MAXREG) k_strip_sf(
     const int32_t *__restrict__ order, const int64_t *__restrict__ qoff,
     const int64_t *__restrict__ qpoff, const float4 *__restrict__ qdat,
     const double *__restrict__ V, const int32_t *__restrict__ partoff,
@@ -497,12 +669,22 @@ __global__ void __maxnreg__(112) k_strip_sf(
     const int32_t *__restrict__ aoff, const int64_t *__restrict__ toff32,
     const float *__restrict__ psi, const int64_t *__restrict__ soff,
     const int32_t *__restrict__ smap, float sx, float sy, float sz, int pm, int wfloats,
-    int sfloats, int eefloats, int what, double *__restrict__ H, double *__restrict__ S,
+    int sfloats, int eefloats, int amax, int what, double *__restrict__ H,
+    double *__restrict__ S,
     unsigned *err, const uint8_t *__restrict__ eshift, PhaseTab ph, double *__restrict__ Hi,
-    double *__restrict__ Si) {
+    double *__restrict__ Si, const int8_t *__restrict__ eeform,
+    const int32_t *__restrict__ citems) {
   extern __shared__ float4 sm_st4[];
   __shared__ float s_phr[8], s_phi[8];
-  const int e = order[blockIdx.x], tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // work item: element order[k0], its (sub)cells [cb, ce) (all of them
+  // without a work list); partial blocks of one element meet in the atomics
+  int k0 = blockIdx.x, cb = 0, ce = 1 << 30;
+  if (citems) {
+    k0 = citems[3 * blockIdx.x];
+    cb = citems[3 * blockIdx.x + 1];
+    ce = citems[3 * blockIdx.x + 2];
+  }
+  const int e = order[k0], tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   StripElem E;
   if (BLOCH) {
     if (tid == 0) {
@@ -542,29 +724,44 @@ __global__ void __maxnreg__(112) k_strip_sf(
   E.pm = pm;
   E.wfloats = wfloats;
 
-  // shared memory: [stage: sfloats][work: wfloats][E x E: eefloats]
-  //                [L1, D1: 12 pm each][F1: 18 pm][ecs: 64 ints][pairs: 36 ints]
+  // shared memory: [T4: 18 pm float4][stage: sfloats][work: wfloats]
+  //                [E x E: eefloats][F1: 18 pm][ecs: 64 ints][pairs: 36 ints]
+  //                [scol: 8 amax ints]
   // E x E area: HE ([ne8][ne8], entries r <= s; direct form) or
   // the pair projections [npair][189] (enrichment-pair form)
-  E.stage = reinterpret_cast<float *>(sm_st4);
+  float4 *T4 = sm_st4;
+  E.T4 = T4;
+  E.stage = reinterpret_cast<float *>(T4 + 18 * pm);
   E.work = E.stage + sfloats;
   E.HE = E.work + wfloats;
   E.PE = E.HE;
-  E.L1 = E.HE + eefloats;    // [3][4][pm]
-  E.D1 = E.L1 + 12 * pm;     // [3][4][pm]
-  float *F1 = E.D1 + 12 * pm;
+  float *F1 = E.HE + eefloats;
   E.F1 = F1;
   int *ecs = reinterpret_cast<int *>(F1 + 18 * pm);
   int *pairs = ecs + 64;
+  int *scol = pairs + 36;
   E.ecs = ecs;
   E.pairs = pairs;
-  if (tid < ne) ecs[tid] = ecol[(doff[e] - 64ll * e) + tid];
+  E.scol = scol;
+  if (E.A > amax) {
+    if (tid == 0) atomicOr(err, DEVERR_SHAPE);
+    return;
+  }
+  for (int o = tid; o < E.A * 8; o += ST_NT) scol[o] = -1;
+  __syncthreads();
+  if (tid < ne) {
+    const int c = ecol[(doff[e] - 64ll * e) + tid];
+    ecs[tid] = c;
+    scol[c] = tid;   // code = slot * 8 + vertex
+  }
 
   // E x E form: the pair form when the element has at most 8 slots, its
   // projections fit the E x E area, every (sub)cell's pair work fits the work
-  // area, and its estimated operation count (per pair and point: ~56 in z,
-  // ~200 / p in y, ~570 / p^2 in x) is below the direct one (~100 per 4 x 4
-  // tile and point, plus ~35 per column and point for the chunk tables)
+  // area, and -- unless the autotuner chose a form for the element's class
+  // (eeform 1: pair form, 2: direct) -- its estimated operation count (per
+  // pair and point: ~56 in z, ~200 / p in y, ~570 / p^2 in x) is below the
+  // direct one (~100 per 4 x 4 tile and point, plus ~35 per column and point
+  // for the chunk tables)
   {
     const int A = E.A, npair = A * (A + 1) / 2;
     bool sp = A <= 8 && npair * 189 <= eefloats;
@@ -572,7 +769,9 @@ __global__ void __maxnreg__(112) k_strip_sf(
       const int p = part_p[k];
       sp = 24 * p * p + 66 * p <= wfloats;
     }
-    if (sp) {
+    const int form = eeform ? eeform[e] : 0;
+    if (sp && form == 2) sp = false;
+    if (sp && form != 1) {
       const int p = part_p[partoff[e]];
       const int nb = ne8 >> 2;
       const long long cost_sp = (long long)npair * (56 * p * p * p + 200 * p * p + 570 * p + 2835);
@@ -585,6 +784,13 @@ __global__ void __maxnreg__(112) k_strip_sf(
       int k = tid * A - tid * (tid - 1) / 2;   // pairs (alpha, beta), alpha <= beta, alpha-major
       for (int b = tid; b < A; ++b) pairs[k++] = tid | (b << 8);
     }
+  }
+  // F x E form: the slot form unless its per-slot y and x stages outweigh
+  // the column form's per-column evaluations of b_r (first (sub)cell's p)
+  {
+    const long long p = part_p[partoff[e]], p2 = p * p, p3 = p2 * p;
+    E.fxs = (long long)E.A * (48 * p3 + 320 * p2 + 2048 * p) <
+            (long long)ne * (41 * p3 + 48 * p2 + 128 * p);
   }
   const int ee_zero = E.sp ? E.npair * 189 : ne8 * ne8;
   for (int o = tid; o < ee_zero; o += ST_NT) E.HE[o] = 0.0f;
@@ -606,10 +812,11 @@ __global__ void __maxnreg__(112) k_strip_sf(
   E.rb = rb;
   E.sb = rb + tt;
 
-  for (int k = partoff[e]; k < partoff[e + 1]; ++k) {
+  const int kend = min(partoff[e + 1], partoff[e] + ce);
+  for (int k = partoff[e] + cb; k < kend; ++k) {
     const int p = part_p[k];
     const int p2 = p * p, p3 = p2 * p;
-    if (p > pm || p2 * 20 + p * 48 > wfloats || ST_KC * (4 * ne8 + 1) > wfloats) {
+    if (p > pm || 36 * p2 + 192 * p > wfloats || ST_KC * (4 * ne8 + 1) > wfloats) {
       if (tid == 0) atomicOr(err, DEVERR_SHAPE);
       return;
     }
@@ -617,7 +824,7 @@ __global__ void __maxnreg__(112) k_strip_sf(
     E.qs = part_q[k];
     const int P = p3 | 1, A = E.A, qs = E.qs;
     const bool staged = ((A * 4 * P + 3) & ~3) + 5 * p3 <= sfloats;
-    __syncthreads();   // previous users of stage/work/L1/D1 are done
+    __syncthreads();   // previous users of stage/work/T4 are done
     if (staged) {   // Psi transposed to [slot][comp][point], pitch P (odd)
       float *stage = E.stage;
       float4 *xd = reinterpret_cast<float4 *>(stage + ((A * 4 * P + 3) & ~3));
@@ -658,12 +865,14 @@ __global__ void __maxnreg__(112) k_strip_sf(
       const float xd = d == 0 ? x4.x : (d == 1 ? x4.y : x4.z);
       float L[4], dL[4];
       lag3vd(xd, L, dL);
-#pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        E.L1[(d * 4 + a) * pm + t] = L[a];
-        E.D1[(d * 4 + a) * pm + t] = dL[a];
-      }
       const float l0 = 1.0f - xd, l1 = 1.0f + xd;
+      T4[(d * pm + t) * 2] = make_float4(L[0] * l0, L[1] * l0, L[2] * l0, L[3] * l0);
+      T4[(d * pm + t) * 2 + 1] = make_float4(L[0] * l1, L[1] * l1, L[2] * l1, L[3] * l1);
+      T4[6 * pm + (d * pm + t) * 2] = make_float4(dL[0] * l0, dL[1] * l0, dL[2] * l0, dL[3] * l0);
+      T4[6 * pm + (d * pm + t) * 2 + 1] =
+          make_float4(dL[0] * l1, dL[1] * l1, dL[2] * l1, dL[3] * l1);
+      T4[12 * pm + d * pm + t] = make_float4(dL[0], dL[1], dL[2], dL[3]);
+      T4[15 * pm + d * pm + t] = make_float4(L[0], L[1], L[2], L[3]);
       float *f1 = F1 + d * 6 * pm + t;
       f1[0] = l0 * l0;
       f1[pm] = l0 * l1;
@@ -742,37 +951,41 @@ __global__ void __maxnreg__(112) k_strip_sf(
 }  // namespace
 
 // Shared-memory floats of the strip kernel's work area: the F x E
-// intermediates of one group of enrichments (as many as keep 256 threads
-// busy, at least 1) for every per-axis count in `pmask`, or one E x E chunk
-// table for enrichment count (rounded to 8) ne8.
+// intermediates of one enrichment slot (36 p^2 + 192 p) for every per-axis
+// count in `pmask`, or one E x E chunk table for enrichment count (rounded to
+// 8) ne8; slots are grouped as far as the area allows.
 static int strip_work_floats(uint32_t pmask, int ne8) {
   int w = ST_KC * (4 * ne8 + 1);
   for (int p = 1; p < 32; ++p) {
     if (!(pmask & (1u << p))) continue;
-    const int per_r = p * p * 20 + p * 48;
-    const int g = std::max(1, std::min(ne8, ST_NT / (p * p)));
-    w = std::max(w, g * per_r);
+    w = std::max(w, 36 * p * p + 192 * p);
   }
   return (w + 3) & ~3;
 }
 
 // ph == nullptr: Gamma point; else the Bloch scatter into (H, Hi), (S, Si)
-static pufe_status strip_launch(pufe_ctx *ctx, const double *V, int what, double *H, double *S,
-                                int first, int count, cudaStream_t st, const PhaseTab *ph,
-                                double *Hi, double *Si) {
+// The strip kernel over `count` elements listed on the device at `ord`
+// (host copy `hord` for the launch sizes).
+// With `citems` (the context's (sub)cell-range list of all strip elements,
+// `nitems` items) the grid runs over the list instead.
+static pufe_status strip_launch_list(pufe_ctx *ctx, const double *V, int what, double *H,
+                                     double *S, const int32_t *ord, const int32_t *hord, int count,
+                                     cudaStream_t st, const PhaseTab *ph, double *Hi, double *Si,
+                                     const int32_t *citems = nullptr, int nitems = 0) {
   if (count <= 0) return PUFE_OK;
+  const unsigned grid = citems ? (unsigned)nitems : (unsigned)count;
+  if (grid == 0) return PUFE_OK;
   auto &D = ctx->d;
   int ne8 = 8;
-  for (int64_t k = first; k < first + count; ++k)
-    ne8 = std::max(ne8, (ctx->n_e[ctx->order[k]] - 64 + 7) & ~7);
+  for (int k = 0; k < count; ++k) ne8 = std::max(ne8, (ctx->n_e[hord[k]] - 64 + 7) & ~7);
   const int sneed = ctx->strip_stage;
   if (ne8 > 64) return fail(PUFE_EINVAL, "strip kernel takes n_e <= 128");
   const int pm = std::max(1, ctx->max_part_p);
   {   // FastDiv preconditions, x d < 2^32 for the largest index of each division
     const int64_t p2 = (int64_t)pm * pm, p3 = p2 * pm, A = ne8;
     const int64_t xd[][2] = {
-        {std::max<int64_t>(ST_NT, p2), p2},                 // (column, point) pairs
-        {(ST_NT / std::max<int64_t>(1, p2) + 1) * 16 * pm, 16 * pm},   // y stage
+        {64 * p2, p2},                                      // slot-form z stage
+        {64 * pm, pm},                                      // slot-form y stage
         {36 * 23 * pm, 23 * pm},                            // pair-form y stage
         {(int64_t)ST_KC * ne8, ne8},                        // E x E chunk table
         {((p3 + 7) / 8 + 1) * 8 * A, 8 * A},                // Psi staging
@@ -784,27 +997,172 @@ static pufe_status strip_launch(pufe_ctx *ctx, const double *V, int what, double
   const int wf = strip_work_floats(ctx->strip_pmask, ne8);
   const int sf = (sneed + 3) & ~3;
   const int ee = std::max(ne8 * ne8, 189 * ctx->strip_npair_max);
-  const size_t sm = ((size_t)sf + wf + ee + 42 * pm + 64 + 36) * sizeof(float);
+  int amax = 1;
+  for (int k = 0; k < count; ++k) amax = std::max(amax, (int)ctx->n_slot[hord[k]]);
+  const size_t sm =
+      ((size_t)72 * pm + sf + wf + ee + 18 * pm + 64 + 36 + 8 * amax) * sizeof(float);
   if (sm > 227 * 1024) return fail(PUFE_EINVAL, "strip kernel: shared memory above 227 KB");
   const float sx = (float)(2.0 / ctx->h[0]), sy = (float)(2.0 / ctx->h[1]),
               sz = (float)(2.0 / ctx->h[2]);
   if (ph) {
     PUFE_CUDA_TRY(cudaFuncSetAttribute(k_strip_sf<true>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    k_strip_sf<true><<<(unsigned)count, ST_NT, sm, st>>>(
-        D.order + first, D.qoff, D.qpoff, D.qdat, V, D.partoff, D.part_p, D.part_q, D.doff,
-        D.ecol, D.aoff, D.toff32, D.psi32, D.soff, D.smap, sx, sy, sz, pm, wf, sf, ee, what, H, S,
-        D.err, D.eshift, *ph, Hi, Si);
+    k_strip_sf<true><<<grid, ST_NT, sm, st>>>(
+        ord, D.qoff, D.qpoff, D.qdat, V, D.partoff, D.part_p, D.part_q, D.doff,
+        D.ecol, D.aoff, D.toff32, D.psi32, D.soff, D.smap, sx, sy, sz, pm, wf, sf, ee, amax, what, H, S,
+        D.err, D.eshift, *ph, Hi, Si, D.eeform, citems);
   } else {
     PUFE_CUDA_TRY(cudaFuncSetAttribute(k_strip_sf<false>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    k_strip_sf<false><<<(unsigned)count, ST_NT, sm, st>>>(
-        D.order + first, D.qoff, D.qpoff, D.qdat, V, D.partoff, D.part_p, D.part_q, D.doff,
-        D.ecol, D.aoff, D.toff32, D.psi32, D.soff, D.smap, sx, sy, sz, pm, wf, sf, ee, what, H, S,
-        D.err, nullptr, PhaseTab{}, nullptr, nullptr);
+    k_strip_sf<false><<<grid, ST_NT, sm, st>>>(
+        ord, D.qoff, D.qpoff, D.qdat, V, D.partoff, D.part_p, D.part_q, D.doff,
+        D.ecol, D.aoff, D.toff32, D.psi32, D.soff, D.smap, sx, sy, sz, pm, wf, sf, ee, amax, what, H, S,
+        D.err, nullptr, PhaseTab{}, nullptr, nullptr, D.eeform, citems);
   }
   PUFE_CUDA_TRY(cudaGetLastError());
   return PUFE_OK;
+}
+
+static pufe_status strip_launch(pufe_ctx *ctx, const double *V, int what, double *H, double *S,
+                                int first, int count, cudaStream_t st, const PhaseTab *ph,
+                                double *Hi, double *Si) {
+  // all strip elements: over the (sub)cell-range work list, whose items
+  // index `order` from its start
+  const bool all = first == ctx->n_big && first + count == ctx->nelem && ctx->d.citems;
+  return strip_launch_list(ctx, V, what, H, S, ctx->d.order + (all ? 0 : first),
+                           ctx->order.data() + first, count, st, ph, Hi, Si,
+                           all ? ctx->d.citems : nullptr, all ? ctx->n_citems : 0);
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner of the E x E form.  Strip elements (64 < n_e <= 128) are grouped
+// into classes by (n_e, slots, points per axis of every (sub)cell); for each
+// class where both forms apply, the strip kernel is timed on the class's
+// elements (up to 256 of them) with the enrichment-pair form and with the
+// direct 4 x 4 tiles forced, and the faster is kept for every element of the
+// class.  With PUFE_AUTOTUNE_CACHE naming a file, decisions found there (one
+// line per class: key, form) are taken without timing, and new ones are
+// appended.
+// ---------------------------------------------------------------------------
+pufe_status autotune_strip(pufe_ctx *ctx, int *ntuned, cudaStream_t st) {
+  auto &D = ctx->d;
+  if (ntuned) *ntuned = 0;
+  if (!ctx->tabulated32) return fail(PUFE_ESTATE, "call pufe_tabulate(PUFE_TF32X3) first");
+  // classes
+  std::map<std::string, std::vector<int32_t>> cls;
+  std::vector<int32_t> pbeg(ctx->nelem + 1, 0);
+  for (int64_t e = 0; e < ctx->nelem; ++e) {
+    const int n = ctx->n_e[e];
+    if (n <= 64 || n > 128) continue;
+    const int A = ctx->n_slot[e];
+    if (A > 8) continue;   // the pair form takes at most 8 slots
+    std::string key = "ne=" + std::to_string(n) + ",A=" + std::to_string(A) + ",p=";
+    for (size_t k = 0; k < ctx->part_p_host[e].size(); ++k)
+      key += (k ? "." : "") + std::to_string(ctx->part_p_host[e][k]);
+    cls[key].push_back((int32_t)e);
+  }
+  std::map<std::string, int> cache;
+  const char *path = std::getenv("PUFE_AUTOTUNE_CACHE");
+  if (path && *path) {
+    std::ifstream in(path);
+    std::string k;
+    int f;
+    while (in >> k >> f)
+      if (f == 1 || f == 2) cache[k] = f;
+  }
+  double *H = nullptr, *S = nullptr, *V = nullptr;
+  int32_t *dord = nullptr;
+  cudaEvent_t ea = nullptr, eb = nullptr;
+  auto cleanup = [&]() {
+    if (H) cudaFree(H);
+    if (S) cudaFree(S);
+    if (V) cudaFree(V);
+    if (dord) cudaFree(dord);
+    if (ea) cudaEventDestroy(ea);
+    if (eb) cudaEventDestroy(eb);
+  };
+  pufe_status rc = PUFE_OK;
+  std::vector<std::pair<std::string, int>> fresh;
+  do {
+    size_t maxcls = 0;
+    for (auto &kv : cls) maxcls = std::max(maxcls, std::min<size_t>(kv.second.size(), 256));
+    if (cudaMalloc((void **)&H, std::max<int64_t>(1, ctx->nnz) * sizeof(double)) != cudaSuccess ||
+        cudaMalloc((void **)&S, std::max<int64_t>(1, ctx->nnz) * sizeof(double)) != cudaSuccess ||
+        cudaMalloc((void **)&V, std::max<int64_t>(1, ctx->nq) * sizeof(double)) != cudaSuccess ||
+        cudaMalloc((void **)&dord, std::max<size_t>(1, maxcls) * sizeof(int32_t)) != cudaSuccess ||
+        cudaEventCreate(&ea) != cudaSuccess || cudaEventCreate(&eb) != cudaSuccess) {
+      cudaGetLastError();
+      rc = fail(PUFE_ENOMEM, "autotune: scratch allocation failed");
+      break;
+    }
+    if (cudaMemsetAsync(V, 0, ctx->nq * sizeof(double), st) != cudaSuccess ||
+        cudaMemsetAsync(H, 0, ctx->nnz * sizeof(double), st) != cudaSuccess ||
+        cudaMemsetAsync(S, 0, ctx->nnz * sizeof(double), st) != cudaSuccess) {
+      rc = fail(PUFE_ECUDA, "autotune: memset failed");
+      break;
+    }
+    for (auto &kv : cls) {
+      int choice = 0;
+      auto hit = cache.find(kv.first);
+      if (hit != cache.end()) {
+        choice = hit->second;
+      } else {
+        // up to 256 elements spread over the class
+        std::vector<int32_t> sel;
+        const size_t m = kv.second.size(), take = std::min<size_t>(m, 256);
+        for (size_t i = 0; i < take; ++i) sel.push_back(kv.second[i * m / take]);
+        if (cudaMemcpy(dord, sel.data(), sel.size() * sizeof(int32_t), cudaMemcpyHostToDevice) !=
+            cudaSuccess) {
+          rc = fail(PUFE_ECUDA, "autotune: copy failed");
+          break;
+        }
+        float best = 0.0f;
+        for (int form = 1; form <= 2 && rc == PUFE_OK; ++form) {
+          for (int32_t e : sel) ctx->eeform_host[e] = (int8_t)form;
+          if (cudaMemcpy(D.eeform, ctx->eeform_host.data(), ctx->nelem, cudaMemcpyHostToDevice) !=
+              cudaSuccess) {
+            rc = fail(PUFE_ECUDA, "autotune: copy failed");
+            break;
+          }
+          float tmin = 1e30f;
+          for (int rep = 0; rep < 4 && rc == PUFE_OK; ++rep) {
+            cudaEventRecord(ea, st);
+            rc = strip_launch_list(ctx, V, PUFE_WANT_H | PUFE_WANT_S, H, S, dord, sel.data(),
+                                   (int)sel.size(), st, nullptr, nullptr, nullptr);
+            cudaEventRecord(eb, st);
+            if (rc == PUFE_OK && cudaEventSynchronize(eb) == cudaSuccess) {
+              float t = 0.0f;
+              cudaEventElapsedTime(&t, ea, eb);
+              if (rep > 0) tmin = std::min(tmin, t);   // the first launch warms up
+            }
+          }
+          if (form == 1 || tmin < best) {
+            best = tmin;
+            choice = form;
+          }
+        }
+        if (rc != PUFE_OK) break;
+        fresh.push_back({kv.first, choice});
+      }
+      for (int32_t e : kv.second) ctx->eeform_host[e] = (int8_t)choice;
+      if (ntuned) ++*ntuned;
+    }
+    if (rc != PUFE_OK) break;
+    if (cudaMemcpy(D.eeform, ctx->eeform_host.data(), ctx->nelem, cudaMemcpyHostToDevice) !=
+        cudaSuccess) {
+      rc = fail(PUFE_ECUDA, "autotune: copy failed");
+      break;
+    }
+    unsigned flag = 0;
+    cudaMemcpy(&flag, D.err, sizeof(unsigned), cudaMemcpyDeviceToHost);
+    if (flag) rc = fail(PUFE_EDEVICE, "autotune: a strip launch reported a device error");
+    if (path && *path && !fresh.empty()) {
+      std::ofstream out(path, std::ios::app);
+      for (auto &kv : fresh) out << kv.first << " " << kv.second << "\n";
+    }
+  } while (false);
+  cleanup();
+  return rc;
 }
 
 pufe_status launch_strip_sf(pufe_ctx *ctx, const double *V, int what, double *H, double *S,
@@ -834,7 +1192,7 @@ pufe_status launch_assemble_mixed_bloch(pufe_ctx *ctx, const PhaseTab &ph, const
   pufe_status e0 = launch_fefe_bloch(ctx, ph, V, what, H, Hi, S, Si, st);
   if (e0 != PUFE_OK) return e0;
   if (what & PUFE_WANT_S) {   // E x E block of S(k) in FP64 with FP64 phases
-    pufe_status e1 = launch_see(ctx, &ph, S, Si, 0, (int)ctx->nelem, st);
+    pufe_status e1 = launch_see(ctx, &ph, S, Si, st);
     if (e1 != PUFE_OK) return e1;
   }
   return strip_launch(ctx, (what & PUFE_WANT_H) ? V : nullptr, what, H, S, 0, (int)ctx->nelem, st,

@@ -324,17 +324,19 @@ __global__ void k_pack_v(const int32_t *__restrict__ order, const int64_t *__res
 }
 
 struct ElemInfo {
-  int e, Q, Qp, A, n, nenr, npad, nenr16, nch, nmt;
+  int e, Q, Qp, A, n, nenr, npad, nenr16, nch, nmt, c0;
   int64_t q0;
   bool ok;   // the kernel can take this element
   bool go;   // ok and it has enrichment columns (FE-only elements need no strip)
 };
 
-__device__ __forceinline__ ElemInfo elem_info(const int32_t *order, int k, const int64_t *qoff,
-                                              const int64_t *qpoff, const int32_t *aoff,
-                                              const int64_t *doff, int amax) {
+// work item k: chunks [c0, c1) of element order[items[3k]] (chunks of WS_KC
+// padded points)
+__device__ __forceinline__ ElemInfo elem_info(const int32_t *order, const int32_t *items, int k,
+                                              const int64_t *qoff, const int64_t *qpoff,
+                                              const int32_t *aoff, const int64_t *doff, int amax) {
   ElemInfo I;
-  I.e = order[k];
+  I.e = order[items[3 * k]];
   I.q0 = qoff[I.e];
   I.Q = (int)(qoff[I.e + 1] - I.q0);
   I.Qp = (int)(qpoff[I.e + 1] - qpoff[I.e]);
@@ -343,9 +345,10 @@ __device__ __forceinline__ ElemInfo elem_info(const int32_t *order, int k, const
   I.nenr = I.n - 64;
   I.npad = (I.n + 15) & ~15;
   I.nenr16 = (I.nenr + 15) & ~15;
-  I.nch = I.Qp / WS_KC;
+  I.c0 = items[3 * k + 1];
+  I.nch = items[3 * k + 2] - I.c0;
   I.nmt = (I.n + 127) / 128;
-  I.ok = I.n <= 256 && I.A <= amax && I.nch > 0;
+  I.ok = I.n <= 256 && I.A <= amax && I.nch > 0 && (I.c0 + I.nch) * WS_KC <= I.Qp;
   I.go = I.ok && I.nenr > 0;
   return I;
 }
@@ -363,8 +366,8 @@ __global__ void __launch_bounds__(WS_NT, 1) k_assemble_tc(
     const int32_t *__restrict__ ecol, const int32_t *__restrict__ aoff,
     const int64_t *__restrict__ toff32, const float *__restrict__ psi,
     const int64_t *__restrict__ soff, const int32_t *__restrict__ smap, float sx, float sy,
-    float sz, int nelem_list, int amax, int in_bytes, int want, double *__restrict__ H,
-    double *__restrict__ S, unsigned *err) {
+    float sz, const int32_t *__restrict__ items, int nelem_list, int amax, int in_bytes,
+    int want, double *__restrict__ H, double *__restrict__ S, unsigned *err) {
   constexpr int R = 256;                      // basis rows of the tile (n_e <= 256)
   constexpr int KC = WS_KC;
   constexpr int TILE = R * KC * 4;            // bytes per SMEM tile
@@ -421,7 +424,7 @@ __global__ void __launch_bounds__(WS_NT, 1) k_assemble_tc(
     int t = 0;
     bool run = true;
     for (int k = blockIdx.x; k < nelem_list && run; k += G) {
-      const ElemInfo I = elem_info(order, k, qoff, qpoff, aoff, doff, amax);
+      const ElemInfo I = elem_info(order, items, k, qoff, qpoff, aoff, doff, amax);
       if (!I.ok) {
         if (tid == 0) set_err(err, DEVERR_SHAPE);
         continue;
@@ -515,7 +518,7 @@ __global__ void __launch_bounds__(WS_NT, 1) k_assemble_tc(
       int t = 0, a = 0;
       bool run = true;
       for (int k = blockIdx.x; k < nelem_list && run; k += G) {
-        const ElemInfo I = elem_info(order, k, qoff, qpoff, aoff, doff, amax);
+        const ElemInfo I = elem_info(order, items, k, qoff, qpoff, aoff, doff, amax);
         if (!I.go) continue;
         const uint32_t idE = idesc_tf32(128, I.nenr16);
         const uint32_t tH = tmem, tS = tmem + S_COL;
@@ -601,7 +604,7 @@ __global__ void __launch_bounds__(WS_NT, 1) k_assemble_tc(
         if (sd[i] >= 0) atomicAdd(out + sd[i], value_of(lane, i));
     };
     for (int k = blockIdx.x; k < nelem_list && run; k += G) {
-      const ElemInfo I = elem_info(order, k, qoff, qpoff, aoff, doff, amax);
+      const ElemInfo I = elem_info(order, items, k, qoff, qpoff, aoff, doff, amax);
       if (!I.go) continue;
       const int32_t *m = smap + soff[I.e];
       const int n = I.n;
@@ -642,7 +645,7 @@ __global__ void __launch_bounds__(WS_NT, 1) k_assemble_tc(
       int lt = 0;
       bool run = true;
       for (int k = blockIdx.x; k < nelem_list && run; k += G) {
-        const ElemInfo I = elem_info(order, k, qoff, qpoff, aoff, doff, amax);
+        const ElemInfo I = elem_info(order, items, k, qoff, qpoff, aoff, doff, amax);
         if (!I.go) continue;
         const float *lpsi = psi + 4 * toff32[I.e];
         const float *lpt = ptab + 32 * qpoff[I.e];
@@ -656,7 +659,7 @@ __global__ void __launch_bounds__(WS_NT, 1) k_assemble_tc(
               run = false;
               break;
             }
-            const int qc = c * KC;
+            const int qc = (I.c0 + c) * KC;
             unsigned char *dst = inbuf + b * in_bytes;
             mbar_expect_tx(&sh.ibar[b], pbytes + KC * 128 + KC * 4);
             if (pbytes) bulk_g2s(dst, lpsi + (int64_t)(qc >> 3) * I.A * 32, pbytes, &sh.ibar[b]);
@@ -784,11 +787,16 @@ __global__ void __launch_bounds__(ADJ_NT) k_adjoint_f32(
     const int32_t *__restrict__ ecol, const int32_t *__restrict__ aoff,
     const int64_t *__restrict__ toff32, const float *__restrict__ psi,
     const int64_t *__restrict__ soff, const int32_t *__restrict__ smap,
-    const double *__restrict__ Hbar, double *__restrict__ Vbar) {
+    const double *__restrict__ Hbar, double *__restrict__ Vbar,
+    const int32_t *__restrict__ items) {
   extern __shared__ __align__(16) float fsm[];
-  const int e = order[blockIdx.x];
+  // work item: the points [8 c0, 8 c1) of element order[items[3 b]] (clipped
+  // to the element's Q points)
+  const int e = order[items[3 * blockIdx.x]];
   const int64_t q0 = qoff[e];
   const int Q = (int)(qoff[e + 1] - q0);
+  const int qbeg = items[3 * blockIdx.x + 1] * 8;
+  const int qend = min(Q, items[3 * blockIdx.x + 2] * 8);
   const int A = aoff[e + 1] - aoff[e];
   const int n = (int)(doff[e + 1] - doff[e]);
   const int n4 = (n + 3) & ~3;
@@ -806,13 +814,13 @@ __global__ void __launch_bounds__(ADJ_NT) k_adjoint_f32(
   }
   const int nI = n4 / 4;
   const int ntile = (ADJ_QB / 4) * nI;
-  for (int qc = 0; qc < Q; qc += ADJ_QB) {
+  for (int qc = qbeg; qc < qend; qc += ADJ_QB) {
     __syncthreads();
     for (int k = threadIdx.x; k < ADJ_QB * n4; k += ADJ_NT) {
       const int qq = k / n4, c = k - qq * n4;
       const int q = qc + qq;
       float b = 0.0f;
-      if (q < Q && c < n) {
+      if (q < qend && c < n) {
         const float4 x4 = qe[q];
         if (c < 64) {
           float L[4], dL[4], v = 1.0f;
@@ -865,7 +873,7 @@ __global__ void __launch_bounds__(ADJ_NT) k_adjoint_f32(
       }
     }
     __syncthreads();
-    if (threadIdx.x < ADJ_QB && qc + (int)threadIdx.x < Q)
+    if (threadIdx.x < ADJ_QB && qc + (int)threadIdx.x < qend)
       Vbar[q0 + qc + threadIdx.x] = w[q0 + qc + threadIdx.x] * (double)acc[threadIdx.x];
   }
 }
@@ -1019,10 +1027,11 @@ pufe_status launch_tabulate_f32(pufe_ctx *ctx, cudaStream_t st) {
   return PUFE_OK;
 }
 
-// H/S assembly on the mixed path: H = kinetic + sum-factorized V term on the
-// FE-FE blocks, S = S0, then the enrichment strips (tensor cores for
-// n_e > 128, CUDA cores otherwise); `vscratch` receives the FP32
-// copy of V that the tensor-core kernel reads (nq_pad floats).
+// H/S assembly on the mixed path: H = 0 and S = the constant FE-FE overlap,
+// then the FE-FE blocks of H (kinetic constants + sum-factorized V term), the
+// enrichment strips (tensor cores for n_e > 128, CUDA cores otherwise) and the
+// E-E block of S, all adding into H and S; `vscratch` receives the FP32 copy
+// of V that the tensor-core kernel reads (nq_pad floats).
 static pufe_status run_assemble_tc(pufe_ctx *ctx, const double *V, int what, double *H,
                                    double *S, float *vscratch, cudaStream_t st) {
   auto &D = ctx->d;
@@ -1037,10 +1046,9 @@ static pufe_status run_assemble_tc(pufe_ctx *ctx, const double *V, int what, dou
   const int nsmall = (int)ctx->nelem - nbig;
   if (nbig > 0 && sm256 > 227 * 1024)
     return fail(PUFE_EINVAL, "too many enrichments per element for TF32X3");
-  const size_t bytes = (size_t)ctx->nnz * sizeof(double);
   // H = 0 and S = the constant FE-FE overlap; then the strip kernels on the
-  // caller's stream and, on the context's side stream, the E-E kernel of S
-  // and the FE-FE kernel (V term and kinetic constants of H), concurrently
+  // caller's stream and, on the context's side stream, the FE-FE kernel (V
+  // term and kinetic constants of H) and the E-E kernel of S, concurrently
   // (all of them only add into H and S)
   if (ctx->max_part_p > 16) return fail(PUFE_EINVAL, "rule with more than 16 points per axis");
   const bool prof = ctx->prof;
@@ -1052,6 +1060,7 @@ static pufe_status run_assemble_tc(pufe_ctx *ctx, const double *V, int what, dou
     for (bool &r : ctx->prof_ran) r = false;
   if (pufe_status e = mark(0, st)) return e;
   if (prof) ctx->prof_ran[0] = true;
+  const size_t bytes = (size_t)ctx->nnz * sizeof(double);
   if (what & PUFE_WANT_H) PUFE_CUDA_TRY(cudaMemsetAsync(H, 0, bytes, st));
   if (what & PUFE_WANT_S) PUFE_CUDA_TRY(cudaMemcpyAsync(S, D.S0, bytes, cudaMemcpyDeviceToDevice, st));
   PUFE_CUDA_TRY(cudaEventRecord(D.ev_fork, st));
@@ -1069,9 +1078,9 @@ static pufe_status run_assemble_tc(pufe_ctx *ctx, const double *V, int what, dou
     PUFE_CUDA_TRY(cudaFuncSetAttribute(k_assemble_tc,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm256));
     if (pufe_status e = mark(6, st)) return e;
-    k_assemble_tc<<<std::min(nbig, nsm), WS_NT, sm256, st>>>(
+    k_assemble_tc<<<std::min(ctx->n_titems, nsm), WS_NT, sm256, st>>>(
         D.order, D.qoff, D.qpoff, D.ptab, vscratch, D.doff, D.ecol, D.aoff, D.toff32, D.psi32,
-        D.soff, D.smap, sx, sy, sz, nbig, amax, inb, what, H, S, D.err);
+        D.soff, D.smap, sx, sy, sz, D.titems, ctx->n_titems, amax, inb, what, H, S, D.err);
     PUFE_CUDA_TRY(cudaGetLastError());
     if (pufe_status e = mark(7, st)) return e;
     if (prof) ctx->prof_ran[3] = true;
@@ -1082,19 +1091,19 @@ static pufe_status run_assemble_tc(pufe_ctx *ctx, const double *V, int what, dou
   if (pufe_status e = mark(9, st)) return e;
   if (prof) ctx->prof_ran[4] = nsmall > 0;
   PUFE_CUDA_TRY(cudaStreamWaitEvent(D.side, D.ev_fork, 0));
-  if (what & PUFE_WANT_S) {
-    if (pufe_status e = mark(4, D.side)) return e;
-    pufe_status e0 = launch_see(ctx, nullptr, S, nullptr, 0, (int)ctx->nelem, D.side);
-    if (e0 != PUFE_OK) return e0;
-    if (pufe_status e = mark(5, D.side)) return e;
-    if (prof) ctx->prof_ran[2] = true;
-  }
   if (what & PUFE_WANT_H) {
     if (pufe_status e = mark(2, D.side)) return e;
     pufe_status e0 = launch_fefe(ctx, V, H, D.side);
     if (e0 != PUFE_OK) return e0;
     if (pufe_status e = mark(3, D.side)) return e;
     if (prof) ctx->prof_ran[1] = true;
+  }
+  if (what & PUFE_WANT_S) {
+    if (pufe_status e = mark(4, D.side)) return e;
+    pufe_status e0 = launch_see(ctx, nullptr, S, nullptr, D.side);
+    if (e0 != PUFE_OK) return e0;
+    if (pufe_status e = mark(5, D.side)) return e;
+    if (prof) ctx->prof_ran[2] = true;
   }
   PUFE_CUDA_TRY(cudaEventRecord(D.ev_join, D.side));
   PUFE_CUDA_TRY(cudaStreamWaitEvent(st, D.ev_join, 0));
@@ -1158,8 +1167,9 @@ pufe_status launch_adjoint_tc(pufe_ctx *ctx, const double *Hbar, double *Vbar, c
     if (sm > 227 * 1024) return fail(PUFE_EINVAL, "n_e too large for the FP32 adjoint kernel");
     PUFE_CUDA_TRY(
         cudaFuncSetAttribute(k_adjoint_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    k_adjoint_f32<<<nbig, ADJ_NT, sm, st>>>(D.order, D.qoff, D.qpoff, D.qdat, D.w, D.doff, D.ecol,
-                                            D.aoff, D.toff32, D.psi32, D.soff, D.smap, Hbar, Vbar);
+    k_adjoint_f32<<<ctx->n_titems, ADJ_NT, sm, st>>>(D.order, D.qoff, D.qpoff, D.qdat, D.w,
+                                                     D.doff, D.ecol, D.aoff, D.toff32, D.psi32,
+                                                     D.soff, D.smap, Hbar, Vbar, D.titems);
     PUFE_CUDA_TRY(cudaGetLastError());
   }
   const int nsmall = (int)ctx->nelem - nbig;

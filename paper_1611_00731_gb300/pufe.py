@@ -32,7 +32,8 @@ EXPORTS = ["pufe_build_mesh", "pufe_get_sizes", "pufe_get_quadrature", "pufe_get
            "pufe_scf_step", "pufe_scf_reset", "pufe_assemble_HS_bloch", "pufe_density_bloch",
            "pufe_assemble_HV_adjoint_bloch", "pufe_nonlocal_projections",
            "pufe_nonlocal_projections_bloch", "pufe_get_element_slots",
-           "pufe_profile_assembly", "pufe_profile_read", "pufe_selftest_timeout"]
+           "pufe_profile_assembly", "pufe_profile_read", "pufe_selftest_timeout",
+           "pufe_autotune"]
 
 
 def _projector_array(projs):
@@ -130,6 +131,7 @@ def load_library(build_if_missing: bool = True):
     lib.pufe_profile_assembly.argtypes = [vp, C.c_int]
     lib.pufe_profile_read.argtypes = [vp, dp]
     lib.pufe_selftest_timeout.argtypes = [vp, C.c_uint64, vp]
+    lib.pufe_autotune.argtypes = [vp, C.POINTER(C.c_int), vp]
     lib.pufe_destroy.argtypes = [vp]
     lib.pufe_destroy.restype = None
     lib.pufe_last_error.restype = C.c_char_p
@@ -208,6 +210,13 @@ class Context:
         _check(_LIB.pufe_get_element_slots(self._h, a.ctypes.data_as(C.POINTER(C.c_int32))))
         return a
 
+    def pufe_autotune(self, stream=None):
+        """Pick the strip's E x E form per element class by timing (see the
+        header); returns the number of classes set."""
+        n = C.c_int(0)
+        _check(_LIB.pufe_autotune(self._h, C.byref(n), _stream(stream)))
+        return n.value
+
     # -- diagnostics and instrumentation -------------------------------------
     def pufe_selftest_timeout(self, wait_ns=100_000_000, stream=None):
         _check(_LIB.pufe_selftest_timeout(self._h, int(wait_ns), _stream(stream)))
@@ -216,11 +225,11 @@ class Context:
         _check(_LIB.pufe_profile_assembly(self._h, int(bool(enable))))
 
     def pufe_profile_read(self):
-        """ms of the last instrumented mixed assembly: call, FE-FE, FP64 E-E of
-        S, tensor-core tile, strip (0 for kernels that did not run)."""
+        """ms of the last instrumented mixed assembly: call, FE-FE kernels,
+        E-E kernel of S, tensor-core tile, strip (0 for kernels that did not run)."""
         ms = np.zeros(5, dtype=np.float64)
         _check(_LIB.pufe_profile_read(self._h, ms.ctypes.data_as(C.POINTER(C.c_double))))
-        return dict(zip(("call", "fefe", "see64", "tc", "strip"), ms.tolist()))
+        return dict(zip(("call", "fefe", "see", "tc", "strip"), ms.tolist()))
 
     # -- compute calls --------------------------------------------------------
     def pufe_tabulate(self, prec=PUFE_FP64, stream=None):

@@ -20,10 +20,13 @@ shift-invert Lanczos.  Against it:
   blocks of S are exact FP64 constants (1e-12); the E-E block of S is FP64
   arithmetic on the FP32-rounded enrichment values and points, whose own
   rounding dominates (5e-6, the FP32 input bound).
-* Eigenvalues of the 8 lowest states: the GPU pencils' eigenvalues by
-  Rayleigh-Ritz on the oracle's 12 lowest eigenvectors (exact to second
-  order in the difference of the pencils), FP64 within 1e-10 Ha, mixed within
-  the 1e-5 Ha target.
+* Eigenvalues of the 8 lowest states: Rayleigh-Ritz of the GPU pencil and of
+  the oracle's pencil on the same subspace (the oracle's 12 lowest
+  eigenvectors), so that the difference is the pencils' own (first order in
+  dH, dS) and not the Lanczos tolerance; FP64 within 1e-11 Ha, mixed within
+  the 1e-5 Ha target.  The oracle's Ritz values on that subspace agree with
+  its Lanczos eigenvalues to 1e-9 Ha (the Lanczos residual, which varies
+  with its random start vector: 6e-11 and 2e-10 Ha in two runs).
 * Density of the 8 states (f = 2, closed shells): FP64 1e-12, mixed 1e-5 of
   max n; sum_q w_q n_q = 16.
 """
@@ -125,9 +128,12 @@ def test_c2_mixed_matrices_per_block(c2):
 
 
 def test_c2_eigenvalues(c2):
-    wo = c2["wo"][:NSTATES]
+    wo = oeig.rayleigh_ritz(c2["Ho"], c2["So"], c2["Xo"])[:NSTATES]
+    lanczos = np.abs(wo - c2["wo"][:NSTATES]).max()
+    print(f"C2 oracle: Ritz values vs Lanczos eigenvalues {lanczos:.2e}")
+    assert lanczos < 1e-9
     res = {}
-    for prec, tol in ((pufe.PUFE_FP64, 1e-10), (pufe.PUFE_TF32X3, TOL_EIG_MIXED)):
+    for prec, tol in ((pufe.PUFE_FP64, 1e-11), (pufe.PUFE_TF32X3, TOL_EIG_MIXED)):
         Hg, Sg = c2["gpu"][prec]
         wg = oeig.rayleigh_ritz(Hg, Sg, c2["Xo"])[:NSTATES]
         res[prec] = np.abs(wg - wo)
@@ -140,7 +146,7 @@ def test_c2_density_of_lowest_states(c2):
     dev = torch.device("cuda:0")
     ro = c2["rho_o"]
     w = c2["rules"][1]
-    assert abs(w @ ro - 2.0 * NSTATES) < 1e-9
+    assert abs(w @ ro - 2.0 * NSTATES) < 1e-8   # ARPACK's S-normalisation of the states
     for prec, tol in ((pufe.PUFE_FP64, TOL64), (pufe.PUFE_TF32X3, 1e-5)):
         rho = torch.empty(ctx.n_q, dtype=torch.float64, device=dev)
         ctx.pufe_tabulate(prec)
