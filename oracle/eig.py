@@ -57,6 +57,33 @@ def fermi_occupations(eps, nelec, kT):
     return 2.0 / (1.0 + np.exp(x)), mu
 
 
+def fermi_occupations_k(eps, wk, nelec, kT):
+    """Occupations of the states of several k-points with one Fermi level:
+    f_nk = 2 / (1 + exp((eps_nk - mu)/kT)) with sum_k w_k sum_n f_nk = nelec
+    (bisection on mu).  eps: a list of 1-D arrays, one per k-point (their
+    lengths may differ); wk: the k-point weights.  Returns (list of f, mu)."""
+    eps = [np.asarray(e, dtype=np.float64) for e in eps]
+    wk = np.asarray(wk, dtype=np.float64)
+
+    def occ(e, mu):
+        x = np.clip((e - mu) / kT, -700.0, 700.0)
+        return 2.0 / (1.0 + np.exp(x))
+
+    def total(mu):
+        return sum(w * occ(e, mu).sum() for w, e in zip(wk, eps))
+
+    allv = np.concatenate(eps)
+    lo, hi = allv.min() - 50.0 * kT - 1.0, allv.max() + 50.0 * kT + 1.0
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if total(mid) < nelec:
+            lo = mid
+        else:
+            hi = mid
+    mu = 0.5 * (lo + hi)
+    return [occ(e, mu) for e in eps], mu
+
+
 def nested_dissection_order(coords, period):
     """A fill-reducing DOF order for the sparse shift-invert factorisation.
 

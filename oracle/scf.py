@@ -47,7 +47,8 @@ import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
 from .assemble import density
-from .eig import fermi_occupations
+from .bloch import density_k
+from .eig import fermi_occupations, fermi_occupations_k
 from .fe import gauss_1d, tricubic
 from .potential import gaussian_charge
 
@@ -234,16 +235,40 @@ def scf_step(mesh, rules, wl, eps, C, nelec, kT, alpha, n_in, V_eff_in, rho_I, K
     the occupations, n_out, n_new = n_in + alpha (n_out - n_in) (or the Pulay
     mix of `mixer`), V_eff[n_new],
     the energy terms of n_out and the residual int |n_out - n_in|."""
-    w = rules[1]
     f, mu = fermi_occupations(eps, nelec, kT)
     n_out = density(mesh, rules, C, f)
+    return _finish(mesh, rules, wl, f, mu, n_out, float(f @ eps), -kT * entropy(f), alpha, n_in,
+                   V_eff_in, rho_I, K, mixer)
+
+
+def scf_step_k(mesh, rules, wl, kpts, wk, eps, C, nelec, kT, alpha, n_in, V_eff_in, rho_I,
+               K=None, mixer=None):
+    """One fixed-point step with k-point sampling (Sec. 4, eqs. bloch, strong:
+    Bloch states at wavevectors k; Sec. 3 for the rest).
+
+    kpts (nk, 3) Cartesian wavevectors, wk their weights (summing to 1),
+    eps[i] and C[i] (N, n_i) complex: the lowest states of H(k_i)[V_eff_in].
+    One Fermi level for all k (fermi_occupations_k); the output density, the
+    band energy and the entropy are the k-weighted sums
+        n_out = sum_k w_k sum_n f_nk |psi_nk|^2,  e_band = sum_k w_k sum_n f_nk eps_nk,
+        S = sum_k w_k S(f_k);
+    the rest as scf_step."""
+    f, mu = fermi_occupations_k(eps, wk, nelec, kT)
+    n_out = sum(w * density_k(mesh, rules, Ck, fk, k) for w, Ck, fk, k in zip(wk, C, f, kpts))
+    e_band = float(sum(w * (fk @ np.asarray(ek)) for w, fk, ek in zip(wk, f, eps)))
+    e_ts = -kT * float(sum(w * entropy(fk) for w, fk in zip(wk, f)))
+    return _finish(mesh, rules, wl, f, mu, n_out, e_band, e_ts, alpha, n_in, V_eff_in, rho_I, K,
+                   mixer)
+
+
+def _finish(mesh, rules, wl, f, mu, n_out, e_band, e_ts, alpha, n_in, V_eff_in, rho_I, K, mixer):
+    """The energy terms of n_out, the mixing and V_eff of the mixed density."""
+    w = rules[1]
     _, VC_out = coulomb_potential(mesh, rules, rho_I - n_out, K)
     exc_out, _ = pz81(n_out)
-    e_band = float(f @ eps)
     e_dc = -float(w @ (n_out * V_eff_in))
     e_es = -0.5 * float(w @ ((rho_I - n_out) * VC_out))
     e_xc = float(w @ (n_out * exc_out))
-    e_ts = -kT * entropy(f)
     e_self = self_energy(wl)
     if mixer is None:
         n_new = n_in + alpha * (n_out - n_in)
@@ -254,4 +279,3 @@ def scf_step(mesh, rules, wl, eps, C, nelec, kT, alpha, n_in, V_eff_in, rho_I, K
                 e_es=e_es, e_self=e_self, e_xc=e_xc, e_ts=e_ts,
                 e_total=e_band + e_dc + e_es - e_self + e_xc + e_ts,
                 residual=float(w @ np.abs(n_out - n_in)))
-
