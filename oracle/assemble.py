@@ -10,7 +10,8 @@ with every integral replaced by the single shared element quadrature rule of
 Sec. 5.2, so that  H = sum_e sum_q w_q [ 1/2 G_q^T G_q + V_q b_q b_q^T ]
 and S = sum_e sum_q w_q b_q b_q^T  on the element's basis columns b_q.
 
-The basis of an element (eq. pufebasis): 64 tricubic FE functions, then
+The basis of an element (eq. pufebasis): the FE functions (64 tricubic or 32
+serendipity, mesh.fe_functions), then
 phi_v^PU Psi_alpha for each enrichment column (v, alpha) of the element; its
 gradient is Psi grad phi^PU + phi^PU grad Psi.
 
@@ -32,31 +33,32 @@ import numpy as np
 import scipy.sparse as sp
 
 from .enrich import enrichment
-from .fe import tricubic, trilinear
+from .fe import trilinear
 
 
 def element_basis(mesh, e, pts):
     """Basis values B (Q, n) and physical gradients G (3, Q, n) of element e."""
     xi = mesh.to_reference(e, pts)
-    N, dN = tricubic(xi)
+    N, dN = mesh.fe_functions(xi)
     P, dP = trilinear(xi)
     dN = mesh.grad_to_physical(dN)
     dP = mesh.grad_to_physical(dP)
     cols = mesh.elem_cols[e]
-    n = 64 + len(cols)
+    nf = mesh.nfe_e
+    n = nf + len(cols)
     Q = pts.shape[0]
     B = np.zeros((Q, n))
     G = np.zeros((3, Q, n))
-    B[:, :64] = N
-    G[:, :, :64] = dN
+    B[:, :nf] = N
+    G[:, :, :nf] = dN
     cache = {}
     for j, (dof, lv, k) in enumerate(cols):
         if k not in cache:
             al = mesh.alphas[k]
             cache[k] = enrichment(al["orb"], al["rc"], al["tau"], mesh.lattice, pts)
         psi, gpsi = cache[k]
-        B[:, 64 + j] = P[:, lv] * psi
-        G[:, :, 64 + j] = dP[:, :, lv] * psi + P[:, lv] * gpsi
+        B[:, nf + j] = P[:, lv] * psi
+        G[:, :, nf + j] = dP[:, :, lv] * psi + P[:, lv] * gpsi
     return B, G
 
 

@@ -37,10 +37,9 @@ def elem_shifts(mesh, e):
     ex, ey, ez = mesh.elem_coords(e)
     m, n = mesh.nfe_axis, mesh.nel
     out = []
-    for c in range(4):
-        for b in range(4):
-            for a in range(4):
-                out.append(((3 * ex + a) // m, (3 * ey + b) // m, (3 * ez + c) // m))
+    for loc in mesh.fe_local:
+        a, b, c = loc & 3, (loc >> 2) & 3, loc >> 4
+        out.append(((3 * ex + a) // m, (3 * ey + b) // m, (3 * ez + c) // m))
     for (_, lv, _) in mesh.elem_cols[e]:
         out.append(((ex + (lv & 1)) // n, (ey + ((lv >> 1) & 1)) // n, (ez + (lv >> 2)) // n))
     return np.array(out, dtype=np.int64)

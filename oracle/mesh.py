@@ -16,6 +16,13 @@ here from its definition):
 * enrichments alpha in (atom, orbital) order; enrichment DOFs follow the FE
   DOFs, ordered by (atom, orbital, enriched vertex index).
 
+Classical FE space: the tricubic Lagrange space (64 nodes per element) or
+the cubic serendipity space (32 nodes per element, the paper's choice in its
+PUFE runs, Sec. 6): the workload key "fe" = "lagrange64" (default) or
+"serendipity32".  Serendipity DOFs are the grid nodes with at most one
+coordinate off the vertex planes (vertices and inner edge nodes), numbered
+compactly in grid order; an element's FE columns follow fe.SERENDIPITY_LOCAL.
+
 Readings: a vertex is enriched when its minimum-image distance to the atom is
 <= r_e + 1e-12 bohr.  The column phi_v^PU Psi_alpha is kept on element e only
 when some image of alpha's atom lies at distance < r_c from the element box
@@ -45,6 +52,7 @@ from __future__ import annotations
 import numpy as np
 
 from .enrich import image_vectors
+from .fe import SERENDIPITY_LOCAL, serendipity32, tricubic
 
 
 def parallelepiped_dist(x0, M, P):
@@ -105,7 +113,26 @@ class Mesh:
             self.lattice = self.a
         self.nelem = self.nel ** 3
         self.nfe_axis = 3 * self.nel
-        self.n_fe = self.nfe_axis ** 3
+        # classical FE space: "lagrange64" (tricubic) or "serendipity32"
+        self.fe = wl.get("fe", "lagrange64")
+        m = self.nfe_axis
+        if self.fe == "lagrange64":
+            self.fe_local = np.arange(64)
+            self.n_fe = m ** 3
+            self._gmap = np.arange(m ** 3)
+        elif self.fe == "serendipity32":
+            # nodes of the periodic tricubic grid with at most one coordinate
+            # off the vertex planes, numbered compactly in grid order
+            self.fe_local = SERENDIPITY_LOCAL
+            g = np.arange(m ** 3)
+            gx, gy, gz = g % m, (g // m) % m, g // (m * m)
+            keep = (gx % 3 != 0).astype(int) + (gy % 3 != 0) + (gz % 3 != 0) <= 1
+            self._gmap = np.full(m ** 3, -1, dtype=np.int64)
+            self._gmap[keep] = np.arange(int(keep.sum()))
+            self.n_fe = int(keep.sum())
+        else:
+            raise ValueError(f"unknown FE space {self.fe!r}")
+        self.nfe_e = len(self.fe_local)
         self.species = wl["species"]
         self.atoms = [(int(s), np.array(t, dtype=np.float64)) for s, t in wl["atoms"]]
         # enrichment functions alpha = (atom, orbital)
@@ -177,15 +204,19 @@ class Mesh:
 
     # -- numbering -----------------------------------------------------------
     def fe_dofs(self, e):
+        """Global FE DOFs of the element's FE columns (local nodes fe_local)."""
         ex, ey, ez = self.elem_coords(e)
         m = self.nfe_axis
-        out = np.empty(64, dtype=np.int64)
-        for c in range(4):
-            for b in range(4):
-                for a in range(4):
-                    gx, gy, gz = (3 * ex + a) % m, (3 * ey + b) % m, (3 * ez + c) % m
-                    out[a + 4 * b + 16 * c] = gx + m * (gy + m * gz)
+        out = np.empty(len(self.fe_local), dtype=np.int64)
+        for j, loc in enumerate(self.fe_local):
+            a, b, c = loc & 3, (loc >> 2) & 3, loc >> 4
+            gx, gy, gz = (3 * ex + a) % m, (3 * ey + b) % m, (3 * ez + c) % m
+            out[j] = self._gmap[gx + m * (gy + m * gz)]
         return out
+
+    def fe_functions(self, xi):
+        """The element's FE functions and reference gradients at xi (Q, 3)."""
+        return tricubic(xi) if self.fe == "lagrange64" else serendipity32(xi)
 
     def elem_vertices(self, e):
         ex, ey, ez = self.elem_coords(e)
@@ -234,7 +265,8 @@ class Mesh:
 
     # -- per-element basis description ------------------------------------
     def elem_dofs(self, e):
-        """Global DOFs of the element's columns: 64 FE, then enrichments."""
+        """Global DOFs of the element's columns: the FE ones (64 or 32), then
+        the enrichments."""
         enr = np.array([c[0] for c in self.elem_cols[e]], dtype=np.int64)
         return np.concatenate([self.fe_dofs(e), enr])
 
