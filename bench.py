@@ -542,17 +542,18 @@ def run_pufe(args):
         peak_source = (f"min(TF32x3 = {src} bf16 burst x nominal TF32/bf16 / 3 = {tf32x3:.1f}, "
                        f"AI x {src} HBM = {ai * hbm / 1e12:.1f}) TFLOP/s")
         if n_big == 0:
-            kernels = "k_fefe_sumfac (V table) + k_fefe_rows + k_see + k_strip_sf"
-            # tabulate, V table, rows, E-E of S, strip, density, adjoint_fefe,
-            # adjoint_strip
-            launches_per_step = 8
-            prec_label = "fp32 (CUDA-core strip and FE-FE V block) + fp64 (E-E block of S)"
+            kernels = "memset H + S0 copy + k_fefe_sumfac + k_see + k_strip_sf"
+            # tabulate, FE-FE block, E-E block of S, strip, density,
+            # adjoint_fefe, adjoint_strip
+            launches_per_step = 7
+            prec_label = ("fp32 (CUDA-core strip and FE-FE V block) + error-free fp32 "
+                          "(E-E block of S, fp64-class sums)")
         else:
-            kernels = ("k_fefe_sumfac (V table) + k_fefe_rows + k_see + k_pack_v + "
+            kernels = ("memset H + S0 copy + k_fefe_sumfac + k_see + k_pack_v + "
                        "k_assemble_tc + k_strip_sf")
-            launches_per_step = 11
+            launches_per_step = 10
             prec_label = ("tf32x3 tensor-core tile (n_e > 128) + fp32 CUDA-core strip + "
-                          "fp64 (E-E block of S)")
+                          "error-free fp32 (E-E block of S, fp64-class sums)")
     roof = {"kernel": f"pufe_assemble_HS ({kernels})", "bound": bound, "achieved": achieved,
             "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": ASM_TRAFFIC.get((args.workload, args.prec)),

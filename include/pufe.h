@@ -24,9 +24,10 @@
  *   Units: bohr and hartree.  Orthorhombic cells, or general (triclinic)
  *   cells given by their lattice vectors (pufe_cell.lattice).
  *   Numbering: elements e = ex + nx (ey + ny ez).  FE DOFs are the nodes of
- *   the (3nx)(3ny)(3nz) periodic grid, index gx + 3nx (gy + 3ny gz); they are
- *   followed by the enrichment DOFs ordered by (atom, orbital, enriched
- *   vertex index).  Quadrature points are stored element by element; within
+ *   the (3nx)(3ny)(3nz) periodic grid, index gx + 3nx (gy + 3ny gz) (the
+ *   serendipity space keeps the vertex and edge nodes, renumbered in that
+ *   order); they are followed by the enrichment DOFs ordered by (atom,
+ *   orbital, enriched vertex index).  Quadrature points are stored element by element; within
  *   an element a tensor rule runs x fastest, and subdivided cells are
  *   visited depth first in the order a + 2b + 4c of their octant offsets.
  *   Matrices: one CSR pattern (int64 row pointers, int32 sorted column
@@ -101,6 +102,18 @@ enum {
 /* what to assemble */
 enum { PUFE_WANT_H = 1, PUFE_WANT_S = 2 };
 
+/* Classical FE part of the basis (Sec. 4; Sec. 6 uses the serendipity one). */
+enum {
+  PUFE_FE_LAGRANGE64 = 0,   /* tricubic Lagrange hexahedra, 64 nodes per element */
+  PUFE_FE_SERENDIPITY32 = 1 /* cubic serendipity hexahedra, 32 nodes per element: the
+                               vertices and two inner nodes per edge of the
+                               tricubic grid, numbered compactly in grid order;
+                               element columns in ascending local-node order.
+                               Tabulation, assembly (Gamma and Bloch), density
+                               and adjoint in PUFE_FP64; the other calls
+                               return PUFE_EINVAL */
+};
+
 typedef struct {
   double a[3];         /* cell edge lengths (bohr) of an orthorhombic cell */
   int nel[3];          /* elements per axis, each >= 1 */
@@ -116,6 +129,7 @@ typedef struct {
                             is not read.  General cells take the FP64 path
                             (tabulation, assembly, Bloch assembly, density,
                             adjoint); the other calls return PUFE_EINVAL. */
+  int fe_space;        /* PUFE_FE_LAGRANGE64 (0) or PUFE_FE_SERENDIPITY32 */
 } pufe_cell;
 
 typedef struct {
@@ -134,6 +148,15 @@ typedef struct {
   int p_min, p_max;    /* PADAPT range (1..16) */
   double tol;          /* absolute tolerance of the adaptive tests */
   int max_depth;       /* HADAPT subdivision depth limit (0..4) */
+  int device_tests;    /* PADAPT / HADAPT: 0 evaluates the tests' integrals
+                          on the host cores, 1 on the current CUDA device
+                          (one CTA per test, every test of an order set or
+                          subdivision level in one launch; PUFE_ECUDA
+                          without a device).  The decisions, points and
+                          point order are those of the host construction;
+                          only the summation order of the integrals
+                          differs (a test within rounding of tol may
+                          decide the other way). */
 } pufe_quad;
 
 /* Build the mesh, enrichment sets, quadrature rules, CSR pattern and scatter
@@ -242,17 +265,23 @@ pufe_status pufe_assemble_HS_bloch(pufe_ctx *ctx, const double *k, const double 
 
 /* Density of complex Bloch states: n_q = sum_j f_j |sum_l B_ql
  * exp(i k.R_l) C_lj|^2 with C = C_re + i C_im (device float64, N x nocc, row
- * stride ldc).  Other arguments as pufe_density; FP64 only.  Asynchronous. */
+ * stride ldc).  Other arguments as pufe_density: PUFE_FP64 (any cell) or
+ * PUFE_TF32X3 (orthorhombic cells: the phased coefficients formed in FP64,
+ * rounded to FP32, real and imaginary parts summed in FP32 on the CUDA
+ * cores).  Asynchronous. */
 pufe_status pufe_density_bloch(pufe_ctx *ctx, const double *k, const double *C_re,
                                const double *C_im, int64_t ldc, const double *f, int nocc,
-                               double *rho, void *stream);
+                               int prec, double *rho, void *stream);
 
 /* Adjoint of V -> H(k) for a complex cotangent Hbar = Hbar_re + i Hbar_im
  * (device, nnz each): Vbar_q = w_q Re sum_ij conj(Hbar[g_i, g_j])
  * exp(i k.(R_j - R_i)) b_i b_j, the derivative of Re sum conj(Hbar) H(k).
- * FP64 only.  Asynchronous. */
+ * PUFE_FP64 (any cell) or PUFE_TF32X3 (orthorhombic cells: the phased real
+ * element block formed in FP64 from the two CSR values, then the kernels of
+ * pufe_assemble_HV_adjoint in FP32).  Asynchronous. */
 pufe_status pufe_assemble_HV_adjoint_bloch(pufe_ctx *ctx, const double *k, const double *Hbar_re,
-                                           const double *Hbar_im, double *Vbar, void *stream);
+                                           const double *Hbar_im, int prec, double *Vbar,
+                                           void *stream);
 
 /* ---- separable nonlocal projectors (Sec. 4, eq. disceig3d) -------------- */
 
@@ -349,6 +378,26 @@ pufe_status pufe_scf_step(pufe_ctx *ctx, int nstates, const double *eps, const d
                           int64_t ldc, double nelec, double kT, double alpha, int pulay, int prec,
                           const double *rho_I, const double *V_eff_in, double *n,
                           double *V_eff_out, double *f_out, pufe_scf_info *info, void *stream);
+
+/* One SCF step with k-point sampling (Sec. 4, eqs. bloch, strong; Sec. 3),
+ * after the caller's eigensolves of H(k) c = eps S(k) c (pufe_assemble_HS_bloch)
+ * at nk wavevectors kpts (host, nk x 3, 1/bohr) with weights wk (host, nk,
+ * each > 0, summing to 1; a time-reversal pair k, -k is one point of twice
+ * the weight): eps (host, nk x nstates, k-major) and the S(k)-orthonormal
+ * eigenvectors C_re[i] + i C_im[i] (host arrays of nk device pointers, each
+ * N x nstates float64 with leading dimension ldc).  One Fermi level for all k:
+ * f_nk = 2 / (1 + exp((eps_nk - mu)/kT)) with sum_k w_k sum_n f_nk = nelec;
+ * n_out = sum_k w_k sum_n f_nk |psi_nk|^2 (pufe_density_bloch with `prec`);
+ * e_band = sum_k w_k sum_n f_nk eps_nk and the entropy term weighted alike;
+ * energies, mixing (the same Pulay history) and the new potential as
+ * pufe_scf_step.  1 <= nk <= 64; f_out (host, nk x nstates) may be NULL.
+ * Blocking: returns after the step has finished on `stream`. */
+pufe_status pufe_scf_step_bloch(pufe_ctx *ctx, int nk, const double *kpts, const double *wk,
+                                int nstates, const double *eps, const double *const *C_re,
+                                const double *const *C_im, int64_t ldc, double nelec, double kT,
+                                double alpha, int pulay, int prec, const double *rho_I,
+                                const double *V_eff_in, double *n, double *V_eff_out,
+                                double *f_out, pufe_scf_info *info, void *stream);
 
 /* Forget the Pulay history of the context (start of a new SCF run). */
 pufe_status pufe_scf_reset(pufe_ctx *ctx);

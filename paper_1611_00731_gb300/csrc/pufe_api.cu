@@ -33,13 +33,18 @@ struct DeviceGuard {
 
 using namespace pufe;
 
+// contexts that only the FP64 kernels take: general (triclinic) cells and
+// the serendipity FE space (the mixed, SCF and projector kernels are written
+// for orthorhombic cells and the tricubic tensor-product space)
+static bool fp64_only(const pufe_ctx *ctx) { return ctx->general || ctx->ser; }
+
 extern "C" {
 
 pufe_status pufe_tabulate(pufe_ctx *ctx, int prec, void *stream) {
   if (pufe_status e0 = need_device(ctx)) return e0;
   if (prec != PUFE_FP64 && prec != PUFE_TF32X3) return fail(PUFE_EINVAL, "unknown precision");
-  if (prec == PUFE_TF32X3 && ctx->general)
-    return fail(PUFE_EINVAL, "PUFE_TF32X3 takes orthorhombic cells; general cells take PUFE_FP64");
+  if (prec == PUFE_TF32X3 && fp64_only(ctx))
+    return fail(PUFE_EINVAL, "PUFE_TF32X3 takes orthorhombic cells with the tricubic space; general cells and the serendipity space take PUFE_FP64");
   DeviceGuard g(ctx->device);
   if (!g.ok) return fail(PUFE_ECUDA, "cudaSetDevice failed");
   pufe_status st;
@@ -54,8 +59,8 @@ pufe_status pufe_tabulate(pufe_ctx *ctx, int prec, void *stream) {
 }
 
 static pufe_status need_table(const pufe_ctx *ctx, int prec) {
-  if (prec == PUFE_TF32X3 && ctx->general)
-    return fail(PUFE_EINVAL, "PUFE_TF32X3 takes orthorhombic cells; general cells take PUFE_FP64");
+  if (prec == PUFE_TF32X3 && fp64_only(ctx))
+    return fail(PUFE_EINVAL, "PUFE_TF32X3 takes orthorhombic cells with the tricubic space; general cells and the serendipity space take PUFE_FP64");
   if (ctx->psi_len == 0) return PUFE_OK;
   if (prec == PUFE_FP64 && !ctx->tabulated)
     return fail(PUFE_ESTATE, "call pufe_tabulate(PUFE_FP64) first");
@@ -85,7 +90,7 @@ pufe_status pufe_assemble_HS(pufe_ctx *ctx, const double *V, int prec, int what,
 pufe_status pufe_assemble_HS_static(pufe_ctx *ctx, const double *V, int what, double *H,
                                     double *S, void *stream) {
   if (pufe_status e0 = need_device(ctx)) return e0;
-  if (ctx->general) return fail(PUFE_EINVAL, "pufe_assemble_HS_static takes orthorhombic cells");
+  if (fp64_only(ctx)) return fail(PUFE_EINVAL, "pufe_assemble_HS_static takes orthorhombic cells with the tricubic space");
   if (pufe_status e1 = need_table(ctx, PUFE_TF32X3)) return e1;
   if (what <= 0 || what > (PUFE_WANT_H | PUFE_WANT_S)) return fail(PUFE_EINVAL, "bad `what` mask");
   if ((what & PUFE_WANT_H) && (!H || !V)) return fail(PUFE_EINVAL, "H wanted: need H and V");
@@ -151,26 +156,39 @@ pufe_status pufe_assemble_HS_bloch(pufe_ctx *ctx, const double *k, const double 
 
 pufe_status pufe_density_bloch(pufe_ctx *ctx, const double *k, const double *C_re,
                                const double *C_im, int64_t ldc, const double *f, int nocc,
-                               double *rho, void *stream) {
+                               int prec, double *rho, void *stream) {
   if (pufe_status e0 = need_device(ctx)) return e0;
-  if (pufe_status e1 = need_table(ctx, PUFE_FP64)) return e1;
+  if (prec != PUFE_FP64 && prec != PUFE_TF32X3) return fail(PUFE_EINVAL, "unknown precision");
+  if (prec == PUFE_TF32X3 && fp64_only(ctx))
+    return fail(PUFE_EINVAL, "PUFE_TF32X3 takes orthorhombic cells with the tricubic space; general cells and the serendipity space take PUFE_FP64");
+  if (pufe_status e1 = need_table(ctx, prec)) return e1;
   if (!k || !C_re || !C_im || !f || !rho) return fail(PUFE_EINVAL, "k, C_re, C_im, f and rho must not be NULL");
   if (nocc < 1 || nocc > 64 || ldc < nocc) return fail(PUFE_EINVAL, "need 1 <= nocc <= 64 and ldc >= nocc");
   DeviceGuard g(ctx->device);
   if (!g.ok) return fail(PUFE_ECUDA, "cudaSetDevice failed");
-  return launch_density_fp64_bloch(ctx, phase_table(ctx, k), C_re, C_im, ldc, f, nocc, rho,
-                                   (cudaStream_t)stream);
+  const PhaseTab ph = phase_table(ctx, k);
+  if (prec == PUFE_TF32X3)
+    return launch_density_tc(ctx, C_re, ldc, f, nocc, rho, (cudaStream_t)stream, C_im, &ph);
+  return launch_density_fp64_bloch(ctx, ph, C_re, C_im, ldc, f, nocc, rho, (cudaStream_t)stream);
 }
 
 pufe_status pufe_assemble_HV_adjoint_bloch(pufe_ctx *ctx, const double *k, const double *Hbar_re,
-                                           const double *Hbar_im, double *Vbar, void *stream) {
+                                           const double *Hbar_im, int prec, double *Vbar,
+                                           void *stream) {
   if (pufe_status e0 = need_device(ctx)) return e0;
-  if (pufe_status e1 = need_table(ctx, PUFE_FP64)) return e1;
+  if (prec != PUFE_FP64 && prec != PUFE_TF32X3) return fail(PUFE_EINVAL, "unknown precision");
+  if (prec == PUFE_TF32X3 && fp64_only(ctx))
+    return fail(PUFE_EINVAL, "PUFE_TF32X3 takes orthorhombic cells with the tricubic space; general cells and the serendipity space take PUFE_FP64");
+  if (pufe_status e1 = need_table(ctx, prec)) return e1;
   if (!k || !Hbar_re || !Hbar_im || !Vbar) return fail(PUFE_EINVAL, "k, Hbar_re, Hbar_im and Vbar must not be NULL");
   DeviceGuard g(ctx->device);
   if (!g.ok) return fail(PUFE_ECUDA, "cudaSetDevice failed");
-  return launch_adjoint_fp64_bloch(ctx, phase_table(ctx, k), Hbar_re, Hbar_im, Vbar,
-                                   (cudaStream_t)stream);
+  const PhaseTab ph = phase_table(ctx, k);
+  if (prec == PUFE_TF32X3) {
+    const BlochCot bc{Hbar_im, ctx->d.eshift, ph};
+    return launch_adjoint_tc(ctx, Hbar_re, Vbar, (cudaStream_t)stream, &bc);
+  }
+  return launch_adjoint_fp64_bloch(ctx, ph, Hbar_re, Hbar_im, Vbar, (cudaStream_t)stream);
 }
 
 // checks the projector list and copies it to the device (blocking copy)
@@ -198,7 +216,7 @@ static pufe_status upload_projectors(pufe_ctx *ctx, int nproj, const pufe_projec
 pufe_status pufe_nonlocal_projections(pufe_ctx *ctx, int nproj, const pufe_projector *proj,
                                       double *F, void *stream) {
   if (pufe_status e0 = need_device(ctx)) return e0;
-  if (ctx->general) return fail(PUFE_EINVAL, "this call takes orthorhombic cells");
+  if (fp64_only(ctx)) return fail(PUFE_EINVAL, "this call takes orthorhombic cells with the tricubic space");
   if (pufe_status e1 = need_table(ctx, PUFE_FP64)) return e1;
   if (!F) return fail(PUFE_EINVAL, "F must not be NULL");
   DeviceGuard g(ctx->device);
@@ -213,7 +231,7 @@ pufe_status pufe_nonlocal_projections_bloch(pufe_ctx *ctx, const double *k, int 
                                             const pufe_projector *proj, double *F_re,
                                             double *F_im, void *stream) {
   if (pufe_status e0 = need_device(ctx)) return e0;
-  if (ctx->general) return fail(PUFE_EINVAL, "this call takes orthorhombic cells");
+  if (fp64_only(ctx)) return fail(PUFE_EINVAL, "this call takes orthorhombic cells with the tricubic space");
   if (pufe_status e1 = need_table(ctx, PUFE_FP64)) return e1;
   if (!k || !F_re || !F_im) return fail(PUFE_EINVAL, "k, F_re and F_im must not be NULL");
   DeviceGuard g(ctx->device);
@@ -229,7 +247,7 @@ pufe_status pufe_nonlocal_projections_bloch(pufe_ctx *ctx, const double *k, int 
 pufe_status pufe_ion_density(pufe_ctx *ctx, int natoms, const double *tau, const double *Z,
                              const double *sigma, double *rho_I, void *stream) {
   if (pufe_status e0 = need_device(ctx)) return e0;
-  if (ctx->general) return fail(PUFE_EINVAL, "this call takes orthorhombic cells");
+  if (fp64_only(ctx)) return fail(PUFE_EINVAL, "this call takes orthorhombic cells with the tricubic space");
   if (natoms < 0 || !rho_I || (natoms > 0 && (!tau || !Z || !sigma)))
     return fail(PUFE_EINVAL, "need natoms >= 0, rho_I, and tau, Z, sigma for the atoms");
   for (int a = 0; a < natoms; ++a)
@@ -242,7 +260,7 @@ pufe_status pufe_ion_density(pufe_ctx *ctx, int natoms, const double *tau, const
 pufe_status pufe_effective_potential(pufe_ctx *ctx, const double *n, const double *rho_I,
                                      double *V_eff, double *V_C, double *eps_xc, void *stream) {
   if (pufe_status e0 = need_device(ctx)) return e0;
-  if (ctx->general) return fail(PUFE_EINVAL, "this call takes orthorhombic cells");
+  if (fp64_only(ctx)) return fail(PUFE_EINVAL, "this call takes orthorhombic cells with the tricubic space");
   if (!n || !rho_I || !V_eff) return fail(PUFE_EINVAL, "n, rho_I and V_eff must not be NULL");
   DeviceGuard g(ctx->device);
   if (!g.ok) return fail(PUFE_ECUDA, "cudaSetDevice failed");
@@ -254,7 +272,7 @@ pufe_status pufe_scf_step(pufe_ctx *ctx, int nstates, const double *eps, const d
                           const double *rho_I, const double *V_eff_in, double *n,
                           double *V_eff_out, double *f_out, pufe_scf_info *info, void *stream) {
   if (pufe_status e0 = need_device(ctx)) return e0;
-  if (ctx->general) return fail(PUFE_EINVAL, "this call takes orthorhombic cells");
+  if (fp64_only(ctx)) return fail(PUFE_EINVAL, "this call takes orthorhombic cells with the tricubic space");
   if (prec != PUFE_FP64 && prec != PUFE_TF32X3) return fail(PUFE_EINVAL, "unknown precision");
   if (pufe_status e1 = need_table(ctx, prec)) return e1;
   if (nstates < 1 || nstates > 64 || ldc < nstates)
@@ -271,6 +289,40 @@ pufe_status pufe_scf_step(pufe_ctx *ctx, int nstates, const double *eps, const d
                          V_eff_out, f_out, info, (cudaStream_t)stream);
 }
 
+pufe_status pufe_scf_step_bloch(pufe_ctx *ctx, int nk, const double *kpts, const double *wk,
+                                int nstates, const double *eps, const double *const *C_re,
+                                const double *const *C_im, int64_t ldc, double nelec, double kT,
+                                double alpha, int pulay, int prec, const double *rho_I,
+                                const double *V_eff_in, double *n, double *V_eff_out,
+                                double *f_out, pufe_scf_info *info, void *stream) {
+  if (pufe_status e0 = need_device(ctx)) return e0;
+  if (fp64_only(ctx)) return fail(PUFE_EINVAL, "this call takes orthorhombic cells with the tricubic space");
+  if (prec != PUFE_FP64 && prec != PUFE_TF32X3) return fail(PUFE_EINVAL, "unknown precision");
+  if (pufe_status e1 = need_table(ctx, prec)) return e1;
+  if (nk < 1 || nk > 64) return fail(PUFE_EINVAL, "need 1 <= nk <= 64");
+  if (nstates < 1 || nstates > 64 || ldc < nstates)
+    return fail(PUFE_EINVAL, "need 1 <= nstates <= 64 and ldc >= nstates");
+  if (!kpts || !wk || !eps || !C_re || !C_im || !rho_I || !V_eff_in || !n || !V_eff_out)
+    return fail(PUFE_EINVAL,
+                "kpts, wk, eps, C_re, C_im, rho_I, V_eff_in, n and V_eff_out must not be NULL");
+  double wsum = 0.0;
+  for (int i = 0; i < nk; ++i) {
+    if (!(wk[i] > 0.0)) return fail(PUFE_EINVAL, "k-point weights must be > 0");
+    if (!C_re[i] || !C_im[i]) return fail(PUFE_EINVAL, "an eigenvector array is NULL");
+    wsum += wk[i];
+  }
+  if (std::fabs(wsum - 1.0) > 1e-12) return fail(PUFE_EINVAL, "k-point weights must sum to 1");
+  if (!(kT > 0.0) || !(nelec > 0.0) || nelec > 2.0 * nstates)
+    return fail(PUFE_EINVAL, "need kT > 0 and 0 < nelec <= 2 nstates");
+  if (!ctx->scf) return fail(PUFE_ESTATE, "call pufe_ion_density first");
+  if (pulay < 0 || pulay > 8) return fail(PUFE_EINVAL, "need 0 <= pulay <= 8");
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return fail(PUFE_ECUDA, "cudaSetDevice failed");
+  return launch_scf_step_bloch(ctx, nk, kpts, wk, nstates, eps, C_re, C_im, ldc, nelec, kT, alpha,
+                               pulay, prec, rho_I, V_eff_in, n, V_eff_out, f_out, info,
+                               (cudaStream_t)stream);
+}
+
 pufe_status pufe_scf_reset(pufe_ctx *ctx) {
   if (pufe_status e0 = need_device(ctx)) return e0;
   scf_reset(ctx);
@@ -279,7 +331,7 @@ pufe_status pufe_scf_reset(pufe_ctx *ctx) {
 
 pufe_status pufe_autotune(pufe_ctx *ctx, int *nclasses, void *stream) {
   if (pufe_status e0 = need_device(ctx)) return e0;
-  if (ctx->general) return fail(PUFE_EINVAL, "the mixed path takes orthorhombic cells");
+  if (fp64_only(ctx)) return fail(PUFE_EINVAL, "the mixed path takes orthorhombic cells with the tricubic space");
   DeviceGuard g(ctx->device);
   if (!g.ok) return fail(PUFE_ECUDA, "cudaSetDevice failed");
   return autotune_strip(ctx, nclasses, (cudaStream_t)stream);

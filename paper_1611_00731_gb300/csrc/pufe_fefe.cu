@@ -139,13 +139,15 @@ __global__ void __launch_bounds__(SF_NT) k_fefe_sumfac(
 // (Hbar restricted to the element's 64 FE columns, general, not symmetric),
 // contracted axis by axis: 4096 p + 256 p^2 + 16 p^3 multiply-adds per cell,
 // then Vbar_q = w_q f(q) is stored (the strip kernel adds the enrichment part).
+template <bool BLOCH>
 __global__ void __launch_bounds__(SF_NT) k_adjoint_fefe(
     const int32_t *__restrict__ order, const int64_t *__restrict__ qoff,
     const double *__restrict__ w, const double *__restrict__ xi_all,
     const int32_t *__restrict__ partoff, const int32_t *__restrict__ part_p,
     const int32_t *__restrict__ part_q, const int64_t *__restrict__ doff,
     const int64_t *__restrict__ soff, const int32_t *__restrict__ smap,
-    const double *__restrict__ Hbar, int pm, double *__restrict__ Vbar, unsigned *err) {
+    const double *__restrict__ Hbar, int pm, double *__restrict__ Vbar, unsigned *err,
+    BlochCot bc) {
   // dynamic shared memory, sized for the largest per-axis count pm:
   // Hs[64][64], L1[3][4][pm], G1[256 pm] = [(a,b),(a',b')][qz],
   // G2[16 pm^2] = [(a,a')][qy + p qz]
@@ -165,6 +167,17 @@ __global__ void __launch_bounds__(SF_NT) k_adjoint_fefe(
     double h[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) h[u] = o0 + u * SF_NT < 4096 ? Hbar[s1[u]] : 0.0;
+    if (BLOCH) {   // at a wavevector: the phased real part (columns' shift codes)
+      double hi[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) hi[u] = o0 + u * SF_NT < 4096 ? bc.Hi[s1[u]] : 0.0;
+      const uint8_t *esh = bc.eshift + doff[e];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int o = o0 + u * SF_NT;
+        if (o < 4096) h[u] = cot_entry(h[u], hi[u], esh[o >> 6], esh[o & 63], bc.ph);
+      }
+    }
 #pragma unroll
     for (int u = 0; u < 8; ++u)
       if (o0 + u * SF_NT < 4096) Hs[o0 + u * SF_NT] = (float)h[u];
@@ -260,17 +273,17 @@ pufe_status launch_fefe_bloch(pufe_ctx *ctx, const PhaseTab &ph, const double *V
 namespace pufe {
 // Vbar = w_q (FE part of b^T Hbar b) for elements order[first .. first+count)
 pufe_status launch_adjoint_fefe(pufe_ctx *ctx, const double *Hbar, double *Vbar, int first,
-                                int count, cudaStream_t st) {
+                                int count, cudaStream_t st, const BlochCot &bc) {
   auto &D = ctx->d;
   if (ctx->max_part_p > SF_PMAX) return fail(PUFE_EINVAL, "rule with more than 16 points per axis");
   if (count <= 0) return PUFE_OK;
   const int pm = std::max(1, ctx->max_part_p);
   const size_t sm = (size_t)(4096 + 12 * pm + 256 * pm + 16 * pm * pm) * sizeof(float);
-  PUFE_CUDA_TRY(
-      cudaFuncSetAttribute(k_adjoint_fefe, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  k_adjoint_fefe<<<(unsigned)count, SF_NT, sm, st>>>(D.order + first, D.qoff, D.w, D.xi, D.partoff,
-                                                     D.part_p, D.part_q, D.doff, D.soff, D.smap,
-                                                     Hbar, pm, Vbar, D.err);
+  auto kern = bc.Hi ? k_adjoint_fefe<true> : k_adjoint_fefe<false>;
+  PUFE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  kern<<<(unsigned)count, SF_NT, sm, st>>>(D.order + first, D.qoff, D.w, D.xi, D.partoff, D.part_p,
+                                           D.part_q, D.doff, D.soff, D.smap, Hbar, pm, Vbar, D.err,
+                                           bc);
   PUFE_CUDA_TRY(cudaGetLastError());
   return PUFE_OK;
 }

@@ -4,8 +4,8 @@
 //   K4  density at quadrature points (Sec. 3, eq. rhoe)
 //   K5  adjoint of V -> H (derivative of sum Hbar_ij H_ij with respect to V_q)
 //
-// The element basis (64 tricubic FE columns, then phi_v^PU Psi_alpha columns)
-// is rebuilt on chip from the reference coordinates of each quadrature point
+// The element basis (the FE columns -- 64 tricubic or 32 cubic serendipity
+// functions -- then phi_v^PU Psi_alpha columns) is rebuilt on chip from the reference coordinates of each quadrature point
 // and the tabulated Psi / grad Psi; it is never stored in HBM.
 #include <math.h>
 
@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(ASM_NT) k_assemble_fp64(
     const double *__restrict__ V, double sx, double sy, double sz, int npad_max, int want,
     double *__restrict__ H, double *__restrict__ S, unsigned *err,
     const uint8_t *__restrict__ eshift, PhaseTab ph, double *__restrict__ Hi,
-    double *__restrict__ Si, const int32_t *__restrict__ wsplit, Mat3 jit) {
+    double *__restrict__ Si, const int32_t *__restrict__ wsplit, Mat3 jit, int nfe) {
   extern __shared__ __align__(16) double smem[];
   // work item: a whole element, or the point range [qa, qb) of one
   const int e = wsplit ? wsplit[3 * blockIdx.x] : order[blockIdx.x];
@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(ASM_NT) k_assemble_fp64(
     if (threadIdx.x == 0) set_err(err, DEVERR_SHAPE);
     return;
   }
-  const int32_t *ec = ecol + (doff[e] - 64ll * e);
+  const int32_t *ec = ecol + (doff[e] - (int64_t)nfe * e);
   const double *pe = psi + 4 * toff[e];
   // shared layout: 5 arrays [QC][npad] then 1D tables
   double *Y0 = smem, *Y1 = Y0 + QC * npad, *Y2 = Y1 + QC * npad, *Z = Y2 + QC * npad,
@@ -188,11 +188,22 @@ __global__ void __launch_bounds__(ASM_NT) k_assemble_fp64(
             y = jit.m[3] * rx + jit.m[4] * ry + jit.m[5] * rz;
             z = jit.m[6] * rx + jit.m[7] * ry + jit.m[8] * rz;
           };
-          if (c < 64) {
-            fe_column(tab[qq], c, GEN ? one : s, b, gx, gy, gz);
+          if (c < nfe) {   // FE column: tricubic (64) or serendipity (32)
+            if (nfe == 64) {
+              fe_column(tab[qq], c, GEN ? one : s, b, gx, gy, gz);
+            } else {
+              const double xq[3] = {xi_all[3 * (q0 + q)], xi_all[3 * (q0 + q) + 1],
+                                    xi_all[3 * (q0 + q) + 2]};
+              const double *sc = GEN ? one : s;
+              double g3[3];
+              serendipity32(c, xq, b, g3);
+              gx = g3[0] * sc[0];
+              gy = g3[1] * sc[1];
+              gz = g3[2] * sc[2];
+            }
             if (GEN) tomap(gx, gy, gz);
           } else {
-            const int code = ec[c - 64];
+            const int code = ec[c - nfe];
             const int slot = code >> 3, lv = code & 7;
             const double *pp = pe + (int64_t)slot * 4 * Q + q;
             const double ps[4] = {pp[0], pp[Q], pp[2 * Q], pp[3 * Q]};
@@ -310,30 +321,41 @@ __global__ void __launch_bounds__(ASM_NT) k_assemble_fp64(
 // element's coefficient block C_e (n x nocc, gathered through the element DOF
 // list) sits in shared memory; each thread evaluates its basis row on the fly.
 // ---------------------------------------------------------------------------
-template <int KC>
+template <int KC, bool SER>
 __device__ __forceinline__ double density_point(const double xi[3], int q, int Q, int nenr,
                                                 const int32_t *ec, const double *pe,
                                                 const double *Cs, const double *fs, int nocc,
                                                 int k0) {
-  double L[3][4], dL[3][4];
-#pragma unroll
-  for (int d = 0; d < 3; ++d) lagrange3(xi[d], L[d], dL[d]);
   double acc[KC];
 #pragma unroll
   for (int k = 0; k < KC; ++k) acc[k] = 0.0;
+  constexpr int NF = SER ? 32 : 64;
+  if (SER) {   // the 32 serendipity columns
+    for (int c = 0; c < 32; ++c) {
+      double b, g3[3];
+      serendipity32(c, xi, b, g3);
+      const double *cr = Cs + c * nocc + k0;
 #pragma unroll
-  for (int c3 = 0; c3 < 4; ++c3)
-#pragma unroll
-    for (int c2 = 0; c2 < 4; ++c2) {
-      const double lyz = L[1][c2] * L[2][c3];
-#pragma unroll
-      for (int c1 = 0; c1 < 4; ++c1) {
-        const double b = L[0][c1] * lyz;
-        const double *cr = Cs + (c1 + 4 * c2 + 16 * c3) * nocc + k0;
-#pragma unroll
-        for (int k = 0; k < KC; ++k) acc[k] = fma(b, cr[k], acc[k]);
-      }
+      for (int k = 0; k < KC; ++k) acc[k] = fma(b, cr[k], acc[k]);
     }
+  } else {
+    double L[3][4], dL[3][4];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) lagrange3(xi[d], L[d], dL[d]);
+#pragma unroll
+    for (int c3 = 0; c3 < 4; ++c3)
+#pragma unroll
+      for (int c2 = 0; c2 < 4; ++c2) {
+        const double lyz = L[1][c2] * L[2][c3];
+#pragma unroll
+        for (int c1 = 0; c1 < 4; ++c1) {
+          const double b = L[0][c1] * lyz;
+          const double *cr = Cs + (c1 + 4 * c2 + 16 * c3) * nocc + k0;
+#pragma unroll
+          for (int k = 0; k < KC; ++k) acc[k] = fma(b, cr[k], acc[k]);
+        }
+      }
+  }
   for (int j = 0; j < nenr; ++j) {
     const int code = ec[j];
     const int slot = code >> 3, lv = code & 7;
@@ -341,7 +363,7 @@ __device__ __forceinline__ double density_point(const double xi[3], int q, int Q
 #pragma unroll
     for (int d = 0; d < 3; ++d) phi *= ((lv >> d) & 1) ? 0.5 * (1.0 + xi[d]) : 0.5 * (1.0 - xi[d]);
     const double b = phi * pe[(int64_t)slot * 4 * Q + q];
-    const double *cr = Cs + (64 + j) * nocc + k0;
+    const double *cr = Cs + (NF + j) * nocc + k0;
 #pragma unroll
     for (int k = 0; k < KC; ++k) acc[k] = fma(b, cr[k], acc[k]);
   }
@@ -353,7 +375,7 @@ __device__ __forceinline__ double density_point(const double xi[3], int q, int Q
 
 // BLOCH: complex coefficients C + i Ci; each element block is gathered with
 // the column phases applied, and n = sum_k f_k (Re psi_k^2 + Im psi_k^2).
-template <bool BLOCH>
+template <bool BLOCH, bool SER>
 __global__ void __launch_bounds__(DEN_NT) k_density_fp64(
     const int32_t *__restrict__ order, const int64_t *__restrict__ qoff,
     const double *__restrict__ xi_all, const int64_t *__restrict__ doff,
@@ -367,8 +389,9 @@ __global__ void __launch_bounds__(DEN_NT) k_density_fp64(
   const int64_t q0 = qoff[e];
   const int Q = (int)(qoff[e + 1] - q0);
   const int n = (int)(doff[e + 1] - doff[e]);
-  const int nenr = n - 64;
-  const int32_t *ec = ecol + (doff[e] - 64ll * e);
+  constexpr int NF = SER ? 32 : 64;   // FE columns
+  const int nenr = n - NF;
+  const int32_t *ec = ecol + (doff[e] - (int64_t)NF * e);
   const int32_t *dl = dofs + doff[e];
   const double *pe = psi + 4 * toff[e];
   double *Cs = smem;             // n x noccp
@@ -396,8 +419,8 @@ __global__ void __launch_bounds__(DEN_NT) k_density_fp64(
     const double xq[3] = {xi_all[3 * (q0 + q)], xi_all[3 * (q0 + q) + 1], xi_all[3 * (q0 + q) + 2]};
     double r = 0.0;
     for (int k0 = 0; k0 < noccp; k0 += 8) {
-      r += density_point<8>(xq, q, Q, nenr, ec, pe, Cs, fs, noccp, k0);
-      if (BLOCH) r += density_point<8>(xq, q, Q, nenr, ec, pe, Cz, fs, noccp, k0);
+      r += density_point<8, SER>(xq, q, Q, nenr, ec, pe, Cs, fs, noccp, k0);
+      if (BLOCH) r += density_point<8, SER>(xq, q, Q, nenr, ec, pe, Cz, fs, noccp, k0);
     }
     rho[q0 + q] = r;
   }
@@ -421,7 +444,7 @@ __global__ void __launch_bounds__(ADJ_NT) k_adjoint_fp64(
     const int64_t *__restrict__ soff, const int32_t *__restrict__ smap,
     const double *__restrict__ Hbar, int hs_in_smem, double *__restrict__ Vbar,
     const uint8_t *__restrict__ eshift, PhaseTab ph, const double *__restrict__ Hbi,
-    const int32_t *__restrict__ wsplit) {
+    const int32_t *__restrict__ wsplit, int nfe) {
   extern __shared__ __align__(16) double smem[];
   // work item: a whole element, or the point range [qa, qb) of one
   const int e = wsplit ? wsplit[3 * blockIdx.x] : order[blockIdx.x];
@@ -430,7 +453,7 @@ __global__ void __launch_bounds__(ADJ_NT) k_adjoint_fp64(
   const int qa = wsplit ? max(wsplit[3 * blockIdx.x + 1], 0) : 0;
   const int qb = wsplit ? min(wsplit[3 * blockIdx.x + 2], Q) : Q;
   const int n = (int)(doff[e + 1] - doff[e]);
-  const int32_t *ec = ecol + (doff[e] - 64ll * e);
+  const int32_t *ec = ecol + (doff[e] - (int64_t)nfe * e);
   const double *pe = psi + 4 * toff[e];
   const int32_t *m = smap + soff[e];
   double *Bc = smem;                 // QC x n
@@ -473,10 +496,17 @@ __global__ void __launch_bounds__(ADJ_NT) k_adjoint_fp64(
       const int q = qc + qq;
       double b = 0, gx, gy, gz;
       if (q < qb) {
-        if (c < 64) {
-          fe_column(tab[qq], c, s, b, gx, gy, gz);
+        if (c < nfe) {   // FE column: tricubic (64) or serendipity (32)
+          if (nfe == 64) {
+            fe_column(tab[qq], c, s, b, gx, gy, gz);
+          } else {
+            const double xq[3] = {xi_all[3 * (q0 + q)], xi_all[3 * (q0 + q) + 1],
+                                  xi_all[3 * (q0 + q) + 2]};
+            double g3[3];
+            serendipity32(c, xq, b, g3);
+          }
         } else {
-          const int code = ec[c - 64];
+          const int code = ec[c - nfe];
           const int slot = code >> 3, lv = code & 7;
           const double *pp = pe + (int64_t)slot * 4 * Q + q;
           const double ps[4] = {pp[0], 0.0, 0.0, 0.0};
@@ -697,7 +727,7 @@ pufe_status launch_assemble_fp64(pufe_ctx *ctx, const double *V, int what, doubl
   kern<<<fp64_items(ctx), ASM_NT, sm, st>>>(
       D.order, D.qoff, D.w, D.xi, D.doff, D.ecol, D.toff, D.psi, D.soff, D.smap, V,
       2.0 / ctx->h[0], 2.0 / ctx->h[1], 2.0 / ctx->h[2], npad, what, H, S, D.err, nullptr,
-      PhaseTab{}, nullptr, nullptr, D.wsplit, jit_of(ctx));
+      PhaseTab{}, nullptr, nullptr, D.wsplit, jit_of(ctx), ctx->nfe_e);
   PUFE_CUDA_TRY(cudaGetLastError());
   return PUFE_OK;
 }
@@ -708,9 +738,9 @@ pufe_status launch_density_fp64(pufe_ctx *ctx, const double *C, int64_t ldc, con
   const int noccp = (nocc + 7) & ~7;
   const size_t sm = ((size_t)ctx->max_basis * noccp + noccp) * sizeof(double);
   if (sm > 227 * 1024) return fail(PUFE_EINVAL, "n_e * nocc too large for the density kernel");
-  PUFE_CUDA_TRY(cudaFuncSetAttribute(k_density_fp64<false>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  k_density_fp64<false><<<(unsigned)ctx->nelem, DEN_NT, sm, st>>>(
+  auto kern = ctx->ser ? k_density_fp64<false, true> : k_density_fp64<false, false>;
+  PUFE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  kern<<<(unsigned)ctx->nelem, DEN_NT, sm, st>>>(
       D.order, D.qoff, D.xi, D.doff, D.dofs, D.ecol, D.toff, D.psi, C, ldc, f, nocc, noccp, rho,
       nullptr, PhaseTab{}, nullptr);
   PUFE_CUDA_TRY(cudaGetLastError());
@@ -728,7 +758,7 @@ pufe_status launch_adjoint_fp64(pufe_ctx *ctx, const double *Hbar, double *Vbar,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
   k_adjoint_fp64<false><<<fp64_items(ctx), ADJ_NT, sm, st>>>(
       D.order, D.qoff, D.w, D.xi, D.doff, D.ecol, D.toff, D.psi, D.soff, D.smap, Hbar, in_smem,
-      Vbar, nullptr, PhaseTab{}, nullptr, D.wsplit);
+      Vbar, nullptr, PhaseTab{}, nullptr, D.wsplit, ctx->nfe_e);
   PUFE_CUDA_TRY(cudaGetLastError());
   return PUFE_OK;
 }
@@ -765,7 +795,7 @@ pufe_status launch_assemble_fp64_bloch(pufe_ctx *ctx, const PhaseTab &ph, const 
   kern<<<fp64_items(ctx), ASM_NT, sm, st>>>(
       D.order, D.qoff, D.w, D.xi, D.doff, D.ecol, D.toff, D.psi, D.soff, D.smap, V,
       2.0 / ctx->h[0], 2.0 / ctx->h[1], 2.0 / ctx->h[2], npad, what, H, S, D.err, D.eshift, ph,
-      Hi, Si, D.wsplit, jit_of(ctx));
+      Hi, Si, D.wsplit, jit_of(ctx), ctx->nfe_e);
   PUFE_CUDA_TRY(cudaGetLastError());
   return PUFE_OK;
 }
@@ -777,9 +807,9 @@ pufe_status launch_density_fp64_bloch(pufe_ctx *ctx, const PhaseTab &ph, const d
   const int noccp = (nocc + 7) & ~7;
   const size_t sm = ((size_t)2 * ctx->max_basis * noccp + noccp) * sizeof(double);
   if (sm > 227 * 1024) return fail(PUFE_EINVAL, "n_e * nocc too large for the density kernel");
-  PUFE_CUDA_TRY(cudaFuncSetAttribute(k_density_fp64<true>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  k_density_fp64<true><<<(unsigned)ctx->nelem, DEN_NT, sm, st>>>(
+  auto kern = ctx->ser ? k_density_fp64<true, true> : k_density_fp64<true, false>;
+  PUFE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  kern<<<(unsigned)ctx->nelem, DEN_NT, sm, st>>>(
       D.order, D.qoff, D.xi, D.doff, D.dofs, D.ecol, D.toff, D.psi, Cr, ldc, f, nocc, noccp, rho,
       D.eshift, ph, Ci);
   PUFE_CUDA_TRY(cudaGetLastError());
@@ -798,7 +828,7 @@ pufe_status launch_adjoint_fp64_bloch(pufe_ctx *ctx, const PhaseTab &ph, const d
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
   k_adjoint_fp64<true><<<fp64_items(ctx), ADJ_NT, sm, st>>>(
       D.order, D.qoff, D.w, D.xi, D.doff, D.ecol, D.toff, D.psi, D.soff, D.smap, Hr, in_smem,
-      Vbar, D.eshift, ph, Hi, D.wsplit);
+      Vbar, D.eshift, ph, Hi, D.wsplit, ctx->nfe_e);
   PUFE_CUDA_TRY(cudaGetLastError());
   return PUFE_OK;
 }

@@ -106,6 +106,7 @@ struct DeviceArrays {
   int32_t *titems = nullptr;
   int32_t *sitems = nullptr;   // E-E kernel of S: (order index, first pair, end pair) triples
   int32_t *citems = nullptr;   // strip kernel: (order index, first cell, end cell) triples
+  int32_t *pitems = nullptr;   // FP32 density / per-point adjoint: (order index, first point, end point)
   int8_t *eeform = nullptr;   // per element: E x E form of the strip (0 model, 1 pair, 2 direct)
   unsigned *err = nullptr;    // device error flag
   // side stream and events: the FE-FE kernel of the mixed assembly runs on
@@ -126,6 +127,8 @@ struct pufe_ctx {
   double a[3] = {0, 0, 0};
   double h[3] = {0, 0, 0};
   bool general = false;        // a general (triclinic) cell: lat, Jit below
+  bool ser = false;            // FE space: cubic serendipity (32 columns) instead of tricubic
+  int nfe_e = 64;              // FE columns per element (64 tricubic, 32 serendipity)
   double lat[9] = {0};         // rows a_1, a_2, a_3 (general cells)
   double Jit[9] = {0};         // J^-T (general cells): physical gradient = Jit grad_xi
   int nel[3] = {0, 0, 0};
@@ -143,6 +146,7 @@ struct pufe_ctx {
   int n_titems = 0;           // items of the mixed path's list for the n_e > 128 elements
   int n_sitems = 0;           // items of the E-E overlap kernel's list (slot-pair ranges)
   int n_citems = 0;           // items of the strip kernel's list ((sub)cell ranges)
+  int n_pitems = 0;           // items of the FP32 per-point list (point ranges of every element)
   int max_part_p = 0;         // largest points-per-axis of any (sub)cell
   int strip_stage = 0;        // floats of the strip kernel's shared-memory stage
   uint32_t strip_pmask = 0;   // per-axis counts (bit p) of the strip kernel's cells
@@ -190,6 +194,52 @@ __host__ __device__ inline void lagrange3(double t, double L[4], double dL[4]) {
   dL[1] = 1.6875 * (c * d + a * d + a * c);
   dL[2] = -1.6875 * (b * d + a * d + a * b);
   dL[3] = 0.5625 * (b * c + a * c + a * b);
+}
+
+// Cubic serendipity hexahedron (32 nodes; the classical FE part of the
+// paper's PUFE runs, Sec. 6): its nodes are the tricubic nodes with at most
+// one index inner (the 8 vertices and two inner nodes per edge).  Column c
+// (0..31) is the local tricubic node ser_local(c) = a + 4 b + 16 c, in
+// ascending order.
+__host__ __device__ inline int ser_local(int c) {
+  constexpr unsigned char t[32] = {0,  1,  2,  3,  4,  7,  8,  11, 12, 13, 14,
+                                   15, 16, 19, 28, 31, 32, 35, 44, 47, 48, 49,
+                                   50, 51, 52, 55, 56, 59, 60, 61, 62, 63};
+  return t[c];
+}
+
+// Value and reference gradient of serendipity column c at xi:
+//   vertex s in {-1, 1}^3:  N = 1/64 prod_d (1 + s_d xi_d) (9 |xi|^2 - 19);
+//   inner node of an edge along axis d (coordinate t = -+1/3, the others
+//   s_e = -+1):  N = 9/64 (1 - xi_d^2) (1 + 9 t xi_d) prod_{e != d} (1 + s_e xi_e).
+__host__ __device__ inline void serendipity32(int c, const double xi[3], double &N, double g[3]) {
+  const int loc = ser_local(c);
+  const int idx[3] = {loc & 3, (loc >> 2) & 3, loc >> 4};
+  double nd[3];
+  int inner = -1;
+  for (int d = 0; d < 3; ++d) {
+    nd[d] = idx[d] == 0 ? -1.0 : (idx[d] == 1 ? -1.0 / 3.0 : (idx[d] == 2 ? 1.0 / 3.0 : 1.0));
+    if (idx[d] == 1 || idx[d] == 2) inner = d;
+  }
+  if (inner < 0) {
+    const double l0 = 1.0 + nd[0] * xi[0], l1 = 1.0 + nd[1] * xi[1], l2 = 1.0 + nd[2] * xi[2];
+    const double G = 9.0 * (xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2]) - 19.0;
+    const double P = l0 * l1 * l2;
+    N = P * G / 64.0;
+    g[0] = (nd[0] * l1 * l2 * G + P * 18.0 * xi[0]) / 64.0;
+    g[1] = (nd[1] * l0 * l2 * G + P * 18.0 * xi[1]) / 64.0;
+    g[2] = (nd[2] * l0 * l1 * G + P * 18.0 * xi[2]) / 64.0;
+    return;
+  }
+  const int d = inner, e1 = (d + 1) % 3, e2 = (d + 2) % 3;
+  const double t = nd[d], x = xi[d];
+  const double f = (1.0 - x * x) * (1.0 + 9.0 * t * x);
+  const double fp = -2.0 * x * (1.0 + 9.0 * t * x) + 9.0 * t * (1.0 - x * x);
+  const double l1 = 1.0 + nd[e1] * xi[e1], l2 = 1.0 + nd[e2] * xi[e2];
+  N = 9.0 / 64.0 * f * l1 * l2;
+  g[d] = 9.0 / 64.0 * fp * l1 * l2;
+  g[e1] = 9.0 / 64.0 * f * nd[e1] * l2;
+  g[e2] = 9.0 / 64.0 * f * l1 * nd[e2];
 }
 
 // Real solid harmonic r^l Y_lm(r^) (unit-normalised Y, no Condon-Shortley
@@ -359,6 +409,23 @@ struct PhaseTab {
   double re[8], im[8];
 };
 PhaseTab phase_table(const pufe_ctx *ctx, const double k[3]);
+// Cotangent of the FP32 adjoint kernels at a wavevector: the complex
+// Hbar + i Hi enters through the real element block
+// Re(conj(Hbar + i Hi)[g_i, g_j] exp(i k.(R_j - R_i))) (the derivative of
+// Re sum conj(Hbar) H(k)); Hi == nullptr is the Gamma point, Hbar real.
+struct BlochCot {
+  const double *Hi;
+  const uint8_t *eshift;   // shift code of every element column (sum n_e)
+  PhaseTab ph;
+};
+// entry of that block from the two CSR values and the columns' shift codes
+__host__ __device__ inline double cot_entry(double hr, double hi, int ci, int cj,
+                                            const PhaseTab &ph) {
+  if (ci == cj) return hr;
+  const double pr = ph.re[ci] * ph.re[cj] + ph.im[ci] * ph.im[cj];
+  const double pim = ph.re[ci] * ph.im[cj] - ph.im[ci] * ph.re[cj];
+  return hr * pr + hi * pim;
+}
 pufe_status launch_assemble_fp64_bloch(pufe_ctx *ctx, const PhaseTab &ph, const double *V,
                                        int what, double *H, double *Hi, double *S, double *Si,
                                        cudaStream_t s);
@@ -368,7 +435,9 @@ pufe_status launch_density_fp64_bloch(pufe_ctx *ctx, const PhaseTab &ph, const d
 pufe_status launch_adjoint_fp64_bloch(pufe_ctx *ctx, const PhaseTab &ph, const double *Hr,
                                       const double *Hi, double *Vbar, cudaStream_t s);
 pufe_status launch_tabulate_f32(pufe_ctx *ctx, cudaStream_t s);
-pufe_status launch_adjoint_tc(pufe_ctx *ctx, const double *Hbar, double *Vbar, cudaStream_t s);
+// FP32 adjoint; bc != nullptr: at a wavevector (complex cotangent)
+pufe_status launch_adjoint_tc(pufe_ctx *ctx, const double *Hbar, double *Vbar, cudaStream_t s,
+                              const BlochCot *bc = nullptr);
 // adds the FE-FE blocks of H (kinetic constants + V term; V == NULL: V = 0)
 pufe_status launch_fefe(pufe_ctx *ctx, const double *V, double *H, cudaStream_t s);
 pufe_status launch_strip_sf(pufe_ctx *ctx, const double *V, int what, double *H, double *S,
@@ -391,10 +460,16 @@ pufe_status launch_scf_step(pufe_ctx *ctx, int nstates, const double *eps, const
                             int64_t ldc, double nelec, double kT, double alpha, int pulay, int prec,
                             const double *rho_I, const double *V_eff_in, double *n, double *V_eff_out,
                             double *f_out, pufe_scf_info *info, cudaStream_t s);
+pufe_status launch_scf_step_bloch(pufe_ctx *ctx, int nk, const double *kpts, const double *wk,
+                                  int nstates, const double *eps, const double *const *C_re,
+                                  const double *const *C_im, int64_t ldc, double nelec, double kT,
+                                  double alpha, int pulay, int prec, const double *rho_I,
+                                  const double *V_eff_in, double *n, double *V_eff_out,
+                                  double *f_out, pufe_scf_info *info, cudaStream_t s);
 pufe_status launch_adjoint_fefe(pufe_ctx *ctx, const double *Hbar, double *Vbar, int first,
-                                int count, cudaStream_t s);
+                                int count, cudaStream_t s, const BlochCot &bc);
 pufe_status launch_adjoint_strip_sf(pufe_ctx *ctx, const double *Hbar, double *Vbar, int first,
-                                    int count, cudaStream_t s);
+                                    int count, cudaStream_t s, const BlochCot &bc);
 // S enrichment-enrichment block with FP64-class sums (mixed path): adds into S (and Si at
 // a wavevector: ph != nullptr) for every element, over the slot-pair work list
 pufe_status launch_see(pufe_ctx *ctx, const PhaseTab *ph, double *S, double *Si, cudaStream_t s);
@@ -410,7 +485,9 @@ pufe_status launch_assemble_tc_static(pufe_ctx *ctx, const double *V, int what, 
                                       double *S, cudaStream_t s);
 pufe_status launch_assemble_tc(pufe_ctx *ctx, const double *V, int what, double *H, double *S,
                                cudaStream_t s);
+// FP32 density; Ci != nullptr: Bloch states C + i Ci at the wavevector of ph
 pufe_status launch_density_tc(pufe_ctx *ctx, const double *C, int64_t ldc, const double *f,
-                              int nocc, double *rho, cudaStream_t s);
+                              int nocc, double *rho, cudaStream_t s, const double *Ci = nullptr,
+                              const PhaseTab *ph = nullptr);
 
 }  // namespace pufe

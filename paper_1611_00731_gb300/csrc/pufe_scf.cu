@@ -34,7 +34,8 @@ struct ScfState {
   double *b = nullptr, *t0 = nullptr, *t1 = nullptr;   // n_fe each
   double *n_out = nullptr, *vc = nullptr, *exc = nullptr, *vxc = nullptr;   // n_q each
   double *sums = nullptr;   // 8 reduction slots
-  double *f = nullptr;      // 64 occupations
+  double *f = nullptr;      // occupations: 64 states x up to 64 k-points (k-major)
+  double *nk = nullptr;     // n_q: one k-point's density (k-point steps)
   double *atoms = nullptr;  // 5 per atom: tau (3), Z, sigma
   int atoms_cap = 0;
   double e_self = 0.0;      // self-energy of the last ionic charge set
@@ -549,7 +550,7 @@ pufe_status scf_prepare(pufe_ctx *ctx) {
   PUFE_CUDA_TRY(cudaMalloc((void **)&S->exc, nq));
   PUFE_CUDA_TRY(cudaMalloc((void **)&S->vxc, nq));
   PUFE_CUDA_TRY(cudaMalloc((void **)&S->sums, 8 * sizeof(double)));
-  PUFE_CUDA_TRY(cudaMalloc((void **)&S->f, 64 * sizeof(double)));
+  PUFE_CUDA_TRY(cudaMalloc((void **)&S->f, 64 * 64 * sizeof(double)));
   return PUFE_OK;
 }
 
@@ -557,7 +558,7 @@ void scf_free(pufe_ctx *ctx) {
   ScfState *S = ctx->scf;
   if (!S) return;
   void *ptrs[] = {S->X[0], S->X[1], S->X[2], S->lam[0], S->lam[1], S->lam[2], S->b, S->t0,
-                  S->t1, S->n_out, S->vc, S->exc, S->vxc, S->sums, S->f, S->atoms,
+                  S->t1, S->n_out, S->vc, S->exc, S->vxc, S->sums, S->f, S->nk, S->atoms,
                   S->hist_n, S->hist_R, S->dots};
   for (void *p : ptrs)
     if (p) cudaFree(p);
@@ -639,53 +640,117 @@ void scf_reset(pufe_ctx *ctx) {
   ctx->scf->next_slot = 0;
 }
 
+// Fermi-Dirac occupations of nk k-points x nstates states (eps and f
+// k-major) with weights wk (nullptr: one k-point of weight 1): mu by bisection
+// on sum_k w_k sum_n f_nk = nelec; the band energy and the entropy sum
+// sum_k w_k sum_n [g ln g + (1 - g) ln(1 - g)] (g = f / 2) weighted alike.
+static double occupations(int nk, const double *wk, int nstates, const double *eps, double nelec,
+                          double kT, std::vector<double> &f, double &e_band, double &ts) {
+  const int nt = nk * nstates;
+  double lo = eps[0], hi = eps[0];
+  for (int k = 1; k < nt; ++k) {
+    lo = std::min(lo, eps[k]);
+    hi = std::max(hi, eps[k]);
+  }
+  lo -= 50.0 * kT + 1.0;
+  hi += 50.0 * kT + 1.0;
+  f.assign(nt, 0.0);
+  auto occ = [&](double mu) {
+    double s = 0.0;
+    for (int k = 0; k < nt; ++k) {
+      const double x = std::min(700.0, std::max(-700.0, (eps[k] - mu) / kT));
+      f[k] = 2.0 / (1.0 + std::exp(x));
+      s += (wk ? wk[k / nstates] : 1.0) * f[k];
+    }
+    return s;
+  };
+  for (int it = 0; it < 200; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (occ(mid) < nelec)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  const double mu = 0.5 * (lo + hi);
+  occ(mu);
+  e_band = 0.0;
+  ts = 0.0;
+  for (int k = 0; k < nt; ++k) {
+    const double w = wk ? wk[k / nstates] : 1.0;
+    e_band += w * f[k] * eps[k];
+    const double g = f[k] / 2.0;
+    if (g > 1e-300 && g < 1.0 - 1e-16) ts += w * (g * std::log(g) + (1.0 - g) * std::log1p(-g));
+  }
+  ts *= -2.0;
+  return mu;
+}
+
+static pufe_status scf_finish(pufe_ctx *ctx, double mu, double e_band, double ts, double kT,
+                              double alpha, int pulay, const double *rho_I,
+                              const double *V_eff_in, double *n, double *V_eff_out,
+                              pufe_scf_info *info, cudaStream_t st);
+
 pufe_status launch_scf_step(pufe_ctx *ctx, int nstates, const double *eps, const double *C,
                             int64_t ldc, double nelec, double kT, double alpha, int pulay, int prec,
                             const double *rho_I, const double *V_eff_in, double *n, double *V_eff_out,
                             double *f_out, pufe_scf_info *info, cudaStream_t st) {
   if (pufe_status e0 = scf_prepare(ctx)) return e0;
   ScfState *S = ctx->scf;
-  // Fermi-Dirac occupations, mu by bisection on sum f = N_e
-  double lo = eps[0], hi = eps[0];
-  for (int k = 1; k < nstates; ++k) {
-    lo = std::min(lo, eps[k]);
-    hi = std::max(hi, eps[k]);
-  }
-  lo -= 50.0 * kT + 1.0;
-  hi += 50.0 * kT + 1.0;
-  auto occ = [&](double mu, std::vector<double> &f) {
-    double s = 0.0;
-    for (int k = 0; k < nstates; ++k) {
-      const double x = std::min(700.0, std::max(-700.0, (eps[k] - mu) / kT));
-      f[k] = 2.0 / (1.0 + std::exp(x));
-      s += f[k];
-    }
-    return s;
-  };
-  std::vector<double> f(nstates);
-  for (int it = 0; it < 200; ++it) {
-    const double mid = 0.5 * (lo + hi);
-    if (occ(mid, f) < nelec)
-      lo = mid;
-    else
-      hi = mid;
-  }
-  const double mu = 0.5 * (lo + hi);
-  occ(mu, f);
+  std::vector<double> f;
   double e_band = 0.0, ts = 0.0;
-  for (int k = 0; k < nstates; ++k) {
-    e_band += f[k] * eps[k];
-    const double g = f[k] / 2.0;
-    if (g > 1e-300 && g < 1.0 - 1e-16) ts += g * std::log(g) + (1.0 - g) * std::log1p(-g);
-  }
-  ts *= -2.0;
+  const double mu = occupations(1, nullptr, nstates, eps, nelec, kT, f, e_band, ts);
   if (f_out) std::copy(f.begin(), f.end(), f_out);
   PUFE_CUDA_TRY(cudaMemcpyAsync(S->f, f.data(), nstates * sizeof(double), cudaMemcpyHostToDevice, st));
-  // n_out, then V_C[n_out] and eps_xc(n_out)
   pufe_status e1 = (prec == PUFE_FP64)
                        ? launch_density_fp64(ctx, C, ldc, S->f, nstates, S->n_out, st)
                        : launch_density_tc(ctx, C, ldc, S->f, nstates, S->n_out, st);
   if (e1 != PUFE_OK) return e1;
+  return scf_finish(ctx, mu, e_band, ts, kT, alpha, pulay, rho_I, V_eff_in, n, V_eff_out, info, st);
+}
+
+pufe_status launch_scf_step_bloch(pufe_ctx *ctx, int nk, const double *kpts, const double *wk,
+                                  int nstates, const double *eps, const double *const *C_re,
+                                  const double *const *C_im, int64_t ldc, double nelec, double kT,
+                                  double alpha, int pulay, int prec, const double *rho_I,
+                                  const double *V_eff_in, double *n, double *V_eff_out,
+                                  double *f_out, pufe_scf_info *info, cudaStream_t st) {
+  if (pufe_status e0 = scf_prepare(ctx)) return e0;
+  ScfState *S = ctx->scf;
+  if (!S->nk) PUFE_CUDA_TRY(cudaMalloc((void **)&S->nk, (size_t)ctx->nq * sizeof(double)));
+  std::vector<double> f;
+  double e_band = 0.0, ts = 0.0;
+  const double mu = occupations(nk, wk, nstates, eps, nelec, kT, f, e_band, ts);
+  if (f_out) std::copy(f.begin(), f.end(), f_out);
+  // n_out = sum_k w_k sum_n f_nk |psi_nk|^2: each k's density with the
+  // occupations w_k f_nk, added into n_out
+  std::vector<double> fw(f.size());
+  for (size_t i = 0; i < f.size(); ++i) fw[i] = wk[i / nstates] * f[i];
+  PUFE_CUDA_TRY(cudaMemcpyAsync(S->f, fw.data(), fw.size() * sizeof(double), cudaMemcpyHostToDevice,
+                                st));
+  for (int i = 0; i < nk; ++i) {
+    const PhaseTab ph = phase_table(ctx, kpts + 3 * i);
+    double *out = i == 0 ? S->n_out : S->nk;
+    const double *fk = S->f + (size_t)i * nstates;
+    pufe_status e1 = (prec == PUFE_FP64)
+                         ? launch_density_fp64_bloch(ctx, ph, C_re[i], C_im[i], ldc, fk, nstates,
+                                                     out, st)
+                         : launch_density_tc(ctx, C_re[i], ldc, fk, nstates, out, st, C_im[i], &ph);
+    if (e1 != PUFE_OK) return e1;
+    if (i > 0) {
+      k_add<<<blocks(ctx->nq, 256), 256, 0, st>>>(ctx->nq, S->n_out, S->nk, S->n_out);
+      PUFE_CUDA_TRY(cudaGetLastError());
+    }
+  }
+  return scf_finish(ctx, mu, e_band, ts, kT, alpha, pulay, rho_I, V_eff_in, n, V_eff_out, info, st);
+}
+
+// the part of an SCF step after the output density S->n_out: V_C[n_out] and
+// eps_xc(n_out), the energies, mixing into n and the new potential
+static pufe_status scf_finish(pufe_ctx *ctx, double mu, double e_band, double ts, double kT,
+                              double alpha, int pulay, const double *rho_I,
+                              const double *V_eff_in, double *n, double *V_eff_out,
+                              pufe_scf_info *info, cudaStream_t st) {
+  ScfState *S = ctx->scf;
   if (pufe_status e2 = coulomb(ctx, S->n_out, rho_I, S->vc, st)) return e2;
   k_xc<<<blocks(ctx->nq, 256), 256, 0, st>>>(ctx->nq, S->n_out, S->exc, nullptr);
   PUFE_CUDA_TRY(cudaMemsetAsync(S->sums, 0, 8 * sizeof(double), st));

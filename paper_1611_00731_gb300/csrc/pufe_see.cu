@@ -39,7 +39,7 @@
 namespace pufe {
 namespace {
 
-constexpr int SE_NT = 128;
+constexpr int SE_NT = 256;
 
 // an unevaluated sum hi + lo of two FP32 numbers (|lo| <= ulp(hi) / 2)
 struct ff {
@@ -100,11 +100,13 @@ __global__ void __launch_bounds__(SE_NT) k_see(
   }
   // shared memory: U [3 axes][u_0, u_1, u_2][pm] pairs | work pairs
   //                | stage [slot][point] floats | scol [slot][vertex] | pairs
+  //                | masks [pair][2]
   ff *U = reinterpret_cast<ff *>(sm_see4);
   ff *work = U + 9 * pm;
   float *stg = reinterpret_cast<float *>(work + work_ff);
   int *scol = reinterpret_cast<int *>(stg + stage_f);
   int *pairs = scol + amax * 8;
+  int *msk = pairs + amax * (amax + 1) / 2;
   __shared__ double s_phr[8], s_phi[8];
   if (BLOCH && tid < 8) {
     s_phr[tid] = ph.re[tid];
@@ -125,6 +127,27 @@ __global__ void __launch_bounds__(SE_NT) k_see(
   if (tid < A) {   // pairs (alpha, beta), alpha <= beta, alpha-major
     int k = tid * A - tid * (tid - 1) / 2;
     for (int b = tid; b < A; ++b) pairs[k++] = tid | (b << 8);
+  }
+  __syncthreads();
+  // the projections a pair's existing vertex pairs use: kz (3 bits) and
+  // (kz, ky) (9 bits) in msk[2 g], (kz, ky, kx) (27 bits) in msk[2 g + 1];
+  // the stages skip the others (slots with few vertex columns need few)
+  for (int g = pb + tid; g < pe_; g += SE_NT) {
+    const int pr = pairs[g], al = pr & 0xff, be = pr >> 8;
+    int mz = 0, myz = 0, mxyz = 0;
+    for (int i = 0; i < 8; ++i) {
+      if (scol[al * 8 + i] < 0) continue;
+      for (int j = al == be ? i : 0; j < 8; ++j) {
+        if (scol[be * 8 + j] < 0) continue;
+        const int kx = (i & 1) + (j & 1), ky = ((i >> 1) & 1) + ((j >> 1) & 1),
+                  kz = (i >> 2) + (j >> 2);
+        mz |= 1 << kz;
+        myz |= 1 << (kz * 3 + ky);
+        mxyz |= 1 << ((kz * 3 + ky) * 3 + kx);
+      }
+    }
+    msk[2 * g] = mz | (myz << 3);
+    msk[2 * g + 1] = mxyz;
   }
   const float *pe = psi + 4 * toff32[e];
   const float4 *qe = qdat + qpoff[e];
@@ -175,14 +198,15 @@ __global__ void __launch_bounds__(SE_NT) k_see(
       for (int it = tid; it < nc * p2; it += SE_NT) {
         const int g = it / p2, qxy = it - g * p2;
         const int pr = pairs[c0 + g], al = pr & 0xff, be = pr >> 8;
+        const int mz = msk[2 * (c0 + g)] & 7;
         ff a0 = {0.0f, 0.0f}, a1 = {0.0f, 0.0f}, a2 = {0.0f, 0.0f};
         for (int qz = 0; qz < p; ++qz) {
           const int lq = qxy + p2 * qz;
           const ff f = staged ? ff_prod(stg[al * p3 + lq], stg[be * p3 + lq])
                               : ff_prod(sval(al, lq), sval(be, lq));
-          a0 = ff_fma(f, U[6 * pm + qz], a0);
-          a1 = ff_fma(f, U[7 * pm + qz], a1);
-          a2 = ff_fma(f, U[8 * pm + qz], a2);
+          if (mz & 1) a0 = ff_fma(f, U[6 * pm + qz], a0);
+          if (mz & 2) a1 = ff_fma(f, U[7 * pm + qz], a1);
+          if (mz & 4) a2 = ff_fma(f, U[8 * pm + qz], a2);
         }
         ff *t1 = T1 + (size_t)it * 3;
         t1[0] = ff_norm(a0);
@@ -193,13 +217,15 @@ __global__ void __launch_bounds__(SE_NT) k_see(
       // y: one thread per (pair, qx, kz)
       for (int it = tid; it < nc * p * 3; it += SE_NT) {
         const int g = it / (3 * p), rem = it - g * 3 * p, qx = rem / 3, kz = rem - qx * 3;
+        const int my = (msk[2 * (c0 + g)] >> (3 + 3 * kz)) & 7;
+        if (!my) continue;
         const ff *t1 = T1 + ((size_t)g * p2 + qx) * 3 + kz;
         ff b0 = {0.0f, 0.0f}, b1 = {0.0f, 0.0f}, b2 = {0.0f, 0.0f};
         for (int qy = 0; qy < p; ++qy) {
           const ff t = t1[qy * p * 3];
-          b0 = ff_fma(t, U[3 * pm + qy], b0);
-          b1 = ff_fma(t, U[4 * pm + qy], b1);
-          b2 = ff_fma(t, U[5 * pm + qy], b2);
+          if (my & 1) b0 = ff_fma(t, U[3 * pm + qy], b0);
+          if (my & 2) b1 = ff_fma(t, U[4 * pm + qy], b1);
+          if (my & 4) b2 = ff_fma(t, U[5 * pm + qy], b2);
         }
         ff *t2 = T2 + ((size_t)g * p + qx) * 9 + kz * 3;
         t2[0] = ff_norm(b0);
@@ -210,13 +236,15 @@ __global__ void __launch_bounds__(SE_NT) k_see(
       // x: one thread per (pair, kz, ky)
       for (int it = tid; it < nc * 9; it += SE_NT) {
         const int g = it / 9, j = it - g * 9;
+        const int mx = (msk[2 * (c0 + g) + 1] >> (3 * j)) & 7;
+        if (!mx) continue;
         const ff *t2 = T2 + (size_t)g * p * 9 + j;
         ff c0v = {0.0f, 0.0f}, c1v = {0.0f, 0.0f}, c2v = {0.0f, 0.0f};
         for (int qx = 0; qx < p; ++qx) {
           const ff t = t2[qx * 9];
-          c0v = ff_fma(t, U[qx], c0v);
-          c1v = ff_fma(t, U[pm + qx], c1v);
-          c2v = ff_fma(t, U[2 * pm + qx], c2v);
+          if (mx & 1) c0v = ff_fma(t, U[qx], c0v);
+          if (mx & 2) c1v = ff_fma(t, U[pm + qx], c1v);
+          if (mx & 4) c2v = ff_fma(t, U[2 * pm + qx], c2v);
         }
         ff *pp = P + g * 27 + j * 3;
         pp[0] = ff_norm(c0v);
@@ -276,7 +304,7 @@ pufe_status launch_see(pufe_ctx *ctx, const PhaseTab *ph, double *S, double *Si,
   int stage = 0;
   for (int64_t e = 0; e < ctx->nelem; ++e)
     if (ctx->see_stage[e] <= SEE_STAGE_MAX_F) stage = std::max(stage, (int)ctx->see_stage[e]);
-  const size_t ints = (size_t)amax * 8 + (size_t)amax * (amax + 1) / 2;
+  const size_t ints = (size_t)amax * 8 + (size_t)3 * amax * (amax + 1) / 2;
   const size_t sm = ((size_t)9 * pm + work) * sizeof(ff) + (size_t)stage * sizeof(float) +
                     ints * sizeof(int);
   if (sm > 227 * 1024) return fail(PUFE_EINVAL, "E-E overlap kernel: shared memory above 227 KB");

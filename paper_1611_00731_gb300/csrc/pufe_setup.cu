@@ -263,6 +263,142 @@ static void hadapt(Setup &S, const std::vector<int> &alphas, const Box &b, int d
       }
 }
 
+// ---- the adaptive tests on the GPU (Sec. 5.2) ---------------------------------
+// One test is the pair of integrals I(Psi^2), I(|grad Psi|^2) of one
+// enrichment on one box with the p^3 Gauss rule, exactly as box_integrals
+// forms them on the host (same points, weights and integrands); the tests of
+// a whole level of the adaptive construction run as one launch, one CTA per
+// test, each thread summing a strided subset of the points and the CTA
+// reducing them in a fixed tree order.  The decisions (which p, which
+// integrands fail, which cells split) stay with the host, on these values.
+struct RuleTest {
+  double lo[3], hi[3];   // box (reference cube of the element for general cells)
+  double x0[3];          // element corner (general cells)
+  int alpha, p;
+};
+
+struct Jmat {
+  double m[9];
+};
+
+constexpr int RT_NT = 128;
+constexpr int RT_PMAX = 18;   // largest Gauss order of the tests (PADAPT reads p_max + 2)
+
+__global__ void __launch_bounds__(RT_NT) k_rule_tests(
+    const RuleTest *__restrict__ tests, const Orbital *__restrict__ orb,
+    const double *__restrict__ gtab, double a0, double a1, double a2, int i0, int i1, int i2,
+    int gen, LatticeDev lat, Jmat J, double detJ, double *__restrict__ out) {
+  __shared__ double r0[RT_NT], r1[RT_NT];
+  const RuleTest T = tests[blockIdx.x];
+  const int p = T.p, p2 = p * p, p3 = p2 * p;
+  const double *gx = gtab + (size_t)p * 2 * RT_PMAX, *gw = gx + RT_PMAX;
+  const Orbital o = orb[T.alpha];
+  const double av[3] = {a0, a1, a2};
+  const int img[3] = {i0, i1, i2};
+  double half[3], mid[3];
+  for (int k = 0; k < 3; ++k) {
+    half[k] = 0.5 * (T.hi[k] - T.lo[k]);
+    mid[k] = 0.5 * (T.hi[k] + T.lo[k]);
+  }
+  double s0 = 0.0, s1 = 0.0;
+  for (int k = threadIdx.x; k < p3; k += RT_NT) {
+    const int kz = k / p2, ky = (k - kz * p2) / p, kx = k - kz * p2 - ky * p;
+    const double pt[3] = {mid[0] + half[0] * gx[kx], mid[1] + half[1] * gx[ky],
+                          mid[2] + half[2] * gx[kz]};
+    double wt = gw[kx] * gw[ky] * gw[kz] * half[0] * half[1] * half[2];
+    double psi, g[3];
+    if (gen) {
+      double x[3];
+      for (int r = 0; r < 3; ++r)
+        x[r] = T.x0[r] + J.m[3 * r] * (pt[0] + 1.0) + J.m[3 * r + 1] * (pt[1] + 1.0) +
+               J.m[3 * r + 2] * (pt[2] + 1.0);
+      enrichment_eval_lat(o, x, lat, psi, g);
+      wt *= detJ;
+    } else {
+      enrichment_eval(o, pt, av, img, psi, g);
+    }
+    s0 += wt * psi * psi;
+    s1 += wt * (g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+  }
+  r0[threadIdx.x] = s0;
+  r1[threadIdx.x] = s1;
+  __syncthreads();
+  for (int w = RT_NT / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) {
+      r0[threadIdx.x] += r0[threadIdx.x + w];
+      r1[threadIdx.x] += r1[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[2 * (size_t)blockIdx.x] = r0[0];
+    out[2 * (size_t)blockIdx.x + 1] = r1[0];
+  }
+}
+
+// Run `tests` on the current device; out[2 t], out[2 t + 1] receive test t's
+// integrals.  Blocking; allocates and frees its own device arrays.
+static pufe_status device_rule_tests(const Setup &S, const std::vector<RuleTest> &tests,
+                                     std::vector<double> &out) {
+  out.assign(2 * tests.size(), 0.0);
+  if (tests.empty()) return PUFE_OK;
+  for (const RuleTest &t : tests)
+    if (t.p < 1 || t.p > RT_PMAX || t.alpha < 0 || t.alpha >= (int)S.orb.size())
+      return fail(PUFE_EINVAL, "internal: bad adaptive test");
+  std::vector<double> gtab((size_t)(RT_PMAX + 1) * 2 * RT_PMAX, 0.0);
+  for (int p = 1; p <= RT_PMAX && p < (int)S.gx.size(); ++p)
+    for (int i = 0; i < p; ++i) {
+      gtab[(size_t)p * 2 * RT_PMAX + i] = S.gx[p][i];
+      gtab[(size_t)p * 2 * RT_PMAX + RT_PMAX + i] = S.gw[p][i];
+    }
+  RuleTest *dt = nullptr;
+  Orbital *dorb = nullptr;
+  double *dg = nullptr, *dout = nullptr;
+  auto release = [&]() {
+    if (dt) cudaFree(dt);
+    if (dorb) cudaFree(dorb);
+    if (dg) cudaFree(dg);
+    if (dout) cudaFree(dout);
+  };
+  auto check = [&](cudaError_t e, const char *what) -> pufe_status {
+    if (e == cudaSuccess) return PUFE_OK;
+    release();
+    return cuda_fail(e, what);
+  };
+  pufe_status st;
+  if ((st = check(cudaMalloc((void **)&dt, tests.size() * sizeof(RuleTest)), "cudaMalloc")))
+    return st;
+  if ((st = check(cudaMalloc((void **)&dorb, std::max<size_t>(1, S.orb.size()) * sizeof(Orbital)),
+                  "cudaMalloc")))
+    return st;
+  if ((st = check(cudaMalloc((void **)&dg, gtab.size() * sizeof(double)), "cudaMalloc"))) return st;
+  if ((st = check(cudaMalloc((void **)&dout, out.size() * sizeof(double)), "cudaMalloc")))
+    return st;
+  if ((st = check(cudaMemcpy(dt, tests.data(), tests.size() * sizeof(RuleTest),
+                             cudaMemcpyHostToDevice), "cudaMemcpy")))
+    return st;
+  if ((st = check(cudaMemcpy(dorb, S.orb.data(), S.orb.size() * sizeof(Orbital),
+                             cudaMemcpyHostToDevice), "cudaMemcpy")))
+    return st;
+  if ((st = check(cudaMemcpy(dg, gtab.data(), gtab.size() * sizeof(double),
+                             cudaMemcpyHostToDevice), "cudaMemcpy")))
+    return st;
+  Jmat J;
+  for (int k = 0; k < 9; ++k) J.m[k] = S.J[k];
+  const size_t chunk = (size_t)1 << 30;
+  for (size_t t0 = 0; t0 < tests.size(); t0 += chunk) {
+    const unsigned nb = (unsigned)std::min(chunk, tests.size() - t0);
+    k_rule_tests<<<nb, RT_NT>>>(dt + t0, dorb, dg, S.a[0], S.a[1], S.a[2], S.img[0], S.img[1],
+                                S.img[2], S.gen ? 1 : 0, S.lat, J, S.detJ, dout + 2 * t0);
+    if ((st = check(cudaGetLastError(), "k_rule_tests launch"))) return st;
+  }
+  if ((st = check(cudaMemcpy(out.data(), dout, out.size() * sizeof(double),
+                             cudaMemcpyDeviceToHost), "cudaMemcpy (adaptive tests)")))
+    return st;
+  release();
+  return PUFE_OK;
+}
+
 static void parallel_for(int64_t n, const std::function<void(int64_t)> &fn) {
   unsigned nt = std::max(1u, std::thread::hardware_concurrency());
   nt = (unsigned)std::min<int64_t>(nt, std::max<int64_t>(1, n));
@@ -322,6 +458,10 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
     return fail(PUFE_EINVAL, "HADAPT needs 0 <= max_depth <= 4 and p_far in [1, 16]");
   if (quad->mode != PUFE_QUAD_FIXED && !(quad->tol > 0.0))
     return fail(PUFE_EINVAL, "adaptive tolerance must be > 0");
+  if (cell->fe_space != PUFE_FE_LAGRANGE64 && cell->fe_space != PUFE_FE_SERENDIPITY32)
+    return fail(PUFE_EINVAL, "unknown FE space");
+  const bool ser = cell->fe_space == PUFE_FE_SERENDIPITY32;
+  const int nfe_e = ser ? 32 : 64;
 
   Setup S;
   double rc_max = 0.0;
@@ -410,7 +550,20 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
   const int64_t nelem = (int64_t)nx * ny * nz;
   const int64_t nv = nelem;
   const int mx = 3 * nx, my = 3 * ny, mz = 3 * nz;
-  const int64_t n_fe = (int64_t)mx * my * mz;
+  // FE DOFs: the nodes of the periodic (3 nx)(3 ny)(3 nz) grid; for the
+  // serendipity space only those with at most one coordinate off the vertex
+  // planes, numbered compactly in grid order (gmap: grid index -> DOF)
+  std::vector<int32_t> gmap;
+  int64_t n_fe = (int64_t)mx * my * mz;
+  if (ser) {
+    gmap.assign((size_t)n_fe, -1);
+    int64_t k = 0;
+    for (int64_t g = 0; g < (int64_t)mx * my * mz; ++g) {
+      const int64_t gx = g % mx, gy = (g / mx) % my, gz = g / ((int64_t)mx * my);
+      if ((gx % 3 != 0) + (gy % 3 != 0) + (gz % 3 != 0) <= 1) gmap[g] = (int32_t)k++;
+    }
+    n_fe = k;
+  }
   const int natoms = cell->natoms;
 
   // the element's box: physical for orthorhombic cells, the reference cube
@@ -544,6 +697,137 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
 
   // ---- quadrature rules ----------------------------------------------------
   std::vector<std::vector<RulePart>> rule(nelem);
+  if (quad->device_tests && quad->mode != PUFE_QUAD_FIXED) {
+    // the integrals of the adaptive tests on the GPU, one launch per order
+    // set (PADAPT) or per subdivision level (HADAPT); same decisions, points
+    // and order as the host construction below
+    int ndev0 = 0;
+    if (cudaGetDeviceCount(&ndev0) != cudaSuccess || ndev0 == 0) {
+      cudaGetLastError();
+      return fail(PUFE_ECUDA, "quad.device_tests needs a CUDA device");
+    }
+    auto make_test = [&](int64_t e, const Box &b, int alpha, int p) {
+      RuleTest t;
+      for (int k = 0; k < 3; ++k) {
+        t.lo[k] = b.lo[k];
+        t.hi[k] = b.hi[k];
+        t.x0[k] = 0.0;
+      }
+      if (S.gen) origin(e, t.x0);
+      t.alpha = alpha;
+      t.p = p;
+      return t;
+    };
+    std::vector<double> out;
+    pufe_status st0;
+    if (quad->mode == PUFE_QUAD_PADAPT) {
+      const int p0 = quad->p_min, p1 = quad->p_max + 2;
+      std::vector<RuleTest> tests;
+      std::vector<int64_t> first(nelem + 1, 0);
+      for (int64_t e = 0; e < nelem; ++e) {
+        first[e] = (int64_t)tests.size();
+        const Box b = elem_box(e);
+        for (int p = p0; p <= p1; ++p)
+          for (int al : ealpha[e]) tests.push_back(make_test(e, b, al, p));
+      }
+      first[nelem] = (int64_t)tests.size();
+      if ((st0 = device_rule_tests(S, tests, out)) != PUFE_OK) return st0;
+      for (int64_t e = 0; e < nelem; ++e) {
+        const Box b = elem_box(e);
+        const int64_t A = (int64_t)ealpha[e].size();
+        if (A == 0) {
+          rule[e].push_back({b, quad->p_min});
+          continue;
+        }
+        // I_p of integrand i (2 per enrichment) of element e
+        auto I = [&](int p, int64_t i) { return out[2 * (first[e] + (p - p0) * A) + i]; };
+        int chosen = quad->p_max;
+        for (int p = quad->p_min; p <= quad->p_max; ++p) {
+          bool ok = true;
+          for (int64_t i = 0; i < 2 * A; ++i) ok = ok && (std::fabs(I(p, i) - I(p + 2, i)) < quad->tol);
+          if (ok) {
+            chosen = p;
+            break;
+          }
+        }
+        rule[e].push_back({b, chosen});
+      }
+    } else {
+      // HADAPT: a tree per element, tested level by level; leaves emitted
+      // depth first in the host's child order a + 2 b + 4 c
+      struct Node {
+        int64_t e;
+        Box b;
+        std::vector<int> al;
+        int depth, child0;
+      };
+      std::vector<Node> nodes;
+      std::vector<int64_t> root(nelem, -1);
+      std::vector<int64_t> level;
+      for (int64_t e = 0; e < nelem; ++e) {
+        if (ealpha[e].empty()) continue;
+        root[e] = (int64_t)nodes.size();
+        level.push_back(root[e]);
+        nodes.push_back(Node{e, elem_box(e), ealpha[e], 0, -1});
+      }
+      while (!level.empty()) {
+        std::vector<RuleTest> tests;
+        std::vector<int64_t> first;
+        for (int64_t id : level) {
+          first.push_back((int64_t)tests.size());
+          for (int al : nodes[id].al) {
+            tests.push_back(make_test(nodes[id].e, nodes[id].b, al, 5));
+            tests.push_back(make_test(nodes[id].e, nodes[id].b, al, 8));
+          }
+        }
+        if ((st0 = device_rule_tests(S, tests, out)) != PUFE_OK) return st0;
+        std::vector<int64_t> next;
+        for (size_t j = 0; j < level.size(); ++j) {
+          const int64_t id = level[j];
+          std::vector<int> failing;
+          for (size_t ia = 0; ia < nodes[id].al.size(); ++ia) {
+            const double *i5 = &out[2 * (first[j] + 2 * (int64_t)ia)], *i8 = i5 + 2;
+            if (std::fabs(i5[0] - i8[0]) >= quad->tol || std::fabs(i5[1] - i8[1]) >= quad->tol)
+              failing.push_back(nodes[id].al[ia]);
+          }
+          if (failing.empty() || nodes[id].depth >= quad->max_depth) continue;
+          const Box pb = nodes[id].b;
+          double mid[3];
+          for (int k = 0; k < 3; ++k) mid[k] = 0.5 * (pb.lo[k] + pb.hi[k]);
+          nodes[id].child0 = (int)nodes.size();
+          const int64_t e = nodes[id].e;
+          const int depth = nodes[id].depth + 1;
+          for (int c = 0; c < 2; ++c)
+            for (int bb = 0; bb < 2; ++bb)
+              for (int a = 0; a < 2; ++a) {
+                const int off[3] = {a, bb, c};
+                Box ch;
+                for (int k = 0; k < 3; ++k) {
+                  ch.lo[k] = off[k] == 0 ? pb.lo[k] : mid[k];
+                  ch.hi[k] = off[k] == 0 ? mid[k] : pb.hi[k];
+                }
+                next.push_back((int64_t)nodes.size());
+                nodes.push_back(Node{e, ch, failing, depth, -1});
+              }
+        }
+        level.swap(next);
+      }
+      for (int64_t e = 0; e < nelem; ++e) {
+        if (root[e] < 0) {
+          rule[e].push_back({elem_box(e), quad->p_far});
+          continue;
+        }
+        std::function<void(int64_t)> emit = [&](int64_t id) {
+          if (nodes[id].child0 < 0) {
+            rule[e].push_back({nodes[id].b, 8});
+            return;
+          }
+          for (int c = 0; c < 8; ++c) emit(nodes[id].child0 + c);
+        };
+        emit(root[e]);
+      }
+    }
+  } else
   parallel_for(nelem, [&](int64_t e) {
     Box b = elem_box(e);
     double x0v[3];
@@ -631,7 +915,7 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
   std::vector<int32_t> aoff(nelem + 1, 0);
   std::vector<int32_t> n_e(nelem), q_e(nelem);
   for (int64_t e = 0; e < nelem; ++e) {
-    n_e[e] = 64 + (int32_t)cols[e].size();
+    n_e[e] = nfe_e + (int32_t)cols[e].size();
     q_e[e] = (int32_t)(qoff[e + 1] - qoff[e]);
     doff[e + 1] = doff[e] + n_e[e];
     aoff[e + 1] = aoff[e] + (int32_t)ealpha[e].size();
@@ -647,7 +931,7 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
   std::vector<float4> qdat(qpoff[nelem]);
   std::vector<float> ptab(32 * qpoff[nelem], 0.0f);
   std::vector<float> eorig(8 * aoff[nelem], 0.0f);
-  std::vector<int32_t> dofs(doff[nelem]), ecol(doff[nelem] - 64 * nelem), alist(aoff[nelem]);
+  std::vector<int32_t> dofs(doff[nelem]), ecol(doff[nelem] - nfe_e * nelem), alist(aoff[nelem]);
   // lattice shift of every element column's node or vertex (bit d: one cell
   // along axis d), for the Bloch phases at k != 0
   std::vector<uint8_t> eshift(doff[nelem]);
@@ -655,15 +939,15 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
   for (int64_t e = 0; e < nelem; ++e) {
     int ex = (int)(e % nx), ey = (int)((e / nx) % ny), ez = (int)(e / ((int64_t)nx * ny));
     int32_t *d = &dofs[doff[e]];
-    for (int c = 0; c < 4; ++c)
-      for (int b = 0; b < 4; ++b)
-        for (int a = 0; a < 4; ++a) {
-          int64_t gx = (3 * ex + a) % mx, gy = (3 * ey + b) % my, gz = (3 * ez + c) % mz;
-          d[a + 4 * b + 16 * c] = (int32_t)(gx + mx * (gy + (int64_t)my * gz));
-          eshift[doff[e] + a + 4 * b + 16 * c] =
-              (uint8_t)((3 * ex + a >= mx ? 1 : 0) | (3 * ey + b >= my ? 2 : 0) |
-                        (3 * ez + c >= mz ? 4 : 0));
-        }
+    for (int j = 0; j < nfe_e; ++j) {   // FE columns: local node a + 4 b + 16 c
+      const int loc = ser ? ser_local(j) : j;
+      const int a = loc & 3, b = (loc >> 2) & 3, c = loc >> 4;
+      const int64_t gx = (3 * ex + a) % mx, gy = (3 * ey + b) % my, gz = (3 * ez + c) % mz;
+      const int64_t g = gx + mx * (gy + (int64_t)my * gz);
+      d[j] = ser ? gmap[g] : (int32_t)g;
+      eshift[doff[e] + j] = (uint8_t)((3 * ex + a >= mx ? 1 : 0) | (3 * ey + b >= my ? 2 : 0) |
+                                      (3 * ez + c >= mz ? 4 : 0));
+    }
     for (size_t k = 0; k < ealpha[e].size(); ++k) {
       alist[aoff[e] + k] = ealpha[e][k];
       // element origin minus the nearest image of the atom, split hi + lo
@@ -699,12 +983,12 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
       qdat[qpoff[e] + q] = v;
     }
     for (size_t j = 0; j < cols[e].size(); ++j) {
-      d[64 + j] = (int32_t)cols[e][j].dof;
+      d[nfe_e + j] = (int32_t)cols[e][j].dof;
       int slot = (int)(std::lower_bound(ealpha[e].begin(), ealpha[e].end(), cols[e][j].alpha) -
                        ealpha[e].begin());
       ecol[ecpos++] = (slot << 3) | cols[e][j].lv;
       const int lv = cols[e][j].lv;
-      eshift[doff[e] + 64 + j] = (uint8_t)((ex + (lv & 1) >= nx ? 1 : 0) |
+      eshift[doff[e] + nfe_e + j] = (uint8_t)((ex + (lv & 1) >= nx ? 1 : 0) |
                                            (ey + ((lv >> 1) & 1) >= ny ? 2 : 0) |
                                            (ez + (lv >> 2) >= nz ? 4 : 0));
     }
@@ -776,7 +1060,8 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
   int min_p = 1 << 30;
   for (auto &parts : rule)
     for (auto &pt : parts) min_p = std::min(min_p, pt.p);
-  const bool fe_exact = min_p >= 4;
+  // (the exact FE-FE constants serve the mixed path, which takes the tricubic space)
+  const bool fe_exact = min_p >= 4 && !ser;
   std::vector<double> TF, SF, S0;
   if (fe_exact) {
     double M1[4][4] = {{0}}, K1[4][4] = {{0}}, D1[4][4] = {{0}};   // D1[a][b] = int L'_a L_b
@@ -854,6 +1139,8 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
     ctx->images[k] = S.img[k];
   }
   ctx->general = S.gen;
+  ctx->ser = ser;
+  ctx->nfe_e = nfe_e;
   for (int k = 0; k < 9; ++k) {
     ctx->lat[k] = S.gen ? S.lat.L[k] : 0.0;
     ctx->Jit[k] = S.gen ? S.Jit[k] : 0.0;
@@ -1167,6 +1454,58 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
   }
   ctx->n_citems = (int)(citems.size() / 3);
 
+  // Work list of the FP32 per-point kernels (density; adjoint of the strip in
+  // its per-point form): every element, cut into ranges of multiples of 256
+  // points so that no range costs (points x basis functions) much more than a
+  // quarter of the mean per SM.  Each point is written by one range only.
+  std::vector<int32_t> pitems;
+  {
+    int nsm = 152;
+    if (ctx->on_device) {
+      int v = 0;
+      if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, ctx->device) == cudaSuccess &&
+          v > 0)
+        nsm = v;
+    }
+    struct PItem {
+      int32_t k, qa, qb;
+      int64_t c;
+    };
+    std::vector<PItem> items;
+    int64_t total = 0;
+    for (int64_t e = 0; e < nelem; ++e) total += (int64_t)q_e[e] * n_e[e];
+    const double target = std::max(1.0, (double)total / (4.0 * nsm));
+    for (int64_t k = 0; k < nelem; ++k) {
+      const int64_t e = order[k];
+      const int32_t Q = q_e[e];
+      int m = (int)std::min<double>(std::ceil((double)Q * n_e[e] / target), 1e6);
+      m = std::max(1, std::min(m, Q / 256));
+      int32_t prev = 0;
+      for (int j = 1; j <= m; ++j) {
+        const int32_t b = (j == m) ? Q : (int32_t)(((int64_t)j * Q / m) & ~(int64_t)255);
+        if (b <= prev) continue;
+        items.push_back(PItem{(int32_t)k, prev, b, (int64_t)(b - prev) * n_e[e]});
+        prev = b;
+      }
+    }
+    std::stable_sort(items.begin(), items.end(),
+                     [](const PItem &x, const PItem &y) { return x.c > y.c; });
+    std::vector<int64_t> covered(nelem, 0);
+    for (auto &it : items) {
+      const int64_t e = order[it.k];
+      if (it.qa < 0 || it.qb <= it.qa || it.qb > q_e[e])
+        return fail(PUFE_EINVAL, "internal: bad point range in the FP32 per-point work list");
+      covered[e] += it.qb - it.qa;
+      pitems.push_back(it.k);
+      pitems.push_back(it.qa);
+      pitems.push_back(it.qb);
+    }
+    for (int64_t e = 0; e < nelem; ++e)
+      if (covered[e] != q_e[e])
+        return fail(PUFE_EINVAL, "internal: the FP32 per-point work list misses points");
+  }
+  ctx->n_pitems = (int)(pitems.size() / 3);
+
   pufe_status st;
   auto &D = ctx->d;
   if (ctx->on_device) {
@@ -1199,6 +1538,7 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
   if (!titems.empty() && (st = upload(&D.titems, titems)) != PUFE_OK) return st;
   if (!sitems.empty() && (st = upload(&D.sitems, sitems)) != PUFE_OK) return st;
   if (!citems.empty() && (st = upload(&D.citems, citems)) != PUFE_OK) return st;
+  if (!pitems.empty() && (st = upload(&D.pitems, pitems)) != PUFE_OK) return st;
   if ((st = upload(&D.eeform, ctx->eeform_host)) != PUFE_OK) return st;
   if (fe_exact) {
     if ((st = upload(&D.Tfe, TF)) != PUFE_OK) return st;
@@ -1243,7 +1583,7 @@ static void free_device(pufe_ctx *ctx) {
                   D.toff, D.psi, D.psi32, D.qpoff, D.qdat, D.ptab, D.vpad, D.toff32, D.eorig,
                   D.Tfe, D.Sfe, D.S0, D.partoff, D.part_p, D.part_q,
                   D.orb, D.orbf, D.rowptr, D.col, D.soff, D.smap, D.order, D.wsplit,
-                  D.titems, D.sitems, D.citems, D.eeform, D.err};
+                  D.titems, D.sitems, D.citems, D.pitems, D.eeform, D.err};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (D.ev_fork) cudaEventDestroy(D.ev_fork);

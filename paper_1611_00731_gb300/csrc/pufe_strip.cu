@@ -1225,6 +1225,7 @@ namespace {
 constexpr int AJ_NT = 256;
 constexpr int AJ_W = 4096;   // work floats: x and y stage outputs of one chunk, or the E x E block
 
+template <bool BLOCH>
 __global__ void __launch_bounds__(AJ_NT, 4) k_adjoint_strip_sf(
     const int32_t *__restrict__ order, const int64_t *__restrict__ qoff,
     const int64_t *__restrict__ qpoff, const float4 *__restrict__ qdat,
@@ -1234,7 +1235,7 @@ __global__ void __launch_bounds__(AJ_NT, 4) k_adjoint_strip_sf(
     const int32_t *__restrict__ partoff, const int32_t *__restrict__ part_p,
     const int32_t *__restrict__ part_q, const int64_t *__restrict__ soff,
     const int32_t *__restrict__ smap, const double *__restrict__ Hbar, int pm, int cfloats,
-    double *__restrict__ Vbar, unsigned *err) {
+    double *__restrict__ Vbar, unsigned *err, BlochCot bc) {
   extern __shared__ float4 sm_aj4[];
   const int e = order[blockIdx.x], tid = threadIdx.x;
   const int n = (int)(doff[e + 1] - doff[e]);
@@ -1295,6 +1296,19 @@ __global__ void __launch_bounds__(AJ_NT, 4) k_adjoint_strip_sf(
       double h[8];
 #pragma unroll
       for (int u = 0; u < 8; ++u) h[u] = o0 + u * AJ_NT < ne * 64 ? Hbar[s1[u]] : 0.0;
+      if (BLOCH) {   // at a wavevector: the phased real part
+        double hi[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) hi[u] = o0 + u * AJ_NT < ne * 64 ? bc.Hi[s1[u]] : 0.0;
+        const uint8_t *esh = bc.eshift + doff[e];
+        for (int u = 0; u < 8; ++u) {
+          const int o = o0 + u * AJ_NT;
+          if (o >= ne * 64) break;
+          const int r = half ? o % ne : o >> 6, j = half ? o / ne : o & 63;
+          h[u] = half ? cot_entry(h[u], hi[u], esh[j], esh[64 + r], bc.ph)
+                      : cot_entry(h[u], hi[u], esh[64 + r], esh[j], bc.ph);
+        }
+      }
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
         const int o = o0 + u * AJ_NT;
@@ -1320,6 +1334,16 @@ __global__ void __launch_bounds__(AJ_NT, 4) k_adjoint_strip_sf(
     double h[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) h[u] = o0 + u * AJ_NT < ne * ne ? Hbar[s1[u]] : 0.0;
+    if (BLOCH) {
+      double hi[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) hi[u] = o0 + u * AJ_NT < ne * ne ? bc.Hi[s1[u]] : 0.0;
+      const uint8_t *esh = bc.eshift + doff[e] + 64;
+      for (int u = 0; u < 8; ++u) {
+        const int o = o0 + u * AJ_NT, r = o / ne, sc = o - r * ne;
+        if (o < ne * ne) h[u] = cot_entry(h[u], hi[u], esh[r], esh[sc], bc.ph);
+      }
+    }
 #pragma unroll
     for (int u = 0; u < 8; ++u)
       if (o0 + u * AJ_NT < ne * ne) HE[o0 + u * AJ_NT] = (float)h[u];
@@ -1479,7 +1503,7 @@ __global__ void __launch_bounds__(AJ_NT, 4) k_adjoint_strip_sf(
 }  // namespace
 
 pufe_status launch_adjoint_strip_sf(pufe_ctx *ctx, const double *Hbar, double *Vbar, int first,
-                                    int count, cudaStream_t st) {
+                                    int count, cudaStream_t st, const BlochCot &bc) {
   if (count <= 0 || ctx->adj_sf_floats == 0) return PUFE_OK;
   auto &D = ctx->d;
   const int pm = std::max(1, ctx->max_part_p);
@@ -1490,11 +1514,11 @@ pufe_status launch_adjoint_strip_sf(pufe_ctx *ctx, const double *Hbar, double *V
   const int cf = (ctx->adj_sf_floats + 3) & ~3;
   const size_t sm = ((size_t)cf + 33 * pm + AJ_W + 16 * 8 + 136) * sizeof(float);
   if (sm > 227 * 1024) return fail(PUFE_EINVAL, "adjoint strip: shared memory above 227 KB");
-  PUFE_CUDA_TRY(
-      cudaFuncSetAttribute(k_adjoint_strip_sf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  k_adjoint_strip_sf<<<(unsigned)count, AJ_NT, sm, st>>>(
+  auto kern = bc.Hi ? k_adjoint_strip_sf<true> : k_adjoint_strip_sf<false>;
+  PUFE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  kern<<<(unsigned)count, AJ_NT, sm, st>>>(
       D.order + first, D.qoff, D.qpoff, D.qdat, D.w, D.doff, D.ecol, D.aoff, D.toff32, D.psi32,
-      D.partoff, D.part_p, D.part_q, D.soff, D.smap, Hbar, pm, cf, Vbar, D.err);
+      D.partoff, D.part_p, D.part_q, D.soff, D.smap, Hbar, pm, cf, Vbar, D.err, bc);
   PUFE_CUDA_TRY(cudaGetLastError());
   return PUFE_OK;
 }

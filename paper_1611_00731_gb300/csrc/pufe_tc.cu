@@ -233,15 +233,28 @@ __global__ void k_tabulate_f32(const int64_t *__restrict__ qpoff, const float4 *
                                const int32_t *__restrict__ aoff, const int32_t *__restrict__ alist,
                                const int64_t *__restrict__ toff32, const OrbitalF *__restrict__ orbf,
                                const float *__restrict__ eorig, float ax, float ay, float az,
-                               float hx, float hy, float hz, float *__restrict__ psi) {
-  const int64_t e = blockIdx.x;
-  const int Qp = (int)(qpoff[e + 1] - qpoff[e]);
-  const int A = aoff[e + 1] - aoff[e];
+                               float hx, float hy, float hz, int nelem,
+                               float *__restrict__ psi) {
   const float av[3] = {ax, ay, az};
   const float inv_a[3] = {1.0f / ax, 1.0f / ay, 1.0f / az};
   const float hh[3] = {0.5f * hx, 0.5f * hy, 0.5f * hz};
-  float *out = psi + 4 * toff32[e];
-  for (int idx = threadIdx.x; idx < Qp * A; idx += blockDim.x) {
+  // one thread per (element, slot, padded point) over the whole table, the
+  // element found by bisection of the table offsets (so elements with many
+  // points and slots spread over many CTAs)
+  const int64_t total = toff32[nelem];
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int lo_e = 0, hi_e = nelem;   // toff32[lo_e] <= t < toff32[hi_e]
+    while (hi_e - lo_e > 1) {
+      const int mid = (lo_e + hi_e) >> 1;
+      if (toff32[mid] <= t) lo_e = mid; else hi_e = mid;
+    }
+    const int e = lo_e;
+    const int Qp = (int)(qpoff[e + 1] - qpoff[e]);
+    const int A = aoff[e + 1] - aoff[e];
+    float *out = psi + 4 * toff32[e];
+    const int idx = (int)(t - toff32[e]);
+    if (A <= 0 || Qp <= 0 || idx >= Qp * A) continue;
     const int slot = idx / Qp, q = idx - slot * Qp;
     const OrbitalF o = orbf[alist[aoff[e] + slot]];
     const float *eo = eorig + 8 * (int64_t)(aoff[e] + slot);
@@ -697,6 +710,7 @@ static size_t assemble_smem(int in_bytes) {
 // ---------------------------------------------------------------------------
 constexpr int DEN_NT = 128;
 
+template <bool BLOCH>
 __global__ void __launch_bounds__(DEN_NT) k_density_f32(
     const int32_t *__restrict__ order, const int64_t *__restrict__ qoff,
     const int64_t *__restrict__ qpoff, const float4 *__restrict__ qdat,
@@ -704,11 +718,14 @@ __global__ void __launch_bounds__(DEN_NT) k_density_f32(
     const int32_t *__restrict__ ecol, const int32_t *__restrict__ aoff,
     const int64_t *__restrict__ toff32, const float *__restrict__ psi,
     const double *__restrict__ C, int64_t ldc, const double *__restrict__ f, int nocc, int noccp,
-    double *__restrict__ rho) {
+    double *__restrict__ rho, const int32_t *__restrict__ pitems, const double *__restrict__ Ci,
+    const uint8_t *__restrict__ eshift, PhaseTab ph) {
   extern __shared__ __align__(16) float fsm[];
-  const int e = order[blockIdx.x];
+  // work item: points [qb, qend) of element order[k]
+  const int e = order[pitems[3 * blockIdx.x]];
+  const int qb = pitems[3 * blockIdx.x + 1];
   const int64_t q0 = qoff[e];
-  const int Q = (int)(qoff[e + 1] - q0);
+  const int Q = min((int)(qoff[e + 1] - q0), pitems[3 * blockIdx.x + 2]);
   const int A = aoff[e + 1] - aoff[e];
   const int n = (int)(doff[e + 1] - doff[e]);
   const int nenr = n - 64;
@@ -718,13 +735,26 @@ __global__ void __launch_bounds__(DEN_NT) k_density_f32(
   const float4 *qe = qdat + qpoff[e];
   float *Cs = fsm;              // n x noccp
   float *fs = Cs + n * noccp;   // noccp
+  float *Cz = fs + noccp;       // n x noccp: imaginary parts (Bloch states, Ci != nullptr)
   for (int k = threadIdx.x; k < n * noccp; k += DEN_NT) {
     const int j = k / noccp, kk = k - j * noccp;
-    Cs[k] = (kk < nocc) ? (float)C[(int64_t)dl[j] * ldc + kk] : 0.0f;
+    if (BLOCH) {   // (C + i Ci) exp(i k.R_j) in FP64, then rounded
+      double cr = 0.0, ci = 0.0;
+      if (kk < nocc) {
+        const double ar = C[(int64_t)dl[j] * ldc + kk], ai = Ci[(int64_t)dl[j] * ldc + kk];
+        const int c = eshift[doff[e] + j];
+        cr = ph.re[c] * ar - ph.im[c] * ai;
+        ci = ph.re[c] * ai + ph.im[c] * ar;
+      }
+      Cs[k] = (float)cr;
+      Cz[k] = (float)ci;
+    } else {
+      Cs[k] = (kk < nocc) ? (float)C[(int64_t)dl[j] * ldc + kk] : 0.0f;
+    }
   }
   for (int k = threadIdx.x; k < noccp; k += DEN_NT) fs[k] = (k < nocc) ? (float)f[k] : 0.0f;
   __syncthreads();
-  for (int q = threadIdx.x; q < Q; q += DEN_NT) {
+  for (int q = qb + threadIdx.x; q < Q; q += DEN_NT) {
     const float4 x4 = qe[q];
     const float xq[3] = {x4.x, x4.y, x4.z};
     float L[3][4], dL[3][4];
@@ -740,32 +770,36 @@ __global__ void __launch_bounds__(DEN_NT) k_density_f32(
     }
     const float *pq = pe + (int64_t)(q >> 3) * A * 32 + (q & 7);
     float r = 0.0f;
-    for (int k0 = 0; k0 < noccp; k0 += 8) {
-      float acc[8];
+    // real parts (the only ones at Gamma), then the imaginary parts
+    for (int part = 0; part < (BLOCH ? 2 : 1); ++part) {
+      const float *Cb = part ? Cz : Cs;
+      for (int k0 = 0; k0 < noccp; k0 += 8) {
+        float acc[8];
 #pragma unroll
-      for (int k = 0; k < 8; ++k) acc[k] = 0.0f;
+        for (int k = 0; k < 8; ++k) acc[k] = 0.0f;
 #pragma unroll
-      for (int c3 = 0; c3 < 4; ++c3)
+        for (int c3 = 0; c3 < 4; ++c3)
 #pragma unroll
-        for (int c2 = 0; c2 < 4; ++c2) {
-          const float lyz = L[1][c2] * L[2][c3];
+          for (int c2 = 0; c2 < 4; ++c2) {
+            const float lyz = L[1][c2] * L[2][c3];
 #pragma unroll
-          for (int c1 = 0; c1 < 4; ++c1) {
-            const float b = L[0][c1] * lyz;
-            const float *cr = Cs + (c1 + 4 * c2 + 16 * c3) * noccp + k0;
+            for (int c1 = 0; c1 < 4; ++c1) {
+              const float b = L[0][c1] * lyz;
+              const float *cr = Cb + (c1 + 4 * c2 + 16 * c3) * noccp + k0;
 #pragma unroll
-            for (int k = 0; k < 8; ++k) acc[k] = fmaf(b, cr[k], acc[k]);
+              for (int k = 0; k < 8; ++k) acc[k] = fmaf(b, cr[k], acc[k]);
+            }
           }
+        for (int j = 0; j < nenr; ++j) {
+          const int code = ec[j];
+          const float b = pu[code & 7] * pq[(code >> 3) * 32];
+          const float *cr = Cb + (64 + j) * noccp + k0;
+#pragma unroll
+          for (int k = 0; k < 8; ++k) acc[k] = fmaf(b, cr[k], acc[k]);
         }
-      for (int j = 0; j < nenr; ++j) {
-        const int code = ec[j];
-        const float b = pu[code & 7] * pq[(code >> 3) * 32];
-        const float *cr = Cs + (64 + j) * noccp + k0;
 #pragma unroll
-        for (int k = 0; k < 8; ++k) acc[k] = fmaf(b, cr[k], acc[k]);
+        for (int k = 0; k < 8; ++k) r = fmaf(fs[k0 + k] * acc[k], acc[k], r);
       }
-#pragma unroll
-      for (int k = 0; k < 8; ++k) r = fmaf(fs[k0 + k] * acc[k], acc[k], r);
     }
     rho[q0 + q] = (double)r;
   }
@@ -775,11 +809,13 @@ __global__ void __launch_bounds__(DEN_NT) k_density_f32(
 // K5' (FP32): Vbar_q = w_q b_q^T Hbar_e b_q.  One CTA per element: Hbar_e
 // (gathered through the scatter map) and a chunk of 32 basis rows sit in
 // shared memory; each thread owns a 4-point x 4-row register tile of
-// t_qi = sum_j Hbar_ij b_qj and reduces b_qi t_qi into the point's sum.
+// t_qi = sum_j Hbar_ij b_qj and stores its rows' sum of b_qi t_qi per point;
+// the row tiles' sums are then added in a fixed order.
 // ---------------------------------------------------------------------------
 constexpr int ADJ_NT = 256;
 constexpr int ADJ_QB = 32;
 
+template <bool BLOCH>
 __global__ void __launch_bounds__(ADJ_NT) k_adjoint_f32(
     const int32_t *__restrict__ order, const int64_t *__restrict__ qoff,
     const int64_t *__restrict__ qpoff, const float4 *__restrict__ qdat,
@@ -788,7 +824,7 @@ __global__ void __launch_bounds__(ADJ_NT) k_adjoint_f32(
     const int64_t *__restrict__ toff32, const float *__restrict__ psi,
     const int64_t *__restrict__ soff, const int32_t *__restrict__ smap,
     const double *__restrict__ Hbar, double *__restrict__ Vbar,
-    const int32_t *__restrict__ items) {
+    const int32_t *__restrict__ items, BlochCot bc) {
   extern __shared__ __align__(16) float fsm[];
   // work item: the points [8 c0, 8 c1) of element order[items[3 b]] (clipped
   // to the element's Q points)
@@ -807,10 +843,17 @@ __global__ void __launch_bounds__(ADJ_NT) k_adjoint_f32(
   const int32_t *m = smap + soff[e];
   float *Hs = fsm;                 // n4 x n4, zero padded
   float *Bq = Hs + n4 * n4;        // ADJ_QB x ldb
-  float *acc = Bq + ADJ_QB * ldb;  // ADJ_QB
+  float *part = Bq + ADJ_QB * ldb; // (n4 / 4) x ADJ_QB: each row tile's sum per point
   for (int k = threadIdx.x; k < n4 * n4; k += ADJ_NT) {
     const int i = k / n4, j = k - i * n4;
-    Hs[k] = (i < n && j < n) ? (float)Hbar[m[i * n + j]] : 0.0f;
+    float v = 0.0f;
+    if (i < n && j < n) {
+      const int32_t sl = m[i * n + j];
+      v = BLOCH ? (float)cot_entry(Hbar[sl], bc.Hi[sl], bc.eshift[doff[e] + i],
+                                   bc.eshift[doff[e] + j], bc.ph)
+                : (float)Hbar[sl];
+    }
+    Hs[k] = v;
   }
   const int nI = n4 / 4;
   const int ntile = (ADJ_QB / 4) * nI;
@@ -841,7 +884,6 @@ __global__ void __launch_bounds__(ADJ_NT) k_adjoint_f32(
       }
       Bq[qq * ldb + c] = b;
     }
-    if (threadIdx.x < ADJ_QB) acc[threadIdx.x] = 0.0f;
     __syncthreads();
     for (int t = threadIdx.x; t < ntile; t += ADJ_NT) {
       const int tq = t & (ADJ_QB / 4 - 1), ti = t / (ADJ_QB / 4);
@@ -869,12 +911,16 @@ __global__ void __launch_bounds__(ADJ_NT) k_adjoint_f32(
         float s = 0.0f;
 #pragma unroll
         for (int y = 0; y < 4; ++y) s = fmaf(b0[x * ldb + 4 * ti + y], a[x][y], s);
-        atomicAdd(acc + 4 * tq + x, s);
+        part[ti * ADJ_QB + 4 * tq + x] = s;
       }
     }
     __syncthreads();
-    if (threadIdx.x < ADJ_QB && qc + (int)threadIdx.x < qend)
-      Vbar[q0 + qc + threadIdx.x] = w[q0 + qc + threadIdx.x] * (double)acc[threadIdx.x];
+    // the row tiles' sums added in a fixed order (a deterministic result)
+    if (threadIdx.x < ADJ_QB && qc + (int)threadIdx.x < qend) {
+      float s = 0.0f;
+      for (int ti = 0; ti < nI; ++ti) s += part[ti * ADJ_QB + threadIdx.x];
+      Vbar[q0 + qc + threadIdx.x] = w[q0 + qc + threadIdx.x] * (double)s;
+    }
   }
 }
 
@@ -894,6 +940,7 @@ __global__ void __launch_bounds__(ADJ_NT) k_adjoint_f32(
 // ---------------------------------------------------------------------------
 constexpr int AS_NT = 256;
 
+template <bool BLOCH>
 __global__ void __launch_bounds__(AS_NT) k_adjoint_strip_f32(
     const int32_t *__restrict__ order, const int64_t *__restrict__ qoff,
     const int64_t *__restrict__ qpoff, const float4 *__restrict__ qdat,
@@ -902,12 +949,15 @@ __global__ void __launch_bounds__(AS_NT) k_adjoint_strip_f32(
     const int64_t *__restrict__ toff32, const float *__restrict__ psi,
     const int64_t *__restrict__ soff, const int32_t *__restrict__ smap,
     const int32_t *__restrict__ partoff, const int32_t *__restrict__ part_p,
-    const double *__restrict__ Hbar, double *__restrict__ Vbar) {
+    const double *__restrict__ Hbar, double *__restrict__ Vbar,
+    const int32_t *__restrict__ pitems, BlochCot bc) {
   extern __shared__ float4 sm_as4[];
-  const int e = order[blockIdx.x], tid = threadIdx.x;
+  // work item: points [qb, Q) of element order[k]
+  const int e = order[pitems[3 * blockIdx.x]], tid = threadIdx.x;
+  const int qb = pitems[3 * blockIdx.x + 1], qend = pitems[3 * blockIdx.x + 2];
   const int n = (int)(doff[e + 1] - doff[e]);
   const int ne = n - 64;
-  if (ne <= 0) return;   // FE-only element: Vbar is already complete
+  if (ne <= 0 || n > 128) return;   // FE-only (Vbar complete) or a tensor-core element
   {  // elements of the slot form are done by k_adjoint_strip_sf
     int pmax = 0;
     for (int k = partoff[e]; k < partoff[e + 1]; ++k) pmax = max(pmax, part_p[k]);
@@ -919,25 +969,32 @@ __global__ void __launch_bounds__(AS_NT) k_adjoint_strip_f32(
   float *bE = Be + ne8 * ne8;                      // [ne8][AS_NT]: b_s at each point
   int *ecs = reinterpret_cast<int *>(bE + ne8 * AS_NT);
   const int64_t q0 = qoff[e];
-  const int Q = (int)(qoff[e + 1] - q0);
+  const int Q = min((int)(qoff[e + 1] - q0), qend);
   const int A = aoff[e + 1] - aoff[e];
   const int32_t *m = smap + soff[e];
   const float *pe = psi + 4 * toff32[e];
   const float4 *qe = qdat + qpoff[e];
   if (tid < ne) ecs[tid] = ecol[(doff[e] - 64ll * e) + tid];
+  // element entry (i, j) of the cotangent (the phased real part at a wavevector)
+  auto hv = [&](int i, int j) -> double {
+    const int32_t sl = m[i * n + j];
+    return BLOCH ? cot_entry(Hbar[sl], bc.Hi[sl], bc.eshift[doff[e] + i], bc.eshift[doff[e] + j],
+                             bc.ph)
+                 : Hbar[sl];
+  };
   for (int o = tid; o < 64 * ne8; o += AS_NT) {
     const int j = o / ne8, r = o - j * ne8;
-    Bf[o] = r < ne ? (float)(Hbar[m[(64 + r) * n + j]] + Hbar[m[j * n + 64 + r]]) : 0.0f;
+    Bf[o] = r < ne ? (float)(hv(64 + r, j) + hv(j, 64 + r)) : 0.0f;
   }
   for (int o = tid; o < ne8 * ne8; o += AS_NT) {
     const int sr = o / ne8, r = o - sr * ne8;
     float v = 0.0f;
-    if (sr < ne && sr > r) v = (float)(Hbar[m[(64 + r) * n + 64 + sr]] + Hbar[m[(64 + sr) * n + 64 + r]]);
-    else if (sr < ne && sr == r) v = (float)Hbar[m[(64 + r) * n + 64 + r]];
+    if (sr < ne && sr > r) v = (float)(hv(64 + r, 64 + sr) + hv(64 + sr, 64 + r));
+    else if (sr < ne && sr == r) v = (float)hv(64 + r, 64 + r);
     Be[o] = v;
   }
   __syncthreads();
-  for (int t0 = 0; t0 < Q; t0 += AS_NT) {
+  for (int t0 = qb; t0 < Q; t0 += AS_NT) {
     const int ql = t0 + tid;
     if (ql >= Q) break;   // no block-wide barrier below
     const float4 x4 = qe[ql];
@@ -1019,10 +1076,16 @@ __global__ void __launch_bounds__(AS_NT) k_adjoint_strip_f32(
 pufe_status launch_tabulate_f32(pufe_ctx *ctx, cudaStream_t st) {
   if (ctx->psi32_len == 0) return PUFE_OK;
   auto &D = ctx->d;
-  k_tabulate_f32<<<(unsigned)ctx->nelem, 256, 0, st>>>(
-      D.qpoff, D.qdat, D.aoff, D.alist, D.toff32, D.orbf, D.eorig, (float)ctx->a[0],
-      (float)ctx->a[1], (float)ctx->a[2], (float)ctx->h[0], (float)ctx->h[1], (float)ctx->h[2],
-      D.psi32);
+  {
+    int nsm = 0;
+    PUFE_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device));
+    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((ctx->psi32_len + 255) / 256,
+                                                                  (int64_t)nsm * 16));
+    k_tabulate_f32<<<(unsigned)blocks, 256, 0, st>>>(
+        D.qpoff, D.qdat, D.aoff, D.alist, D.toff32, D.orbf, D.eorig, (float)ctx->a[0],
+        (float)ctx->a[1], (float)ctx->a[2], (float)ctx->h[0], (float)ctx->h[1],
+        (float)ctx->h[2], (int)ctx->nelem, D.psi32);
+  }
   PUFE_CUDA_TRY(cudaGetLastError());
   return PUFE_OK;
 }
@@ -1143,33 +1206,40 @@ pufe_status launch_assemble_tc(pufe_ctx *ctx, const double *V, int what, double 
 }
 
 pufe_status launch_density_tc(pufe_ctx *ctx, const double *C, int64_t ldc, const double *f,
-                              int nocc, double *rho, cudaStream_t st) {
+                              int nocc, double *rho, cudaStream_t st, const double *Ci,
+                              const PhaseTab *ph) {
   auto &D = ctx->d;
   const int noccp = (nocc + 7) & ~7;
-  const size_t sm = ((size_t)ctx->max_basis * noccp + noccp) * sizeof(float);
-  PUFE_CUDA_TRY(
-      cudaFuncSetAttribute(k_density_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  k_density_f32<<<(unsigned)ctx->nelem, DEN_NT, sm, st>>>(D.order, D.qoff, D.qpoff, D.qdat,
-                                                          D.doff, D.dofs, D.ecol, D.aoff,
-                                                          D.toff32, D.psi32, C, ldc, f, nocc,
-                                                          noccp, rho);
+  const size_t sm = ((size_t)ctx->max_basis * noccp * (Ci ? 2 : 1) + noccp) * sizeof(float);
+  if (sm > 227 * 1024) return fail(PUFE_EINVAL, "density: basis x states beyond shared memory");
+  if (Ci && !ph) return fail(PUFE_EINVAL, "internal: Bloch density without phases");
+  auto kern = Ci ? k_density_f32<true> : k_density_f32<false>;
+  PUFE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  if (ctx->n_pitems <= 0) return PUFE_OK;
+  kern<<<(unsigned)ctx->n_pitems, DEN_NT, sm, st>>>(
+      D.order, D.qoff, D.qpoff, D.qdat, D.doff, D.dofs, D.ecol, D.aoff, D.toff32, D.psi32, C,
+      ldc, f, nocc, noccp, rho, D.pitems, Ci, D.eshift, ph ? *ph : PhaseTab{});
   PUFE_CUDA_TRY(cudaGetLastError());
   return PUFE_OK;
 }
 
-pufe_status launch_adjoint_tc(pufe_ctx *ctx, const double *Hbar, double *Vbar, cudaStream_t st) {
+pufe_status launch_adjoint_tc(pufe_ctx *ctx, const double *Hbar, double *Vbar, cudaStream_t st,
+                              const BlochCot *bcp) {
   auto &D = ctx->d;
+  const BlochCot bc = bcp ? *bcp : BlochCot{nullptr, nullptr, PhaseTab{}};
   const int nbig = ctx->n_big;
   if (nbig > 0) {  // n_e > 128: FP32 CUDA-core kernel
     const int n4 = (ctx->max_basis + 3) & ~3;
     const int ldb = n4 + 36;
-    const size_t sm = ((size_t)n4 * n4 + (size_t)ADJ_QB * ldb + ADJ_QB) * sizeof(float);
+    const size_t sm = ((size_t)n4 * n4 + (size_t)ADJ_QB * ldb + (size_t)(n4 / 4) * ADJ_QB) *
+                      sizeof(float);
     if (sm > 227 * 1024) return fail(PUFE_EINVAL, "n_e too large for the FP32 adjoint kernel");
-    PUFE_CUDA_TRY(
-        cudaFuncSetAttribute(k_adjoint_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    k_adjoint_f32<<<ctx->n_titems, ADJ_NT, sm, st>>>(D.order, D.qoff, D.qpoff, D.qdat, D.w,
+    auto kern = bc.Hi ? k_adjoint_f32<true> : k_adjoint_f32<false>;
+    PUFE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    kern<<<ctx->n_titems, ADJ_NT, sm, st>>>(D.order, D.qoff, D.qpoff, D.qdat, D.w,
                                                      D.doff, D.ecol, D.aoff, D.toff32, D.psi32,
-                                                     D.soff, D.smap, Hbar, Vbar, D.titems);
+                                                     D.soff, D.smap, Hbar, Vbar, D.titems,
+                                                     bc);
     PUFE_CUDA_TRY(cudaGetLastError());
   }
   const int nsmall = (int)ctx->nelem - nbig;
@@ -1179,18 +1249,19 @@ pufe_status launch_adjoint_tc(pufe_ctx *ctx, const double *Hbar, double *Vbar, c
       ne8 = std::max(ne8, (ctx->n_e[ctx->order[k]] - 64 + 7) & ~7);
     const size_t sm = ((size_t)64 * ne8 + (size_t)ne8 * ne8 + (size_t)ne8 * AS_NT + ne8) * 4;
     if (sm > 227 * 1024) return fail(PUFE_EINVAL, "n_e too large for the strip adjoint");
-    pufe_status e0 = launch_adjoint_fefe(ctx, Hbar, Vbar, nbig, nsmall, st);
+    pufe_status e0 = launch_adjoint_fefe(ctx, Hbar, Vbar, nbig, nsmall, st, bc);
     if (e0 != PUFE_OK) return e0;
     // the slot form where it fits (all elements of the usual rules), the
     // direct per-point form for the rest
-    pufe_status e1 = launch_adjoint_strip_sf(ctx, Hbar, Vbar, nbig, nsmall, st);
+    pufe_status e1 = launch_adjoint_strip_sf(ctx, Hbar, Vbar, nbig, nsmall, st, bc);
     if (e1 != PUFE_OK) return e1;
     if (!ctx->adj_sf_all) {
-      PUFE_CUDA_TRY(cudaFuncSetAttribute(k_adjoint_strip_f32,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-      k_adjoint_strip_f32<<<nsmall, AS_NT, sm, st>>>(
-          D.order + nbig, D.qoff, D.qpoff, D.qdat, D.w, D.doff, D.ecol, D.aoff, D.toff32,
-          D.psi32, D.soff, D.smap, D.partoff, D.part_p, Hbar, Vbar);
+      auto kern = bc.Hi ? k_adjoint_strip_f32<true> : k_adjoint_strip_f32<false>;
+      PUFE_CUDA_TRY(
+          cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+      kern<<<(unsigned)ctx->n_pitems, AS_NT, sm, st>>>(
+          D.order, D.qoff, D.qpoff, D.qdat, D.w, D.doff, D.ecol, D.aoff, D.toff32, D.psi32,
+          D.soff, D.smap, D.partoff, D.part_p, Hbar, Vbar, D.pitems, bc);
       PUFE_CUDA_TRY(cudaGetLastError());
     }
   }

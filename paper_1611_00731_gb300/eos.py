@@ -3,11 +3,13 @@
 Sec. 6 computes the LiH energy-volume curve at a series of lattice constants
 and fits a fourth-order Birch-Murnaghan form to it (Table 2: V_0, a_0, B_0).
 Here one self-consistent field (Sec. 3) runs per lattice constant on the GPU:
-every iteration replays the H/S assemblies of all cells from one captured
-CUDA graph, takes each cell's lowest states from a host FP64 generalized
-eigensolve (LAPACK; the eigensolver is not part of the library), and calls
-pufe_scf_step for the occupations, output density, energy terms, Pulay mixing
-and the next potential.  The fit is host arithmetic on the converged energies.
+every iteration replays the H/S assemblies of all cells (and of all their
+k-points, Sec. 4 eqs. bloch, strong) from one captured CUDA graph, takes each
+cell's lowest states from a host FP64 generalized eigensolve (LAPACK; the
+eigensolver is not part of the library), and calls pufe_scf_step (or
+pufe_scf_step_bloch) for the occupations, output density, energy terms, Pulay
+mixing and the next potential.  The fit is host arithmetic on the converged
+energies.
 """
 from __future__ import annotations
 
@@ -19,6 +21,12 @@ import scipy.sparse as sp
 from . import pufe
 
 HA_PER_BOHR3_IN_GPA = 29421.02648438959
+
+# The 1/4-shifted 2x2x2 Monkhorst-Pack grid reduced by time reversal (k and
+# -k carry the same density and eigenvalues): four k-points in units of
+# 2 pi / a per axis, equal weights.
+MP2_SHIFTED = ([(0.25, 0.25, 0.25), (0.25, 0.25, -0.25), (0.25, -0.25, 0.25),
+                (-0.25, 0.25, 0.25)], [0.25, 0.25, 0.25, 0.25])
 
 
 def birch_murnaghan4_fit(V, E):
@@ -63,11 +71,18 @@ def _atoms(wl):
 
 
 class _Cell:
-    """Device state of one cell's self-consistent field."""
+    """Device state of one cell's self-consistent field (at the Gamma point,
+    or at the k-points `kpoints` = (fractions of 2 pi / a, weights))."""
 
-    def __init__(self, wl, prec, dev):
+    def __init__(self, wl, prec, dev, kpoints=None):
         import torch
         self.wl, self.prec = wl, prec
+        self.kpts = self.wk = None
+        if kpoints is not None:
+            kf, w = kpoints
+            self.kpts = [2.0 * np.pi / float(wl["a"]) * np.asarray(k, dtype=np.float64)
+                         for k in kf]
+            self.wk = np.asarray(w, dtype=np.float64)
         self.ctx = pufe.pufe_build_mesh(wl)
         c = self.ctx
         c.pufe_tabulate(pufe.PUFE_FP64)
@@ -83,25 +98,50 @@ class _Cell:
         c.pufe_effective_potential(self.n, self.rho_I, self.V_in)
         self.H = torch.empty(c.nnz, **f64)
         self.S = torch.empty(c.nnz, **f64)
+        if self.kpts is not None:   # H(k), S(k) as (re, im) pairs
+            mk = lambda: (torch.empty(c.nnz, **f64), torch.empty(c.nnz, **f64))
+            self.Hk = [mk() for _ in self.kpts]
+            self.Sk = [mk() for _ in self.kpts]
         rowptr, col = c.pattern()
         self.pattern = (rowptr, col)
         c.pufe_scf_reset()
         self.energies, self.info, self.converged = [], None, False
 
     def assemble(self):
-        self.ctx.pufe_assemble_HS(self.V_in, self.H, self.S, prec=self.prec)
+        if self.kpts is None:
+            self.ctx.pufe_assemble_HS(self.V_in, self.H, self.S, prec=self.prec)
+            return
+        for k, Hk, Sk in zip(self.kpts, self.Hk, self.Sk):
+            self.ctx.pufe_assemble_HS_bloch(k, self.V_in, Hk, Sk, prec=self.prec)
+
+    def _dense(self, re, im=None):
+        rowptr, col = self.pattern
+        N = self.ctx.n_dof
+        v = re.cpu().numpy() if im is None else re.cpu().numpy() + 1j * im.cpu().numpy()
+        return sp.csr_matrix((v, col, rowptr), shape=(N, N)).toarray()
 
     def step(self, nstates, kT, alpha, pulay, tol):
         import torch
-        rowptr, col = self.pattern
-        N = self.ctx.n_dof
-        Hd = sp.csr_matrix((self.H.cpu().numpy(), col, rowptr), shape=(N, N)).toarray()
-        Sd = sp.csr_matrix((self.S.cpu().numpy(), col, rowptr), shape=(N, N)).toarray()
-        eps, C = sla.eigh(Hd, Sd, subset_by_index=[0, nstates - 1])
-        Cd = torch.tensor(np.ascontiguousarray(C), device=self.H.device)
-        _, info = self.ctx.pufe_scf_step(eps, Cd, float(self.wl["nelec"]), kT, alpha, self.rho_I,
-                                         self.V_in, self.n, self.V_out, prec=self.prec,
-                                         pulay=pulay)
+        dev = self.H.device
+        if self.kpts is None:
+            eps, C = sla.eigh(self._dense(self.H), self._dense(self.S),
+                              subset_by_index=[0, nstates - 1])
+            Cd = torch.tensor(np.ascontiguousarray(C), device=dev)
+            _, info = self.ctx.pufe_scf_step(eps, Cd, float(self.wl["nelec"]), kT, alpha,
+                                             self.rho_I, self.V_in, self.n, self.V_out,
+                                             prec=self.prec, pulay=pulay)
+        else:
+            eps, Cs = [], []
+            for Hk, Sk in zip(self.Hk, self.Sk):
+                e, C = sla.eigh(self._dense(*Hk), self._dense(*Sk),
+                                subset_by_index=[0, nstates - 1])
+                eps.append(e)
+                Cs.append((torch.tensor(np.ascontiguousarray(C.real), device=dev),
+                           torch.tensor(np.ascontiguousarray(C.imag), device=dev)))
+            _, info = self.ctx.pufe_scf_step_bloch(np.array(self.kpts), self.wk, np.array(eps),
+                                                   Cs, float(self.wl["nelec"]), kT, alpha,
+                                                   self.rho_I, self.V_in, self.n, self.V_out,
+                                                   prec=self.prec, pulay=pulay)
         self.V_in.copy_(self.V_out)
         self.info = info
         self.energies.append(info["e_total"])
@@ -109,14 +149,17 @@ class _Cell:
 
 
 def scf_sweep(workloads, prec=pufe.PUFE_FP64, nstates=None, kT=0.01, alpha=0.5, pulay=4,
-              tol=1e-6, max_iter=80, use_graph=True):
+              tol=1e-6, max_iter=80, use_graph=True, kpoints=None):
     """Self-consistent total energies of several cells (one workload dict
     each), iterated together until every cell's total energy changes by less
-    than `tol` Ha between iterations.  Returns a list of dicts (e_total,
-    iterations, the final info of pufe_scf_step)."""
+    than `tol` Ha between iterations.  At the Gamma point, or with `kpoints`
+    = (list of k in units of 2 pi / a per axis, weights summing to 1) at those
+    Bloch wavevectors (H(k), S(k) of every k and cell in the one graph; the
+    complex states of each k from a host FP64 eigensolve; pufe_scf_step_bloch).
+    Returns a list of dicts (e_total, iterations, the final info of the step)."""
     import torch
     dev = torch.device("cuda", torch.cuda.current_device())
-    cells = [_Cell(wl, prec, dev) for wl in workloads]
+    cells = [_Cell(wl, prec, dev, kpoints) for wl in workloads]
     ns = [nstates or max(4, int(np.ceil(float(wl["nelec"]) / 2.0)) + 4) for wl in workloads]
     graph = None
     if use_graph:

@@ -20,6 +20,7 @@ from . import workloads as W
 
 PUFE_FP64, PUFE_TF32X3 = 0, 1
 PUFE_WANT_H, PUFE_WANT_S = 1, 2
+PUFE_FE_LAGRANGE64, PUFE_FE_SERENDIPITY32 = 0, 1
 STATUS = {0: "PUFE_OK", 1: "PUFE_EINVAL", 2: "PUFE_ENOMEM", 3: "PUFE_ECUDA",
           4: "PUFE_ENOTSPD", 5: "PUFE_ENOTCONV", 6: "PUFE_ETIMEOUT",
           7: "PUFE_EDEVICE", 8: "PUFE_ESTATE"}
@@ -33,7 +34,7 @@ EXPORTS = ["pufe_build_mesh", "pufe_get_sizes", "pufe_get_quadrature", "pufe_get
            "pufe_assemble_HV_adjoint_bloch", "pufe_nonlocal_projections",
            "pufe_nonlocal_projections_bloch", "pufe_get_element_slots",
            "pufe_profile_assembly", "pufe_profile_read", "pufe_selftest_timeout",
-           "pufe_autotune"]
+           "pufe_autotune", "pufe_scf_step_bloch"]
 
 
 def _projector_array(projs):
@@ -53,7 +54,7 @@ class PufeError(RuntimeError):
 class _Cell(C.Structure):
     _fields_ = [("a", C.c_double * 3), ("nel", C.c_int * 3), ("natoms", C.c_int),
                 ("tau", C.POINTER(C.c_double)), ("species", C.POINTER(C.c_int)),
-                ("lattice", C.POINTER(C.c_double))]
+                ("lattice", C.POINTER(C.c_double)), ("fe_space", C.c_int)]
 
 
 class _Species(C.Structure):
@@ -65,7 +66,7 @@ class _Species(C.Structure):
 class _Quad(C.Structure):
     _fields_ = [("mode", C.c_int), ("p_far", C.c_int), ("p_near", C.c_int),
                 ("p_min", C.c_int), ("p_max", C.c_int), ("tol", C.c_double),
-                ("max_depth", C.c_int)]
+                ("max_depth", C.c_int), ("device_tests", C.c_int)]
 
 
 class Projector(C.Structure):
@@ -120,13 +121,17 @@ def load_library(build_if_missing: bool = True):
     lib.pufe_scf_step.argtypes = [vp, C.c_int, dp, vp, C.c_int64, C.c_double, C.c_double,
                                   C.c_double, C.c_int, C.c_int, vp, vp, vp, vp, dp,
                                   C.POINTER(ScfInfo), vp]
+    lib.pufe_scf_step_bloch.argtypes = [vp, C.c_int, dp, dp, C.c_int, dp, C.POINTER(vp),
+                                        C.POINTER(vp), C.c_int64, C.c_double, C.c_double,
+                                        C.c_double, C.c_int, C.c_int, vp, vp, vp, vp, dp,
+                                        C.POINTER(ScfInfo), vp]
     lib.pufe_scf_reset.argtypes = [vp]
     lib.pufe_nonlocal_projections.argtypes = [vp, C.c_int, C.POINTER(Projector), vp, vp]
     lib.pufe_nonlocal_projections_bloch.argtypes = [vp, dp, C.c_int, C.POINTER(Projector), vp,
                                                     vp, vp]
     lib.pufe_assemble_HS_bloch.argtypes = [vp, dp, vp, C.c_int, C.c_int, vp, vp, vp, vp, vp]
-    lib.pufe_density_bloch.argtypes = [vp, dp, vp, vp, C.c_int64, vp, C.c_int, vp, vp]
-    lib.pufe_assemble_HV_adjoint_bloch.argtypes = [vp, dp, vp, vp, vp, vp]
+    lib.pufe_density_bloch.argtypes = [vp, dp, vp, vp, C.c_int64, vp, C.c_int, C.c_int, vp, vp]
+    lib.pufe_assemble_HV_adjoint_bloch.argtypes = [vp, dp, vp, vp, C.c_int, vp, vp]
     lib.pufe_get_element_slots.argtypes = [vp, i32p]
     lib.pufe_profile_assembly.argtypes = [vp, C.c_int]
     lib.pufe_profile_read.argtypes = [vp, dp]
@@ -301,6 +306,38 @@ class Context:
                                   C.byref(info), _stream(stream)))
         return f, info.as_dict()
 
+    def pufe_scf_step_bloch(self, kpts, wk, eps, Cs, nelec, kT, alpha, rho_I, V_eff_in, n,
+                            V_eff_out, prec=PUFE_FP64, pulay=0, stream=None):
+        """One SCF step with k-points: kpts (nk, 3) Cartesian 1/bohr, wk (nk),
+        eps (nk, nstates), Cs a list of nk (C_re, C_im) pairs of N x nstates
+        device tensors with one stride.  Returns (occupations (nk, nstates),
+        info dict).  Blocking."""
+        import numpy as np
+        import torch
+        kp = np.ascontiguousarray(kpts, dtype=np.float64).reshape(-1, 3)
+        w = np.ascontiguousarray(wk, dtype=np.float64).reshape(-1)
+        eps = np.ascontiguousarray(eps, dtype=np.float64).reshape(len(w), -1)
+        nk, ns = eps.shape
+        if len(kp) != nk or len(Cs) != nk:
+            raise ValueError("kpts, wk, eps and Cs must have one entry per k-point")
+        ld = int(Cs[0][0].stride(0))
+        for cr, ci in Cs:
+            if cr.stride(0) != ld or ci.stride(0) != ld or cr.shape[1] < ns or ci.shape != cr.shape:
+                raise ValueError("every C_re, C_im must be N x nstates with one row stride")
+        pre = (C.c_void_p * nk)(*[_ptr(cr, torch.float64).value for cr, _ in Cs])
+        pim = (C.c_void_p * nk)(*[_ptr(ci, torch.float64).value for _, ci in Cs])
+        f = np.zeros((nk, ns))
+        info = ScfInfo()
+        dp = C.POINTER(C.c_double)
+        _check(_LIB.pufe_scf_step_bloch(self._h, nk, kp.ctypes.data_as(dp), w.ctypes.data_as(dp),
+                                        ns, eps.ctypes.data_as(dp), pre, pim, ld, float(nelec),
+                                        float(kT), float(alpha), int(pulay), int(prec),
+                                        _ptr(rho_I, torch.float64),
+                                        _ptr(V_eff_in, torch.float64), _ptr(n, torch.float64),
+                                        _ptr(V_eff_out, torch.float64), f.ctypes.data_as(dp),
+                                        C.byref(info), _stream(stream)))
+        return f, info.as_dict()
+
     def pufe_assemble_HS_bloch(self, k, V, H=None, S=None, what=None, stream=None,
                                prec=PUFE_FP64):
         """H(k), S(k) at wavevector k: H and S are (re, im) pairs of nnz tensors."""
@@ -316,7 +353,7 @@ class Context:
                                            _ptr(Hi, f64), _ptr(Sr, f64), _ptr(Si, f64),
                                            _stream(stream)))
 
-    def pufe_density_bloch(self, k, Cre, Cim, f, rho, stream=None):
+    def pufe_density_bloch(self, k, Cre, Cim, f, rho, stream=None, prec=PUFE_FP64):
         import torch
         kk = (C.c_double * 3)(*[float(x) for x in k])
         if Cre.shape != Cim.shape or Cre.stride() != Cim.stride():
@@ -324,14 +361,15 @@ class Context:
         f64 = torch.float64
         _check(_LIB.pufe_density_bloch(self._h, kk, _ptr(Cre, f64), _ptr(Cim, f64),
                                        int(Cre.stride(0)), _ptr(f, f64), int(Cre.shape[1]),
-                                       _ptr(rho, f64), _stream(stream)))
+                                       int(prec), _ptr(rho, f64), _stream(stream)))
 
-    def pufe_assemble_HV_adjoint_bloch(self, k, Hbar_re, Hbar_im, Vbar, stream=None):
+    def pufe_assemble_HV_adjoint_bloch(self, k, Hbar_re, Hbar_im, Vbar, stream=None,
+                                       prec=PUFE_FP64):
         import torch
         kk = (C.c_double * 3)(*[float(x) for x in k])
         f64 = torch.float64
         _check(_LIB.pufe_assemble_HV_adjoint_bloch(self._h, kk, _ptr(Hbar_re, f64),
-                                                   _ptr(Hbar_im, f64), _ptr(Vbar, f64),
+                                                   _ptr(Hbar_im, f64), int(prec), _ptr(Vbar, f64),
                                                    _stream(stream)))
 
     def pufe_nonlocal_projections(self, projs, F, stream=None):
@@ -378,15 +416,17 @@ def pufe_build_mesh(wl: dict) -> Context:
     tau = (C.c_double * max(1, 3 * natoms))(*[c for _, t in wl["atoms"] for c in t])
     spec = (C.c_int * max(1, natoms))(*[int(s) for s, _ in wl["atoms"]])
     nel = int(wl["nel"])
+    fe_space = {"lagrange64": PUFE_FE_LAGRANGE64,
+                "serendipity32": PUFE_FE_SERENDIPITY32}[wl.get("fe", "lagrange64")]
     if wl.get("lattice") is not None:   # a general cell: rows a_1, a_2, a_3
         lat = (C.c_double * 9)(*[float(c) for row in wl["lattice"] for c in row])
         cell = _Cell((C.c_double * 3)(0.0, 0.0, 0.0), (C.c_int * 3)(nel, nel, nel), natoms, tau,
-                     spec, lat)
+                     spec, lat, fe_space)
     else:
         a = float(wl["a"])
         lat = None
         cell = _Cell((C.c_double * 3)(a, a, a), (C.c_int * 3)(nel, nel, nel), natoms, tau, spec,
-                     None)
+                     None, fe_space)
     keep = []
     sp = (_Species * max(1, len(wl["species"])))()
     for i, s in enumerate(wl["species"]):
@@ -399,7 +439,8 @@ def pufe_build_mesh(wl: dict) -> Context:
         sp[i] = _Species(len(orbs), n, l, m, z, float(s["r_c"]), float(s["r_e"]))
     q = wl["quad"]
     quad = _Quad(int(q["mode"]), int(q["p_far"]), int(q["p_near"]), int(q["p_min"]),
-                 int(q["p_max"]), float(q["tol"]), int(q["max_depth"]))
+                 int(q["p_max"]), float(q["tol"]), int(q["max_depth"]),
+                 int(q.get("device_tests", 0)))
     h = C.c_void_p()
     _check(lib.pufe_build_mesh(C.byref(cell), sp, len(wl["species"]), C.byref(quad), C.byref(h)))
     del lat

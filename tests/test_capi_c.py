@@ -29,8 +29,8 @@ int main(void) {
   const int n1[5] = {1, 2, 2, 2, 2}, l1[5] = {0, 0, 1, 1, 1}, m1[5] = {0, 0, -1, 0, 1};
   const double z1[5] = {2.70, 0.65, 0.65, 0.65, 0.65};
   pufe_species sp[2] = {{1, n0, l0, m0, z0, 1.5, 1.5}, {5, n1, l1, m1, z1, 1.5, 1.5}};
-  pufe_cell cell = {{4.0, 4.0, 4.0}, {2, 2, 2}, 2, tau, spec, NULL};   /* orthorhombic */
-  pufe_quad quad = {PUFE_QUAD_FIXED, 4, 4, 0, 0, 1e-6, 0};
+  pufe_cell cell = {{4.0, 4.0, 4.0}, {2, 2, 2}, 2, tau, spec, NULL, PUFE_FE_LAGRANGE64};
+  pufe_quad quad = {PUFE_QUAD_FIXED, 4, 4, 0, 0, 1e-6, 0, 0};
   pufe_ctx *ctx = NULL;
   pufe_status s;
   int64_t N = 0, nnz = 0, nq = 0, ne = 0, nb = 0, i;

@@ -70,6 +70,10 @@ def _compare(wl):
     lambda: W.ceal_like(nel=2),                    # general (triclinic) cells, Sec. 6.2
     lambda: W.ceal_like(nel=3, r_e=2.0),
     lambda: W.sheared_empty(nel=3),
+    # the cubic serendipity FE space (32 nodes per element, Sec. 6)
+    lambda: dict(W.small_two_atom(nel=2), fe="serendipity32"),
+    lambda: dict(W.small_two_atom(nel=1, quad_p=3), fe="serendipity32"),
+    lambda: dict(W.ceal_like(nel=2), fe="serendipity32"),
 ])
 def test_host_setup_matches_oracle(lib, maker):
     _compare(maker())
@@ -102,3 +106,9 @@ def test_compute_calls_need_a_device_context(lib):
     ctx = pufe.pufe_build_mesh(W.small_two_atom(nel=2))
     assert pufe._LIB.pufe_tabulate(ctx._h, 0, None) == 8  # PUFE_ESTATE
     assert b"without a CUDA device" in pufe._LIB.pufe_last_error()
+    # adaptive tests on the device need one: PUFE_ECUDA, no host fallback
+    wl = W.workload("c2_rocksalt_2cube")
+    wl["quad"] = dict(wl["quad"], device_tests=1)
+    with pytest.raises(pufe.PufeError) as ei:
+        pufe.pufe_build_mesh(wl)
+    assert ei.value.status == 3 and "device_tests" in str(ei.value)

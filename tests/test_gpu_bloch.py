@@ -151,3 +151,79 @@ def test_mixed_bloch_assembly_matches_oracle(name):
     assert float(Hi.abs().max()) == 0.0 and float(Si.abs().max()) == 0.0
     assert _rel(Hr.cpu().numpy(), H0.cpu().numpy()) < 1e-6
     assert _rel(Sr.cpu().numpy(), S0.cpu().numpy()) < 1e-6
+
+
+def _c3_like_large():
+    wl = W.workload("c3_cscl_4cube")
+    wl["species"] = [dict(s) for s in wl["species"]]
+    wl["species"][0]["orbitals"] = [o for o in wl["species"][0]["orbitals"] if o[0] >= 3]
+    wl["species"][0]["r_e"] = 1.5
+    wl["quad"] = dict(wl["quad"], mode=W.QUAD_FIXED, p_far=5, p_near=5)
+    return wl
+
+
+def _mixed_rule_sizes():
+    wl = W.small_two_atom(nel=4, a=6.0, r_c=1.2, r_e=3.0)
+    wl["quad"] = dict(mode=W.QUAD_PADAPT, p_far=6, p_near=10, p_min=9, p_max=11, tol=1e-6,
+                      max_depth=0)
+    return wl
+
+
+# every FP32 adjoint kernel: the FE-FE form and the slot-form strip (first
+# two), the tensor-core-class kernel (n_e > 128) and the per-point strip (11^3
+# rules)
+MIXED_DA_CASES = {
+    "two_atom_2cube": lambda: W.small_two_atom(nel=2, quad_p=6),
+    "c1_two_atom_4cube": lambda: W.workload("c1_two_atom_4cube"),
+    "c3_like_large_elements": _c3_like_large,
+    "p_adaptive_9_11": _mixed_rule_sizes,
+}
+
+
+@pytest.mark.parametrize("name", list(MIXED_DA_CASES))
+def test_mixed_bloch_density_and_adjoint_match_oracle(name):
+    """PUFE_TF32X3 density of complex states and adjoint of V -> H(k) against
+    the oracle's FP64 ones (the Gamma-point mixed bounds: 1e-5 for the FP32
+    density sums, 1e-4 for the adjoint); at k = 0 with real inputs both equal
+    the Gamma-point mixed calls bit for bit (phase 1 + 0i multiplies exactly)."""
+    wl = MIXED_DA_CASES[name]()
+    m = omesh.Mesh(wl)
+    rules = oq.all_rules(m)
+    ctx = pufe.pufe_build_mesh(wl)
+    ctx.pufe_tabulate(pufe.PUFE_TF32X3)
+    dev = torch.device("cuda:0")
+    k = 2.0 * math.pi / wl["a"] * K_FRAC
+    rng = np.random.default_rng(31)
+    nocc = 6
+    C = rng.standard_normal((m.n_dof, nocc)) + 1j * rng.standard_normal((m.n_dof, nocc))
+    f = W.random_occupations(nocc, seed=31)
+    Cr = torch.tensor(np.ascontiguousarray(C.real), device=dev)
+    Ci = torch.tensor(np.ascontiguousarray(C.imag), device=dev)
+    fd = torch.tensor(f, device=dev)
+    rho = torch.empty(ctx.n_q, dtype=torch.float64, device=dev)
+    ctx.pufe_density_bloch(k, Cr, Ci, fd, rho, prec=pufe.PUFE_TF32X3)
+    V = W.random_potential(len(rules[1]), seed=32)
+    Ho, _ = ob.assemble_HS_k(m, rules, V, k)
+    Hbar = Ho.copy()
+    Hbar.data = rng.standard_normal(Ho.nnz) + 1j * rng.standard_normal(Ho.nnz)
+    Hre = torch.tensor(Hbar.data.real.copy(), device=dev)
+    Him = torch.tensor(Hbar.data.imag.copy(), device=dev)
+    vbar = torch.empty_like(rho)
+    ctx.pufe_assemble_HV_adjoint_bloch(k, Hre, Him, vbar, prec=pufe.PUFE_TF32X3)
+    ctx.pufe_sync_status()
+    e_rho = _rel(rho.cpu().numpy(), ob.density_k(m, rules, C, f, k))
+    e_adj = _rel(vbar.cpu().numpy(), ob.adjoint_V_k(m, rules, Hbar, k))
+    print(f"\n{name}: mixed Bloch density {e_rho:.1e}, adjoint {e_adj:.1e}")
+    assert e_rho < 1e-5 and e_adj < 1e-4, (name, e_rho, e_adj)
+    # k = 0, real inputs: the Gamma-point mixed calls
+    zero = torch.zeros_like(Cr)
+    ctx.pufe_density_bloch((0.0, 0.0, 0.0), Cr, zero, fd, rho, prec=pufe.PUFE_TF32X3)
+    rho0 = torch.empty_like(rho)
+    ctx.pufe_density(Cr, fd, rho0, prec=pufe.PUFE_TF32X3)
+    ctx.pufe_assemble_HV_adjoint_bloch((0.0, 0.0, 0.0), Hre, torch.zeros_like(Hre), vbar,
+                                       prec=pufe.PUFE_TF32X3)
+    v0 = torch.empty_like(rho)
+    ctx.pufe_assemble_HV_adjoint(Hre, v0, prec=pufe.PUFE_TF32X3)
+    ctx.pufe_sync_status()
+    assert torch.equal(rho, rho0)
+    assert torch.equal(vbar, v0)

@@ -3,11 +3,15 @@
 converged to 1e-8 Ha) with all assemblies replayed from one CUDA graph, against
 the oracle's own SCF loop at three lattice constants; the mixed-precision
 sweep against the FP64 one within 1e-6 Ha per atom; and the fourth-order
-Birch-Murnaghan fit of the curve."""
+Birch-Murnaghan fit of the curve.  The same at the four k-points of the
+1/4-shifted 2x2x2 grid (time-reversal reduced): one step against the oracle's
+scf_step_k, the sweep against the oracle's k-point SCF loop."""
 import numpy as np
 import pytest
+import scipy.linalg as sla
 
-from oracle import assemble as oasm, eig as oeig, mesh as omesh, quadrature as oq, scf as oscf
+from oracle import assemble as oasm, bloch as ob, eig as oeig, mesh as omesh, quadrature as oq
+from oracle import scf as oscf
 from paper_1611_00731_gb300 import eos, pufe, workloads as W
 
 torch = pytest.importorskip("torch")
@@ -76,3 +80,106 @@ def test_birch_murnaghan_fit_of_the_sweep(fp64_sweep):
     # coarse 2^3 mesh's E(V) is smooth but not exactly of Birch-Murnaghan form)
     assert fit["rms"] < 1e-3 * (E.max() - E.min())
     assert fit["E0"] <= E.min() + 3.0 * fit["rms"]
+
+
+# ---- k-point sampling (Sec. 4, eqs. bloch, strong) ------------------------
+KP = eos.MP2_SHIFTED   # the 1/4-shifted 2x2x2 grid reduced by time reversal
+
+
+def _kpts(wl):
+    return [2.0 * np.pi / wl["a"] * np.asarray(k) for k in KP[0]], list(KP[1])
+
+
+def _oracle_states_k(m, rules, V, kpts, nstates):
+    eps, C = [], []
+    for k in kpts:
+        H, S = ob.assemble_HS_k(m, rules, V, k)
+        e, c = sla.eigh(H.toarray(), S.toarray(), subset_by_index=[0, nstates - 1])
+        eps.append(e)
+        C.append(c)
+    return eps, C
+
+
+def _oracle_scf_k(wl, tol=1e-8, nstates=6):
+    m = omesh.Mesh(wl)
+    rules = oq.all_rules(m)
+    K = oscf.fe_stiffness(m)
+    rho = oscf.ion_density(wl, rules[0])
+    n = np.full(len(rules[1]), wl["nelec"] / wl["a"] ** 3)
+    V, _, _ = oscf.effective_potential(m, rules, n, rho, K)
+    kpts, wk = _kpts(wl)
+    mixer = oscf.PulayMixer(4)
+    E = []
+    for _ in range(80):
+        eps, C = _oracle_states_k(m, rules, V, kpts, nstates)
+        r = oscf.scf_step_k(m, rules, wl, kpts, wk, eps, C, wl["nelec"], 0.01, 0.5, n, V, rho, K,
+                            mixer=mixer)
+        n, V = r["n_new"], r["V_eff"]
+        E.append(r["e_total"])
+        if len(E) > 1 and abs(E[-1] - E[-2]) < tol:
+            break
+    return E[-1]
+
+
+@pytest.mark.parametrize("prec", [pufe.PUFE_FP64, pufe.PUFE_TF32X3])
+def test_one_k_point_step_matches_oracle(prec):
+    """One pufe_scf_step_bloch at the four k-points against scf_step_k from
+    the same input density: the GPU's own H(k), S(k) and host eigensolve
+    against the oracle's (energies, mixed density and new potential)."""
+    wl = _cells()[3]
+    m = omesh.Mesh(wl)
+    rules = oq.all_rules(m)
+    K = oscf.fe_stiffness(m)
+    rho = oscf.ion_density(wl, rules[0])
+    n0 = np.full(len(rules[1]), wl["nelec"] / wl["a"] ** 3)
+    V0, _, _ = oscf.effective_potential(m, rules, n0, rho, K)
+    kpts, wk = _kpts(wl)
+    eps_o, C_o = _oracle_states_k(m, rules, V0, kpts, 6)
+    ro = oscf.scf_step_k(m, rules, wl, kpts, wk, eps_o, C_o, wl["nelec"], 0.01, 0.5, n0, V0, rho,
+                         K)
+    cell = eos._Cell(wl, prec, torch.device("cuda:0"), KP)
+    assert np.abs(cell.V_in.cpu().numpy() - V0).max() < 1e-10 * np.abs(V0).max()
+    cell.assemble()
+    torch.cuda.synchronize()
+    cell.step(6, 0.01, 0.5, 0, 1e-8)
+    info = cell.info
+    tol = 1e-10 if prec == pufe.PUFE_FP64 else 2e-6
+    for key in ("e_band", "e_dc", "e_es", "e_xc", "e_ts", "e_total"):
+        assert abs(info[key] - ro[key]) < tol * max(1.0, abs(ro[key])), (key, info[key], ro[key])
+    dn = np.abs(cell.n.cpu().numpy() - ro["n_new"]).max() / np.abs(ro["n_new"]).max()
+    dv = np.abs(cell.V_out.cpu().numpy() - ro["V_eff"]).max() / np.abs(ro["V_eff"]).max()
+    print(f"\nk-point step prec {prec}: e_total {info['e_total'] - ro['e_total']:.1e}, "
+          f"n {dn:.1e}, V {dv:.1e}")
+    assert dn < tol * 10 and dv < tol * 10
+
+
+@pytest.fixture(scope="module")
+def fp64_sweep_k():
+    res = eos.scf_sweep(_cells(), prec=pufe.PUFE_FP64, nstates=6, tol=1e-8, kpoints=KP)
+    assert all(r["converged"] for r in res)
+    return res
+
+
+def test_k_point_sweep_matches_oracle_scf(fp64_sweep_k):
+    for i in (0, 5, 10):
+        wl = _cells()[i]
+        e_o = _oracle_scf_k(wl)
+        assert abs(fp64_sweep_k[i]["e_total"] - e_o) < 1e-8, (wl["a"], fp64_sweep_k[i]["e_total"],
+                                                               e_o)
+
+
+def test_mixed_precision_k_point_sweep_within_target(fp64_sweep_k):
+    res = eos.scf_sweep(_cells(), prec=pufe.PUFE_TF32X3, nstates=6, tol=1e-8, kpoints=KP)
+    assert all(r["converged"] for r in res)
+    dE = max(abs(a["e_total"] - b["e_total"]) for a, b in zip(res, fp64_sweep_k)) / 2
+    V = np.array([r["a"] ** 3 for r in fp64_sweep_k])
+    E = np.array([r["e_total"] for r in fp64_sweep_k])
+    Em = np.array([r["e_total"] for r in res])
+    fit, fitm = eos.birch_murnaghan4_fit(V, E), eos.birch_murnaghan4_fit(V, Em)
+    print(f"\n4 k-points: mixed vs FP64 total energy max {dE:.2e} Ha/atom; "
+          f"a0 {fit['V0'] ** (1 / 3):.5f} / {fitm['V0'] ** (1 / 3):.5f} bohr, "
+          f"B0 {fit['B0'] * eos.HA_PER_BOHR3_IN_GPA:.3f} / "
+          f"{fitm['B0'] * eos.HA_PER_BOHR3_IN_GPA:.3f} GPa")
+    assert dE < 1e-6
+    assert V.min() < fit["V0"] < V.max() and fit["B0"] > 0.0
+    assert abs(fitm["V0"] - fit["V0"]) < 1e-3 * fit["V0"]
