@@ -107,6 +107,7 @@ struct DeviceArrays {
   int32_t *sitems = nullptr;   // E-E kernel of S: (order index, first pair, end pair) triples
   int32_t *citems = nullptr;   // strip kernel: (order index, first cell, end cell) triples
   int32_t *pitems = nullptr;   // FP32 density / per-point adjoint: (order index, first point, end point)
+  int32_t *tblk = nullptr;     // nelem + 1: FP32 tabulation CTAs per element, prefix summed
   int8_t *eeform = nullptr;   // per element: E x E form of the strip (0 model, 1 pair, 2 direct)
   unsigned *err = nullptr;    // device error flag
   // side stream and events: the FE-FE kernel of the mixed assembly runs on
@@ -147,6 +148,7 @@ struct pufe_ctx {
   int n_sitems = 0;           // items of the E-E overlap kernel's list (slot-pair ranges)
   int n_citems = 0;           // items of the strip kernel's list ((sub)cell ranges)
   int n_pitems = 0;           // items of the FP32 per-point list (point ranges of every element)
+  int n_tblk = 0;             // CTAs of the FP32 tabulation (TAB_CHUNK table items each)
   int max_part_p = 0;         // largest points-per-axis of any (sub)cell
   int strip_stage = 0;        // floats of the strip kernel's shared-memory stage
   uint32_t strip_pmask = 0;   // per-axis counts (bit p) of the strip kernel's cells
@@ -178,6 +180,8 @@ namespace pufe {
 // Elements (n_e <= 128) whose enrichment strip of the adjoint runs in the
 // slot form: at most 16 enrichment slots and 10 points per axis per (sub)cell.
 __host__ __device__ inline bool adjoint_sf_fits(int A, int pmax) { return A <= 16 && pmax <= 10; }
+// (slot, padded point) items of the FP32 enrichment table per tabulation CTA
+constexpr int TAB_CHUNK = 2048;
 
 // ---------------------------------------------------------------------------
 // basis functions shared by host setup and device kernels

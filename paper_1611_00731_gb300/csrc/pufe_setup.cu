@@ -1506,6 +1506,15 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
   }
   ctx->n_pitems = (int)(pitems.size() / 3);
 
+  // CTAs of the FP32 tabulation: TAB_CHUNK table items of one element each
+  std::vector<int32_t> tblk(nelem + 1, 0);
+  for (int64_t e = 0; e < nelem; ++e) {
+    const int64_t items = toff32[e + 1] - toff32[e];
+    if (items > INT32_MAX) return fail(PUFE_EINVAL, "element table beyond 32-bit item indices");
+    tblk[e + 1] = tblk[e] + (int32_t)((items + TAB_CHUNK - 1) / TAB_CHUNK);
+  }
+  ctx->n_tblk = tblk[nelem];
+
   pufe_status st;
   auto &D = ctx->d;
   if (ctx->on_device) {
@@ -1539,6 +1548,7 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
   if (!sitems.empty() && (st = upload(&D.sitems, sitems)) != PUFE_OK) return st;
   if (!citems.empty() && (st = upload(&D.citems, citems)) != PUFE_OK) return st;
   if (!pitems.empty() && (st = upload(&D.pitems, pitems)) != PUFE_OK) return st;
+  if ((st = upload(&D.tblk, tblk)) != PUFE_OK) return st;
   if ((st = upload(&D.eeform, ctx->eeform_host)) != PUFE_OK) return st;
   if (fe_exact) {
     if ((st = upload(&D.Tfe, TF)) != PUFE_OK) return st;
@@ -1583,7 +1593,7 @@ static void free_device(pufe_ctx *ctx) {
                   D.toff, D.psi, D.psi32, D.qpoff, D.qdat, D.ptab, D.vpad, D.toff32, D.eorig,
                   D.Tfe, D.Sfe, D.S0, D.partoff, D.part_p, D.part_q,
                   D.orb, D.orbf, D.rowptr, D.col, D.soff, D.smap, D.order, D.wsplit,
-                  D.titems, D.sitems, D.citems, D.pitems, D.eeform, D.err};
+                  D.titems, D.sitems, D.citems, D.pitems, D.tblk, D.eeform, D.err};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (D.ev_fork) cudaEventDestroy(D.ev_fork);

@@ -229,32 +229,37 @@ __device__ __forceinline__ void lagrange3f(float t, float L[4], float dL[4]) {
 // with the element-origin displacement precomputed in FP64 and split into two
 // floats, so it keeps FP32 accuracy even next to the nucleus.
 // ---------------------------------------------------------------------------
-__global__ void k_tabulate_f32(const int64_t *__restrict__ qpoff, const float4 *__restrict__ qdat,
-                               const int32_t *__restrict__ aoff, const int32_t *__restrict__ alist,
-                               const int64_t *__restrict__ toff32, const OrbitalF *__restrict__ orbf,
-                               const float *__restrict__ eorig, float ax, float ay, float az,
-                               float hx, float hy, float hz, int nelem,
-                               float *__restrict__ psi) {
+constexpr int TAB_NT = 256;
+
+__global__ void __launch_bounds__(TAB_NT) k_tabulate_f32(
+    const int64_t *__restrict__ qpoff, const float4 *__restrict__ qdat,
+    const int32_t *__restrict__ aoff, const int32_t *__restrict__ alist,
+    const int64_t *__restrict__ toff32, const OrbitalF *__restrict__ orbf,
+    const float *__restrict__ eorig, float ax, float ay, float az, float hx, float hy, float hz,
+    const int32_t *__restrict__ tblk, int nelem, float *__restrict__ psi) {
   const float av[3] = {ax, ay, az};
   const float inv_a[3] = {1.0f / ax, 1.0f / ay, 1.0f / az};
   const float hh[3] = {0.5f * hx, 0.5f * hy, 0.5f * hz};
-  // one thread per (element, slot, padded point) over the whole table, the
-  // element found by bisection of the table offsets (so elements with many
-  // points and slots spread over many CTAs)
-  const int64_t total = toff32[nelem];
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    int lo_e = 0, hi_e = nelem;   // toff32[lo_e] <= t < toff32[hi_e]
+  // CTA b takes the (slot, padded point) items [c TAB_CHUNK, (c + 1) TAB_CHUNK)
+  // of element e, c = b - tblk[e] (tblk: CTAs per element, prefix summed), so
+  // elements with many points and slots spread over many CTAs
+  __shared__ int s_e;
+  if (threadIdx.x == 0) {
+    int lo_e = 0, hi_e = nelem;   // tblk[lo_e] <= b < tblk[hi_e]
     while (hi_e - lo_e > 1) {
       const int mid = (lo_e + hi_e) >> 1;
-      if (toff32[mid] <= t) lo_e = mid; else hi_e = mid;
+      if (tblk[mid] <= (int)blockIdx.x) lo_e = mid; else hi_e = mid;
     }
-    const int e = lo_e;
-    const int Qp = (int)(qpoff[e + 1] - qpoff[e]);
-    const int A = aoff[e + 1] - aoff[e];
-    float *out = psi + 4 * toff32[e];
-    const int idx = (int)(t - toff32[e]);
-    if (A <= 0 || Qp <= 0 || idx >= Qp * A) continue;
+    s_e = lo_e;
+  }
+  __syncthreads();
+  const int e = s_e;
+  const int Qp = (int)(qpoff[e + 1] - qpoff[e]);
+  const int A = aoff[e + 1] - aoff[e];
+  float *out = psi + 4 * toff32[e];
+  const int base = ((int)blockIdx.x - tblk[e]) * TAB_CHUNK;
+  const int end = min(base + TAB_CHUNK, Qp * A);
+  for (int idx = base + threadIdx.x; idx < end; idx += TAB_NT) {
     const int slot = idx / Qp, q = idx - slot * Qp;
     const OrbitalF o = orbf[alist[aoff[e] + slot]];
     const float *eo = eorig + 8 * (int64_t)(aoff[e] + slot);
@@ -1076,16 +1081,11 @@ __global__ void __launch_bounds__(AS_NT) k_adjoint_strip_f32(
 pufe_status launch_tabulate_f32(pufe_ctx *ctx, cudaStream_t st) {
   if (ctx->psi32_len == 0) return PUFE_OK;
   auto &D = ctx->d;
-  {
-    int nsm = 0;
-    PUFE_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device));
-    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((ctx->psi32_len + 255) / 256,
-                                                                  (int64_t)nsm * 16));
-    k_tabulate_f32<<<(unsigned)blocks, 256, 0, st>>>(
-        D.qpoff, D.qdat, D.aoff, D.alist, D.toff32, D.orbf, D.eorig, (float)ctx->a[0],
-        (float)ctx->a[1], (float)ctx->a[2], (float)ctx->h[0], (float)ctx->h[1],
-        (float)ctx->h[2], (int)ctx->nelem, D.psi32);
-  }
+  if (ctx->n_tblk <= 0) return PUFE_OK;
+  k_tabulate_f32<<<(unsigned)ctx->n_tblk, TAB_NT, 0, st>>>(
+      D.qpoff, D.qdat, D.aoff, D.alist, D.toff32, D.orbf, D.eorig, (float)ctx->a[0],
+      (float)ctx->a[1], (float)ctx->a[2], (float)ctx->h[0], (float)ctx->h[1], (float)ctx->h[2],
+      D.tblk, (int)ctx->nelem, D.psi32);
   PUFE_CUDA_TRY(cudaGetLastError());
   return PUFE_OK;
 }
