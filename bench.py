@@ -31,10 +31,12 @@ UNIT = "QPC/s"
 L2_BYTES = 129 * 1024 * 1024
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 TF32_PER_BF16 = 1.1 / 2.25      # nominal dense TF32 / BF16 tensor rates
-# DRAM bytes (read + write) per launch of the assembly call's kernels, from
-# the ncu capture summarised under profiles/ (None: the kernels changed since
-# the last capture)
-ASM_TRAFFIC = {}
+# DRAM bytes (read + write) per launch of the assembly call's kernels (the
+# strip, the FE-FE block and the E-E block of S) and of the strip alone, from
+# the one-kernel ncu captures summarised under profiles/ (absent: not
+# captured for that workload)
+ASM_TRAFFIC = {("c2_rocksalt_12cube", "tf32x3"): 318.8e6}
+STRIP_TRAFFIC = {("c2_rocksalt_12cube", "tf32x3"): 168.0e6}
 
 
 def _dist():
@@ -578,7 +580,8 @@ def run_pufe(args):
                 "fp32_cuda_core_frac": a_strip / FP32_PEAK_TFLOPS,
                 "flops_per_launch": flops_strip,
                 "flops_count": "sum over strip elements of 5 Q_e (n_e (n_e + 1) - 64 * 65)",
-                "algorithmic_bytes_per_launch": bytes_strip}
+                "algorithmic_bytes_per_launch": bytes_strip,
+                "traffic": STRIP_TRAFFIC.get((args.workload, args.prec))}
         roof["kernel_ms"] = km
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
