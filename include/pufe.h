@@ -442,10 +442,11 @@ pufe_status pufe_selftest_timeout(pufe_ctx *ctx, uint64_t wait_ns, void *stream)
 pufe_status pufe_profile_assembly(pufe_ctx *ctx, int enable);
 
 /* Durations in ms of the last instrumented assembly call, ms[5] (host):
- * [0] the whole call, [1] the FE-FE kernels (the V-block table and the row
- * writer of every CSR entry), [2] the enrichment-enrichment kernel of S, [3]
- * the tensor-core tile kernel, [4] the enrichment strip kernel; 0 for a
- * kernel the call did not launch.  Waits for the call to finish.  PUFE_ESTATE if no
+ * [0] the whole call, [1] the FE-FE kernel (kinetic constants and the V
+ * block), [2] the enrichment-enrichment kernel of S, [3] the tensor-core tile
+ * kernel, [4] the enrichment strip kernel; 0 for a kernel the call did not
+ * launch.  Kernels on the two streams overlap, so the parts need not add up
+ * to the whole.  Waits for the call to finish.  PUFE_ESTATE if no
  * instrumented call was made. */
 pufe_status pufe_profile_read(pufe_ctx *ctx, double *ms);
 
