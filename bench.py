@@ -292,6 +292,77 @@ def c3_timing(dev, flush, stream, reps=5):
     return out
 
 
+def c5_timing(dev, flush, stream, reps=3):
+    """The equation-of-state configuration's hot path at its full size: the
+    2x2x2 supercell of the rocksalt cube (64 atoms, 16^3 elements per cube,
+    32^3 in all) at the four k-points of the 1/4-shifted 2x2x2 grid reduced
+    by time reversal: per k-point the mixed-precision H(k), S(k) and the
+    density of 64 complex states, L2 flushed before each timed 4-k step; one
+    FP64 k-point beside it.  (The self-consistent sweep at this size needs an
+    iterative complex eigensolver, which the library does not provide.)"""
+    import numpy as np
+    import torch
+
+    from paper_1611_00731_gb300 import eos, pufe, workloads as W
+
+    name = "c5_rocksalt_2x2x2_16cube"
+    wl = W.workload(name)
+    t0 = time.time()
+    ctx = pufe.pufe_build_mesh(wl)
+    build_s = time.time() - t0
+    nocc = int(wl["nocc"])
+    a = float(wl["a"])
+    ks = [2.0 * np.pi / a * np.asarray(k) for k in eos.MP2_SHIFTED[0]]
+    wk = eos.MP2_SHIFTED[1]
+    V = torch.tensor(W.random_potential(ctx.n_q, seed=5), device=dev)
+    rng = np.random.default_rng(5)
+    Cr = torch.tensor(rng.standard_normal((ctx.n_dof, nocc)), device=dev)
+    Ci = torch.tensor(rng.standard_normal((ctx.n_dof, nocc)), device=dev)
+    f = torch.tensor(W.random_occupations(nocc, seed=5), device=dev)
+    mk = lambda: torch.empty(ctx.nnz, dtype=torch.float64, device=dev)
+    H, S = (mk(), mk()), (mk(), mk())
+    rho = torch.empty(ctx.n_q, dtype=torch.float64, device=dev)
+    nk = torch.empty_like(rho)
+
+    def timed(fn, n=reps):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(n):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    def kstep(prec, kl):
+        for i, k in enumerate(kl):
+            ctx.pufe_assemble_HS_bloch(k, V, H, S, prec=prec)
+            ctx.pufe_density_bloch(k, Cr, Ci, f, rho if i == 0 else nk, prec=prec)
+            if i:
+                rho.add_(nk, alpha=wk[i] / wk[0])
+
+    ctx.pufe_tabulate(pufe.PUFE_TF32X3)
+    ms = timed(lambda: kstep(pufe.PUFE_TF32X3, ks))
+    asm = timed(lambda: ctx.pufe_assemble_HS_bloch(ks[0], V, H, S, prec=pufe.PUFE_TF32X3))
+    den = timed(lambda: ctx.pufe_density_bloch(ks[0], Cr, Ci, f, rho, prec=pufe.PUFE_TF32X3))
+    ctx.pufe_tabulate(pufe.PUFE_FP64)
+    ms64 = timed(lambda: kstep(pufe.PUFE_FP64, ks[:1]), n=1)
+    ctx.pufe_sync_status()
+    return {"workload": name, "atoms": len(wl["atoms"]), "n_elem": ctx.n_elem, "n_q": ctx.n_q,
+            "n_dof": ctx.n_dof, "nnz": ctx.nnz, "states": nocc, "kpoints": len(ks),
+            "build_s": round(build_s, 2), "tf32x3_4k_step_ms": ms,
+            "value": len(ks) * ctx.n_q / (ms * 1e-3), "unit": "QPC/s",
+            "tf32x3_assemble_bloch_ms": asm, "tf32x3_density_bloch_ms": den,
+            "fp64_1k_step_ms": ms64, "fp64_over_tf32x3_per_k": ms64 / (ms / len(ks)),
+            "note": "per k-point: mixed H(k), S(k) (FP32 element blocks, FP64 accumulation) "
+                    "and the density of 64 complex states; random V and C"}
+
+
 def projection_timing(ctx, wl, dev, reps=3):
     """Time of the projections onto s + p Gaussian projectors (r_p = 0.8) on
     every atom of the workload (FP64, Gamma point)."""
@@ -510,6 +581,8 @@ def run_pufe(args):
                if args.scf and args.prec != "fp64" else None)
     c3 = (c3_timing(dev, flush, stream)
           if args.scf and args.workload == "c2_rocksalt_12cube" else None)
+    c5 = (c5_timing(dev, flush, stream)
+          if args.scf and args.workload == "c2_rocksalt_12cube" else None)
 
     if ws > 1:
         total_ms, e2e_ms = _max_over_ranks([total_ms, e2e_ms], dev)
@@ -603,6 +676,7 @@ def run_pufe(args):
         "bloch": bloch,
         "nonlocal": nonlocal_,
         "c3": c3,
+        "c5": c5,
         "fp64_path": (None if fp64_ms is None else {
             "ms_per_step": fp64_ms, "speedup_of_this_path": fp64_ms / ms_per_step,
             "note": "same step on the plain FP64 kernels (direct element contraction, the "

@@ -92,6 +92,18 @@ def workload(name: str) -> dict:
                     quad=dict(mode=QUAD_PADAPT, p_far=6, p_near=10, p_min=6,
                               p_max=10, tol=1e-6, max_depth=0),
                     nocc=8, nelec=16.0)
+    if name.startswith("c5_rocksalt_2x2x2"):
+        # 2x2x2 supercell of the LiH-like rocksalt cube (64 atoms, a = 15.2);
+        # the name gives the elements per conventional cube ("..._16cube":
+        # 32^3 elements in all, the equation-of-state configuration)
+        per = int(name.split("_")[3].replace("cube", "")) if name.count("_") >= 3 else 16
+        c = workload(f"c2_rocksalt_{per}cube")
+        a0 = c["a"]
+        atoms = [(s, tuple(t[d] + a0 * m[d] for d in range(3)))
+                 for m in [(i, j, k) for k in range(2) for j in range(2) for i in range(2)]
+                 for s, t in c["atoms"]]
+        return dict(name=name, a=2 * a0, nel=2 * per, species=c["species"], atoms=atoms,
+                    quad=c["quad"], nocc=64, nelec=128.0)
     if name.startswith("c3_cscl"):
         # CsCl-type a=5.8, Ce-like + Al-like, 16^3 elements, h-adaptive depth 1
         nel = int(name.split("_")[2].replace("cube", "")) if name.count("_") >= 2 else 16
