@@ -215,9 +215,10 @@ def _enriched_element_identities(m, rules, e, V):
     xi = 2.0 * (p - lo) / m.h - 1.0
     mono, gmono = _monomials(xi, m.h)
     Pv = _vertex_matrix()
+    nf = m.nfe_e   # FE columns: 64 tricubic or 32 serendipity
     by_alpha = {}
     for j, (dof, lv, k) in enumerate(m.elem_cols[e]):
-        by_alpha.setdefault(k, {})[lv] = 64 + j
+        by_alpha.setdefault(k, {})[lv] = nf + j
     full = {k: c for k, c in by_alpha.items() if len(c) == 8}
     assert full, "the element needs an enrichment on all 8 vertices"
     psi = {}
@@ -241,16 +242,21 @@ def _enriched_element_identities(m, rules, e, V):
             Ho = Pv.T @ He[np.ix_(ca, cb)] @ Pv
             So = Pv.T @ Se[np.ix_(ca, cb)] @ Pv
             worst = max(worst, np.abs(Ho - Hc).max() / hs, np.abs(So - Sc).max() / ss)
-        # FE x E through the tricubic reproduction u_i = t(node_i)
+        # FE x E through the FE space's reproduction u_i = t(node_i): any
+        # polynomial of degree <= 3 per axis for the tricubic space; the
+        # cubic serendipity space's own monomials (P3 and the superlinear
+        # ones) for the serendipity space
         nodes = np.array([[ofe.CUBIC_NODES[i & 3], ofe.CUBIC_NODES[(i >> 2) & 3],
-                           ofe.CUBIC_NODES[i >> 4]] for i in range(64)])
-        for powers in ((0, 0, 0), (1, 0, 0), (0, 2, 1), (3, 1, 2), (2, 3, 3)):
+                           ofe.CUBIC_NODES[i >> 4]] for i in m.fe_local])
+        polys = (((0, 0, 0), (1, 0, 0), (0, 2, 1), (3, 1, 2), (2, 3, 3)) if nf == 64 else
+                 ((0, 0, 0), (1, 0, 0), (0, 2, 1), (3, 1, 1), (1, 1, 3)))
+        for powers in polys:
             u = _tricubic_poly(nodes, m.h, powers)[0]
             t, gt = _tricubic_poly(xi, m.h, powers)
             hc = 0.5 * np.einsum("dq,q,dqj->j", gt, w, Ga) + np.einsum("q,q,qj->j", t, w * v, fa)
             sc = np.einsum("q,q,qj->j", t, w, fa)
-            ho = u @ He[:64, ca] @ Pv
-            so = u @ Se[:64, ca] @ Pv
+            ho = u @ He[:nf, ca] @ Pv
+            so = u @ Se[:nf, ca] @ Pv
             worst = max(worst, np.abs(ho - hc).max() / hs, np.abs(so - sc).max() / ss)
     return worst
 
@@ -267,6 +273,18 @@ def test_enriched_blocks_reproduce_multilinear_times_enrichment():
         m, rules = _setup(_all_enriched_cell(nel))
         nq = len(rules[1])
         for V in (np.zeros(nq), W.random_potential(nq, seed=31)):
+            for e in (0, m.nelem - 1):
+                assert _enriched_element_identities(m, rules, e, V) < 1e-12, (nel, e)
+
+
+def test_enriched_blocks_on_the_serendipity_space():
+    """The same closed forms with the cubic serendipity FE part (its FE x E
+    block through the serendipity space's own reproduced monomials)."""
+    for nel in (2, 3):
+        m, rules = _setup(dict(_all_enriched_cell(nel), fe="serendipity32"))
+        assert m.nfe_e == 32
+        nq = len(rules[1])
+        for V in (np.zeros(nq), W.random_potential(nq, seed=33)):
             for e in (0, m.nelem - 1):
                 assert _enriched_element_identities(m, rules, e, V) < 1e-12, (nel, e)
 
