@@ -105,6 +105,9 @@ struct DeviceArrays {
   // `order`, first chunk, end chunk; chunks of 8 padded points), largest first
   int32_t *titems = nullptr;
   int32_t *sitems = nullptr;   // E-E kernel of S: (order index, first pair, end pair) triples
+  // E-E block of S in the Gram form, 5 per item: (order index, row tile,
+  // column tile, first point, end point); tiles of 32 (gitems32) or 64 columns
+  int32_t *gitems32 = nullptr, *gitems64 = nullptr;
   int32_t *citems = nullptr;   // strip kernel: (order index, first cell, end cell) triples
   int32_t *pitems = nullptr;   // FP32 density / per-point adjoint: (order index, first point, end point)
   int32_t *tblk = nullptr;     // nelem + 1: FP32 tabulation CTAs per element, prefix summed
@@ -146,6 +149,7 @@ struct pufe_ctx {
   int64_t n_wsplit = 0;       // items of the FP64 point-range work list (0: none)
   int n_titems = 0;           // items of the mixed path's list for the n_e > 128 elements
   int n_sitems = 0;           // items of the E-E overlap kernel's list (slot-pair ranges)
+  int n_gitems32 = 0, n_gitems64 = 0;   // items of the Gram-form lists
   int n_citems = 0;           // items of the strip kernel's list ((sub)cell ranges)
   int n_pitems = 0;           // items of the FP32 per-point list (point ranges of every element)
   int n_tblk = 0;             // CTAs of the FP32 tabulation (TAB_CHUNK table items each)
@@ -182,6 +186,11 @@ namespace pufe {
 __host__ __device__ inline bool adjoint_sf_fits(int A, int pmax) { return A <= 16 && pmax <= 10; }
 // (slot, padded point) items of the FP32 enrichment table per tabulation CTA
 constexpr int TAB_CHUNK = 2048;
+// Shared-memory stage of the E-E overlap kernel (floats): elements whose
+// slots' Psi values on one (sub)cell exceed it take the Gram form instead
+constexpr int SEE_STAGE_MAX_F = 8192;
+// points per Gram-form work item
+constexpr int GRAM_QCHUNK = 512;
 
 // ---------------------------------------------------------------------------
 // basis functions shared by host setup and device kernels

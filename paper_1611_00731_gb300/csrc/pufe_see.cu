@@ -285,16 +285,164 @@ __global__ void __launch_bounds__(SE_NT) k_see(
   }
 }
 
+
+// Gram form, for elements whose (sub)cells hold more Psi values than the
+// projection kernel's stage: S_rs = sum_q c_r(q) c_s(q) over the element's
+// points with the column values c_r = s_alpha phi_v as unevaluated pairs:
+// s_alpha = fl(sqrt(w) Psi_alpha) as above, phi_v = l_x l_y l_z with the exact
+// halved linears l = (1 -+ xi) / 2 of the vertex's bits (the same factors as
+// the projection form), each product of a pair and an FP32 value kept as a
+// pair (~2^-48), the pair products and their sums as in ff_fma.  Work item
+// b: (order index, row tile, column tile, first point, end point) =
+// items[5 b .. 5 b + 4]; tiles of 16 TB enrichment columns, each thread a
+// TB x TB block of (r, s) pairs; points in chunks of GK, the chunk's column
+// values staged in shared memory (hi and lo parts apart, point-major).  The
+// lower triangle (r >= s) goes into both triangles of S; the point ranges of
+// an element meet in the FP64 atomics.
+constexpr int GK = 32;
+
+template <bool BLOCH, int TB>
+__global__ void __launch_bounds__(SE_NT) k_see_gram(
+    const int32_t *__restrict__ order, const int32_t *__restrict__ items,
+    const int64_t *__restrict__ qpoff, const float4 *__restrict__ qdat,
+    const int64_t *__restrict__ doff, const int32_t *__restrict__ ecol,
+    const int32_t *__restrict__ aoff, const int64_t *__restrict__ toff32,
+    const float *__restrict__ psi, const int64_t *__restrict__ soff,
+    const int32_t *__restrict__ smap, double *__restrict__ S, unsigned *err,
+    const uint8_t *__restrict__ eshift, PhaseTab ph, double *__restrict__ Si) {
+  constexpr int T = 16 * TB;   // columns per tile
+  __shared__ float rh[GK][T], rl[GK][T], ch[GK][T], cl[GK][T];
+  __shared__ double s_phr[8], s_phi[8];
+  const int tid = threadIdx.x;
+  const int *it5 = items + 5 * blockIdx.x;
+  const int e = order[it5[0]], rt = it5[1], ct = it5[2], qa = it5[3], qb = it5[4];
+  const int n = (int)(doff[e + 1] - doff[e]), ne = n - 64;
+  const int A = aoff[e + 1] - aoff[e];
+  if (ne <= 0 || ct > rt || (rt + 1) * T > ((ne + T - 1) / T) * T || qa < 0 || qb <= qa ||
+      (int64_t)qb > qpoff[e + 1] - qpoff[e]) {
+    if (tid == 0) atomicOr(err, DEVERR_SHAPE);
+    return;
+  }
+  if (BLOCH && tid < 8) {
+    s_phr[tid] = ph.re[tid];
+    s_phi[tid] = ph.im[tid];
+  }
+  const int32_t *ecs = ecol + (doff[e] - 64ll * e);
+  const float *pe = psi + 4 * toff32[e];
+  const float4 *qe = qdat + qpoff[e];
+  const int r0 = rt * T, c0 = ct * T;
+  const int ti = tid >> 4, tj = tid & 15;
+  ff acc[TB][TB];
+#pragma unroll
+  for (int a = 0; a < TB; ++a)
+#pragma unroll
+    for (int b = 0; b < TB; ++b) acc[a][b] = {0.0f, 0.0f};
+  // c_r at point q of the element (zero past the element's columns)
+  auto colval = [&](int r, int q) -> ff {
+    if (r >= ne) return {0.0f, 0.0f};
+    const int code = ecs[r], lv = code & 7, slot = code >> 3;
+    if (slot >= A) return {0.0f, 0.0f};
+    const float4 x4 = qe[q];
+    const float xs[3] = {x4.x, x4.y, x4.z};
+    float l[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+      l[d] = ((lv >> d) & 1) ? 0.5f * __fadd_rn(1.0f, xs[d]) : 0.5f * __fsub_rn(1.0f, xs[d]);
+    const float sv = __fmul_rn(__fsqrt_rn(x4.w), pe[((int64_t)(q >> 3) * A + slot) * 32 + (q & 7)]);
+    ff t = ff_prod(l[0], l[1]);                        // exact
+    ff u = ff_prod(t.hi, l[2]);
+    u.lo = __fmaf_rn(t.lo, l[2], u.lo);                // phi_v as a pair
+    ff c = ff_prod(u.hi, sv);
+    c.lo = __fmaf_rn(u.lo, sv, c.lo);                  // s phi_v as a pair
+    return ff_norm(c);
+  };
+  for (int q0 = qa; q0 < qb; q0 += GK) {
+    __syncthreads();   // the previous chunk's readers are done
+    for (int o = tid; o < GK * T; o += SE_NT) {
+      const int kq = o / T, j = o - kq * T, q = q0 + kq;
+      ff vr = {0.0f, 0.0f}, vc = {0.0f, 0.0f};
+      if (q < qb) {
+        vr = colval(r0 + j, q);
+        vc = (ct == rt) ? vr : colval(c0 + j, q);
+      }
+      rh[kq][j] = vr.hi;
+      rl[kq][j] = vr.lo;
+      ch[kq][j] = vc.hi;
+      cl[kq][j] = vc.lo;
+    }
+    __syncthreads();
+    const int nk = min(GK, qb - q0);
+    for (int kq = 0; kq < nk; ++kq) {
+      ff xr[TB], xc[TB];
+#pragma unroll
+      for (int a = 0; a < TB; ++a) xr[a] = {rh[kq][ti * TB + a], rl[kq][ti * TB + a]};
+#pragma unroll
+      for (int b = 0; b < TB; ++b) xc[b] = {ch[kq][tj * TB + b], cl[kq][tj * TB + b]};
+#pragma unroll
+      for (int a = 0; a < TB; ++a)
+#pragma unroll
+        for (int b = 0; b < TB; ++b) acc[a][b] = ff_fma(xr[a], xc[b], acc[a][b]);
+    }
+  }
+  // the lower triangle into both triangles of S
+  const int32_t *m = smap + soff[e];
+  const uint8_t *esh = BLOCH ? eshift + doff[e] : nullptr;
+#pragma unroll
+  for (int a = 0; a < TB; ++a)
+#pragma unroll
+    for (int b = 0; b < TB; ++b) {
+      const int r = r0 + ti * TB + a, sc = c0 + tj * TB + b;
+      if (r >= ne || sc >= ne || sc > r) continue;
+      const ff pv = ff_norm(acc[a][b]);
+      const double v = (double)pv.hi + (double)pv.lo;
+      const int s_rs = m[(64 + r) * n + 64 + sc], s_sr = m[(64 + sc) * n + 64 + r];
+      if (BLOCH) {   // (r, s) with conj(ph_r) ph_s, (s, r) with its conjugate
+        const int ca = esh[64 + r], cb = esh[64 + sc];
+        const double pr_ = s_phr[ca] * s_phr[cb] + s_phi[ca] * s_phi[cb];
+        const double pi_ = s_phr[ca] * s_phi[cb] - s_phi[ca] * s_phr[cb];
+        atomicAdd(S + s_rs, v * pr_);
+        atomicAdd(Si + s_rs, v * pi_);
+        if (r != sc) {
+          atomicAdd(S + s_sr, v * pr_);
+          atomicAdd(Si + s_sr, -v * pi_);
+        }
+      } else {
+        atomicAdd(S + s_rs, v);
+        if (r != sc) atomicAdd(S + s_sr, v);
+      }
+    }
+}
+
 }  // namespace
 
-// Shared-memory budget of the Psi stage (floats); cells with more enrichment
-// values than this read the FP32 table directly.
-static constexpr int SEE_STAGE_MAX_F = 8192;
+// Work area of the projection form (FP32 pairs): the stage outputs of a chunk
+// of slot pairs.
 static constexpr int SEE_WORK_FF = 2048;
 
 pufe_status launch_see(pufe_ctx *ctx, const PhaseTab *ph, double *S, double *Si, cudaStream_t st) {
-  if (ctx->n_sitems <= 0) return PUFE_OK;
   auto &D = ctx->d;
+  // the Gram form first (the elements too large for the stage: the heaviest
+  // items), 32- and 64-column tiles
+  auto gram = [&](auto k32, auto k64, const uint8_t *esh, PhaseTab tab, double *si) -> pufe_status {
+    if (ctx->n_gitems32 > 0) {
+      k32<<<(unsigned)ctx->n_gitems32, SE_NT, 0, st>>>(D.order, D.gitems32, D.qpoff, D.qdat,
+                                                        D.doff, D.ecol, D.aoff, D.toff32, D.psi32,
+                                                        D.soff, D.smap, S, D.err, esh, tab, si);
+      PUFE_CUDA_TRY(cudaGetLastError());
+    }
+    if (ctx->n_gitems64 > 0) {
+      k64<<<(unsigned)ctx->n_gitems64, SE_NT, 0, st>>>(D.order, D.gitems64, D.qpoff, D.qdat,
+                                                        D.doff, D.ecol, D.aoff, D.toff32, D.psi32,
+                                                        D.soff, D.smap, S, D.err, esh, tab, si);
+      PUFE_CUDA_TRY(cudaGetLastError());
+    }
+    return PUFE_OK;
+  };
+  const pufe_status eg = ph ? gram(k_see_gram<true, 2>, k_see_gram<true, 4>, D.eshift, *ph, Si)
+                            : gram(k_see_gram<false, 2>, k_see_gram<false, 4>, nullptr,
+                                   PhaseTab{}, nullptr);
+  if (eg != PUFE_OK) return eg;
+  if (ctx->n_sitems <= 0) return PUFE_OK;
   const int pm = std::max(1, ctx->max_part_p);
   const int amax = std::max(1, ctx->max_alpha);
   if (amax > 255) return fail(PUFE_EINVAL, "more than 255 enrichments on one element");

@@ -1369,15 +1369,22 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
     };
     std::vector<SItem> items;
     int64_t total = 0;
+    // elements too large for the projection form's stage whose enrichment
+    // slots hold one vertex column each take the Gram form (with more columns
+    // per slot the projections, shared by a slot pair's vertex pairs, cost
+    // several times fewer operations than the Gram products)
+    auto gram = [&](int64_t e) {
+      return ctx->see_stage[e] > SEE_STAGE_MAX_F && n_e[e] - 64 <= (int)ealpha[e].size();
+    };
     for (int64_t k = 0; k < nelem; ++k) {
       const int64_t e = order[k];
       const int64_t A = (int64_t)ealpha[e].size();
-      if (n_e[e] > 64) total += A * (A + 1) / 2 * (qoff[e + 1] - qoff[e]);
+      if (n_e[e] > 64 && !gram(e)) total += A * (A + 1) / 2 * (qoff[e + 1] - qoff[e]);
     }
     const double target = std::max(1.0, (double)total / (4.0 * nsm));
     for (int64_t k = 0; k < nelem; ++k) {
       const int64_t e = order[k];
-      if (n_e[e] <= 64) continue;
+      if (n_e[e] <= 64 || gram(e)) continue;
       const int A = (int)ealpha[e].size(), np = A * (A + 1) / 2;
       const int64_t Q = qoff[e + 1] - qoff[e];
       const int m = std::max(1, std::min(np, (int)std::ceil((double)np * Q / target)));
@@ -1397,6 +1404,35 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
     }
   }
   ctx->n_sitems = (int)(sitems.size() / 3);
+
+  // Gram-form list of the E-E block of S: per element taking that form (see
+  // the E-E list above), the
+  // lower triangle of (row tile, column tile) pairs of its enrichment columns
+  // (tiles of 32 columns when there are at most 32, else 64), each over ranges
+  // of GRAM_QCHUNK points whose partial blocks meet in the FP64 atomics
+  std::vector<int32_t> gitems32, gitems64;
+  for (int64_t k = 0; k < nelem; ++k) {
+    const int64_t e = order[k];
+    if (n_e[e] <= 64 || ctx->see_stage[e] <= SEE_STAGE_MAX_F ||
+        n_e[e] - 64 > (int)ealpha[e].size())
+      continue;
+    const int nE = n_e[e] - 64;
+    const int T = nE <= 32 ? 32 : 64;
+    const int nt = (nE + T - 1) / T;
+    const int32_t Q = q_e[e];
+    std::vector<int32_t> &L = T == 32 ? gitems32 : gitems64;
+    for (int rt = 0; rt < nt; ++rt)
+      for (int ct = 0; ct <= rt; ++ct)
+        for (int32_t qa = 0; qa < Q; qa += GRAM_QCHUNK) {
+          L.push_back((int32_t)k);
+          L.push_back(rt);
+          L.push_back(ct);
+          L.push_back(qa);
+          L.push_back(std::min<int32_t>(Q, qa + GRAM_QCHUNK));
+        }
+  }
+  ctx->n_gitems32 = (int)(gitems32.size() / 5);
+  ctx->n_gitems64 = (int)(gitems64.size() / 5);
 
   // Work list of the strip kernel (64 < n_e <= 128, after the n_e > 128
   // elements in `order`): an element whose cost (points x enrichment columns)
@@ -1546,6 +1582,8 @@ static pufe_status build(const pufe_cell *cell, const pufe_species *species, int
   if (!wsplit.empty() && (st = upload(&D.wsplit, wsplit)) != PUFE_OK) return st;
   if (!titems.empty() && (st = upload(&D.titems, titems)) != PUFE_OK) return st;
   if (!sitems.empty() && (st = upload(&D.sitems, sitems)) != PUFE_OK) return st;
+  if (!gitems32.empty() && (st = upload(&D.gitems32, gitems32)) != PUFE_OK) return st;
+  if (!gitems64.empty() && (st = upload(&D.gitems64, gitems64)) != PUFE_OK) return st;
   if (!citems.empty() && (st = upload(&D.citems, citems)) != PUFE_OK) return st;
   if (!pitems.empty() && (st = upload(&D.pitems, pitems)) != PUFE_OK) return st;
   if ((st = upload(&D.tblk, tblk)) != PUFE_OK) return st;
@@ -1593,7 +1631,7 @@ static void free_device(pufe_ctx *ctx) {
                   D.toff, D.psi, D.psi32, D.qpoff, D.qdat, D.ptab, D.vpad, D.toff32, D.eorig,
                   D.Tfe, D.Sfe, D.S0, D.partoff, D.part_p, D.part_q,
                   D.orb, D.orbf, D.rowptr, D.col, D.soff, D.smap, D.order, D.wsplit,
-                  D.titems, D.sitems, D.citems, D.pitems, D.tblk, D.eeform, D.err};
+                  D.titems, D.sitems, D.gitems32, D.gitems64, D.citems, D.pitems, D.tblk, D.eeform, D.err};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (D.ev_fork) cudaEventDestroy(D.ev_fork);

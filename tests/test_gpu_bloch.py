@@ -227,3 +227,40 @@ def test_mixed_bloch_density_and_adjoint_match_oracle(name):
     ctx.pufe_sync_status()
     assert torch.equal(rho, rho0)
     assert torch.equal(vbar, v0)
+
+
+def test_mixed_bloch_gram_form_of_the_EE_overlap_block():
+    """An h-adaptive CsCl-like cell whose Ce-like elements carry 25 one-vertex
+    enrichment slots on eight 8^3 sub-cells: their cells hold more Psi values
+    than the projection form's shared-memory stage, so the E-E block of S
+    takes the Gram form.  H(k), S(k) of the mixed path against the oracle at
+    k, and S's E-E block against its own largest entry (the mixed bound 5e-6)."""
+    wl = W.workload("c3_cscl_4cube")
+    wl["species"] = [dict(s) for s in wl["species"]]
+    wl["species"][0]["orbitals"] = [o for o in wl["species"][0]["orbitals"] if o[0] >= 3]
+    wl["species"][0]["r_e"] = 0.8
+    m = omesh.Mesh(wl)
+    rules = oq.all_rules(m)
+    assert 4096 in set(np.diff(rules[2]).tolist())
+    ctx = pufe.pufe_build_mesh(wl)
+    ctx.pufe_tabulate(pufe.PUFE_TF32X3)
+    dev = torch.device("cuda:0")
+    k = 2.0 * math.pi / wl["a"] * K_FRAC
+    V = W.random_potential(len(rules[1]), seed=61)
+    mk = lambda: torch.empty(ctx.nnz, dtype=torch.float64, device=dev)
+    Hr, Hi, Sr, Si = mk(), mk(), mk(), mk()
+    ctx.pufe_assemble_HS_bloch(k, torch.tensor(V, device=dev), (Hr, Hi), (Sr, Si),
+                               prec=pufe.PUFE_TF32X3)
+    ctx.pufe_sync_status()
+    rowptr, col = ctx.pattern()
+    N = ctx.n_dof
+    csr = lambda re, im: sp.csr_matrix((re.cpu().numpy() + 1j * im.cpu().numpy(), col, rowptr),
+                                       shape=(N, N))
+    Hg, Sg = csr(Hr, Hi), csr(Sr, Si)
+    Ho, So = ob.assemble_HS_k(m, rules, V, k)
+    assert _rel(Hg, Ho) < TOL_TF32 and _rel(Sg, So) < TOL_TF32, (_rel(Hg, Ho), _rel(Sg, So))
+    nfe = (3 * int(wl["nel"])) ** 3
+    D = (Sg - So).tocsr()[nfe:, nfe:]
+    ee = float(abs(D).max() / abs(So.tocsr()[nfe:, nfe:]).max())
+    print(f"\nGram form at k: S E-E block {ee:.1e}")
+    assert ee < 5e-6
