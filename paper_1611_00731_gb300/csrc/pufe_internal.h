@@ -190,7 +190,7 @@ constexpr int TAB_CHUNK = 2048;
 // slots' Psi values on one (sub)cell exceed it take the Gram form instead
 constexpr int SEE_STAGE_MAX_F = 8192;
 // points per Gram-form work item
-constexpr int GRAM_QCHUNK = 512;
+constexpr int GRAM_QCHUNK = 128;
 
 // ---------------------------------------------------------------------------
 // basis functions shared by host setup and device kernels
